@@ -1,0 +1,335 @@
+"""Benchmark: dipole fields per second of the Cartesian FMM on one GB300.
+
+Workload (one step = the whole hot path over one input): the 10^6-dipole
+ferrofluid (uniform in a 100^3 box, minimum separation 0.5, unit moments),
+p = 6, theta = 0.5, leaf occupancy from Eq. so; tree, lists and D tables
+rebuilt every step (fmm_set_positions), then the field evaluation
+(fmm_field), FP32 bulk with FP64 derivative tensors and FP64 local
+accumulation.  Inputs are resident on the device; L2 is flushed (256 MB
+write) between timed steps.  Also reported: the evaluation alone (tree
+reused), the end-to-end call with host buffers, the roofline of the
+dominant kernel, the accuracy gate, the SM clocks during timing and the CPU
+oracle on a bounded sample.
+
+--impl reference times the CPU oracle (FP64, all host cores) on the same
+workload instead.  Multi-GPU (torchrun): independent replicas, one per rank.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dipole fields/s at RMS err ≤1e-4 (FP32 vs FP64 FMM, 1 GB300); % roofline"
+P, THETA = 6, 0.5
+FP32_LANES_PER_SM, SMS = 128, 152
+# dram read+write bytes per launch from ncu, with the hash of the kernel
+# source they were taken on; reported only while the source is unchanged
+NCU_TRAFFIC = {}
+
+
+def _src_hash(name):
+    with open(os.path.join(ROOT, "paper_0810_0233_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def workload():
+    from paper_0810_0233_gb300 import workloads as W
+    pos, mom = W.ferrofluid()
+    return pos, mom
+
+
+def describe(n, leaf):
+    return {"workload": "ferrofluid: N=%d uniform in [0,100]^3, min separation 0.5, unit moments "
+                        "uniform on the sphere (seed 810235)" % n,
+            "N": n, "p": P, "theta": THETA, "leaf_size": leaf,
+            "precision": "FP32 bulk; FP64 D tensors and FP64 local-expansion accumulation",
+            "step": "tree + lists + D tables + field evaluation (P2M..P2P, unpermute)",
+            "l2": "flushed between timed steps by a 256 MB write"}
+
+
+def cpu_oracle_sample(pos, mom, nleaves=32, seed=11):
+    """The CPU oracle on a bounded sample of the workload: tree, lists and
+    upward pass over every dipole, then the downward pass and near field for
+    `nleaves` random occupied leaves.  Fields/s is extrapolated to the full
+    evaluation: N / (t_setup + t_sample * occupied_leaves / nleaves)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    f = O.OracleFMM(pos, mom, P, THETA, 0.0)
+    f.upward()
+    t_setup = time.perf_counter() - t0
+    leaf_of = f.leaf_of()
+    occ = np.unique(leaf_of)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(occ, size=min(nleaves, len(occ)), replace=False)
+    mask = np.zeros(1 << f.depth, np.uint8)
+    mask[pick] = 1
+    t1 = time.perf_counter()
+    f.downward(mask)
+    t_sample = time.perf_counter() - t1
+    t_full = t_setup + t_sample * len(occ) / len(pick)
+    value = len(pos) / t_full
+    return {"value": value, "unit": "fields/s", "cores": O.threads(), "kind": "oracle",
+            "sample": "FP64 CPU oracle: tree, lists and upward pass over all %d dipoles (%.1f s), "
+                      "downward pass + near field for %d random occupied leaves of %d (%.1f s, "
+                      "%d fields); fields/s extrapolated to all leaves"
+                      % (len(pos), t_setup, len(pick), len(occ), t_sample,
+                         int(np.isin(leaf_of, pick).sum())),
+            "seconds": t_setup + t_sample}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pos, mom = workload()
+    times = []
+    res = None
+    for it in range(args.warmup + args.steps):
+        res = cpu_oracle_sample(pos, mom, nleaves=16, seed=100 + it)
+        if it >= args.warmup:
+            times.append(len(pos) / res["value"])
+    t = float(np.mean(times))
+    value = len(pos) / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "fields/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(len(pos), 0.74 * P * P),
+            "cpu_baseline": {"value": value, "unit": "fields/s", "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="warm-up and a few steps only (for ncu launch lists)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_0810_0233_gb300 import ccfmm as C
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    pos, mom = workload()
+    n = len(pos)
+    pos_d = torch.from_numpy(pos).to(dev)
+    mom_d = torch.from_numpy(mom).to(dev)
+    H_d = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    f = C.FMM(pos_d, mom_d, P, THETA, 0.0, precision=args.precision, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(step, k, w):
+        for _ in range(w):
+            step()
+        barrier()
+        total = 0.0
+        for _ in range(k):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b) / 1e3
+        barrier()
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total
+
+    def step_full():
+        f.set_positions(pos_d, mom_d)
+        f.field(H_d)
+
+    def step_eval():
+        f.field(H_d)
+
+    steps = 2 if args.profile else args.steps
+    warm = 1 if args.profile else args.warmup
+    launches0 = C.kernel_launches()
+    with ClockSampler(local) as clk:
+        t_full = timed(step_full, steps, warm)
+    launches = (C.kernel_launches() - launches0) // (steps + warm)
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": 1e3 * t_full / steps}))
+        return
+    f.reset_stats()
+    t_eval = timed(step_eval, steps, 0)
+    st = f.stats()
+
+    # end to end through the C-ABI with host buffers: H2D of positions and
+    # moments and D2H of the field inside every step
+    pos_h = torch.from_numpy(pos).pin_memory()
+    mom_h = torch.from_numpy(mom).pin_memory()
+    H_h = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        f.set_positions(pos_h, mom_h)
+        f.field(H_h)
+
+    t_e2e = timed(step_e2e, steps, 1)
+
+    value = world * n * steps / t_full
+    line = {"metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * t_full / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": describe(n, st["leaf_target"]),
+            "eval": {"value": world * n * steps / t_eval, "unit": "fields/s",
+                     "ms_per_step": 1e3 * t_eval / steps, "note": "tree and lists reused"},
+            "e2e": {"value": world * n * steps / t_e2e, "unit": "fields/s",
+                    "ms_per_step": 1e3 * t_e2e / steps,
+                    "h2d_bytes_per_step": int(pos.nbytes + mom.nbytes),
+                    "d2h_bytes_per_step": int(n * 3 * 8)},
+            "gpu_launches": int(launches)}
+
+    # roofline of the dominant kernel, from the library's stage events of the
+    # timed evaluations (same stream)
+    K = (P + 1) * (P + 2) * (P + 3) // 6 - 1
+    ms = st["ms_stage"]
+    stages = {"p2p": ms[5], "m2l": ms[2], "p2m": ms[0], "m2m": ms[1], "l2l": ms[3], "l2p": ms[4],
+              "finish": ms[6]}
+    peaks = _peaks()
+    clock = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12  # TFLOP/s
+    flops = {"p2p": 30.0 * st["p2p_pairs"], "m2l": 2.0 * K * K * st["far_pairs"]}
+    dom = max(("p2p", "m2l"), key=lambda k: stages[k])
+    ach = flops[dom] / (stages[dom] * 1e-3) / 1e12
+    src = {"p2p": "p2p.cu", "m2l": "m2l.cu"}[dom]
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes"] if tr and tr.get("src") == _src_hash(src) else None
+    line["roofline"] = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak,
+                        "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
+                        "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clock,
+                        "algorithmic": {"p2p_flop_per_pair": 30, "p2p_pairs": st["p2p_pairs"],
+                                        "m2l_flop_per_far_pair": 2 * K * K,
+                                        "far_pairs": st["far_pairs"]},
+                        "stage_ms": stages,
+                        "other": {k: {"achieved": flops[k] / (stages[k] * 1e-3) / 1e12,
+                                      "frac": flops[k] / (stages[k] * 1e-3) / 1e12 / fp32_peak}
+                                  for k in flops}}
+    line["clocks"] = clk.summary()
+    line["build_ms"] = st["ms_build"]
+
+    if not args.no_accuracy:
+        from paper_0810_0233_gb300 import workloads as W
+        sub = W.subset(n, 10000, 77)
+        Hd = C.direct_field(pos_d, mom_d, targets=torch.from_numpy(sub).to(dev), stream=stream)
+        H = H_d.cpu().numpy()
+        Hd = Hd if isinstance(Hd, np.ndarray) else Hd
+        err_direct = float(np.sqrt(((H[sub] - Hd) ** 2).sum() / (Hd ** 2).sum()))
+        acc = {"rms_vs_direct_10k": err_direct}
+        if args.precision == "mixed":
+            with C.FMM(pos_d, mom_d, P, THETA, 0.0, precision="fp64", stream=stream) as g:
+                H64 = torch.zeros_like(H_d)
+                g.field(H64)
+                torch.cuda.synchronize()
+                acc["rms_vs_fp64_fmm"] = float(torch.sqrt(((H_d - H64) ** 2).sum() /
+                                                          (H64 ** 2).sum()).item())
+        line["accuracy"] = acc
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(pos, mom)
+    f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

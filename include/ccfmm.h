@@ -1,0 +1,200 @@
+/*
+ * ccfmm.h -- C-ABI of libccfmm, a GB300 (sm_103a) implementation of the
+ * Cartesian-coordinates fast multipole method for point dipoles of
+ * W. Zhang and S. Haas, "Adaptation and Performance of the Cartesian
+ * Coordinates Fast Multipole Method for Nanomagnetic Simulations".
+ *
+ * Problem (Sec. III, Eqs. H and H2): N point dipoles m_i at positions r_i,
+ * open boundaries.  The library returns the dipolar field at every dipole,
+ *     H_i = sum_{j != i} [3 (m_j . u_ij) u_ij - m_j] / |r_i - r_j|^3,
+ *     u_ij = (r_i - r_j) / |r_i - r_j|,
+ * and the energy E = -1/2 sum_i m_i . H_i (Appendix, updateField), both in
+ * units where mu0/4pi = 1.  A source located exactly at the field point
+ * contributes nothing (Appendix, updateField).  The fast method replaces the
+ * far part of the sum by the multipole / Taylor expansions of Sec. III.
+ *
+ * Conventions for every entry point:
+ *   - Arrays of 3-vectors are N x 3, row-major, float64 (x0 y0 z0 x1 ...).
+ *   - A pointer may be host memory (pageable or pinned) or device memory of
+ *     the current CUDA device; the kind is detected per call.  Inputs are
+ *     copied into library-owned device memory before the call returns or, for
+ *     device pointers, in stream order on the handle's stream.  Outputs are
+ *     caller-owned.  Host outputs are complete when the call returns; device
+ *     outputs are complete in stream order on the handle's stream.
+ *   - No entry point throws, aborts or exits.  Each returns a ccfmm_status;
+ *     on failure ccfmm_last_error() gives a message for the calling thread.
+ *   - A handle is used by one host thread at a time.
+ *   - All GPU work runs on the handle's stream (fmm_create_ex) or on the
+ *     legacy default stream (fmm_create).
+ */
+#ifndef CCFMM_H
+#define CCFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ccfmm_s *ccfmm_t; /* opaque; owned by the library */
+
+typedef enum {
+    CCFMM_OK = 0,
+    CCFMM_ERR_ARG = -1,     /* invalid argument (sizes, ranges, NaN, null) */
+    CCFMM_ERR_ALLOC = -2,   /* device or host allocation failed */
+    CCFMM_ERR_CUDA = -3,    /* a CUDA call failed; message has the reason */
+    CCFMM_ERR_TIMEOUT = -4, /* a bounded device wait gave up */
+    CCFMM_ERR_STATE = -5    /* call not valid in the handle's state */
+} ccfmm_status;
+
+typedef enum {
+    CCFMM_FP64 = 0,  /* every stage in FP64 */
+    CCFMM_MIXED = 1  /* FP32 bulk; FP64 derivative tensors (Eqs. Dn, Dnr) and
+                        FP64 per-cell local-expansion accumulation */
+} ccfmm_prec;
+
+/* Counters and per-stage times of the last build / evaluation. */
+typedef struct {
+    int32_t depth;            /* L: leaves are at level L (Sec. II) */
+    int32_t depth_capped;     /* 1 if the depth rule wanted L > 24 */
+    int32_t p;                /* expansion order p_m */
+    int32_t precision;        /* ccfmm_prec */
+    double theta;             /* opening-angle threshold alpha_m */
+    double leaf_target;       /* s used by the depth rule */
+    double box[6];            /* lo xyz, hi xyz */
+    double leaf_width[3];     /* widths of a leaf cell */
+    int64_t n;                /* number of dipoles */
+    int64_t nonempty_leaves;
+    int64_t near_leaf_pairs;  /* (leaf, nearPartner) entries, self included */
+    int64_t far_pairs;        /* (cell, Partner) entries over all levels */
+    int64_t p2p_pairs;        /* dipole pairs evaluated by the near field (j != i) */
+    int64_t m2l_tile_entries; /* (target tile, offset) work items of M2L */
+    int64_t far_offsets;      /* distinct (level, integer offset) D tables */
+    double ms_build;          /* tree + lists + D tables of the last build */
+    double ms_eval;           /* mean evaluation time (P2M ... unpermute) */
+    double ms_stage[8];       /* mean stage times: P2M, M2M, M2L, L2L, L2P, P2P,
+                                 finish; [7] = number of evaluations averaged */
+} ccfmm_stats;
+
+/* ------------------------------------------------------------------------
+ * fmm_create: build the tree, the interaction lists and the derivative
+ * tensors for N dipoles (Sec. II steps 0-1, Appendix createPartners) and
+ * upload the moments.
+ *   positions, moments  N x 3 float64, host or device.
+ *   N                   >= 1 and < 2^31.
+ *   p                   expansion order p_m, 1..8 (Sec. III truncation).
+ *   theta               opening-angle threshold alpha_m, 0 < theta < 1
+ *                       (Sec. II: a pair is near iff 2r/d > alpha_m).
+ *   leaf_size           target mean number of dipoles in a leaf, s (Sec. IV);
+ *                       <= 0 selects Eq. so (0.74 p^2 for p > 3, else 8);
+ *                       0 < leaf_size < 1 is rejected.
+ *   out                 receives the handle.
+ * The box is the bounding box widened by 2^-20 of its largest extent on
+ * every side; the precision is CCFMM_MIXED; the stream is the legacy default
+ * stream.  Errors: CCFMM_ERR_ARG for bad sizes, ranges, null or non-finite
+ * input; CCFMM_ERR_ALLOC; CCFMM_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+ccfmm_status fmm_create(const double *positions, const double *moments, int64_t N, int p,
+                        double theta, double leaf_size, ccfmm_t *out);
+
+/* As fmm_create, with
+ *   box     NULL, or {lo_x, lo_y, lo_z, hi_x, hi_y, hi_z} with lo < hi; every
+ *           position must lie in [lo, hi] (else CCFMM_ERR_ARG).  The paper's
+ *           lattice examples use the lattice-cell box (Sec. IV).
+ *   prec    CCFMM_FP64 or CCFMM_MIXED.
+ *   stream  a cudaStream_t of the current device, or NULL for the legacy
+ *           default stream.  The library never synchronises other streams. */
+ccfmm_status fmm_create_ex(const double *positions, const double *moments, int64_t N, int p,
+                           double theta, double leaf_size, const double *box, ccfmm_prec prec,
+                           void *stream, ccfmm_t *out);
+
+/* Rebuild tree, lists and derivative tensors for new positions (and
+ * moments) with the same N, p, theta, leaf_size, box rule and precision,
+ * reusing the handle's device memory where it suffices. */
+ccfmm_status fmm_set_positions(ccfmm_t h, const double *positions, const double *moments);
+
+/* Replace the moments; the tree and lists are kept (positions unchanged). */
+ccfmm_status fmm_set_moments(ccfmm_t h, const double *moments);
+
+/* Evaluate the field at every dipole: upward pass (Eqs. multipolemoments,
+ * momentshift), downward pass (Eqs. taylorcalc, taylorshift), smooth field
+ * (Eq. H) and near field (Eq. H2).  H_out: N x 3 float64 in input order,
+ * host or device, caller-owned; NULL evaluates without copying out (the
+ * result stays in the handle for fmm_energy / fmm_get_field). */
+ccfmm_status fmm_field(ccfmm_t h, double *H_out);
+
+/* Evaluate (as fmm_field) and return E = -1/2 sum_i m_i . H_i in *E_out
+ * (host pointer).  H_out may be NULL. */
+ccfmm_status fmm_field_energy(ccfmm_t h, double *H_out, double *E_out);
+
+/* E of the current moments (evaluates the field first). */
+ccfmm_status fmm_energy(ccfmm_t h, double *E_out);
+
+/* Counters and stage times (host struct).  Stage times are CUDA-event
+ * durations on the handle's stream, averaged over the evaluations since the
+ * last fmm_reset_stats (at most the last 32).  Synchronises the stream. */
+ccfmm_status fmm_stats(ccfmm_t h, ccfmm_stats *out);
+
+/* Start a new averaging window for the stage times of fmm_stats. */
+ccfmm_status fmm_reset_stats(ccfmm_t h);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void fmm_destroy(ccfmm_t h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ccfmm_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Inspection of the build, for verification (tests compare each stage with
+ * an independent implementation).  All outputs are host arrays.
+ * Cell numbering: level l holds 2^l cells keyed 0..2^l-1 by the bits of the
+ * recursive bisection (bit 0 = lower half along the axis split at that
+ * level, most significant bit = level 1); the cell's heap id is 2^l + key.
+ * ---------------------------------------------------------------------- */
+
+/* Split axis (0=x,1=y,2=z) of levels 1..L into axes[0..L). */
+ccfmm_status fmm_get_axes(ccfmm_t h, int32_t *axes);
+
+/* Leaf key of every dipole, input order (N int64). */
+ccfmm_status fmm_get_leaf_of(ccfmm_t h, int64_t *leaf_of);
+
+/* Interaction lists as (cell heap id, partner heap id) pairs.
+ * kind 0: nearPartners of the leaves (self included);
+ * kind 1: Partners (far pairs, M2L) of every cell.
+ * Only non-empty cells appear.  *count receives the number of pairs; pairs
+ * (2 x count int64) is filled when not NULL and capacity >= count. */
+ccfmm_status fmm_get_pairs(ccfmm_t h, int kind, int64_t *pairs, int64_t capacity,
+                           int64_t *count);
+
+/* Multi-index ordering of the library: orders 0..order, T(order) x 3 int32. */
+ccfmm_status ccfmm_multi_indices(int order, int32_t *out);
+
+/* Multipole moments Q (kind 0) or Taylor coefficients V (kind 1) of every
+ * cell after the last evaluation, float64, (2^(L+1)) x T(p) in heap-id rows
+ * (row 0 unused) and library multi-index order.  Q_0 = V_0 = 0. */
+ccfmm_status fmm_get_expansions(ccfmm_t h, int kind, double *out);
+
+/* ------------------------------------------------------------------------
+ * Direct sum (the O(N^2) definition, Eq. H2 as above) on the GPU in FP64,
+ * at the targets tgt[0..nt) (NULL: every dipole, nt = N).  Used to measure
+ * the error of the fast method; not part of the fast path.
+ *   positions, moments  N x 3 float64, host or device.
+ *   H_out               nt x 3 float64, host or device.
+ *   stream              cudaStream_t or NULL.
+ * ---------------------------------------------------------------------- */
+ccfmm_status ccfmm_direct_field(const double *positions, const double *moments, int64_t N,
+                                const int64_t *tgt, int64_t nt, double *H_out, void *stream);
+
+/* Number of kernels the library has launched in this process (all handles,
+ * all threads); a diagnostic for counting GPU work per call. */
+int64_t ccfmm_kernel_launches(void);
+
+/* Eq. so: rule-of-thumb leaf occupancy for order p (8 for p <= 3, else 0.74 p^2). */
+double ccfmm_leaf_size_rule(int p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCFMM_H */

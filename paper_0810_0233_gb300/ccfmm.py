@@ -1,0 +1,267 @@
+"""Thin Python binding of libccfmm (include/ccfmm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays may be NumPy arrays (host) or torch tensors (host or
+CUDA, float64, contiguous); outputs are written to the array the caller
+passes or to a new NumPy array.  The library is loaded on first use and a
+missing ``libccfmm.so`` raises ``RuntimeError``: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libccfmm.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_ALLOC, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5
+FP64, MIXED = 0, 1
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+_int = ctypes.c_int
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("depth", ctypes.c_int32), ("depth_capped", ctypes.c_int32), ("p", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("theta", _dbl), ("leaf_target", _dbl),
+        ("box", _dbl * 6), ("leaf_width", _dbl * 3), ("n", _i64), ("nonempty_leaves", _i64),
+        ("near_leaf_pairs", _i64), ("far_pairs", _i64), ("p2p_pairs", _i64),
+        ("m2l_tile_entries", _i64), ("far_offsets", _i64), ("ms_build", _dbl),
+        ("ms_eval", _dbl), ("ms_stage", _dbl * 8),
+    ]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+class CCFMMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libccfmm status %d: %s" % (status, msg))
+        self.status = status
+
+
+def load():
+    """Load libccfmm.so; raises RuntimeError when it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libccfmm.so not found at %s: run __graft_entry__.build() "
+                               "(nvcc, sm_103a) first; there is no CPU fallback" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "fmm_create": (_int, [_vp, _vp, _i64, _int, _dbl, _dbl, ctypes.POINTER(_vp)]),
+            "fmm_create_ex": (_int, [_vp, _vp, _i64, _int, _dbl, _dbl, _vp, _int, _vp,
+                                     ctypes.POINTER(_vp)]),
+            "fmm_set_positions": (_int, [_vp, _vp, _vp]),
+            "fmm_set_moments": (_int, [_vp, _vp]),
+            "fmm_field": (_int, [_vp, _vp]),
+            "fmm_field_energy": (_int, [_vp, _vp, ctypes.POINTER(_dbl)]),
+            "fmm_energy": (_int, [_vp, ctypes.POINTER(_dbl)]),
+            "fmm_stats": (_int, [_vp, ctypes.POINTER(Stats)]),
+            "fmm_destroy": (None, [_vp]),
+            "fmm_reset_stats": (_int, [_vp]),
+            "ccfmm_last_error": (ctypes.c_char_p, []),
+            "fmm_get_axes": (_int, [_vp, _vp]),
+            "fmm_get_leaf_of": (_int, [_vp, _vp]),
+            "fmm_get_pairs": (_int, [_vp, _int, _vp, _i64, ctypes.POINTER(_i64)]),
+            "ccfmm_multi_indices": (_int, [_int, _vp]),
+            "fmm_get_expansions": (_int, [_vp, _int, _vp]),
+            "ccfmm_direct_field": (_int, [_vp, _vp, _i64, _vp, _i64, _vp, _vp]),
+            "ccfmm_leaf_size_rule": (_dbl, [_int]),
+            "ccfmm_kernel_launches": (_i64, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(st):
+    if st != OK:
+        raise CCFMMError(st, load().ccfmm_last_error().decode(errors="replace"))
+
+
+def _ptr(a, n3=None, dtype=np.float64):
+    """(pointer, keepalive) for a NumPy array or torch tensor."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        want = {np.float64: "torch.float64", np.int64: "torch.int64"}[dtype]
+        if str(a.dtype) != want:
+            raise ValueError("tensor must be %s" % want)
+        if n3 is not None and a.numel() != n3:
+            raise ValueError("expected %d elements, got %d" % (n3, a.numel()))
+        return _vp(a.data_ptr()), a
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    if n3 is not None and arr.size != n3:
+        raise ValueError("expected %d elements, got %d" % (n3, arr.size))
+    return _vp(arr.ctypes.data), arr
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(load().ccfmm_kernel_launches())
+
+
+def leaf_size_rule(p: int) -> float:
+    """Eq. so (the library's copy)."""
+    return load().ccfmm_leaf_size_rule(int(p))
+
+
+def multi_indices(order: int) -> np.ndarray:
+    out = np.zeros(((order + 1) * (order + 2) * (order + 3) // 6, 3), dtype=np.int32)
+    _check(load().ccfmm_multi_indices(int(order), _vp(out.ctypes.data)))
+    return out
+
+
+def direct_field(positions, moments, targets=None, out=None, stream=None):
+    """FP64 GPU direct sum at ``targets`` (all dipoles when None)."""
+    lib = load()
+    n = len(positions) if not hasattr(positions, "shape") else positions.shape[0]
+    pp, k1 = _ptr(positions, 3 * n)
+    pm, k2 = _ptr(moments, 3 * n)
+    if targets is None:
+        pt, k3, nt = None, None, n
+    else:
+        pt, k3 = _ptr(targets, dtype=np.int64)
+        nt = k3.numel() if hasattr(k3, "numel") else k3.size
+    if out is None:
+        out = np.zeros((nt, 3))
+    po, k4 = _ptr(out, 3 * nt)
+    _check(lib.ccfmm_direct_field(pp, pm, n, pt, nt, po, _stream_ptr(stream)))
+    return out
+
+
+class FMM:
+    """One dipole system on the GPU (fmm_create_ex ... fmm_destroy)."""
+
+    def __init__(self, positions, moments, p, theta, leaf_size=0.0, box=None,
+                 precision="mixed", stream=None):
+        lib = load()
+        self._lib = lib
+        n = positions.shape[0]
+        self.n = int(n)
+        self.p = int(p)
+        pp, k1 = _ptr(positions, 3 * n)
+        pm, k2 = _ptr(moments, 3 * n)
+        bx, kb = (None, None) if box is None else _ptr(np.asarray(box, np.float64).reshape(6))
+        prec = {"mixed": MIXED, "fp32": MIXED, "fp64": FP64}[precision]
+        self._stream = stream
+        h = _vp()
+        _check(lib.fmm_create_ex(pp, pm, n, self.p, float(theta), float(leaf_size), bx, prec,
+                                 _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_positions(self, positions, moments):
+        pp, k1 = _ptr(positions, 3 * self.n)
+        pm, k2 = _ptr(moments, 3 * self.n)
+        _check(self._lib.fmm_set_positions(self._h, pp, pm))
+
+    def set_moments(self, moments):
+        pm, k = _ptr(moments, 3 * self.n)
+        _check(self._lib.fmm_set_moments(self._h, pm))
+
+    def field(self, out=None):
+        """H at every dipole, input order (N x 3 float64)."""
+        if out is None:
+            out = np.zeros((self.n, 3))
+        po, k = _ptr(out, 3 * self.n)
+        _check(self._lib.fmm_field(self._h, po))
+        return out
+
+    def evaluate(self):
+        """Run the evaluation and keep the result on the device."""
+        _check(self._lib.fmm_field(self._h, None))
+
+    def field_energy(self, out=None):
+        if out is None:
+            out = np.zeros((self.n, 3))
+        po, k = _ptr(out, 3 * self.n)
+        e = _dbl()
+        _check(self._lib.fmm_field_energy(self._h, po, ctypes.byref(e)))
+        return out, e.value
+
+    def energy(self):
+        e = _dbl()
+        _check(self._lib.fmm_energy(self._h, ctypes.byref(e)))
+        return e.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.fmm_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(self._lib.fmm_reset_stats(self._h))
+
+    def axes(self) -> np.ndarray:
+        d = self.stats()["depth"]
+        out = np.zeros(max(d, 1), dtype=np.int32)
+        _check(self._lib.fmm_get_axes(self._h, _vp(out.ctypes.data)))
+        return out[:d]
+
+    def leaf_of(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int64)
+        _check(self._lib.fmm_get_leaf_of(self._h, _vp(out.ctypes.data)))
+        return out
+
+    def pairs(self, kind: str) -> np.ndarray:
+        k = {"near": 0, "far": 1}[kind]
+        cnt = _i64()
+        _check(self._lib.fmm_get_pairs(self._h, k, None, 0, ctypes.byref(cnt)))
+        out = np.zeros((max(cnt.value, 1), 2), dtype=np.int64)
+        _check(self._lib.fmm_get_pairs(self._h, k, _vp(out.ctypes.data), cnt.value,
+                                       ctypes.byref(cnt)))
+        return out[: cnt.value]
+
+    def expansions(self, kind: str) -> np.ndarray:
+        """Q ("Q") or V ("V") of every cell, (2^(L+1)) x T(p), library order."""
+        k = {"Q": 0, "V": 1}[kind]
+        d = self.stats()["depth"]
+        T = (self.p + 1) * (self.p + 2) * (self.p + 3) // 6
+        out = np.zeros((1 << (d + 1), T))
+        _check(self._lib.fmm_get_expansions(self._h, k, _vp(out.ctypes.data)))
+        return out

@@ -1,0 +1,1006 @@
+// api.cu -- the C-ABI of libccfmm (include/ccfmm.h): handle, validation,
+// device memory, the build (tree, lists, D tables) and the evaluation graph
+// of kernels, with a small number of host synchronisation points during the
+// build (depth choice, per-level sizes, list totals).
+#include "../../include/ccfmm.h"
+#include "ccfmm_dev.cuh"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+using namespace ccfmm;
+
+
+// ---------------------------------------------------------------- launches
+#include <atomic>
+static std::atomic<long long> g_launches(0);
+void ccfmm::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+static ccfmm_status fail(ccfmm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            return fail(CCFMM_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                                     \
+        }                                                                                        \
+    } while (0)
+#define TRY(x)                                                                                   \
+    do {                                                                                         \
+        ccfmm_status s_ = (x);                                                                   \
+        if (s_ != CCFMM_OK) return s_;                                                           \
+    } while (0)
+#define KCHECK() CK(cudaGetLastError())
+
+// test hook: CCFMM_FAIL_ALLOC=k makes the k-th device allocation of the
+// process fail (k >= 1), to exercise the error path without a GPU fault.
+static long long g_alloc_count = 0;
+static long long fail_alloc_at()
+{
+    static long long v = -2;
+    if (v == -2) {
+        const char *e = getenv("CCFMM_FAIL_ALLOC");
+        v = e ? atoll(e) : -1;
+    }
+    return v;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+static ccfmm_status ensure(DevBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.bytes >= bytes) return CCFMM_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    ++g_alloc_count;
+    if (fail_alloc_at() > 0 && g_alloc_count == fail_alloc_at())
+        return fail(CCFMM_ERR_ALLOC, "device allocation of %zu bytes failed (injected)", bytes);
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(CCFMM_ERR_ALLOC, "device allocation of %zu bytes failed: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return CCFMM_OK;
+}
+
+template <typename T> static T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+// small block of device values read back at the build's sync points
+struct Readback {
+    int flags;
+    int hist[LCAP + 1];
+    int ne[LCAP + 1];
+    int near_total[LCAP + 1];
+    int far_total[LCAP + 1];
+    int ent_total;
+    int pad;
+    unsigned long long pairs;
+    double box6[6];
+    double E;
+};
+
+struct LevelPlan {
+    std::vector<int> nearv, farv;  // packed offsets
+    int R[3] = {0, 0, 0};
+    long long cube_base = 0;
+    long long near_bound = 0, far_bound = 0, far_base = 0;
+    int gid_base = 0;
+};
+
+// build events, then a ring of per-evaluation stage events so that stage
+// times of evaluations inside a caller's timed region can be read afterwards
+enum { EV_B0, EV_B1, EV_NB };
+enum { EV_E0, EV_P2M, EV_M2M, EV_M2L, EV_L2L, EV_L2P, EV_P2P, EV_FIN, EV_NE };
+constexpr int EV_RING = 32;
+
+struct ccfmm_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    long long N = 0;
+    int p = 0;
+    double theta = 0.0, leaf_req = 0.0, leaf_target = 0.0;
+    ccfmm_prec prec = CCFMM_MIXED;
+    bool has_box = false;
+    double box_user[6] = {0, 0, 0, 0, 0, 0};
+    int K = 0, KP = 0, TD = 0, ldD = 0;
+    size_t rsz = 4;  // sizeof(real)
+
+    Geom geom;
+    int L = 0;
+    bool capped = false;
+    std::vector<LevelPlan> plan;
+    int n_off = 0, ntiles = 0, max_bits = 0;
+    long long near_leaf_total = 0, far_total = 0, ent_total = 0;
+    bool built = false, evaluated = false;
+    bool leaf_perm_valid = false;
+
+    DevBuf pos, mom, keys, keys2, keys3, idx, idx2, idx3, sorttemp, scantemp;
+    DevBuf geomd, box6, userbox, partial, rb;
+    DevBuf leaf_start, A, B, H;
+    DevBuf cube, nsA, nsB, neA, neB, ncnt, fcnt, fstart;
+    DevBuf far, far_off, far_num, tiles, tcount, tstart, ent_u, ent_src;
+    DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
+    DevBuf Hout, epart;
+    Readback *hrb = nullptr;  // pinned
+    int *near_start_leaf = nullptr;
+    NearEnt *near_leaf = nullptr;
+    cudaEvent_t evb[EV_NB];
+    cudaEvent_t eve[EV_RING][EV_NE];
+    long long n_eval = 0, n_eval_reset = 0;
+    bool ev_ok = false;
+    ccfmm_stats st;
+};
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static ccfmm_status copy_in(ccfmm_t h, DevBuf &dst, const double *src, long long n)
+{
+    TRY(ensure(dst, sizeof(double) * (size_t)n));
+    cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(dst.p, src, sizeof(double) * (size_t)n, k, h->stream));
+    return CCFMM_OK;
+}
+
+double ccfmm_leaf_size_rule(int p) { return p > 3 ? 0.74 * (double)p * (double)p : 8.0; }
+
+// ------------------------------------------------------------ offset plan
+// near iff alpha = 2r/d > theta, r = |w|/2: |w|^2 > theta^2 d^2 (1 + 1e-12);
+// the factor makes a computed tie alpha == theta count as far.
+static bool near_offset(const int o[3], const double w[3], double theta)
+{
+    double W2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double x = (double)o[a] * w[a];
+        d2 += x * x;
+    }
+    return W2 > theta * theta * d2 * (1.0 + 1e-12);
+}
+
+static inline int packo(int x, int y, int z)
+{
+    return ((x + 512) & 1023) | (((y + 512) & 1023) << 10) | (((z + 512) & 1023) << 20);
+}
+static inline void unpacko(int v, int o[3])
+{
+    o[0] = (v & 1023) - 512;
+    o[1] = ((v >> 10) & 1023) - 512;
+    o[2] = ((v >> 20) & 1023) - 512;
+}
+
+// Offsets a near parent pair can produce at each level, classified near/far
+// (createPartners restated on integer offsets of congruent cells).
+static ccfmm_status make_plan(ccfmm_t h)
+{
+    int L = h->L;
+    h->plan.assign(L + 1, LevelPlan());
+    h->plan[0].nearv.push_back(packo(0, 0, 0));
+    long long cube_total = 0;
+    int gid = 0;
+    for (int l = 1; l <= L; ++l) {
+        int s = h->geom.axis[l];
+        std::vector<int> cand;
+        cand.reserve(h->plan[l - 1].nearv.size() * 3);
+        for (int v : h->plan[l - 1].nearv) {
+            int O[3];
+            unpacko(v, O);
+            for (int d = -1; d <= 1; ++d) {
+                int o[3] = {O[0], O[1], O[2]};
+                o[s] = 2 * O[s] + d;
+                for (int a = 0; a < 3; ++a) {
+                    long long nmax = (1ll << h->geom.nsplit[l][a]) - 1;
+                    if (o[a] > nmax || o[a] < -nmax) goto skip;
+                }
+                if (abs(o[0]) > 511 || abs(o[1]) > 511 || abs(o[2]) > 511)
+                    return fail(CCFMM_ERR_ARG, "theta %g too small for this tree: partner offsets "
+                                "exceed 511 cells", h->theta);
+                cand.push_back(packo(o[0], o[1], o[2]));
+            skip:;
+            }
+        }
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        LevelPlan &lp = h->plan[l];
+        for (int v : cand) {
+            int o[3];
+            unpacko(v, o);
+            bool self = o[0] == 0 && o[1] == 0 && o[2] == 0;
+            if (self || near_offset(o, h->geom.w[l], h->theta))
+                lp.nearv.push_back(v);
+            else
+                lp.farv.push_back(v);
+            for (int a = 0; a < 3; ++a) lp.R[a] = std::max(lp.R[a], abs(o[a]));
+        }
+        lp.cube_base = cube_total;
+        cube_total += (long long)(2 * lp.R[0] + 1) * (2 * lp.R[1] + 1) * (2 * lp.R[2] + 1);
+        lp.gid_base = gid;
+        gid += (int)lp.farv.size();
+        if ((long long)lp.farv.size() > (1 << 18))
+            return fail(CCFMM_ERR_ARG, "theta %g too small: %zu far offsets at level %d",
+                        h->theta, lp.farv.size(), l);
+    }
+    if (cube_total > (1ll << 28)) return fail(CCFMM_ERR_ARG, "theta %g too small", h->theta);
+    h->n_off = gid;
+    // concatenated cube tables
+    std::vector<int> cube((size_t)std::max(cube_total, 1ll), OFF_NONE);
+    std::vector<int4> offs((size_t)std::max(gid, 1));
+    for (int l = 1; l <= L; ++l) {
+        LevelPlan &lp = h->plan[l];
+        auto at = [&](const int o[3]) {
+            return lp.cube_base + ((long long)(o[2] + lp.R[2]) * (2 * lp.R[1] + 1) + (o[1] + lp.R[1])) *
+                                      (2 * lp.R[0] + 1) + (o[0] + lp.R[0]);
+        };
+        for (int v : lp.nearv) {
+            int o[3];
+            unpacko(v, o);
+            cube[at(o)] = OFF_NEAR;
+        }
+        for (size_t u = 0; u < lp.farv.size(); ++u) {
+            int o[3];
+            unpacko(lp.farv[u], o);
+            cube[at(o)] = lp.gid_base + (int)u;
+            offs[lp.gid_base + u] = make_int4(o[0], o[1], o[2], l);
+        }
+    }
+    TRY(ensure(h->cube, sizeof(int) * cube.size()));
+    CK(cudaMemcpyAsync(h->cube.p, cube.data(), sizeof(int) * cube.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    TRY(ensure(h->offs, sizeof(int4) * offs.size()));
+    CK(cudaMemcpyAsync(h->offs.p, offs.data(), sizeof(int4) * offs.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    // the host vectors are released when this function returns; make the
+    // pageable copies complete first
+    CK(cudaStreamSynchronize(h->stream));
+    return CCFMM_OK;
+}
+
+// ------------------------------------------------------------ build
+static ccfmm_status check_flags(ccfmm_t h, int flags)
+{
+    if (flags & FLAG_NONFINITE) return fail(CCFMM_ERR_ARG, "non-finite position or moment");
+    if (flags & FLAG_OUTSIDE_BOX) return fail(CCFMM_ERR_ARG, "a position lies outside the box");
+    if (flags & FLAG_OFFSET_RANGE)
+        return fail(CCFMM_ERR_STATE, "internal: partner offset outside the planned range");
+    if (flags & FLAG_LIST_OVERFLOW) return fail(CCFMM_ERR_STATE, "internal: list overflow");
+    (void)h;
+    return CCFMM_OK;
+}
+
+static ccfmm_status build(ccfmm_t h, const double *positions, const double *moments)
+{
+    cudaStream_t s = h->stream;
+    long long N = h->N;
+    h->built = h->evaluated = false;
+    if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_B0], s));
+    TRY(copy_in(h, h->pos, positions, 3 * N));
+    TRY(copy_in(h, h->mom, moments, 3 * N));
+    TRY(ensure(h->rb, sizeof(Readback)));
+    TRY(ensure(h->geomd, sizeof(Geom)));
+    TRY(ensure(h->box6, 6 * sizeof(double)));
+    TRY(ensure(h->partial, 6 * sizeof(double) * 1024));
+    Readback *drb = P<Readback>(h->rb);
+    CK(cudaMemsetAsync(drb, 0, sizeof(Readback), s));
+    const double *ubox = nullptr;
+    if (h->has_box) {
+        TRY(ensure(h->userbox, 6 * sizeof(double)));
+        CK(cudaMemcpyAsync(h->userbox.p, h->box_user, 6 * sizeof(double), cudaMemcpyHostToDevice, s));
+        ubox = P<double>(h->userbox);
+    }
+    launch_check_finite(P<double>(h->mom), 3 * N, &drb->flags, s);
+    launch_bbox(P<double>(h->pos), N, ubox, P<double>(h->box6), P<double>(h->partial), &drb->flags, s);
+    launch_geom(P<double>(h->box6), P<Geom>(h->geomd), s);
+    // keys and sort
+    TRY(ensure(h->keys, sizeof(uint32_t) * N));
+    TRY(ensure(h->keys2, sizeof(uint32_t) * N));
+    TRY(ensure(h->keys3, sizeof(uint32_t) * N));
+    TRY(ensure(h->idx, sizeof(int) * N));
+    TRY(ensure(h->idx2, sizeof(int) * N));
+    TRY(ensure(h->idx3, sizeof(int) * N));
+    TRY(ensure(h->sorttemp, radix_temp_bytes(N)));
+    launch_keys(P<double>(h->pos), N, P<Geom>(h->geomd), P<uint32_t>(h->keys), P<int>(h->idx2),
+                &drb->flags, h->has_box ? 1 : 0, s);
+    // sorted keys -> keys2, permutation (sorted -> input index) -> idx
+    radix_sort(P<uint32_t>(h->keys), P<int>(h->idx2), P<uint32_t>(h->keys2), P<int>(h->idx),
+               P<uint32_t>(h->keys3), P<int>(h->idx3), N, LCAP, h->sorttemp.p, s);
+    launch_depth_hist(P<uint32_t>(h->keys2), N, drb->hist, s);
+    KCHECK();
+    // sync 1: flags, box, depth histogram, geometry
+    CK(cudaMemcpyAsync(h->hrb, drb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&h->geom, h->geomd.p, sizeof(Geom), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    TRY(check_flags(h, h->hrb->flags));
+
+    // depth: L minimising |N / nonempty_L - s| (ties to the smaller L);
+    // N / nonempty_L never increases, so the scan stops once it is <= s
+    {
+        double best = INFINITY;
+        int bestL = 0;
+        long long ne = 1;
+        bool stopped = false;
+        for (int l = 0; l <= LCAP; ++l) {
+            ne += h->hrb->hist[l];
+            double avg = (double)N / (double)ne;
+            double dev = fabs(avg - h->leaf_target);
+            if (dev < best) {
+                best = dev;
+                bestL = l;
+            }
+            if (avg <= h->leaf_target) {
+                stopped = true;
+                break;
+            }
+        }
+        h->L = bestL;
+        h->capped = !stopped;
+        h->geom.L = bestL;
+    }
+    const int L = h->L;
+    const long long nleaf = 1ll << L, ncellp = 1ll << (L + 1);
+
+    TRY(ensure(h->leaf_start, sizeof(int) * (nleaf + 1)));
+    launch_leaf_start(P<uint32_t>(h->keys2), N, L, P<int>(h->leaf_start), s);
+    const size_t rs = h->rsz;
+    TRY(ensure(h->A, 4 * rs * N));
+    TRY(ensure(h->B, 2 * rs * N));
+    TRY(ensure(h->H, 4 * rs * N));
+    if (h->prec == CCFMM_MIXED)
+        launch_sort_points<float>(P<double>(h->pos), P<double>(h->mom), P<int>(h->idx),
+                                  P<uint32_t>(h->keys2), N, P<Geom>(h->geomd), L, P<float4>(h->A),
+                                  P<float2>(h->B), s);
+    else
+        launch_sort_points<double>(P<double>(h->pos), P<double>(h->mom), P<int>(h->idx),
+                                   P<uint32_t>(h->keys2), N, P<Geom>(h->geomd), L,
+                                   P<double4>(h->A), P<double2>(h->B), s);
+    launch_level_counts(P<int>(h->leaf_start), L, drb->ne, s);
+    KCHECK();
+    // sync 2: non-empty cells per level
+    CK(cudaMemcpyAsync(h->hrb, drb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->leaf_perm_valid = true;
+
+    TRY(make_plan(h));
+    long long near_max = 1, far_sum = 0;
+    for (int l = 0; l <= L; ++l) {
+        LevelPlan &lp = h->plan[l];
+        lp.near_bound = (long long)h->hrb->ne[l] * (long long)lp.nearv.size();
+        lp.far_bound = (long long)h->hrb->ne[l] * (long long)lp.farv.size();
+        lp.far_base = far_sum;
+        far_sum += lp.far_bound;
+        near_max = std::max(near_max, lp.near_bound);
+    }
+    if (near_max >= (1ll << 31) || far_sum >= (1ll << 31))
+        return fail(CCFMM_ERR_ARG, "interaction lists too large for 32-bit offsets");
+    TRY(ensure(h->nsA, sizeof(int) * (nleaf + 1)));
+    TRY(ensure(h->nsB, sizeof(int) * (nleaf + 1)));
+    TRY(ensure(h->neA, sizeof(NearEnt) * near_max));
+    TRY(ensure(h->neB, sizeof(NearEnt) * near_max));
+    TRY(ensure(h->ncnt, sizeof(int) * (nleaf + 1)));
+    TRY(ensure(h->fcnt, sizeof(int) * (nleaf + 1)));
+    TRY(ensure(h->fstart, sizeof(int) * (nleaf + 1)));
+    TRY(ensure(h->far, sizeof(FarEnt) * std::max(far_sum, 1ll)));
+    TRY(ensure(h->far_off, sizeof(int) * ncellp));
+    TRY(ensure(h->far_num, sizeof(int) * ncellp));
+    TRY(ensure(h->scantemp, scan_temp_bytes(std::max(nleaf, 4096ll) * 256)));
+    CK(cudaMemsetAsync(h->far_num.p, 0, sizeof(int) * ncellp, s));
+    CK(cudaMemsetAsync(h->far_off.p, 0, sizeof(int) * ncellp, s));
+    // level 0: the root is near itself
+    {
+        int ns0[2] = {0, 1};
+        NearEnt e0 = {0, 0, 0, 0};
+        CK(cudaMemcpyAsync(h->nsA.p, ns0, sizeof(ns0), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->neA.p, &e0, sizeof(e0), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    DevBuf *nsPrev = &h->nsA, *nsCur = &h->nsB, *nePrev = &h->neA, *neCur = &h->neB;
+    for (int l = 1; l <= L; ++l) {
+        LevelPlan &lp = h->plan[l];
+        OffsetCube ci;
+        ci.R[0] = lp.R[0];
+        ci.R[1] = lp.R[1];
+        ci.R[2] = lp.R[2];
+        ci.base = lp.cube_base;
+        long long nc = 1ll << l;
+        launch_list_count(l, P<int>(h->leaf_start), L, P<int>(*nsPrev), P<NearEnt>(*nePrev),
+                          P<int>(h->cube), ci, h->geom.axis[l], P<int>(h->ncnt), P<int>(h->fcnt),
+                          &drb->flags, s);
+        scan_exclusive(P<int>(h->ncnt), P<int>(*nsCur), nc, P<int>(*nsCur) + nc, h->scantemp.p, s);
+        scan_exclusive(P<int>(h->fcnt), P<int>(h->fstart), nc, P<int>(h->fstart) + nc,
+                       h->scantemp.p, s);
+        CK(cudaMemcpyAsync(&drb->near_total[l], P<int>(*nsCur) + nc, sizeof(int),
+                           cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(&drb->far_total[l], P<int>(h->fstart) + nc, sizeof(int),
+                           cudaMemcpyDeviceToDevice, s));
+        launch_list_fill_impl(l, P<int>(h->leaf_start), L, P<int>(*nsPrev), P<NearEnt>(*nePrev),
+                              P<int>(h->cube), ci, h->geom.axis[l], P<int>(*nsCur),
+                              P<NearEnt>(*neCur), P<int>(h->fstart), lp.far_base,
+                              P<FarEnt>(h->far), P<int>(h->far_off), P<int>(h->far_num),
+                              &drb->flags, s);
+        std::swap(nsPrev, nsCur);
+        std::swap(nePrev, neCur);
+    }
+    KCHECK();
+    h->near_start_leaf = P<int>(*nsPrev);
+    h->near_leaf = P<NearEnt>(*nePrev);
+
+    // M2L tiles: TT same-parity cells of one level
+    std::vector<Tile> tiles;
+    h->max_bits = 32;
+    for (int l = 2; l <= L; ++l) {
+        LevelPlan &lp = h->plan[l];
+        if (lp.farv.empty()) continue;
+        long long half = 1ll << (l - 1);
+        for (int par = 0; par < 2; ++par)
+            for (long long f = 0; f < half; f += TT) {
+                Tile t;
+                t.level = l;
+                t.first = (int)f;
+                t.parity = par;
+                t.nt = (int)std::min<long long>(TT, half - f);
+                t.ent_start = t.ent_count = 0;
+                t.nbits = (int)lp.farv.size();
+                t.gid_base = lp.gid_base;
+                tiles.push_back(t);
+            }
+        h->max_bits = std::max(h->max_bits, (int)lp.farv.size());
+    }
+    h->ntiles = (int)tiles.size();
+    TRY(ensure(h->tiles, sizeof(Tile) * std::max<size_t>(tiles.size(), 1)));
+    TRY(ensure(h->tcount, sizeof(int) * (tiles.size() + 1)));
+    TRY(ensure(h->tstart, sizeof(int) * (tiles.size() + 1)));
+    if (h->ntiles) {
+        CK(cudaMemcpyAsync(h->tiles.p, tiles.data(), sizeof(Tile) * tiles.size(),
+                           cudaMemcpyHostToDevice, s));
+        launch_tile_count(P<Tile>(h->tiles), h->ntiles, P<int>(h->far_off), P<int>(h->far_num),
+                          P<FarEnt>(h->far), h->max_bits, P<int>(h->tcount), s);
+        scan_exclusive(P<int>(h->tcount), P<int>(h->tstart), h->ntiles, &drb->ent_total,
+                       h->scantemp.p, s);
+        CK(cudaMemcpyAsync(P<int>(h->tstart) + h->ntiles, &drb->ent_total, sizeof(int),
+                           cudaMemcpyDeviceToDevice, s));
+    }
+    KCHECK();
+    // sync 3: list totals and M2L work size
+    CK(cudaMemcpyAsync(h->hrb, drb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    TRY(check_flags(h, h->hrb->flags));
+    h->near_leaf_total = L == 0 ? 1 : h->hrb->near_total[L];
+    h->far_total = 0;
+    for (int l = 1; l <= L; ++l) h->far_total += h->hrb->far_total[l];
+    h->ent_total = h->ntiles ? h->hrb->ent_total : 0;
+    TRY(ensure(h->ent_u, sizeof(int) * std::max(h->ent_total, 1ll)));
+    TRY(ensure(h->ent_src, sizeof(int) * (size_t)TT * std::max(h->ent_total, 1ll)));
+    if (h->ntiles)
+        launch_tile_fill(P<Tile>(h->tiles), h->ntiles, P<int>(h->tstart), P<int>(h->far_off),
+                         P<int>(h->far_num), P<FarEnt>(h->far), h->max_bits, P<int>(h->ent_u),
+                         P<int>(h->ent_src), s);
+
+    // F table and derivative tensors of every (level, far offset), FP64
+    int O = 2 * h->p;
+    h->TD = nterms(O);
+    h->ldD = ((h->TD + 1 + 3) / 4) * 4;
+    TRY(ensure(h->fdense, ftable_scratch_bytes(O)));
+    TRY(ensure(h->fst, sizeof(int) * (h->TD + 1)));
+    TRY(ensure(h->fq, sizeof(uint16_t) * h->TD * 160));
+    TRY(ensure(h->fval, sizeof(double) * h->TD * 160));
+    launch_ftable(O, P<double>(h->fdense), P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval), s);
+    TRY(ensure(h->D, rs * (size_t)std::max(h->n_off, 1) * h->ldD));
+    if (h->prec == CCFMM_MIXED)
+        launch_dtables<float>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
+                              P<int4>(h->offs), h->n_off, P<Geom>(h->geomd), P<float>(h->D), h->ldD, s);
+    else
+        launch_dtables<double>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
+                               P<int4>(h->offs), h->n_off, P<Geom>(h->geomd), P<double>(h->D), h->ldD, s);
+    TRY(ensure(h->itab, sizeof(uint16_t) * h->KP * h->KP));
+    launch_itable(h->p, h->KP, P<uint16_t>(h->itab), s);
+    TRY(ensure(h->Q, rs * (size_t)ncellp * h->KP));
+    TRY(ensure(h->V, sizeof(double) * (size_t)ncellp * h->KP));
+    TRY(ensure(h->epart, sizeof(double) * ((N + 255) / 256 + 1)));
+    launch_p2p_pair_count(L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf, &drb->pairs, s);
+    KCHECK();
+    if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_B1], s));
+    h->built = true;
+    return CCFMM_OK;
+}
+
+// ------------------------------------------------------------ evaluation
+template <typename real>
+static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
+{
+    typedef typename vec4<real>::t R4;
+    typedef typename vec2<real>::t R2;
+    cudaStream_t s = h->stream;
+    const int L = h->L, p = h->p, KP = h->KP;
+    const long long ncellp = 1ll << (L + 1);
+    bool ev = h->ev_ok;
+    cudaEvent_t *evs = h->eve[h->n_eval % EV_RING];
+    if (ev) CK(cudaEventRecord(evs[EV_E0], s));
+    CK(cudaMemsetAsync(h->V.p, 0, sizeof(double) * (size_t)ncellp * KP, s));
+    launch_p2m<real>(p, KP, L, P<int>(h->leaf_start), P<R4>(h->A), P<R2>(h->B), P<real>(h->Q), s);
+    if (ev) CK(cudaEventRecord(evs[EV_P2M], s));
+    for (int l = L - 1; l >= 0; --l) launch_m2m<real>(p, KP, l, P<Geom>(h->geomd), P<real>(h->Q), s);
+    if (ev) CK(cudaEventRecord(evs[EV_M2M], s));
+    launch_m2l<real>(p, KP, P<Tile>(h->tiles), h->ntiles, P<int>(h->ent_u), P<int>(h->ent_src),
+                     P<real>(h->Q), P<real>(h->D), h->ldD, P<uint16_t>(h->itab), P<Geom>(h->geomd),
+                     P<double>(h->V), s);
+    if (ev) CK(cudaEventRecord(evs[EV_M2L], s));
+    for (int l = 2; l <= L; ++l)
+        launch_l2l(p, KP, l, L, P<Geom>(h->geomd), P<int>(h->leaf_start), P<double>(h->V), s);
+    if (ev) CK(cudaEventRecord(evs[EV_L2L], s));
+    launch_l2p<real>(p, KP, L, P<int>(h->leaf_start), P<R4>(h->A), P<double>(h->V), P<R4>(h->H), s);
+    if (ev) CK(cudaEventRecord(evs[EV_L2P], s));
+    launch_p2p<real>(L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf, P<Geom>(h->geomd),
+                     P<R4>(h->A), P<R2>(h->B), P<R4>(h->H), s);
+    if (ev) CK(cudaEventRecord(evs[EV_P2P], s));
+    Readback *drb = P<Readback>(h->rb);
+    launch_finish<real>(P<R4>(h->H), P<int>(h->idx), P<double>(h->mom), h->N, Hdev,
+                        P<double>(h->epart), &drb->E, s);
+    if (ev) CK(cudaEventRecord(evs[EV_FIN], s));
+    KCHECK();
+    h->evaluated = true;
+    h->n_eval++;
+    return CCFMM_OK;
+}
+
+static ccfmm_status evaluate(ccfmm_t h, double *H_out)
+{
+    if (!h->built) return fail(CCFMM_ERR_STATE, "handle has no tree");
+    double *Hdev = nullptr;
+    bool host_out = false;
+    if (H_out) {
+        if (is_device_ptr(H_out)) {
+            Hdev = H_out;
+        } else {
+            TRY(ensure(h->Hout, sizeof(double) * 3 * h->N));
+            Hdev = P<double>(h->Hout);
+            host_out = true;
+        }
+    }
+    if (h->prec == CCFMM_MIXED)
+        TRY(eval_t<float>(h, Hdev));
+    else
+        TRY(eval_t<double>(h, Hdev));
+    if (host_out) {
+        CK(cudaMemcpyAsync(H_out, Hdev, sizeof(double) * 3 * h->N, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return CCFMM_OK;
+}
+
+// ------------------------------------------------------------ C-ABI
+extern "C" {
+
+const char *ccfmm_last_error(void) { return g_err.c_str(); }
+
+int64_t ccfmm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+ccfmm_status fmm_create_ex(const double *positions, const double *moments, int64_t N, int p,
+                           double theta, double leaf_size, const double *box, ccfmm_prec prec,
+                           void *stream, ccfmm_t *out)
+{
+    g_err.clear();
+    if (!out) return fail(CCFMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!positions || !moments) return fail(CCFMM_ERR_ARG, "positions or moments is NULL");
+    if (N < 1 || N >= (1ll << 31) - 1) return fail(CCFMM_ERR_ARG, "N = %lld out of range", (long long)N);
+    if (p < 1 || p > PMAX) return fail(CCFMM_ERR_ARG, "p = %d out of range 1..%d", p, PMAX);
+    if (!(theta > 0.0 && theta < 1.0)) return fail(CCFMM_ERR_ARG, "theta = %g not in (0, 1)", theta);
+    if (leaf_size != leaf_size || (leaf_size > 0.0 && leaf_size < 1.0) || isinf(leaf_size))
+        return fail(CCFMM_ERR_ARG, "leaf_size = %g invalid", leaf_size);
+    if (prec != CCFMM_FP64 && prec != CCFMM_MIXED) return fail(CCFMM_ERR_ARG, "bad precision");
+    if (box) {
+        for (int a = 0; a < 3; ++a)
+            if (!(isfinite(box[a]) && isfinite(box[3 + a]) && box[a] < box[3 + a]))
+                return fail(CCFMM_ERR_ARG, "box must have finite lo < hi");
+    }
+    ccfmm_t h = new (std::nothrow) ccfmm_s();
+    if (!h) return fail(CCFMM_ERR_ALLOC, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(CCFMM_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    h->stream = (cudaStream_t)stream;
+    h->N = N;
+    h->p = p;
+    h->theta = theta;
+    h->leaf_req = leaf_size;
+    h->leaf_target = leaf_size > 0.0 ? leaf_size : ccfmm_leaf_size_rule(p);
+    h->prec = prec;
+    h->rsz = prec == CCFMM_MIXED ? 4 : 8;
+    h->K = nterms(p) - 1;
+    h->KP = padded_k(p);
+    if (box) {
+        h->has_box = true;
+        memcpy(h->box_user, box, sizeof(h->box_user));
+    }
+    if (cudaMallocHost((void **)&h->hrb, sizeof(Readback)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(CCFMM_ERR_ALLOC, "pinned host allocation failed");
+    }
+    h->ev_ok = true;
+    for (int i = 0; i < EV_NB; ++i)
+        if (cudaEventCreate(&h->evb[i]) != cudaSuccess) h->ev_ok = false;
+    for (int r = 0; r < EV_RING; ++r)
+        for (int i = 0; i < EV_NE; ++i)
+            if (cudaEventCreate(&h->eve[r][i]) != cudaSuccess) h->ev_ok = false;
+    cudaGetLastError();
+    ccfmm_status st = build(h, positions, moments);
+    if (st != CCFMM_OK) {
+        std::string msg = g_err;
+        fmm_destroy(h);
+        g_err = msg;
+        return st;
+    }
+    *out = h;
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_create(const double *positions, const double *moments, int64_t N, int p,
+                        double theta, double leaf_size, ccfmm_t *out)
+{
+    return fmm_create_ex(positions, moments, N, p, theta, leaf_size, nullptr, CCFMM_MIXED, nullptr,
+                         out);
+}
+
+ccfmm_status fmm_set_positions(ccfmm_t h, const double *positions, const double *moments)
+{
+    g_err.clear();
+    if (!h) return fail(CCFMM_ERR_ARG, "handle is NULL");
+    if (!positions || !moments) return fail(CCFMM_ERR_ARG, "positions or moments is NULL");
+    CK(cudaSetDevice(h->device));
+    return build(h, positions, moments);
+}
+
+ccfmm_status fmm_set_moments(ccfmm_t h, const double *moments)
+{
+    g_err.clear();
+    if (!h) return fail(CCFMM_ERR_ARG, "handle is NULL");
+    if (!moments) return fail(CCFMM_ERR_ARG, "moments is NULL");
+    if (!h->built) return fail(CCFMM_ERR_STATE, "handle has no tree");
+    CK(cudaSetDevice(h->device));
+    TRY(copy_in(h, h->mom, moments, 3 * h->N));
+    Readback *drb = P<Readback>(h->rb);
+    CK(cudaMemsetAsync(&drb->flags, 0, sizeof(int), h->stream));
+    launch_check_finite(P<double>(h->mom), 3 * h->N, &drb->flags, h->stream);
+    if (h->prec == CCFMM_MIXED)
+        launch_permute_moments<float>(P<double>(h->mom), P<int>(h->idx), h->N, P<float4>(h->A),
+                                      P<float2>(h->B), h->stream);
+    else
+        launch_permute_moments<double>(P<double>(h->mom), P<int>(h->idx), h->N, P<double4>(h->A),
+                                       P<double2>(h->B), h->stream);
+    KCHECK();
+    int flags = 0;
+    CK(cudaMemcpyAsync(&h->hrb->flags, &drb->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    flags = h->hrb->flags;
+    h->evaluated = false;
+    return check_flags(h, flags);
+}
+
+ccfmm_status fmm_field(ccfmm_t h, double *H_out)
+{
+    g_err.clear();
+    if (!h) return fail(CCFMM_ERR_ARG, "handle is NULL");
+    CK(cudaSetDevice(h->device));
+    return evaluate(h, H_out);
+}
+
+ccfmm_status fmm_field_energy(ccfmm_t h, double *H_out, double *E_out)
+{
+    g_err.clear();
+    if (!h) return fail(CCFMM_ERR_ARG, "handle is NULL");
+    if (!E_out) return fail(CCFMM_ERR_ARG, "E_out is NULL");
+    CK(cudaSetDevice(h->device));
+    TRY(evaluate(h, H_out));
+    Readback *drb = P<Readback>(h->rb);
+    CK(cudaMemcpyAsync(&h->hrb->E, &drb->E, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *E_out = h->hrb->E;
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_energy(ccfmm_t h, double *E_out) { return fmm_field_energy(h, nullptr, E_out); }
+
+ccfmm_status fmm_stats(ccfmm_t h, ccfmm_stats *out)
+{
+    g_err.clear();
+    if (!h || !out) return fail(CCFMM_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    Readback *drb = P<Readback>(h->rb);
+    CK(cudaMemcpy(&h->hrb->pairs, &drb->pairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    ccfmm_stats st;
+    memset(&st, 0, sizeof(st));
+    st.depth = h->L;
+    st.depth_capped = h->capped ? 1 : 0;
+    st.p = h->p;
+    st.precision = (int)h->prec;
+    st.theta = h->theta;
+    st.leaf_target = h->leaf_target;
+    for (int a = 0; a < 3; ++a) {
+        st.box[a] = h->geom.lo[a];
+        st.box[3 + a] = h->geom.lo[a] + h->geom.ext[a];
+        st.leaf_width[a] = h->geom.w[h->L][a];
+    }
+    st.n = h->N;
+    st.nonempty_leaves = h->hrb->ne[h->L];
+    st.near_leaf_pairs = h->near_leaf_total;
+    st.far_pairs = h->far_total;
+    st.p2p_pairs = (int64_t)h->hrb->pairs;
+    st.m2l_tile_entries = h->ent_total;
+    st.far_offsets = h->n_off;
+    if (h->ev_ok) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->evb[EV_B0], h->evb[EV_B1]) == cudaSuccess) st.ms_build = ms;
+        // mean over the evaluations since the last fmm_reset_stats (at most
+        // the last EV_RING of them)
+        long long n = std::min<long long>(h->n_eval - h->n_eval_reset, EV_RING);
+        for (long long j = 0; j < n; ++j) {
+            cudaEvent_t *e = h->eve[(h->n_eval - 1 - j) % EV_RING];
+            if (cudaEventElapsedTime(&ms, e[EV_E0], e[EV_FIN]) == cudaSuccess) st.ms_eval += ms / n;
+            for (int i = 0; i < 7; ++i)
+                if (cudaEventElapsedTime(&ms, e[i], e[i + 1]) == cudaSuccess) st.ms_stage[i] += ms / n;
+        }
+        st.ms_stage[7] = (double)n;
+        cudaGetLastError();
+    }
+    *out = st;
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_reset_stats(ccfmm_t h)
+{
+    g_err.clear();
+    if (!h) return fail(CCFMM_ERR_ARG, "handle is NULL");
+    h->n_eval_reset = h->n_eval;
+    return CCFMM_OK;
+}
+
+void fmm_destroy(ccfmm_t h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&h->pos, &h->mom, &h->keys, &h->keys2, &h->keys3, &h->idx, &h->idx2,
+                      &h->idx3, &h->sorttemp, &h->scantemp, &h->geomd, &h->box6, &h->userbox,
+                      &h->partial, &h->rb, &h->leaf_start, &h->A, &h->B, &h->H, &h->cube,
+                      &h->nsA, &h->nsB, &h->neA, &h->neB, &h->ncnt, &h->fcnt, &h->fstart,
+                      &h->far, &h->far_off, &h->far_num, &h->tiles, &h->tcount, &h->tstart,
+                      &h->ent_u, &h->ent_src, &h->offs, &h->fst, &h->fq, &h->fval, &h->fdense,
+                      &h->D, &h->itab, &h->Q, &h->V, &h->Hout, &h->epart};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (h->hrb) cudaFreeHost(h->hrb);
+    if (h->ev_ok) {
+        for (int i = 0; i < EV_NB; ++i) cudaEventDestroy(h->evb[i]);
+        for (int r = 0; r < EV_RING; ++r)
+            for (int i = 0; i < EV_NE; ++i) cudaEventDestroy(h->eve[r][i]);
+    }
+    cudaGetLastError();
+    delete h;
+}
+
+// ------------------------------------------------------------ inspection
+ccfmm_status fmm_get_axes(ccfmm_t h, int32_t *axes)
+{
+    g_err.clear();
+    if (!h || !axes) return fail(CCFMM_ERR_ARG, "NULL argument");
+    for (int l = 1; l <= h->L; ++l) axes[l - 1] = h->geom.axis[l];
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_get_leaf_of(ccfmm_t h, int64_t *leaf_of)
+{
+    g_err.clear();
+    if (!h || !leaf_of) return fail(CCFMM_ERR_ARG, "NULL argument");
+    if (!h->leaf_perm_valid) return fail(CCFMM_ERR_STATE, "no tree");
+    CK(cudaSetDevice(h->device));
+    std::vector<uint32_t> k(h->N);
+    std::vector<int> perm(h->N);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(k.data(), h->keys2.p, sizeof(uint32_t) * h->N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(perm.data(), h->idx.p, sizeof(int) * h->N, cudaMemcpyDeviceToHost));
+    for (long long s = 0; s < h->N; ++s) leaf_of[perm[s]] = (int64_t)(k[s] >> (LCAP - h->L));
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_get_pairs(ccfmm_t h, int kind, int64_t *pairs, int64_t capacity, int64_t *count)
+{
+    g_err.clear();
+    if (!h || !count) return fail(CCFMM_ERR_ARG, "NULL argument");
+    if (!h->built) return fail(CCFMM_ERR_STATE, "no tree");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    const int L = h->L;
+    std::vector<int64_t> out;
+    if (kind == 0) {
+        long long nleaf = 1ll << L;
+        std::vector<int> ns(nleaf + 1);
+        CK(cudaMemcpy(ns.data(), h->near_start_leaf, sizeof(int) * (nleaf + 1), cudaMemcpyDeviceToHost));
+        std::vector<NearEnt> ent(std::max(ns[nleaf], 1));
+        CK(cudaMemcpy(ent.data(), h->near_leaf, sizeof(NearEnt) * ns[nleaf], cudaMemcpyDeviceToHost));
+        for (long long k = 0; k < nleaf; ++k)
+            for (int e = ns[k]; e < ns[k + 1]; ++e) {
+                out.push_back(nleaf + k);
+                out.push_back(nleaf + ent[e].src);
+            }
+    } else if (kind == 1) {
+        long long ncellp = 1ll << (L + 1);
+        std::vector<int> off(ncellp), num(ncellp);
+        CK(cudaMemcpy(off.data(), h->far_off.p, sizeof(int) * ncellp, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(num.data(), h->far_num.p, sizeof(int) * ncellp, cudaMemcpyDeviceToHost));
+        size_t nfar = h->far.bytes / sizeof(FarEnt);
+        std::vector<FarEnt> far(nfar);
+        CK(cudaMemcpy(far.data(), h->far.p, sizeof(FarEnt) * nfar, cudaMemcpyDeviceToHost));
+        for (long long hid = 1; hid < ncellp; ++hid) {
+            int l = 63 - __builtin_clzll((unsigned long long)hid);
+            for (int e = 0; e < num[hid]; ++e) {
+                out.push_back(hid);
+                out.push_back((1ll << l) + far[off[hid] + e].src);
+            }
+        }
+    } else {
+        return fail(CCFMM_ERR_ARG, "kind must be 0 (near) or 1 (far)");
+    }
+    *count = (int64_t)(out.size() / 2);
+    if (pairs && capacity >= *count) memcpy(pairs, out.data(), sizeof(int64_t) * out.size());
+    return CCFMM_OK;
+}
+
+ccfmm_status ccfmm_multi_indices(int order, int32_t *out)
+{
+    g_err.clear();
+    if (!out || order < 0 || order > 2 * PMAX) return fail(CCFMM_ERR_ARG, "bad argument");
+    for (int t = 0; t < nterms(order); ++t) {
+        int x, y, z;
+        midx_inv(t, x, y, z);
+        out[3 * t] = x;
+        out[3 * t + 1] = y;
+        out[3 * t + 2] = z;
+    }
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_get_expansions(ccfmm_t h, int kind, double *out)
+{
+    g_err.clear();
+    if (!h || !out) return fail(CCFMM_ERR_ARG, "NULL argument");
+    if (!h->evaluated) return fail(CCFMM_ERR_STATE, "no evaluation yet");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    long long ncellp = 1ll << (h->L + 1);
+    int T = nterms(h->p), KP = h->KP, K = h->K;
+    std::vector<double> rows((size_t)ncellp * KP);
+    if (kind == 0) {
+        if (h->prec == CCFMM_MIXED) {
+            std::vector<float> f((size_t)ncellp * KP);
+            CK(cudaMemcpy(f.data(), h->Q.p, sizeof(float) * f.size(), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < f.size(); ++i) rows[i] = f[i];
+        } else {
+            CK(cudaMemcpy(rows.data(), h->Q.p, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost));
+        }
+    } else if (kind == 1) {
+        CK(cudaMemcpy(rows.data(), h->V.p, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost));
+    } else {
+        return fail(CCFMM_ERR_ARG, "kind must be 0 (Q) or 1 (V)");
+    }
+    for (long long r = 0; r < ncellp; ++r) {
+        out[r * T] = 0.0;
+        for (int c = 0; c < K; ++c) out[r * T + c + 1] = r ? rows[r * KP + c] : 0.0;
+    }
+    return CCFMM_OK;
+}
+
+ccfmm_status ccfmm_direct_field(const double *positions, const double *moments, int64_t N,
+                                const int64_t *tgt, int64_t nt, double *H_out, void *stream)
+{
+    g_err.clear();
+    if (!positions || !moments || !H_out) return fail(CCFMM_ERR_ARG, "NULL argument");
+    if (N < 1) return fail(CCFMM_ERR_ARG, "N < 1");
+    if (!tgt) nt = N;
+    if (nt < 1) return fail(CCFMM_ERR_ARG, "nt < 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf pos, mom, tg, out;
+    const double *dp = positions, *dm = moments;
+    const long long *dt = nullptr;
+    double *dout = H_out;
+    ccfmm_status st = CCFMM_OK;
+    auto cleanup = [&]() {
+        cudaFree(pos.p);
+        cudaFree(mom.p);
+        cudaFree(tg.p);
+        cudaFree(out.p);
+    };
+#define DTRY(x)                                                                                  \
+    do {                                                                                         \
+        st = (x);                                                                                \
+        if (st != CCFMM_OK) {                                                                    \
+            cleanup();                                                                           \
+            return st;                                                                           \
+        }                                                                                        \
+    } while (0)
+#define DCK(call)                                                                                \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            cleanup();                                                                           \
+            return fail(CCFMM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));               \
+        }                                                                                        \
+    } while (0)
+    if (!is_device_ptr(positions)) {
+        DTRY(ensure(pos, sizeof(double) * 3 * N));
+        DCK(cudaMemcpyAsync(pos.p, positions, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+        dp = P<double>(pos);
+    }
+    if (!is_device_ptr(moments)) {
+        DTRY(ensure(mom, sizeof(double) * 3 * N));
+        DCK(cudaMemcpyAsync(mom.p, moments, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+        dm = P<double>(mom);
+    }
+    if (tgt) {
+        if (!is_device_ptr(tgt)) {
+            DTRY(ensure(tg, sizeof(long long) * nt));
+            DCK(cudaMemcpyAsync(tg.p, tgt, sizeof(long long) * nt, cudaMemcpyHostToDevice, s));
+            dt = P<long long>(tg);
+        } else {
+            dt = reinterpret_cast<const long long *>(tgt);
+        }
+    }
+    bool host_out = !is_device_ptr(H_out);
+    if (host_out) {
+        DTRY(ensure(out, sizeof(double) * 3 * nt));
+        dout = P<double>(out);
+    }
+    launch_direct(dp, dm, N, dt, nt, dout, s);
+    DCK(cudaGetLastError());
+    if (host_out)
+        DCK(cudaMemcpyAsync(H_out, dout, sizeof(double) * 3 * nt, cudaMemcpyDeviceToHost, s));
+    DCK(cudaStreamSynchronize(s));
+    cleanup();
+#undef DTRY
+#undef DCK
+    return CCFMM_OK;
+}
+
+}  // extern "C"

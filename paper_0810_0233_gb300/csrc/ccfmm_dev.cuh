@@ -1,0 +1,192 @@
+// ccfmm_dev.cuh -- internal declarations shared by the libccfmm translation
+// units (kernels and the host orchestrator).  Not part of the C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ccfmm {
+
+// Depth limit of the complete tree: leaf keys are LCAP-bit integers and the
+// dense per-level arrays hold 2^l cells.
+constexpr int LCAP = 24;
+constexpr int PMAX = 8;
+// Targets per M2L tile (same level, same parity along the last split).
+constexpr int TT = 128;
+
+// ---------------------------------------------------------------------------
+// Multi-indices n = (nx, ny, nz).  The library orders them by total order k,
+// then inside an order by nz ascending, then ny ascending (nx = k - ny - nz).
+// Coefficient arrays Q and V store the multi-indices 1 .. T(p)-1 (Q_0 = 0
+// for dipoles, V_0 never reaches the field) in columns 0 .. K-1, K = T(p)-1,
+// padded with zeros to KP columns.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int nterms(int k) { return k < 0 ? 0 : (k + 1) * (k + 2) * (k + 3) / 6; }
+__host__ __device__ inline int midx(int nx, int ny, int nz)
+{
+    int k = nx + ny + nz;
+    return nterms(k - 1) + nz * (2 * k + 3 - nz) / 2 + ny;
+}
+__host__ __device__ inline void midx_inv(int t, int &nx, int &ny, int &nz)
+{
+    int k = 0;
+    while (nterms(k) <= t) ++k;
+    int r = t - nterms(k - 1);
+    nz = 0;
+    while (r >= k + 1 - nz) {
+        r -= k + 1 - nz;
+        ++nz;
+    }
+    ny = r;
+    nx = k - ny - nz;
+}
+inline int padded_k(int p) { return ((nterms(p) - 1 + 7) / 8) * 8; }
+
+template <typename T> struct vec4;
+template <> struct vec4<float> { typedef float4 t; };
+template <> struct vec4<double> { typedef double4 t; };
+template <typename T> struct vec2;
+template <> struct vec2<float> { typedef float2 t; };
+template <> struct vec2<double> { typedef double2 t; };
+
+// Tree geometry, in device memory.  Level l cells have widths w[l]; h[l] is
+// the cell "radius" (half the diagonal, Sec. II), the scale of the M2L
+// operands at that level.
+struct Geom {
+    double lo[3], ext[3];
+    int axis[LCAP + 1];          // axis[l]: axis halved to make level l (l >= 1)
+    int nsplit[LCAP + 1][3];     // splits of each axis in the first l levels
+    double w[LCAP + 1][3];
+    double h[LCAP + 1];
+    int L;                       // chosen depth (set once known)
+};
+
+// Flag bits written by kernels into the handle's device status word.
+enum : int {
+    FLAG_NONFINITE = 1,
+    FLAG_OUTSIDE_BOX = 2,
+    FLAG_OFFSET_RANGE = 4,
+    FLAG_LIST_OVERFLOW = 8,
+    FLAG_TILE_OVERFLOW = 16
+};
+
+// Per-level table classifying an integer cell offset o = (coords of field
+// cell) - (coords of partner), for offsets inside the cube |o_a| <= R[a]:
+// value >= 0 : a far offset, its global D-table id;
+// NEAR (-2)  : a near offset (self included);
+// NONE (-1)  : not reachable from a near parent pair.
+struct OffsetCube {
+    int R[3];
+    long long base;   // start of this level's table in the concatenated array
+};
+constexpr int OFF_NEAR = -2;
+constexpr int OFF_NONE = -1;
+
+struct NearEnt {   // leaf-level / per-level near entry
+    int src;       // partner key at the same level
+    int ox, oy, oz;
+};
+struct FarEnt {    // far entry of one cell
+    int src;       // partner key
+    int gid;       // global far-offset id (D table row)
+};
+struct Tile {      // M2L work unit
+    int level;
+    int first;     // targets are keys 2*(first+i) + parity, 0 <= i < nt
+    int parity;
+    int nt;
+    int ent_start; // entries [ent_start, ent_start + ent_count)
+    int ent_count;
+    int nbits;     // far offsets of this level (bitmap width)
+    int gid_base;  // first global offset id of this level
+};
+
+// Count of kernel launches issued by the library in this process.
+void note_launch(int n = 1);
+
+// ------------------------------------------------------------------ prims.cu
+size_t scan_temp_bytes(long long n);
+// exclusive scan of n int32 values; total (if not null) written to device
+void scan_exclusive(const int *in, int *out, long long n, int *d_total, void *temp,
+                    cudaStream_t s);
+size_t radix_temp_bytes(long long n);
+// stable sort of (key, value) by the low `bits` bits of key; results in
+// (k_out, v_out)
+void radix_sort(const uint32_t *k_in, const int *v_in, uint32_t *k_out, int *v_out,
+                uint32_t *k_tmp, int *v_tmp, long long n, int bits, void *temp, cudaStream_t s);
+
+// ------------------------------------------------------------------ tree.cu
+void launch_bbox(const double *pos, long long n, const double *user_box, double *d_geom_box,
+                 double *partial, int *d_flags, cudaStream_t s);
+void launch_geom(const double *d_box6, Geom *d_geom, cudaStream_t s);
+void launch_keys(const double *pos, long long n, const Geom *d_geom, uint32_t *keys, int *idx,
+                 int *d_flags, int check_box, cudaStream_t s);
+void launch_depth_hist(const uint32_t *keys_sorted, long long n, int *d_hist, cudaStream_t s);
+void launch_leaf_start(const uint32_t *keys_sorted, long long n, int L, int *leaf_start,
+                       cudaStream_t s);
+template <typename real>
+void launch_sort_points(const double *pos, const double *mom, const int *perm,
+                        const uint32_t *keys_sorted, long long n, const Geom *d_geom, int L,
+                        typename vec4<real>::t *A, typename vec2<real>::t *B, cudaStream_t s);
+template <typename real>
+void launch_permute_moments(const double *mom, const int *perm, long long n,
+                            typename vec4<real>::t *A, typename vec2<real>::t *B,
+                            cudaStream_t s);
+void launch_level_counts(const int *leaf_start, int L, int *d_ne, cudaStream_t s);
+void launch_check_finite(const double *x, long long n, int *d_flags, cudaStream_t s);
+
+// ------------------------------------------------------------------ lists.cu
+void launch_list_count(int level, const int *leaf_start, int L, const int *near_start_prev,
+                       const NearEnt *near_prev, const int *cube, OffsetCube cube_info, int axis,
+                       int *ncnt, int *fcnt, int *d_flags, cudaStream_t s);
+void launch_list_fill_impl(int level, const int *leaf_start, int L, const int *near_start_prev,
+                           const NearEnt *near_prev, const int *cube, OffsetCube cube_info,
+                           int axis, const int *near_start, NearEnt *near_out,
+                           const int *far_start, long long far_base, FarEnt *far_out,
+                           int *far_off, int *far_num, int *d_flags, cudaStream_t s);
+void launch_tile_count(const Tile *tiles, int ntiles, const int *far_off, const int *far_num,
+                       const FarEnt *far, int max_bits, int *counts, cudaStream_t s);
+void launch_tile_fill(Tile *tiles, int ntiles, const int *ent_start, const int *far_off,
+                      const int *far_num, const FarEnt *far, int max_bits, int *ent_u,
+                      int *ent_src, cudaStream_t s);
+
+// ------------------------------------------------------------------ expand.cu
+size_t ftable_scratch_bytes(int order);
+void launch_ftable(int order, double *dense_scratch, int *f_start, uint16_t *f_q, double *f_val,
+                   cudaStream_t s);
+template <typename real>
+void launch_dtables(int p, const int *f_start, const uint16_t *f_q, const double *f_val,
+                    const int4 *offs, int noff, const Geom *d_geom, real *D, int ldD,
+                    cudaStream_t s);
+void launch_itable(int p, int KP, uint16_t *it, cudaStream_t s);
+template <typename real>
+void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
+                const typename vec2<real>::t *B, real *Q, cudaStream_t s);
+template <typename real>
+void launch_m2m(int p, int KP, int level, const Geom *d_geom, real *Q, cudaStream_t s);
+void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *leaf_start,
+                double *V, cudaStream_t s);
+template <typename real>
+void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
+                const double *V, typename vec4<real>::t *H, cudaStream_t s);
+
+// ------------------------------------------------------------------ m2l.cu
+template <typename real>
+void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
+                const int *ent_src, const real *Q, const real *D, int ldD, const uint16_t *it,
+                const Geom *d_geom, double *V, cudaStream_t s);
+
+// ------------------------------------------------------------------ p2p.cu
+template <typename real>
+void launch_p2p(int L, const int *leaf_start, const int *near_start, const NearEnt *near,
+                const Geom *d_geom, const typename vec4<real>::t *A,
+                const typename vec2<real>::t *B, typename vec4<real>::t *H, cudaStream_t s);
+template <typename real>
+void launch_finish(const typename vec4<real>::t *H, const int *perm, const double *mom,
+                   long long n, double *H_out, double *partial, double *d_E, cudaStream_t s);
+void launch_direct(const double *pos, const double *mom, long long n, const long long *tgt,
+                   long long nt, double *H_out, cudaStream_t s);
+void launch_p2p_pair_count(int L, const int *leaf_start, const int *near_start,
+                           const NearEnt *near, unsigned long long *d_count, cudaStream_t s);
+
+}  // namespace ccfmm

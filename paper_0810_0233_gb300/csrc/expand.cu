@@ -1,0 +1,437 @@
+// expand.cu -- Cartesian expansion operators of Sec. III on the GPU:
+//   F table of Eqs. Dn / Dnr and the derivative tensors D_n per distinct
+//   (level, far offset), P2M (Eq. multipolemoments), M2M (Eq. momentshift),
+//   L2L (Eq. taylorshift) and L2P (Eq. H, H = -grad V).
+#include "ccfmm_dev.cuh"
+
+namespace ccfmm {
+
+__device__ __forceinline__ int order_of(int t)
+{
+    int k = 0;
+    while (nterms(k) <= t) ++k;
+    return k;
+}
+
+// position of a multi-index inside its order (library ordering)
+__device__ __forceinline__ int loc_in_order(int nx, int ny, int nz)
+{
+    int k = nx + ny + nz;
+    return nz * (2 * k + 3 - nz) / 2 + ny;
+}
+
+__device__ __forceinline__ unsigned pack3(int a, int b, int c)
+{
+    return (unsigned)a | ((unsigned)b << 5) | ((unsigned)c << 10);
+}
+
+// fill an smem table of the coefficient multi-indices mi[c] = index c+1
+__device__ __forceinline__ void fill_mi(unsigned *mi, int K)
+{
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        int x, y, z;
+        midx_inv(c + 1, x, y, z);
+        mi[c] = pack3(x, y, z);
+    }
+}
+__device__ __forceinline__ int px(unsigned v) { return (int)(v & 31u); }
+__device__ __forceinline__ int py(unsigned v) { return (int)((v >> 5) & 31u); }
+__device__ __forceinline__ int pz(unsigned v) { return (int)((v >> 10) & 31u); }
+
+// ---------------------------------------------------------------------------
+// F table (Eqs. Dn, Dnr).  D_n(r) = r^-(2|n|+1) sum_{|q|=|n|} F_n(q) r^q with
+// D_{n+e_v} = -d/dx_v D_n, so F_{n} is built from F_{n-e_v} (v = first axis
+// with n_v > 0):  F_n(q'+e_v) += (2|m|+1-q'_v) F_m(q'),
+//                 F_n(q'-e_v+2e_mu) += -q'_v F_m(q')  (mu != v),  m = n-e_v,
+// from F_0(0) = 1.  Dense per-order blocks in scratch, then the non-zeros.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline long long ft_block_off(int k)
+{
+    long long off = 0;
+    for (int j = 0; j < k; ++j) {
+        long long t = (long long)(j + 1) * (j + 2) / 2;
+        off += t * t;
+    }
+    return off;
+}
+
+size_t ftable_scratch_bytes(int order) { return (size_t)ft_block_off(order + 1) * sizeof(double); }
+
+__global__ void k_ftable(int O, double *dense, int *f_start, uint16_t *f_q, double *f_val)
+{
+    if (threadIdx.x == 0) dense[0] = 1.0;
+    __syncthreads();
+    for (int k = 1; k <= O; ++k) {
+        int Tk = (k + 1) * (k + 2) / 2, Tm = k * (k + 1) / 2;
+        double *blk = dense + ft_block_off(k);
+        const double *pb = dense + ft_block_off(k - 1);
+        for (int r = threadIdx.x; r < Tk; r += blockDim.x) {
+            int nx, ny, nz;
+            midx_inv(nterms(k - 1) + r, nx, ny, nz);
+            int n[3] = {nx, ny, nz};
+            int v = n[0] > 0 ? 0 : (n[1] > 0 ? 1 : 2);
+            int m[3] = {n[0], n[1], n[2]};
+            m[v] -= 1;
+            int rm = loc_in_order(m[0], m[1], m[2]);
+            double *row = blk + (long long)r * Tk;
+            for (int q = 0; q < Tk; ++q) row[q] = 0.0;
+            for (int j = 0; j < Tm; ++j) {
+                double f = pb[(long long)rm * Tm + j];
+                if (f == 0.0) continue;
+                int qx, qy, qz;
+                midx_inv(nterms(k - 2) + j, qx, qy, qz);
+                int q[3] = {qx, qy, qz};
+                int a[3] = {q[0], q[1], q[2]};
+                a[v] += 1;
+                row[loc_in_order(a[0], a[1], a[2])] += (double)(2 * (k - 1) + 1 - q[v]) * f;
+                if (q[v] > 0) {
+                    for (int mu = 0; mu < 3; ++mu) {
+                        if (mu == v) continue;
+                        int b[3] = {q[0], q[1], q[2]};
+                        b[v] -= 1;
+                        b[mu] += 2;
+                        row[loc_in_order(b[0], b[1], b[2])] += -(double)q[v] * f;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // sparse rows: one row per multi-index t, entries (packed q, F_n(q))
+    int T = nterms(O);
+    if (threadIdx.x == 0) {
+        int nnz = 0;
+        for (int t = 0; t < T; ++t) {
+            f_start[t] = nnz;
+            int k = order_of(t), Tk = (k + 1) * (k + 2) / 2;
+            const double *row = dense + ft_block_off(k) + (long long)(t - nterms(k - 1)) * Tk;
+            for (int q = 0; q < Tk; ++q)
+                if (row[q] != 0.0) ++nnz;
+        }
+        f_start[T] = nnz;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        int k = order_of(t), Tk = (k + 1) * (k + 2) / 2;
+        const double *row = dense + ft_block_off(k) + (long long)(t - nterms(k - 1)) * Tk;
+        int e = f_start[t];
+        for (int q = 0; q < Tk; ++q) {
+            if (row[q] == 0.0) continue;
+            int qx, qy, qz;
+            midx_inv(nterms(k - 1) + q, qx, qy, qz);
+            f_q[e] = (uint16_t)pack3(qx, qy, qz);
+            f_val[e] = row[q];
+            ++e;
+        }
+    }
+}
+
+void launch_ftable(int order, double *dense_scratch, int *f_start, uint16_t *f_q, double *f_val,
+                   cudaStream_t s)
+{
+    note_launch();
+    k_ftable<<<1, 256, 0, s>>>(order, dense_scratch, f_start, f_q, f_val);
+}
+
+// D tensors of one (level, offset) per block, in FP64, at the scaled
+// separation c/h (c = o * w_l, h = cell radius of the level):
+// D~_n = D_n(c/h) = D_n(c) h^(|n|+1).  Row gid of D, with a zero at column
+// T(2p) used for padding.
+template <typename real>
+__global__ void k_dtables(int O, const int *f_start, const uint16_t *f_q, const double *f_val,
+                          const int4 *offs, const Geom *g, real *D, int ldD)
+{
+    __shared__ double xp[2 * PMAX + 1], yp[2 * PMAX + 1], zp[2 * PMAX + 1], rp[2 * PMAX + 1];
+    int gid = blockIdx.x;
+    int4 o = offs[gid];
+    if (threadIdx.x == 0) {
+        int l = o.w;
+        double h = g->h[l];
+        double x = (double)o.x * g->w[l][0] / h;
+        double y = (double)o.y * g->w[l][1] / h;
+        double z = (double)o.z * g->w[l][2] / h;
+        double rinv = 1.0 / sqrt(x * x + y * y + z * z);
+        double r2inv = rinv * rinv;
+        xp[0] = yp[0] = zp[0] = 1.0;
+        rp[0] = rinv;
+        for (int j = 1; j <= O; ++j) {
+            xp[j] = xp[j - 1] * x;
+            yp[j] = yp[j - 1] * y;
+            zp[j] = zp[j - 1] * z;
+            rp[j] = rp[j - 1] * r2inv;
+        }
+    }
+    __syncthreads();
+    int T = nterms(O);
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        double s = 0.0;
+        for (int e = f_start[t]; e < f_start[t + 1]; ++e) {
+            unsigned q = f_q[e];
+            s += f_val[e] * xp[px(q)] * yp[py(q)] * zp[pz(q)];
+        }
+        D[(long long)gid * ldD + t] = (real)(s * rp[order_of(t)]);
+    }
+    for (int t = T + threadIdx.x; t < ldD; t += blockDim.x) D[(long long)gid * ldD + t] = (real)0;
+}
+
+template <typename real>
+void launch_dtables(int p, const int *f_start, const uint16_t *f_q, const double *f_val,
+                    const int4 *offs, int noff, const Geom *d_geom, real *D, int ldD,
+                    cudaStream_t s)
+{
+    if (noff <= 0) return;
+    note_launch();
+    k_dtables<real><<<noff, 128, 0, s>>>(2 * p, f_start, f_q, f_val, offs, d_geom, D, ldD);
+}
+
+// M2L index table: it[k][n] = D-row column of multi-index (n + k) for
+// coefficient columns n, k < K; the zero column T(2p) for padding.
+__global__ void k_itable(int p, int KP, uint16_t *it)
+{
+    int K = nterms(p) - 1, zero = nterms(2 * p);
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= KP * KP) return;
+    int ck = j / KP, cn = j % KP;
+    int v = zero;
+    if (ck < K && cn < K) {
+        int ax, ay, az, bx, by, bz;
+        midx_inv(ck + 1, ax, ay, az);
+        midx_inv(cn + 1, bx, by, bz);
+        v = midx(ax + bx, ay + by, az + bz);
+    }
+    it[j] = (uint16_t)v;
+}
+
+void launch_itable(int p, int KP, uint16_t *it, cudaStream_t s)
+{
+    note_launch();
+    k_itable<<<(KP * KP + 255) / 256, 256, 0, s>>>(p, KP, it);
+}
+
+// ---------------------------------------------------------------------------
+// P2M (Eq. multipolemoments): Q_n = sum_i sum_a m_ia r_i^(n-e_a)/(n-e_a)!
+// about the leaf centre, for every leaf (empty leaves get zeros).
+// ---------------------------------------------------------------------------
+constexpr int P2M_T = 128;
+
+template <typename real>
+__global__ void __launch_bounds__(P2M_T) k_p2m(int p, int KP, int L, const int *leaf_start,
+                                               const typename vec4<real>::t *A,
+                                               const typename vec2<real>::t *B, real *Q)
+{
+    __shared__ real pw[P2M_T][3][PMAX];
+    __shared__ real mm[P2M_T][3];
+    __shared__ unsigned mi[nterms(PMAX)];
+    int K = nterms(p) - 1;
+    fill_mi(mi, K);
+    long long key = blockIdx.x;
+    int s0 = leaf_start[key], s1 = leaf_start[key + 1];
+    real acc[2] = {(real)0, (real)0};
+    for (int base = s0; base < s1; base += P2M_T) {
+        __syncthreads();
+        int i = base + threadIdx.x;
+        if (i < s1) {
+            typename vec4<real>::t a = A[i];
+            typename vec2<real>::t b = B[i];
+            real x[3] = {a.x, a.y, a.z};
+            for (int d = 0; d < 3; ++d) {
+                real v = (real)1;
+                pw[threadIdx.x][d][0] = v;
+                for (int j = 1; j < p; ++j) {
+                    v = v * x[d] / (real)j;
+                    pw[threadIdx.x][d][j] = v;
+                }
+            }
+            mm[threadIdx.x][0] = a.w;
+            mm[threadIdx.x][1] = b.x;
+            mm[threadIdx.x][2] = b.y;
+        }
+        __syncthreads();
+        int cnt = min(P2M_T, s1 - base);
+        for (int r = 0; r < 2; ++r) {
+            int c = threadIdx.x + r * P2M_T;
+            if (c >= K) break;
+            unsigned n = mi[c];
+            int nx = px(n), ny = py(n), nz = pz(n);
+            real s = (real)0;
+            for (int d = 0; d < cnt; ++d) {
+                if (nx > 0) s += mm[d][0] * pw[d][0][nx - 1] * pw[d][1][ny] * pw[d][2][nz];
+                if (ny > 0) s += mm[d][1] * pw[d][0][nx] * pw[d][1][ny - 1] * pw[d][2][nz];
+                if (nz > 0) s += mm[d][2] * pw[d][0][nx] * pw[d][1][ny] * pw[d][2][nz - 1];
+            }
+            acc[r] += s;
+        }
+    }
+    long long hid = (1ll << L) + key;
+    for (int r = 0; r < 2; ++r) {
+        int c = threadIdx.x + r * P2M_T;
+        if (c < KP) Q[hid * KP + c] = c < K ? acc[r] : (real)0;
+    }
+}
+
+template <typename real>
+void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
+                const typename vec2<real>::t *B, real *Q, cudaStream_t s)
+{
+    note_launch();
+    k_p2m<real><<<(unsigned)(1ll << L), P2M_T, 0, s>>>(p, KP, L, leaf_start, A, B, Q);
+}
+
+// ---------------------------------------------------------------------------
+// M2M (Eq. momentshift) from level l+1 to level l.  The child centre sits at
+// -w/2 (bit 0) or +w/2 (bit 1) along the axis split at level l+1, so only
+// shifts along that axis appear: Q_n += sum_j c^j/j! Q^child_{n - j e_s}.
+// ---------------------------------------------------------------------------
+template <typename real>
+__global__ void k_m2m(int p, int KP, int l, const Geom *g, real *Q)
+{
+    int K = nterms(p) - 1;
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long ncell = 1ll << l;
+    if (j >= ncell * KP) return;
+    long long key = j / KP;
+    int c = (int)(j % KP);
+    long long hid = ncell + key;
+    if (c >= K) {
+        Q[hid * KP + c] = (real)0;
+        return;
+    }
+    int n[3];
+    midx_inv(c + 1, n[0], n[1], n[2]);
+    int s = g->axis[l + 1];
+    real hw = (real)(0.5 * g->w[l + 1][s]);
+    real acc = (real)0;
+    for (int b = 0; b < 2; ++b) {
+        real cs = b ? hw : -hw;
+        const real *Qc = Q + (2 * hid + b) * KP;
+        real f = (real)1;
+        for (int t = 0; t <= n[s]; ++t) {
+            int m[3] = {n[0], n[1], n[2]};
+            m[s] -= t;
+            if (m[0] + m[1] + m[2] > 0) acc += f * Qc[midx(m[0], m[1], m[2]) - 1];
+            f = f * cs / (real)(t + 1);
+        }
+    }
+    Q[hid * KP + c] = acc;
+}
+
+template <typename real>
+void launch_m2m(int p, int KP, int level, const Geom *d_geom, real *Q, cudaStream_t s)
+{
+    long long n = (1ll << level) * KP;
+    note_launch();
+    k_m2m<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, KP, level, d_geom, Q);
+}
+
+// ---------------------------------------------------------------------------
+// L2L (Eq. taylorshift) from level l-1 to level l, in FP64:
+// V^child_n += sum_j c^j/j! V^parent_{n + j e_s}, |n| + j <= p.
+// ---------------------------------------------------------------------------
+__global__ void k_l2l(int p, int KP, int l, int L, const Geom *g, const int *leaf_start, double *V)
+{
+    int K = nterms(p) - 1;
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long ncell = 1ll << l;
+    if (j >= ncell * K) return;
+    long long key = j / K;
+    int c = (int)(j % K);
+    int sh = L - l;
+    if (leaf_start[(key + 1) << sh] == leaf_start[key << sh]) return;
+    long long hid = ncell + key;
+    int n[3];
+    midx_inv(c + 1, n[0], n[1], n[2]);
+    int s = g->axis[l];
+    double cs = (key & 1) ? 0.5 * g->w[l][s] : -0.5 * g->w[l][s];
+    const double *Vp = V + (hid >> 1) * KP;
+    int kn = n[0] + n[1] + n[2];
+    double acc = 0.0, f = 1.0;
+    for (int t = 0; t <= p - kn; ++t) {
+        int m[3] = {n[0], n[1], n[2]};
+        m[s] += t;
+        acc += f * Vp[midx(m[0], m[1], m[2]) - 1];
+        f = f * cs / (double)(t + 1);
+    }
+    V[hid * KP + c] += acc;
+}
+
+void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *leaf_start,
+                double *V, cudaStream_t s)
+{
+    long long n = (1ll << level) * (nterms(p) - 1);
+    note_launch();
+    k_l2l<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, KP, level, L, d_geom, leaf_start, V);
+}
+
+// ---------------------------------------------------------------------------
+// L2P (Eq. H with H = -grad V): H_a = -sum_{n_a >= 1} V_n r^(n-e_a)/(n-e_a)!,
+// r relative to the leaf centre.  Writes the smooth field of every dipole.
+// ---------------------------------------------------------------------------
+constexpr int L2P_T = 128;
+
+template <typename real>
+__global__ void __launch_bounds__(L2P_T) k_l2p(int p, int KP, int L, const int *leaf_start,
+                                               const typename vec4<real>::t *A, const double *V,
+                                               typename vec4<real>::t *H)
+{
+    __shared__ real pw[L2P_T][3][PMAX];
+    __shared__ real v[nterms(PMAX)];
+    __shared__ unsigned mi[nterms(PMAX)];
+    int K = nterms(p) - 1;
+    long long key = blockIdx.x;
+    int s0 = leaf_start[key], s1 = leaf_start[key + 1];
+    if (s0 == s1) return;
+    fill_mi(mi, K);
+    long long hid = (1ll << L) + key;
+    for (int c = threadIdx.x; c < K; c += blockDim.x) v[c] = (real)V[hid * KP + c];
+    __syncthreads();
+    for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        typename vec4<real>::t a = A[i];
+        real x[3] = {a.x, a.y, a.z};
+        for (int d = 0; d < 3; ++d) {
+            real t = (real)1;
+            pw[threadIdx.x][d][0] = t;
+            for (int j = 1; j < p; ++j) {
+                t = t * x[d] / (real)j;
+                pw[threadIdx.x][d][j] = t;
+            }
+        }
+        real h[3] = {(real)0, (real)0, (real)0};
+        for (int c = 0; c < K; ++c) {
+            unsigned n = mi[c];
+            int nx = px(n), ny = py(n), nz = pz(n);
+            real vc = v[c];
+            if (nx > 0) h[0] -= vc * pw[threadIdx.x][0][nx - 1] * pw[threadIdx.x][1][ny] * pw[threadIdx.x][2][nz];
+            if (ny > 0) h[1] -= vc * pw[threadIdx.x][0][nx] * pw[threadIdx.x][1][ny - 1] * pw[threadIdx.x][2][nz];
+            if (nz > 0) h[2] -= vc * pw[threadIdx.x][0][nx] * pw[threadIdx.x][1][ny] * pw[threadIdx.x][2][nz - 1];
+        }
+        typename vec4<real>::t out;
+        out.x = h[0];
+        out.y = h[1];
+        out.z = h[2];
+        out.w = (real)0;
+        H[i] = out;
+    }
+}
+
+template <typename real>
+void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
+                const double *V, typename vec4<real>::t *H, cudaStream_t s)
+{
+    note_launch();
+    k_l2p<real><<<(unsigned)(1ll << L), L2P_T, 0, s>>>(p, KP, L, leaf_start, A, V, H);
+}
+
+#define INST(real)                                                                              \
+    template void launch_dtables<real>(int, const int *, const uint16_t *, const double *,      \
+                                       const int4 *, int, const Geom *, real *, int,            \
+                                       cudaStream_t);                                           \
+    template void launch_p2m<real>(int, int, int, const int *, const vec4<real>::t *,           \
+                                   const vec2<real>::t *, real *, cudaStream_t);                \
+    template void launch_m2m<real>(int, int, int, const Geom *, real *, cudaStream_t);          \
+    template void launch_l2p<real>(int, int, int, const int *, const vec4<real>::t *,           \
+                                   const double *, vec4<real>::t *, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace ccfmm

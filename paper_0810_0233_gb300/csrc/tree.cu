@@ -1,0 +1,347 @@
+// tree.cu -- recursive-bisection tree on the GPU (Sec. II; Sec. IV rule of
+// thumb): bounding box and split sequence, LCAP-bit bisection keys, the
+// non-empty-leaf histogram that selects the depth, leaf ranges, and the
+// sorted dipole arrays (coordinates relative to the leaf centre).
+#include "ccfmm_dev.cuh"
+
+#include <math.h>
+
+namespace ccfmm {
+
+constexpr int BB_T = 256, BB_BLOCKS = 1024;
+
+__global__ void __launch_bounds__(BB_T) k_bbox_partial(const double *pos, long long n,
+                                                       double *partial, int *flags)
+{
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (long long i = (long long)blockIdx.x * BB_T + threadIdx.x; i < n;
+         i += (long long)gridDim.x * BB_T) {
+        for (int a = 0; a < 3; ++a) {
+            double x = pos[3 * i + a];
+            if (!isfinite(x)) bad = 1;
+            mn[a] = fmin(mn[a], x);
+            mx[a] = fmax(mx[a], x);
+        }
+    }
+    __shared__ double sm[6][BB_T / 32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+        if (lane == 0) {
+            sm[a][warp] = mn[a];
+            sm[3 + a][warp] = mx[a];
+        }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad && lane == 0) atomicOr(flags, FLAG_NONFINITE);
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = sm[threadIdx.x][0];
+        for (int w = 1; w < BB_T / 32; ++w)
+            v = threadIdx.x < 3 ? fmin(v, sm[threadIdx.x][w]) : fmax(v, sm[threadIdx.x][w]);
+        partial[6 * blockIdx.x + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_bbox_final(const double *partial, int nparts, const double *user_box,
+                             double *box6, int *flags)
+{
+    if (threadIdx.x != 0) return;
+    double mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = partial[a];
+        mx[a] = partial[3 + a];
+    }
+    for (int b = 1; b < nparts; ++b)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin(mn[a], partial[6 * b + a]);
+            mx[a] = fmax(mx[a], partial[6 * b + 3 + a]);
+        }
+    if (user_box) {
+        for (int a = 0; a < 3; ++a) {
+            if (mn[a] < user_box[a] || mx[a] > user_box[3 + a]) atomicOr(flags, FLAG_OUTSIDE_BOX);
+            box6[a] = user_box[a];
+            box6[3 + a] = user_box[3 + a];
+        }
+    } else {
+        // bounding box widened by 2^-20 of its largest extent on every side
+        double m = 0.0;
+        for (int a = 0; a < 3; ++a)
+            if (mx[a] - mn[a] > m) m = mx[a] - mn[a];
+        if (m == 0.0) m = 1.0;
+        double pad = m * 9.5367431640625e-07;  // 2^-20
+        for (int a = 0; a < 3; ++a) {
+            box6[a] = mn[a] - pad;
+            box6[3 + a] = mx[a] + pad;
+        }
+    }
+}
+
+// split sequence: at every level halve the currently widest axis, ties x<y<z
+__global__ void k_geom(const double *box6, Geom *g)
+{
+    if (threadIdx.x != 0) return;
+    for (int a = 0; a < 3; ++a) {
+        g->lo[a] = box6[a];
+        g->ext[a] = box6[3 + a] - box6[a];
+        g->nsplit[0][a] = 0;
+        g->w[0][a] = g->ext[a];
+    }
+    g->axis[0] = -1;
+    for (int l = 1; l <= LCAP; ++l) {
+        const double *w = g->w[l - 1];
+        int a = 0;
+        if (w[1] > w[a]) a = 1;
+        if (w[2] > w[a]) a = 2;
+        g->axis[l] = a;
+        for (int b = 0; b < 3; ++b) g->nsplit[l][b] = g->nsplit[l - 1][b] + (b == a);
+        for (int b = 0; b < 3; ++b) g->w[l][b] = ldexp(g->ext[b], -g->nsplit[l][b]);
+    }
+    for (int l = 0; l <= LCAP; ++l) {
+        const double *w = g->w[l];
+        g->h[l] = 0.5 * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    }
+    g->L = -1;
+}
+
+void launch_bbox(const double *pos, long long n, const double *user_box, double *d_box6,
+                 double *partial, int *d_flags, cudaStream_t s)
+{
+    int nb = (int)((n + BB_T - 1) / BB_T);
+    if (nb > BB_BLOCKS) nb = BB_BLOCKS;
+    if (nb < 1) nb = 1;
+    note_launch();
+    k_bbox_partial<<<nb, BB_T, 0, s>>>(pos, n, partial, d_flags);
+    note_launch();
+    k_bbox_final<<<1, 32, 0, s>>>(partial, nb, user_box, d_box6, d_flags);
+}
+
+void launch_geom(const double *d_box6, Geom *d_geom, cudaStream_t s)
+{
+    note_launch();
+    k_geom<<<1, 32, 0, s>>>(d_box6, d_geom);
+}
+
+// LCAP-bit key of each point: leaf coordinate per axis at depth LCAP,
+// c_a = min(floor((x_a - lo_a) * n_a / ext_a), n_a - 1), with the bits of the
+// axes interleaved in split order (level 1 = most significant bit).
+__global__ void k_keys(const double *pos, long long n, const Geom *g, uint32_t *keys, int *idx,
+                       int *flags, int check_box)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long c[3];
+    int nb[3];
+    for (int a = 0; a < 3; ++a) {
+        nb[a] = g->nsplit[LCAP][a];
+        long long na = 1ll << nb[a];
+        double t = (pos[3 * i + a] - g->lo[a]) * (double)na / g->ext[a];
+        long long ca = (long long)floor(t);
+        if (check_box && (t < 0.0 || t > (double)na)) atomicOr(flags, FLAG_OUTSIDE_BOX);
+        if (ca > na - 1) ca = na - 1;
+        if (ca < 0) ca = 0;
+        c[a] = ca;
+    }
+    uint32_t key = 0;
+    int used[3] = {0, 0, 0};
+    for (int j = 1; j <= LCAP; ++j) {
+        int a = g->axis[j];
+        uint32_t bit = (uint32_t)((c[a] >> (nb[a] - 1 - used[a])) & 1);
+        used[a]++;
+        key = (key << 1) | bit;
+    }
+    keys[i] = key;
+    idx[i] = (int)i;
+}
+
+void launch_keys(const double *pos, long long n, const Geom *d_geom, uint32_t *keys, int *idx,
+                 int *d_flags, int check_box, cudaStream_t s)
+{
+    if (n <= 0) return;
+    note_launch();
+    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, d_geom, keys, idx, d_flags,
+                                                       check_box);
+}
+
+// hist[L] = number of adjacent sorted keys whose depth-L prefixes first differ
+// at level L; nonempty leaves at depth L = 1 + sum_{L' <= L} hist[L'].
+__global__ void k_depth_hist(const uint32_t *keys, long long n, int *hist)
+{
+    __shared__ int h[LCAP + 1];
+    if (threadIdx.x <= LCAP) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        uint32_t x = keys[i] ^ keys[i - 1];
+        if (x) {
+            int hb = 31 - __clz(x);
+            atomicAdd(&h[LCAP - hb], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x <= LCAP && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+void launch_depth_hist(const uint32_t *keys_sorted, long long n, int *d_hist, cudaStream_t s)
+{
+    cudaMemsetAsync(d_hist, 0, sizeof(int) * (LCAP + 1), s);
+    long long nb = (n + 255) / 256;
+    if (nb > 4096) nb = 4096;
+    if (nb < 1) nb = 1;
+    note_launch();
+    k_depth_hist<<<(unsigned)nb, 256, 0, s>>>(keys_sorted, n, d_hist);
+}
+
+// leaf_start[k] = first sorted index with leaf key >= k, k = 0 .. 2^L
+__global__ void k_leaf_start(const uint32_t *keys, long long n, int L, int *leaf_start)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    int sh = LCAP - L;
+    long long prev = (i == 0) ? -1 : (long long)(keys[i - 1] >> sh);
+    long long cur = (i == n) ? (1ll << L) : (long long)(keys[i] >> sh);
+    for (long long k = prev + 1; k <= cur; ++k) leaf_start[k] = (int)i;
+}
+
+void launch_leaf_start(const uint32_t *keys_sorted, long long n, int L, int *leaf_start,
+                       cudaStream_t s)
+{
+    note_launch();
+    k_leaf_start<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(keys_sorted, n, L, leaf_start);
+}
+
+__device__ __forceinline__ void leaf_coords(const Geom *g, int L, uint32_t k, int ic[3])
+{
+    ic[0] = ic[1] = ic[2] = 0;
+    for (int j = 1; j <= L; ++j) {
+        int bit = (int)((k >> (L - j)) & 1u);
+        int a = g->axis[j];
+        ic[a] = 2 * ic[a] + bit;
+    }
+}
+
+template <typename real>
+__global__ void k_sort_points(const double *pos, const double *mom, const int *perm,
+                              const uint32_t *keys, long long n, const Geom *g, int L,
+                              typename vec4<real>::t *A, typename vec2<real>::t *B)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int i = perm[s];
+    uint32_t k = keys[s] >> (LCAP - L);
+    int ic[3];
+    leaf_coords(g, L, k, ic);
+    double l[3];
+    for (int a = 0; a < 3; ++a) {
+        double c = g->lo[a] + ((double)ic[a] + 0.5) * g->w[L][a];
+        l[a] = pos[3 * (long long)i + a] - c;
+    }
+    typename vec4<real>::t av;
+    av.x = (real)l[0];
+    av.y = (real)l[1];
+    av.z = (real)l[2];
+    av.w = (real)mom[3 * (long long)i];
+    typename vec2<real>::t bv;
+    bv.x = (real)mom[3 * (long long)i + 1];
+    bv.y = (real)mom[3 * (long long)i + 2];
+    A[s] = av;
+    B[s] = bv;
+}
+
+template <typename real>
+void launch_sort_points(const double *pos, const double *mom, const int *perm,
+                        const uint32_t *keys_sorted, long long n, const Geom *d_geom, int L,
+                        typename vec4<real>::t *A, typename vec2<real>::t *B, cudaStream_t s)
+{
+    if (n <= 0) return;
+    note_launch();
+    k_sort_points<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, mom, perm, keys_sorted,
+                                                                    n, d_geom, L, A, B);
+}
+
+template <typename real>
+__global__ void k_permute_moments(const double *mom, const int *perm, long long n,
+                                  typename vec4<real>::t *A, typename vec2<real>::t *B)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    long long i = perm[s];
+    A[s].w = (real)mom[3 * i];
+    typename vec2<real>::t bv;
+    bv.x = (real)mom[3 * i + 1];
+    bv.y = (real)mom[3 * i + 2];
+    B[s] = bv;
+}
+
+template <typename real>
+void launch_permute_moments(const double *mom, const int *perm, long long n,
+                            typename vec4<real>::t *A, typename vec2<real>::t *B, cudaStream_t s)
+{
+    if (n <= 0) return;
+    note_launch();
+    k_permute_moments<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mom, perm, n, A, B);
+}
+
+// non-empty cells per level (levels 0..L), from the leaf ranges
+__global__ void k_level_counts(const int *leaf_start, int L, int *ne)
+{
+    __shared__ int h[LCAP + 1];
+    if (threadIdx.x <= LCAP) h[threadIdx.x] = 0;
+    __syncthreads();
+    long long ncell = (1ll << (L + 1)) - 1;
+    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < ncell;
+         id += (long long)gridDim.x * blockDim.x) {
+        long long hid = id + 1;
+        int l = 63 - __clzll(hid);
+        long long key = hid - (1ll << l);
+        int sh = L - l;
+        if (leaf_start[(key + 1) << sh] > leaf_start[key << sh]) atomicAdd(&h[l], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x <= LCAP && h[threadIdx.x]) atomicAdd(&ne[threadIdx.x], h[threadIdx.x]);
+}
+
+void launch_level_counts(const int *leaf_start, int L, int *d_ne, cudaStream_t s)
+{
+    cudaMemsetAsync(d_ne, 0, sizeof(int) * (LCAP + 1), s);
+    long long ncell = (1ll << (L + 1)) - 1;
+    long long nb = (ncell + 255) / 256;
+    if (nb > 4096) nb = 4096;
+    note_launch();
+    k_level_counts<<<(unsigned)nb, 256, 0, s>>>(leaf_start, L, d_ne);
+}
+
+__global__ void k_check_finite(const double *x, long long n, int *flags)
+{
+    int bad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(x[i])) bad = 1;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, FLAG_NONFINITE);
+}
+
+void launch_check_finite(const double *x, long long n, int *d_flags, cudaStream_t s)
+{
+    long long nb = (n + 255) / 256;
+    if (nb > 2048) nb = 2048;
+    if (nb < 1) nb = 1;
+    note_launch();
+    k_check_finite<<<(unsigned)nb, 256, 0, s>>>(x, n, d_flags);
+}
+
+template void launch_sort_points<float>(const double *, const double *, const int *,
+                                        const uint32_t *, long long, const Geom *, int, float4 *,
+                                        float2 *, cudaStream_t);
+template void launch_sort_points<double>(const double *, const double *, const int *,
+                                         const uint32_t *, long long, const Geom *, int,
+                                         double4 *, double2 *, cudaStream_t);
+template void launch_permute_moments<float>(const double *, const int *, long long, float4 *,
+                                            float2 *, cudaStream_t);
+template void launch_permute_moments<double>(const double *, const int *, long long, double4 *,
+                                             double2 *, cudaStream_t);
+
+}  // namespace ccfmm
