@@ -186,6 +186,33 @@ ccfmm_status fmm_get_expansions(ccfmm_t h, int kind, double *out);
 ccfmm_status ccfmm_direct_field(const double *positions, const double *moments, int64_t N,
                                 const int64_t *tgt, int64_t nt, double *H_out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free direct field and energy.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * code running inside a host application that owns all GPU memory through
+ * its own pool, or a plugin that must not change the device's allocation
+ * state.  It computes what ccfmm_direct_field computes (FP64 O(N^2) field,
+ * j != i and coincident points skipped) and E = -1/2 sum_i m_i . H_i, and
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *   positions, moments  N x 3 float64, DEVICE memory of the current device.
+ *   N                   1 <= N <= 4,194,304; larger N returns CCFMM_ERR_ARG.
+ *   H_out               N x 3 float64, DEVICE memory, caller-owned.
+ *   E_out               one float64, host or device memory.
+ *   stream              cudaStream_t or NULL; the call synchronises it.
+ * Scratch: a fixed array of 32,769 doubles (about 256 KB) in the library's
+ * device memory, held on every GPU that loads the library until the process
+ * exits.  Its device address is looked up on the first call on each device
+ * (with that device current), so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's values;
+ * every value a call reads is written earlier in the same call.  Calls whose
+ * GPU work overlaps (other streams, other host threads) race on the array:
+ * serialise them.  Errors: CCFMM_ERR_ARG for NULL, N out of range or
+ * non-device arrays; CCFMM_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+ccfmm_status ccfmm_direct_field_energy_noalloc(const double *positions, const double *moments,
+                                               int64_t N, double *H_out, double *E_out,
+                                               void *stream);
+
 /* Number of kernels the library has launched in this process (all handles,
  * all threads); a diagnostic for counting GPU work per call. */
 int64_t ccfmm_kernel_launches(void);

@@ -27,6 +27,8 @@ void ccfmm::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relax
 // ---------------------------------------------------------------- errors
 static thread_local std::string g_err;
 
+void ccfmm::set_last_error(const char *msg) { g_err = msg; }
+
 static ccfmm_status fail(ccfmm_status st, const char *fmt, ...)
 {
     char buf[512];

@@ -103,6 +103,8 @@ struct Tile {      // M2L work unit
 
 // Count of kernel launches issued by the library in this process.
 void note_launch(int n = 1);
+// Message returned by ccfmm_last_error() on this thread.
+void set_last_error(const char *msg);
 
 // ------------------------------------------------------------------ prims.cu
 size_t scan_temp_bytes(long long n);
