@@ -99,10 +99,13 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def workload():
+def workload(n=1_000_000):
+    """The ferrofluid; n < 10^6 keeps the density (box side scaled) and is
+    used only for small profiling cases."""
     from paper_0810_0233_gb300 import workloads as W
-    pos, mom = W.ferrofluid()
-    return pos, mom
+    if n == 1_000_000:
+        return W.ferrofluid()
+    return W.ferrofluid(n, side=100.0 * (n / 1e6) ** (1.0 / 3.0))
 
 
 def describe(n, leaf):
@@ -114,7 +117,7 @@ def describe(n, leaf):
             "l2": "flushed between timed steps by a 256 MB write"}
 
 
-def cpu_oracle_sample(pos, mom, nleaves=32, seed=11):
+def cpu_oracle_sample(pos, mom, nleaves=2048, seed=11):
     """The CPU oracle on a bounded sample of the workload: tree, lists and
     upward pass over every dipole, then the downward pass and near field for
     `nleaves` random occupied leaves.  Fields/s is extrapolated to the full
@@ -152,7 +155,7 @@ def run_reference(args):
     times = []
     res = None
     for it in range(args.warmup + args.steps):
-        res = cpu_oracle_sample(pos, mom, nleaves=16, seed=100 + it)
+        res = cpu_oracle_sample(pos, mom, nleaves=256, seed=100 + it)
         if it >= args.warmup:
             times.append(len(pos) / res["value"])
     t = float(np.mean(times))
@@ -179,7 +182,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--profile", action="store_true",
-                    help="warm-up and a few steps only (for ncu launch lists)")
+                    help="one warm-up and two steps only (for ncu launch lists and captures)")
+    ap.add_argument("--n", type=int, default=1_000_000,
+                    help="dipoles; below 10^6 only for small profiling cases")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -197,7 +202,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    pos, mom = workload()
+    pos, mom = workload(args.n)
     n = len(pos)
     pos_d = torch.from_numpy(pos).to(dev)
     mom_d = torch.from_numpy(mom).to(dev)

@@ -143,7 +143,7 @@ struct ccfmm_s {
     std::vector<LevelPlan> plan;
     int n_off = 0, ntiles = 0, max_bits = 0;
     long long near_leaf_total = 0, far_total = 0, ent_total = 0;
-    bool built = false, evaluated = false;
+    bool built = false, evaluated = false, ftable_ready = false;
     bool leaf_perm_valid = false;
 
     DevBuf pos, mom, keys, keys2, keys3, idx, idx2, idx3, sorttemp, scantemp;
@@ -152,7 +152,8 @@ struct ccfmm_s {
     DevBuf cube, nsA, nsB, neA, neB, ncnt, fcnt, fstart;
     DevBuf far, far_off, far_num, tiles, tcount, tstart, ent_u, ent_src;
     DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
-    DevBuf Hout, epart;
+    DevBuf Hout, epart, items, titem0, tnitems, Ps;
+    int nitems = 0;
     Readback *hrb = nullptr;  // pinned
     int *near_start_leaf = nullptr;
     NearEnt *near_leaf = nullptr;
@@ -506,6 +507,35 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     h->far_total = 0;
     for (int l = 1; l <= L; ++l) h->far_total += h->hrb->far_total[l];
     h->ent_total = h->ntiles ? h->hrb->ent_total : 0;
+    // FP32 M2L work items: runs of at most M2L_EC entries of one tile
+    if (h->ntiles) {
+        std::vector<int> ts(h->ntiles + 1);
+        CK(cudaMemcpy(ts.data(), h->tstart.p, sizeof(int) * (h->ntiles + 1), cudaMemcpyDeviceToHost));
+        std::vector<M2LItem> items;
+        std::vector<int> i0(h->ntiles), ni(h->ntiles);
+        for (int t = 0; t < h->ntiles; ++t) {
+            i0[t] = (int)items.size();
+            for (int e = ts[t]; e < ts[t + 1]; e += M2L_EC) {
+                M2LItem it;
+                it.tile = t;
+                it.e0 = e;
+                it.e1 = std::min(e + M2L_EC, ts[t + 1]);
+                items.push_back(it);
+            }
+            ni[t] = (int)items.size() - i0[t];
+        }
+        h->nitems = (int)items.size();
+        TRY(ensure(h->items, sizeof(M2LItem) * std::max<size_t>(items.size(), 1)));
+        TRY(ensure(h->titem0, sizeof(int) * h->ntiles));
+        TRY(ensure(h->tnitems, sizeof(int) * h->ntiles));
+        if (!items.empty())
+            CK(cudaMemcpy(h->items.p, items.data(), sizeof(M2LItem) * items.size(),
+                          cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->titem0.p, i0.data(), sizeof(int) * h->ntiles, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->tnitems.p, ni.data(), sizeof(int) * h->ntiles, cudaMemcpyHostToDevice));
+        if (h->prec == CCFMM_MIXED)
+            TRY(ensure(h->Ps, sizeof(float) * (size_t)std::max(h->nitems, 1) * TT * h->KP));
+    }
     TRY(ensure(h->ent_u, sizeof(int) * std::max(h->ent_total, 1ll)));
     TRY(ensure(h->ent_src, sizeof(int) * (size_t)TT * std::max(h->ent_total, 1ll)));
     if (h->ntiles)
@@ -517,11 +547,18 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     int O = 2 * h->p;
     h->TD = nterms(O);
     h->ldD = ((h->TD + 1 + 3) / 4) * 4;
-    TRY(ensure(h->fdense, ftable_scratch_bytes(O)));
-    TRY(ensure(h->fst, sizeof(int) * (h->TD + 1)));
-    TRY(ensure(h->fq, sizeof(uint16_t) * h->TD * 160));
-    TRY(ensure(h->fval, sizeof(double) * h->TD * 160));
-    launch_ftable(O, P<double>(h->fdense), P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval), s);
+    if (!h->ftable_ready) {
+        // the F table depends on p only: built once per handle
+        TRY(ensure(h->fdense, ftable_scratch_bytes(O)));
+        TRY(ensure(h->fst, sizeof(int) * (h->TD + 1)));
+        TRY(ensure(h->fq, sizeof(uint16_t) * h->TD * 160));
+        TRY(ensure(h->fval, sizeof(double) * h->TD * 160));
+        launch_ftable(O, P<double>(h->fdense), P<int>(h->fst), P<uint16_t>(h->fq),
+                      P<double>(h->fval), s);
+        TRY(ensure(h->itab, sizeof(uint16_t) * h->KP * h->KP));
+        launch_itable(h->p, h->KP, P<uint16_t>(h->itab), s);
+        h->ftable_ready = true;
+    }
     TRY(ensure(h->D, rs * (size_t)std::max(h->n_off, 1) * h->ldD));
     if (h->prec == CCFMM_MIXED)
         launch_dtables<float>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
@@ -529,8 +566,6 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     else
         launch_dtables<double>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
                                P<int4>(h->offs), h->n_off, P<Geom>(h->geomd), P<double>(h->D), h->ldD, s);
-    TRY(ensure(h->itab, sizeof(uint16_t) * h->KP * h->KP));
-    launch_itable(h->p, h->KP, P<uint16_t>(h->itab), s);
     TRY(ensure(h->Q, rs * (size_t)ncellp * h->KP));
     TRY(ensure(h->V, sizeof(double) * (size_t)ncellp * h->KP));
     TRY(ensure(h->epart, sizeof(double) * ((N + 255) / 256 + 1)));
@@ -558,17 +593,22 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
     if (ev) CK(cudaEventRecord(evs[EV_P2M], s));
     for (int l = L - 1; l >= 0; --l) launch_m2m<real>(p, KP, l, P<Geom>(h->geomd), P<real>(h->Q), s);
     if (ev) CK(cudaEventRecord(evs[EV_M2M], s));
-    launch_m2l<real>(p, KP, P<Tile>(h->tiles), h->ntiles, P<int>(h->ent_u), P<int>(h->ent_src),
-                     P<real>(h->Q), P<real>(h->D), h->ldD, P<uint16_t>(h->itab), P<Geom>(h->geomd),
-                     P<double>(h->V), s);
+    if (sizeof(real) == 4 && m2l_f32_supported(KP, h->ldD))
+        launch_m2l_f32(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
+                       P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
+                       P<float>(h->Q), P<float>(h->D), h->ldD, P<uint16_t>(h->itab),
+                       P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V), s);
+    else
+        launch_m2l<real>(p, KP, P<Tile>(h->tiles), h->ntiles, P<int>(h->ent_u), P<int>(h->ent_src),
+                         P<real>(h->Q), P<real>(h->D), h->ldD, P<uint16_t>(h->itab),
+                         P<Geom>(h->geomd), P<double>(h->V), s);
     if (ev) CK(cudaEventRecord(evs[EV_M2L], s));
     for (int l = 2; l <= L; ++l)
         launch_l2l(p, KP, l, L, P<Geom>(h->geomd), P<int>(h->leaf_start), P<double>(h->V), s);
     if (ev) CK(cudaEventRecord(evs[EV_L2L], s));
-    launch_l2p<real>(p, KP, L, P<int>(h->leaf_start), P<R4>(h->A), P<double>(h->V), P<R4>(h->H), s);
     if (ev) CK(cudaEventRecord(evs[EV_L2P], s));
-    launch_p2p<real>(L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf, P<Geom>(h->geomd),
-                     P<R4>(h->A), P<R2>(h->B), P<R4>(h->H), s);
+    launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf,
+                     P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), P<double>(h->V), P<R4>(h->H), s);
     if (ev) CK(cudaEventRecord(evs[EV_P2P], s));
     Readback *drb = P<Readback>(h->rb);
     launch_finish<real>(P<R4>(h->H), P<int>(h->idx), P<double>(h->mom), h->N, Hdev,
@@ -809,7 +849,8 @@ void fmm_destroy(ccfmm_t h)
                       &h->nsA, &h->nsB, &h->neA, &h->neB, &h->ncnt, &h->fcnt, &h->fstart,
                       &h->far, &h->far_off, &h->far_num, &h->tiles, &h->tcount, &h->tstart,
                       &h->ent_u, &h->ent_src, &h->offs, &h->fst, &h->fq, &h->fval, &h->fdense,
-                      &h->D, &h->itab, &h->Q, &h->V, &h->Hout, &h->epart};
+                      &h->D, &h->itab, &h->Q, &h->V, &h->Hout, &h->epart, &h->items,
+                      &h->titem0, &h->tnitems, &h->Ps};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hrb) cudaFreeHost(h->hrb);

@@ -168,11 +168,19 @@ template <typename real>
 void launch_m2m(int p, int KP, int level, const Geom *d_geom, real *Q, cudaStream_t s);
 void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *leaf_start,
                 double *V, cudaStream_t s);
-template <typename real>
-void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
-                const double *V, typename vec4<real>::t *H, cudaStream_t s);
 
 // ------------------------------------------------------------------ m2l.cu
+// FP32 M2L work item: a run of at most M2L_EC consecutive entries of a tile
+constexpr int M2L_EC = 64;
+struct M2LItem {
+    int tile;
+    int e0, e1;
+};
+bool m2l_f32_supported(int KP, int ldD);
+void launch_m2l_f32(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items,
+                    int nitems, const int *tile_item0, const int *tile_nitems, const int *ent_u,
+                    const int *ent_src, const float *Q, const float *D, int ldD,
+                    const uint16_t *it, const Geom *g, float *Ps, double *V, cudaStream_t s);
 template <typename real>
 void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
                 const int *ent_src, const real *Q, const real *D, int ldD, const uint16_t *it,
@@ -180,9 +188,10 @@ void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
 
 // ------------------------------------------------------------------ p2p.cu
 template <typename real>
-void launch_p2p(int L, const int *leaf_start, const int *near_start, const NearEnt *near,
-                const Geom *d_geom, const typename vec4<real>::t *A,
-                const typename vec2<real>::t *B, typename vec4<real>::t *H, cudaStream_t s);
+void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_start,
+                const NearEnt *near, const Geom *d_geom, const typename vec4<real>::t *A,
+                const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
+                cudaStream_t s);
 template <typename real>
 void launch_finish(const typename vec4<real>::t *H, const int *perm, const double *mom,
                    long long n, double *H_out, double *partial, double *d_E, cudaStream_t s);

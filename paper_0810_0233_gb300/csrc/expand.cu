@@ -362,65 +362,6 @@ void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *
     k_l2l<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, KP, level, L, d_geom, leaf_start, V);
 }
 
-// ---------------------------------------------------------------------------
-// L2P (Eq. H with H = -grad V): H_a = -sum_{n_a >= 1} V_n r^(n-e_a)/(n-e_a)!,
-// r relative to the leaf centre.  Writes the smooth field of every dipole.
-// ---------------------------------------------------------------------------
-constexpr int L2P_T = 128;
-
-template <typename real>
-__global__ void __launch_bounds__(L2P_T) k_l2p(int p, int KP, int L, const int *leaf_start,
-                                               const typename vec4<real>::t *A, const double *V,
-                                               typename vec4<real>::t *H)
-{
-    __shared__ real pw[L2P_T][3][PMAX];
-    __shared__ real v[nterms(PMAX)];
-    __shared__ unsigned mi[nterms(PMAX)];
-    int K = nterms(p) - 1;
-    long long key = blockIdx.x;
-    int s0 = leaf_start[key], s1 = leaf_start[key + 1];
-    if (s0 == s1) return;
-    fill_mi(mi, K);
-    long long hid = (1ll << L) + key;
-    for (int c = threadIdx.x; c < K; c += blockDim.x) v[c] = (real)V[hid * KP + c];
-    __syncthreads();
-    for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-        typename vec4<real>::t a = A[i];
-        real x[3] = {a.x, a.y, a.z};
-        for (int d = 0; d < 3; ++d) {
-            real t = (real)1;
-            pw[threadIdx.x][d][0] = t;
-            for (int j = 1; j < p; ++j) {
-                t = t * x[d] / (real)j;
-                pw[threadIdx.x][d][j] = t;
-            }
-        }
-        real h[3] = {(real)0, (real)0, (real)0};
-        for (int c = 0; c < K; ++c) {
-            unsigned n = mi[c];
-            int nx = px(n), ny = py(n), nz = pz(n);
-            real vc = v[c];
-            if (nx > 0) h[0] -= vc * pw[threadIdx.x][0][nx - 1] * pw[threadIdx.x][1][ny] * pw[threadIdx.x][2][nz];
-            if (ny > 0) h[1] -= vc * pw[threadIdx.x][0][nx] * pw[threadIdx.x][1][ny - 1] * pw[threadIdx.x][2][nz];
-            if (nz > 0) h[2] -= vc * pw[threadIdx.x][0][nx] * pw[threadIdx.x][1][ny] * pw[threadIdx.x][2][nz - 1];
-        }
-        typename vec4<real>::t out;
-        out.x = h[0];
-        out.y = h[1];
-        out.z = h[2];
-        out.w = (real)0;
-        H[i] = out;
-    }
-}
-
-template <typename real>
-void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
-                const double *V, typename vec4<real>::t *H, cudaStream_t s)
-{
-    note_launch();
-    k_l2p<real><<<(unsigned)(1ll << L), L2P_T, 0, s>>>(p, KP, L, leaf_start, A, V, H);
-}
-
 #define INST(real)                                                                              \
     template void launch_dtables<real>(int, const int *, const uint16_t *, const double *,      \
                                        const int4 *, int, const Geom *, real *, int,            \
@@ -428,8 +369,7 @@ void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4
     template void launch_p2m<real>(int, int, int, const int *, const vec4<real>::t *,           \
                                    const vec2<real>::t *, real *, cudaStream_t);                \
     template void launch_m2m<real>(int, int, int, const Geom *, real *, cudaStream_t);          \
-    template void launch_l2p<real>(int, int, int, const int *, const vec4<real>::t *,           \
-                                   const double *, vec4<real>::t *, cudaStream_t);
+
 INST(float)
 INST(double)
 #undef INST

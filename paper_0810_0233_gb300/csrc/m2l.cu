@@ -123,6 +123,193 @@ __global__ void __launch_bounds__(KP * 4) k_m2l(int p, const Tile *tiles, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 M2L with split work and asynchronous operand staging.
+//
+// A work item is (tile, a run of at most M2L_EC consecutive entries of that
+// tile); items write FP32 partial sums Ps[item][t][n] that m2l_reduce adds in
+// FP64, in item order, into V.  Per entry the partners' moment rows are
+// copied with cp.async into a row-major buffer Qr[t][k] (row stride KP+4
+// floats: 16-byte aligned rows whose 16-byte reads by consecutive cells fall
+// in distinct banks) while the previous entry is being multiplied; M is
+// rebuilt in shared memory from the entry's D row, M[k][n] = D~_{n+k} h^(1-|k|).
+// Thread (warp w, lane): cells lane + 32i (i < 4) x coefficients 8w..8w+7.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int bytes)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <int KP>
+__global__ void __launch_bounds__(KP * 4) k_m2l_f32(int p, const Tile *tiles, const M2LItem *items,
+                                                    const int *ent_u, const int *ent_src,
+                                                    const float *Q, const float *D, int ldD,
+                                                    const uint16_t *it_g, const Geom *g,
+                                                    float *Ps)
+{
+    constexpr int RS = KP + 4;               // Qr row stride (floats)
+    constexpr int NT = KP * 4;               // threads
+    constexpr int CHQ = KP / 4;              // 16-byte chunks per moment row
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *Qr = reinterpret_cast<float *>(smraw);          // [2][TT][RS]
+    float *Ms = Qr + 2 * TT * RS;                           // [KP][KP]
+    float *Db = Ms + KP * KP;                               // [2][ldD]
+    float *gk = Db + 2 * ldD;                               // [KP]
+    uint16_t *its = reinterpret_cast<uint16_t *>(gk + KP);  // [KP*KP]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const M2LItem item = items[blockIdx.x];
+    const Tile t = tiles[item.tile];
+    const int K = nterms(p) - 1;
+    const double h = g->h[t.level];
+    for (int c = tid; c < KP; c += NT) {
+        double gv = 0.0;
+        if (c < K) {
+            int nx, ny, nz;
+            midx_inv(c + 1, nx, ny, nz);
+            gv = pow(h, (double)(1 - (nx + ny + nz)));
+        }
+        gk[c] = (float)gv;
+    }
+    for (int i = tid; i < KP * KP; i += NT) its[i] = it_g[i];
+
+    auto issue = [&](int row, int buf) {
+        float *dq = Qr + buf * TT * RS;
+        const int *srow = ent_src + (long long)row * TT;
+        for (int i = tid; i < TT * CHQ; i += NT) {
+            int ti = i / CHQ, ch = i - ti * CHQ;
+            int sr = srow[ti];
+            const float *src = sr >= 0 ? Q + (long long)sr * KP + 4 * ch : Q;
+            cp_async16(dq + ti * RS + 4 * ch, src, sr >= 0 ? 16 : 0);
+        }
+        const float *drow = D + (long long)ent_u[row] * ldD;
+        float *dd = Db + buf * ldD;
+        for (int i = tid; i < ldD / 4; i += NT) cp_async16(dd + 4 * i, drow + 4 * i, 16);
+        cp_async_commit();
+    };
+
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    const int ne = item.e1 - item.e0;
+    if (ne > 0) issue(item.e0, 0);
+    for (int e = 0; e < ne; ++e) {
+        const int buf = e & 1;
+        if (e + 1 < ne) {
+            issue(item.e0 + e + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float *Dl = Db + buf * ldD;
+        for (int i = tid; i < KP * KP; i += NT) {
+            int kk = i / KP;
+            Ms[i] = Dl[its[i]] * gk[kk];
+        }
+        __syncthreads();
+        const float *q0 = Qr + buf * TT * RS + lane * RS;
+#pragma unroll 2
+        for (int k4 = 0; k4 < KP; k4 += 4) {
+            float4 qv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) qv[i] = *reinterpret_cast<const float4 *>(q0 + 32 * i * RS + k4);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float *mr = Ms + (k4 + j) * KP + 8 * warp;
+                float4 m0 = *reinterpret_cast<const float4 *>(mr);
+                float4 m1 = *reinterpret_cast<const float4 *>(mr + 4);
+                float mm[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float qj = j == 0 ? qv[i].x : (j == 1 ? qv[i].y : (j == 2 ? qv[i].z : qv[i].w));
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[i][c] += qj * mm[c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    float *out = Ps + (long long)blockIdx.x * TT * KP;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float *o = out + (lane + 32 * i) * KP + 8 * warp;
+        *reinterpret_cast<float4 *>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4 *>(o + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+}
+
+// V_n of each field cell = (-1)^|n| h^-(|n|+2) * sum over the tile's items
+// of the partial sums, in FP64 and in item order.
+__global__ void k_m2l_reduce(int p, int KP, const Tile *tiles, const int *tile_item0,
+                             const int *tile_nitems, const float *Ps, const Geom *g, double *V)
+{
+    const int tile = blockIdx.x;
+    const Tile t = tiles[tile];
+    const int K = nterms(p) - 1;
+    const double h = g->h[t.level];
+    const int i0 = tile_item0[tile], ni = tile_nitems[tile];
+    for (int j = threadIdx.x; j < t.nt * K; j += blockDim.x) {
+        int ti = j / K, n = j - ti * K;
+        double s = 0.0;
+        for (int it = 0; it < ni; ++it) s += (double)Ps[((long long)(i0 + it) * TT + ti) * KP + n];
+        int nx, ny, nz;
+        midx_inv(n + 1, nx, ny, nz);
+        int kn = nx + ny + nz;
+        double en = ((kn & 1) ? -1.0 : 1.0) * pow(h, -(double)(kn + 2));
+        long long hid = (1ll << t.level) + 2ll * (t.first + ti) + t.parity;
+        V[hid * KP + n] = s * en;
+    }
+}
+
+size_t m2l_f32_smem(int KP, int ldD)
+{
+    return sizeof(float) * ((size_t)2 * TT * (KP + 4) + (size_t)KP * KP + 2 * ldD + KP) +
+           sizeof(uint16_t) * (size_t)KP * KP + 64;
+}
+
+bool m2l_f32_supported(int KP, int ldD)
+{
+    return (KP == 8 || KP == 16 || KP == 24 || KP == 40 || KP == 56 || KP == 88 || KP == 120) &&
+           m2l_f32_smem(KP, ldD) <= 227 * 1024;
+}
+
+void launch_m2l_f32(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items,
+                    int nitems, const int *tile_item0, const int *tile_nitems, const int *ent_u,
+                    const int *ent_src, const float *Q, const float *D, int ldD,
+                    const uint16_t *it, const Geom *g, float *Ps, double *V, cudaStream_t s)
+{
+    if (nitems > 0) {
+        size_t smem = m2l_f32_smem(KP, ldD);
+#define M2LF(KPV)                                                                               \
+    case KPV:                                                                                   \
+        cudaFuncSetAttribute(k_m2l_f32<KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                             (int)smem);                                                        \
+        note_launch();                                                                          \
+        k_m2l_f32<KPV><<<nitems, KPV * 4, smem, s>>>(p, tiles, items, ent_u, ent_src, Q, D,    \
+                                                     ldD, it, g, Ps);                           \
+        break;
+        switch (KP) {
+            M2LF(8) M2LF(16) M2LF(24) M2LF(40) M2LF(56) M2LF(88) M2LF(120)
+        default: break;
+        }
+#undef M2LF
+    }
+    if (ntiles > 0) {
+        note_launch();
+        k_m2l_reduce<<<ntiles, 256, 0, s>>>(p, KP, tiles, tile_item0, tile_nitems, Ps, g, V);
+    }
+}
+
 template <typename real, int KP, int KC>
 static void run_m2l(int p, const Tile *tiles, int ntiles, const int *ent_u, const int *ent_src,
                     const real *Q, const real *D, int ldD, const uint16_t *it, const Geom *g,

@@ -6,142 +6,269 @@
 
 namespace ccfmm {
 
-constexpr int P2P_T = 128;
-constexpr int P2P_CH = 1024;  // sources staged in shared memory per batch
+constexpr int P2P_T = 128;    // threads per block
+constexpr int P2P_CH = 1536;  // sources staged in shared memory per batch
+constexpr int P2P_NE = 256;   // near-list entries whose metadata is staged at once
 
-template <typename real> __device__ __forceinline__ real rsqrt_or_zero(real r2);
-template <> __device__ __forceinline__ float rsqrt_or_zero<float>(float r2)
+template <typename real> __device__ __forceinline__ real rsq(real r2);
+template <> __device__ __forceinline__ float rsq<float>(float r2) { return rsqrtf(r2); }
+template <> __device__ __forceinline__ double rsq<double>(double r2) { return 1.0 / sqrt(r2); }
+
+// Field of dipole (m) at s on the target t: h += [3 (m.u) u - m] / r^3,
+// written as h += r^-3 (3 (m.r) r^-2 r - m).  SELF: the source may sit on the
+// target (r = 0), which then contributes nothing.
+template <typename real, bool SELF>
+__device__ __forceinline__ void dip_pair(real tx, real ty, real tz, real sx, real sy, real sz,
+                                         real mx, real my, real mz, real &hx, real &hy, real &hz)
 {
-    return r2 > 0.f ? rsqrtf(r2) : 0.f;
-}
-template <> __device__ __forceinline__ double rsqrt_or_zero<double>(double r2)
-{
-    return r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+    real rx = tx - sx, ry = ty - sy, rz = tz - sz;
+    real r2 = rx * rx + ry * ry + rz * rz;
+    real ri = rsq<real>(r2);
+    if (SELF) ri = r2 > (real)0 ? ri : (real)0;
+    real ri2 = ri * ri;
+    real ri3 = ri2 * ri;
+    real t = (real)3 * (mx * rx + my * ry + mz * rz) * ri2;
+    hx += ri3 * (t * rx - mx);
+    hy += ri3 * (t * ry - my);
+    hz += ri3 * (t * rz - mz);
 }
 
-// One block per target leaf.  Targets are spread over the block's threads
-// with S = floor(128 / nt) stripes of sources per target; source dipoles of
-// the near leaves are staged in shared memory with positions relative to the
-// target leaf centre, s_j = l_j - (c_target - c_source), so every difference
-// is formed between numbers of leaf-size magnitude.  A source located at the
-// field point (the target itself) gives r = 0 and contributes nothing.
+template <typename real, bool SELF>
+__device__ __forceinline__ void p2p_range(const typename vec4<real>::t *sp,
+                                          const typename vec2<real>::t *sm, int j0, int j1,
+                                          real xa, real ya, real za, real xb, real yb, real zb,
+                                          real ha[3], real hb[3])
+{
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        typename vec4<real>::t s = sp[j];
+        typename vec2<real>::t m = sm[j];
+        dip_pair<real, SELF>(xa, ya, za, s.x, s.y, s.z, s.w, m.x, m.y, ha[0], ha[1], ha[2]);
+        dip_pair<real, SELF>(xb, yb, zb, s.x, s.y, s.z, s.w, m.x, m.y, hb[0], hb[1], hb[2]);
+    }
+}
+
+// Smooth field (Eq. H, H = -grad V) of one target from its leaf's Taylor
+// coefficients vs[] (multi-indices mi[]), powers pw[3][PMAX] = x^j / j!.
 template <typename real>
-__global__ void __launch_bounds__(P2P_T) k_p2p(int L, const int *leaf_start,
+__device__ __forceinline__ void l2p_one(int p, int K, const real *vs, const unsigned *mi, real *pw,
+                                        real x, real y, real z, real h[3])
+{
+    real c[3] = {x, y, z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        real t = (real)1;
+        pw[d * PMAX] = t;
+        for (int j = 1; j < p; ++j) {
+            t = t * c[d] / (real)j;
+            pw[d * PMAX + j] = t;
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        unsigned n = mi[k];
+        int nx = (int)(n & 31u), ny = (int)((n >> 5) & 31u), nz = (int)((n >> 10) & 31u);
+        real v = vs[k];
+        if (nx > 0) h[0] -= v * pw[nx - 1] * pw[PMAX + ny] * pw[2 * PMAX + nz];
+        if (ny > 0) h[1] -= v * pw[nx] * pw[PMAX + ny - 1] * pw[2 * PMAX + nz];
+        if (nz > 0) h[2] -= v * pw[nx] * pw[PMAX + ny] * pw[2 * PMAX + nz - 1];
+    }
+}
+
+// One block per target leaf; writes H = smooth field (L2P) + near field of
+// every dipole of the leaf.
+//  * Each thread owns two targets and one stripe (a contiguous chunk) of the
+//    staged sources; S = floor(128 / target pairs) stripes per batch.
+//  * Sources are staged in shared memory relative to the target leaf centre,
+//    s_j = l_j - (c_target - c_source), so differences are formed between
+//    numbers of leaf-size magnitude; the shift is computed once per near
+//    entry in FP64.
+//  * The leaf's own dipoles are processed first, with the r = 0 test (a
+//    source on the field point contributes nothing, Appendix updateField);
+//    no other leaf can hold a point at the target's position.
+template <typename real>
+__global__ void __launch_bounds__(P2P_T) k_p2p(int p, int KP, int L, const int *leaf_start,
                                                const int *near_start, const NearEnt *near,
                                                const Geom *g, const typename vec4<real>::t *A,
-                                               const typename vec2<real>::t *B,
+                                               const typename vec2<real>::t *B, const double *V,
                                                typename vec4<real>::t *H)
 {
     typedef typename vec4<real>::t R4;
-    __shared__ R4 sp[P2P_CH];          // (sx, sy, sz, mx)
-    __shared__ real sm2[P2P_CH][2];    // (my, mz)
+    typedef typename vec2<real>::t R2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R4 *sp = reinterpret_cast<R4 *>(smraw);              // [P2P_CH]
+    R2 *sm = reinterpret_cast<R2 *>(sp + P2P_CH);         // [P2P_CH]
+    R4 *esh = reinterpret_cast<R4 *>(sm + P2P_CH);        // [P2P_NE] source shift
+    int *est = reinterpret_cast<int *>(esh + P2P_NE);     // [P2P_NE] source start
+    int *epf = est + P2P_NE;                              // [P2P_NE + 1] prefix of counts
+    real *vs = reinterpret_cast<real *>(epf + P2P_NE + 4);  // [KP]
+    unsigned *mi = reinterpret_cast<unsigned *>(vs + KP);   // [KP]
+    __shared__ int wsum[P2P_T / 32];
+
     const long long key = blockIdx.x;
     const int t0 = leaf_start[key], nt = leaf_start[key + 1] - t0;
     if (nt == 0) return;
     const int e0 = near_start[key], e1 = near_start[key + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = nterms(p) - 1;
+    const long long hid = (1ll << L) + key;
+    for (int c = tid; c < K; c += P2P_T) {
+        vs[c] = (real)V[hid * KP + c];
+        int x, y, z;
+        midx_inv(c + 1, x, y, z);
+        mi[c] = (unsigned)x | ((unsigned)y << 5) | ((unsigned)z << 10);
+    }
     const double wx = g->w[L][0], wy = g->w[L][1], wz = g->w[L][2];
-    const int tid = threadIdx.x;
 
-    for (int tb = 0; tb < nt; tb += P2P_T) {
-        const int ntc = min(nt - tb, P2P_T);
-        const int S = max(1, P2P_T / ntc);
-        const int ti = tid % ntc, stripe = tid / ntc;
+    for (int tb = 0; tb < nt; tb += 2 * P2P_T) {
+        const int ntc = min(nt - tb, 2 * P2P_T);
+        const int npair = (ntc + 1) >> 1;
+        const int S = max(1, P2P_T / npair);
+        const int q = tid % npair, stripe = tid / npair;
         const bool active = stripe < S;
-        real xi = 0, yi = 0, zi = 0;
-        if (active) {
-            R4 a = A[t0 + tb + ti];
-            xi = a.x;
-            yi = a.y;
-            zi = a.z;
-        }
-        real hx = 0, hy = 0, hz = 0;
-        int fill = 0;
-        for (int e = e0; e <= e1; ++e) {
-            int cnt = 0, sb = 0;
-            real dx = 0, dy = 0, dz = 0;
-            if (e < e1) {
-                NearEnt ne = near[e];
-                sb = leaf_start[ne.src];
-                cnt = leaf_start[ne.src + 1] - sb;
-                dx = (real)((double)ne.ox * wx);
-                dy = (real)((double)ne.oy * wy);
-                dz = (real)((double)ne.oz * wz);
+        const int ia = tb + 2 * q, ib = min(ia + 1, tb + ntc - 1);
+        R4 ta = A[t0 + ia], tbv = A[t0 + ib];
+        real ha[3] = {0, 0, 0}, hb[3] = {0, 0, 0};
+
+        // 1) the leaf's own dipoles (shift 0), r = 0 possible
+        for (int b0 = 0; b0 < nt; b0 += P2P_CH) {
+            const int len = min(P2P_CH, nt - b0);
+            __syncthreads();
+            for (int v = tid; v < len; v += P2P_T) {
+                sp[v] = A[t0 + b0 + v];
+                sm[v] = B[t0 + b0 + v];
             }
-            int done = 0;
-            while (true) {
-                int take = min(cnt - done, P2P_CH - fill);
-                bool flush = (e == e1) ? (fill > 0) : (take < cnt - done || fill + take == P2P_CH);
-                for (int j = tid; j < take; j += P2P_T) {
-                    R4 a = A[sb + done + j];
-                    typename vec2<real>::t b = B[sb + done + j];
-                    R4 v;
-                    v.x = a.x - dx;
-                    v.y = a.y - dy;
-                    v.z = a.z - dz;
-                    v.w = a.w;
-                    sp[fill + j] = v;
-                    sm2[fill + j][0] = b.x;
-                    sm2[fill + j][1] = b.y;
+            __syncthreads();
+            if (active) {
+                int chunk = (len + S - 1) / S, j0 = min(len, stripe * chunk);
+                p2p_range<real, true>(sp, sm, j0, min(len, j0 + chunk), ta.x, ta.y, ta.z, tbv.x,
+                                      tbv.y, tbv.z, ha, hb);
+            }
+        }
+        // 2) the other near leaves, in chunks of P2P_NE entries
+        for (int ec = e0; ec < e1; ec += P2P_NE) {
+            const int nec = min(P2P_NE, e1 - ec);
+            __syncthreads();
+            int c0 = 0, c1 = 0;
+            for (int r = 0; r < 2; ++r) {
+                int e = 2 * tid + r;
+                int cnt = 0;
+                if (e < nec) {
+                    NearEnt x = near[ec + e];
+                    int st = leaf_start[x.src];
+                    cnt = (x.src == (int)key) ? 0 : leaf_start[x.src + 1] - st;
+                    est[e] = st;
+                    R4 sh;
+                    sh.x = (real)((double)x.ox * wx);
+                    sh.y = (real)((double)x.oy * wy);
+                    sh.z = (real)((double)x.oz * wz);
+                    sh.w = (real)0;
+                    esh[e] = sh;
                 }
-                fill += take;
-                done += take;
-                if (flush) {
-                    __syncthreads();
-                    if (active) {
-#pragma unroll 4
-                        for (int j = stripe; j < fill; j += S) {
-                            R4 s = sp[j];
-                            real mx = s.w, my = sm2[j][0], mz = sm2[j][1];
-                            real rx = xi - s.x, ry = yi - s.y, rz = zi - s.z;
-                            real r2 = rx * rx + ry * ry + rz * rz;
-                            real ri = rsqrt_or_zero<real>(r2);
-                            real ri2 = ri * ri;
-                            real ri3 = ri2 * ri;
-                            real mr = mx * rx + my * ry + mz * rz;
-                            real t3 = (real)3 * mr * ri2 * ri3;
-                            hx += t3 * rx - mx * ri3;
-                            hy += t3 * ry - my * ri3;
-                            hz += t3 * rz - mz * ri3;
-                        }
+                if (r == 0) c0 = cnt; else c1 = cnt;
+            }
+            // exclusive prefix of the counts (two per thread)
+            int v = c0 + c1, x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
+            __syncthreads();
+            int base = 0;
+            for (int w = 0; w < warp; ++w) base += wsum[w];
+            int ex = base + x - v;
+            if (2 * tid < nec) epf[2 * tid] = ex;
+            if (2 * tid + 1 < nec) epf[2 * tid + 1] = ex + c0;
+            if (tid == 0) {
+                int tot = 0;
+                for (int w = 0; w < P2P_T / 32; ++w) tot += wsum[w];
+                epf[nec] = tot;
+            }
+            __syncthreads();
+            const int total = epf[nec];
+            for (int b0 = 0; b0 < total; b0 += P2P_CH) {
+                const int len = min(P2P_CH, total - b0);
+                if (b0) __syncthreads();
+                for (int e = warp; e < nec; e += P2P_T / 32) {
+                    int lo = max(epf[e], b0), hi = min(epf[e + 1], b0 + len);
+                    if (lo >= hi) continue;
+                    int off = est[e] - epf[e];
+                    R4 sh = esh[e];
+                    for (int gv = lo + lane; gv < hi; gv += 32) {
+                        R4 a = A[off + gv];
+                        R4 o;
+                        o.x = a.x - sh.x;
+                        o.y = a.y - sh.y;
+                        o.z = a.z - sh.z;
+                        o.w = a.w;
+                        sp[gv - b0] = o;
+                        sm[gv - b0] = B[off + gv];
                     }
-                    __syncthreads();
-                    fill = 0;
                 }
-                if (done >= cnt) break;
+                __syncthreads();
+                if (active) {
+                    int chunk = (len + S - 1) / S, j0 = min(len, stripe * chunk);
+                    p2p_range<real, false>(sp, sm, j0, min(len, j0 + chunk), ta.x, ta.y, ta.z,
+                                           tbv.x, tbv.y, tbv.z, ha, hb);
+                }
+                __syncthreads();
             }
         }
-        // reduce the stripes of each target through shared memory
+        // 3) reduce the stripes, add the smooth field, store
+        __syncthreads();
         real *red = reinterpret_cast<real *>(sp);
-        red[3 * tid + 0] = hx;
-        red[3 * tid + 1] = hy;
-        red[3 * tid + 2] = hz;
-        __syncthreads();
-        if (tid < ntc) {
-            real sx = 0, sy = 0, sz = 0;
-            for (int st = 0; st < S; ++st) {
-                int q = st * ntc + tid;
-                sx += red[3 * q + 0];
-                sy += red[3 * q + 1];
-                sz += red[3 * q + 2];
-            }
-            R4 h = H[t0 + tb + tid];
-            h.x += sx;
-            h.y += sy;
-            h.z += sz;
-            H[t0 + tb + tid] = h;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            red[6 * tid + k] = ha[k];
+            red[6 * tid + 3 + k] = hb[k];
         }
         __syncthreads();
+        real fa[3] = {0, 0, 0}, fb[3] = {0, 0, 0};
+        if (tid < npair) {
+            for (int st = 0; st < S; ++st) {
+                const real *r6 = red + 6 * (st * npair + tid);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    fa[k] += r6[k];
+                    fb[k] += r6[3 + k];
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < npair) {
+            real *pw = reinterpret_cast<real *>(sp) + tid * 3 * PMAX;
+            l2p_one<real>(p, K, vs, mi, pw, ta.x, ta.y, ta.z, fa);
+            R4 o;
+            o.x = fa[0];
+            o.y = fa[1];
+            o.z = fa[2];
+            o.w = (real)0;
+            H[t0 + ia] = o;
+            if (ia + 1 < tb + ntc) {
+                l2p_one<real>(p, K, vs, mi, pw, tbv.x, tbv.y, tbv.z, fb);
+                o.x = fb[0];
+                o.y = fb[1];
+                o.z = fb[2];
+                H[t0 + ia + 1] = o;
+            }
+        }
     }
 }
 
 template <typename real>
-void launch_p2p(int L, const int *leaf_start, const int *near_start, const NearEnt *near,
-                const Geom *d_geom, const typename vec4<real>::t *A,
-                const typename vec2<real>::t *B, typename vec4<real>::t *H, cudaStream_t s)
+void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_start,
+                const NearEnt *near, const Geom *d_geom, const typename vec4<real>::t *A,
+                const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
+                cudaStream_t s)
 {
+    size_t smem = (size_t)P2P_CH * (sizeof(typename vec4<real>::t) + sizeof(typename vec2<real>::t)) +
+                  (size_t)P2P_NE * sizeof(typename vec4<real>::t) + (2 * P2P_NE + 4) * sizeof(int) +
+                  (size_t)KP * (sizeof(real) + sizeof(unsigned)) + 64;
+    static_assert(P2P_CH * 4 >= 3 * PMAX * P2P_T, "L2P powers reuse the staging buffer");
+    cudaFuncSetAttribute(k_p2p<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
-    k_p2p<real><<<(unsigned)(1ll << L), P2P_T, 0, s>>>(L, leaf_start, near_start, near, d_geom, A,
-                                                      B, H);
+    k_p2p<real><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start, near_start, near,
+                                                         d_geom, A, B, V, H);
 }
 
 // unpermute to input order in FP64 and form per-block partial sums of m.H
@@ -285,9 +412,9 @@ void launch_p2p_pair_count(int L, const int *leaf_start, const int *near_start,
 }
 
 #define INST(real)                                                                              \
-    template void launch_p2p<real>(int, const int *, const int *, const NearEnt *,             \
+    template void launch_p2p<real>(int, int, int, const int *, const int *, const NearEnt *,   \
                                    const Geom *, const vec4<real>::t *, const vec2<real>::t *,  \
-                                   vec4<real>::t *, cudaStream_t);                             \
+                                   const double *, vec4<real>::t *, cudaStream_t);              \
     template void launch_finish<real>(const vec4<real>::t *, const int *, const double *,       \
                                       long long, double *, double *, double *, cudaStream_t);
 INST(float)

@@ -47,20 +47,31 @@ __global__ void __launch_bounds__(BB_T) k_bbox_partial(const double *pos, long l
     }
 }
 
-__global__ void k_bbox_final(const double *partial, int nparts, const double *user_box,
-                             double *box6, int *flags)
+__global__ void __launch_bounds__(256) k_bbox_final(const double *partial, int nparts,
+                                                    const double *user_box, double *box6, int *flags)
 {
+    __shared__ double sm[6][256];
+    double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nparts; b += 256)
+        for (int a = 0; a < 3; ++a) {
+            v[a] = fmin(v[a], partial[6 * b + a]);
+            v[3 + a] = fmax(v[3 + a], partial[6 * b + 3 + a]);
+        }
+    for (int a = 0; a < 6; ++a) sm[a][threadIdx.x] = v[a];
+    __syncthreads();
+    for (int w = 128; w; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int a = 0; a < 6; ++a)
+                sm[a][threadIdx.x] = a < 3 ? fmin(sm[a][threadIdx.x], sm[a][threadIdx.x + w])
+                                           : fmax(sm[a][threadIdx.x], sm[a][threadIdx.x + w]);
+        __syncthreads();
+    }
     if (threadIdx.x != 0) return;
     double mn[3], mx[3];
     for (int a = 0; a < 3; ++a) {
-        mn[a] = partial[a];
-        mx[a] = partial[3 + a];
+        mn[a] = sm[a][0];
+        mx[a] = sm[3 + a][0];
     }
-    for (int b = 1; b < nparts; ++b)
-        for (int a = 0; a < 3; ++a) {
-            mn[a] = fmin(mn[a], partial[6 * b + a]);
-            mx[a] = fmax(mx[a], partial[6 * b + 3 + a]);
-        }
     if (user_box) {
         for (int a = 0; a < 3; ++a) {
             if (mn[a] < user_box[a] || mx[a] > user_box[3 + a]) atomicOr(flags, FLAG_OUTSIDE_BOX);
@@ -117,7 +128,7 @@ void launch_bbox(const double *pos, long long n, const double *user_box, double 
     note_launch();
     k_bbox_partial<<<nb, BB_T, 0, s>>>(pos, n, partial, d_flags);
     note_launch();
-    k_bbox_final<<<1, 32, 0, s>>>(partial, nb, user_box, d_box6, d_flags);
+    k_bbox_final<<<1, 256, 0, s>>>(partial, nb, user_box, d_box6, d_flags);
 }
 
 void launch_geom(const double *d_box6, Geom *d_geom, cudaStream_t s)
