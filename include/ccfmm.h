@@ -187,6 +187,48 @@ ccfmm_status ccfmm_direct_field(const double *positions, const double *moments, 
                                 const int64_t *tgt, int64_t nt, double *H_out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Ensemble of independent samples (a project addition; the paper evaluates
+ * one system).  The samples' trees, lists and derivative tensors are built
+ * once (positions stay fixed); each step turns every moment by a random
+ * rotation and evaluates every sample's field, as one CUDA graph launch.
+ *   positions, moments  concatenated samples, total x 3 float64, host or
+ *                       device; sample i is rows offsets[i] .. offsets[i+1].
+ *   offsets             nsamples + 1 host int64, offsets[0] = 0, increasing.
+ *   p, theta, leaf_size, prec   as in fmm_create_ex, shared by the samples.
+ *   stream              cudaStream_t (not the legacy default stream) or NULL
+ *                       for a stream owned by the batch.
+ * ---------------------------------------------------------------------- */
+typedef struct ccfmm_batch_s *ccfmm_batch_t;
+
+ccfmm_status fmm_batch_create(const double *positions, const double *moments,
+                              const int64_t *offsets, int nsamples, int p, double theta,
+                              double leaf_size, ccfmm_prec prec, void *stream, ccfmm_batch_t *out);
+
+/* One time step: every moment m_i (global row i) is turned about a random
+ * axis by a random angle, drawn from Philox4x64-10 (Salmon et al., SC 2011)
+ * with key (seed, step) and counter (i, 0, 0, 0): from its outputs x0..x3,
+ * u_j = (x_j >> 11) 2^-53, axis = (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi,
+ * z) with z = 1 - 2 u0, phi = 2 pi u1, angle = max_angle u2 (Rodrigues'
+ * formula, FP64).  Then every sample's field is evaluated.
+ *   H_out  total x 3 float64 (host, device or NULL).
+ *   E_out  nsamples float64 energies, E = -1/2 sum m.H per sample (host,
+ *          device or NULL). */
+ccfmm_status fmm_batch_step(ccfmm_batch_t b, uint64_t seed, uint64_t step, double max_angle,
+                            double *H_out, double *E_out);
+
+/* Evaluate every sample for the current moments (no rotation). */
+ccfmm_status fmm_batch_evaluate(ccfmm_batch_t b, double *H_out, double *E_out);
+
+/* Current moments (total x 3), and replacing them. */
+ccfmm_status fmm_batch_get_moments(ccfmm_batch_t b, double *out);
+ccfmm_status fmm_batch_set_moments(ccfmm_batch_t b, const double *moments);
+
+/* Total dipoles and kernels launched by one step's graph. */
+ccfmm_status fmm_batch_info(ccfmm_batch_t b, int64_t *total_n, int64_t *kernels_per_step);
+
+void fmm_batch_destroy(ccfmm_batch_t b);
+
+/* ------------------------------------------------------------------------
  * Allocation-free direct field and energy.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc, such as
  * code running inside a host application that owns all GPU memory through

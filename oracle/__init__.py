@@ -31,6 +31,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 _lp = ctypes.POINTER(ctypes.c_int64)
 _up = ctypes.POINTER(ctypes.c_uint8)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
 def build(force: bool = False) -> str:
@@ -81,6 +82,9 @@ def _bind(path):
         "orc_fmm_locals": (None, [ctypes.c_void_p, _dp]),
         "orc_fmm_field": (None, [ctypes.c_void_p, _dp]),
         "orc_fmm_energy": (ctypes.c_double, [ctypes.c_void_p]),
+        "orc_philox4x64": (None, [_u64p, _u64p, _u64p]),
+        "orc_rotate_moments": (None, [_i64, _dp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                                      _i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +240,23 @@ def leaf_size_rule(p: int) -> float:
 def error_estimate(p: int, alpha: float) -> float:
     """e = [alpha/(2-alpha)]^p (Sec. III, Sec. IV)."""
     return _load().orc_error_estimate(p, alpha)
+
+
+def philox4x64(counter, key) -> np.ndarray:
+    """Philox4x64-10 block function (Salmon et al., SC 2011)."""
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint64).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64).reshape(2))
+    out = np.zeros(4, dtype=np.uint64)
+    _load().orc_philox4x64(c.ctypes.data_as(_u64p), k.ctypes.data_as(_u64p), out.ctypes.data_as(_u64p))
+    return out
+
+
+def rotate_moments(mom, seed, step, max_angle, first=0) -> np.ndarray:
+    """The ensemble time step: every moment turned by a Philox-drawn random
+    rotation (axis uniform on the sphere, angle uniform in [0, max_angle])."""
+    m = np.array(mom, dtype=np.float64).reshape(-1, 3).copy()
+    _load().orc_rotate_moments(len(m), _d(m), int(seed), int(step), float(max_angle), int(first))
+    return m
 
 
 def threads() -> int:

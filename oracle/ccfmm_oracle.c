@@ -929,3 +929,67 @@ double orc_fmm_energy(const orc_fmm *f)
                  f->mom[3 * i + 2] * f->H[3 * i + 2];
     return -0.5 * e;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Ensemble time step (a project addition, not in the paper): every moment  */
+/* is turned about a random axis by a random angle.  The random numbers come */
+/* from the counter-based generator Philox4x64-10 (Salmon, Moraes, Dror,     */
+/* Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011): key =      */
+/* (seed, step), counter = (dipole index, 0, 0, 0).  From the four 64-bit    */
+/* outputs x0..x3, u_i = (x_i >> 11) 2^-53; axis z = 1 - 2 u0,               */
+/* phi = 2 pi u1, axis = (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z);      */
+/* angle = max_angle * u2.  The turn is Rodrigues' formula                   */
+/* m' = m cos a + (k x m) sin a + k (k.m)(1 - cos a).                        */
+/* ------------------------------------------------------------------------- */
+
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint64_t k[2] = {key_in[0], key_in[1]};
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(M0, c[0], &hi0, &lo0);
+        mulhilo64(M1, c[2], &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c[1] ^ k[0], n2 = hi0 ^ c[3] ^ k[1];
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k[0] += W0;
+        k[1] += W1;
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+/* turn moments mom[0..n) (rows of 3) in place; dipole i has global index first + i */
+void orc_rotate_moments(i64 n, double *mom, uint64_t seed, uint64_t step, double max_angle, i64 first)
+{
+    const double two53 = 1.0 / 9007199254740992.0;
+    const double pi = 3.14159265358979323846;
+    for (i64 i = 0; i < n; ++i) {
+        uint64_t ctr[4] = {(uint64_t)(first + i), 0, 0, 0}, key[2] = {seed, step}, x[4];
+        orc_philox4x64(ctr, key, x);
+        double u0 = (double)(x[0] >> 11) * two53, u1 = (double)(x[1] >> 11) * two53;
+        double u2 = (double)(x[2] >> 11) * two53;
+        double z = 1.0 - 2.0 * u0, phi = 2.0 * pi * u1, s = sqrt(1.0 - z * z);
+        double k[3] = {s * cos(phi), s * sin(phi), z};
+        double a = max_angle * u2, ca = cos(a), sa = sin(a);
+        double *m = &mom[3 * i];
+        double kxm[3] = {k[1] * m[2] - k[2] * m[1], k[2] * m[0] - k[0] * m[2], k[0] * m[1] - k[1] * m[0]};
+        double km = k[0] * m[0] + k[1] * m[1] + k[2] * m[2];
+        double r[3];
+        for (int d = 0; d < 3; ++d) r[d] = m[d] * ca + kxm[d] * sa + k[d] * km * (1.0 - ca);
+        m[0] = r[0];
+        m[1] = r[1];
+        m[2] = r[2];
+    }
+}

@@ -83,6 +83,14 @@ def load():
             "ccfmm_direct_field": (_int, [_vp, _vp, _i64, _vp, _i64, _vp, _vp]),
             "ccfmm_leaf_size_rule": (_dbl, [_int]),
             "ccfmm_kernel_launches": (_i64, []),
+            "fmm_batch_create": (_int, [_vp, _vp, _vp, _int, _int, _dbl, _dbl, _int, _vp,
+                                        ctypes.POINTER(_vp)]),
+            "fmm_batch_step": (_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, _dbl, _vp, _vp]),
+            "fmm_batch_evaluate": (_int, [_vp, _vp, _vp]),
+            "fmm_batch_get_moments": (_int, [_vp, _vp]),
+            "fmm_batch_set_moments": (_int, [_vp, _vp]),
+            "fmm_batch_info": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+            "fmm_batch_destroy": (None, [_vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -265,3 +273,65 @@ class FMM:
         out = np.zeros((1 << (d + 1), T))
         _check(self._lib.fmm_get_expansions(self._h, k, _vp(out.ctypes.data)))
         return out
+
+
+class Batch:
+    """An ensemble of independent samples stepped together (fmm_batch_*)."""
+
+    def __init__(self, positions, moments, offsets, p, theta, leaf_size=0.0, precision="mixed",
+                 stream=None):
+        lib = load()
+        self._lib = lib
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.offsets = off
+        self.ns = len(off) - 1
+        self.total = int(off[-1])
+        pp, k1 = _ptr(positions, 3 * self.total)
+        pm, k2 = _ptr(moments, 3 * self.total)
+        prec = {"mixed": MIXED, "fp32": MIXED, "fp64": FP64}[precision]
+        h = _vp()
+        _check(lib.fmm_batch_create(pp, pm, _vp(off.ctypes.data), self.ns, int(p), float(theta),
+                                    float(leaf_size), prec, _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fmm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, seed, step, max_angle, H_out=None, E_out=None):
+        """Rotate every moment (Philox(seed, step)) and evaluate every sample."""
+        ph, k1 = _ptr(H_out, 3 * self.total) if H_out is not None else (None, None)
+        pe, k2 = _ptr(E_out, self.ns) if E_out is not None else (None, None)
+        _check(self._lib.fmm_batch_step(self._h, int(seed), int(step), float(max_angle), ph, pe))
+
+    def evaluate(self, H_out=None, E_out=None):
+        ph, k1 = _ptr(H_out, 3 * self.total) if H_out is not None else (None, None)
+        pe, k2 = _ptr(E_out, self.ns) if E_out is not None else (None, None)
+        _check(self._lib.fmm_batch_evaluate(self._h, ph, pe))
+
+    def moments(self):
+        out = np.zeros((self.total, 3))
+        _check(self._lib.fmm_batch_get_moments(self._h, _vp(out.ctypes.data)))
+        return out
+
+    def set_moments(self, moments):
+        pm, k = _ptr(moments, 3 * self.total)
+        _check(self._lib.fmm_batch_set_moments(self._h, pm))
+
+    def kernels_per_step(self):
+        n, k = _i64(), _i64()
+        _check(self._lib.fmm_batch_info(self._h, ctypes.byref(n), ctypes.byref(k)))
+        return int(k.value)

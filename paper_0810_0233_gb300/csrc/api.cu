@@ -154,6 +154,10 @@ struct ccfmm_s {
     DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
     DevBuf Hout, epart, items, titem0, tnitems, Ps;
     int nitems = 0;
+    // batch members: energy input and output redirected, no stage events
+    const double *mom_energy = nullptr;
+    double *E_dst = nullptr;
+    bool quiet = false;
     Readback *hrb = nullptr;  // pinned
     int *near_start_leaf = nullptr;
     NearEnt *near_leaf = nullptr;
@@ -585,7 +589,7 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
     cudaStream_t s = h->stream;
     const int L = h->L, p = h->p, KP = h->KP;
     const long long ncellp = 1ll << (L + 1);
-    bool ev = h->ev_ok;
+    bool ev = h->ev_ok && !h->quiet;
     cudaEvent_t *evs = h->eve[h->n_eval % EV_RING];
     if (ev) CK(cudaEventRecord(evs[EV_E0], s));
     CK(cudaMemsetAsync(h->V.p, 0, sizeof(double) * (size_t)ncellp * KP, s));
@@ -611,12 +615,12 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
                      P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), P<double>(h->V), P<R4>(h->H), s);
     if (ev) CK(cudaEventRecord(evs[EV_P2P], s));
     Readback *drb = P<Readback>(h->rb);
-    launch_finish<real>(P<R4>(h->H), P<int>(h->idx), P<double>(h->mom), h->N, Hdev,
-                        P<double>(h->epart), &drb->E, s);
+    launch_finish<real>(P<R4>(h->H), P<int>(h->idx), h->mom_energy ? h->mom_energy : P<double>(h->mom),
+                        h->N, Hdev, P<double>(h->epart), h->E_dst ? h->E_dst : &drb->E, s);
     if (ev) CK(cudaEventRecord(evs[EV_FIN], s));
     KCHECK();
     h->evaluated = true;
-    h->n_eval++;
+    if (ev) h->n_eval++;
     return CCFMM_OK;
 }
 
@@ -1043,6 +1047,270 @@ ccfmm_status ccfmm_direct_field(const double *positions, const double *moments, 
     cleanup();
 #undef DTRY
 #undef DCK
+    return CCFMM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ ensemble
+// A batch of independent samples: one handle (tree, lists, buffers) per
+// sample, built once; a step turns every moment (k_rotate) and evaluates
+// every sample.  The whole step is one CUDA graph launch: the rotation, then
+// the samples' evaluations on BR parallel branches (samples s, s+BR, ... on
+// branch s % BR).
+struct ccfmm_batch_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int ns = 0, nbr = 0;
+    std::vector<long long> off;
+    long long total = 0;
+    ccfmm_prec prec = CCFMM_MIXED;
+    std::vector<ccfmm_t> h;
+    std::vector<cudaStream_t> br;
+    std::vector<cudaEvent_t> evj;
+    cudaEvent_t evf = nullptr;
+    DevBuf mom, H, E, prm;
+    RotateParams *hprm = nullptr;  // pinned
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [0] evaluate, [1] rotate + evaluate
+    long long graph_kernels[2] = {0, 0};
+};
+
+static ccfmm_status batch_capture(ccfmm_batch_t b, int rotate)
+{
+    cudaStream_t s = b->stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    ccfmm_status st = CCFMM_OK;
+    do {
+        if (rotate) launch_rotate(P<double>(b->mom), b->total, P<RotateParams>(b->prm), s);
+        if (cudaEventRecord(b->evf, s) != cudaSuccess) { st = fail(CCFMM_ERR_CUDA, "capture fork"); break; }
+        for (int r = 0; r < b->nbr; ++r)
+            if (cudaStreamWaitEvent(b->br[r], b->evf, 0) != cudaSuccess) st = fail(CCFMM_ERR_CUDA, "capture wait");
+        if (st != CCFMM_OK) break;
+        for (int i = 0; i < b->ns && st == CCFMM_OK; ++i) {
+            ccfmm_t hs = b->h[i];
+            const double *ms = P<double>(b->mom) + 3 * b->off[i];
+            if (hs->prec == CCFMM_MIXED) {
+                launch_permute_moments<float>(ms, P<int>(hs->idx), hs->N, P<float4>(hs->A),
+                                              P<float2>(hs->B), hs->stream);
+                st = eval_t<float>(hs, P<double>(b->H) + 3 * b->off[i]);
+            } else {
+                launch_permute_moments<double>(ms, P<int>(hs->idx), hs->N, P<double4>(hs->A),
+                                               P<double2>(hs->B), hs->stream);
+                st = eval_t<double>(hs, P<double>(b->H) + 3 * b->off[i]);
+            }
+        }
+        if (st != CCFMM_OK) break;
+        for (int r = 0; r < b->nbr; ++r) {
+            if (cudaEventRecord(b->evj[r], b->br[r]) != cudaSuccess ||
+                cudaStreamWaitEvent(s, b->evj[r], 0) != cudaSuccess)
+                st = fail(CCFMM_ERR_CUDA, "capture join");
+        }
+    } while (0);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != CCFMM_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CCFMM_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    }
+    size_t nn = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    long long nk = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
+    }
+    b->graph_kernels[rotate] = nk;
+    e = cudaGraphInstantiate(&b->exec[rotate], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->exec[rotate] = nullptr;
+        return fail(CCFMM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return CCFMM_OK;
+}
+
+static ccfmm_status batch_run(ccfmm_batch_t b, int rotate, double *H_out, double *E_out)
+{
+    if (!b->exec[rotate]) TRY(batch_capture(b, rotate));
+    CK(cudaGraphLaunch(b->exec[rotate], b->stream));
+    note_launch((int)b->graph_kernels[rotate]);
+    if (H_out) {
+        cudaMemcpyKind k = is_device_ptr(H_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpyAsync(H_out, b->H.p, sizeof(double) * 3 * b->total, k, b->stream));
+    }
+    if (E_out) {
+        cudaMemcpyKind k = is_device_ptr(E_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpyAsync(E_out, b->E.p, sizeof(double) * b->ns, k, b->stream));
+    }
+    if ((H_out && !is_device_ptr(H_out)) || (E_out && !is_device_ptr(E_out)))
+        CK(cudaStreamSynchronize(b->stream));
+    return CCFMM_OK;
+}
+
+extern "C" {
+
+void fmm_batch_destroy(ccfmm_batch_t b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int r = 0; r < 2; ++r)
+        if (b->exec[r]) cudaGraphExecDestroy(b->exec[r]);
+    for (ccfmm_t h : b->h) fmm_destroy(h);
+    for (cudaStream_t s : b->br) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->evj) cudaEventDestroy(e);
+    if (b->evf) cudaEventDestroy(b->evf);
+    DevBuf *bufs[] = {&b->mom, &b->H, &b->E, &b->prm};
+    for (DevBuf *d : bufs)
+        if (d->p) cudaFree(d->p);
+    if (b->hprm) cudaFreeHost(b->hprm);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+ccfmm_status fmm_batch_create(const double *positions, const double *moments,
+                              const int64_t *offsets, int nsamples, int p, double theta,
+                              double leaf_size, ccfmm_prec prec, void *stream, ccfmm_batch_t *out)
+{
+    g_err.clear();
+    if (!out || !positions || !moments || !offsets) return fail(CCFMM_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (nsamples < 1) return fail(CCFMM_ERR_ARG, "nsamples < 1");
+    if (offsets[0] != 0) return fail(CCFMM_ERR_ARG, "offsets[0] must be 0");
+    for (int i = 0; i < nsamples; ++i)
+        if (offsets[i + 1] <= offsets[i]) return fail(CCFMM_ERR_ARG, "sample %d is empty", i);
+    ccfmm_batch_t b = new (std::nothrow) ccfmm_batch_s();
+    if (!b) return fail(CCFMM_ERR_ALLOC, "host allocation failed");
+    ccfmm_status st = CCFMM_OK;
+#define BTRY(x)                                                                                  \
+    do {                                                                                         \
+        st = (x);                                                                                \
+        if (st != CCFMM_OK) {                                                                    \
+            std::string m_ = g_err;                                                              \
+            fmm_batch_destroy(b);                                                                \
+            g_err = m_;                                                                          \
+            return st;                                                                           \
+        }                                                                                        \
+    } while (0)
+#define BCK(call)                                                                                \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            fmm_batch_destroy(b);                                                                \
+            return fail(CCFMM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+        }                                                                                        \
+    } while (0)
+    BCK(cudaGetDevice(&b->device));
+    b->ns = nsamples;
+    b->prec = prec;
+    b->off.assign(offsets, offsets + nsamples + 1);
+    b->total = b->off[nsamples];
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        b->own_stream = true;
+    }
+    b->nbr = std::min(nsamples, 32);
+    for (int r = 0; r < b->nbr; ++r) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        BCK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        b->br.push_back(s);
+        BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->evj.push_back(e);
+    }
+    BCK(cudaEventCreateWithFlags(&b->evf, cudaEventDisableTiming));
+    BTRY(ensure(b->mom, sizeof(double) * 3 * b->total));
+    BTRY(ensure(b->H, sizeof(double) * 3 * b->total));
+    BTRY(ensure(b->E, sizeof(double) * nsamples));
+    BTRY(ensure(b->prm, sizeof(RotateParams)));
+    BCK(cudaMallocHost((void **)&b->hprm, sizeof(RotateParams)));
+    {
+        cudaMemcpyKind k = is_device_ptr(moments) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        BCK(cudaMemcpyAsync(b->mom.p, moments, sizeof(double) * 3 * b->total, k, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+    }
+    for (int i = 0; i < nsamples; ++i) {
+        ccfmm_t hs = nullptr;
+        long long o = b->off[i], n = b->off[i + 1] - o;
+        BTRY(fmm_create_ex(positions + 3 * o, P<double>(b->mom) + 3 * o, n, p, theta, leaf_size,
+                           nullptr, prec, b->br[i % b->nbr], &hs));
+        hs->quiet = true;
+        hs->mom_energy = P<double>(b->mom) + 3 * o;
+        hs->E_dst = P<double>(b->E) + i;
+        b->h.push_back(hs);
+    }
+#undef BTRY
+#undef BCK
+    *out = b;
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_batch_step(ccfmm_batch_t b, uint64_t seed, uint64_t step, double max_angle,
+                            double *H_out, double *E_out)
+{
+    g_err.clear();
+    if (!b) return fail(CCFMM_ERR_ARG, "batch is NULL");
+    if (!(max_angle >= 0.0) || isinf(max_angle)) return fail(CCFMM_ERR_ARG, "bad max_angle");
+    CK(cudaSetDevice(b->device));
+    // the previous step's graph may still read the parameter block
+    CK(cudaStreamSynchronize(b->stream));
+    b->hprm->seed = seed;
+    b->hprm->step = step;
+    b->hprm->max_angle = max_angle;
+    CK(cudaMemcpyAsync(b->prm.p, b->hprm, sizeof(RotateParams), cudaMemcpyHostToDevice, b->stream));
+    return batch_run(b, 1, H_out, E_out);
+}
+
+ccfmm_status fmm_batch_evaluate(ccfmm_batch_t b, double *H_out, double *E_out)
+{
+    g_err.clear();
+    if (!b) return fail(CCFMM_ERR_ARG, "batch is NULL");
+    CK(cudaSetDevice(b->device));
+    return batch_run(b, 0, H_out, E_out);
+}
+
+ccfmm_status fmm_batch_get_moments(ccfmm_batch_t b, double *out)
+{
+    g_err.clear();
+    if (!b || !out) return fail(CCFMM_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(b->device));
+    cudaMemcpyKind k = is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(out, b->mom.p, sizeof(double) * 3 * b->total, k, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_batch_set_moments(ccfmm_batch_t b, const double *moments)
+{
+    g_err.clear();
+    if (!b || !moments) return fail(CCFMM_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(b->device));
+    CK(cudaStreamSynchronize(b->stream));
+    cudaMemcpyKind k = is_device_ptr(moments) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(b->mom.p, moments, sizeof(double) * 3 * b->total, k, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_batch_info(ccfmm_batch_t b, int64_t *total_n, int64_t *kernels_per_step)
+{
+    g_err.clear();
+    if (!b) return fail(CCFMM_ERR_ARG, "batch is NULL");
+    if (total_n) *total_n = b->total;
+    if (kernels_per_step) *kernels_per_step = b->graph_kernels[1];
     return CCFMM_OK;
 }
 

@@ -106,6 +106,14 @@ void note_launch(int n = 1);
 // Message returned by ccfmm_last_error() on this thread.
 void set_last_error(const char *msg);
 
+// Parameters of the ensemble rotation step, read by the kernel from device
+// memory so that a captured graph serves every step.
+struct RotateParams {
+    unsigned long long seed, step;
+    double max_angle;
+};
+void launch_rotate(double *mom, long long n, const RotateParams *prm, cudaStream_t s);
+
 // ------------------------------------------------------------------ prims.cu
 size_t scan_temp_bytes(long long n);
 // exclusive scan of n int32 values; total (if not null) written to device

@@ -33,51 +33,68 @@ __device__ __forceinline__ void dip_pair(real tx, real ty, real tz, real sx, rea
     hz += ri3 * (t * rz - mz);
 }
 
+constexpr int P2P_TPT = 2;    // targets per thread
+
 template <typename real, bool SELF>
 __device__ __forceinline__ void p2p_range(const typename vec4<real>::t *sp,
                                           const typename vec2<real>::t *sm, int j0, int j1,
-                                          real xa, real ya, real za, real xb, real yb, real zb,
-                                          real ha[3], real hb[3])
+                                          const real (&tx)[P2P_TPT][3], real (&hs)[P2P_TPT][3])
 {
-#pragma unroll 4
+#pragma unroll 2
     for (int j = j0; j < j1; ++j) {
         typename vec4<real>::t s = sp[j];
         typename vec2<real>::t m = sm[j];
-        dip_pair<real, SELF>(xa, ya, za, s.x, s.y, s.z, s.w, m.x, m.y, ha[0], ha[1], ha[2]);
-        dip_pair<real, SELF>(xb, yb, zb, s.x, s.y, s.z, s.w, m.x, m.y, hb[0], hb[1], hb[2]);
+#pragma unroll
+        for (int i = 0; i < P2P_TPT; ++i)
+            dip_pair<real, SELF>(tx[i][0], tx[i][1], tx[i][2], s.x, s.y, s.z, s.w, m.x, m.y,
+                                 hs[i][0], hs[i][1], hs[i][2]);
     }
+}
+
+// contiguous stripe [j0, j1) of a batch of len sources; the chunk length is
+// odd so that lanes of different stripes read different shared-memory banks
+__device__ __forceinline__ void stripe_range(int len, int S, int stripe, int &j0, int &j1)
+{
+    int chunk = ((len + S - 1) / S) | 1;
+    j0 = min(len, stripe * chunk);
+    j1 = min(len, j0 + chunk);
 }
 
 // Smooth field (Eq. H, H = -grad V) of one target from its leaf's Taylor
 // coefficients vs[] (multi-indices mi[]), powers pw[3][PMAX] = x^j / j!.
 template <typename real>
 __device__ __forceinline__ void l2p_one(int p, int K, const real *vs, const unsigned *mi, real *pw,
-                                        real x, real y, real z, real h[3])
+                                        real x, real y, real z, real &h0, real &h1, real &h2)
 {
+    const real inv[PMAX] = {(real)0, (real)1, (real)0.5, (real)1 / (real)3, (real)0.25,
+                            (real)0.2, (real)1 / (real)6, (real)1 / (real)7};
     real c[3] = {x, y, z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         real t = (real)1;
         pw[d * PMAX] = t;
-        for (int j = 1; j < p; ++j) {
-            t = t * c[d] / (real)j;
-            pw[d * PMAX + j] = t;
+#pragma unroll
+        for (int j = 1; j < PMAX; ++j) {
+            if (j < p) {
+                t = t * c[d] * inv[j];
+                pw[d * PMAX + j] = t;
+            }
         }
     }
     for (int k = 0; k < K; ++k) {
         unsigned n = mi[k];
         int nx = (int)(n & 31u), ny = (int)((n >> 5) & 31u), nz = (int)((n >> 10) & 31u);
         real v = vs[k];
-        if (nx > 0) h[0] -= v * pw[nx - 1] * pw[PMAX + ny] * pw[2 * PMAX + nz];
-        if (ny > 0) h[1] -= v * pw[nx] * pw[PMAX + ny - 1] * pw[2 * PMAX + nz];
-        if (nz > 0) h[2] -= v * pw[nx] * pw[PMAX + ny] * pw[2 * PMAX + nz - 1];
+        if (nx > 0) h0 -= v * pw[nx - 1] * pw[PMAX + ny] * pw[2 * PMAX + nz];
+        if (ny > 0) h1 -= v * pw[nx] * pw[PMAX + ny - 1] * pw[2 * PMAX + nz];
+        if (nz > 0) h2 -= v * pw[nx] * pw[PMAX + ny] * pw[2 * PMAX + nz - 1];
     }
 }
 
 // One block per target leaf; writes H = smooth field (L2P) + near field of
 // every dipole of the leaf.
 //  * Each thread owns two targets and one stripe (a contiguous chunk) of the
-//    staged sources; S = floor(128 / target pairs) stripes per batch.
+//    staged sources; S = floor(128 / target groups) stripes per batch.
 //  * Sources are staged in shared memory relative to the target leaf centre,
 //    s_j = l_j - (c_target - c_source), so differences are formed between
 //    numbers of leaf-size magnitude; the shift is computed once per near
@@ -86,7 +103,7 @@ __device__ __forceinline__ void l2p_one(int p, int K, const real *vs, const unsi
 //    source on the field point contributes nothing, Appendix updateField);
 //    no other leaf can hold a point at the target's position.
 template <typename real>
-__global__ void __launch_bounds__(P2P_T) k_p2p(int p, int KP, int L, const int *leaf_start,
+__global__ void __launch_bounds__(P2P_T, 4) k_p2p(int p, int KP, int L, const int *leaf_start,
                                                const int *near_start, const NearEnt *near,
                                                const Geom *g, const typename vec4<real>::t *A,
                                                const typename vec2<real>::t *B, const double *V,
@@ -119,15 +136,22 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(int p, int KP, int L, const int *
     }
     const double wx = g->w[L][0], wy = g->w[L][1], wz = g->w[L][2];
 
-    for (int tb = 0; tb < nt; tb += 2 * P2P_T) {
-        const int ntc = min(nt - tb, 2 * P2P_T);
-        const int npair = (ntc + 1) >> 1;
-        const int S = max(1, P2P_T / npair);
-        const int q = tid % npair, stripe = tid / npair;
+    for (int tb = 0; tb < nt; tb += P2P_TPT * P2P_T) {
+        const int ntc = min(nt - tb, P2P_TPT * P2P_T);
+        const int ngrp = (ntc + P2P_TPT - 1) / P2P_TPT;
+        const int S = max(1, P2P_T / ngrp);
+        const int q = tid % ngrp, stripe = tid / ngrp;
         const bool active = stripe < S;
-        const int ia = tb + 2 * q, ib = min(ia + 1, tb + ntc - 1);
-        R4 ta = A[t0 + ia], tbv = A[t0 + ib];
-        real ha[3] = {0, 0, 0}, hb[3] = {0, 0, 0};
+        const int i0 = tb + P2P_TPT * q;
+        real tx[P2P_TPT][3], hs[P2P_TPT][3];
+#pragma unroll
+        for (int i = 0; i < P2P_TPT; ++i) {
+            R4 a = A[t0 + min(i0 + i, tb + ntc - 1)];
+            tx[i][0] = a.x;
+            tx[i][1] = a.y;
+            tx[i][2] = a.z;
+            hs[i][0] = hs[i][1] = hs[i][2] = (real)0;
+        }
 
         // 1) the leaf's own dipoles (shift 0), r = 0 possible
         for (int b0 = 0; b0 < nt; b0 += P2P_CH) {
@@ -139,9 +163,9 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(int p, int KP, int L, const int *
             }
             __syncthreads();
             if (active) {
-                int chunk = (len + S - 1) / S, j0 = min(len, stripe * chunk);
-                p2p_range<real, true>(sp, sm, j0, min(len, j0 + chunk), ta.x, ta.y, ta.z, tbv.x,
-                                      tbv.y, tbv.z, ha, hb);
+                int j0, j1;
+                stripe_range(len, S, stripe, j0, j1);
+                p2p_range<real, true>(sp, sm, j0, j1, tx, hs);
             }
         }
         // 2) the other near leaves, in chunks of P2P_NE entries
@@ -207,9 +231,9 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(int p, int KP, int L, const int *
                 }
                 __syncthreads();
                 if (active) {
-                    int chunk = (len + S - 1) / S, j0 = min(len, stripe * chunk);
-                    p2p_range<real, false>(sp, sm, j0, min(len, j0 + chunk), ta.x, ta.y, ta.z,
-                                           tbv.x, tbv.y, tbv.z, ha, hb);
+                    int j0, j1;
+                    stripe_range(len, S, stripe, j0, j1);
+                    p2p_range<real, false>(sp, sm, j0, j1, tx, hs);
                 }
                 __syncthreads();
             }
@@ -218,38 +242,35 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(int p, int KP, int L, const int *
         __syncthreads();
         real *red = reinterpret_cast<real *>(sp);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            red[6 * tid + k] = ha[k];
-            red[6 * tid + 3 + k] = hb[k];
-        }
-        __syncthreads();
-        real fa[3] = {0, 0, 0}, fb[3] = {0, 0, 0};
-        if (tid < npair) {
-            for (int st = 0; st < S; ++st) {
-                const real *r6 = red + 6 * (st * npair + tid);
+        for (int i = 0; i < P2P_TPT; ++i)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    fa[k] += r6[k];
-                    fb[k] += r6[3 + k];
-                }
+            for (int k = 0; k < 3; ++k) red[(3 * P2P_TPT) * tid + 3 * i + k] = hs[i][k];
+        __syncthreads();
+        real f[P2P_TPT][3];
+#pragma unroll
+        for (int i = 0; i < P2P_TPT; ++i) f[i][0] = f[i][1] = f[i][2] = (real)0;
+        if (tid < ngrp) {
+            for (int st = 0; st < S; ++st) {
+                const real *rr = red + (3 * P2P_TPT) * (st * ngrp + tid);
+#pragma unroll
+                for (int i = 0; i < P2P_TPT; ++i)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) f[i][k] += rr[3 * i + k];
             }
         }
         __syncthreads();
-        if (tid < npair) {
+        if (tid < ngrp) {
             real *pw = reinterpret_cast<real *>(sp) + tid * 3 * PMAX;
-            l2p_one<real>(p, K, vs, mi, pw, ta.x, ta.y, ta.z, fa);
-            R4 o;
-            o.x = fa[0];
-            o.y = fa[1];
-            o.z = fa[2];
-            o.w = (real)0;
-            H[t0 + ia] = o;
-            if (ia + 1 < tb + ntc) {
-                l2p_one<real>(p, K, vs, mi, pw, tbv.x, tbv.y, tbv.z, fb);
-                o.x = fb[0];
-                o.y = fb[1];
-                o.z = fb[2];
-                H[t0 + ia + 1] = o;
+#pragma unroll
+            for (int i = 0; i < P2P_TPT; ++i) {
+                l2p_one<real>(p, K, vs, mi, pw, tx[i][0], tx[i][1], tx[i][2], f[i][0], f[i][1],
+                              f[i][2]);
+                R4 o;
+                o.x = f[i][0];
+                o.y = f[i][1];
+                o.z = f[i][2];
+                o.w = (real)0;
+                if (i0 + i < tb + ntc) H[t0 + i0 + i] = o;
             }
         }
     }
@@ -264,7 +285,8 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_sta
     size_t smem = (size_t)P2P_CH * (sizeof(typename vec4<real>::t) + sizeof(typename vec2<real>::t)) +
                   (size_t)P2P_NE * sizeof(typename vec4<real>::t) + (2 * P2P_NE + 4) * sizeof(int) +
                   (size_t)KP * (sizeof(real) + sizeof(unsigned)) + 64;
-    static_assert(P2P_CH * 4 >= 3 * PMAX * P2P_T, "L2P powers reuse the staging buffer");
+    static_assert(P2P_CH * 4 >= 3 * PMAX * P2P_T && P2P_CH * 4 >= 3 * P2P_TPT * P2P_T,
+                  "the stripe sums and the L2P powers reuse the staging buffer");
     cudaFuncSetAttribute(k_p2p<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
     k_p2p<real><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start, near_start, near,

@@ -1,0 +1,71 @@
+"""Ensemble step (fmm_batch_*): the Philox rotation of every moment against
+the oracle's rotation, and every sample's field against a single-system
+evaluation and the oracle FMM, over several steps."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0810_0233_gb300 import ccfmm as C
+from paper_0810_0233_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def _ensemble(ns=5, seed=77):
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(800, 4000, size=ns)
+    pos, mom = [], []
+    for i, n in enumerate(sizes):
+        p_, m_ = W.clustered(int(n), seed=seed * 100 + i)
+        pos.append(p_)
+        mom.append(m_)
+    off = np.concatenate([[0], np.cumsum([len(x) for x in pos])]).astype(np.int64)
+    return np.concatenate(pos), np.concatenate(mom), off
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_batch_steps_match_oracle(prec, tol):
+    pos, mom, off = _ensemble()
+    p, theta = 5, 0.5
+    ref_m = mom.copy()
+    with C.Batch(pos, mom, off, p, theta, precision=prec) as b:
+        assert b.kernels_per_step() == 0  # graph not captured yet
+        for step in range(3):
+            H = np.zeros((b.total, 3))
+            E = np.zeros(b.ns)
+            b.step(seed=99, step=step, max_angle=0.05, H_out=H, E_out=E)
+            ref_m = O.rotate_moments(ref_m, 99, step, 0.05)
+            assert np.abs(b.moments() - ref_m).max() < 1e-14
+            for s in range(b.ns):
+                sl = slice(off[s], off[s + 1])
+                Hr, Er, _ = O.fmm_field(pos[sl], ref_m[sl], p, theta)
+                assert rel(H[sl], Hr) < tol, (prec, step, s)
+                assert abs(E[s] - Er) <= 10 * tol * abs(Er)
+        assert b.kernels_per_step() > b.ns
+
+
+def test_batch_equals_single_systems_bitwise():
+    pos, mom, off = _ensemble(ns=4, seed=78)
+    with C.Batch(pos, mom, off, 4, 0.5) as b:
+        H = np.zeros((b.total, 3))
+        b.evaluate(H_out=H)
+        H2 = np.zeros((b.total, 3))
+        b.evaluate(H_out=H2)
+    assert np.array_equal(H, H2)
+    for s in range(4):
+        sl = slice(off[s], off[s + 1])
+        with C.FMM(pos[sl], mom[sl], 4, 0.5) as f:
+            assert np.array_equal(f.field(), H[sl])
+
+
+def test_batch_rejects_bad_offsets():
+    pos = np.random.default_rng(0).uniform(0, 5, (10, 3))
+    mom = np.ones((10, 3))
+    with pytest.raises(C.CCFMMError):
+        C.Batch(pos, mom, [0, 5, 5, 10], 4, 0.5)
+    with pytest.raises(C.CCFMMError):
+        C.Batch(pos, mom, [1, 10], 4, 0.5)

@@ -620,3 +620,39 @@ def test_sampled_downward_matches_full():
     sel = np.isin(f.leaf_of(), [3, 77, 100])
     assert np.array_equal(Hs[sel], H[sel])
     assert np.all(np.isnan(Hs[~sel]))
+
+
+# --------------------------------------------------------------------------
+# Ensemble time step: Philox4x64-10 and the random rotation
+# --------------------------------------------------------------------------
+
+def test_philox_matches_numpy():
+    """The oracle's Philox4x64-10 equals numpy's Philox bit generator, which
+    increments its counter before each block."""
+    for key, ctr in (((7, 11), 5), ((0, 0), 0), ((810233, 3), 123456789)):
+        bg = np.random.Philox(key=np.array(key, dtype=np.uint64),
+                              counter=np.array([ctr, 0, 0, 0], dtype=np.uint64))
+        want = bg.random_raw(4)
+        got = O.philox4x64([ctr + 1, 0, 0, 0], key)
+        assert np.array_equal(got, want)
+
+
+def test_rotation_properties():
+    """Rotations keep |m|, turn by at most max_angle, and are reproducible;
+    axes are isotropic and angles uniform over many draws."""
+    rng = np.random.default_rng(31)
+    m = W.unit_vectors(20000, rng)
+    r = O.rotate_moments(m, seed=5, step=2, max_angle=0.05)
+    assert np.allclose(np.linalg.norm(r, axis=1), 1.0, atol=1e-14)
+    ang = np.arccos(np.clip((m * r).sum(1), -1, 1))
+    assert ang.max() <= 0.05 + 1e-12 and ang.mean() > 0.01
+    assert np.array_equal(r, O.rotate_moments(m, 5, 2, 0.05))
+    assert not np.array_equal(r, O.rotate_moments(m, 5, 3, 0.05))
+    # the first 10 dipoles drawn as a slice equal the same dipoles in the full call
+    assert np.array_equal(O.rotate_moments(m[100:110], 5, 2, 0.05, first=100), r[100:110])
+    # a large angle: the rotation of the axis itself is the identity
+    e = np.tile([0.0, 0.0, 1.0], (5000, 1))
+    big = O.rotate_moments(e, 9, 0, np.pi)
+    assert np.abs((big ** 2).sum(1) - 1).max() < 1e-14
+    # isotropy of the drawn axes: the mean of m' - m over random directions
+    assert np.abs((big - e).mean(0)[:2]).max() < 0.05
