@@ -167,6 +167,15 @@ ccfmm_status fmm_get_leaf_of(ccfmm_t h, int64_t *leaf_of);
 ccfmm_status fmm_get_pairs(ccfmm_t h, int kind, int64_t *pairs, int64_t capacity,
                            int64_t *count);
 
+/* M2L operands: sizes[0..3] = (distinct far offsets, T(2p), M2L entries,
+ * tiles); D_out (offsets x T(2p) float64, the D tensors at scaled
+ * separations, Eqs. Dn/Dnr), ent_u_out (entries: offset id), ent_src_out
+ * (entries x 128: partner heap id or -1), tiles_out (tiles x 8 int32:
+ * level, first, parity, cells, entry start, entry count, offsets, first
+ * offset id).  Any output may be NULL; call with all NULL to get sizes. */
+ccfmm_status fmm_get_m2l_data(ccfmm_t h, int64_t *sizes, double *D_out, int32_t *ent_u_out,
+                              int32_t *ent_src_out, int32_t *tiles_out);
+
 /* Multi-index ordering of the library: orders 0..order, T(order) x 3 int32. */
 ccfmm_status ccfmm_multi_indices(int order, int32_t *out);
 
@@ -223,10 +232,74 @@ ccfmm_status fmm_batch_evaluate(ccfmm_batch_t b, double *H_out, double *E_out);
 ccfmm_status fmm_batch_get_moments(ccfmm_batch_t b, double *out);
 ccfmm_status fmm_batch_set_moments(ccfmm_batch_t b, const double *moments);
 
+/* Handle of sample i, owned by the batch (valid until fmm_batch_destroy),
+ * for inspection with fmm_stats / fmm_get_* only. */
+ccfmm_status fmm_batch_sample(ccfmm_batch_t b, int i, ccfmm_t *out);
+
 /* Total dipoles and kernels launched by one step's graph. */
 ccfmm_status fmm_batch_info(ccfmm_batch_t b, int64_t *total_n, int64_t *kernels_per_step);
 
 void fmm_batch_destroy(ccfmm_batch_t b);
+
+/* ------------------------------------------------------------------------
+ * Parameter selector (a project addition).  The paper chooses the leaf
+ * occupancy by Eq. so and (p_m, alpha_m) by hand from Table II / Fig. 3
+ * (Sec. IV).  Here a small network predicts, for a dipole set's features and
+ * a configuration (p, theta, leaf), y0 = log10(time per dipole in ns) and
+ * y1 = log10(relative RMS field error) of the FMM; fmm_select picks the
+ * fastest grid configuration predicted to meet a target error.
+ *
+ * Features (ccfmm_features, 9 floats): log10 N; occupancy of the depth-Lr
+ * cells of the bisection tree (Lr = max(0, floor(log2(N/16)))):
+ * slog(CV^2), slog(skewness), slog(excess kurtosis), slog(x) = sign(x)
+ * log10(1+|x|); the nearest-neighbour distances of min(N, 2048) sample
+ * points: coefficient of variation, min/mean, Clark-Evans ratio
+ * mean / (0.55396 (V/N)^(1/3)); the box extents sorted: middle/largest,
+ * smallest/largest.  The network input is the 9 features followed by
+ * p, theta and log2(leaf).
+ *
+ * Network: 12-64-64-64-2, ReLU, parameters in the order W1 (12x64,
+ * row-major), b1, W2, b2, W3, b3, W4 (64x2), b4 (ccfmm_mlp_num_params()
+ * floats); normalisation block mu_x[12], sd_x[12], mu_y[2], sd_y[2]
+ * (inputs and targets standardised).  FP32 master weights; the forward and
+ * backward passes use their BF16 roundings with FP32 accumulation.  Loss:
+ * masked mean squared error in standardised units.  Training: Adam
+ * (beta 0.9/0.999, eps 1e-8) over contiguous mini-batches.
+ * All arrays may be host or device memory; calls synchronise the device.
+ * ---------------------------------------------------------------------- */
+typedef struct ccfmm_mlp_s *ccfmm_mlp_t;
+
+ccfmm_status ccfmm_mlp_create(ccfmm_mlp_t *out);
+void ccfmm_mlp_destroy(ccfmm_mlp_t m);
+int32_t ccfmm_mlp_num_params(void);
+/* params: ccfmm_mlp_num_params() floats or NULL; norm: 28 floats or NULL.
+ * Setting resets the Adam state. */
+ccfmm_status ccfmm_mlp_set_params(ccfmm_mlp_t m, const float *params, const float *norm);
+ccfmm_status ccfmm_mlp_get_params(ccfmm_mlp_t m, float *params, float *norm);
+/* Normalisation from data: X (B x 12), T (B x 2) targets, mask (B x 2, 0/1). */
+ccfmm_status ccfmm_mlp_fit_norm(ccfmm_mlp_t m, const float *X, const float *T, const float *mask,
+                                int64_t B);
+/* Loss and its gradient with respect to the (BF16-rounded) parameters. */
+ccfmm_status ccfmm_mlp_gradient(ccfmm_mlp_t m, const float *X, const float *T, const float *mask,
+                                int64_t B, float *grad_out, float *loss_out);
+/* `epochs` passes of Adam over mini-batches of `batch` rows; *loss_out gets
+ * the mean mini-batch loss of the last epoch. */
+ccfmm_status ccfmm_mlp_train(ccfmm_mlp_t m, const float *X, const float *T, const float *mask,
+                             int64_t B, int64_t batch, int32_t epochs, float lr, uint64_t seed,
+                             float *loss_out);
+/* Predictions in physical units: Y (B x 2) = (log10 ns per dipole, log10 error). */
+ccfmm_status ccfmm_mlp_predict(ccfmm_mlp_t m, const float *X, int64_t B, float *Y);
+/* The nine features of a dipole set (positions N x 3 float64). */
+ccfmm_status ccfmm_features(const double *positions, int64_t N, float *out9);
+/* Choose (p, theta, leaf) for a target relative RMS field error: the fastest
+ * configuration on the grid p in 2..8, theta in {0.3..0.7}, leaf in
+ * {4, 8, 16, 32, 64} whose predicted error is below target/2.  Falls back to
+ * the rule of thumb (Eq. so; (5, 0.71) for targets >= 1e-2, else (6, 0.48),
+ * Sec. IV) when m is NULL, the features lie outside the training range (more
+ * than 5 standard deviations) or no configuration qualifies;
+ * *fallback_out (may be NULL) tells which. */
+ccfmm_status fmm_select(ccfmm_mlp_t m, const double *positions, int64_t N, double target_error,
+                        int32_t *p_out, double *theta_out, double *leaf_out, int32_t *fallback_out);
 
 /* ------------------------------------------------------------------------
  * Allocation-free direct field and energy.  The paper has no counterpart:

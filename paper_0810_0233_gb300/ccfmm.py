@@ -91,6 +91,20 @@ def load():
             "fmm_batch_set_moments": (_int, [_vp, _vp]),
             "fmm_batch_info": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
             "fmm_batch_destroy": (None, [_vp]),
+            "fmm_batch_sample": (_int, [_vp, _int, ctypes.POINTER(_vp)]),
+            "fmm_get_m2l_data": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+            "ccfmm_mlp_create": (_int, [ctypes.POINTER(_vp)]),
+            "ccfmm_mlp_destroy": (None, [_vp]),
+            "ccfmm_mlp_num_params": (ctypes.c_int32, []),
+            "ccfmm_mlp_set_params": (_int, [_vp, _vp, _vp]),
+            "ccfmm_mlp_get_params": (_int, [_vp, _vp, _vp]),
+            "ccfmm_mlp_fit_norm": (_int, [_vp, _vp, _vp, _vp, _i64]),
+            "ccfmm_mlp_gradient": (_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+            "ccfmm_mlp_train": (_int, [_vp, _vp, _vp, _vp, _i64, _i64, ctypes.c_int32,
+                                       ctypes.c_float, ctypes.c_uint64, _vp]),
+            "ccfmm_mlp_predict": (_int, [_vp, _vp, _i64, _vp]),
+            "ccfmm_features": (_int, [_vp, _i64, _vp]),
+            "fmm_select": (_int, [_vp, _vp, _i64, _dbl, _vp, _vp, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -187,9 +201,9 @@ class FMM:
         self._h = h
 
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and not getattr(self, "_borrowed", False):
             self._lib.fmm_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -265,6 +279,19 @@ class FMM:
                                        ctypes.byref(cnt)))
         return out[: cnt.value]
 
+    def m2l_data(self):
+        """(D tables, entry offset ids, entry partners, tile descriptors)."""
+        sz = np.zeros(4, dtype=np.int64)
+        _check(self._lib.fmm_get_m2l_data(self._h, _vp(sz.ctypes.data), None, None, None, None))
+        noff, td, ne, nt = (int(x) for x in sz)
+        D = np.zeros((max(noff, 1), td))
+        u = np.zeros(max(ne, 1), dtype=np.int32)
+        s = np.zeros((max(ne, 1), 128), dtype=np.int32)
+        t = np.zeros((max(nt, 1), 8), dtype=np.int32)
+        _check(self._lib.fmm_get_m2l_data(self._h, _vp(sz.ctypes.data), _vp(D.ctypes.data),
+                                          _vp(u.ctypes.data), _vp(s.ctypes.data), _vp(t.ctypes.data)))
+        return D[:noff], u[:ne], s[:ne], t[:nt]
+
     def expansions(self, kind: str) -> np.ndarray:
         """Q ("Q") or V ("V") of every cell, (2^(L+1)) x T(p), library order."""
         k = {"Q": 0, "V": 1}[kind]
@@ -290,6 +317,7 @@ class Batch:
         pm, k2 = _ptr(moments, 3 * self.total)
         prec = {"mixed": MIXED, "fp32": MIXED, "fp64": FP64}[precision]
         h = _vp()
+        self._p = int(p)
         _check(lib.fmm_batch_create(pp, pm, _vp(off.ctypes.data), self.ns, int(p), float(theta),
                                     float(leaf_size), prec, _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
@@ -331,7 +359,113 @@ class Batch:
         pm, k = _ptr(moments, 3 * self.total)
         _check(self._lib.fmm_batch_set_moments(self._h, pm))
 
+    def sample(self, i):
+        """Borrowed FMM view of sample i (inspection only; owned by the batch)."""
+        h = _vp()
+        _check(self._lib.fmm_batch_sample(self._h, int(i), ctypes.byref(h)))
+        f = FMM.__new__(FMM)
+        f._lib = self._lib
+        f._h = h
+        f.n = int(self.offsets[i + 1] - self.offsets[i])
+        f.p = self._p
+        f._borrowed = True
+        return f
+
     def kernels_per_step(self):
         n, k = _i64(), _i64()
         _check(self._lib.fmm_batch_info(self._h, ctypes.byref(n), ctypes.byref(k)))
         return int(k.value)
+
+
+def _f32(a, n=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if n is not None and arr.size != n:
+        raise ValueError("expected %d elements, got %d" % (n, arr.size))
+    return arr
+
+
+def features(positions):
+    """The selector's nine features of a dipole set (ccfmm_features)."""
+    n = positions.shape[0]
+    pp, k = _ptr(positions, 3 * n)
+    out = np.zeros(9, dtype=np.float32)
+    _check(load().ccfmm_features(pp, n, _vp(out.ctypes.data)))
+    return out
+
+
+class MLP:
+    """The selector network (ccfmm_mlp_*): 12-64-64-64-2, BF16 weights."""
+
+    def __init__(self, params=None, norm=None):
+        lib = load()
+        self._lib = lib
+        h = _vp()
+        _check(lib.ccfmm_mlp_create(ctypes.byref(h)))
+        self._h = h
+        self.n_params = int(lib.ccfmm_mlp_num_params())
+        if params is not None or norm is not None:
+            self.set_params(params, norm)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ccfmm_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params=None, norm=None):
+        p = None if params is None else _f32(params, self.n_params)
+        q = None if norm is None else _f32(norm, 28)
+        _check(self._lib.ccfmm_mlp_set_params(
+            self._h, None if p is None else _vp(p.ctypes.data), None if q is None else _vp(q.ctypes.data)))
+
+    def get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        q = np.zeros(28, dtype=np.float32)
+        _check(self._lib.ccfmm_mlp_get_params(self._h, _vp(p.ctypes.data), _vp(q.ctypes.data)))
+        return p, q
+
+    def fit_norm(self, X, T, mask):
+        X, T, M = _f32(X), _f32(T), _f32(mask)
+        _check(self._lib.ccfmm_mlp_fit_norm(self._h, _vp(X.ctypes.data), _vp(T.ctypes.data),
+                                            _vp(M.ctypes.data), len(X)))
+
+    def gradient(self, X, T, mask):
+        X, T, M = _f32(X), _f32(T), _f32(mask)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(self._lib.ccfmm_mlp_gradient(self._h, _vp(X.ctypes.data), _vp(T.ctypes.data),
+                                            _vp(M.ctypes.data), len(X), _vp(g.ctypes.data),
+                                            ctypes.byref(loss)))
+        return float(loss.value), g
+
+    def train(self, X, T, mask, batch=256, epochs=1, lr=1e-3, seed=0):
+        X, T, M = _f32(X), _f32(T), _f32(mask)
+        loss = ctypes.c_float()
+        _check(self._lib.ccfmm_mlp_train(self._h, _vp(X.ctypes.data), _vp(T.ctypes.data),
+                                         _vp(M.ctypes.data), len(X), int(batch), int(epochs),
+                                         float(lr), int(seed), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def predict(self, X):
+        X = _f32(X)
+        Y = np.zeros((len(X), 2), dtype=np.float32)
+        _check(self._lib.ccfmm_mlp_predict(self._h, _vp(X.ctypes.data), len(X), _vp(Y.ctypes.data)))
+        return Y
+
+
+def select(mlp, positions, target_error):
+    """fmm_select: (p, theta, leaf, used_fallback) for a target RMS error."""
+    n = positions.shape[0]
+    pp, k = _ptr(positions, 3 * n)
+    p = ctypes.c_int32()
+    th = _dbl()
+    lf = _dbl()
+    fb = ctypes.c_int32()
+    _check(load().fmm_select(None if mlp is None else mlp._h, pp, n, float(target_error),
+                             ctypes.byref(p), ctypes.byref(th), ctypes.byref(lf), ctypes.byref(fb)))
+    return int(p.value), float(th.value), float(lf.value), bool(fb.value)

@@ -307,6 +307,7 @@ static ccfmm_status check_flags(ccfmm_t h, int flags)
     if (flags & FLAG_OFFSET_RANGE)
         return fail(CCFMM_ERR_STATE, "internal: partner offset outside the planned range");
     if (flags & FLAG_LIST_OVERFLOW) return fail(CCFMM_ERR_STATE, "internal: list overflow");
+    if (flags & FLAG_TIMEOUT) return fail(CCFMM_ERR_TIMEOUT, "a bounded device wait gave up");
     (void)h;
     return CCFMM_OK;
 }
@@ -529,6 +530,12 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
             ni[t] = (int)items.size() - i0[t];
         }
         h->nitems = (int)items.size();
+        // entry ranges of the tiles, known on the host from the scan
+        for (int t = 0; t < h->ntiles; ++t) {
+            tiles[t].ent_start = ts[t];
+            tiles[t].ent_count = ts[t + 1] - ts[t];
+        }
+        CK(cudaMemcpy(h->tiles.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice));
         TRY(ensure(h->items, sizeof(M2LItem) * std::max<size_t>(items.size(), 1)));
         TRY(ensure(h->titem0, sizeof(int) * h->ntiles));
         TRY(ensure(h->tnitems, sizeof(int) * h->ntiles));
@@ -576,11 +583,22 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     launch_p2p_pair_count(L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf, &drb->pairs, s);
     KCHECK();
     if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_B1], s));
+    // the handle is complete when the build returns
+    CK(cudaStreamSynchronize(s));
     h->built = true;
     return CCFMM_OK;
 }
 
 // ------------------------------------------------------------ evaluation
+// M2L contraction engine for the FP32 path: the FP32 FMA kernel, or the
+// tensor-core kernel (orders p = 4..7) when CCFMM_M2L=tc.
+static bool m2l_use_tc()
+{
+    const char *e = getenv("CCFMM_M2L");
+    if (e && !strcmp(e, "tc")) return true;
+    return false;
+}
+
 template <typename real>
 static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
 {
@@ -597,7 +615,13 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
     if (ev) CK(cudaEventRecord(evs[EV_P2M], s));
     for (int l = L - 1; l >= 0; --l) launch_m2m<real>(p, KP, l, P<Geom>(h->geomd), P<real>(h->Q), s);
     if (ev) CK(cudaEventRecord(evs[EV_M2M], s));
-    if (sizeof(real) == 4 && m2l_f32_supported(KP, h->ldD))
+    if (sizeof(real) == 4 && m2l_use_tc() && m2l_tc_supported(KP, h->ldD))
+        launch_m2l_tc(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
+                      P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
+                      P<float>(h->Q), P<float>(h->D), h->ldD, P<uint16_t>(h->itab),
+                      P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V),
+                      &P<Readback>(h->rb)->flags, s);
+    else if (sizeof(real) == 4 && m2l_f32_supported(KP, h->ldD))
         launch_m2l_f32(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
                        P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
                        P<float>(h->Q), P<float>(h->D), h->ldD, P<uint16_t>(h->itab),
@@ -644,7 +668,10 @@ static ccfmm_status evaluate(ccfmm_t h, double *H_out)
         TRY(eval_t<double>(h, Hdev));
     if (host_out) {
         CK(cudaMemcpyAsync(H_out, Hdev, sizeof(double) * 3 * h->N, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(&h->hrb->flags, &P<Readback>(h->rb)->flags, sizeof(int),
+                           cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
+        TRY(check_flags(h, h->hrb->flags));
     }
     return CCFMM_OK;
 }
@@ -934,6 +961,41 @@ ccfmm_status fmm_get_pairs(ccfmm_t h, int kind, int64_t *pairs, int64_t capacity
     return CCFMM_OK;
 }
 
+ccfmm_status fmm_get_m2l_data(ccfmm_t h, int64_t *sizes, double *D_out, int32_t *ent_u_out,
+                              int32_t *ent_src_out, int32_t *tiles_out)
+{
+    g_err.clear();
+    if (!h || !sizes) return fail(CCFMM_ERR_ARG, "NULL argument");
+    if (!h->built) return fail(CCFMM_ERR_STATE, "no tree");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    sizes[0] = h->n_off;
+    sizes[1] = h->TD;
+    sizes[2] = h->ent_total;
+    sizes[3] = h->ntiles;
+    if (D_out && h->n_off > 0) {
+        size_t n = (size_t)h->n_off * h->ldD;
+        std::vector<double> d(n);
+        if (h->prec == CCFMM_MIXED) {
+            std::vector<float> f(n);
+            CK(cudaMemcpy(f.data(), h->D.p, sizeof(float) * n, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < n; ++i) d[i] = f[i];
+        } else {
+            CK(cudaMemcpy(d.data(), h->D.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        }
+        for (int r = 0; r < h->n_off; ++r)
+            for (int t = 0; t < h->TD; ++t) D_out[(size_t)r * h->TD + t] = d[(size_t)r * h->ldD + t];
+    }
+    if (ent_u_out && h->ent_total > 0)
+        CK(cudaMemcpy(ent_u_out, h->ent_u.p, sizeof(int) * h->ent_total, cudaMemcpyDeviceToHost));
+    if (ent_src_out && h->ent_total > 0)
+        CK(cudaMemcpy(ent_src_out, h->ent_src.p, sizeof(int) * TT * h->ent_total,
+                      cudaMemcpyDeviceToHost));
+    if (tiles_out && h->ntiles > 0)
+        CK(cudaMemcpy(tiles_out, h->tiles.p, sizeof(Tile) * h->ntiles, cudaMemcpyDeviceToHost));
+    return CCFMM_OK;
+}
+
 ccfmm_status ccfmm_multi_indices(int order, int32_t *out)
 {
     g_err.clear();
@@ -1138,11 +1200,44 @@ static ccfmm_status batch_capture(ccfmm_batch_t b, int rotate)
     return CCFMM_OK;
 }
 
+// the step without a graph: the same launches issued directly on the branch
+// streams (CCFMM_BATCH_NOGRAPH=1)
+static ccfmm_status batch_direct(ccfmm_batch_t b, int rotate)
+{
+    cudaStream_t s = b->stream;
+    if (rotate) launch_rotate(P<double>(b->mom), b->total, P<RotateParams>(b->prm), s);
+    CK(cudaEventRecord(b->evf, s));
+    for (int r = 0; r < b->nbr; ++r) CK(cudaStreamWaitEvent(b->br[r], b->evf, 0));
+    for (int i = 0; i < b->ns; ++i) {
+        ccfmm_t hs = b->h[i];
+        const double *ms = P<double>(b->mom) + 3 * b->off[i];
+        if (hs->prec == CCFMM_MIXED) {
+            launch_permute_moments<float>(ms, P<int>(hs->idx), hs->N, P<float4>(hs->A),
+                                          P<float2>(hs->B), hs->stream);
+            TRY(eval_t<float>(hs, P<double>(b->H) + 3 * b->off[i]));
+        } else {
+            launch_permute_moments<double>(ms, P<int>(hs->idx), hs->N, P<double4>(hs->A),
+                                           P<double2>(hs->B), hs->stream);
+            TRY(eval_t<double>(hs, P<double>(b->H) + 3 * b->off[i]));
+        }
+    }
+    for (int r = 0; r < b->nbr; ++r) {
+        CK(cudaEventRecord(b->evj[r], b->br[r]));
+        CK(cudaStreamWaitEvent(s, b->evj[r], 0));
+    }
+    return CCFMM_OK;
+}
+
 static ccfmm_status batch_run(ccfmm_batch_t b, int rotate, double *H_out, double *E_out)
 {
-    if (!b->exec[rotate]) TRY(batch_capture(b, rotate));
-    CK(cudaGraphLaunch(b->exec[rotate], b->stream));
-    note_launch((int)b->graph_kernels[rotate]);
+    const char *ng = getenv("CCFMM_BATCH_NOGRAPH");
+    if (ng && atoi(ng)) {
+        TRY(batch_direct(b, rotate));
+    } else {
+        if (!b->exec[rotate]) TRY(batch_capture(b, rotate));
+        CK(cudaGraphLaunch(b->exec[rotate], b->stream));
+        note_launch((int)b->graph_kernels[rotate]);
+    }
     if (H_out) {
         cudaMemcpyKind k = is_device_ptr(H_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         CK(cudaMemcpyAsync(H_out, b->H.p, sizeof(double) * 3 * b->total, k, b->stream));
@@ -1222,7 +1317,10 @@ ccfmm_status fmm_batch_create(const double *positions, const double *moments,
         BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
         b->own_stream = true;
     }
-    b->nbr = std::min(nsamples, 32);
+    // parallel branches of the step graph (CCFMM_BATCH_BRANCHES overrides)
+    int maxbr = 32;
+    if (const char *e = getenv("CCFMM_BATCH_BRANCHES")) maxbr = std::max(1, atoi(e));
+    b->nbr = std::min(nsamples, maxbr);
     for (int r = 0; r < b->nbr; ++r) {
         cudaStream_t s;
         cudaEvent_t e;
@@ -1252,6 +1350,9 @@ ccfmm_status fmm_batch_create(const double *positions, const double *moments,
         hs->E_dst = P<double>(b->E) + i;
         b->h.push_back(hs);
     }
+    // the handles' builds end with kernels still queued on the branch
+    // streams; a captured graph would not depend on them
+    for (cudaStream_t s : b->br) BCK(cudaStreamSynchronize(s));
 #undef BTRY
 #undef BCK
     *out = b;
@@ -1302,6 +1403,15 @@ ccfmm_status fmm_batch_set_moments(ccfmm_batch_t b, const double *moments)
     cudaMemcpyKind k = is_device_ptr(moments) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(b->mom.p, moments, sizeof(double) * 3 * b->total, k, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_batch_sample(ccfmm_batch_t b, int i, ccfmm_t *out)
+{
+    g_err.clear();
+    if (!b || !out || i < 0 || i >= b->ns) return fail(CCFMM_ERR_ARG, "bad argument");
+    CK(cudaStreamSynchronize(b->stream));
+    *out = b->h[i];
     return CCFMM_OK;
 }
 

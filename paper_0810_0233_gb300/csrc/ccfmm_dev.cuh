@@ -67,7 +67,8 @@ enum : int {
     FLAG_OUTSIDE_BOX = 2,
     FLAG_OFFSET_RANGE = 4,
     FLAG_LIST_OVERFLOW = 8,
-    FLAG_TILE_OVERFLOW = 16
+    FLAG_TILE_OVERFLOW = 16,
+    FLAG_TIMEOUT = 32
 };
 
 // Per-level table classifying an integer cell offset o = (coords of field
@@ -189,6 +190,15 @@ void launch_m2l_f32(int p, int KP, const Tile *tiles, int ntiles, const M2LItem 
                     int nitems, const int *tile_item0, const int *tile_nitems, const int *ent_u,
                     const int *ent_src, const float *Q, const float *D, int ldD,
                     const uint16_t *it, const Geom *g, float *Ps, double *V, cudaStream_t s);
+void launch_m2l_reduce(int p, int KP, const Tile *tiles, int ntiles, const int *tile_item0,
+                       const int *tile_nitems, const float *Ps, const Geom *g, double *V,
+                       cudaStream_t s);
+// tensor-core (tcgen05, 3xTF32) M2L for KP in {40, 56, 88, 120}
+bool m2l_tc_supported(int KP, int ldD);
+void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items, int nitems,
+                   const int *tile_item0, const int *tile_nitems, const int *ent_u,
+                   const int *ent_src, const float *Q, const float *D, int ldD, const uint16_t *it,
+                   const Geom *g, float *Ps, double *V, int *flags, cudaStream_t s);
 template <typename real>
 void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
                 const int *ent_src, const real *Q, const real *D, int ldD, const uint16_t *it,

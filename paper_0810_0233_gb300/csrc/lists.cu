@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(TL_T) k_tile_count(const Tile *tiles, const in
     }
 }
 
-__global__ void __launch_bounds__(TL_T) k_tile_fill(Tile *tiles, const int *ent_start,
+__global__ void __launch_bounds__(TL_T) k_tile_fill(const Tile *tiles, const int *ent_start,
                                                     const int *far_off, const int *far_num,
                                                     const FarEnt *far, int *ent_u, int *ent_src)
 {
@@ -268,10 +268,6 @@ __global__ void __launch_bounds__(TL_T) k_tile_fill(Tile *tiles, const int *ent_
     __syncthreads();
     int start = ent_start[blockIdx.x];
     int count = ent_start[blockIdx.x + 1] - start;
-    if (threadIdx.x == 0) {
-        tiles[blockIdx.x].ent_start = start;
-        tiles[blockIdx.x].ent_count = count;
-    }
     for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
         unsigned b = bm[w];
         int r = (int)wpre[w];

@@ -65,6 +65,9 @@ __global__ void __launch_bounds__(KP * 4) k_m2l(int p, const Tile *tiles, const 
         gk[c] = (real)gv;
         en[c] = ev;
     }
+    // gk and en are read across warps; a tile may have no entries, in which
+    // case the entry loop (and its barriers) does not run
+    __syncthreads();
     real acc[4][8];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -304,10 +307,16 @@ void launch_m2l_f32(int p, int KP, const Tile *tiles, int ntiles, const M2LItem 
         }
 #undef M2LF
     }
-    if (ntiles > 0) {
-        note_launch();
-        k_m2l_reduce<<<ntiles, 256, 0, s>>>(p, KP, tiles, tile_item0, tile_nitems, Ps, g, V);
-    }
+    launch_m2l_reduce(p, KP, tiles, ntiles, tile_item0, tile_nitems, Ps, g, V, s);
+}
+
+void launch_m2l_reduce(int p, int KP, const Tile *tiles, int ntiles, const int *tile_item0,
+                       const int *tile_nitems, const float *Ps, const Geom *g, double *V,
+                       cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    note_launch();
+    k_m2l_reduce<<<ntiles, 256, 0, s>>>(p, KP, tiles, tile_item0, tile_nitems, Ps, g, V);
 }
 
 template <typename real, int KP, int KC>

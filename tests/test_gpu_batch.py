@@ -69,3 +69,22 @@ def test_batch_rejects_bad_offsets():
         C.Batch(pos, mom, [0, 5, 5, 10], 4, 0.5)
     with pytest.raises(C.CCFMMError):
         C.Batch(pos, mom, [1, 10], 4, 0.5)
+
+
+def test_fp64_pair_with_levels_without_m2l_entries():
+    """Two clustered samples whose first has levels with far offsets but no
+    M2L entries: that tile's epilogue must not depend on the entry loop's
+    barriers (it once read scale factors other warps had not yet written)."""
+    pos, mom, off = _ensemble()
+    o = off[:3]
+    P, M = pos[:o[-1]], mom[:o[-1]]
+    with C.Batch(P, M, o, 5, 0.5, precision="fp64") as b:
+        H = np.zeros((b.total, 3))
+        b.evaluate(H_out=H)
+        tiles = b.sample(0).m2l_data()[3]
+    assert np.any(tiles[:, 5] == 0)  # a tile with no entries
+    assert np.all(np.isfinite(H))
+    for s in range(2):
+        sl = slice(o[s], o[s + 1])
+        with C.FMM(P[sl], M[sl], 5, 0.5, precision="fp64") as f:
+            assert rel(H[sl], f.field()) < 1e-13

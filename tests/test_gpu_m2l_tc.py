@@ -1,0 +1,43 @@
+"""The tensor-core M2L (tcgen05, TF32 three-product split) against the FP32
+FMA M2L and the FP64 oracle, for every order it supports (p = 4..7)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0810_0233_gb300 import ccfmm as C
+from paper_0810_0233_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def _run(engine, pos, mom, p, theta):
+    old = os.environ.get("CCFMM_M2L")
+    os.environ["CCFMM_M2L"] = engine
+    try:
+        with C.FMM(pos, mom, p, theta) as f:
+            H = f.field()
+            V = f.expansions("V")
+    finally:
+        if old is None:
+            del os.environ["CCFMM_M2L"]
+        else:
+            os.environ["CCFMM_M2L"] = old
+    return H, V
+
+
+@pytest.mark.parametrize("p", [4, 5, 6, 7])
+def test_tensor_core_m2l_matches(p):
+    pos, mom = W.ferrofluid(20000, side=100.0 * 0.02 ** (1 / 3), seed=W.BASE_SEED + 30 + p)
+    Hf, Vf = _run("fma", pos, mom, p, 0.5)
+    Ht, Vt = _run("tc", pos, mom, p, 0.5)
+    nz = np.abs(Vf).sum(1) > 0
+    assert rel(Vt[nz], Vf[nz]) < 2e-5
+    assert rel(Ht, Hf) < 2e-6
+    Href = O.fmm_field(pos, mom, p, 0.5)[0]
+    assert rel(Ht, Href) < 1e-5

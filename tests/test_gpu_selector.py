@@ -1,0 +1,78 @@
+"""The parameter selector on the GPU: gradients of the library's MLP kernels
+against the CPU oracle (oracle/mlp.py), features on known sets, training
+reducing the loss, and a small sweep -> train -> select that beats the rule
+of thumb at a 1e-4 target on a held-out instance."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_0810_0233_gb300 import ccfmm as C
+from paper_0810_0233_gb300 import selector as S
+from paper_0810_0233_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_gradient_matches_oracle():
+    rng = np.random.default_rng(0)
+    B = 1000
+    theta = (rng.standard_normal(M.n_params()) * 0.15).astype(np.float32)
+    X = (rng.standard_normal((B, 12)) * 2 + 0.5).astype(np.float32)
+    T = rng.standard_normal((B, 2)).astype(np.float32)
+    mask = (rng.uniform(size=(B, 2)) > 0.1).astype(np.float32)
+    mlp = C.MLP(theta)
+    mlp.fit_norm(X, T, mask)
+    _, norm = mlp.get_params()
+    nrm = (norm[:12].astype(np.float64), norm[12:24].astype(np.float64),
+           norm[24:26].astype(np.float64), norm[26:28].astype(np.float64))
+    L_gpu, g_gpu = mlp.gradient(X, T, mask)
+    L_ref, g_ref = M.loss_and_grad(M.bf16(theta), X, T, mask, nrm)
+    assert abs(L_gpu - L_ref) <= 1e-5 * abs(L_ref)
+    rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    assert rel < 1e-4, rel
+    # predictions are the forward pass in physical units
+    Y = mlp.predict(X[:50])
+    Yr, _ = M.forward(M.bf16(theta), X[:50], nrm)
+    assert np.allclose(Y, Yr * nrm[3] + nrm[2], rtol=1e-4, atol=1e-4)
+
+
+def test_training_reduces_loss():
+    rng = np.random.default_rng(1)
+    X = rng.uniform(-1, 1, size=(4096, 12)).astype(np.float32)
+    T = np.stack([np.sin(2 * X[:, 0]) + X[:, 1] * X[:, 2], np.cos(X[:, 3]) - X[:, 4] ** 2],
+                 axis=1).astype(np.float32)
+    mlp, _ = S.train(X, T, epochs=1)
+    mask = np.ones_like(T)
+    L0, _ = mlp.gradient(X, T, mask)
+    for _ in range(40):
+        mlp.train(X, T, mask, batch=256, epochs=1, lr=2e-3)
+    L1, _ = mlp.gradient(X, T, mask)
+    assert L1 < 0.2 * L0, (L0, L1)
+
+
+def test_features_distinguish_sets():
+    lat, _, _ = W.lattice(20)
+    clu, _ = W.clustered(8000, seed=5)
+    fl = C.features(lat)
+    fc = C.features(clu)
+    assert abs(fl[0] - math.log10(8000)) < 1e-6
+    # a lattice has equal nearest-neighbour distances and flat occupancy
+    assert fl[4] < 1e-3 and abs(fl[5] - 1) < 1e-3
+    assert fc[1] > fl[1] and fc[4] > 0.05
+    assert abs(fl[7] - 1) < 1e-6 and abs(fl[8] - 1) < 1e-6
+
+
+def test_selector_beats_rule_of_thumb():
+    """Small sweep and training; on a held-out instance at target 1e-4 the
+    selected configuration meets the target and is faster than the rule of
+    thumb (which is far more accurate than needed)."""
+    X, T = S.sweep(n_runs=1200, per_instance=40, n_lo=3000, n_hi=40000, seed=11)
+    mlp, loss = S.train(X, T, epochs=60)
+    pos, mom = S.instance("uniform", 120000, seed=4242)
+    res = S.evaluate(mlp, pos, mom, target=1e-4, autotune_leaves=(16, 26.64, 48))
+    sel, rule = res["selector"], res["rule_of_thumb"]
+    assert sel["error"] <= 1e-4, res
+    assert rule["error"] <= 1e-4
+    assert sel["ns_per_dipole"] < rule["ns_per_dipole"], res
