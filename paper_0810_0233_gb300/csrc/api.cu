@@ -109,6 +109,11 @@ struct Readback {
     unsigned long long pairs;
     double box6[6];
     double E;
+    // raised by evaluation kernels (bounded waits); kept across builds until
+    // a synchronising call has reported it.  Last member: the build clears
+    // everything before it.
+    int eflags;
+    int pad2;
 };
 
 struct LevelPlan {
@@ -144,6 +149,8 @@ struct ccfmm_s {
     int n_off = 0, ntiles = 0, max_bits = 0;
     long long near_leaf_total = 0, far_total = 0, ent_total = 0;
     bool built = false, evaluated = false, ftable_ready = false;
+    bool tc_ops_ready = false;  // tensor-core M2L operators of the current build
+    bool rb_fresh = true;       // device readback block not yet initialised
     bool leaf_perm_valid = false;
 
     DevBuf pos, mom, keys, keys2, keys3, idx, idx2, idx3, sorttemp, scantemp;
@@ -153,6 +160,7 @@ struct ccfmm_s {
     DevBuf far, far_off, far_num, tiles, tcount, tstart, ent_u, ent_src;
     DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
     DevBuf Hout, epart, items, titem0, tnitems, Ps;
+    DevBuf Qs, Bop, gkt;  // tensor-core M2L: split moments, operators, level scales
     int nitems = 0;
     // batch members: energy input and output redirected, no stage events
     const double *mom_energy = nullptr;
@@ -325,7 +333,12 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     TRY(ensure(h->box6, 6 * sizeof(double)));
     TRY(ensure(h->partial, 6 * sizeof(double) * 1024));
     Readback *drb = P<Readback>(h->rb);
-    CK(cudaMemsetAsync(drb, 0, sizeof(Readback), s));
+    if (h->rb_fresh) {
+        CK(cudaMemsetAsync(drb, 0, sizeof(Readback), s));
+        h->rb_fresh = false;
+    } else {
+        CK(cudaMemsetAsync(drb, 0, offsetof(Readback, eflags), s));
+    }
     const double *ubox = nullptr;
     if (h->has_box) {
         TRY(ensure(h->userbox, 6 * sizeof(double)));
@@ -354,6 +367,13 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     CK(cudaMemcpyAsync(h->hrb, drb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&h->geom, h->geomd.p, sizeof(Geom), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (h->hrb->eflags) {
+        // reported once: an evaluation since the last synchronising call
+        // gave up on a bounded wait
+        CK(cudaMemsetAsync(&drb->eflags, 0, sizeof(int), s));
+        CK(cudaStreamSynchronize(s));
+        TRY(check_flags(h, h->hrb->eflags));
+    }
     TRY(check_flags(h, h->hrb->flags));
 
     // depth: L minimising |N / nonempty_L - s| (ties to the smaller L);
@@ -586,17 +606,22 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     // the handle is complete when the build returns
     CK(cudaStreamSynchronize(s));
     h->built = true;
+    h->tc_ops_ready = false;
     return CCFMM_OK;
 }
 
 // ------------------------------------------------------------ evaluation
-// M2L contraction engine for the FP32 path: the FP32 FMA kernel, or the
-// tensor-core kernel (orders p = 4..7) when CCFMM_M2L=tc.
-static bool m2l_use_tc()
+// M2L contraction engine for the FP32 path of a standalone handle: the
+// tensor-core kernel (orders p = 4..7) unless CCFMM_M2L=fma, which selects
+// the FP32 FMA kernel.  Ensemble members use the FMA kernel (the tensor-core
+// operators are stored per handle).
+static bool m2l_use_tc(ccfmm_t h)
 {
+    if (h->prec != CCFMM_MIXED || h->quiet || !m2l_tc_supported(h->KP)) return false;
     const char *e = getenv("CCFMM_M2L");
+    if (e && !strcmp(e, "fma")) return false;
     if (e && !strcmp(e, "tc")) return true;
-    return false;
+    return M2L_TC_DEFAULT;
 }
 
 template <typename real>
@@ -615,12 +640,22 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
     if (ev) CK(cudaEventRecord(evs[EV_P2M], s));
     for (int l = L - 1; l >= 0; --l) launch_m2m<real>(p, KP, l, P<Geom>(h->geomd), P<real>(h->Q), s);
     if (ev) CK(cudaEventRecord(evs[EV_M2M], s));
-    if (sizeof(real) == 4 && m2l_use_tc() && m2l_tc_supported(KP, h->ldD))
+    if (sizeof(real) == 4 && m2l_use_tc(h)) {
+        const int KT = m2l_tc_kt(KP);
+        if (!h->tc_ops_ready) {
+            TRY(ensure(h->Bop, m2l_tc_op_bytes(KP) * (size_t)std::max(h->n_off, 1)));
+            TRY(ensure(h->gkt, sizeof(float) * (size_t)(LCAP + 1) * KT));
+            launch_m2l_tc_ops(p, KP, L, h->n_off, P<Geom>(h->geomd), P<float>(h->D), h->ldD,
+                              P<uint16_t>(h->itab), P<float>(h->gkt), P<float>(h->Bop), s);
+            h->tc_ops_ready = true;
+        }
+        TRY(ensure(h->Qs, sizeof(float) * 2 * (size_t)ncellp * KT));
         launch_m2l_tc(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
                       P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
-                      P<float>(h->Q), P<float>(h->D), h->ldD, P<uint16_t>(h->itab),
-                      P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V),
-                      &P<Readback>(h->rb)->flags, s);
+                      P<float>(h->Q), ncellp, P<float>(h->gkt), P<float>(h->Qs),
+                      P<float>(h->Bop), P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V),
+                      &P<Readback>(h->rb)->eflags, s);
+    }
     else if (sizeof(real) == 4 && m2l_f32_supported(KP, h->ldD))
         launch_m2l_f32(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
                        P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
@@ -670,7 +705,14 @@ static ccfmm_status evaluate(ccfmm_t h, double *H_out)
         CK(cudaMemcpyAsync(H_out, Hdev, sizeof(double) * 3 * h->N, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaMemcpyAsync(&h->hrb->flags, &P<Readback>(h->rb)->flags, sizeof(int),
                            cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(&h->hrb->eflags, &P<Readback>(h->rb)->eflags, sizeof(int),
+                           cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
+        if (h->hrb->eflags) {
+            CK(cudaMemsetAsync(&P<Readback>(h->rb)->eflags, 0, sizeof(int), h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            TRY(check_flags(h, h->hrb->eflags));
+        }
         TRY(check_flags(h, h->hrb->flags));
     }
     return CCFMM_OK;
@@ -881,7 +923,7 @@ void fmm_destroy(ccfmm_t h)
                       &h->far, &h->far_off, &h->far_num, &h->tiles, &h->tcount, &h->tstart,
                       &h->ent_u, &h->ent_src, &h->offs, &h->fst, &h->fq, &h->fval, &h->fdense,
                       &h->D, &h->itab, &h->Q, &h->V, &h->Hout, &h->epart, &h->items,
-                      &h->titem0, &h->tnitems, &h->Ps};
+                      &h->titem0, &h->tnitems, &h->Ps, &h->Qs, &h->Bop, &h->gkt};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hrb) cudaFreeHost(h->hrb);

@@ -41,3 +41,21 @@ def test_tensor_core_m2l_matches(p):
     assert rel(Ht, Hf) < 2e-6
     Href = O.fmm_field(pos, mom, p, 0.5)[0]
     assert rel(Ht, Href) < 1e-5
+
+
+@pytest.mark.parametrize("kind", ["clustered", "ring"])
+def test_tensor_core_m2l_irregular(kind):
+    """Clustered and flat point sets: tiles with many cells lacking a given
+    partner (zero rows) and boxes whose levels are not cubes."""
+    if kind == "clustered":
+        pos, mom = W.clustered(30000, seed=W.BASE_SEED + 41)
+    else:
+        pos, mom = W.ring(r_out=60.0, r_in=20.0, seed=W.BASE_SEED + 42)
+    Hf, Vf = _run("fma", pos, mom, 6, 0.5)
+    Ht, Vt = _run("tc", pos, mom, 6, 0.5)
+    nz = np.abs(Vf).sum(1) > 0
+    assert rel(Vt[nz], Vf[nz]) < 2e-5
+    assert rel(Ht, Hf) < 2e-6
+    sub = W.subset(len(pos), 300, 5)
+    Hd = C.direct_field(pos, mom, targets=sub)
+    assert rel(Ht[sub], Hd) < 1e-4
