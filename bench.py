@@ -31,9 +31,13 @@ sys.path.insert(0, ROOT)
 METRIC = "dipole fields/s at RMS err ≤1e-4 (FP32 vs FP64 FMM, 1 GB300); % roofline"
 P, THETA = 6, 0.5
 FP32_LANES_PER_SM, SMS = 128, 152
-# dram read+write bytes per launch from ncu, with the hash of the kernel
-# source they were taken on; reported only while the source is unchanged
-NCU_TRAFFIC = {}
+# dram read+write bytes per launch of the 10^6-dipole workload from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the
+# kernel source they were taken on; reported only while it is unchanged
+NCU_TRAFFIC = {"p2p": {"bytes": 133587456, "src": "6ce6d8ef0cc8"},
+               "m2l": {"bytes": 395494656, "src": "615b8261679a"}}
+# dense TF32 tensor peak = measured bf16 peak x nominal 1.1 / 2.25
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def _src_hash(name):
@@ -117,7 +121,7 @@ def describe(n, leaf):
             "l2": "flushed between timed steps by a 256 MB write"}
 
 
-def cpu_oracle_sample(pos, mom, nleaves=2048, seed=11):
+def cpu_oracle_sample(pos, mom, nleaves=4096, seed=11):
     """The CPU oracle on a bounded sample of the workload: tree, lists and
     upward pass over every dipole, then the downward pass and near field for
     `nleaves` random occupied leaves.  Fields/s is extrapolated to the full
@@ -293,21 +297,34 @@ def main():
     clock = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12  # TFLOP/s
     flops = {"p2p": 30.0 * st["p2p_pairs"], "m2l": 2.0 * K * K * st["far_pairs"]}
+    tc = args.precision == "mixed" and os.environ.get("CCFMM_M2L", "tc") != "fma"
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
+    src = {"p2p": "p2p.cu", "m2l": "m2l_tc.cu" if tc else "m2l.cu"}
+
+    def traffic(k):
+        tr = NCU_TRAFFIC.get(k)
+        return tr["bytes"] if tr and tr.get("src") == _src_hash(src[k]) else None
+
+    def roof(k):
+        ach = flops[k] / (stages[k] * 1e-3) / 1e12
+        if k == "m2l" and tc:
+            return {"kernel": "m2l", "bound": "tensor", "achieved": ach, "peak": tf32_peak,
+                    "unit": "TFLOP/s", "frac": ach / tf32_peak, "traffic": traffic(k),
+                    "peak_note": "dense TF32 tensor peak = measured bf16 %.0f TFLOP/s x 1.1/2.25; "
+                                 "3xTF32 issues 3 MMAs per product, so 1/3 of it is the ceiling for "
+                                 "FP32-accurate results" % peaks.get("bf16_tflops", 1900.0),
+                    "frac_of_3xtf32": 3 * ach / tf32_peak,
+                    "stage": "moment split + tcgen05 contraction + FP64 reduce"}
+        return {"kernel": k, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": traffic(k),
+                "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clock}
+
     dom = max(("p2p", "m2l"), key=lambda k: stages[k])
-    ach = flops[dom] / (stages[dom] * 1e-3) / 1e12
-    src = {"p2p": "p2p.cu", "m2l": "m2l.cu"}[dom]
-    tr = NCU_TRAFFIC.get(dom)
-    traffic = tr["bytes"] if tr and tr.get("src") == _src_hash(src) else None
-    line["roofline"] = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak,
-                        "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
-                        "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x %.0f MHz" % clock,
-                        "algorithmic": {"p2p_flop_per_pair": 30, "p2p_pairs": st["p2p_pairs"],
-                                        "m2l_flop_per_far_pair": 2 * K * K,
-                                        "far_pairs": st["far_pairs"]},
-                        "stage_ms": stages,
-                        "other": {k: {"achieved": flops[k] / (stages[k] * 1e-3) / 1e12,
-                                      "frac": flops[k] / (stages[k] * 1e-3) / 1e12 / fp32_peak}
-                                  for k in flops}}
+    line["roofline"] = dict(roof(dom), **{
+        "algorithmic": {"p2p_flop_per_pair": 30, "p2p_pairs": st["p2p_pairs"],
+                        "m2l_flop_per_far_pair": 2 * K * K, "far_pairs": st["far_pairs"]},
+        "stage_ms": stages,
+        "other": {k: roof(k) for k in flops if k != dom}})
     line["clocks"] = clk.summary()
     line["build_ms"] = st["ms_build"]
 
@@ -316,7 +333,6 @@ def main():
         sub = W.subset(n, 10000, 77)
         Hd = C.direct_field(pos_d, mom_d, targets=torch.from_numpy(sub).to(dev), stream=stream)
         H = H_d.cpu().numpy()
-        Hd = Hd if isinstance(Hd, np.ndarray) else Hd
         err_direct = float(np.sqrt(((H[sub] - Hd) ** 2).sum() / (Hd ** 2).sum()))
         acc = {"rms_vs_direct_10k": err_direct}
         if args.precision == "mixed":

@@ -256,21 +256,27 @@ __global__ void __launch_bounds__(KP * 4) k_m2l_f32(int p, const Tile *tiles, co
 __global__ void k_m2l_reduce(int p, int KP, const Tile *tiles, const int *tile_item0,
                              const int *tile_nitems, const float *Ps, const Geom *g, double *V)
 {
+    // en[n] = (-1)^|n| h^-(|n|+2) of the tile's level, once per block (FP64
+    // pow is costly; one per coefficient, not one per output)
+    extern __shared__ double en[];
     const int tile = blockIdx.x;
     const Tile t = tiles[tile];
     const int K = nterms(p) - 1;
     const double h = g->h[t.level];
+    for (int n = threadIdx.x; n < K; n += blockDim.x) {
+        int nx, ny, nz;
+        midx_inv(n + 1, nx, ny, nz);
+        const int kn = nx + ny + nz;
+        en[n] = ((kn & 1) ? -1.0 : 1.0) * pow(h, -(double)(kn + 2));
+    }
+    __syncthreads();
     const int i0 = tile_item0[tile], ni = tile_nitems[tile];
     for (int j = threadIdx.x; j < t.nt * K; j += blockDim.x) {
         int ti = j / K, n = j - ti * K;
         double s = 0.0;
         for (int it = 0; it < ni; ++it) s += (double)Ps[((long long)(i0 + it) * TT + ti) * KP + n];
-        int nx, ny, nz;
-        midx_inv(n + 1, nx, ny, nz);
-        int kn = nx + ny + nz;
-        double en = ((kn & 1) ? -1.0 : 1.0) * pow(h, -(double)(kn + 2));
         long long hid = (1ll << t.level) + 2ll * (t.first + ti) + t.parity;
-        V[hid * KP + n] = s * en;
+        V[hid * KP + n] = s * en[n];
     }
 }
 
@@ -316,7 +322,8 @@ void launch_m2l_reduce(int p, int KP, const Tile *tiles, int ntiles, const int *
 {
     if (ntiles <= 0) return;
     note_launch();
-    k_m2l_reduce<<<ntiles, 256, 0, s>>>(p, KP, tiles, tile_item0, tile_nitems, Ps, g, V);
+    k_m2l_reduce<<<ntiles, 256, sizeof(double) * (nterms(p) - 1), s>>>(p, KP, tiles, tile_item0,
+                                                                     tile_nitems, Ps, g, V);
 }
 
 template <typename real, int KP, int KC>
