@@ -29,7 +29,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "dipole fields/s at RMS err ≤1e-4 (FP32 vs FP64 FMM, 1 GB300); % roofline"
-P, THETA = 6, 0.5
 FP32_LANES_PER_SM, SMS = 128, 152
 # dram read+write bytes per launch of the 10^6-dipole workload from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the
@@ -103,32 +102,48 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def workload(n=1_000_000):
-    """The ferrofluid; n < 10^6 keeps the density (box side scaled) and is
-    used only for small profiling cases."""
+# (p, theta) per workload
+WORKLOADS = {"ferrofluid": (6, 0.5), "ring": (6, 0.4), "ring-stated": (6, 0.4),
+             "ensemble": (5, 0.5)}
+
+
+def workload(name="ferrofluid", n=1_000_000):
+    """Positions and moments of a single-system workload.  The ferrofluid at
+    n < 10^6 keeps the density (box side scaled) and is used only for small
+    profiling cases."""
     from paper_0810_0233_gb300 import workloads as W
+    if name == "ring":
+        return W.ring()
+    if name == "ring-stated":
+        return W.ring(r_out=1200.0, r_in=400.0)
     if n == 1_000_000:
         return W.ferrofluid()
     return W.ferrofluid(n, side=100.0 * (n / 1e6) ** (1.0 / 3.0))
 
 
-def describe(n, leaf):
-    return {"workload": "ferrofluid: N=%d uniform in [0,100]^3, min separation 0.5, unit moments "
-                        "uniform on the sphere (seed 810235)" % n,
-            "N": n, "p": P, "theta": THETA, "leaf_size": leaf,
+def describe(name, n, leaf, p, theta):
+    text = {
+        "ferrofluid": "ferrofluid: N=%d uniform in [0,100]^3, min separation 0.5, unit moments "
+                      "uniform on the sphere (seed 810235)" % n,
+        "ring": "ring: N=%d, 3 layers at spacing 1, radii 707.58/235.86 (the stated ring scaled "
+                "to 2^22 points), tilted vortex moments (seed 810236)" % n,
+        "ring-stated": "ring: N=%d, 3 layers at spacing 1, radii 1200/400 as stated, tilted "
+                       "vortex moments (seed 810236)" % n,
+    }[name]
+    return {"workload": text, "N": n, "p": p, "theta": theta, "leaf_size": leaf,
             "precision": "FP32 bulk; FP64 D tensors and FP64 local-expansion accumulation",
             "step": "tree + lists + D tables + field evaluation (P2M..P2P, unpermute)",
             "l2": "flushed between timed steps by a 256 MB write"}
 
 
-def cpu_oracle_sample(pos, mom, nleaves=4096, seed=11):
+def cpu_oracle_sample(pos, mom, p, theta, nleaves=4096, seed=11):
     """The CPU oracle on a bounded sample of the workload: tree, lists and
     upward pass over every dipole, then the downward pass and near field for
     `nleaves` random occupied leaves.  Fields/s is extrapolated to the full
     evaluation: N / (t_setup + t_sample * occupied_leaves / nleaves)."""
     import oracle as O
     t0 = time.perf_counter()
-    f = O.OracleFMM(pos, mom, P, THETA, 0.0)
+    f = O.OracleFMM(pos, mom, p, theta, 0.0)
     f.upward()
     t_setup = time.perf_counter() - t0
     leaf_of = f.leaf_of()
@@ -151,29 +166,177 @@ def cpu_oracle_sample(pos, mom, nleaves=4096, seed=11):
             "seconds": t_setup + t_sample}
 
 
+def oracle_ensemble_sample(pos, mom, off, p, theta, budget_s=15.0, seed=12):
+    """The CPU oracle over whole samples of the ensemble, drawn at random
+    until about budget_s seconds of work; fields/s over those samples."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(off) - 1)
+    t0 = time.perf_counter()
+    done = fields = 0
+    for i in order:
+        sl = slice(int(off[i]), int(off[i + 1]))
+        O.fmm_field(pos[sl], mom[sl], p, theta)
+        done += 1
+        fields += sl.stop - sl.start
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    return {"value": fields / t, "unit": "fields/s", "cores": O.threads(), "kind": "oracle",
+            "sample": "FP64 CPU oracle, full FMM (tree, lists, all passes) of %d random samples "
+                      "of the ensemble, %d fields in %.1f s" % (done, fields, t),
+            "seconds": t}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    pos, mom = workload()
+    p, theta = WORKLOADS[args.workload]
     times = []
     res = None
-    for it in range(args.warmup + args.steps):
-        res = cpu_oracle_sample(pos, mom, nleaves=256, seed=100 + it)
-        if it >= args.warmup:
-            times.append(len(pos) / res["value"])
+    if args.workload == "ensemble":
+        from paper_0810_0233_gb300 import workloads as W
+        pos, mom, off = W.ensemble()
+        for it in range(args.warmup + args.steps):
+            res = oracle_ensemble_sample(pos, mom, off, p, theta, budget_s=5.0, seed=100 + it)
+            if it >= args.warmup:
+                times.append(len(pos) / res["value"])
+        config = describe_ensemble(len(off) - 1, len(pos), p, theta)
+    else:
+        pos, mom = workload(args.workload)
+        for it in range(args.warmup + args.steps):
+            res = cpu_oracle_sample(pos, mom, p, theta, nleaves=256, seed=100 + it)
+            if it >= args.warmup:
+                times.append(len(pos) / res["value"])
+        config = describe(args.workload, len(pos), 0.74 * p * p, p, theta)
     t = float(np.mean(times))
     value = len(pos) / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "fields/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": describe(len(pos), 0.74 * P * P),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
             "cpu_baseline": {"value": value, "unit": "fields/s", "cores": res["cores"],
                              "kind": "oracle", "sample": res["sample"]},
             "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def describe_ensemble(ns, total, p, theta):
+    return {"workload": "ensemble: %d clustered samples (80%% Gaussian blobs sigma 3 of 500, 20%% "
+                        "chains of 20), N log-uniform in [1e3, 2e5], sum N = %d (seed 810237)"
+                        % (ns, total),
+            "N": total, "samples": ns, "p": p, "theta": theta,
+            "precision": "FP32 bulk; FP64 D tensors and FP64 local-expansion accumulation",
+            "step": "rotate every moment (Philox4x64-10, angle U[0, 0.05]) + field and energy "
+                    "of every sample; trees fixed; one CUDA graph launch",
+            "l2": "inputs (%.0f MB of moments) larger than L2" % (total * 24 / 1e6)}
+
+
+def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
+    """The ensemble step: every rank steps all samples of its share
+    (samples dealt round-robin over ranks, no collective in the step)."""
+    from paper_0810_0233_gb300 import workloads as W
+    p, theta = WORKLOADS["ensemble"]
+    pos, mom, off = W.ensemble()
+    ns = len(off) - 1
+    mine = list(range(rank, ns, world))
+    sp = [pos[off[i]:off[i + 1]] for i in mine]
+    sm = [mom[off[i]:off[i + 1]] for i in mine]
+    o = np.concatenate([[0], np.cumsum([len(x) for x in sp])]).astype(np.int64)
+    P_, M_ = np.concatenate(sp), np.concatenate(sm)
+    total = int(o[-1])
+    b = C.Batch(torch.from_numpy(P_).to(dev), torch.from_numpy(M_).to(dev), o, p, theta,
+                precision=args.precision, stream=stream)
+    E_d = torch.zeros(len(mine), dtype=torch.float64, device=dev)
+    counter = [0]
+
+    def step():
+        b.step(seed=810237, step=counter[0], max_angle=0.05, E_out=E_d)
+        counter[0] += 1
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        z.record(stream)
+        z.synchronize()
+        total_t = a.elapsed_time(z) / 1e3
+        barrier()
+        if world > 1:
+            t = torch.tensor([total_t], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_t = float(t.item())
+        return total_t
+
+    launches0 = C.kernel_launches()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t_step = timed(step, args.steps, args.warmup)
+    launches = (C.kernel_launches() - launches0) // (args.steps + args.warmup)
+    H_h = torch.zeros((total, 3), dtype=torch.float64).pin_memory()
+    E_h = torch.zeros(len(mine), dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        b.step(seed=810237, step=counter[0], max_angle=0.05, H_out=H_h, E_out=E_h)
+        counter[0] += 1
+
+    t_e2e = timed(step_e2e, args.steps, 1)
+    if world > 1:
+        t = torch.tensor([float(total)], device=dev)
+        dist.all_reduce(t)
+        all_total = int(t.item())
+    else:
+        all_total = total
+    # algorithmic work of one step, summed over this rank's samples
+    K = (p + 1) * (p + 2) * (p + 3) // 6 - 1
+    pairs = far = 0
+    for i in range(len(mine)):
+        st = b.sample(i).stats()
+        pairs += st["p2p_pairs"]
+        far += st["far_pairs"]
+    peaks = _peaks()
+    clock = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
+    flops = 30.0 * pairs + 2.0 * K * K * far
+    ach = flops / (t_step / args.steps) / 1e12
+    line = {"metric": METRIC, "value": all_total * args.steps / t_step, "unit": "fields/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": describe_ensemble(ns, len(pos), p, theta),
+            "e2e": {"value": all_total * args.steps / t_e2e, "unit": "fields/s",
+                    "ms_per_step": 1e3 * t_e2e / args.steps, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(total * 24 + len(mine) * 8),
+                    "note": "the step's fields and energies read back to pinned host memory"},
+            "gpu_launches": int(launches),
+            "roofline": {"kernel": "whole step (graph)", "bound": "alu", "achieved": ach,
+                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                         "traffic": None,
+                         "algorithmic": {"p2p_pairs": pairs, "far_pairs": far,
+                                         "flop": flops},
+                         "note": "all near-pair and M2L flops of the step over the step time; "
+                                 "ensemble members contract M2L on the FP32 FMA kernel"},
+            "clocks": clk.summary(),
+            "samples_per_rank": len(mine)}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_ensemble_sample(pos, mom, off, p, theta)
+    b.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():
@@ -188,7 +351,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="one warm-up and two steps only (for ncu launch lists and captures)")
     ap.add_argument("--n", type=int, default=1_000_000,
-                    help="dipoles; below 10^6 only for small profiling cases")
+                    help="ferrofluid dipoles; below 10^6 only for small profiling cases")
+    ap.add_argument("--workload", default="ferrofluid", choices=sorted(WORKLOADS),
+                    help="ferrofluid (the default line), ring (4.19e6), ring-stated (1.2e7), "
+                         "ensemble (512 samples)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -205,8 +371,11 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    if args.workload == "ensemble":
+        return run_ensemble(args, torch, dist, C, world, rank, dev, stream)
 
-    pos, mom = workload(args.n)
+    P, THETA = WORKLOADS[args.workload]
+    pos, mom = workload(args.workload, args.n)
     n = len(pos)
     pos_d = torch.from_numpy(pos).to(dev)
     mom_d = torch.from_numpy(mom).to(dev)
@@ -278,7 +447,7 @@ def main():
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * t_full / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": describe(n, st["leaf_target"]),
+            "config": describe(args.workload, n, st["leaf_target"], P, THETA),
             "eval": {"value": world * n * steps / t_eval, "unit": "fields/s",
                      "ms_per_step": 1e3 * t_eval / steps, "note": "tree and lists reused"},
             "e2e": {"value": world * n * steps / t_e2e, "unit": "fields/s",
@@ -344,7 +513,7 @@ def main():
                                                           (H64 ** 2).sum()).item())
         line["accuracy"] = acc
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_sample(pos, mom)
+        line["cpu_baseline"] = cpu_oracle_sample(pos, mom, P, THETA)
     f.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -163,6 +163,20 @@ def ensemble_sizes(count: int = 512, n_lo: int = 1_000, n_hi: int = 200_000,
     return np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count)).astype(np.int64)
 
 
+def ensemble(count: int = 512, seed: int = BASE_SEED + 4):
+    """The ensemble workload: `count` clustered samples with log-uniform sizes
+    (ensemble_sizes), sample i drawn by clustered(N_i, seed * 1000 + i).
+    Returns (positions, moments, offsets), offsets of length count + 1."""
+    sizes = ensemble_sizes(count, seed=seed)
+    pos, mom = [], []
+    for i, n in enumerate(sizes):
+        p_, m_ = clustered(int(n), seed=seed * 1000 + i)
+        pos.append(p_)
+        mom.append(m_)
+    off = np.concatenate([[0], np.cumsum([len(x) for x in pos])]).astype(np.int64)
+    return np.ascontiguousarray(np.concatenate(pos)), np.ascontiguousarray(np.concatenate(mom)), off
+
+
 def rotation_draws(n: int, max_angle: float, rng: np.random.Generator):
     """Random rotation per moment: axis uniform on the sphere and angle
     uniform in [0, max_angle].  Returns (axis n x 3, angle n)."""
