@@ -11,25 +11,37 @@
 // from TF32 operands: x = x_hi + x_lo, x_hi = x rounded to TF32 (cvt.rna),
 // x_lo = x - x_hi (exact), and A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi.
 // Both operands are split outside the contraction loop: the scaled moments
-// once per evaluation (k_q_split, rows of KT floats), the operators once per
-// tree build (k_m2l_ops, one per far offset class), stored in global memory
-// in exactly the shared-memory layout the MMA reads, so that a unit's
-// operator chunk arrives with one bulk copy.
+// once per evaluation (k_q_split, hi and lo planes of rows of KT floats), the
+// operators once per tree build (k_m2l_ops, one per far offset class),
+// stored in exactly the shared-memory layout the MMA reads so that a unit's
+// operator chunk is one bulk copy.  B_lo follows B_hi in shared memory, so
+// one MMA of width 2N forms A_hi [B_hi | B_lo] (two accumulator halves,
+// added in the epilogue) and a second of width N adds A_lo B_hi: A_hi is
+// read once per k-step, which matters because at TF32 the MMAs' operand
+// reads are what bounds shared-memory bandwidth.
 //
-// Shared-memory operands use the no-swizzle K-major canonical layout: core
-// matrices of 8 rows x 16 bytes (4 TF32), adjacent along K at 128 bytes
-// (leading-dimension offset), 8-row groups at 1024 bytes (stride offset).
+// Shared-memory operands use the 128-byte-swizzled K-major layout: a unit's
+// row of 32 TF32 is one 128-byte line, 8-row atoms of 1024 bytes (stride
+// offset), and the 16-byte chunk j of row r sits in slot j ^ (r mod 8), so
+// that the chunks of one row, and chunk j of eight rows, fall in different
+// banks (the gather's shared-memory writes are conflict-free).  Stage bases
+// are 1024-byte aligned; a k-step of 8 advances the start address by 32 B.
 //
-// Pipeline, TC_ST stages of one unit = (entry, 32-wide K chunk) each:
-//   warps 0-3  wait for the stage to be free, gather the 128 partner rows of
-//              the chunk (cp.async; zero rows for cells without that
-//              partner), and thread 0 starts the bulk copy of the operator
-//              chunk; a thread marks the stage full after its own copies of
-//              the unit have landed (one unit later, so two are in flight);
-//   warp 4     one thread issues the unit's 12 MMAs once the stage is full
-//              and frees the stage with tcgen05.commit;
-//   warps 0-3  finally read the accumulator (tcgen05.ld) into the item's
-//              FP32 partial sums, which k_m2l_reduce adds in FP64.
+// Pipeline, 3 or 4 stages (as many as fit) of one unit = (entry, 32-wide K
+// chunk) each:
+//   producers  (4 or 8 warps) wait for the stage to be free, gather the 128
+//              partner rows of the chunk (cp.async, hi and lo; zero rows for
+//              cells without that partner), and thread 0 starts the bulk
+//              copy of the operator chunk.  stages - 1 units later, before
+//              waiting for the next free stage, each warp marks the unit's
+//              stage full once its own copies have landed (one arrival per
+//              warp);
+//   last warp  one thread issues the unit's 8 MMAs once the rows and the
+//              operator chunk have landed and frees the stage with
+//              tcgen05.commit;
+//   producers  finally read the accumulator (tcgen05.ld; warp w reads TMEM
+//              lanes 32 (w mod 4) ..) into the item's FP32 partial sums,
+//              which k_m2l_reduce adds in FP64.
 // Every wait is bounded; on time-out the kernel raises FLAG_TIMEOUT, lets
 // its copies and MMAs finish (again bounded), frees its tensor memory and
 // returns.
@@ -39,10 +51,15 @@ namespace ccfmm {
 
 constexpr int TC_M = 128;       // field cells per tile (MMA M = TMEM lanes)
 constexpr int TC_KC = 32;       // K per unit: 4 MMA k-steps of 8
-constexpr int TC_ST = 3;        // pipeline stages
-constexpr int TC_PROD = 128;    // producer / epilogue threads (warps 0-3)
+constexpr int TC_SMEM = 227 * 1024;
+#ifndef CCFMM_TC_PROD
+#define CCFMM_TC_PROD 256
+#endif
+constexpr int TC_PROD = CCFMM_TC_PROD;  // producer / epilogue threads (128 or 256)
+constexpr int TC_PW = TC_PROD / 64;     // 8-row groups gathered per pass
+static_assert(TC_PROD == 128 || TC_PROD == 256, "4 or 8 producer warps");
 constexpr int TC_THREADS = TC_PROD + 32;
-constexpr int TC_SBO = (TC_KC / 4) * 128;  // bytes between 8-row groups
+constexpr int TC_SBO = 1024;               // bytes between 8-row atoms
 constexpr long long TC_SPIN = 1ll << 22;
 
 template <int KP> struct TcShape {
@@ -53,7 +70,11 @@ template <int KP> struct TcShape {
     static constexpr int B_BYTES = N * TC_KC * 4;
     static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr int OP_BYTES = NCH * 2 * B_BYTES;            // one offset class
-    static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    // pipeline stages that fit (at most 4), and how many units a producer
+    // keeps in flight before marking the oldest one full
+    static constexpr int ST = (TC_SMEM - 2048) / STAGE >= 4 ? 4 : 3;
+    static constexpr int LAG = ST - 1;
+    static constexpr int TMEM_COLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256);
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -65,10 +86,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;              // leading-dimension offset
-    d |= (uint64_t)(((uint32_t)TC_SBO >> 4) & 0x3FFFu) << 32;  // stride offset
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    return d;                // base offset 0, no swizzle
+    d |= (uint64_t)1 << 16;                                    // leading offset (unused)
+    d |= (uint64_t)(((uint32_t)TC_SBO >> 4) & 0x3FFFu) << 32;  // stride offset: 8-row atoms
+    d |= (uint64_t)1 << 46;                                    // descriptor version (tcgen05)
+    d |= (uint64_t)2 << 61;                                    // 128-byte swizzle
+    return d;                                                  // base offset 0
+}
+
+// byte offset of (row r, 16-byte chunk j) in a 128-byte-swizzled operand
+__host__ __device__ constexpr uint32_t sw128(int r, int j)
+{
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
 }
 
 __device__ __forceinline__ float to_tf32(float x)
@@ -188,9 +216,9 @@ __global__ void k_m2l_ops(int p, const float *D, int ldD, const uint16_t *it_g, 
     constexpr int PER = S::N * TC_KC;  // floats per (chunk, part)
     for (int o = threadIdx.x; o < S::NCH * PER; o += blockDim.x) {
         const int c = o / PER, q = o - c * PER;
-        // float index q = (n&7)*4 + (kl>>2)*32 + (n>>3)*256 + (kl&3)
-        const int kl = (q & 3) | (((q >> 5) & 7) << 2);
-        const int n = ((q >> 2) & 7) | ((q >> 8) << 3);
+        // float index q = (n>>3)*256 + (n&7)*32 + ((kl>>2) ^ (n&7))*4 + (kl&3)
+        const int n = ((q >> 5) & 7) | ((q >> 8) << 3);
+        const int kl = (q & 3) | ((((q >> 2) & 7) ^ (n & 7)) << 2);
         const int k = c * TC_KC + kl;
         const float v = (n < K && k < K) ? Dl[it_g[k * KP + n]] : 0.f;
         const float hi = to_tf32(v);
@@ -214,11 +242,11 @@ __global__ void k_q_split(int p, long long ncell, const float *Q, const float *g
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (k4 < KP) {
         const float4 q = *reinterpret_cast<const float4 *>(Q + hid * KP + k4);
-        const float4 s = *reinterpret_cast<const float4 *>(gk + level * KT + k4);
-        v[0] = q.x * s.x;
-        v[1] = q.y * s.y;
-        v[2] = q.z * s.z;
-        v[3] = q.w * s.w;
+        const float4 g = *reinterpret_cast<const float4 *>(gk + level * KT + k4);
+        v[0] = q.x * g.x;
+        v[1] = q.y * g.y;
+        v[2] = q.z * g.z;
+        v[3] = q.w * g.w;
     }
     float hi[4], lo[4];
 #pragma unroll
@@ -232,6 +260,18 @@ __global__ void k_q_split(int p, long long ncell, const float *Q, const float *g
         make_float4(lo[0], lo[1], lo[2], lo[3]);
 }
 
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
 // ------------------------------------------------------------ contraction
 template <int KP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -240,7 +280,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 {
     typedef TcShape<KP> S;
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) unsigned long long bar_full[TC_ST], bar_b[TC_ST], bar_empty[TC_ST];
+    constexpr int TC_ST = S::ST;
+    __shared__ __align__(8) unsigned long long bar_full[4], bar_b[4], bar_empty[4];
     __shared__ __align__(8) unsigned long long bar_done;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
@@ -250,20 +291,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const M2LItem item = items[blockIdx.x];
     const int ne = item.e1 - item.e0;
     const int nunits = ne * S::NCH;
-    const uint32_t sbase = smem_u32(smraw);
+    const uint32_t sbase = (smem_u32(smraw) + 1023u) & ~1023u;  // swizzle atoms
     const uint32_t done = smem_u32(&bar_done);
 
     if (tid == 0) {
         *abort = 0;
         for (int s = 0; s < TC_ST; ++s) {
-            mbar_init(smem_u32(&bar_full[s]), TC_PROD);
+            mbar_init(smem_u32(&bar_full[s]), TC_PROD / 32);
             mbar_init(smem_u32(&bar_b[s]), 1);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (warp == 4) {
+    constexpr int MMA_WARP = TC_PROD / 32;
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
                      "r"(S::TMEM_COLS));
@@ -274,57 +316,80 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
 
-    if (warp < 4) {
-        // ---------------- producers
+    if (warp < MMA_WARP) {
+        // ---------------- producers: thread -> (row r = 8 (rh0 + TC_PW m) + rl,
+        // 16-byte column j) for m < MR
+        constexpr int MR = 16 / TC_PW;
         const int rl = tid & 7, j = (tid >> 3) & 7, rh0 = tid >> 6;
-        const uint32_t dst0 = (uint32_t)(rl * 16 + j * 128 + rh0 * TC_SBO);
-        int src[8];
+        const uint32_t dst0 = sw128(8 * rh0 + rl, j);  // + m TC_PW atoms
+        // partner rows and operator class of the current entry, and of the
+        // next one, loaded an entry ahead so that no gather waits on them
+        int src[MR], srcn[MR], gid = 0, gidn = 0;
+        if (ne > 0) {
+            const int *sr = ent_src + (long long)item.e0 * TT;
+#pragma unroll
+            for (int m = 0; m < MR; ++m) srcn[m] = sr[(rh0 + TC_PW * m) * 8 + rl];
+            if (tid == 0) gidn = ent_u[item.e0];
+        }
         int issued = 0;
         bool ok = true;
+        // unit v: this warp's rows have landed (the caller waited for them);
+        // make them visible to the tensor cores and mark the stage full
+        auto finish = [&](int v) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_full[v % TC_ST]));
+        };
         for (int u = 0; u < nunits; ++u) {
             const int s = u % TC_ST, r = u / TC_ST;
             const int e = u / S::NCH, c = u - e * S::NCH;
-            if (r > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (r - 1) & 1, abort)) {
+            if (u >= S::LAG) {
+                // unit u - LAG: own rows landed (at most LAG - 1 newer groups
+                // pending), split, mark full
+                asm volatile("cp.async.wait_group %0;\n" ::"n"(S::LAG - 1) : "memory");
+                finish(u - S::LAG);
+            }
+            if (c == 0) {
+#pragma unroll
+                for (int m = 0; m < MR; ++m) src[m] = srcn[m];
+                gid = gidn;
+                if (e + 1 < ne) {
+                    const long long nrow = (long long)item.e0 + e + 1;
+                    const int *sr = ent_src + nrow * TT;
+#pragma unroll
+                    for (int m = 0; m < MR; ++m) srcn[m] = sr[(rh0 + TC_PW * m) * 8 + rl];
+                    if (tid == 0) gidn = ent_u[nrow];
+                }
+            }
+            if (r > 0 &&
+                !__all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_empty[s]), (r - 1) & 1, abort))) {
                 ok = false;
                 break;
             }
             const uint32_t st = sbase + (uint32_t)(s * S::STAGE);
-            const long long row = (long long)item.e0 + e;
             if (tid == 0) {
                 const uint32_t bb = smem_u32(&bar_b[s]);
                 mbar_expect_tx(bb, 2 * S::B_BYTES);
                 bulk_g2s(st + 2 * S::A_BYTES,
-                         Bop + ((long long)ent_u[row] * S::NCH + c) * (2 * S::B_BYTES),
-                         2 * S::B_BYTES, bb);
-            }
-            if (c == 0) {
-                const int *sr = ent_src + row * TT;
-#pragma unroll
-                for (int m = 0; m < 8; ++m) src[m] = sr[(rh0 + 2 * m) * 8 + rl];
+                         Bop + ((long long)gid * S::NCH + c) * (2 * S::B_BYTES), 2 * S::B_BYTES,
+                         bb);
             }
 #pragma unroll
             for (int part = 0; part < 2; ++part) {
                 const float *qb = Qs + part * qplane + c * TC_KC + 4 * j;
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
+                for (int m = 0; m < MR; ++m) {
                     const bool v = src[m] >= 0;
-                    tc_cp16(st + part * S::A_BYTES + dst0 + m * 2 * TC_SBO,
+                    tc_cp16(st + part * S::A_BYTES + dst0 + m * TC_PW * TC_SBO,
                             qb + (v ? (long long)src[m] * S::KT : 0ll), v ? 16 : 0);
                 }
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             issued = u + 1;
-            if (u > 0) {
-                asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(smem_u32(&bar_full[(u - 1) % TC_ST]));
-            }
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
-        if (ok && nunits > 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(smem_u32(&bar_full[(nunits - 1) % TC_ST]));
-        }
+        if (ok)
+            for (int u = nunits - S::LAG > 0 ? nunits - S::LAG : 0; u < nunits; ++u) finish(u);
         if (!ok) {
             *abort = 1;
             atomicOr(flags, FLAG_TIMEOUT);
@@ -342,37 +407,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const bool have = nunits > 0 && mbar_wait(done, 0, abort) && !*abort;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!*abort) {
-            float *out = Ps + ((long long)blockIdx.x * TT + warp * 32 + lane) * KP;
+            const int quad = warp & 3, half = warp >> 2;
+            float *out = Ps + ((long long)blockIdx.x * TT + quad * 32 + lane) * KP;
+            const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
 #pragma unroll
-            for (int c0 = 0; c0 < S::N; c0 += 16) {
-                uint32_t rr[16];
+            for (int c0 = 16 * half; c0 < S::N; c0 += 16 * (TC_PROD / 128)) {
+                uint32_t rh[16], rl2[16];
                 if (have) {
-                    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,"
-                        "%10,%11,%12,%13,%14,%15}, [%16];\n"
-                        : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]),
-                          "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]),
-                          "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]),
-                          "=r"(rr[15])
-                        : "r"(taddr));
+                    tmem_ld16(trow + (uint32_t)c0, rh);
+                    tmem_ld16(trow + (uint32_t)(S::N + c0), rl2);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) rr[q] = 0u;
+                    for (int q = 0; q < 16; ++q) rh[q] = rl2[q] = 0u;
                 }
 #pragma unroll
                 for (int q = 0; q < 16; q += 4)
                     if (c0 + q < KP)
-                        *reinterpret_cast<float4 *>(out + c0 + q) =
-                            make_float4(__uint_as_float(rr[q]), __uint_as_float(rr[q + 1]),
-                                        __uint_as_float(rr[q + 2]), __uint_as_float(rr[q + 3]));
+                        *reinterpret_cast<float4 *>(out + c0 + q) = make_float4(
+                            __uint_as_float(rh[q]) + __uint_as_float(rl2[q]),
+                            __uint_as_float(rh[q + 1]) + __uint_as_float(rl2[q + 1]),
+                            __uint_as_float(rh[q + 2]) + __uint_as_float(rl2[q + 2]),
+                            __uint_as_float(rh[q + 3]) + __uint_as_float(rl2[q + 3]));
             }
         }
     } else if (lane == 0) {
         // ---------------- MMA issue (one thread)
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
-                               ((uint32_t)(S::N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+        const uint32_t idesc2 = (1u << 4) | (2u << 7) | (2u << 10) |
+                                ((uint32_t)(2 * S::N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+        const uint32_t idesc1 = (1u << 4) | (2u << 7) | (2u << 10) |
+                                ((uint32_t)(S::N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
         bool ok = true;
         for (int u = 0; u < nunits; ++u) {
             const int s = u % TC_ST, r = u / TC_ST;
@@ -383,14 +447,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = sbase + (uint32_t)(s * S::STAGE), a1 = a0 + S::A_BYTES;
-            const uint32_t b0 = a0 + 2 * S::A_BYTES, b1 = b0 + S::B_BYTES;
+            const uint32_t b0 = a0 + 2 * S::A_BYTES;  // B_hi, then B_lo: 2N rows
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 8; ++kk) {
-                const uint32_t o = kk * 256;
-                tc_mma(tmem, umma_desc(a0 + o), umma_desc(b0 + o), idesc,
+                const uint32_t o = kk * 32;
+                // [acc_hi | acc_lo] += A_hi [B_hi | B_lo];  acc_hi += A_lo B_hi
+                tc_mma(tmem, umma_desc(a0 + o), umma_desc(b0 + o), idesc2,
                        (u == 0 && kk == 0) ? 0u : 1u);
-                tc_mma(tmem, umma_desc(a0 + o), umma_desc(b1 + o), idesc, 1u);
-                tc_mma(tmem, umma_desc(a1 + o), umma_desc(b0 + o), idesc, 1u);
+                tc_mma(tmem, umma_desc(a1 + o), umma_desc(b0 + o), idesc1, 1u);
             }
             tc_commit(smem_u32(&bar_empty[s]));
         }
@@ -403,7 +467,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 4) {
+    if (warp == MMA_WARP) {
         if (*abort && lane == 0) mbar_wait_plain(done, 0);
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -412,7 +476,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
-template <int KP> static size_t tc_smem() { return (size_t)TC_ST * TcShape<KP>::STAGE + 1024; }
+template <int KP> static size_t tc_smem()
+{
+    return (size_t)TcShape<KP>::ST * TcShape<KP>::STAGE + 1024;
+}
 
 bool m2l_tc_supported(int KP)
 {

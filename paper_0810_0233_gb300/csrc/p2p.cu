@@ -6,8 +6,16 @@
 
 namespace ccfmm {
 
+// sources staged per batch and resident blocks per SM (the register budget);
+// compile-time tunables
+#ifndef CCFMM_P2P_CH
+#define CCFMM_P2P_CH 1536
+#endif
+#ifndef CCFMM_P2P_MINB
+#define CCFMM_P2P_MINB 4
+#endif
 constexpr int P2P_T = 128;    // threads per block
-constexpr int P2P_CH = 1536;  // sources staged in shared memory per batch
+constexpr int P2P_CH = CCFMM_P2P_CH;  // sources staged in shared memory per batch
 constexpr int P2P_NE = 256;   // near-list entries whose metadata is staged at once
 
 template <typename real> __device__ __forceinline__ real rsq(real r2);
@@ -103,7 +111,7 @@ __device__ __forceinline__ void l2p_one(int p, int K, const real *vs, const unsi
 //    source on the field point contributes nothing, Appendix updateField);
 //    no other leaf can hold a point at the target's position.
 template <typename real>
-__global__ void __launch_bounds__(P2P_T, 4) k_p2p(int p, int KP, int L, const int *leaf_start,
+__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, int L, const int *leaf_start,
                                                const int *near_start, const NearEnt *near,
                                                const Geom *g, const typename vec4<real>::t *A,
                                                const typename vec2<real>::t *B, const double *V,
