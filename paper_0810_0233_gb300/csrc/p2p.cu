@@ -19,7 +19,14 @@ constexpr int P2P_CH = CCFMM_P2P_CH;  // sources staged in shared memory per bat
 constexpr int P2P_NE = 256;   // near-list entries whose metadata is staged at once
 
 template <typename real> __device__ __forceinline__ real rsq(real r2);
-template <> __device__ __forceinline__ float rsq<float>(float r2) { return rsqrtf(r2); }
+// one MUFU operation: separations here are never subnormal, so the
+// subnormal-range handling that rsqrtf carries is not needed
+template <> __device__ __forceinline__ float rsq<float>(float r2)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(r2));
+    return r;
+}
 template <> __device__ __forceinline__ double rsq<double>(double r2) { return 1.0 / sqrt(r2); }
 
 // Field of dipole (m) at s on the target t: h += [3 (m.u) u - m] / r^3,
