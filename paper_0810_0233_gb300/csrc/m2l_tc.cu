@@ -56,7 +56,6 @@ constexpr int TC_SMEM = 227 * 1024;
 #define CCFMM_TC_PROD 256
 #endif
 constexpr int TC_PROD = CCFMM_TC_PROD;  // producer / epilogue threads (128 or 256)
-constexpr int TC_PW = TC_PROD / 64;     // 8-row groups gathered per pass
 static_assert(TC_PROD == 128 || TC_PROD == 256, "4 or 8 producer warps");
 constexpr int TC_THREADS = TC_PROD + 32;
 constexpr int TC_SBO = 1024;               // bytes between 8-row atoms
@@ -317,18 +316,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp < MMA_WARP) {
-        // ---------------- producers: thread -> (row r = 8 (rh0 + TC_PW m) + rl,
-        // 16-byte column j) for m < MR
-        constexpr int MR = 16 / TC_PW;
-        const int rl = tid & 7, j = (tid >> 3) & 7, rh0 = tid >> 6;
-        const uint32_t dst0 = sw128(8 * rh0 + rl, j);  // + m TC_PW atoms
+        // ---------------- producers: a warp instruction copies 4 whole unit
+        // rows (128 B each, one global line and one shared line): lane ->
+        // (row r = 4 (warp + NW m) + lane / 8, 16-byte chunk j = lane mod 8)
+        constexpr int NW = TC_PROD / 32, MR = 32 / NW;
+        const int j = lane & 7, rq = lane >> 3;
+        const uint32_t dst0 = sw128(4 * warp + rq, j);  // + m NW/2 atoms
+        auto rowof = [&](int m) { return 4 * (warp + NW * m) + rq; };
         // partner rows and operator class of the current entry, and of the
         // next one, loaded an entry ahead so that no gather waits on them
         int src[MR], srcn[MR], gid = 0, gidn = 0;
         if (ne > 0) {
             const int *sr = ent_src + (long long)item.e0 * TT;
 #pragma unroll
-            for (int m = 0; m < MR; ++m) srcn[m] = sr[(rh0 + TC_PW * m) * 8 + rl];
+            for (int m = 0; m < MR; ++m) srcn[m] = sr[rowof(m)];
             if (tid == 0) gidn = ent_u[item.e0];
         }
         int issued = 0;
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const long long nrow = (long long)item.e0 + e + 1;
                     const int *sr = ent_src + nrow * TT;
 #pragma unroll
-                    for (int m = 0; m < MR; ++m) srcn[m] = sr[(rh0 + TC_PW * m) * 8 + rl];
+                    for (int m = 0; m < MR; ++m) srcn[m] = sr[rowof(m)];
                     if (tid == 0) gidn = ent_u[nrow];
                 }
             }
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int m = 0; m < MR; ++m) {
                     const bool v = src[m] >= 0;
-                    tc_cp16(st + part * S::A_BYTES + dst0 + m * TC_PW * TC_SBO,
+                    tc_cp16(st + part * S::A_BYTES + dst0 + m * (NW / 2) * TC_SBO,
                             qb + (v ? (long long)src[m] * S::KT : 0ll), v ? 16 : 0);
                 }
             }
