@@ -333,7 +333,7 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
                          "algorithmic": {"p2p_pairs": pairs, "far_pairs": far,
                                          "flop": flops},
                          "note": "all near-pair and M2L flops of the step over the step time; "
-                                 "ensemble members contract M2L on the FP32 FMA kernel"},
+                                 "M2L on the tensor cores in every member"},
             "clocks": clk.summary(),
             "samples_per_rank": len(mine)}
     if rank == 0 and not args.no_cpu:

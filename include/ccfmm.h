@@ -70,7 +70,7 @@ typedef struct {
     int64_t far_pairs;        /* (cell, Partner) entries over all levels */
     int64_t p2p_pairs;        /* dipole pairs evaluated by the near field (j != i) */
     int64_t m2l_tile_entries; /* (target tile, offset) work items of M2L */
-    int64_t far_offsets;      /* distinct (level, integer offset) D tables */
+    int64_t far_offsets;      /* distinct D tables (scaled separations) of the far offsets */
     double ms_build;          /* tree + lists + D tables of the last build */
     double ms_eval;           /* mean evaluation time (P2M ... unpermute) */
     double ms_stage[8];       /* mean stage times: P2M, M2M, M2L, L2L, L2P, P2P,
@@ -167,9 +167,10 @@ ccfmm_status fmm_get_leaf_of(ccfmm_t h, int64_t *leaf_of);
 ccfmm_status fmm_get_pairs(ccfmm_t h, int kind, int64_t *pairs, int64_t capacity,
                            int64_t *count);
 
-/* M2L operands: sizes[0..3] = (distinct far offsets, T(2p), M2L entries,
- * tiles); D_out (offsets x T(2p) float64, the D tensors at scaled
- * separations, Eqs. Dn/Dnr), ent_u_out (entries: offset id), ent_src_out
+/* M2L operands: sizes[0..3] = (D tables, T(2p), M2L entries, tiles); D_out
+ * (tables x T(2p) float64, the D tensors at scaled separations c/h, Eqs.
+ * Dn/Dnr; one per distinct scaled separation, shared by levels of the same
+ * cell shape), ent_u_out (entries: D table id), ent_src_out
  * (entries x 128: partner heap id or -1), tiles_out (tiles x 8 int32:
  * level, first, parity, cells, entry start, entry count, offsets, first
  * offset id).  Any output may be NULL; call with all NULL to get sizes. */

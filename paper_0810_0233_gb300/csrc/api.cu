@@ -12,6 +12,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -147,6 +149,7 @@ struct ccfmm_s {
     bool capped = false;
     std::vector<LevelPlan> plan;
     int n_off = 0, ntiles = 0, max_bits = 0;
+    int n_d = 0;  // distinct scaled separations (D tables) over all far offset classes
     long long near_leaf_total = 0, far_total = 0, ent_total = 0;
     bool built = false, evaluated = false, ftable_ready = false;
     bool tc_ops_ready = false;  // tensor-core M2L operators of the current build
@@ -161,6 +164,16 @@ struct ccfmm_s {
     DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
     DevBuf Hout, epart, items, titem0, tnitems, Ps;
     DevBuf Qs, Bop, gkt;  // tensor-core M2L: split moments, operators, level scales
+    DevBuf dmap, dsep;    // far offset class -> D table; scaled separation of each D table
+    // host sources of the build's asynchronous uploads, kept until the next
+    // build (which starts after the previous one has synchronised)
+    std::vector<int> h_cube, h_dmap, h_i0, h_ni;
+    std::vector<int4> h_offs;
+    std::vector<double4> h_dsep;
+    std::vector<M2LItem> h_items;
+    std::vector<Tile> h_tiles;
+    int h_ns0[2] = {0, 1};
+    NearEnt h_e0 = {0, 0, 0, 0};
     int nitems = 0;
     // batch members: energy input and output redirected, no stage events
     const double *mom_energy = nullptr;
@@ -275,8 +288,10 @@ static ccfmm_status make_plan(ccfmm_t h)
     if (cube_total > (1ll << 28)) return fail(CCFMM_ERR_ARG, "theta %g too small", h->theta);
     h->n_off = gid;
     // concatenated cube tables
-    std::vector<int> cube((size_t)std::max(cube_total, 1ll), OFF_NONE);
-    std::vector<int4> offs((size_t)std::max(gid, 1));
+    std::vector<int> &cube = h->h_cube;
+    std::vector<int4> &offs = h->h_offs;
+    cube.assign((size_t)std::max(cube_total, 1ll), OFF_NONE);
+    offs.assign((size_t)std::max(gid, 1), make_int4(0, 0, 0, 0));
     for (int l = 1; l <= L; ++l) {
         LevelPlan &lp = h->plan[l];
         auto at = [&](const int o[3]) {
@@ -295,15 +310,46 @@ static ccfmm_status make_plan(ccfmm_t h)
             offs[lp.gid_base + u] = make_int4(o[0], o[1], o[2], l);
         }
     }
+    // D tables depend on the separation in units of the level's cell radius
+    // only, c/h = (o_x w_x, o_y w_y, o_z w_z) / h; levels of the same cell
+    // shape (every third level of a cubic box) share them.  One table per
+    // distinct scaled separation (exact FP64 equality).
+    std::vector<int> &dmap = h->h_dmap;
+    std::vector<double4> &dsep = h->h_dsep;
+    dmap.assign((size_t)std::max(gid, 1), 0);
+    dsep.clear();
+    {
+        std::map<std::array<uint64_t, 3>, int> seen;
+        for (int g = 0; g < gid; ++g) {
+            const int4 o = offs[g];
+            const int l = o.w;
+            const double hl = h->geom.h[l];
+            double v[3] = {(double)o.x * h->geom.w[l][0] / hl, (double)o.y * h->geom.w[l][1] / hl,
+                           (double)o.z * h->geom.w[l][2] / hl};
+            std::array<uint64_t, 3> key;
+            for (int a = 0; a < 3; ++a) memcpy(&key[a], &v[a], 8);
+            auto it = seen.find(key);
+            if (it == seen.end()) {
+                it = seen.emplace(key, (int)dsep.size()).first;
+                dsep.push_back(make_double4(v[0], v[1], v[2], 0.0));
+            }
+            dmap[g] = it->second;
+        }
+    }
+    h->n_d = (int)dsep.size();
     TRY(ensure(h->cube, sizeof(int) * cube.size()));
     CK(cudaMemcpyAsync(h->cube.p, cube.data(), sizeof(int) * cube.size(), cudaMemcpyHostToDevice,
                        h->stream));
     TRY(ensure(h->offs, sizeof(int4) * offs.size()));
     CK(cudaMemcpyAsync(h->offs.p, offs.data(), sizeof(int4) * offs.size(), cudaMemcpyHostToDevice,
                        h->stream));
-    // the host vectors are released when this function returns; make the
-    // pageable copies complete first
-    CK(cudaStreamSynchronize(h->stream));
+    TRY(ensure(h->dmap, sizeof(int) * dmap.size()));
+    CK(cudaMemcpyAsync(h->dmap.p, dmap.data(), sizeof(int) * dmap.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    TRY(ensure(h->dsep, sizeof(double4) * std::max<size_t>(dsep.size(), 1)));
+    if (!dsep.empty())
+        CK(cudaMemcpyAsync(h->dsep.p, dsep.data(), sizeof(double4) * dsep.size(),
+                           cudaMemcpyHostToDevice, h->stream));
     return CCFMM_OK;
 }
 
@@ -451,11 +497,8 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     CK(cudaMemsetAsync(h->far_off.p, 0, sizeof(int) * ncellp, s));
     // level 0: the root is near itself
     {
-        int ns0[2] = {0, 1};
-        NearEnt e0 = {0, 0, 0, 0};
-        CK(cudaMemcpyAsync(h->nsA.p, ns0, sizeof(ns0), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(h->neA.p, &e0, sizeof(e0), cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
+        CK(cudaMemcpyAsync(h->nsA.p, h->h_ns0, sizeof(h->h_ns0), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->neA.p, &h->h_e0, sizeof(h->h_e0), cudaMemcpyHostToDevice, s));
     }
     DevBuf *nsPrev = &h->nsA, *nsCur = &h->nsB, *nePrev = &h->neA, *neCur = &h->neB;
     for (int l = 1; l <= L; ++l) {
@@ -489,7 +532,8 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     h->near_leaf = P<NearEnt>(*nePrev);
 
     // M2L tiles: TT same-parity cells of one level
-    std::vector<Tile> tiles;
+    std::vector<Tile> &tiles = h->h_tiles;
+    tiles.clear();
     h->max_bits = 32;
     for (int l = 2; l <= L; ++l) {
         LevelPlan &lp = h->plan[l];
@@ -535,9 +579,14 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     // FP32 M2L work items: runs of at most M2L_EC entries of one tile
     if (h->ntiles) {
         std::vector<int> ts(h->ntiles + 1);
-        CK(cudaMemcpy(ts.data(), h->tstart.p, sizeof(int) * (h->ntiles + 1), cudaMemcpyDeviceToHost));
-        std::vector<M2LItem> items;
-        std::vector<int> i0(h->ntiles), ni(h->ntiles);
+        CK(cudaMemcpyAsync(ts.data(), h->tstart.p, sizeof(int) * (h->ntiles + 1),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::vector<M2LItem> &items = h->h_items;
+        std::vector<int> &i0 = h->h_i0, &ni = h->h_ni;
+        items.clear();
+        i0.assign(h->ntiles, 0);
+        ni.assign(h->ntiles, 0);
         for (int t = 0; t < h->ntiles; ++t) {
             i0[t] = (int)items.size();
             for (int e = ts[t]; e < ts[t + 1]; e += M2L_EC) {
@@ -555,15 +604,20 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
             tiles[t].ent_start = ts[t];
             tiles[t].ent_count = ts[t + 1] - ts[t];
         }
-        CK(cudaMemcpy(h->tiles.p, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice));
+        // uploads ordered on the handle's stream (which may be a non-blocking
+        // stream); their host sources belong to the handle
         TRY(ensure(h->items, sizeof(M2LItem) * std::max<size_t>(items.size(), 1)));
         TRY(ensure(h->titem0, sizeof(int) * h->ntiles));
         TRY(ensure(h->tnitems, sizeof(int) * h->ntiles));
+        CK(cudaMemcpyAsync(h->tiles.p, tiles.data(), sizeof(Tile) * tiles.size(),
+                           cudaMemcpyHostToDevice, s));
         if (!items.empty())
-            CK(cudaMemcpy(h->items.p, items.data(), sizeof(M2LItem) * items.size(),
-                          cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(h->titem0.p, i0.data(), sizeof(int) * h->ntiles, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(h->tnitems.p, ni.data(), sizeof(int) * h->ntiles, cudaMemcpyHostToDevice));
+            CK(cudaMemcpyAsync(h->items.p, items.data(), sizeof(M2LItem) * items.size(),
+                               cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->titem0.p, i0.data(), sizeof(int) * h->ntiles, cudaMemcpyHostToDevice,
+                           s));
+        CK(cudaMemcpyAsync(h->tnitems.p, ni.data(), sizeof(int) * h->ntiles,
+                           cudaMemcpyHostToDevice, s));
         if (h->prec == CCFMM_MIXED)
             TRY(ensure(h->Ps, sizeof(float) * (size_t)std::max(h->nitems, 1) * TT * h->KP));
     }
@@ -571,8 +625,8 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     TRY(ensure(h->ent_src, sizeof(int) * (size_t)TT * std::max(h->ent_total, 1ll)));
     if (h->ntiles)
         launch_tile_fill(P<Tile>(h->tiles), h->ntiles, P<int>(h->tstart), P<int>(h->far_off),
-                         P<int>(h->far_num), P<FarEnt>(h->far), h->max_bits, P<int>(h->ent_u),
-                         P<int>(h->ent_src), s);
+                         P<int>(h->far_num), P<FarEnt>(h->far), h->max_bits, P<int>(h->dmap),
+                         P<int>(h->ent_u), P<int>(h->ent_src), s);
 
     // F table and derivative tensors of every (level, far offset), FP64
     int O = 2 * h->p;
@@ -590,13 +644,13 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
         launch_itable(h->p, h->KP, P<uint16_t>(h->itab), s);
         h->ftable_ready = true;
     }
-    TRY(ensure(h->D, rs * (size_t)std::max(h->n_off, 1) * h->ldD));
+    TRY(ensure(h->D, rs * (size_t)std::max(h->n_d, 1) * h->ldD));
     if (h->prec == CCFMM_MIXED)
         launch_dtables<float>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
-                              P<int4>(h->offs), h->n_off, P<Geom>(h->geomd), P<float>(h->D), h->ldD, s);
+                              P<double4>(h->dsep), h->n_d, P<float>(h->D), h->ldD, s);
     else
         launch_dtables<double>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
-                               P<int4>(h->offs), h->n_off, P<Geom>(h->geomd), P<double>(h->D), h->ldD, s);
+                               P<double4>(h->dsep), h->n_d, P<double>(h->D), h->ldD, s);
     TRY(ensure(h->Q, rs * (size_t)ncellp * h->KP));
     TRY(ensure(h->V, sizeof(double) * (size_t)ncellp * h->KP));
     TRY(ensure(h->epart, sizeof(double) * ((N + 255) / 256 + 1)));
@@ -611,17 +665,33 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
 }
 
 // ------------------------------------------------------------ evaluation
-// M2L contraction engine for the FP32 path of a standalone handle: the
-// tensor-core kernel (orders p = 4..7) unless CCFMM_M2L=fma, which selects
-// the FP32 FMA kernel.  Ensemble members use the FMA kernel (the tensor-core
-// operators are stored per handle).
+// M2L contraction engine for the FP32 path: the tensor-core kernel (orders
+// p = 4..7) unless CCFMM_M2L=fma, which selects the FP32 FMA kernel.
 static bool m2l_use_tc(ccfmm_t h)
 {
-    if (h->prec != CCFMM_MIXED || h->quiet || !m2l_tc_supported(h->KP)) return false;
+    if (h->prec != CCFMM_MIXED || !m2l_tc_supported(h->KP)) return false;
     const char *e = getenv("CCFMM_M2L");
     if (e && !strcmp(e, "fma")) return false;
     if (e && !strcmp(e, "tc")) return true;
     return M2L_TC_DEFAULT;
+}
+
+// Buffers and operators of the tensor-core M2L for the current tree, built
+// on the handle's stream at the first evaluation after a build (ensemble
+// members: before their evaluation is captured).
+static ccfmm_status tc_prepare(ccfmm_t h)
+{
+    const int KT = m2l_tc_kt(h->KP);
+    const long long ncellp = 1ll << (h->L + 1);
+    TRY(ensure(h->Qs, sizeof(float) * 2 * (size_t)ncellp * KT));
+    if (!h->tc_ops_ready) {
+        TRY(ensure(h->Bop, m2l_tc_op_bytes(h->KP) * (size_t)std::max(h->n_d, 1)));
+        TRY(ensure(h->gkt, sizeof(float) * (size_t)(LCAP + 1) * KT));
+        launch_m2l_tc_ops(h->p, h->KP, h->L, h->n_d, P<Geom>(h->geomd), P<float>(h->D), h->ldD,
+                          P<uint16_t>(h->itab), P<float>(h->gkt), P<float>(h->Bop), h->stream);
+        h->tc_ops_ready = true;
+    }
+    return CCFMM_OK;
 }
 
 template <typename real>
@@ -641,15 +711,7 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
     for (int l = L - 1; l >= 0; --l) launch_m2m<real>(p, KP, l, P<Geom>(h->geomd), P<real>(h->Q), s);
     if (ev) CK(cudaEventRecord(evs[EV_M2M], s));
     if (sizeof(real) == 4 && m2l_use_tc(h)) {
-        const int KT = m2l_tc_kt(KP);
-        if (!h->tc_ops_ready) {
-            TRY(ensure(h->Bop, m2l_tc_op_bytes(KP) * (size_t)std::max(h->n_off, 1)));
-            TRY(ensure(h->gkt, sizeof(float) * (size_t)(LCAP + 1) * KT));
-            launch_m2l_tc_ops(p, KP, L, h->n_off, P<Geom>(h->geomd), P<float>(h->D), h->ldD,
-                              P<uint16_t>(h->itab), P<float>(h->gkt), P<float>(h->Bop), s);
-            h->tc_ops_ready = true;
-        }
-        TRY(ensure(h->Qs, sizeof(float) * 2 * (size_t)ncellp * KT));
+        TRY(tc_prepare(h));
         launch_m2l_tc(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
                       P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
                       P<float>(h->Q), ncellp, P<float>(h->gkt), P<float>(h->Qs),
@@ -882,7 +944,7 @@ ccfmm_status fmm_stats(ccfmm_t h, ccfmm_stats *out)
     st.far_pairs = h->far_total;
     st.p2p_pairs = (int64_t)h->hrb->pairs;
     st.m2l_tile_entries = h->ent_total;
-    st.far_offsets = h->n_off;
+    st.far_offsets = h->n_d;
     if (h->ev_ok) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->evb[EV_B0], h->evb[EV_B1]) == cudaSuccess) st.ms_build = ms;
@@ -923,7 +985,8 @@ void fmm_destroy(ccfmm_t h)
                       &h->far, &h->far_off, &h->far_num, &h->tiles, &h->tcount, &h->tstart,
                       &h->ent_u, &h->ent_src, &h->offs, &h->fst, &h->fq, &h->fval, &h->fdense,
                       &h->D, &h->itab, &h->Q, &h->V, &h->Hout, &h->epart, &h->items,
-                      &h->titem0, &h->tnitems, &h->Ps, &h->Qs, &h->Bop, &h->gkt};
+                      &h->titem0, &h->tnitems, &h->Ps, &h->Qs, &h->Bop, &h->gkt, &h->dmap,
+                      &h->dsep};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hrb) cudaFreeHost(h->hrb);
@@ -1011,12 +1074,12 @@ ccfmm_status fmm_get_m2l_data(ccfmm_t h, int64_t *sizes, double *D_out, int32_t 
     if (!h->built) return fail(CCFMM_ERR_STATE, "no tree");
     CK(cudaSetDevice(h->device));
     CK(cudaStreamSynchronize(h->stream));
-    sizes[0] = h->n_off;
+    sizes[0] = h->n_d;
     sizes[1] = h->TD;
     sizes[2] = h->ent_total;
     sizes[3] = h->ntiles;
-    if (D_out && h->n_off > 0) {
-        size_t n = (size_t)h->n_off * h->ldD;
+    if (D_out && h->n_d > 0) {
+        size_t n = (size_t)h->n_d * h->ldD;
         std::vector<double> d(n);
         if (h->prec == CCFMM_MIXED) {
             std::vector<float> f(n);
@@ -1025,7 +1088,7 @@ ccfmm_status fmm_get_m2l_data(ccfmm_t h, int64_t *sizes, double *D_out, int32_t 
         } else {
             CK(cudaMemcpy(d.data(), h->D.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
         }
-        for (int r = 0; r < h->n_off; ++r)
+        for (int r = 0; r < h->n_d; ++r)
             for (int t = 0; t < h->TD; ++t) D_out[(size_t)r * h->TD + t] = d[(size_t)r * h->ldD + t];
     }
     if (ent_u_out && h->ent_total > 0)
@@ -1184,6 +1247,15 @@ static ccfmm_status batch_capture(ccfmm_batch_t b, int rotate)
 {
     cudaStream_t s = b->stream;
     cudaGraph_t g = nullptr;
+    // allocations and one-time operator builds happen before the capture
+    bool prepared = false;
+    for (ccfmm_t hs : b->h)
+        if (m2l_use_tc(hs)) {
+            TRY(tc_prepare(hs));
+            prepared = true;
+        }
+    if (prepared)
+        for (int r = 0; r < b->nbr; ++r) CK(cudaStreamSynchronize(b->br[r]));
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     ccfmm_status st = CCFMM_OK;
     do {

@@ -157,18 +157,19 @@ void launch_list_fill_impl(int level, const int *leaf_start, int L, const int *n
                            int *far_off, int *far_num, int *d_flags, cudaStream_t s);
 void launch_tile_count(const Tile *tiles, int ntiles, const int *far_off, const int *far_num,
                        const FarEnt *far, int max_bits, int *counts, cudaStream_t s);
+// entries get the D table of their offset class (dmap[class])
 void launch_tile_fill(Tile *tiles, int ntiles, const int *ent_start, const int *far_off,
-                      const int *far_num, const FarEnt *far, int max_bits, int *ent_u,
-                      int *ent_src, cudaStream_t s);
+                      const int *far_num, const FarEnt *far, int max_bits, const int *dmap,
+                      int *ent_u, int *ent_src, cudaStream_t s);
 
 // ------------------------------------------------------------------ expand.cu
 size_t ftable_scratch_bytes(int order);
 void launch_ftable(int order, double *dense_scratch, int *f_start, uint16_t *f_q, double *f_val,
                    cudaStream_t s);
 template <typename real>
+// one D table per scaled separation sep[i] = (c_x, c_y, c_z) / h
 void launch_dtables(int p, const int *f_start, const uint16_t *f_q, const double *f_val,
-                    const int4 *offs, int noff, const Geom *d_geom, real *D, int ldD,
-                    cudaStream_t s);
+                    const double4 *sep, int nd, real *D, int ldD, cudaStream_t s);
 void launch_itable(int p, int KP, uint16_t *it, cudaStream_t s);
 template <typename real>
 void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,

@@ -139,17 +139,13 @@ void launch_ftable(int order, double *dense_scratch, int *f_start, uint16_t *f_q
 // T(2p) used for padding.
 template <typename real>
 __global__ void k_dtables(int O, const int *f_start, const uint16_t *f_q, const double *f_val,
-                          const int4 *offs, const Geom *g, real *D, int ldD)
+                          const double4 *sep, real *D, int ldD)
 {
     __shared__ double xp[2 * PMAX + 1], yp[2 * PMAX + 1], zp[2 * PMAX + 1], rp[2 * PMAX + 1];
     int gid = blockIdx.x;
-    int4 o = offs[gid];
     if (threadIdx.x == 0) {
-        int l = o.w;
-        double h = g->h[l];
-        double x = (double)o.x * g->w[l][0] / h;
-        double y = (double)o.y * g->w[l][1] / h;
-        double z = (double)o.z * g->w[l][2] / h;
+        const double4 c = sep[gid];  // separation / cell radius
+        double x = c.x, y = c.y, z = c.z;
         double rinv = 1.0 / sqrt(x * x + y * y + z * z);
         double r2inv = rinv * rinv;
         xp[0] = yp[0] = zp[0] = 1.0;
@@ -176,12 +172,11 @@ __global__ void k_dtables(int O, const int *f_start, const uint16_t *f_q, const 
 
 template <typename real>
 void launch_dtables(int p, const int *f_start, const uint16_t *f_q, const double *f_val,
-                    const int4 *offs, int noff, const Geom *d_geom, real *D, int ldD,
-                    cudaStream_t s)
+                    const double4 *sep, int nd, real *D, int ldD, cudaStream_t s)
 {
-    if (noff <= 0) return;
+    if (nd <= 0) return;
     note_launch();
-    k_dtables<real><<<noff, 128, 0, s>>>(2 * p, f_start, f_q, f_val, offs, d_geom, D, ldD);
+    k_dtables<real><<<nd, 128, 0, s>>>(2 * p, f_start, f_q, f_val, sep, D, ldD);
 }
 
 // M2L index table: it[k][n] = D-row column of multi-index (n + k) for
@@ -376,8 +371,7 @@ void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *
 
 #define INST(real)                                                                              \
     template void launch_dtables<real>(int, const int *, const uint16_t *, const double *,      \
-                                       const int4 *, int, const Geom *, real *, int,            \
-                                       cudaStream_t);                                           \
+                                       const double4 *, int, real *, int, cudaStream_t);        \
     template void launch_p2m<real>(int, int, int, const int *, const vec4<real>::t *,           \
                                    const vec2<real>::t *, real *, cudaStream_t);                \
     template void launch_m2m<real>(int, int, int, const Geom *, real *, cudaStream_t);          \

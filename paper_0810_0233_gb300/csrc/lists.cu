@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(TL_T) k_tile_count(const Tile *tiles, const in
 
 __global__ void __launch_bounds__(TL_T) k_tile_fill(const Tile *tiles, const int *ent_start,
                                                     const int *far_off, const int *far_num,
-                                                    const FarEnt *far, int *ent_u, int *ent_src)
+                                                    const FarEnt *far, const int *dmap, int *ent_u,
+                                                    int *ent_src)
 {
     extern __shared__ unsigned bm[];
     __shared__ int sm[32];
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(TL_T) k_tile_fill(const Tile *tiles, const int
         int r = (int)wpre[w];
         while (b) {
             int bit = __ffs(b) - 1;
-            ent_u[start + r] = t.gid_base + w * 32 + bit;
+            ent_u[start + r] = dmap[t.gid_base + w * 32 + bit];  // D table of the class
             ++r;
             b &= b - 1;
         }
@@ -306,7 +307,7 @@ void launch_tile_count(const Tile *tiles, int ntiles, const int *far_off, const 
 }
 
 void launch_tile_fill(Tile *tiles, int ntiles, const int *ent_start, const int *far_off,
-                      const int *far_num, const FarEnt *far, int max_bits, int *ent_u,
+                      const int *far_num, const FarEnt *far, int max_bits, const int *dmap, int *ent_u,
                       int *ent_src, cudaStream_t s)
 {
     if (ntiles <= 0) return;
@@ -314,7 +315,7 @@ void launch_tile_fill(Tile *tiles, int ntiles, const int *ent_start, const int *
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_tile_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
-    k_tile_fill<<<ntiles, TL_T, smem, s>>>(tiles, ent_start, far_off, far_num, far, ent_u, ent_src);
+    k_tile_fill<<<ntiles, TL_T, smem, s>>>(tiles, ent_start, far_off, far_num, far, dmap, ent_u, ent_src);
 }
 
 }  // namespace ccfmm

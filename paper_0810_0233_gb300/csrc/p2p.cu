@@ -14,8 +14,12 @@ namespace ccfmm {
 #ifndef CCFMM_P2P_MINB
 #define CCFMM_P2P_MINB 4
 #endif
+#ifndef CCFMM_P2P_UNROLL
+#define CCFMM_P2P_UNROLL 2
+#endif
 constexpr int P2P_T = 128;    // threads per block
 constexpr int P2P_CH = CCFMM_P2P_CH;  // sources staged in shared memory per batch
+constexpr int P2P_UNROLL = CCFMM_P2P_UNROLL;  // unroll of the pair loop
 constexpr int P2P_NE = 256;   // near-list entries whose metadata is staged at once
 
 template <typename real> __device__ __forceinline__ real rsq(real r2);
@@ -55,7 +59,7 @@ __device__ __forceinline__ void p2p_range(const typename vec4<real>::t *sp,
                                           const typename vec2<real>::t *sm, int j0, int j1,
                                           const real (&tx)[P2P_TPT][3], real (&hs)[P2P_TPT][3])
 {
-#pragma unroll 2
+#pragma unroll P2P_UNROLL
     for (int j = j0; j < j1; ++j) {
         typename vec4<real>::t s = sp[j];
         typename vec2<real>::t m = sm[j];

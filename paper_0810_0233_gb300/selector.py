@@ -87,7 +87,7 @@ def row(feat, p, theta, leaf):
     return np.concatenate([feat, [p, theta, math.log2(leaf)]]).astype(np.float32)
 
 
-def sweep(n_runs=20000, per_instance=50, n_lo=2000, n_hi=60000, seed=2024, log=None):
+def sweep(n_runs=20000, per_instance=50, n_lo=2000, n_hi=2_000_000, seed=2024, log=None):
     """Run random (p, theta, leaf) cells on random instances.  Returns
     X (runs x 12), T (runs x 2) = (log10 ns per dipole, log10 error)."""
     rng = np.random.default_rng(seed)
@@ -165,6 +165,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--runs", type=int, default=20000)
     ap.add_argument("--per-instance", type=int, default=50)
+    ap.add_argument("--n-hi", type=int, default=2_000_000, help="largest training instance")
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--eval", action="store_true")
     ap.add_argument("--eval-n", type=int, default=10_000_000)
@@ -173,7 +174,7 @@ def main():
     args = ap.parse_args()
     log = lambda s: print(s, flush=True)
     t = time.time()
-    X, T = sweep(args.runs, args.per_instance, log=log)
+    X, T = sweep(args.runs, args.per_instance, n_hi=args.n_hi, log=log)
     log("sweep done: %d runs in %.0f s" % (len(X), time.time() - t))
     n_hold = len(X) // 10
     mlp, loss = train(X[n_hold:], T[n_hold:], epochs=args.epochs)

@@ -48,10 +48,11 @@ def test_batch_steps_match_oracle(prec, tol):
         assert b.kernels_per_step() > b.ns
 
 
-def test_batch_equals_single_systems_bitwise(monkeypatch):
-    """Ensemble members contract M2L on the FP32 FMA kernel; standalone
-    handles with that engine give the same bits."""
-    monkeypatch.setenv("CCFMM_M2L", "fma")
+@pytest.mark.parametrize("engine", ["fma", "tc"])
+def test_batch_equals_single_systems_bitwise(monkeypatch, engine):
+    """Ensemble members and standalone handles with the same M2L engine
+    give the same bits."""
+    monkeypatch.setenv("CCFMM_M2L", engine)
     pos, mom, off = _ensemble(ns=4, seed=78)
     with C.Batch(pos, mom, off, 4, 0.5) as b:
         H = np.zeros((b.total, 3))

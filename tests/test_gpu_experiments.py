@@ -1,0 +1,29 @@
+"""Scaling experiments of Sec. IV (experiments.py) on small lattices: the
+measurements are well formed and the tree responds to the occupancy."""
+import pytest
+
+from paper_0810_0233_gb300 import ccfmm as C
+from paper_0810_0233_gb300 import experiments as X
+
+pytestmark = pytest.mark.gpu
+
+
+def test_scaling_rows():
+    rows = X.scaling(sizes=(8, 12), params=((4, 0.5),), direct_max=10_000)
+    assert [r["N"] for r in rows] == [512, 1728]
+    for r in rows:
+        assert r["fmm_p4_a0.50_ms"] > 0 and r["direct_ms"] > 0 and r["depth_p4"] >= 1
+
+
+def test_leaf_sweep_depth_falls_with_occupancy():
+    res = X.leaf_sweep(n=16, p=3, theta=0.54, leaves=(2, 8, 32))
+    depths = [r["depth"] for r in res]
+    assert depths == sorted(depths, reverse=True) and depths[0] > depths[-1]
+    # the paper's 32^3 example: s = 8 gives 8 x 8 x 8 leaves of 8 points (Sec. IV)
+    assert X.leaf_sweep(n=32, p=3, theta=0.54, leaves=(8,))[0]["depth"] == 12
+
+
+def test_optimal_leaf_small():
+    res = X.optimal_leaf(ps=(3,), sizes=(30,))
+    assert res[3]["rule"] == C.leaf_size_rule(3)
+    assert 1.0 <= res[3]["s_o"] <= 512.0
