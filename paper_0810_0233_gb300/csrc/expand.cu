@@ -207,59 +207,77 @@ void launch_itable(int p, int KP, uint16_t *it, cudaStream_t s)
 // P2M (Eq. multipolemoments): Q_n = sum_i sum_a m_ia r_i^(n-e_a)/(n-e_a)!
 // about the leaf centre, for every leaf (empty leaves get zeros).
 // ---------------------------------------------------------------------------
-constexpr int P2M_T = 128;
+// One warp per leaf, P2M_W leaves per block: a lane stages one dipole of the
+// leaf (powers x^j/j! of its leaf-relative coordinates, by reciprocal
+// constants) and then owns coefficients lane, lane + 32, ...
+constexpr int P2M_W = 4;
+constexpr int P2M_R = (nterms(PMAX) - 1 + 31) / 32;  // coefficient rounds per lane
 
 template <typename real>
-__global__ void __launch_bounds__(P2M_T) k_p2m(int p, int KP, int L, const int *leaf_start,
-                                               const typename vec4<real>::t *A,
-                                               const typename vec2<real>::t *B, real *Q)
+__global__ void __launch_bounds__(32 * P2M_W) k_p2m(int p, int KP, int L, const int *leaf_start,
+                                                    const typename vec4<real>::t *A,
+                                                    const typename vec2<real>::t *B, real *Q)
 {
-    __shared__ real pw[P2M_T][3][PMAX];
-    __shared__ real mm[P2M_T][3];
+    __shared__ real pw[P2M_W][32][3][PMAX];
+    __shared__ real mm[P2M_W][32][3];
     __shared__ unsigned mi[nterms(PMAX)];
-    int K = nterms(p) - 1;
+    const real inv[PMAX] = {(real)0, (real)1, (real)0.5, (real)1 / (real)3, (real)0.25,
+                            (real)0.2, (real)1 / (real)6, (real)1 / (real)7};
+    const int K = nterms(p) - 1;
     fill_mi(mi, K);
-    long long key = blockIdx.x;
-    int s0 = leaf_start[key], s1 = leaf_start[key + 1];
-    real acc[2] = {(real)0, (real)0};
-    for (int base = s0; base < s1; base += P2M_T) {
-        __syncthreads();
-        int i = base + threadIdx.x;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long key = (long long)blockIdx.x * P2M_W + w;
+    if (key >= (1ll << L)) return;
+    const int s0 = leaf_start[key], s1 = leaf_start[key + 1];
+    real acc[P2M_R];
+#pragma unroll
+    for (int r = 0; r < P2M_R; ++r) acc[r] = (real)0;
+    for (int base = s0; base < s1; base += 32) {
+        __syncwarp();
+        const int i = base + lane;
         if (i < s1) {
-            typename vec4<real>::t a = A[i];
-            typename vec2<real>::t b = B[i];
-            real x[3] = {a.x, a.y, a.z};
+            const typename vec4<real>::t a = A[i];
+            const typename vec2<real>::t b = B[i];
+            const real x[3] = {a.x, a.y, a.z};
+#pragma unroll
             for (int d = 0; d < 3; ++d) {
                 real v = (real)1;
-                pw[threadIdx.x][d][0] = v;
-                for (int j = 1; j < p; ++j) {
-                    v = v * x[d] / (real)j;
-                    pw[threadIdx.x][d][j] = v;
-                }
+                pw[w][lane][d][0] = v;
+#pragma unroll
+                for (int j = 1; j < PMAX; ++j)
+                    if (j < p) {
+                        v = v * x[d] * inv[j];
+                        pw[w][lane][d][j] = v;
+                    }
             }
-            mm[threadIdx.x][0] = a.w;
-            mm[threadIdx.x][1] = b.x;
-            mm[threadIdx.x][2] = b.y;
+            mm[w][lane][0] = a.w;
+            mm[w][lane][1] = b.x;
+            mm[w][lane][2] = b.y;
         }
-        __syncthreads();
-        int cnt = min(P2M_T, s1 - base);
-        for (int r = 0; r < 2; ++r) {
-            int c = threadIdx.x + r * P2M_T;
-            if (c >= K) break;
-            unsigned n = mi[c];
-            int nx = px(n), ny = py(n), nz = pz(n);
-            real s = (real)0;
-            for (int d = 0; d < cnt; ++d) {
-                if (nx > 0) s += mm[d][0] * pw[d][0][nx - 1] * pw[d][1][ny] * pw[d][2][nz];
-                if (ny > 0) s += mm[d][1] * pw[d][0][nx] * pw[d][1][ny - 1] * pw[d][2][nz];
-                if (nz > 0) s += mm[d][2] * pw[d][0][nx] * pw[d][1][ny] * pw[d][2][nz - 1];
+        __syncwarp();
+        const int cnt = min(32, s1 - base);
+#pragma unroll
+        for (int r = 0; r < P2M_R; ++r) {
+            const int c = lane + 32 * r;
+            if (c < K) {
+                const unsigned n = mi[c];
+                const int nx = px(n), ny = py(n), nz = pz(n);
+                real sum = (real)0;
+                for (int d = 0; d < cnt; ++d) {
+                    const real(*q)[PMAX] = pw[w][d];
+                    if (nx > 0) sum += mm[w][d][0] * q[0][nx - 1] * q[1][ny] * q[2][nz];
+                    if (ny > 0) sum += mm[w][d][1] * q[0][nx] * q[1][ny - 1] * q[2][nz];
+                    if (nz > 0) sum += mm[w][d][2] * q[0][nx] * q[1][ny] * q[2][nz - 1];
+                }
+                acc[r] += sum;
             }
-            acc[r] += s;
         }
     }
-    long long hid = (1ll << L) + key;
-    for (int r = 0; r < 2; ++r) {
-        int c = threadIdx.x + r * P2M_T;
+    const long long hid = (1ll << L) + key;
+#pragma unroll
+    for (int r = 0; r < P2M_R; ++r) {
+        const int c = lane + 32 * r;
         if (c < KP) Q[hid * KP + c] = c < K ? acc[r] : (real)0;
     }
 }
@@ -268,8 +286,10 @@ template <typename real>
 void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, real *Q, cudaStream_t s)
 {
+    const long long nleaf = 1ll << L;
     note_launch();
-    k_p2m<real><<<(unsigned)(1ll << L), P2M_T, 0, s>>>(p, KP, L, leaf_start, A, B, Q);
+    k_p2m<real><<<(unsigned)((nleaf + P2M_W - 1) / P2M_W), 32 * P2M_W, 0, s>>>(p, KP, L,
+                                                                             leaf_start, A, B, Q);
 }
 
 // ---------------------------------------------------------------------------
@@ -277,34 +297,46 @@ void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4
 // -w/2 (bit 0) or +w/2 (bit 1) along the axis split at level l+1, so only
 // shifts along that axis appear: Q_n += sum_j c^j/j! Q^child_{n - j e_s}.
 // ---------------------------------------------------------------------------
+// Block: threadIdx.x = coefficient (KP rounded up to a warp multiple),
+// threadIdx.y = one of SH_C cells; the shift factors c^t/t! of the two
+// children are formed once per block by the same recurrence as per term.
+constexpr int SH_C = 4;
+
 template <typename real>
 __global__ void k_m2m(int p, int KP, int l, const Geom *g, real *Q)
 {
-    int K = nterms(p) - 1;
-    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long ncell = 1ll << l;
-    if (j >= ncell * KP) return;
-    long long key = j / KP;
-    int c = (int)(j % KP);
-    long long hid = ncell + key;
+    __shared__ real fs[2][PMAX + 1];
+    const int s = g->axis[l + 1];
+    if (threadIdx.y == 0 && threadIdx.x < 2) {
+        const real hw = (real)(0.5 * g->w[l + 1][s]);
+        const real cs = threadIdx.x ? hw : -hw;
+        real f = (real)1;
+        fs[threadIdx.x][0] = f;
+        for (int t = 1; t <= p; ++t) {
+            f = f * cs / (real)t;
+            fs[threadIdx.x][t] = f;
+        }
+    }
+    __syncthreads();
+    const int K = nterms(p) - 1;
+    const long long ncell = 1ll << l;
+    const long long key = (long long)blockIdx.x * SH_C + threadIdx.y;
+    const int c = threadIdx.x;
+    if (key >= ncell || c >= KP) return;
+    const long long hid = ncell + key;
     if (c >= K) {
         Q[hid * KP + c] = (real)0;
         return;
     }
     int n[3];
     midx_inv(c + 1, n[0], n[1], n[2]);
-    int s = g->axis[l + 1];
-    real hw = (real)(0.5 * g->w[l + 1][s]);
     real acc = (real)0;
     for (int b = 0; b < 2; ++b) {
-        real cs = b ? hw : -hw;
         const real *Qc = Q + (2 * hid + b) * KP;
-        real f = (real)1;
         for (int t = 0; t <= n[s]; ++t) {
             int m[3] = {n[0], n[1], n[2]};
             m[s] -= t;
-            if (m[0] + m[1] + m[2] > 0) acc += f * Qc[midx(m[0], m[1], m[2]) - 1];
-            f = f * cs / (real)(t + 1);
+            if (m[0] + m[1] + m[2] > 0) acc += fs[b][t] * Qc[midx(m[0], m[1], m[2]) - 1];
         }
     }
     Q[hid * KP + c] = acc;
@@ -313,9 +345,10 @@ __global__ void k_m2m(int p, int KP, int l, const Geom *g, real *Q)
 template <typename real>
 void launch_m2m(int p, int KP, int level, const Geom *d_geom, real *Q, cudaStream_t s)
 {
-    long long n = (1ll << level) * KP;
+    const long long ncell = 1ll << level;
+    const dim3 blk((unsigned)((KP + 31) / 32 * 32), SH_C);
     note_launch();
-    k_m2m<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, KP, level, d_geom, Q);
+    k_m2m<real><<<(unsigned)((ncell + SH_C - 1) / SH_C), blk, 0, s>>>(p, KP, level, d_geom, Q);
 }
 
 // ---------------------------------------------------------------------------
@@ -328,7 +361,7 @@ __global__ void k_l2l(int p, int KP, int l, int L, const Geom *g, const int *lea
     // (upper): 2p FP64 divisions per block instead of one per term
     __shared__ double fs[2][PMAX + 1];
     const int s = g->axis[l];
-    if (threadIdx.x < 2) {
+    if (threadIdx.y == 0 && threadIdx.x < 2) {
         const double cs = threadIdx.x ? 0.5 * g->w[l][s] : -0.5 * g->w[l][s];
         double f = 1.0;
         fs[threadIdx.x][0] = 1.0;
@@ -338,20 +371,19 @@ __global__ void k_l2l(int p, int KP, int l, int L, const Geom *g, const int *lea
         }
     }
     __syncthreads();
-    int K = nterms(p) - 1;
-    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long ncell = 1ll << l;
-    if (j >= ncell * K) return;
-    long long key = j / K;
-    int c = (int)(j % K);
-    int sh = L - l;
+    const int K = nterms(p) - 1;
+    const long long ncell = 1ll << l;
+    const long long key = (long long)blockIdx.x * SH_C + threadIdx.y;
+    const int c = threadIdx.x;
+    if (key >= ncell || c >= K) return;
+    const int sh = L - l;
     if (leaf_start[(key + 1) << sh] == leaf_start[key << sh]) return;
-    long long hid = ncell + key;
+    const long long hid = ncell + key;
     int n[3];
     midx_inv(c + 1, n[0], n[1], n[2]);
     const double *f = fs[key & 1];
     const double *Vp = V + (hid >> 1) * KP;
-    int kn = n[0] + n[1] + n[2];
+    const int kn = n[0] + n[1] + n[2];
     double acc = 0.0;
     for (int t = 0; t <= p - kn; ++t) {
         int m[3] = {n[0], n[1], n[2]};
@@ -364,9 +396,11 @@ __global__ void k_l2l(int p, int KP, int l, int L, const Geom *g, const int *lea
 void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *leaf_start,
                 double *V, cudaStream_t s)
 {
-    long long n = (1ll << level) * (nterms(p) - 1);
+    const long long ncell = 1ll << level;
+    const dim3 blk((unsigned)((nterms(p) - 1 + 31) / 32 * 32), SH_C);
     note_launch();
-    k_l2l<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, KP, level, L, d_geom, leaf_start, V);
+    k_l2l<<<(unsigned)((ncell + SH_C - 1) / SH_C), blk, 0, s>>>(p, KP, level, L, d_geom,
+                                                               leaf_start, V);
 }
 
 #define INST(real)                                                                              \
