@@ -47,6 +47,8 @@
 // returns.
 #include "ccfmm_dev.cuh"
 
+#include <stdlib.h>
+
 namespace ccfmm {
 
 constexpr int TC_M = 128;       // field cells per tile (MMA M = TMEM lanes)
@@ -139,10 +141,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait; gives up early once another thread has given up
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort)
+// bounded wait (spin iterations); gives up early once another thread has
+// given up
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort,
+                                          long long spin)
 {
-    for (long long i = 0; i < TC_SPIN; ++i) {
+    for (long long i = 0; i < spin; ++i) {
         if (mbar_try(a, parity)) return true;
         if ((i & 31) == 31 && *abort) return false;
     }
@@ -275,7 +279,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 template <int KP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_m2l_tc(const M2LItem *items, const int *ent_u, const int *ent_src, const float *Qs,
-             long long qplane, const unsigned char *Bop, float *Ps, int *flags)
+             long long qplane, const unsigned char *Bop, float *Ps, int *flags, long long spin,
+             int stall)
 {
     typedef TcShape<KP> S;
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -362,8 +367,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (tid == 0) gidn = ent_u[nrow];
                 }
             }
-            if (r > 0 &&
-                !__all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_empty[s]), (r - 1) & 1, abort))) {
+            if (r > 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_empty[s]),
+                                                            (r - 1) & 1, abort, spin))) {
                 ok = false;
                 break;
             }
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
         // ---------------- epilogue: accumulator -> partial sums
-        const bool have = nunits > 0 && mbar_wait(done, 0, abort) && !*abort;
+        const bool have = nunits > 0 && mbar_wait(done, 0, abort, spin) && !*abort;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!*abort) {
             const int quad = warp & 3, half = warp >> 2;
@@ -439,10 +444,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t idesc1 = (1u << 4) | (2u << 7) | (2u << 10) |
                                 ((uint32_t)(S::N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
         bool ok = true;
-        for (int u = 0; u < nunits; ++u) {
+        // stall (failure-path tests only): issue nothing, so that the
+        // producers' bounded waits for a free stage run out
+        for (int u = 0; u < (stall ? 0 : nunits); ++u) {
             const int s = u % TC_ST, r = u / TC_ST;
-            if (!mbar_wait(smem_u32(&bar_full[s]), r & 1, abort) ||
-                !mbar_wait(smem_u32(&bar_b[s]), r & 1, abort)) {
+            if (!mbar_wait(smem_u32(&bar_full[s]), r & 1, abort, spin) ||
+                !mbar_wait(smem_u32(&bar_b[s]), r & 1, abort, spin)) {
                 ok = false;
                 break;
             }
@@ -541,6 +548,12 @@ void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *
                    float *Qs, const float *Bop, const Geom *g, float *Ps, double *V, int *flags,
                    cudaStream_t s)
 {
+    // CCFMM_TC_STALL=1 (failure-path tests): the MMA thread issues nothing
+    // and the waits give up after 2^12 polls; the evaluation then reports
+    // CCFMM_ERR_TIMEOUT
+    const char *sv = getenv("CCFMM_TC_STALL");
+    const int stall = (sv && atoi(sv)) ? 1 : 0;
+    const long long spin = stall ? (1ll << 12) : TC_SPIN;
     if (nitems > 0) {
 #define M2LTC(KPV)                                                                              \
     case KPV: {                                                                                 \
@@ -554,7 +567,7 @@ void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *
         note_launch();                                                                          \
         k_m2l_tc<KPV><<<nitems, TC_THREADS, smem, s>>>(                                         \
             items, ent_u, ent_src, Qs, ncell * S::KT,                                           \
-            reinterpret_cast<const unsigned char *>(Bop), Ps, flags);                           \
+            reinterpret_cast<const unsigned char *>(Bop), Ps, flags, spin, stall);              \
     } break;
         switch (KP) {
             M2LTC(40) M2LTC(56) M2LTC(88) M2LTC(120)

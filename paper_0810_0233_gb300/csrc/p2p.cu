@@ -52,7 +52,17 @@ __device__ __forceinline__ void dip_pair(real tx, real ty, real tz, real sx, rea
     hz += ri3 * (t * rz - mz);
 }
 
-constexpr int P2P_TPT = 2;    // targets per thread
+// targets per thread, and whether target groups are padded to whole warps
+// (then all lanes of a warp share one stripe of sources: broadcast shared
+// loads, uniform loop bounds)
+#ifndef CCFMM_P2P_TPT
+#define CCFMM_P2P_TPT 2
+#endif
+#ifndef CCFMM_P2P_WARPS
+#define CCFMM_P2P_WARPS 0
+#endif
+constexpr int P2P_TPT = CCFMM_P2P_TPT;
+constexpr bool P2P_WARP_STRIPES = CCFMM_P2P_WARPS != 0;
 
 template <typename real, bool SELF>
 __device__ __forceinline__ void p2p_range(const typename vec4<real>::t *sp,
@@ -157,7 +167,8 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
 
     for (int tb = 0; tb < nt; tb += P2P_TPT * P2P_T) {
         const int ntc = min(nt - tb, P2P_TPT * P2P_T);
-        const int ngrp = (ntc + P2P_TPT - 1) / P2P_TPT;
+        const int ngrp = P2P_WARP_STRIPES ? 32 * ((ntc + 32 * P2P_TPT - 1) / (32 * P2P_TPT))
+                                          : (ntc + P2P_TPT - 1) / P2P_TPT;
         const int S = max(1, P2P_T / ngrp);
         const int q = tid % ngrp, stripe = tid / ngrp;
         const bool active = stripe < S;
