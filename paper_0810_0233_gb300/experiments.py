@@ -6,7 +6,11 @@
 * leaf_sweep(): time against the leaf occupancy s for the 32^3 lattice at
   (p, alpha) = (3, 0.54) (the paper's Table I, whose optimum is s = 8);
 * optimal_leaf(): the best occupancy s_o(p), averaged over lattices 30^3 ..
-  59^3 as in Fig. 2, to set beside the rule of thumb of Eq. so.
+  59^3 as in Fig. 2, to set beside the rule of thumb of Eq. so;
+* error_budget(): for error estimates e = [alpha/(2 - alpha)]^p (Sec. IV),
+  every order p with the alpha that meets e, timed on the 32^3 lattice with
+  the measured field and energy errors against the direct sum (Table II and
+  the optimal-time-versus-accuracy curve of Fig. 3).
 
 Times are CUDA-event times of the library's own call sequence (tree, lists
 and D tables, then the field) on the current device, best of `repeats`.  The
@@ -128,28 +132,73 @@ def optimal_leaf(ps=(2, 3, 4, 5, 6, 7, 8), sizes=range(30, 60), theta=0.54, seed
     return res
 
 
+def alpha_for(e, p):
+    """The opening angle whose error estimate [alpha/(2-alpha)]^p equals e."""
+    r = e ** (1.0 / p)
+    return 2.0 * r / (1.0 + r)
+
+
+def error_budget(n=32, es=(0.05, 0.01, 1e-3, 2e-4), ps=(2, 3, 4, 5, 6, 7, 8), seed=4):
+    """Table II / Fig. 3: time per (e, p) and the errors actually reached."""
+    import torch
+    run, stream = _timer()
+    pos, mom, box = _lattice(n, seed)
+    pd = torch.from_numpy(pos).cuda()
+    md = torch.from_numpy(mom).cuda()
+    Hd = C.direct_field(pd, md, stream=stream)
+    Ed = -0.5 * float((mom * Hd).sum())
+    H = torch.zeros((len(pos), 3), dtype=torch.float64, device="cuda")
+    rows = []
+    for e in es:
+        for p in ps:
+            a = alpha_for(e, p)
+            with C.FMM(pd, md, p, a, 0.0, box=box, stream=stream) as f:
+                _, E = f.field_energy(H)
+
+                def step():
+                    f.set_positions(pd, md)
+                    f.field(H)
+
+                ms = run(step, 3)
+                Hf = H.cpu().numpy()
+            err = float(np.sqrt(((Hf - Hd) ** 2).sum() / (Hd ** 2).sum()))
+            rows.append({"e": e, "p": p, "alpha": a, "ms": ms, "rms_field_error": err,
+                         "energy_error": abs(E - Ed) / abs(Ed)})
+    best = {}
+    for e in es:
+        cand = [r for r in rows if r["e"] == e]
+        b = min(cand, key=lambda r: r["ms"])
+        best[e] = {"p": b["p"], "alpha": b["alpha"], "ms": b["ms"]}
+    return {"rows": rows, "fastest": best}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="fewer sizes (smoke run)")
+    ap.add_argument("--part", default="all",
+                    choices=["all", "scaling", "leaf_sweep", "optimal_leaf", "error_budget"])
     ap.add_argument("--out", default="experiments.json")
     args = ap.parse_args()
     t0 = time.time()
+    quick = {"scaling": dict(sizes=(8, 16, 32), params=((4, 0.5),)),
+             "leaf_sweep": dict(leaves=(4, 8, 16)),
+             "optimal_leaf": dict(ps=(3, 5), sizes=(30, 31)),
+             "error_budget": dict(n=16, es=(0.05,), ps=(3, 5))}
+    parts = {"scaling": scaling, "leaf_sweep": leaf_sweep, "optimal_leaf": optimal_leaf,
+             "error_budget": error_budget}
     res = {}
-    if args.quick:
-        res["scaling"] = scaling(sizes=(8, 16, 32), params=((4, 0.5),))
-        res["leaf_sweep"] = leaf_sweep(leaves=(4, 8, 16))
-        res["optimal_leaf"] = optimal_leaf(ps=(3, 5), sizes=(30, 31))
-    else:
-        res["scaling"] = scaling()
-        print(json.dumps(res["scaling"]), flush=True)
-        res["leaf_sweep"] = leaf_sweep()
-        print(json.dumps(res["leaf_sweep"]), flush=True)
-        res["optimal_leaf"] = optimal_leaf()
+    for name, fn in parts.items():
+        if args.part not in ("all", name):
+            continue
+        res[name] = fn(**quick[name]) if args.quick else fn()
+        show = res[name]
+        if name == "optimal_leaf":
+            show = {p: {"s_o": v["s_o"], "rule": v["rule"]} for p, v in show.items()}
+        elif name == "error_budget":
+            show = show["fastest"]
+        print(json.dumps({name: show}), flush=True)
     res["seconds"] = time.time() - t0
     json.dump(res, open(args.out, "w"), indent=1)
-    print(json.dumps({k: v for k, v in res.items() if k != "optimal_leaf"}), flush=True)
-    print(json.dumps({p: {"s_o": v["s_o"], "rule": v["rule"]}
-                      for p, v in res["optimal_leaf"].items()}), flush=True)
 
 
 if __name__ == "__main__":

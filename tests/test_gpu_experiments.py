@@ -27,3 +27,16 @@ def test_optimal_leaf_small():
     res = X.optimal_leaf(ps=(3,), sizes=(30,))
     assert res[3]["rule"] == C.leaf_size_rule(3)
     assert 1.0 <= res[3]["s_o"] <= 512.0
+
+
+def test_error_budget_small():
+    """Table II's construction: alpha from the estimate e = [a/(2-a)]^p, and
+    at e = 0.05 the errors reached stay inside the estimate, with the energy
+    error below 1 % (Sec. IV)."""
+    res = X.error_budget(n=16, es=(0.05,), ps=(3, 5))
+    for r in res["rows"]:
+        a = r["alpha"]
+        assert abs((a / (2 - a)) ** r["p"] - 0.05) < 1e-12
+        assert r["rms_field_error"] < 0.05
+        assert r["energy_error"] < 0.01
+    assert res["fastest"][0.05]["p"] in (3, 5)
