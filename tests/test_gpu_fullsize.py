@@ -73,3 +73,33 @@ def test_ring_4m_p6_theta04():
     assert rel(Hm[sel], Href[sel]) < 1e-5
     sub = W.subset(len(pos), 1000, 4)
     assert rel(Hm[sub], C.direct_field(pos, mom, targets=sub)) < 1e-4
+
+
+def test_ensemble_512_p5():
+    """The ensemble in the bench's configuration: all 512 samples (sum N =
+    18,752,310) stepped by one graph launch per step.  After two steps every
+    rotated moment against the oracle's rotation, and the field and energy of
+    sampled samples (the six smallest and two random ones) against the oracle
+    FMM on the rotated moments."""
+    pos, mom, off = W.ensemble()
+    assert len(off) == 513 and off[-1] == 18_752_310
+    p, theta, seed = 5, 0.5, 810237
+    with C.Batch(pos, mom, off, p, theta) as b:
+        H = np.zeros((b.total, 3))
+        E = np.zeros(b.ns)
+        for step in range(2):
+            b.step(seed=seed, step=step, max_angle=0.05, H_out=H, E_out=E)
+        M = b.moments()
+    ref_m = mom
+    for step in range(2):
+        ref_m = O.rotate_moments(ref_m, seed, step, 0.05)
+    assert np.abs(M - ref_m).max() < 1e-14
+    sizes = np.diff(off)
+    rng = np.random.default_rng(9)
+    pick = list(np.argsort(sizes)[:6]) + list(rng.choice(np.where(sizes < 40000)[0], 2,
+                                                          replace=False))
+    for s in pick:
+        sl = slice(off[s], off[s + 1])
+        Hr, Er, _ = O.fmm_field(pos[sl], ref_m[sl], p, theta)
+        assert rel(H[sl], Hr) < 1e-5, s
+        assert abs(E[s] - Er) <= 1e-4 * abs(Er), s
