@@ -74,7 +74,10 @@ typedef struct {
     double ms_build;          /* tree + lists + D tables of the last build */
     double ms_eval;           /* mean evaluation time (P2M ... unpermute) */
     double ms_stage[8];       /* mean stage times: P2M, M2M, M2L, L2L, L2P, P2P,
-                                 finish; [7] = number of evaluations averaged */
+                                 finish; [7] = number of evaluations averaged.
+                                 With the near/far overlap (default) P2P runs
+                                 concurrently with P2M..L2L, so the stages do
+                                 not add up to ms_eval */
 } ccfmm_stats;
 
 /* ------------------------------------------------------------------------

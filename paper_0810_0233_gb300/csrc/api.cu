@@ -129,7 +129,9 @@ struct LevelPlan {
 // build events, then a ring of per-evaluation stage events so that stage
 // times of evaluations inside a caller's timed region can be read afterwards
 enum { EV_B0, EV_B1, EV_NB };
-enum { EV_E0, EV_P2M, EV_M2M, EV_M2L, EV_L2L, EV_L2P, EV_P2P, EV_FIN, EV_NE };
+// evaluation events: far chain E0..L2L, near field P2P0..P2P1, then the join
+// (both done), L2P and the unpermute (FIN)
+enum { EV_E0, EV_P2M, EV_M2M, EV_M2L, EV_L2L, EV_JOIN, EV_L2P, EV_FIN, EV_P2P0, EV_P2P1, EV_NE };
 constexpr int EV_RING = 32;
 
 struct ccfmm_s {
@@ -186,6 +188,10 @@ struct ccfmm_s {
     cudaEvent_t eve[EV_RING][EV_NE];
     long long n_eval = 0, n_eval_reset = 0;
     bool ev_ok = false;
+    // near/far overlap: the far chain runs on s_far (highest priority) while
+    // the near field runs on the handle's stream
+    cudaStream_t s_far = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ccfmm_stats st;
 };
 
@@ -694,6 +700,34 @@ static ccfmm_status tc_prepare(ccfmm_t h)
     return CCFMM_OK;
 }
 
+constexpr int OVERLAP_DEFAULT = 1;
+
+// Near/far overlap for standalone handles (ensemble members already run
+// eight-way concurrent inside their graph): 0 off (CCFMM_OVERLAP=0); 1 the
+// far chain on the high-priority stream; 2 the near field on it.
+static int use_overlap(ccfmm_t h)
+{
+    if (h->quiet) return 0;
+    const char *e = getenv("CCFMM_OVERLAP");
+    if (e && (!strcmp(e, "0") || !strcmp(e, "1") || !strcmp(e, "2"))) return e[0] - '0';
+    return OVERLAP_DEFAULT;
+}
+
+static ccfmm_status overlap_prepare(ccfmm_t h)
+{
+    if (h->s_far) return CCFMM_OK;
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&h->s_far, cudaStreamNonBlocking, greatest));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    return CCFMM_OK;
+}
+
+// One evaluation.  The near field (P2P, Appendix updateField) needs only the
+// sorted dipoles and the near lists; the far chain (P2M, M2M, M2L, L2L) only
+// the tree.  With the overlap they run on two streams, joined before L2P;
+// otherwise in sequence on the handle's stream with L2P fused into P2P.
 template <typename real>
 static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
 {
@@ -702,39 +736,68 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
     cudaStream_t s = h->stream;
     const int L = h->L, p = h->p, KP = h->KP;
     const long long ncellp = 1ll << (L + 1);
+    const bool tc = sizeof(real) == 4 && m2l_use_tc(h);
+    const int mode = use_overlap(h);
+    const bool ovl = mode != 0;
+    // one-time operator builds go on s before the fork
+    if (tc) TRY(tc_prepare(h));
+    if (ovl) TRY(overlap_prepare(h));
+    // s_far: the extra (high-priority) stream; it carries the far chain
+    // (mode 1) or the near field (mode 2)
+    cudaStream_t sf = mode == 1 ? h->s_far : s;
+    cudaStream_t sn = mode == 2 ? h->s_far : s;
     bool ev = h->ev_ok && !h->quiet;
     cudaEvent_t *evs = h->eve[h->n_eval % EV_RING];
     if (ev) CK(cudaEventRecord(evs[EV_E0], s));
-    CK(cudaMemsetAsync(h->V.p, 0, sizeof(double) * (size_t)ncellp * KP, s));
-    launch_p2m<real>(p, KP, L, P<int>(h->leaf_start), P<R4>(h->A), P<R2>(h->B), P<real>(h->Q), s);
-    if (ev) CK(cudaEventRecord(evs[EV_P2M], s));
-    for (int l = L - 1; l >= 0; --l) launch_m2m<real>(p, KP, l, P<Geom>(h->geomd), P<real>(h->Q), s);
-    if (ev) CK(cudaEventRecord(evs[EV_M2M], s));
-    if (sizeof(real) == 4 && m2l_use_tc(h)) {
-        TRY(tc_prepare(h));
+    if (ovl) {
+        CK(cudaEventRecord(h->ev_fork, s));
+        CK(cudaStreamWaitEvent(h->s_far, h->ev_fork, 0));
+        // near field only; L2P after the join
+        if (ev) CK(cudaEventRecord(evs[EV_P2P0], sn));
+        launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf,
+                         P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), nullptr, P<R4>(h->H), sn);
+        if (ev) CK(cudaEventRecord(evs[EV_P2P1], sn));
+    }
+    // far chain
+    CK(cudaMemsetAsync(h->V.p, 0, sizeof(double) * (size_t)ncellp * KP, sf));
+    launch_p2m<real>(p, KP, L, P<int>(h->leaf_start), P<R4>(h->A), P<R2>(h->B), P<real>(h->Q), sf);
+    if (ev) CK(cudaEventRecord(evs[EV_P2M], sf));
+    for (int l = L - 1; l >= 0; --l) launch_m2m<real>(p, KP, l, P<Geom>(h->geomd), P<real>(h->Q), sf);
+    if (ev) CK(cudaEventRecord(evs[EV_M2M], sf));
+    if (tc)
         launch_m2l_tc(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
                       P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
                       P<float>(h->Q), ncellp, P<float>(h->gkt), P<float>(h->Qs),
                       P<float>(h->Bop), P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V),
-                      &P<Readback>(h->rb)->eflags, s);
-    }
+                      &P<Readback>(h->rb)->eflags, sf);
     else if (sizeof(real) == 4 && m2l_f32_supported(KP, h->ldD))
         launch_m2l_f32(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
                        P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
                        P<float>(h->Q), P<float>(h->D), h->ldD, P<uint16_t>(h->itab),
-                       P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V), s);
+                       P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V), sf);
     else
         launch_m2l<real>(p, KP, P<Tile>(h->tiles), h->ntiles, P<int>(h->ent_u), P<int>(h->ent_src),
                          P<real>(h->Q), P<real>(h->D), h->ldD, P<uint16_t>(h->itab),
-                         P<Geom>(h->geomd), P<double>(h->V), s);
-    if (ev) CK(cudaEventRecord(evs[EV_M2L], s));
+                         P<Geom>(h->geomd), P<double>(h->V), sf);
+    if (ev) CK(cudaEventRecord(evs[EV_M2L], sf));
     for (int l = 2; l <= L; ++l)
-        launch_l2l(p, KP, l, L, P<Geom>(h->geomd), P<int>(h->leaf_start), P<double>(h->V), s);
-    if (ev) CK(cudaEventRecord(evs[EV_L2L], s));
+        launch_l2l(p, KP, l, L, P<Geom>(h->geomd), P<int>(h->leaf_start), P<double>(h->V), sf);
+    if (ev) CK(cudaEventRecord(evs[EV_L2L], sf));
+    if (ovl) {
+        CK(cudaEventRecord(h->ev_join, h->s_far));
+        CK(cudaStreamWaitEvent(s, h->ev_join, 0));
+        if (ev) CK(cudaEventRecord(evs[EV_JOIN], s));
+        launch_l2p<real>(p, KP, L, P<int>(h->leaf_start), P<R4>(h->A), P<double>(h->V),
+                         P<R4>(h->H), s);
+    } else {
+        if (ev) CK(cudaEventRecord(evs[EV_P2P0], s));
+        launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf,
+                         P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), P<double>(h->V),
+                         P<R4>(h->H), s);
+        if (ev) CK(cudaEventRecord(evs[EV_P2P1], s));
+        if (ev) CK(cudaEventRecord(evs[EV_JOIN], s));
+    }
     if (ev) CK(cudaEventRecord(evs[EV_L2P], s));
-    launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf,
-                     P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), P<double>(h->V), P<R4>(h->H), s);
-    if (ev) CK(cudaEventRecord(evs[EV_P2P], s));
     Readback *drb = P<Readback>(h->rb);
     launch_finish<real>(P<R4>(h->H), P<int>(h->idx), h->mom_energy ? h->mom_energy : P<double>(h->mom),
                         h->N, Hdev, P<double>(h->epart), h->E_dst ? h->E_dst : &drb->E, s);
@@ -954,8 +1017,12 @@ ccfmm_status fmm_stats(ccfmm_t h, ccfmm_stats *out)
         for (long long j = 0; j < n; ++j) {
             cudaEvent_t *e = h->eve[(h->n_eval - 1 - j) % EV_RING];
             if (cudaEventElapsedTime(&ms, e[EV_E0], e[EV_FIN]) == cudaSuccess) st.ms_eval += ms / n;
+            // p2m, m2m, m2l, l2l (far chain), l2p, p2p (near field), finish
+            const int from[7] = {EV_E0, EV_P2M, EV_M2M, EV_M2L, EV_JOIN, EV_P2P0, EV_L2P};
+            const int to[7] = {EV_P2M, EV_M2M, EV_M2L, EV_L2L, EV_L2P, EV_P2P1, EV_FIN};
             for (int i = 0; i < 7; ++i)
-                if (cudaEventElapsedTime(&ms, e[i], e[i + 1]) == cudaSuccess) st.ms_stage[i] += ms / n;
+                if (cudaEventElapsedTime(&ms, e[from[i]], e[to[i]]) == cudaSuccess)
+                    st.ms_stage[i] += ms / n;
         }
         st.ms_stage[7] = (double)n;
         cudaGetLastError();
@@ -990,6 +1057,12 @@ void fmm_destroy(ccfmm_t h)
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->hrb) cudaFreeHost(h->hrb);
+    if (h->s_far) {
+        cudaStreamSynchronize(h->s_far);
+        cudaStreamDestroy(h->s_far);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_ok) {
         for (int i = 0; i < EV_NB; ++i) cudaEventDestroy(h->evb[i]);
         for (int r = 0; r < EV_RING; ++r)

@@ -217,6 +217,10 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_sta
                 const NearEnt *near, const Geom *d_geom, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
                 cudaStream_t s);
+// V == nullptr: near field only; launch_l2p then adds the smooth field
+template <typename real>
+void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
+                const double *V, typename vec4<real>::t *H, cudaStream_t s);
 template <typename real>
 void launch_finish(const typename vec4<real>::t *H, const int *perm, const double *mom,
                    long long n, double *H_out, double *partial, double *d_E, cudaStream_t s);

@@ -54,6 +54,11 @@ namespace ccfmm {
 constexpr int TC_M = 128;       // field cells per tile (MMA M = TMEM lanes)
 constexpr int TC_KC = 32;       // K per unit: 4 MMA k-steps of 8
 constexpr int TC_SMEM = 227 * 1024;
+// at most this many pipeline stages (3 leaves room on the SM for a block of
+// the near-field kernel running concurrently)
+#ifndef CCFMM_TC_MAXST
+#define CCFMM_TC_MAXST 4
+#endif
 #ifndef CCFMM_TC_PROD
 #define CCFMM_TC_PROD 256
 #endif
@@ -73,7 +78,7 @@ template <int KP> struct TcShape {
     static constexpr int OP_BYTES = NCH * 2 * B_BYTES;            // one offset class
     // pipeline stages that fit (at most 4), and how many units a producer
     // keeps in flight before marking the oldest one full
-    static constexpr int ST = (TC_SMEM - 2048) / STAGE >= 4 ? 4 : 3;
+    static constexpr int ST = (TC_SMEM - 2048) / STAGE >= 4 && CCFMM_TC_MAXST >= 4 ? 4 : 3;
     static constexpr int LAG = ST - 1;
     static constexpr int TMEM_COLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256);
 };

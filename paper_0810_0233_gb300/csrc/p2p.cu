@@ -90,10 +90,13 @@ __device__ __forceinline__ void stripe_range(int len, int S, int stripe, int &j0
 }
 
 // Smooth field (Eq. H, H = -grad V) of one target from its leaf's Taylor
-// coefficients vs[] (multi-indices mi[]), powers pw[3][PMAX] = x^j / j!.
+// coefficients vs[] (multi-indices mi[]), powers x^j / j! kept in pw[i * ps]
+// for i = d * PMAX + j (ps: the caller's stride, so that the lanes of a warp
+// use consecutive words and no bank twice).
 template <typename real>
 __device__ __forceinline__ void l2p_one(int p, int K, const real *vs, const unsigned *mi, real *pw,
-                                        real x, real y, real z, real &h0, real &h1, real &h2)
+                                        int ps, real x, real y, real z, real &h0, real &h1,
+                                        real &h2)
 {
     const real inv[PMAX] = {(real)0, (real)1, (real)0.5, (real)1 / (real)3, (real)0.25,
                             (real)0.2, (real)1 / (real)6, (real)1 / (real)7};
@@ -101,12 +104,12 @@ __device__ __forceinline__ void l2p_one(int p, int K, const real *vs, const unsi
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         real t = (real)1;
-        pw[d * PMAX] = t;
+        pw[(d * PMAX) * ps] = t;
 #pragma unroll
         for (int j = 1; j < PMAX; ++j) {
             if (j < p) {
                 t = t * c[d] * inv[j];
-                pw[d * PMAX + j] = t;
+                pw[(d * PMAX + j) * ps] = t;
             }
         }
     }
@@ -114,9 +117,11 @@ __device__ __forceinline__ void l2p_one(int p, int K, const real *vs, const unsi
         unsigned n = mi[k];
         int nx = (int)(n & 31u), ny = (int)((n >> 5) & 31u), nz = (int)((n >> 10) & 31u);
         real v = vs[k];
-        if (nx > 0) h0 -= v * pw[nx - 1] * pw[PMAX + ny] * pw[2 * PMAX + nz];
-        if (ny > 0) h1 -= v * pw[nx] * pw[PMAX + ny - 1] * pw[2 * PMAX + nz];
-        if (nz > 0) h2 -= v * pw[nx] * pw[PMAX + ny] * pw[2 * PMAX + nz - 1];
+        // loads only inside the branches: there every index is at most p - 1
+        // (|n| <= p and the derivative's component is >= 1)
+        if (nx > 0) h0 -= v * pw[(nx - 1) * ps] * pw[(PMAX + ny) * ps] * pw[(2 * PMAX + nz) * ps];
+        if (ny > 0) h1 -= v * pw[nx * ps] * pw[(PMAX + ny - 1) * ps] * pw[(2 * PMAX + nz) * ps];
+        if (nz > 0) h2 -= v * pw[nx * ps] * pw[(PMAX + ny) * ps] * pw[(2 * PMAX + nz - 1) * ps];
     }
 }
 
@@ -157,12 +162,15 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = nterms(p) - 1;
     const long long hid = (1ll << L) + key;
-    for (int c = tid; c < K; c += P2P_T) {
-        vs[c] = (real)V[hid * KP + c];
-        int x, y, z;
-        midx_inv(c + 1, x, y, z);
-        mi[c] = (unsigned)x | ((unsigned)y << 5) | ((unsigned)z << 10);
-    }
+    // V == nullptr: near field only (L2P by k_l2p once V is complete)
+    const bool with_l2p = V != nullptr;
+    if (with_l2p)
+        for (int c = tid; c < K; c += P2P_T) {
+            vs[c] = (real)V[hid * KP + c];
+            int x, y, z;
+            midx_inv(c + 1, x, y, z);
+            mi[c] = (unsigned)x | ((unsigned)y << 5) | ((unsigned)z << 10);
+        }
     const double wx = g->w[L][0], wy = g->w[L][1], wz = g->w[L][2];
 
     for (int tb = 0; tb < nt; tb += P2P_TPT * P2P_T) {
@@ -290,11 +298,12 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
         }
         __syncthreads();
         if (tid < ngrp) {
-            real *pw = reinterpret_cast<real *>(sp) + tid * 3 * PMAX;
+            real *pw = reinterpret_cast<real *>(sp) + tid;  // stride P2P_T
 #pragma unroll
             for (int i = 0; i < P2P_TPT; ++i) {
-                l2p_one<real>(p, K, vs, mi, pw, tx[i][0], tx[i][1], tx[i][2], f[i][0], f[i][1],
-                              f[i][2]);
+                if (with_l2p)
+                    l2p_one<real>(p, K, vs, mi, pw, P2P_T, tx[i][0], tx[i][1], tx[i][2], f[i][0],
+                                  f[i][1], f[i][2]);
                 R4 o;
                 o.x = f[i][0];
                 o.y = f[i][1];
@@ -321,6 +330,55 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_sta
     note_launch();
     k_p2p<real><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start, near_start, near,
                                                          d_geom, A, B, V, H);
+}
+
+// L2P (Eq. H, H = -grad V) of every dipole of a leaf (one warp per leaf),
+// added to the near field that k_p2p stored without its fused L2P: the same
+// operations in the same order as the fused epilogue.
+constexpr int L2P_W = 4;  // leaves (warps) per block
+
+template <typename real>
+__global__ void __launch_bounds__(32 * L2P_W) k_l2p(int p, int KP, int L, const int *leaf_start,
+                                                    const typename vec4<real>::t *A,
+                                                    const double *V, typename vec4<real>::t *H)
+{
+    __shared__ real vs[L2P_W][nterms(PMAX)];
+    __shared__ unsigned mi[nterms(PMAX)];
+    __shared__ real pw[L2P_W][3 * PMAX][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = nterms(p) - 1;
+    for (int c = threadIdx.x; c < K; c += 32 * L2P_W) {
+        int x, y, z;
+        midx_inv(c + 1, x, y, z);
+        mi[c] = (unsigned)x | ((unsigned)y << 5) | ((unsigned)z << 10);
+    }
+    const long long key = (long long)blockIdx.x * L2P_W + w;
+    const bool live = key < (1ll << L);
+    const int t0 = live ? leaf_start[key] : 0, nt = live ? leaf_start[key + 1] - t0 : 0;
+    const long long hid = (1ll << L) + key;
+    if (nt > 0)
+        for (int c = lane; c < K; c += 32) vs[w][c] = (real)V[hid * KP + c];
+    __syncthreads();
+    for (int i = lane; i < nt; i += 32) {
+        const typename vec4<real>::t a = A[t0 + i];
+        typename vec4<real>::t h = H[t0 + i];
+        real f0 = h.x, f1 = h.y, f2 = h.z;
+        l2p_one<real>(p, K, vs[w], mi, &pw[w][0][lane], 32, a.x, a.y, a.z, f0, f1, f2);
+        h.x = f0;
+        h.y = f1;
+        h.z = f2;
+        H[t0 + i] = h;
+    }
+}
+
+template <typename real>
+void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
+                const double *V, typename vec4<real>::t *H, cudaStream_t s)
+{
+    const long long nleaf = 1ll << L;
+    note_launch();
+    k_l2p<real><<<(unsigned)((nleaf + L2P_W - 1) / L2P_W), 32 * L2P_W, 0, s>>>(p, KP, L,
+                                                                             leaf_start, A, V, H);
 }
 
 // unpermute to input order in FP64 and form per-block partial sums of m.H
@@ -468,7 +526,9 @@ void launch_p2p_pair_count(int L, const int *leaf_start, const int *near_start,
                                    const Geom *, const vec4<real>::t *, const vec2<real>::t *,  \
                                    const double *, vec4<real>::t *, cudaStream_t);              \
     template void launch_finish<real>(const vec4<real>::t *, const int *, const double *,       \
-                                      long long, double *, double *, double *, cudaStream_t);
+                                      long long, double *, double *, double *, cudaStream_t);  \
+    template void launch_l2p<real>(int, int, int, const int *, const vec4<real>::t *,           \
+                                   const double *, vec4<real>::t *, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST
