@@ -33,8 +33,8 @@ FP32_LANES_PER_SM, SMS = 128, 152
 # dram read+write bytes per launch of the 10^6-dipole workload from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the
 # kernel source they were taken on; reported only while it is unchanged
-NCU_TRAFFIC = {"p2p": {"bytes": 133892352, "src": "728943824c38"},
-               "m2l": {"bytes": 307199232, "src": "c52cf26fe7c4"}}
+NCU_TRAFFIC = {"p2p": {"bytes": 112033792, "src": "0f64c8bef282"},
+               "m2l": {"bytes": 305294080, "src": "e0ed57b7bc2d"}}
 # dense TF32 tensor peak = measured bf16 peak x nominal 1.1 / 2.25
 TF32_PER_BF16 = 1.1 / 2.25
 
@@ -501,6 +501,27 @@ def main():
                         "m2l_flop_per_far_pair": 2 * K * K, "far_pairs": st["far_pairs"]},
         "stage_ms": stages,
         "other": {k: roof(k) for k in flops if k != dom}})
+    # the same kernels timed alone (near/far overlap off, a few untimed-step
+    # evaluations outside the timed regions)
+    prev = os.environ.get("CCFMM_OVERLAP")
+    os.environ["CCFMM_OVERLAP"] = "0"
+    f.reset_stats()
+    timed(step_eval, min(steps, 10), 1)
+    st_iso = f.stats()
+    if prev is None:
+        del os.environ["CCFMM_OVERLAP"]
+    else:
+        os.environ["CCFMM_OVERLAP"] = prev
+    ms_iso = st_iso["ms_stage"]
+    iso = {"p2p": ms_iso[5], "m2l": ms_iso[2]}
+    line["roofline"]["isolated"] = {
+        k: {"ms": iso[k], "achieved": flops[k] / (iso[k] * 1e-3) / 1e12,
+            "frac": flops[k] / (iso[k] * 1e-3) / 1e12 /
+            (tf32_peak if (k == "m2l" and tc) else fp32_peak)}
+        for k in iso}
+    line["roofline"]["note"] = ("stage times of the timed evaluations, where P2P runs concurrently "
+                                "with P2M..L2L on a second stream; 'isolated': the same kernels "
+                                "timed with the overlap off")
     line["clocks"] = clk.summary()
     line["build_ms"] = st["ms_build"]
 
