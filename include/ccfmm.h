@@ -114,7 +114,11 @@ ccfmm_status fmm_create_ex(const double *positions, const double *moments, int64
 
 /* Rebuild tree, lists and derivative tensors for new positions (and
  * moments) with the same N, p, theta, leaf_size, box rule and precision,
- * reusing the handle's device memory where it suffices. */
+ * reusing the handle's device memory where it suffices.  Returns once the
+ * inputs have been read (the caller may then change or free them); the last
+ * build kernels may still be running on the handle's stream, and every later
+ * call on the handle is ordered after them.  (fmm_create builds the same
+ * way.) */
 ccfmm_status fmm_set_positions(ccfmm_t h, const double *positions, const double *moments);
 
 /* Replace the moments; the tree and lists are kept (positions unchanged). */

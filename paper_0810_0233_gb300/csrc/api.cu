@@ -663,8 +663,12 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     launch_p2p_pair_count(L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf, &drb->pairs, s);
     KCHECK();
     if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_B1], s));
-    // the handle is complete when the build returns
-    CK(cudaStreamSynchronize(s));
+    // The last kernels (tile fill, D tables, pair count) may still run when
+    // the build returns: everything later on the handle's stream is ordered
+    // after them, their flags are read by the next synchronising call, the
+    // host sources of their uploads belong to the handle and change only
+    // after the next build's first synchronisation, and stats, accessors and
+    // destroy synchronise first.  The next evaluation is enqueued meanwhile.
     h->built = true;
     h->tc_ops_ready = false;
     return CCFMM_OK;
