@@ -325,21 +325,48 @@ static ccfmm_status make_plan(ccfmm_t h)
     dmap.assign((size_t)std::max(gid, 1), 0);
     dsep.clear();
     {
-        std::map<std::array<uint64_t, 3>, int> seen;
-        for (int g = 0; g < gid; ++g) {
-            const int4 o = offs[g];
-            const int l = o.w;
+        // levels grouped by their exact scaled cell shape w/h; inside a group
+        // an open-addressing table maps the packed integer offset to a D
+        // table, which is reused only when its separation is bitwise equal
+        size_t cap = 64;
+        while (cap < 4 * (size_t)std::max(gid, 1)) cap <<= 1;
+        std::vector<std::array<double, 3>> shapes;
+        std::vector<std::vector<std::pair<int, int>>> tabs;  // (packed offset, D table)
+        for (int l = 1; l <= L; ++l) {
+            const LevelPlan &lp = h->plan[l];
+            if (lp.farv.empty()) continue;
             const double hl = h->geom.h[l];
-            double v[3] = {(double)o.x * h->geom.w[l][0] / hl, (double)o.y * h->geom.w[l][1] / hl,
-                           (double)o.z * h->geom.w[l][2] / hl};
-            std::array<uint64_t, 3> key;
-            for (int a = 0; a < 3; ++a) memcpy(&key[a], &v[a], 8);
-            auto it = seen.find(key);
-            if (it == seen.end()) {
-                it = seen.emplace(key, (int)dsep.size()).first;
-                dsep.push_back(make_double4(v[0], v[1], v[2], 0.0));
+            const std::array<double, 3> shp = {h->geom.w[l][0] / hl, h->geom.w[l][1] / hl,
+                                               h->geom.w[l][2] / hl};
+            size_t gi = 0;
+            while (gi < shapes.size() && memcmp(&shapes[gi], &shp, sizeof(shp)) != 0) ++gi;
+            if (gi == shapes.size()) {
+                shapes.push_back(shp);
+                tabs.emplace_back(cap, std::make_pair(-1, -1));
             }
-            dmap[g] = it->second;
+            std::vector<std::pair<int, int>> &tab = tabs[gi];
+            for (size_t u = 0; u < lp.farv.size(); ++u) {
+                const int key = lp.farv[u];
+                int o[3];
+                unpacko(key, o);
+                const double v[3] = {(double)o[0] * h->geom.w[l][0] / hl,
+                                     (double)o[1] * h->geom.w[l][1] / hl,
+                                     (double)o[2] * h->geom.w[l][2] / hl};
+                size_t k = ((uint32_t)key * 2654435761u) & (cap - 1);
+                while (tab[k].first != -1 && tab[k].first != key) k = (k + 1) & (cap - 1);
+                int d = tab[k].first == key ? tab[k].second : -1;
+                if (d >= 0) {
+                    const double4 &e = dsep[d];
+                    const double w3[3] = {e.x, e.y, e.z};
+                    if (memcmp(w3, v, sizeof(v)) != 0) d = -1;
+                }
+                if (d < 0) {
+                    d = (int)dsep.size();
+                    dsep.push_back(make_double4(v[0], v[1], v[2], 0.0));
+                    tab[k] = std::make_pair(key, d);
+                }
+                dmap[lp.gid_base + u] = d;
+            }
         }
     }
     h->n_d = (int)dsep.size();
