@@ -155,6 +155,8 @@ struct ccfmm_s {
     long long near_leaf_total = 0, far_total = 0, ent_total = 0;
     bool built = false, evaluated = false, ftable_ready = false;
     bool tc_ops_ready = false;  // tensor-core M2L operators of the current build
+    bool pairs_counted = false; // near-pair count of the current build taken
+    long long pairs = 0;
     bool rb_fresh = true;       // device readback block not yet initialised
     bool leaf_perm_valid = false;
 
@@ -687,7 +689,8 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     TRY(ensure(h->Q, rs * (size_t)ncellp * h->KP));
     TRY(ensure(h->V, sizeof(double) * (size_t)ncellp * h->KP));
     TRY(ensure(h->epart, sizeof(double) * ((N + 255) / 256 + 1)));
-    launch_p2p_pair_count(L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf, &drb->pairs, s);
+    // the near-pair count (statistics only) is taken by fmm_stats on demand
+    h->pairs_counted = false;
     KCHECK();
     if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_B1], s));
     // The last kernels (tile fill, D tables, pair count) may still run when
@@ -1016,9 +1019,18 @@ ccfmm_status fmm_stats(ccfmm_t h, ccfmm_stats *out)
     g_err.clear();
     if (!h || !out) return fail(CCFMM_ERR_ARG, "NULL argument");
     CK(cudaSetDevice(h->device));
-    CK(cudaStreamSynchronize(h->stream));
     Readback *drb = P<Readback>(h->rb);
-    CK(cudaMemcpy(&h->hrb->pairs, &drb->pairs, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    if (h->built && !h->pairs_counted) {
+        CK(cudaMemsetAsync(&drb->pairs, 0, sizeof(unsigned long long), h->stream));
+        launch_p2p_pair_count(h->L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf,
+                              &drb->pairs, h->stream);
+        CK(cudaMemcpyAsync(&h->hrb->pairs, &drb->pairs, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->pairs = (long long)h->hrb->pairs;
+        h->pairs_counted = true;
+    }
+    CK(cudaStreamSynchronize(h->stream));
     ccfmm_stats st;
     memset(&st, 0, sizeof(st));
     st.depth = h->L;
@@ -1036,7 +1048,7 @@ ccfmm_status fmm_stats(ccfmm_t h, ccfmm_stats *out)
     st.nonempty_leaves = h->hrb->ne[h->L];
     st.near_leaf_pairs = h->near_leaf_total;
     st.far_pairs = h->far_total;
-    st.p2p_pairs = (int64_t)h->hrb->pairs;
+    st.p2p_pairs = h->built ? (int64_t)h->pairs : 0;
     st.m2l_tile_entries = h->ent_total;
     st.far_offsets = h->n_d;
     if (h->ev_ok) {

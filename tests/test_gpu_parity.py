@@ -265,3 +265,20 @@ def test_injected_allocation_failure():
                        timeout=300)
     assert r.returncode == 0, r.stderr
     assert "STATUS -2" in r.stdout and "AFTER True" in r.stdout, r.stdout
+
+
+def test_near_pair_count_from_the_lists():
+    """fmm_stats' p2p_pairs (counted on demand once per build) equals the
+    ordered near pairs i != j implied by the leaf near lists, before and
+    after a rebuild."""
+    pos, mom = W.ferrofluid(20000, side=100.0 * 0.02 ** (1 / 3), seed=W.BASE_SEED + 61)
+    with C.FMM(pos, mom, 6, 0.5) as f:
+        for step in range(2):
+            if step:
+                pos = pos * 0.7
+                f.set_positions(pos, mom)
+            st = f.stats()
+            L = st["depth"]
+            cnt = np.bincount(f.leaf_of(), minlength=1 << L)
+            pr = f.pairs("near") - (1 << L)
+            assert st["p2p_pairs"] == int((cnt[pr[:, 0]] * cnt[pr[:, 1]]).sum()) - len(pos)
