@@ -243,15 +243,13 @@ def describe_ensemble(ns, total, p, theta):
 def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
     """The ensemble step: every rank steps all samples of its share
     (samples dealt round-robin over ranks, no collective in the step)."""
+    from paper_0810_0233_gb300 import ranks as R
     from paper_0810_0233_gb300 import workloads as W
     p, theta = WORKLOADS["ensemble"]
     pos, mom, off = W.ensemble()
     ns = len(off) - 1
-    mine = list(range(rank, ns, world))
-    sp = [pos[off[i]:off[i + 1]] for i in mine]
-    sm = [mom[off[i]:off[i + 1]] for i in mine]
-    o = np.concatenate([[0], np.cumsum([len(x) for x in sp])]).astype(np.int64)
-    P_, M_ = np.concatenate(sp), np.concatenate(sm)
+    mine, o, rows = R.shard(off, rank, world)
+    P_, M_ = R.gather_rows(pos, rows), R.gather_rows(mom, rows)
     total = int(o[-1])
     b = C.Batch(torch.from_numpy(P_).to(dev), torch.from_numpy(M_).to(dev), o, p, theta,
                 precision=args.precision, stream=stream)
@@ -280,11 +278,7 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
         z.synchronize()
         total_t = a.elapsed_time(z) / 1e3
         barrier()
-        if world > 1:
-            t = torch.tensor([total_t], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_t = float(t.item())
-        return total_t
+        return R.max_over_ranks(total_t, dist if world > 1 else None, dev)
 
     launches0 = C.kernel_launches()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
@@ -298,12 +292,7 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
         counter[0] += 1
 
     t_e2e = timed(step_e2e, args.steps, 1)
-    if world > 1:
-        t = torch.tensor([float(total)], device=dev)
-        dist.all_reduce(t)
-        all_total = int(t.item())
-    else:
-        all_total = total
+    all_total = int(R.sum_over_ranks(total, dist if world > 1 else None, dev))
     # algorithmic work of one step, summed over this rank's samples
     K = (p + 1) * (p + 2) * (p + 3) // 6 - 1
     pairs = far = 0
@@ -368,6 +357,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_0810_0233_gb300 import ccfmm as C
+    from paper_0810_0233_gb300 import ranks as R
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -409,11 +399,7 @@ def main():
             b.synchronize()
             total += a.elapsed_time(b) / 1e3
         barrier()
-        if world > 1:
-            t = torch.tensor([total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-        return total
+        return R.max_over_ranks(total, dist if world > 1 else None, dev)
 
     def step_full():
         f.set_positions(pos_d, mom_d)
