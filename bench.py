@@ -514,10 +514,16 @@ def main():
     if not args.no_accuracy:
         from paper_0810_0233_gb300 import workloads as W
         sub = W.subset(n, 10000, 77)
-        Hd = C.direct_field(pos_d, mom_d, targets=torch.from_numpy(sub).to(dev), stream=stream)
+        sub_d = torch.from_numpy(sub).to(dev)
+        t0 = time.perf_counter()
+        Hd = C.direct_field(pos_d, mom_d, targets=sub_d, stream=stream)
+        t_direct = time.perf_counter() - t0
         H = H_d.cpu().numpy()
         err_direct = float(np.sqrt(((H[sub] - Hd) ** 2).sum() / (Hd ** 2).sum()))
-        acc = {"rms_vs_direct_10k": err_direct}
+        acc = {"rms_vs_direct_10k": err_direct,
+               "direct_sum_10k_ms": 1e3 * t_direct,
+               "direct_sum_note": "FP64 GPU direct sum at the 10k subset over all N sources "
+                                  "(wall time of the call)"}
         if args.precision == "mixed":
             with C.FMM(pos_d, mom_d, P, THETA, 0.0, precision="fp64", stream=stream) as g:
                 H64 = torch.zeros_like(H_d)
@@ -528,6 +534,15 @@ def main():
         line["accuracy"] = acc
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(pos, mom, P, THETA)
+        # the same oracle on one host thread, on a smaller sample
+        import oracle as O
+        nthr = O.threads()
+        O.set_threads(1)
+        try:
+            one = cpu_oracle_sample(pos, mom, P, THETA, nleaves=128, seed=12)
+        finally:
+            O.set_threads(nthr)
+        line["cpu_baseline"]["single_thread"] = {k: one[k] for k in ("value", "cores", "sample")}
     f.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
