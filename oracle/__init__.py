@@ -56,6 +56,8 @@ def _bind(path):
         "orc_m2m": (None, [ctypes.c_int, _dp, _dp, _dp]),
         "orc_l2l": (None, [ctypes.c_int, _dp, _dp, _dp]),
         "orc_m2l": (None, [ctypes.c_int, _dp, _dp, _dp]),
+        "orc_m2l_degree": (None, [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]),
+        "orc_fmm_set_truncation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
         "orc_l2p": (None, [ctypes.c_int, _dp, _dp, _dp]),
         "orc_direct_field": (None, [_i64, _dp, _dp, _i64, _lp, _dp]),
         "orc_energy_from_field": (ctypes.c_double, [_i64, _dp, _dp]),
@@ -192,12 +194,16 @@ def l2l(p, c, Vparent, Vchild=None) -> np.ndarray:
     return Vc
 
 
-def m2l(p, c, Q, V=None) -> np.ndarray:
-    """Eq. taylorcalc; c = field-cell centre relative to the source-cell centre."""
+def m2l(p, c, Q, V=None, max_degree=None) -> np.ndarray:
+    """Eq. taylorcalc; c = field-cell centre relative to the source-cell centre.
+    ``max_degree`` None: square truncation; else only terms |n|+|k| <= it."""
     c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(3))
     Q = np.ascontiguousarray(Q, dtype=np.float64)
     V = np.zeros(nterms(p)) if V is None else np.array(V, dtype=np.float64)
-    _load().orc_m2l(p, _d(c), _d(Q), _d(V))
+    if max_degree is None:
+        _load().orc_m2l(p, _d(c), _d(Q), _d(V))
+    else:
+        _load().orc_m2l_degree(p, int(max_degree), _d(c), _d(Q), _d(V))
     return V
 
 
@@ -343,6 +349,11 @@ class OracleFMM:
         self._lib.orc_fmm_near_pairs(self._h, out.ctypes.data_as(_lp))
         return out[:k]
 
+    def set_truncation(self, max_degree=None) -> None:
+        """Square truncation (None) or the total-degree bound |n|+|k| <= max_degree."""
+        if self._lib.orc_fmm_set_truncation(self._h, 0 if max_degree is None else int(max_degree)):
+            raise ValueError("truncation bound outside [2, 2p]")
+
     def upward(self) -> None:
         self._lib.orc_fmm_upward(self._h)
 
@@ -375,9 +386,13 @@ class OracleFMM:
         return self._lib.orc_fmm_energy(self._h)
 
 
-def fmm_field(pos, mom, p, theta, leaf_size=0.0, box=None, leaf_mask=None):
-    """Run the whole oracle FMM; returns (H in input order, E, OracleFMM)."""
+def fmm_field(pos, mom, p, theta, leaf_size=0.0, box=None, leaf_mask=None, max_degree=None):
+    """Run the whole oracle FMM; returns (H in input order, E, OracleFMM).
+    ``max_degree``: None for the square truncation of Eq. taylorcalc, else
+    the total-degree bound on |n|+|k|."""
     f = OracleFMM(pos, mom, p, theta, leaf_size, box)
+    if max_degree is not None:
+        f.set_truncation(max_degree)
     f.upward()
     f.downward(leaf_mask)
     return f.field(), f.energy(), f

@@ -22,8 +22,13 @@
  *     the leaf energy against double counting), in units of mu0/4pi.
  *   - "alpha_m == 2r/d" (Sec. II) is read as alpha == 2r/d; a pair is near
  *     when alpha > alpha_m strictly, so alpha == alpha_m is far.
- *   - Truncation of Eq. taylorcalc is "square": every stored Q_k (1<=|k|<=p)
- *     feeds every stored V_n (1<=|n|<=p); V_0 never reaches H and is skipped.
+ *   - Truncation of Eq. taylorcalc is "square" by default: every stored Q_k
+ *     (1<=|k|<=p) feeds every stored V_n (1<=|n|<=p); V_0 never reaches H and
+ *     is skipped.  The error discussion of Sec. II ("terms after the p_m-th
+ *     order") also admits a total-degree reading, kept as an option: the term
+ *     (n, k) is taken only when |n|+|k| <= P for a bound P in [2, 2p]; P = 2p
+ *     is the square truncation and P = p+1 keeps exactly the Taylor polynomial
+ *     of degree p-1 of each far field in (target - source) offsets.
  *   - The tree splits the currently longest axis, ties x<y<z; its depth L
  *     minimises |N / (non-empty leaves) - s| (ties to the smaller L); a point
  *     on a cell boundary belongs to the upper cell.
@@ -313,8 +318,10 @@ void orc_l2l(int p, const double c[3], const double *Vparent, double *Vchild)
 
 /* Eq. taylorcalc: V_n += (-1)^|n| sum_k D_{n+k}(c) Q_k, where c is the
  * centre of this (field) cell relative to the centre of the partner whose
- * moments are Q.  Square truncation: 1<=|n|<=p, 1<=|k|<=p; D to order 2p. */
-static void m2l_one(const ftable *F, int p, const double c[3], const double *Q, double *V, double *Dbuf)
+ * moments are Q.  1<=|n|<=p, 1<=|k|<=p, and the term (n, k) only when
+ * |n|+|k| <= maxdeg (maxdeg = 2p: the square truncation); D to order 2p. */
+static void m2l_one(const ftable *F, int p, int maxdeg, const double c[3], const double *Q,
+                    double *V, double *Dbuf)
 {
     dtensors(F, c, Dbuf);
     int T = orc_nterms(p);
@@ -325,20 +332,27 @@ static void m2l_one(const ftable *F, int p, const double c[3], const double *Q, 
         double s = 0.0;
         for (int u = 1; u < T; ++u) {
             const int *k = &ml->n[3 * u];
+            if (kn + k[0] + k[1] + k[2] > maxdeg) continue;
             s += Dbuf[orc_index(n[0] + k[0], n[1] + k[1], n[2] + k[2])] * Q[u];
         }
         V[t] += ((kn % 2) ? -1.0 : 1.0) * s;
     }
 }
 
-void orc_m2l(int p, const double c[3], const double *Q, double *V)
+/* maxdeg <= 0: the square truncation (2p) */
+void orc_m2l_degree(int p, int maxdeg, const double c[3], const double *Q, double *V)
 {
     ftable F;
     ftable_make(&F, 2 * p);
     double *D = (double *)malloc(sizeof(double) * (size_t)F.T);
-    m2l_one(&F, p, c, Q, V, D);
+    m2l_one(&F, p, maxdeg > 0 ? maxdeg : 2 * p, c, Q, V, D);
     free(D);
     ftable_free(&F);
+}
+
+void orc_m2l(int p, const double c[3], const double *Q, double *V)
+{
+    orc_m2l_degree(p, 2 * p, c, Q, V);
 }
 
 /* Eq. H, with the sign of H = -grad V restored:
@@ -462,6 +476,7 @@ static void ivec_push(ivec *a, i64 x)
 typedef struct orc_fmm {
     i64 n;
     int p;
+    int maxdeg;                 /* M2L terms with |n|+|k| <= maxdeg (2p: square) */
     double theta, leaf_size;
     double *pos, *mom;          /* copies, n x 3 */
     double lo[3], ext[3];
@@ -612,6 +627,7 @@ orc_fmm *orc_fmm_new(i64 n, const double *pos, const double *mom, int p, double 
     orc_fmm *f = (orc_fmm *)calloc(1, sizeof(orc_fmm));
     f->n = n;
     f->p = p;
+    f->maxdeg = 2 * p;
     f->theta = theta;
     f->leaf_size = (leaf_size > 0.0) ? leaf_size : orc_leaf_size_rule(p);
     f->pos = (double *)malloc(sizeof(double) * 3 * (size_t)n);
@@ -727,6 +743,17 @@ void orc_fmm_free(orc_fmm *f)
     free(f->H);
     free(f->have_H);
     free(f);
+}
+
+/* Truncation of Eq. taylorcalc for later downward passes: maxdeg <= 0 is the
+ * square truncation; otherwise the bound P on |n|+|k|, 2 <= P <= 2p.
+ * Returns 0, or -1 (unchanged) for a bound outside that range. */
+int orc_fmm_set_truncation(orc_fmm *f, int maxdeg)
+{
+    if (maxdeg <= 0) maxdeg = 2 * f->p;
+    if (maxdeg < 2 || maxdeg > 2 * f->p) return -1;
+    f->maxdeg = maxdeg;
+    return 0;
 }
 
 int orc_fmm_depth(const orc_fmm *f) { return f->L; }
@@ -867,7 +894,7 @@ void orc_fmm_downward(orc_fmm *f, const unsigned char *leaf_mask)
                 double ca[3], rel[3];
                 cell_center(f, A, ca);
                 for (int a = 0; a < 3; ++a) rel[a] = cen[a] - ca[a];
-                m2l_one(&f->F, f->p, rel, &f->Q[(size_t)A * T], V, Dbuf);
+                m2l_one(&f->F, f->p, f->maxdeg, rel, &f->Q[(size_t)A * T], V, Dbuf);
             }
             free(Dbuf);
         }

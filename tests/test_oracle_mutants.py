@@ -58,6 +58,12 @@ MUTANTS = {
     "m2l_offset_reversed": (
         "for (int a = 0; a < 3; ++a) rel[a] = cen[a] - ca[a];",
         "for (int a = 0; a < 3; ++a) rel[a] = ca[a] - cen[a];"),
+    "degree_bound_off_by_one": (
+        "if (kn + k[0] + k[1] + k[2] > maxdeg) continue;",
+        "if (kn + k[0] + k[1] + k[2] >= maxdeg) continue;"),
+    "fmm_ignores_truncation": (
+        "m2l_one(&f->F, f->p, f->maxdeg, rel,",
+        "m2l_one(&f->F, f->p, 2 * f->p, rel,"),
     "leaf_not_self_near": (
         "ivec_push(&f->nearp[c], c);",
         "(void)0;"),
@@ -80,7 +86,7 @@ PINS = [P.pin_axial_equatorial, P.pin_field_is_minus_grad_potential, P.pin_pair_
         P.pin_p2m_single_dipole, P.pin_p2m_charge_limit, P.pin_multipole_potential,
         P.pin_m2m_exact, P.pin_l2l_l2p, P.pin_l2p_gradient, P.pin_m2l_convergence,
         P.pin_worked_examples, P.pin_eq_so, P.pin_fmm_converges, P.pin_root_moments,
-        _c1_checks]
+        P.pin_total_degree_is_taylor, P.pin_fmm_total_degree_brute_force, _c1_checks]
 
 
 def _run_pins():

@@ -385,6 +385,118 @@ def test_m2l_convergence():
 
 
 # --------------------------------------------------------------------------
+# Total-degree truncation of Eq. taylorcalc (the alternative reading of the
+# "terms after the p_m-th order" of Sec. II)
+# --------------------------------------------------------------------------
+
+def _dipole_field(w, m):
+    """Field of a dipole m at offset w (rows), real or complex w:
+    (3 (m.w) w - m (w.w)) / (w.w)^(5/2)."""
+    ww = (w * w).sum(-1)[..., None]
+    mw = (w * m).sum(-1)[..., None]
+    return (3 * mw * w - m * ww) / ww ** 2.5
+
+
+def _taylor_field(R, z, m, deg, M=64):
+    """Taylor polynomial of degree ``deg`` of H(R + z) in z, evaluated at z,
+    for dipoles m (rows) and offsets z (rows) against one centre offset R.
+    The coefficients of f(t) = H(R + t z) are Cauchy integrals over the unit
+    circle, taken by the trapezoid rule (Lyness & Moler, SIAM J. Numer. Anal.
+    4 (1967) 202); the sum of the first deg+1 of them is the polynomial at
+    t = 1.  With |z| < 0.45 |R|, w.w keeps a positive real part on the
+    circle, so the principal power is analytic there."""
+    z = np.atleast_2d(z)
+    m = np.atleast_2d(m)
+    th = 2 * np.pi * np.arange(M) / M
+    t = np.exp(1j * th)                                           # (M,)
+    w = R[None, None, :] + t[:, None, None] * z[None, :, :]      # (M, n, 3)
+    f = _dipole_field(w, m[None, :, :])
+    j = np.arange(deg + 1)
+    a = np.einsum("mnc,jm->jnc", f, np.exp(-1j * np.outer(j, th))) / M
+    return a.sum(0).real
+
+
+def pin_total_degree_is_taylor():
+    """One source dipole at c_s + y, one target at c_t + x, R = c_t - c_s:
+    P2M, M2L with the terms |n|+|k| <= P (2 <= P <= p+1), then L2P give the
+    Taylor polynomial of degree P-2 of the dipole field H(R + z) in
+    z = x - y (the multinomial theorem regroups the double series of Eq.
+    taylorcalc by |n|+|k|).  The square truncation is not that polynomial,
+    so the check tells the two readings apart."""
+    rng = _rng(41)
+    R = np.array([4.0, -2.5, 3.0])
+    worst, gap = 0.0, np.inf
+    for p in (2, 3, 4, 6):
+        for P in range(2, p + 2):
+            y = rng.uniform(-0.5, 0.5, 3)
+            x = rng.uniform(-0.5, 0.5, 3)
+            m = W.unit_vectors(1, rng)[0]
+            Q = O.p2m(p, [0.0, 0.0, 0.0], y[None], m[None])
+            H = O.l2p(p, x, O.m2l(p, R, Q, max_degree=P))
+            T = _taylor_field(R, x - y, m, P - 2)[0]
+            worst = max(worst, np.abs(H - T).max() / np.linalg.norm(T))
+            if P == p + 1:
+                Hs = O.l2p(p, x, O.m2l(p, R, Q))
+                gap = min(gap, np.abs(Hs - T).max() / np.linalg.norm(T))
+    return worst < 1e-12 and gap > 1e-8
+
+
+def pin_fmm_total_degree_brute_force():
+    """The whole FMM with the total-degree bound P = p+1 at a sample of
+    targets equals, to rounding, the brute-force sum over the oracle's lists:
+    the exact field of every source in the target leaf's Near leaves, plus,
+    for every ancestor cell c of the target leaf (the leaf included) and every
+    Far partner A of c, the Taylor polynomial of degree p-1 of each source's
+    field about R = c - A (centres).  M2M and L2L are exact, so every far
+    interaction reaches the target as that polynomial."""
+    pos, mom, box = W.lattice(7, seed=77)
+    p, P = 4, 5
+    f = O.OracleFMM(pos, mom, p, 0.5, 4.0, box=box)
+    f.set_truncation(P)
+    f.upward()
+    f.downward()
+    H = f.field()
+    L = f.depth
+    heap = (1 << L) + f.leaf_of()
+    far, near = f.far_pairs(), f.near_pairs()
+    rng = _rng(42)
+    worst = 0.0
+    for i in rng.choice(len(pos), 12, replace=False):
+        h = np.zeros(3)
+        for a in near[near[:, 0] == heap[i], 1]:
+            js = np.flatnonzero((heap == a) & (np.arange(len(pos)) != i))
+            h += _dipole_field(pos[i] - pos[js], mom[js]).sum(0)
+        for l in range(L + 1):
+            c = heap[i] >> (L - l)
+            cc = f.cell_center(c)
+            for a in far[far[:, 0] == c, 1]:
+                js = np.flatnonzero((heap >> (L - l)) == a)
+                ca = f.cell_center(a)
+                z = (pos[i] - cc)[None, :] - (pos[js] - ca)
+                h += _taylor_field(cc - ca, z, mom[js], P - 2).sum(0)
+        worst = max(worst, np.linalg.norm(H[i] - h) / np.linalg.norm(h))
+    return worst < 1e-11
+
+
+def test_total_degree_is_taylor():
+    assert pin_total_degree_is_taylor()
+
+
+def test_fmm_total_degree_brute_force():
+    assert pin_fmm_total_degree_brute_force()
+
+
+def test_truncation_bounds():
+    pos, mom, box = W.lattice(4)
+    f = O.OracleFMM(pos, mom, 3, 0.5, 4.0, box=box)
+    for bad in (1, 7):
+        with pytest.raises(ValueError):
+            f.set_truncation(bad)
+    f.set_truncation(6)   # 2p: the square truncation
+    f.set_truncation(None)
+
+
+# --------------------------------------------------------------------------
 # Tree and rule of thumb (Sec. II, Sec. IV, Eq. so, Tables I and II)
 # --------------------------------------------------------------------------
 
