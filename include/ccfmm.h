@@ -124,6 +124,24 @@ ccfmm_status fmm_set_positions(ccfmm_t h, const double *positions, const double 
 /* Replace the moments; the tree and lists are kept (positions unchanged). */
 ccfmm_status fmm_set_moments(ccfmm_t h, const double *moments);
 
+/* Truncation of the far-field series of Eq. taylorcalc (Sec. II, the error
+ * estimate "after the p-th order").  max_degree <= 0 selects the default
+ * square truncation: every stored Q_k (1 <= |k| <= p) feeds every stored V_n
+ * (1 <= |n| <= p).  Otherwise only the terms with |n| + |k| <= max_degree
+ * are kept, 2 <= max_degree <= 2p.  2p is the square truncation again.
+ * max_degree = p + 1 makes every far interaction the Taylor polynomial of
+ * degree p - 1 of the dipole field in the target-source offset.  It applies
+ * to every later evaluation, on all M2L engines.  The FMA engines (FP64,
+ * and FP32 under CCFMM_M2L=fma) skip the dropped terms.  The tensor-core
+ * engine multiplies zero operands in their place, so its cost is unchanged.
+ * Errors: CCFMM_ERR_ARG for a bound outside that range; CCFMM_ERR_STATE for
+ * a handle owned by an ensemble (fmm_batch_sample), which keeps the square
+ * truncation.  Asynchronous on the handle's stream, like fmm_set_positions. */
+ccfmm_status fmm_set_truncation(ccfmm_t h, int max_degree);
+
+/* The handle's current bound on |n| + |k| (2p for the square truncation). */
+ccfmm_status fmm_get_truncation(ccfmm_t h, int *max_degree);
+
 /* Evaluate the field at every dipole: upward pass (Eqs. multipolemoments,
  * momentshift), downward pass (Eqs. taylorcalc, taylorshift), smooth field
  * (Eq. H) and near field (Eq. H2).  H_out: N x 3 float64 in input order,

@@ -68,6 +68,8 @@ def load():
                                      ctypes.POINTER(_vp)]),
             "fmm_set_positions": (_int, [_vp, _vp, _vp]),
             "fmm_set_moments": (_int, [_vp, _vp]),
+            "fmm_set_truncation": (_int, [_vp, _int]),
+            "fmm_get_truncation": (_int, [_vp, ctypes.POINTER(_int)]),
             "fmm_field": (_int, [_vp, _vp]),
             "fmm_field_energy": (_int, [_vp, _vp, ctypes.POINTER(_dbl)]),
             "fmm_energy": (_int, [_vp, ctypes.POINTER(_dbl)]),
@@ -225,6 +227,17 @@ class FMM:
     def set_moments(self, moments):
         pm, k = _ptr(moments, 3 * self.n)
         _check(self._lib.fmm_set_moments(self._h, pm))
+
+    def set_truncation(self, max_degree=None):
+        """fmm_set_truncation: None for the square truncation of Eq.
+        taylorcalc, else keep the terms with |n|+|k| <= max_degree."""
+        _check(self._lib.fmm_set_truncation(self._h, 0 if max_degree is None else int(max_degree)))
+
+    @property
+    def max_degree(self) -> int:
+        v = _int()
+        _check(self._lib.fmm_get_truncation(self._h, ctypes.byref(v)))
+        return int(v.value)
 
     def field(self, out=None):
         """H at every dipole, input order (N x 3 float64)."""

@@ -144,6 +144,7 @@ struct ccfmm_s {
     bool has_box = false;
     double box_user[6] = {0, 0, 0, 0, 0, 0};
     int K = 0, KP = 0, TD = 0, ldD = 0;
+    int maxdeg = 0;  // M2L terms with |n|+|k| <= maxdeg (2p: square truncation)
     size_t rsz = 4;  // sizeof(real)
 
     Geom geom;
@@ -676,7 +677,7 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
         launch_ftable(O, P<double>(h->fdense), P<int>(h->fst), P<uint16_t>(h->fq),
                       P<double>(h->fval), s);
         TRY(ensure(h->itab, sizeof(uint16_t) * h->KP * h->KP));
-        launch_itable(h->p, h->KP, P<uint16_t>(h->itab), s);
+        launch_itable(h->p, h->KP, h->maxdeg, P<uint16_t>(h->itab), s);
         h->ftable_ready = true;
     }
     TRY(ensure(h->D, rs * (size_t)std::max(h->n_d, 1) * h->ldD));
@@ -807,11 +808,11 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
     else if (sizeof(real) == 4 && m2l_f32_supported(KP, h->ldD))
         launch_m2l_f32(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
                        P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
-                       P<float>(h->Q), P<float>(h->D), h->ldD, P<uint16_t>(h->itab),
+                       P<float>(h->Q), P<float>(h->D), h->ldD, P<uint16_t>(h->itab), h->maxdeg,
                        P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V), sf);
     else
         launch_m2l<real>(p, KP, P<Tile>(h->tiles), h->ntiles, P<int>(h->ent_u), P<int>(h->ent_src),
-                         P<real>(h->Q), P<real>(h->D), h->ldD, P<uint16_t>(h->itab),
+                         P<real>(h->Q), P<real>(h->D), h->ldD, P<uint16_t>(h->itab), h->maxdeg,
                          P<Geom>(h->geomd), P<double>(h->V), sf);
     if (ev) CK(cudaEventRecord(evs[EV_M2L], sf));
     for (int l = 2; l <= L; ++l)
@@ -921,6 +922,7 @@ ccfmm_status fmm_create_ex(const double *positions, const double *moments, int64
     h->rsz = prec == CCFMM_MIXED ? 4 : 8;
     h->K = nterms(p) - 1;
     h->KP = padded_k(p);
+    h->maxdeg = 2 * p;
     if (box) {
         h->has_box = true;
         memcpy(h->box_user, box, sizeof(h->box_user));
@@ -988,6 +990,34 @@ ccfmm_status fmm_set_moments(ccfmm_t h, const double *moments)
     flags = h->hrb->flags;
     h->evaluated = false;
     return check_flags(h, flags);
+}
+
+ccfmm_status fmm_set_truncation(ccfmm_t h, int max_degree)
+{
+    g_err.clear();
+    if (!h) return fail(CCFMM_ERR_ARG, "handle is NULL");
+    if (h->quiet) return fail(CCFMM_ERR_STATE, "ensemble members keep the square truncation");
+    const int bound = max_degree <= 0 ? 2 * h->p : max_degree;
+    if (bound < 2 || bound > 2 * h->p)
+        return fail(CCFMM_ERR_ARG, "max_degree = %d outside 2..%d", max_degree, 2 * h->p);
+    if (bound == h->maxdeg) return CCFMM_OK;
+    CK(cudaSetDevice(h->device));
+    h->maxdeg = bound;
+    if (h->ftable_ready) {
+        launch_itable(h->p, h->KP, h->maxdeg, P<uint16_t>(h->itab), h->stream);
+        KCHECK();
+    }
+    h->tc_ops_ready = false;  // the tensor-core operators read the index table
+    h->evaluated = false;
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_get_truncation(ccfmm_t h, int *max_degree)
+{
+    g_err.clear();
+    if (!h || !max_degree) return fail(CCFMM_ERR_ARG, "handle or output is NULL");
+    *max_degree = h->maxdeg;
+    return CCFMM_OK;
 }
 
 ccfmm_status fmm_field(ccfmm_t h, double *H_out)

@@ -41,6 +41,20 @@ __host__ __device__ inline void midx_inv(int t, int &nx, int &ny, int &nz)
     nx = k - ny - nz;
 }
 inline int padded_k(int p) { return ((nterms(p) - 1 + 7) / 8) * 8; }
+// M2L truncation: the term (n, k) of Eq. taylorcalc is kept when
+// |n|+|k| <= maxdeg (2p: every stored pair, the square truncation).  The
+// coefficient columns are ordered by degree, so the columns k that can meet
+// column n form a prefix; its length, 0 for padding columns n >= K.
+__host__ __device__ inline int m2l_kend(int p, int maxdeg, int n)
+{
+    const int K = nterms(p) - 1;
+    if (n >= K) return 0;
+    int d = 1;
+    while (nterms(d) <= n + 1) ++d;  // degree of multi-index n + 1
+    const int r = maxdeg - d;
+    if (r < 1) return 0;
+    return r >= p ? K : nterms(r) - 1;
+}
 
 template <typename T> struct vec4;
 template <> struct vec4<float> { typedef float4 t; };
@@ -170,7 +184,7 @@ template <typename real>
 // one D table per scaled separation sep[i] = (c_x, c_y, c_z) / h
 void launch_dtables(int p, const int *f_start, const uint16_t *f_q, const double *f_val,
                     const double4 *sep, int nd, real *D, int ldD, cudaStream_t s);
-void launch_itable(int p, int KP, uint16_t *it, cudaStream_t s);
+void launch_itable(int p, int KP, int maxdeg, uint16_t *it, cudaStream_t s);
 template <typename real>
 void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, real *Q, cudaStream_t s);
@@ -190,7 +204,8 @@ bool m2l_f32_supported(int KP, int ldD);
 void launch_m2l_f32(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items,
                     int nitems, const int *tile_item0, const int *tile_nitems, const int *ent_u,
                     const int *ent_src, const float *Q, const float *D, int ldD,
-                    const uint16_t *it, const Geom *g, float *Ps, double *V, cudaStream_t s);
+                    const uint16_t *it, int maxdeg, const Geom *g, float *Ps, double *V,
+                    cudaStream_t s);
 void launch_m2l_reduce(int p, int KP, const Tile *tiles, int ntiles, const int *tile_item0,
                        const int *tile_nitems, const float *Ps, const Geom *g, double *V,
                        cudaStream_t s);
@@ -209,7 +224,7 @@ void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *
 template <typename real>
 void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
                 const int *ent_src, const real *Q, const real *D, int ldD, const uint16_t *it,
-                const Geom *d_geom, double *V, cudaStream_t s);
+                int maxdeg, const Geom *d_geom, double *V, cudaStream_t s);
 
 // ------------------------------------------------------------------ p2p.cu
 template <typename real>

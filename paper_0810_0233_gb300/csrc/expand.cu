@@ -180,15 +180,16 @@ void launch_dtables(int p, const int *f_start, const uint16_t *f_q, const double
 }
 
 // M2L index table: it[k][n] = D-row column of multi-index (n + k) for
-// coefficient columns n, k < K; the zero column T(2p) for padding.
-__global__ void k_itable(int p, int KP, uint16_t *it)
+// coefficient columns n, k < K with |n|+|k| <= maxdeg; the zero column T(2p)
+// for padding and for the pairs that the truncation drops.
+__global__ void k_itable(int p, int KP, int maxdeg, uint16_t *it)
 {
     int K = nterms(p) - 1, zero = nterms(2 * p);
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= KP * KP) return;
     int ck = j / KP, cn = j % KP;
     int v = zero;
-    if (ck < K && cn < K) {
+    if (ck < K && cn < K && ck < m2l_kend(p, maxdeg, cn)) {
         int ax, ay, az, bx, by, bz;
         midx_inv(ck + 1, ax, ay, az);
         midx_inv(cn + 1, bx, by, bz);
@@ -197,10 +198,10 @@ __global__ void k_itable(int p, int KP, uint16_t *it)
     it[j] = (uint16_t)v;
 }
 
-void launch_itable(int p, int KP, uint16_t *it, cudaStream_t s)
+void launch_itable(int p, int KP, int maxdeg, uint16_t *it, cudaStream_t s)
 {
     note_launch();
-    k_itable<<<(KP * KP + 255) / 256, 256, 0, s>>>(p, KP, it);
+    k_itable<<<(KP * KP + 255) / 256, 256, 0, s>>>(p, KP, maxdeg, it);
 }
 
 // ---------------------------------------------------------------------------

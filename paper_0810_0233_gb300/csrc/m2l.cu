@@ -1,7 +1,9 @@
 // m2l.cu -- M2L (Eq. taylorcalc) as offset-grouped dense contractions.
 //
 // V_n = (-1)^|n| sum_k D_{n+k}(c) Q_k, c = field-cell centre - partner centre,
-// square truncation 1 <= |n|, |k| <= p.  All cells of a level are congruent,
+// 1 <= |n|, |k| <= p: the square truncation, or, on request, only the terms
+// with |n|+|k| <= maxdeg (the index table maps the dropped pairs to a zero
+// column, and each warp stops at the last moment column its rows can meet).  All cells of a level are congruent,
 // so c = o * w_l for an integer offset o and D depends only on (level, o).
 // A tile holds up to TT field cells of one level and one parity (keys
 // 2(first+i)+parity); for every far offset present among them the tile has
@@ -38,8 +40,8 @@ template <> struct v4<double> {
 template <typename real, int KP, int KC>
 __global__ void __launch_bounds__(KP * 4) k_m2l(int p, const Tile *tiles, const int *ent_u,
                                                 const int *ent_src, const real *Q, const real *D,
-                                                int ldD, const uint16_t *it, const Geom *g,
-                                                double *V)
+                                                int ldD, const uint16_t *it, int maxdeg,
+                                                const Geom *g, double *V)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     real *Qs = reinterpret_cast<real *>(smraw);            // [KC][TT]
@@ -51,6 +53,8 @@ __global__ void __launch_bounds__(KP * 4) k_m2l(int p, const Tile *tiles, const 
 
     const int K = nterms(p) - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // moment columns this warp's rows 8w.. can meet (warp-uniform)
+    const int kend = m2l_kend(p, maxdeg, 8 * warp);
     const Tile t = tiles[blockIdx.x];
     const double h = g->h[t.level];
     for (int c = tid; c < KP; c += blockDim.x) {
@@ -95,8 +99,9 @@ __global__ void __launch_bounds__(KP * 4) k_m2l(int p, const Tile *tiles, const 
                 Ms[idx] = Dl[it[(k0 + kk) * KP + n]];
             }
             __syncthreads();
+            const int kc = min(KC, kend - k0);
 #pragma unroll 4
-            for (int kk = 0; kk < KC; ++kk) {
+            for (int kk = 0; kk < kc; ++kk) {
                 real q[4], m0[4], m1[4];
                 v4<real>::ld(Qs + kk * TT + 4 * lane, q);
                 v4<real>::ld(Ms + kk * KP + 8 * warp, m0);
@@ -153,8 +158,8 @@ template <int KP>
 __global__ void __launch_bounds__(KP * 4) k_m2l_f32(int p, const Tile *tiles, const M2LItem *items,
                                                     const int *ent_u, const int *ent_src,
                                                     const float *Q, const float *D, int ldD,
-                                                    const uint16_t *it_g, const Geom *g,
-                                                    float *Ps)
+                                                    const uint16_t *it_g, int maxdeg,
+                                                    const Geom *g, float *Ps)
 {
     constexpr int RS = KP + 4;               // Qr row stride (floats)
     constexpr int NT = KP * 4;               // threads
@@ -170,6 +175,8 @@ __global__ void __launch_bounds__(KP * 4) k_m2l_f32(int p, const Tile *tiles, co
     const M2LItem item = items[blockIdx.x];
     const Tile t = tiles[item.tile];
     const int K = nterms(p) - 1;
+    // moment columns this warp's rows 8w.. can meet, in whole float4 steps
+    const int kend4 = min(KP, (m2l_kend(p, maxdeg, 8 * warp) + 3) & ~3);
     const double h = g->h[t.level];
     for (int c = tid; c < KP; c += NT) {
         double gv = 0.0;
@@ -222,7 +229,7 @@ __global__ void __launch_bounds__(KP * 4) k_m2l_f32(int p, const Tile *tiles, co
         __syncthreads();
         const float *q0 = Qr + buf * TT * RS + lane * RS;
 #pragma unroll 2
-        for (int k4 = 0; k4 < KP; k4 += 4) {
+        for (int k4 = 0; k4 < kend4; k4 += 4) {
             float4 qv[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) qv[i] = *reinterpret_cast<const float4 *>(q0 + 32 * i * RS + k4);
@@ -295,7 +302,8 @@ bool m2l_f32_supported(int KP, int ldD)
 void launch_m2l_f32(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items,
                     int nitems, const int *tile_item0, const int *tile_nitems, const int *ent_u,
                     const int *ent_src, const float *Q, const float *D, int ldD,
-                    const uint16_t *it, const Geom *g, float *Ps, double *V, cudaStream_t s)
+                    const uint16_t *it, int maxdeg, const Geom *g, float *Ps, double *V,
+                    cudaStream_t s)
 {
     if (nitems > 0) {
         size_t smem = m2l_f32_smem(KP, ldD);
@@ -305,7 +313,7 @@ void launch_m2l_f32(int p, int KP, const Tile *tiles, int ntiles, const M2LItem 
                              (int)smem);                                                        \
         note_launch();                                                                          \
         k_m2l_f32<KPV><<<nitems, KPV * 4, smem, s>>>(p, tiles, items, ent_u, ent_src, Q, D,    \
-                                                     ldD, it, g, Ps);                           \
+                                                     ldD, it, maxdeg, g, Ps);                   \
         break;
         switch (KP) {
             M2LF(8) M2LF(16) M2LF(24) M2LF(40) M2LF(56) M2LF(88) M2LF(120)
@@ -328,48 +336,48 @@ void launch_m2l_reduce(int p, int KP, const Tile *tiles, int ntiles, const int *
 
 template <typename real, int KP, int KC>
 static void run_m2l(int p, const Tile *tiles, int ntiles, const int *ent_u, const int *ent_src,
-                    const real *Q, const real *D, int ldD, const uint16_t *it, const Geom *g,
-                    double *V, cudaStream_t s)
+                    const real *Q, const real *D, int ldD, const uint16_t *it, int maxdeg,
+                    const Geom *g, double *V, cudaStream_t s)
 {
     size_t smem = sizeof(real) * ((size_t)KC * TT + (size_t)KC * KP + ldD + KP + (KP & 1)) +
                   sizeof(double) * KP + sizeof(int) * TT + 64;
     auto kern = k_m2l<real, KP, KC>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
-    kern<<<ntiles, KP * 4, smem, s>>>(p, tiles, ent_u, ent_src, Q, D, ldD, it, g, V);
+    kern<<<ntiles, KP * 4, smem, s>>>(p, tiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, g, V);
 }
 
 template <typename real>
 void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
                 const int *ent_src, const real *Q, const real *D, int ldD, const uint16_t *it,
-                const Geom *d_geom, double *V, cudaStream_t s)
+                int maxdeg, const Geom *d_geom, double *V, cudaStream_t s)
 {
     if (ntiles <= 0) return;
     const bool dbl = sizeof(real) == 8;
     switch (KP) {
-    case 8: run_m2l<real, 8, 8>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s); break;
-    case 16: run_m2l<real, 16, 16>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s); break;
-    case 24: run_m2l<real, 24, 24>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s); break;
-    case 40: run_m2l<real, 40, 40>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s); break;
-    case 56: run_m2l<real, 56, 56>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s); break;
-    case 88: run_m2l<real, 88, 88>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s); break;
+    case 8: run_m2l<real, 8, 8>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s); break;
+    case 16: run_m2l<real, 16, 16>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s); break;
+    case 24: run_m2l<real, 24, 24>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s); break;
+    case 40: run_m2l<real, 40, 40>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s); break;
+    case 56: run_m2l<real, 56, 56>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s); break;
+    case 88: run_m2l<real, 88, 88>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s); break;
     case 120:
-        if (dbl) run_m2l<real, 120, 40>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s);
-        else run_m2l<real, 120, 120>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s);
+        if (dbl) run_m2l<real, 120, 40>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s);
+        else run_m2l<real, 120, 120>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s);
         break;
     case 168:
-        if (dbl) run_m2l<real, 168, 56>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s);
-        else run_m2l<real, 168, 168>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, d_geom, V, s);
+        if (dbl) run_m2l<real, 168, 56>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s);
+        else run_m2l<real, 168, 168>(p, tiles, ntiles, ent_u, ent_src, Q, D, ldD, it, maxdeg, d_geom, V, s);
         break;
     default: break;
     }
 }
 
 template void launch_m2l<float>(int, int, const Tile *, int, const int *, const int *,
-                                const float *, const float *, int, const uint16_t *, const Geom *,
+                                const float *, const float *, int, const uint16_t *, int, const Geom *,
                                 double *, cudaStream_t);
 template void launch_m2l<double>(int, int, const Tile *, int, const int *, const int *,
                                  const double *, const double *, int, const uint16_t *,
-                                 const Geom *, double *, cudaStream_t);
+                                 int, const Geom *, double *, cudaStream_t);
 
 }  // namespace ccfmm

@@ -11,6 +11,10 @@
   every order p with the alpha that meets e, timed on the 32^3 lattice with
   the measured field and energy errors against the direct sum (Table II and
   the optimal-time-versus-accuracy curve of Fig. 3).
+* truncation(): the square truncation of Eq. taylorcalc against the
+  total-degree one (terms |n|+|k| <= p+1) on the ferrofluid workload: field
+  error against the direct sum, evaluation time, and the M2L stage time of
+  the tensor-core and the FP32 FMA engines.
 
 Times are CUDA-event times of the library's own call sequence (tree, lists
 and D tables, then the field) on the current device, best of `repeats`.  The
@@ -172,20 +176,66 @@ def error_budget(n=32, es=(0.05, 0.01, 1e-3, 2e-4), ps=(2, 3, 4, 5, 6, 7, 8), se
     return {"rows": rows, "fastest": best}
 
 
+def truncation(n=1_000_000, ps=(4, 5, 6, 7), theta=0.5, nsub=10_000, evals=10, seed=5):
+    """Square against total-degree truncation on the ferrofluid (one dipole
+    per unit volume, minimum separation 0.5), mixed precision."""
+    import os
+    import torch
+    pos, mom = W.ferrofluid(n, side=n ** (1.0 / 3.0), seed=810233 + 50 + seed)
+    stream = torch.cuda.current_stream()
+    pd = torch.from_numpy(pos).cuda()
+    md = torch.from_numpy(mom).cuda()
+    sub = np.random.default_rng(seed).choice(n, min(nsub, n), replace=False)
+    Hd = C.direct_field(pd, md, targets=torch.from_numpy(sub).cuda(), stream=stream)
+    H = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    saved = os.environ.get("CCFMM_M2L")
+    rows = []
+    try:
+        for p in ps:
+            for bound in (None, p + 1):
+                row = {"p": p, "max_degree": 2 * p if bound is None else bound,
+                       "truncation": "square" if bound is None else "total degree"}
+                for eng in ("tc", "fma"):
+                    os.environ["CCFMM_M2L"] = eng
+                    with C.FMM(pd, md, p, theta, stream=stream) as f:
+                        f.set_truncation(bound)
+                        f.field(H)
+                        if eng == "tc":
+                            Hf = H.cpu().numpy()[sub]
+                            row["rms_field_error"] = float(
+                                np.sqrt(((Hf - Hd) ** 2).sum() / (Hd ** 2).sum()))
+                        f.reset_stats()
+                        for _ in range(evals):
+                            f.evaluate()
+                        torch.cuda.synchronize()
+                        st = f.stats()
+                    row["%s_eval_ms" % eng] = st["ms_eval"]
+                    row["%s_m2l_ms" % eng] = st["ms_stage"][2]
+                rows.append(row)
+    finally:
+        if saved is None:
+            os.environ.pop("CCFMM_M2L", None)
+        else:
+            os.environ["CCFMM_M2L"] = saved
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="fewer sizes (smoke run)")
     ap.add_argument("--part", default="all",
-                    choices=["all", "scaling", "leaf_sweep", "optimal_leaf", "error_budget"])
+                    choices=["all", "scaling", "leaf_sweep", "optimal_leaf", "error_budget",
+                             "truncation"])
     ap.add_argument("--out", default="experiments.json")
     args = ap.parse_args()
     t0 = time.time()
     quick = {"scaling": dict(sizes=(8, 16, 32), params=((4, 0.5),)),
              "leaf_sweep": dict(leaves=(4, 8, 16)),
              "optimal_leaf": dict(ps=(3, 5), sizes=(30, 31)),
-             "error_budget": dict(n=16, es=(0.05,), ps=(3, 5))}
+             "error_budget": dict(n=16, es=(0.05,), ps=(3, 5)),
+             "truncation": dict(n=100_000, ps=(4, 6), evals=3)}
     parts = {"scaling": scaling, "leaf_sweep": leaf_sweep, "optimal_leaf": optimal_leaf,
-             "error_budget": error_budget}
+             "error_budget": error_budget, "truncation": truncation}
     res = {}
     for name, fn in parts.items():
         if args.part not in ("all", name):

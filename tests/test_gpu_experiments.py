@@ -40,3 +40,14 @@ def test_error_budget_small():
         assert r["rms_field_error"] < 0.05
         assert r["energy_error"] < 0.01
     assert res["fastest"][0.05]["p"] in (3, 5)
+
+
+def test_truncation_small():
+    rows = X.truncation(n=20_000, ps=(4,), evals=2)
+    assert [(r["p"], r["max_degree"]) for r in rows] == [(4, 8), (4, 5)]
+    sq, td = rows
+    for r in rows:
+        assert 0.0 < r["rms_field_error"] < 5e-2
+        assert r["tc_eval_ms"] > 0 and r["fma_m2l_ms"] > 0
+    # fewer far-field terms cannot make the field markedly more accurate
+    assert td["rms_field_error"] > 0.5 * sq["rms_field_error"]
