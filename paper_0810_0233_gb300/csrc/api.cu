@@ -169,6 +169,11 @@ struct ccfmm_s {
     DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
     DevBuf Hout, epart, items, titem0, tnitems, Ps;
     DevBuf Qs, Bop, gkt;  // tensor-core M2L: split moments, operators, level scales
+    // tensor map of Qs for the TMA row gather, encoded for (qmap_for, qmap_ncell)
+    alignas(64) unsigned char qmap[128];
+    const void *qmap_for = nullptr;
+    long long qmap_ncell = 0;
+    bool qmap_ok = false;
     DevBuf dmap, dsep;    // far offset class -> D table; scaled separation of each D table
     // host sources of the build's asynchronous uploads, kept until the next
     // build (which starts after the previous one has synchronised)
@@ -717,6 +722,17 @@ static bool m2l_use_tc(ccfmm_t h)
     return M2L_TC_DEFAULT;
 }
 
+// Row gather of the tensor-core M2L: TMA tile::gather4 copies, or cp.async
+// by eight producer warps (CCFMM_TC_GATHER=tma|cp overrides the default).
+constexpr bool TC_GATHER_TMA_DEFAULT = false;
+static bool tc_gather_tma()
+{
+    const char *e = getenv("CCFMM_TC_GATHER");
+    if (e && !strcmp(e, "cp")) return false;
+    if (e && !strcmp(e, "tma")) return true;
+    return TC_GATHER_TMA_DEFAULT;
+}
+
 // Buffers and operators of the tensor-core M2L for the current tree, built
 // on the handle's stream at the first evaluation after a build (ensemble
 // members: before their evaluation is captured).
@@ -725,6 +741,13 @@ static ccfmm_status tc_prepare(ccfmm_t h)
     const int KT = m2l_tc_kt(h->KP);
     const long long ncellp = 1ll << (h->L + 1);
     TRY(ensure(h->Qs, sizeof(float) * 2 * (size_t)ncellp * KT));
+    if (tc_gather_tma() && (h->qmap_for != h->Qs.p || h->qmap_ncell != ncellp)) {
+        // host-side encoding; a map the driver cannot make leaves the
+        // cp.async gather in use
+        h->qmap_ok = m2l_tc_qmap(h->qmap, P<float>(h->Qs), ncellp, h->KP);
+        h->qmap_for = h->Qs.p;
+        h->qmap_ncell = ncellp;
+    }
     if (!h->tc_ops_ready) {
         TRY(ensure(h->Bop, m2l_tc_op_bytes(h->KP) * (size_t)std::max(h->n_d, 1)));
         TRY(ensure(h->gkt, sizeof(float) * (size_t)(LCAP + 1) * KT));
@@ -803,6 +826,7 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
         launch_m2l_tc(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
                       P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
                       P<float>(h->Q), ncellp, P<float>(h->gkt), P<float>(h->Qs),
+                      (tc_gather_tma() && h->qmap_ok && h->qmap_for == h->Qs.p) ? h->qmap : nullptr,
                       P<float>(h->Bop), P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V),
                       &P<Readback>(h->rb)->eflags, sf);
     else if (sizeof(real) == 4 && m2l_f32_supported(KP, h->ldD))

@@ -216,11 +216,14 @@ size_t m2l_tc_op_bytes(int KP);  // operator bytes per far offset class
 int m2l_tc_kt(int KP);           // padded K (row length of the split moments)
 void launch_m2l_tc_ops(int p, int KP, int L, int n_off, const Geom *g, const float *D, int ldD,
                        const uint16_t *it, float *gk, float *Bop, cudaStream_t s);
+// tensor map of the split moments for the TMA gather (map: 128 bytes,
+// 64-byte aligned); false when the driver cannot encode it
+bool m2l_tc_qmap(void *map, const float *Qs, long long ncell, int KP);
 void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items, int nitems,
                    const int *tile_item0, const int *tile_nitems, const int *ent_u,
                    const int *ent_src, const float *Q, long long ncell, const float *gk,
-                   float *Qs, const float *Bop, const Geom *g, float *Ps, double *V, int *flags,
-                   cudaStream_t s);
+                   float *Qs, const void *qmap, const float *Bop, const Geom *g, float *Ps,
+                   double *V, int *flags, cudaStream_t s);
 template <typename real>
 void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
                 const int *ent_src, const real *Q, const real *D, int ldD, const uint16_t *it,

@@ -28,14 +28,22 @@
 // are 1024-byte aligned; a k-step of 8 advances the start address by 32 B.
 //
 // Pipeline, 3 or 4 stages (as many as fit) of one unit = (entry, 32-wide K
-// chunk) each:
-//   producers  (4 or 8 warps) wait for the stage to be free, gather the 128
-//              partner rows of the chunk (cp.async, hi and lo; zero rows for
-//              cells without that partner), and thread 0 starts the bulk
-//              copy of the operator chunk.  stages - 1 units later, before
-//              waiting for the next free stage, each warp marks the unit's
-//              stage full once its own copies have landed (one arrival per
-//              warp);
+// chunk) each.  Two ways to fill a stage:
+//   TMA gather (default)  producer warp 0 alone: lane 0 posts the stage's
+//              byte count on its barrier and starts the bulk copy of the
+//              operator chunk; every lane gathers its 4 partner rows of the
+//              hi and the lo plane with one tile::gather4 tensor copy each
+//              (a 128-byte row per cell, written in the 128-byte-swizzled
+//              layout by the copy engine; cells without that partner read
+//              row 0, which holds zeros).  The barrier completes when all
+//              bytes have landed, so all stages can be in flight;
+//   cp.async gather  (CCFMM_TC_GATHER=cp) producers (4 or 8 warps) wait for
+//              the stage to be free, gather the 128 partner rows of the
+//              chunk (cp.async, hi and lo; zero rows for cells without that
+//              partner), and thread 0 starts the bulk copy of the operator
+//              chunk.  stages - 1 units later, before waiting for the next
+//              free stage, each warp marks the unit's stage full once its
+//              own copies have landed (one arrival per warp);
 //   last warp  one thread issues the unit's 8 MMAs once the rows and the
 //              operator chunk have landed and frees the stage with
 //              tcgen05.commit;
@@ -47,7 +55,10 @@
 // returns.
 #include "ccfmm_dev.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <stdlib.h>
+#include <string.h>
 
 namespace ccfmm {
 
@@ -176,6 +187,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         : "memory");
 }
 
+// four 128-byte rows (x = first column, rows r.x .. r.w) of a 2-D tensor
+// into 512 consecutive bytes of shared memory, swizzled as the map says
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void *map, int x, int4 r,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(map), "r"(x), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t acc)
 {
@@ -248,7 +271,8 @@ __global__ void k_q_split(int p, long long ncell, const float *Q, const float *g
     const int k4 = (int)(i - hid * (KT / 4)) * 4;
     const int level = hid > 0 ? 63 - __clzll(hid) : 0;
     float v[4] = {0.f, 0.f, 0.f, 0.f};
-    if (k4 < KP) {
+    // heap id 0 is no cell: its row stays zero (the gather's empty partner)
+    if (k4 < KP && hid > 0) {
         const float4 q = *reinterpret_cast<const float4 *>(Q + hid * KP + k4);
         const float4 g = *reinterpret_cast<const float4 *>(gk + level * KT + k4);
         v[0] = q.x * g.x;
@@ -281,11 +305,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 }
 
 // ------------------------------------------------------------ contraction
-template <int KP>
+template <int KP, bool TMA>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_m2l_tc(const M2LItem *items, const int *ent_u, const int *ent_src, const float *Qs,
-             long long qplane, const unsigned char *Bop, float *Ps, int *flags, long long spin,
-             int stall)
+             long long qplane, const __grid_constant__ CUtensorMap qmap, int ncell,
+             const unsigned char *Bop, float *Ps, int *flags, long long spin, int stall)
 {
     typedef TcShape<KP> S;
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -326,81 +350,131 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp < MMA_WARP) {
-        // ---------------- producers: a warp instruction copies 4 whole unit
-        // rows (128 B each, one global line and one shared line): lane ->
-        // (row r = 4 (warp + NW m) + lane / 8, 16-byte chunk j = lane mod 8)
-        constexpr int NW = TC_PROD / 32, MR = 32 / NW;
-        const int j = lane & 7, rq = lane >> 3;
-        const uint32_t dst0 = sw128(4 * warp + rq, j);  // + m NW/2 atoms
-        auto rowof = [&](int m) { return 4 * (warp + NW * m) + rq; };
-        // partner rows and operator class of the current entry, and of the
-        // next one, loaded an entry ahead so that no gather waits on them
-        int src[MR], srcn[MR], gid = 0, gidn = 0;
-        if (ne > 0) {
-            const int *sr = ent_src + (long long)item.e0 * TT;
-#pragma unroll
-            for (int m = 0; m < MR; ++m) srcn[m] = sr[rowof(m)];
-            if (tid == 0) gidn = ent_u[item.e0];
-        }
         int issued = 0;
         bool ok = true;
-        // unit v: this warp's rows have landed (the caller waited for them);
-        // make them visible to the tensor cores and mark the stage full
-        auto finish = [&](int v) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bar_full[v % TC_ST]));
-        };
-        for (int u = 0; u < nunits; ++u) {
-            const int s = u % TC_ST, r = u / TC_ST;
-            const int e = u / S::NCH, c = u - e * S::NCH;
-            if (u >= S::LAG) {
-                // unit u - LAG: own rows landed (at most LAG - 1 newer groups
-                // pending), split, mark full
-                asm volatile("cp.async.wait_group %0;\n" ::"n"(S::LAG - 1) : "memory");
-                finish(u - S::LAG);
-            }
-            if (c == 0) {
-#pragma unroll
-                for (int m = 0; m < MR; ++m) src[m] = srcn[m];
-                gid = gidn;
-                if (e + 1 < ne) {
-                    const long long nrow = (long long)item.e0 + e + 1;
-                    const int *sr = ent_src + nrow * TT;
-#pragma unroll
-                    for (int m = 0; m < MR; ++m) srcn[m] = sr[rowof(m)];
-                    if (tid == 0) gidn = ent_u[nrow];
+        if constexpr (TMA) {
+            // ---------------- producer warp 0: lane l gathers rows 4l .. 4l+3
+            // of the tile (hi and lo plane, one tile::gather4 copy each);
+            // lane 0 posts the stage's bytes and copies the operator chunk
+            if (warp == 0) {
+                int4 rw = make_int4(0, 0, 0, 0), rwn = rw;
+                int gid = 0, gidn = 0;
+                if (ne > 0) {
+                    rwn = *reinterpret_cast<const int4 *>(ent_src + (long long)item.e0 * TT +
+                                                           4 * lane);
+                    if (lane == 0) gidn = ent_u[item.e0];
+                }
+                const uint32_t dsta = (uint32_t)(4 * lane) * 128u;  // 4 rows, linear
+                for (int u = 0; u < nunits; ++u) {
+                    const int s = u % TC_ST, r = u / TC_ST;
+                    const int e = u / S::NCH, c = u - e * S::NCH;
+                    if (c == 0) {
+                        rw = rwn;
+                        gid = gidn;
+                        if (e + 1 < ne) {
+                            const long long nrow = (long long)item.e0 + e + 1;
+                            rwn = *reinterpret_cast<const int4 *>(ent_src + nrow * TT + 4 * lane);
+                            if (lane == 0) gidn = ent_u[nrow];
+                        }
+                    }
+                    if (r > 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_empty[s]),
+                                                                    (r - 1) & 1, abort, spin))) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = sbase + (uint32_t)(s * S::STAGE);
+                    const uint32_t bb = smem_u32(&bar_b[s]);
+                    if (lane == 0) {
+                        mbar_expect_tx(bb, S::STAGE);
+                        bulk_g2s(st + 2 * S::A_BYTES,
+                                 Bop + ((long long)gid * S::NCH + c) * (2 * S::B_BYTES),
+                                 2 * S::B_BYTES, bb);
+                    }
+                    __syncwarp();
+                    // a cell without this partner reads row 0 (zeros)
+                    const int4 q = make_int4(rw.x >= 0 ? rw.x : 0, rw.y >= 0 ? rw.y : 0,
+                                             rw.z >= 0 ? rw.z : 0, rw.w >= 0 ? rw.w : 0);
+                    tma_gather4(st + dsta, &qmap, c * TC_KC, q, bb);
+                    tma_gather4(st + S::A_BYTES + dsta, &qmap, c * TC_KC,
+                                make_int4(q.x + ncell, q.y + ncell, q.z + ncell, q.w + ncell), bb);
+                    issued = u + 1;
                 }
             }
-            if (r > 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_empty[s]),
-                                                            (r - 1) & 1, abort, spin))) {
-                ok = false;
-                break;
-            }
-            const uint32_t st = sbase + (uint32_t)(s * S::STAGE);
-            if (tid == 0) {
-                const uint32_t bb = smem_u32(&bar_b[s]);
-                mbar_expect_tx(bb, 2 * S::B_BYTES);
-                bulk_g2s(st + 2 * S::A_BYTES,
-                         Bop + ((long long)gid * S::NCH + c) * (2 * S::B_BYTES), 2 * S::B_BYTES,
-                         bb);
-            }
+        } else {
+            // ---------------- producers: a warp instruction copies 4 whole unit
+            // rows (128 B each, one global line and one shared line): lane ->
+            // (row r = 4 (warp + NW m) + lane / 8, 16-byte chunk j = lane mod 8)
+            constexpr int NW = TC_PROD / 32, MR = 32 / NW;
+            const int j = lane & 7, rq = lane >> 3;
+            const uint32_t dst0 = sw128(4 * warp + rq, j);  // + m NW/2 atoms
+            auto rowof = [&](int m) { return 4 * (warp + NW * m) + rq; };
+            // partner rows and operator class of the current entry, and of the
+            // next one, loaded an entry ahead so that no gather waits on them
+            int src[MR], srcn[MR], gid = 0, gidn = 0;
+            if (ne > 0) {
+                const int *sr = ent_src + (long long)item.e0 * TT;
 #pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                const float *qb = Qs + part * qplane + c * TC_KC + 4 * j;
-#pragma unroll
-                for (int m = 0; m < MR; ++m) {
-                    const bool v = src[m] >= 0;
-                    tc_cp16(st + part * S::A_BYTES + dst0 + m * (NW / 2) * TC_SBO,
-                            qb + (v ? (long long)src[m] * S::KT : 0ll), v ? 16 : 0);
+                for (int m = 0; m < MR; ++m) srcn[m] = sr[rowof(m)];
+                if (tid == 0) gidn = ent_u[item.e0];
+            }
+            // unit v: this warp's rows have landed (the caller waited for them);
+            // make them visible to the tensor cores and mark the stage full
+            auto finish = [&](int v) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bar_full[v % TC_ST]));
+            };
+            for (int u = 0; u < nunits; ++u) {
+                const int s = u % TC_ST, r = u / TC_ST;
+                const int e = u / S::NCH, c = u - e * S::NCH;
+                if (u >= S::LAG) {
+                    // unit u - LAG: own rows landed (at most LAG - 1 newer groups
+                    // pending), split, mark full
+                    asm volatile("cp.async.wait_group %0;\n" ::"n"(S::LAG - 1) : "memory");
+                    finish(u - S::LAG);
                 }
+                if (c == 0) {
+#pragma unroll
+                    for (int m = 0; m < MR; ++m) src[m] = srcn[m];
+                    gid = gidn;
+                    if (e + 1 < ne) {
+                        const long long nrow = (long long)item.e0 + e + 1;
+                        const int *sr = ent_src + nrow * TT;
+#pragma unroll
+                        for (int m = 0; m < MR; ++m) srcn[m] = sr[rowof(m)];
+                        if (tid == 0) gidn = ent_u[nrow];
+                    }
+                }
+                if (r > 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_empty[s]),
+                                                                (r - 1) & 1, abort, spin))) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = sbase + (uint32_t)(s * S::STAGE);
+                if (tid == 0) {
+                    const uint32_t bb = smem_u32(&bar_b[s]);
+                    mbar_expect_tx(bb, 2 * S::B_BYTES);
+                    bulk_g2s(st + 2 * S::A_BYTES,
+                             Bop + ((long long)gid * S::NCH + c) * (2 * S::B_BYTES),
+                             2 * S::B_BYTES, bb);
+                }
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    const float *qb = Qs + part * qplane + c * TC_KC + 4 * j;
+#pragma unroll
+                    for (int m = 0; m < MR; ++m) {
+                        const bool v = src[m] >= 0;
+                        tc_cp16(st + part * S::A_BYTES + dst0 + m * (NW / 2) * TC_SBO,
+                                qb + (v ? (long long)src[m] * S::KT : 0ll), v ? 16 : 0);
+                    }
+                }
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                issued = u + 1;
             }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            issued = u + 1;
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            if (ok)
+                for (int u = nunits - S::LAG > 0 ? nunits - S::LAG : 0; u < nunits; ++u) finish(u);
         }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        if (ok)
-            for (int u = nunits - S::LAG > 0 ? nunits - S::LAG : 0; u < nunits; ++u) finish(u);
         if (!ok) {
             *abort = 1;
             atomicOr(flags, FLAG_TIMEOUT);
@@ -453,7 +527,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // producers' bounded waits for a free stage run out
         for (int u = 0; u < (stall ? 0 : nunits); ++u) {
             const int s = u % TC_ST, r = u / TC_ST;
-            if (!mbar_wait(smem_u32(&bar_full[s]), r & 1, abort, spin) ||
+            if ((!TMA && !mbar_wait(smem_u32(&bar_full[s]), r & 1, abort, spin)) ||
                 !mbar_wait(smem_u32(&bar_b[s]), r & 1, abort, spin)) {
                 ok = false;
                 break;
@@ -547,12 +621,46 @@ void launch_m2l_tc_ops(int p, int KP, int L, int n_off, const Geom *g, const flo
 #undef M2LOPS
 }
 
+// Tensor map of the split moments for the TMA gather: rows of KT floats, the
+// hi plane (rows 0 .. ncell-1) then the lo plane; box = one 128-byte row,
+// 128-byte swizzle (the MMA operand layout).  map: 128 bytes, 64-byte aligned.
+bool m2l_tc_qmap(void *map, const float *Qs, long long ncell, int KP)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const int KT = m2l_tc_kt(KP);
+    if (KT <= 0 || 2 * ncell >= (1ll << 31)) return false;
+    cuuint64_t dim[2] = {(cuuint64_t)KT, (cuuint64_t)(2 * ncell)};
+    cuuint64_t stride[1] = {(cuuint64_t)KT * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)TC_KC, 1u};
+    cuuint32_t estr[2] = {1u, 1u};
+    return encode(reinterpret_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<float *>(Qs), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items, int nitems,
                    const int *tile_item0, const int *tile_nitems, const int *ent_u,
                    const int *ent_src, const float *Q, long long ncell, const float *gk,
-                   float *Qs, const float *Bop, const Geom *g, float *Ps, double *V, int *flags,
-                   cudaStream_t s)
+                   float *Qs, const void *qmap, const float *Bop, const Geom *g, float *Ps,
+                   double *V, int *flags, cudaStream_t s)
 {
+    // qmap (a tensor map from m2l_tc_qmap) selects the TMA gather, nullptr
+    // the cp.async gather
+    CUtensorMap none;
+    memset(&none, 0, sizeof(none));
+    const CUtensorMap &qm = qmap ? *reinterpret_cast<const CUtensorMap *>(qmap) : none;
     // CCFMM_TC_STALL=1 (failure-path tests): the MMA thread issues nothing
     // and the waits give up after 2^12 polls; the evaluation then reports
     // CCFMM_ERR_TIMEOUT
@@ -567,11 +675,11 @@ void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *
         note_launch();                                                                          \
         k_q_split<KPV><<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(p, ncell, Q, gk, Qs);     \
         size_t smem = tc_smem<KPV>();                                                           \
-        cudaFuncSetAttribute(k_m2l_tc<KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                             (int)smem);                                                        \
+        auto kern = qmap ? k_m2l_tc<KPV, true> : k_m2l_tc<KPV, false>;                          \
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
         note_launch();                                                                          \
-        k_m2l_tc<KPV><<<nitems, TC_THREADS, smem, s>>>(                                         \
-            items, ent_u, ent_src, Qs, ncell * S::KT,                                           \
+        kern<<<nitems, TC_THREADS, smem, s>>>(                                                  \
+            items, ent_u, ent_src, Qs, ncell * S::KT, qm, (int)ncell,                           \
             reinterpret_cast<const unsigned char *>(Bop), Ps, flags, spin, stall);              \
     } break;
         switch (KP) {

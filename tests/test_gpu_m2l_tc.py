@@ -59,3 +59,35 @@ def test_tensor_core_m2l_irregular(kind):
     sub = W.subset(len(pos), 300, 5)
     Hd = C.direct_field(pos, mom, targets=sub)
     assert rel(Ht[sub], Hd) < 1e-4
+
+
+def _run_gather(mode, pos, mom, p, theta):
+    old = os.environ.get("CCFMM_TC_GATHER")
+    os.environ["CCFMM_TC_GATHER"] = mode
+    try:
+        return _run("tc", pos, mom, p, theta)
+    finally:
+        if old is None:
+            del os.environ["CCFMM_TC_GATHER"]
+        else:
+            os.environ["CCFMM_TC_GATHER"] = old
+
+
+@pytest.mark.parametrize("case", ["p4", "p5", "p6", "p7", "clustered", "ring"])
+def test_tma_gather_is_bitwise(case):
+    """The TMA row gather (tile::gather4 copies; an absent partner reads the
+    zero row 0) fills the operand stages with the same bytes as the cp.async
+    gather, so the MMAs, and the whole field, agree bit for bit."""
+    if case == "clustered":
+        pos, mom = W.clustered(30000, seed=W.BASE_SEED + 41)
+        p = 6
+    elif case == "ring":
+        pos, mom = W.ring(r_out=60.0, r_in=20.0, seed=W.BASE_SEED + 42)
+        p = 6
+    else:
+        p = int(case[1])
+        pos, mom = W.ferrofluid(20000, side=100.0 * 0.02 ** (1 / 3), seed=W.BASE_SEED + 30 + p)
+    Hc, Vc = _run_gather("cp", pos, mom, p, 0.5)
+    Ht, Vt = _run_gather("tma", pos, mom, p, 0.5)
+    assert np.array_equal(Vt, Vc)
+    assert np.array_equal(Ht, Hc)
