@@ -78,6 +78,16 @@ typedef struct {
                                  With the near/far overlap (default) P2P runs
                                  concurrently with P2M..L2L, so the stages do
                                  not add up to ms_eval */
+    double ms_build_stage[6]; /* the last build by phase (device time between
+                                 stream events, so waits for the host count):
+                                 [0] input upload, box, keys, sort;
+                                 [1] depth choice (host), leaf ranges, sorted
+                                 points, cells per level; [2] lists of every
+                                 level and tile counts (after the plan, which
+                                 the host builds while [1] runs); [3] M2L
+                                 work items (host) and their upload; [4] tile
+                                 fill, F table (first build), D tables;
+                                 [5] host time of the plan alone */
 } ccfmm_stats;
 
 /* ------------------------------------------------------------------------

@@ -35,7 +35,7 @@ class Stats(ctypes.Structure):
         ("box", _dbl * 6), ("leaf_width", _dbl * 3), ("n", _i64), ("nonempty_leaves", _i64),
         ("near_leaf_pairs", _i64), ("far_pairs", _i64), ("p2p_pairs", _i64),
         ("m2l_tile_entries", _i64), ("far_offsets", _i64), ("ms_build", _dbl),
-        ("ms_eval", _dbl), ("ms_stage", _dbl * 8),
+        ("ms_eval", _dbl), ("ms_stage", _dbl * 8), ("ms_build_stage", _dbl * 6),
     ]
 
     def as_dict(self):

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <map>
 #include <string>
 #include <unordered_map>
@@ -128,7 +129,7 @@ struct LevelPlan {
 
 // build events, then a ring of per-evaluation stage events so that stage
 // times of evaluations inside a caller's timed region can be read afterwards
-enum { EV_B0, EV_B1, EV_NB };
+enum { EV_B0, EV_BS1, EV_BS2, EV_BS3, EV_BS4, EV_B1, EV_NB };
 // evaluation events: far chain E0..L2L, near field P2P0..P2P1, then the join
 // (both done), L2P and the unpermute (FIN)
 enum { EV_E0, EV_P2M, EV_M2M, EV_M2L, EV_L2L, EV_JOIN, EV_L2P, EV_FIN, EV_P2P0, EV_P2P1, EV_NE };
@@ -154,6 +155,7 @@ struct ccfmm_s {
     int n_off = 0, ntiles = 0, max_bits = 0;
     int n_d = 0;  // distinct scaled separations (D tables) over all far offset classes
     long long near_leaf_total = 0, far_total = 0, ent_total = 0;
+    double ms_plan_host = 0.0;  // host time of the last make_plan
     bool built = false, evaluated = false, ftable_ready = false;
     bool tc_ops_ready = false;  // tensor-core M2L operators of the current build
     bool pairs_counted = false; // near-pair count of the current build taken
@@ -407,6 +409,8 @@ static ccfmm_status check_flags(ccfmm_t h, int flags)
     return CCFMM_OK;
 }
 
+static ccfmm_status overlap_prepare(ccfmm_t h);
+
 static ccfmm_status build(ccfmm_t h, const double *positions, const double *moments)
 {
     cudaStream_t s = h->stream;
@@ -450,6 +454,7 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
                P<uint32_t>(h->keys3), P<int>(h->idx3), N, LCAP, h->sorttemp.p, s);
     launch_depth_hist(P<uint32_t>(h->keys2), N, drb->hist, s);
     KCHECK();
+    if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_BS1], s));
     // sync 1: flags, box, depth histogram, geometry
     CK(cudaMemcpyAsync(h->hrb, drb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&h->geom, h->geomd.p, sizeof(Geom), cudaMemcpyDeviceToHost, s));
@@ -506,12 +511,54 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
                                    P<double4>(h->A), P<double2>(h->B), s);
     launch_level_counts(P<int>(h->leaf_start), L, drb->ne, s);
     KCHECK();
+    if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_BS2], s));
+    // the plan needs only the depth and the geometry: the host builds it
+    // while the kernels above run (its uploads queue behind them)
+    const auto tp0 = std::chrono::steady_clock::now();
+    TRY(make_plan(h));
+    h->ms_plan_host =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp0).count();
+    // F table and derivative tensors of every (level, far offset), FP64.
+    // They need only the plan, so they run on the far stream beside the
+    // list construction and join the handle's stream before the build ends.
+    // (ensemble members keep them on their own stream: their builds already
+    // run side by side on the ensemble's branch streams)
+    const bool side = !h->quiet;
+    if (side) {
+        TRY(overlap_prepare(h));
+        CK(cudaEventRecord(h->ev_fork, s));
+        CK(cudaStreamWaitEvent(h->s_far, h->ev_fork, 0));
+    }
+    const cudaStream_t sd = side ? h->s_far : s;
+    int O = 2 * h->p;
+    h->TD = nterms(O);
+    h->ldD = ((h->TD + 1 + 3) / 4) * 4;
+    if (!h->ftable_ready) {
+        // the F table depends on p only: built once per handle
+        TRY(ensure(h->fdense, ftable_scratch_bytes(O)));
+        TRY(ensure(h->fst, sizeof(int) * (h->TD + 1)));
+        TRY(ensure(h->fq, sizeof(uint16_t) * h->TD * 160));
+        TRY(ensure(h->fval, sizeof(double) * h->TD * 160));
+        launch_ftable(O, P<double>(h->fdense), P<int>(h->fst), P<uint16_t>(h->fq),
+                      P<double>(h->fval), sd);
+        TRY(ensure(h->itab, sizeof(uint16_t) * h->KP * h->KP));
+        launch_itable(h->p, h->KP, h->maxdeg, P<uint16_t>(h->itab), sd);
+        h->ftable_ready = true;
+    }
+    TRY(ensure(h->D, rs * (size_t)std::max(h->n_d, 1) * h->ldD));
+    if (h->prec == CCFMM_MIXED)
+        launch_dtables<float>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
+                              P<double4>(h->dsep), h->n_d, P<float>(h->D), h->ldD, sd);
+    else
+        launch_dtables<double>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
+                               P<double4>(h->dsep), h->n_d, P<double>(h->D), h->ldD, sd);
+    KCHECK();
+    if (side) CK(cudaEventRecord(h->ev_join, sd));
     // sync 2: non-empty cells per level
     CK(cudaMemcpyAsync(h->hrb, drb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     h->leaf_perm_valid = true;
 
-    TRY(make_plan(h));
     long long near_max = 1, far_sum = 0;
     for (int l = 0; l <= L; ++l) {
         LevelPlan &lp = h->plan[l];
@@ -556,15 +603,11 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
         scan_exclusive(P<int>(h->ncnt), P<int>(*nsCur), nc, P<int>(*nsCur) + nc, h->scantemp.p, s);
         scan_exclusive(P<int>(h->fcnt), P<int>(h->fstart), nc, P<int>(h->fstart) + nc,
                        h->scantemp.p, s);
-        CK(cudaMemcpyAsync(&drb->near_total[l], P<int>(*nsCur) + nc, sizeof(int),
-                           cudaMemcpyDeviceToDevice, s));
-        CK(cudaMemcpyAsync(&drb->far_total[l], P<int>(h->fstart) + nc, sizeof(int),
-                           cudaMemcpyDeviceToDevice, s));
         launch_list_fill_impl(l, P<int>(h->leaf_start), L, P<int>(*nsPrev), P<NearEnt>(*nePrev),
                               P<int>(h->cube), ci, h->geom.axis[l], P<int>(*nsCur),
                               P<NearEnt>(*neCur), P<int>(h->fstart), lp.far_base,
                               P<FarEnt>(h->far), P<int>(h->far_off), P<int>(h->far_num),
-                              &drb->flags, s);
+                              &drb->near_total[l], &drb->far_total[l], &drb->flags, s);
         std::swap(nsPrev, nsCur);
         std::swap(nePrev, neCur);
     }
@@ -609,6 +652,7 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
                            cudaMemcpyDeviceToDevice, s));
     }
     KCHECK();
+    if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_BS3], s));
     // sync 3: list totals and M2L work size
     CK(cudaMemcpyAsync(h->hrb, drb, sizeof(Readback), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -662,6 +706,7 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
         if (h->prec == CCFMM_MIXED)
             TRY(ensure(h->Ps, sizeof(float) * (size_t)std::max(h->nitems, 1) * TT * h->KP));
     }
+    if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_BS4], s));
     TRY(ensure(h->ent_u, sizeof(int) * std::max(h->ent_total, 1ll)));
     TRY(ensure(h->ent_src, sizeof(int) * (size_t)TT * std::max(h->ent_total, 1ll)));
     if (h->ntiles)
@@ -669,35 +714,13 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
                          P<int>(h->far_num), P<FarEnt>(h->far), h->max_bits, P<int>(h->dmap),
                          P<int>(h->ent_u), P<int>(h->ent_src), s);
 
-    // F table and derivative tensors of every (level, far offset), FP64
-    int O = 2 * h->p;
-    h->TD = nterms(O);
-    h->ldD = ((h->TD + 1 + 3) / 4) * 4;
-    if (!h->ftable_ready) {
-        // the F table depends on p only: built once per handle
-        TRY(ensure(h->fdense, ftable_scratch_bytes(O)));
-        TRY(ensure(h->fst, sizeof(int) * (h->TD + 1)));
-        TRY(ensure(h->fq, sizeof(uint16_t) * h->TD * 160));
-        TRY(ensure(h->fval, sizeof(double) * h->TD * 160));
-        launch_ftable(O, P<double>(h->fdense), P<int>(h->fst), P<uint16_t>(h->fq),
-                      P<double>(h->fval), s);
-        TRY(ensure(h->itab, sizeof(uint16_t) * h->KP * h->KP));
-        launch_itable(h->p, h->KP, h->maxdeg, P<uint16_t>(h->itab), s);
-        h->ftable_ready = true;
-    }
-    TRY(ensure(h->D, rs * (size_t)std::max(h->n_d, 1) * h->ldD));
-    if (h->prec == CCFMM_MIXED)
-        launch_dtables<float>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
-                              P<double4>(h->dsep), h->n_d, P<float>(h->D), h->ldD, s);
-    else
-        launch_dtables<double>(h->p, P<int>(h->fst), P<uint16_t>(h->fq), P<double>(h->fval),
-                               P<double4>(h->dsep), h->n_d, P<double>(h->D), h->ldD, s);
     TRY(ensure(h->Q, rs * (size_t)ncellp * h->KP));
     TRY(ensure(h->V, sizeof(double) * (size_t)ncellp * h->KP));
     TRY(ensure(h->epart, sizeof(double) * ((N + 255) / 256 + 1)));
     // the near-pair count (statistics only) is taken by fmm_stats on demand
     h->pairs_counted = false;
     KCHECK();
+    if (side) CK(cudaStreamWaitEvent(s, h->ev_join, 0));  // D tables (far stream)
     if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_B1], s));
     // The last kernels (tile fill, D tables, pair count) may still run when
     // the build returns: everything later on the handle's stream is ordered
@@ -909,9 +932,10 @@ const char *ccfmm_last_error(void) { return g_err.c_str(); }
 
 int64_t ccfmm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
-ccfmm_status fmm_create_ex(const double *positions, const double *moments, int64_t N, int p,
-                           double theta, double leaf_size, const double *box, ccfmm_prec prec,
-                           void *stream, ccfmm_t *out)
+// member: the handle belongs to an ensemble (set before its first build)
+static ccfmm_status create_handle(const double *positions, const double *moments, int64_t N,
+                                  int p, double theta, double leaf_size, const double *box,
+                                  ccfmm_prec prec, void *stream, bool member, ccfmm_t *out)
 {
     g_err.clear();
     if (!out) return fail(CCFMM_ERR_ARG, "out is NULL");
@@ -937,6 +961,7 @@ ccfmm_status fmm_create_ex(const double *positions, const double *moments, int64
         return fail(CCFMM_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
     }
     h->stream = (cudaStream_t)stream;
+    h->quiet = member;
     h->N = N;
     h->p = p;
     h->theta = theta;
@@ -972,6 +997,14 @@ ccfmm_status fmm_create_ex(const double *positions, const double *moments, int64
     }
     *out = h;
     return CCFMM_OK;
+}
+
+ccfmm_status fmm_create_ex(const double *positions, const double *moments, int64_t N, int p,
+                           double theta, double leaf_size, const double *box, ccfmm_prec prec,
+                           void *stream, ccfmm_t *out)
+{
+    return create_handle(positions, moments, N, p, theta, leaf_size, box, prec, stream, false,
+                         out);
 }
 
 ccfmm_status fmm_create(const double *positions, const double *moments, int64_t N, int p,
@@ -1108,6 +1141,11 @@ ccfmm_status fmm_stats(ccfmm_t h, ccfmm_stats *out)
     if (h->ev_ok) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->evb[EV_B0], h->evb[EV_B1]) == cudaSuccess) st.ms_build = ms;
+        const int marks[6] = {EV_B0, EV_BS1, EV_BS2, EV_BS3, EV_BS4, EV_B1};
+        for (int i = 0; i < 5; ++i)
+            if (cudaEventElapsedTime(&ms, h->evb[marks[i]], h->evb[marks[i + 1]]) == cudaSuccess)
+                st.ms_build_stage[i] = ms;
+        st.ms_build_stage[5] = h->ms_plan_host;
         // mean over the evaluations since the last fmm_reset_stats (at most
         // the last EV_RING of them)
         long long n = std::min<long long>(h->n_eval - h->n_eval_reset, EV_RING);
@@ -1627,9 +1665,8 @@ ccfmm_status fmm_batch_create(const double *positions, const double *moments,
     for (int i = 0; i < nsamples; ++i) {
         ccfmm_t hs = nullptr;
         long long o = b->off[i], n = b->off[i + 1] - o;
-        BTRY(fmm_create_ex(positions + 3 * o, P<double>(b->mom) + 3 * o, n, p, theta, leaf_size,
-                           nullptr, prec, b->br[i % b->nbr], &hs));
-        hs->quiet = true;
+        BTRY(create_handle(positions + 3 * o, P<double>(b->mom) + 3 * o, n, p, theta, leaf_size,
+                           nullptr, prec, b->br[i % b->nbr], true, &hs));
         hs->mom_energy = P<double>(b->mom) + 3 * o;
         hs->E_dst = P<double>(b->E) + i;
         b->h.push_back(hs);

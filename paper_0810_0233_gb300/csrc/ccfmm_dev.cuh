@@ -164,11 +164,13 @@ void launch_check_finite(const double *x, long long n, int *d_flags, cudaStream_
 void launch_list_count(int level, const int *leaf_start, int L, const int *near_start_prev,
                        const NearEnt *near_prev, const int *cube, OffsetCube cube_info, int axis,
                        int *ncnt, int *fcnt, int *d_flags, cudaStream_t s);
+// near_total / far_total: where the level's list totals are copied for the host
 void launch_list_fill_impl(int level, const int *leaf_start, int L, const int *near_start_prev,
                            const NearEnt *near_prev, const int *cube, OffsetCube cube_info,
                            int axis, const int *near_start, NearEnt *near_out,
                            const int *far_start, long long far_base, FarEnt *far_out,
-                           int *far_off, int *far_num, int *d_flags, cudaStream_t s);
+                           int *far_off, int *far_num, int *near_total, int *far_total,
+                           int *d_flags, cudaStream_t s);
 void launch_tile_count(const Tile *tiles, int ntiles, const int *far_off, const int *far_num,
                        const FarEnt *far, int max_bits, int *counts, cudaStream_t s);
 // entries get the D table of their offset class (dmap[class])

@@ -38,14 +38,14 @@ __device__ __forceinline__ int cube_class(const int *cube, const OffsetCube &ci,
     return v;
 }
 
-// warp per cell c of level lv: count its near and far candidates
-__global__ void k_list_count(int lv, const int *leaf_start, int L, const int *nstart_prev,
-                             const NearEnt *near_prev, const int *cube, OffsetCube ci, int axis,
-                             int *ncnt, int *fcnt, int *flags)
+// warp per cell c of level lv: count its near and far candidates; returns
+// (near, far) in every lane
+__device__ __forceinline__ int2 list_count_cell(int lv, long long c, int lane,
+                                                const int *leaf_start, int L,
+                                                const int *nstart_prev, const NearEnt *near_prev,
+                                                const int *cube, const OffsetCube &ci, int axis,
+                                                int *flags)
 {
-    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (c >= (1ll << lv)) return;
     int nn = 0, nf = 0;
     if (cell_count(leaf_start, L, lv, c) > 0) {
         long long P = c >> 1;
@@ -70,9 +70,21 @@ __global__ void k_list_count(int lv, const int *leaf_start, int L, const int *ns
         nn += __shfl_xor_sync(0xffffffffu, nn, o);
         nf += __shfl_xor_sync(0xffffffffu, nf, o);
     }
+    return make_int2(nn, nf);
+}
+
+__global__ void k_list_count(int lv, const int *leaf_start, int L, const int *nstart_prev,
+                             const NearEnt *near_prev, const int *cube, OffsetCube ci, int axis,
+                             int *ncnt, int *fcnt, int *flags)
+{
+    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (c >= (1ll << lv)) return;
+    int2 r = list_count_cell(lv, c, lane, leaf_start, L, nstart_prev, near_prev, cube, ci, axis,
+                             flags);
     if (lane == 0) {
-        ncnt[c] = nn;
-        fcnt[c] = nf;
+        ncnt[c] = r.x;
+        fcnt[c] = r.y;
     }
 }
 
@@ -88,15 +100,15 @@ __device__ __forceinline__ int warp_excl(int v, int lane, int *total)
 }
 
 // warp per cell: write the candidates in the order (partner entry, child bit)
-__global__ void k_list_fill(int lv, const int *leaf_start, int L, const int *nstart_prev,
-                            const NearEnt *near_prev, const int *cube, OffsetCube ci, int axis,
-                            const int *near_start, NearEnt *near_out, const int *far_start,
-                            long long far_base, FarEnt *far_out, int *far_off, int *far_num,
-                            int *flags)
+__device__ __forceinline__ void list_fill_cell(int lv, long long c, int lane,
+                                               const int *leaf_start, int L,
+                                               const int *nstart_prev, const NearEnt *near_prev,
+                                               const int *cube, const OffsetCube &ci, int axis,
+                                               const int *near_start, NearEnt *near_out,
+                                               const int *far_start, long long far_base,
+                                               FarEnt *far_out, int *far_off, int *far_num,
+                                               int *flags)
 {
-    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (c >= (1ll << lv)) return;
     long long hid = (1ll << lv) + c;
     long long fs = far_base + far_start[c];
     int fn = far_start[c + 1] - far_start[c];
@@ -159,6 +171,26 @@ __global__ void k_list_fill(int lv, const int *leaf_start, int L, const int *nst
     }
 }
 
+// one level; thread 0 also copies the level's list totals (the last entries
+// of the scanned counts) to near_total / far_total for the host
+__global__ void k_list_fill(int lv, const int *leaf_start, int L, const int *nstart_prev,
+                            const NearEnt *near_prev, const int *cube, OffsetCube ci, int axis,
+                            const int *near_start, NearEnt *near_out, const int *far_start,
+                            long long far_base, FarEnt *far_out, int *far_off, int *far_num,
+                            int *near_total, int *far_total, int *flags)
+{
+    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    const long long nc = 1ll << lv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *near_total = near_start[nc];
+        *far_total = far_start[nc];
+    }
+    if (c >= nc) return;
+    list_fill_cell(lv, c, lane, leaf_start, L, nstart_prev, near_prev, cube, ci, axis, near_start,
+                   near_out, far_start, far_base, far_out, far_off, far_num, flags);
+}
+
 void launch_list_count(int level, const int *leaf_start, int L, const int *near_start_prev,
                        const NearEnt *near_prev, const int *cube, OffsetCube cube_info, int axis,
                        int *ncnt, int *fcnt, int *d_flags, cudaStream_t s)
@@ -174,13 +206,14 @@ void launch_list_fill_impl(int level, const int *leaf_start, int L, const int *n
                            const NearEnt *near_prev, const int *cube, OffsetCube cube_info,
                            int axis, const int *near_start, NearEnt *near_out,
                            const int *far_start, long long far_base, FarEnt *far_out,
-                           int *far_off, int *far_num, int *d_flags, cudaStream_t s)
+                           int *far_off, int *far_num, int *near_total, int *far_total,
+                           int *d_flags, cudaStream_t s)
 {
     long long threads = (1ll << level) * 32;
     note_launch();
     k_list_fill<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
         level, leaf_start, L, near_start_prev, near_prev, cube, cube_info, axis, near_start,
-        near_out, far_start, far_base, far_out, far_off, far_num, d_flags);
+        near_out, far_start, far_base, far_out, far_off, far_num, near_total, far_total, d_flags);
 }
 
 // ---------------------------------------------------------------------------
