@@ -626,18 +626,20 @@ void launch_m2l_tc_ops(int p, int KP, int L, int n_off, const Geom *g, const flo
 // 128-byte swizzle (the MMA operand layout).  map: 128 bytes, 64-byte aligned.
 bool m2l_tc_qmap(void *map, const float *Qs, long long ncell, int KP)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // resolved once (thread-safe static initialisation); nullptr if the
+    // driver does not provide it
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                              cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn) {
+            q != cudaDriverEntryPointSuccess) {
             cudaGetLastError();
-            return false;
+            fn = nullptr;
         }
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return false;
     const int KT = m2l_tc_kt(KP);
     if (KT <= 0 || 2 * ncell >= (1ll << 31)) return false;
     cuuint64_t dim[2] = {(cuuint64_t)KT, (cuuint64_t)(2 * ncell)};
