@@ -600,9 +600,8 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
         launch_list_count(l, P<int>(h->leaf_start), L, P<int>(*nsPrev), P<NearEnt>(*nePrev),
                           P<int>(h->cube), ci, h->geom.axis[l], P<int>(h->ncnt), P<int>(h->fcnt),
                           &drb->flags, s);
-        scan_exclusive(P<int>(h->ncnt), P<int>(*nsCur), nc, P<int>(*nsCur) + nc, h->scantemp.p, s);
-        scan_exclusive(P<int>(h->fcnt), P<int>(h->fstart), nc, P<int>(h->fstart) + nc,
-                       h->scantemp.p, s);
+        scan_exclusive2(P<int>(h->ncnt), P<int>(*nsCur), P<int>(*nsCur) + nc, P<int>(h->fcnt),
+                        P<int>(h->fstart), P<int>(h->fstart) + nc, nc, h->scantemp.p, s);
         launch_list_fill_impl(l, P<int>(h->leaf_start), L, P<int>(*nsPrev), P<NearEnt>(*nePrev),
                               P<int>(h->cube), ci, h->geom.axis[l], P<int>(*nsCur),
                               P<NearEnt>(*neCur), P<int>(h->fstart), lp.far_base,

@@ -134,6 +134,10 @@ size_t scan_temp_bytes(long long n);
 // exclusive scan of n int32 values; total (if not null) written to device
 void scan_exclusive(const int *in, int *out, long long n, int *d_total, void *temp,
                     cudaStream_t s);
+// two exclusive scans of the same length in one launch set; scratch: twice
+// what scan_exclusive needs for n
+void scan_exclusive2(const int *in0, int *out0, int *total0, const int *in1, int *out1,
+                     int *total1, long long n, void *temp, cudaStream_t s);
 size_t radix_temp_bytes(long long n);
 // stable sort of (key, value) by the low `bits` bits of key; results in
 // (k_out, v_out)

@@ -96,6 +96,81 @@ void scan_exclusive(const int *in, int *out, long long n, int *d_total, void *te
     }
 }
 
+// Two arrays of the same length in one launch set (blockIdx.y picks the
+// array): the near and far counts of a level.
+struct Scan2 {
+    const int *in[2];
+    int *out[2];
+    int *total[2];
+};
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_blocks2(Scan2 a, long long n, int *bsum,
+                                                         long long nb)
+{
+    __shared__ int sm[32];
+    const int y = blockIdx.y;
+    const int *in = a.in[y];
+    int *out = a.out[y];
+    long long base = (long long)blockIdx.x * SCAN_B + (long long)threadIdx.x * SCAN_I;
+    int v[SCAN_I];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+        long long j = base + i;
+        v[i] = j < n ? in[j] : 0;
+        s += v[i];
+    }
+    int tot;
+    int ex = block_exclusive_scan(s, sm, &tot);
+#pragma unroll
+    for (int i = 0; i < SCAN_I; ++i) {
+        long long j = base + i;
+        if (j < n) out[j] = ex;
+        ex += v[i];
+    }
+    if (threadIdx.x == 0) {
+        bsum[y * nb + blockIdx.x] = tot;
+        if (gridDim.x == 1 && a.total[y]) *a.total[y] = tot;
+    }
+}
+
+__global__ void k_scan_add2(int *out0, int *out1, long long n, const int *boff, long long nb)
+{
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (blockIdx.y == 0)
+        out0[j] += boff[j / SCAN_B];
+    else
+        out1[j] += boff[nb + j / SCAN_B];
+}
+
+void scan_exclusive2(const int *in0, int *out0, int *total0, const int *in1, int *out1,
+                     int *total1, long long n, void *temp, cudaStream_t s)
+{
+    if (n <= 0) {
+        if (total0) cudaMemsetAsync(total0, 0, sizeof(int), s);
+        if (total1) cudaMemsetAsync(total1, 0, sizeof(int), s);
+        return;
+    }
+    long long nb = (n + SCAN_B - 1) / SCAN_B;
+    int *bsum = (int *)temp;  // [2][nb]
+    char *next = (char *)temp + (((size_t)2 * nb * sizeof(int) + 255) / 256) * 256;
+    Scan2 a;
+    a.in[0] = in0;
+    a.in[1] = in1;
+    a.out[0] = out0;
+    a.out[1] = out1;
+    a.total[0] = total0;
+    a.total[1] = total1;
+    note_launch();
+    k_scan_blocks2<<<dim3((unsigned)nb, 2), SCAN_T, 0, s>>>(a, n, bsum, nb);
+    if (nb > 1) {
+        scan_exclusive2(bsum, bsum, total0, bsum + nb, bsum + nb, total1, nb, next, s);
+        note_launch();
+        k_scan_add2<<<dim3((unsigned)((n + 255) / 256), 2), 256, 0, s>>>(out0, out1, n, bsum, nb);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort, 8-bit digits, tiles of 2048 keys (8 rounds of 256).
 // Within a tile the rank of a key among equal digits follows input order:
