@@ -315,7 +315,8 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
                     "ms_per_step": 1e3 * t_e2e / args.steps, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(total * 24 + len(mine) * 8),
                     "note": "the step's fields and energies read back to pinned host memory"},
-            "gpu_launches": int(launches),
+            "gpu_launches": int(launches) * args.steps,
+            "gpu_launches_per_step": int(launches),
             "roofline": {"kernel": "whole step (graph)", "bound": "alu", "achieved": ach,
                          "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
                          "traffic": None,
@@ -447,7 +448,8 @@ def main():
                     "ms_per_step": 1e3 * t_e2e / steps,
                     "h2d_bytes_per_step": int(pos.nbytes + mom.nbytes),
                     "d2h_bytes_per_step": int(n * 3 * 8)},
-            "gpu_launches": int(launches)}
+            "gpu_launches": int(launches) * steps,
+            "gpu_launches_per_step": int(launches)}
 
     # roofline of the dominant kernel, from the library's stage events of the
     # timed evaluations (same stream)
