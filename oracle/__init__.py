@@ -8,7 +8,9 @@ never imports it.
 
 Pins: every routine is checked in ``tests/test_oracle_*.py`` against
 closed forms, the paper's worked examples and tables, symbolic
-differentiation and brute force (see the docstrings there).  Parity
+differentiation and brute force (see the docstrings there); the
+adaptive-depth tree (``OracleAFMM``, a project extension) in
+``tests/test_oracle_adaptive.py``.  Parity
 unpinned: none of the functions exported here.
 """
 from __future__ import annotations
@@ -84,6 +86,16 @@ def _bind(path):
         "orc_fmm_locals": (None, [ctypes.c_void_p, _dp]),
         "orc_fmm_field": (None, [ctypes.c_void_p, _dp]),
         "orc_fmm_energy": (ctypes.c_double, [ctypes.c_void_p]),
+        "orc_afmm_new": (ctypes.c_void_p, [_i64, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, _dp]),
+        "orc_afmm_free": (None, [ctypes.c_void_p]),
+        "orc_afmm_run": (None, [ctypes.c_void_p]),
+        "orc_afmm_field": (None, [ctypes.c_void_p, _dp]),
+        "orc_afmm_energy": (ctypes.c_double, [ctypes.c_void_p]),
+        "orc_afmm_ncells": (_i64, [ctypes.c_void_p]),
+        "orc_afmm_cell": (None, [ctypes.c_void_p, _i64, _lp]),
+        "orc_afmm_perm": (None, [ctypes.c_void_p, _lp]),
+        "orc_afmm_pairs": (_i64, [ctypes.c_void_p, ctypes.c_int, _lp]),
         "orc_philox4x64": (None, [_u64p, _u64p, _u64p]),
         "orc_rotate_moments": (None, [_i64, _dp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
                                       _i64]),
@@ -395,4 +407,73 @@ def fmm_field(pos, mom, p, theta, leaf_size=0.0, box=None, leaf_mask=None, max_d
         f.set_truncation(max_degree)
     f.upward()
     f.downward(leaf_mask)
+    return f.field(), f.energy(), f
+
+
+# ---------------------------------------------------------------- adaptive tree
+class OracleAFMM:
+    """Adaptive-depth tree (a project extension of the paper's complete tree):
+    a cell is split while it holds more than ``s`` points; lists by the
+    unequal-level extension of createPartners (see the C source)."""
+
+    def __init__(self, pos, mom, p, theta, s, box=None):
+        self._lib = _load()
+        self.pos = _arr3(pos).reshape(-1, 3)
+        self.mom = _arr3(mom).reshape(-1, 3)
+        self.n = len(self.pos)
+        self.p = int(p)
+        bx = None
+        if box is not None:
+            self._box = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(6))
+            bx = _d(self._box)
+        h = self._lib.orc_afmm_new(self.n, _d(self.pos), _d(self.mom), self.p, float(theta),
+                                   float(s), bx)
+        if not h:
+            raise ValueError("oracle rejected the arguments")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc_afmm_free(h)
+            self._h = None
+
+    def run(self):
+        self._lib.orc_afmm_run(self._h)
+
+    def field(self) -> np.ndarray:
+        out = np.zeros((self.n, 3))
+        self._lib.orc_afmm_field(self._h, _d(out))
+        return out
+
+    def energy(self) -> float:
+        return self._lib.orc_afmm_energy(self._h)
+
+    def cells(self) -> np.ndarray:
+        """Per cell: level, parent, child0, child1, first point, count, leaf."""
+        nc = self._lib.orc_afmm_ncells(self._h)
+        out = np.zeros((nc, 7), dtype=np.int64)
+        row = np.zeros(7, dtype=np.int64)
+        for c in range(nc):
+            self._lib.orc_afmm_cell(self._h, c, row.ctypes.data_as(_lp))
+            out[c] = row
+        return out
+
+    def perm(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int64)
+        self._lib.orc_afmm_perm(self._h, out.ctypes.data_as(_lp))
+        return out
+
+    def pairs(self, kind: str) -> np.ndarray:
+        k = {"near": 0, "far": 1}[kind]
+        cnt = self._lib.orc_afmm_pairs(self._h, k, None)
+        out = np.zeros((max(cnt, 1), 2), dtype=np.int64)
+        self._lib.orc_afmm_pairs(self._h, k, out.ctypes.data_as(_lp))
+        return out[:cnt]
+
+
+def afmm_field(pos, mom, p, theta, s, box=None):
+    """Run the adaptive-tree oracle; returns (H in input order, E, OracleAFMM)."""
+    f = OracleAFMM(pos, mom, p, theta, s, box)
+    f.run()
     return f.field(), f.energy(), f

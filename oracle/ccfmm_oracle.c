@@ -1020,3 +1020,393 @@ void orc_rotate_moments(i64 n, double *mom, uint64_t seed, uint64_t step, double
         m[2] = r[2];
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Adaptive-depth tree (a project extension; the paper's tree is complete,  */
+/* Sec. II and Appendix).  Readings taken here:                             */
+/*   - Cells are the uniform tree's cells (same box, split sequence and     */
+/*     point membership), but a cell is split only while it holds more than */
+/*     s points; empty children are not created.                             */
+/*   - Two cells of different levels are near when (r_A + r_B) / d > theta, */
+/*     r = half the cell diagonal, d = distance of the centres; for equal   */
+/*     levels this is the paper's 2r/d > alpha_m, evaluated exactly as the  */
+/*     uniform tree does.                                                   */
+/*   - createPartners with unequal levels: the near candidates N(c) of a    */
+/*     cell are cells of its level or coarser leaves.  A child of c takes   */
+/*     as candidates the children of every internal member of N(c) (its own */
+/*     sibling pair from c itself) and every leaf member as it is; a far    */
+/*     candidate goes to its Partners (M2L source), a near one stays in its  */
+/*     N.  At a leaf, near leaves become nearPartners (the finer cell keeps */
+/*     the coarser near leaf), and a near internal cell is refined against  */
+/*     the leaf: its far descendants become Partners of the leaf, its near  */
+/*     leaves nearPartners.                                                 */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int level;
+    i64 ic[3];            /* integer coordinates at its level */
+    i64 parent, child[2]; /* -1 when absent */
+    i64 p0, np;           /* points perm[p0 .. p0+np) */
+    ivec cand, farp, nearp;
+} acell;
+
+typedef struct orc_afmm {
+    i64 n;
+    int p;
+    double theta, s;
+    double *pos, *mom;
+    double lo[3], ext[3];
+    int axis[ORC_MAXL + 1];
+    int nsplit[ORC_MAXL + 1][3];
+    acell *c;
+    i64 nc, cap;
+    i64 *perm;
+    ftable F;
+    double *Q, *V, *H;    /* nc x T(p), nc x T(p), n x 3 */
+} orc_afmm;
+
+static void a_widths(const orc_afmm *f, int l, double w[3])
+{
+    for (int a = 0; a < 3; ++a) w[a] = f->ext[a] / ipow(2.0, f->nsplit[l][a]);
+}
+
+static void a_center(const orc_afmm *f, i64 c, double cen[3])
+{
+    double w[3];
+    a_widths(f, f->c[c].level, w);
+    for (int a = 0; a < 3; ++a) cen[a] = f->lo[a] + ((double)f->c[c].ic[a] + 0.5) * w[a];
+}
+
+/* coordinate of x along axis a at a level with n_a = 2^ns cells (the uniform
+ * tree's membership rule) */
+static i64 a_coord(const orc_afmm *f, int a, int ns, double x)
+{
+    i64 na = (i64)1 << ns;
+    double t = (x - f->lo[a]) * (double)na / f->ext[a];
+    i64 ca = (i64)floor(t);
+    if (ca > na - 1) ca = na - 1;
+    if (ca < 0) ca = 0;
+    return ca;
+}
+
+static i64 a_new_cell(orc_afmm *f)
+{
+    if (f->nc == f->cap) {
+        f->cap = f->cap ? 2 * f->cap : 64;
+        f->c = (acell *)realloc(f->c, sizeof(acell) * (size_t)f->cap);
+    }
+    memset(&f->c[f->nc], 0, sizeof(acell));
+    f->c[f->nc].parent = f->c[f->nc].child[0] = f->c[f->nc].child[1] = -1;
+    return f->nc++;
+}
+
+/* split cell c while it holds more than s points */
+static void a_split(orc_afmm *f, i64 c)
+{
+    if ((double)f->c[c].np <= f->s || f->c[c].level >= ORC_MAXL) return;
+    const int l = f->c[c].level + 1, a = f->axis[l];
+    const i64 p0 = f->c[c].p0, np = f->c[c].np;
+    /* stable partition by the child bit along the split axis: the lower
+     * child's points, then the upper child's, each in their old order */
+    i64 *tmp = (i64 *)malloc(sizeof(i64) * (size_t)np);
+    i64 nlo = 0, k = 0;
+    for (i64 e = 0; e < np; ++e) {
+        i64 i = f->perm[p0 + e];
+        if ((a_coord(f, a, f->nsplit[l][a], f->pos[3 * i + a]) & 1) == 0) tmp[k++] = i;
+    }
+    nlo = k;
+    for (i64 e = 0; e < np; ++e) {
+        i64 i = f->perm[p0 + e];
+        if ((a_coord(f, a, f->nsplit[l][a], f->pos[3 * i + a]) & 1) == 1) tmp[k++] = i;
+    }
+    memcpy(&f->perm[p0], tmp, sizeof(i64) * (size_t)np);
+    free(tmp);
+    for (int side = 0; side < 2; ++side) {
+        i64 cnt = side == 0 ? nlo : np - nlo;
+        if (cnt == 0) continue;
+        i64 ch = a_new_cell(f);
+        acell *C = &f->c[c], *H = &f->c[ch];
+        H->level = l;
+        H->parent = c;
+        for (int b = 0; b < 3; ++b) H->ic[b] = C->ic[b];
+        H->ic[a] = 2 * C->ic[a] + side;
+        H->p0 = side == 0 ? p0 : p0 + nlo;
+        H->np = cnt;
+        C->child[side] = ch;
+        a_split(f, ch);
+    }
+}
+
+static int a_is_leaf(const orc_afmm *f, i64 c) { return f->c[c].child[0] < 0 && f->c[c].child[1] < 0; }
+
+static int a_near(const orc_afmm *f, i64 x, i64 y)
+{
+    double cx[3], cy[3], wx[3], wy[3];
+    a_center(f, x, cx);
+    a_center(f, y, cy);
+    a_widths(f, f->c[x].level, wx);
+    a_widths(f, f->c[y].level, wy);
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) d2 += (cx[a] - cy[a]) * (cx[a] - cy[a]);
+    if (f->c[x].level == f->c[y].level) {
+        double w2 = wx[0] * wx[0] + wx[1] * wx[1] + wx[2] * wx[2];
+        return w2 > f->theta * f->theta * d2 * (1.0 + 1e-12);
+    }
+    double rx = 0.5 * sqrt(wx[0] * wx[0] + wx[1] * wx[1] + wx[2] * wx[2]);
+    double ry = 0.5 * sqrt(wy[0] * wy[0] + wy[1] * wy[1] + wy[2] * wy[2]);
+    return (rx + ry) * (rx + ry) > f->theta * f->theta * d2 * (1.0 + 1e-12);
+}
+
+static void a_consider(orc_afmm *f, i64 ci, i64 b)
+{
+    if (b == ci || a_near(f, ci, b))
+        ivec_push(&f->c[ci].cand, b);
+    else
+        ivec_push(&f->c[ci].farp, b);
+}
+
+/* leaf c against the subtree of a near internal cell a */
+static void a_resolve(orc_afmm *f, i64 c, i64 a)
+{
+    for (int s = 0; s < 2; ++s) {
+        i64 b = f->c[a].child[s];
+        if (b < 0) continue;
+        if (!a_near(f, c, b))
+            ivec_push(&f->c[c].farp, b);
+        else if (a_is_leaf(f, b))
+            ivec_push(&f->c[c].nearp, b);
+        else
+            a_resolve(f, c, b);
+    }
+}
+
+static void a_partners(orc_afmm *f, i64 c)
+{
+    if (a_is_leaf(f, c)) {
+        for (i64 e = 0; e < f->c[c].cand.n; ++e) {
+            i64 a = f->c[c].cand.v[e];
+            if (a == c || a_is_leaf(f, a))
+                ivec_push(&f->c[c].nearp, a);
+            else
+                a_resolve(f, c, a);
+        }
+        return;
+    }
+    for (int s = 0; s < 2; ++s) {
+        i64 ci = f->c[c].child[s];
+        if (ci < 0) continue;
+        for (i64 e = 0; e < f->c[c].cand.n; ++e) {
+            i64 a = f->c[c].cand.v[e];
+            if (a == c) {
+                for (int t = 0; t < 2; ++t)
+                    if (f->c[c].child[t] >= 0) a_consider(f, ci, f->c[c].child[t]);
+            } else if (a_is_leaf(f, a)) {
+                a_consider(f, ci, a);
+            } else {
+                for (int t = 0; t < 2; ++t)
+                    if (f->c[a].child[t] >= 0) a_consider(f, ci, f->c[a].child[t]);
+            }
+        }
+    }
+    for (int s = 0; s < 2; ++s)
+        if (f->c[c].child[s] >= 0) a_partners(f, f->c[c].child[s]);
+}
+
+/* Tree and lists for n points; s: split while a cell holds more than s
+ * points; box as for the uniform tree (NULL: widened bounding box). */
+orc_afmm *orc_afmm_new(i64 n, const double *pos, const double *mom, int p, double theta, double s,
+                       const double *box)
+{
+    if (n < 1 || p < 1 || p > ORC_MAXP || !(theta > 0.0 && theta < 1.0) || !(s >= 1.0)) return NULL;
+    orc_afmm *f = (orc_afmm *)calloc(1, sizeof(orc_afmm));
+    f->n = n;
+    f->p = p;
+    f->theta = theta;
+    f->s = s;
+    f->pos = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    f->mom = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    memcpy(f->pos, pos, sizeof(double) * 3 * (size_t)n);
+    memcpy(f->mom, mom, sizeof(double) * 3 * (size_t)n);
+    /* the uniform tree's box and split sequence */
+    orc_fmm *u = orc_fmm_new(n, pos, mom, p, theta, s, box);
+    if (!u) {
+        free(f->pos);
+        free(f->mom);
+        free(f);
+        return NULL;
+    }
+    for (int a = 0; a < 3; ++a) {
+        f->lo[a] = u->lo[a];
+        f->ext[a] = u->ext[a];
+    }
+    memcpy(f->axis, u->axis, sizeof(f->axis));
+    memcpy(f->nsplit, u->nsplit, sizeof(f->nsplit));
+    orc_fmm_free(u);
+
+    f->perm = (i64 *)malloc(sizeof(i64) * (size_t)n);
+    for (i64 i = 0; i < n; ++i) f->perm[i] = i;
+    i64 root = a_new_cell(f);
+    f->c[root].level = 0;
+    f->c[root].p0 = 0;
+    f->c[root].np = n;
+    a_split(f, root);
+    /* lists: the root is its own near candidate */
+    ivec_push(&f->c[root].cand, root);
+    a_partners(f, root);
+
+    ftable_make(&f->F, 2 * p);
+    int T = orc_nterms(p);
+    f->Q = (double *)calloc((size_t)f->nc * T, sizeof(double));
+    f->V = (double *)calloc((size_t)f->nc * T, sizeof(double));
+    f->H = (double *)calloc(3 * (size_t)n, sizeof(double));
+    return f;
+}
+
+void orc_afmm_free(orc_afmm *f)
+{
+    if (!f) return;
+    for (i64 c = 0; c < f->nc; ++c) {
+        free(f->c[c].cand.v);
+        free(f->c[c].farp.v);
+        free(f->c[c].nearp.v);
+    }
+    free(f->c);
+    free(f->perm);
+    free(f->pos);
+    free(f->mom);
+    ftable_free(&f->F);
+    free(f->Q);
+    free(f->V);
+    free(f->H);
+    free(f);
+}
+
+/* children are created after their parent, so index order is top-down and
+ * reverse index order bottom-up */
+static void a_upward(orc_afmm *f, const mlist *ml)
+{
+    int T = orc_nterms(f->p);
+    memset(f->Q, 0, sizeof(double) * (size_t)f->nc * T);
+    for (i64 c = f->nc - 1; c >= 0; --c) {
+        double cen[3];
+        a_center(f, c, cen);
+        double *Q = &f->Q[(size_t)c * T];
+        if (a_is_leaf(f, c)) {
+            /* Eq. multipolemoments about the leaf centre */
+            for (i64 e = 0; e < f->c[c].np; ++e) {
+                i64 i = f->perm[f->c[c].p0 + e];
+                p2m_one(ml, f->p, cen, &f->pos[3 * i], &f->mom[3 * i], Q);
+            }
+        } else {
+            /* Eq. momentshift from each child */
+            for (int s = 0; s < 2; ++s) {
+                i64 ch = f->c[c].child[s];
+                if (ch < 0) continue;
+                double cc[3], rel[3];
+                a_center(f, ch, cc);
+                for (int a = 0; a < 3; ++a) rel[a] = cc[a] - cen[a];
+                m2m_one(ml, f->p, rel, &f->Q[(size_t)ch * T], Q);
+            }
+        }
+    }
+}
+
+static void a_downward(orc_afmm *f, const mlist *ml)
+{
+    int T = orc_nterms(f->p);
+    memset(f->V, 0, sizeof(double) * (size_t)f->nc * T);
+    double *Dbuf = (double *)malloc(sizeof(double) * (size_t)f->F.T);
+    for (i64 c = 0; c < f->nc; ++c) {
+        double cen[3];
+        a_center(f, c, cen);
+        double *V = &f->V[(size_t)c * T];
+        i64 par = f->c[c].parent;
+        if (par >= 0) {
+            /* Eq. taylorshift from the parent */
+            double cp[3], rel[3];
+            a_center(f, par, cp);
+            for (int a = 0; a < 3; ++a) rel[a] = cen[a] - cp[a];
+            l2l_one(ml, f->p, rel, &f->V[(size_t)par * T], V);
+        }
+        /* Eq. taylorcalc from every Partner (any level) */
+        for (i64 e = 0; e < f->c[c].farp.n; ++e) {
+            i64 b = f->c[c].farp.v[e];
+            double cb[3], rel[3];
+            a_center(f, b, cb);
+            for (int a = 0; a < 3; ++a) rel[a] = cen[a] - cb[a];
+            m2l_one(&f->F, f->p, 2 * f->p, rel, &f->Q[(size_t)b * T], V, Dbuf);
+        }
+        if (!a_is_leaf(f, c)) continue;
+        /* Eq. H (L2P) and the near field over nearPartners, j != i */
+        for (i64 e = 0; e < f->c[c].np; ++e) {
+            i64 i = f->perm[f->c[c].p0 + e];
+            double h[3] = {0.0, 0.0, 0.0};
+            double r[3] = {f->pos[3 * i] - cen[0], f->pos[3 * i + 1] - cen[1], f->pos[3 * i + 2] - cen[2]};
+            l2p_one(ml, f->p, r, V, h);
+            for (i64 q = 0; q < f->c[c].nearp.n; ++q) {
+                i64 b = f->c[c].nearp.v[q];
+                for (i64 g = 0; g < f->c[b].np; ++g) {
+                    i64 j = f->perm[f->c[b].p0 + g];
+                    if (j == i) continue;
+                    pair_field(&f->pos[3 * i], &f->pos[3 * j], &f->mom[3 * j], h);
+                }
+            }
+            for (int a = 0; a < 3; ++a) f->H[3 * i + a] = h[a];
+        }
+    }
+    free(Dbuf);
+}
+
+void orc_afmm_run(orc_afmm *f)
+{
+    mlist ml;
+    mlist_make(&ml, f->p);
+    a_upward(f, &ml);
+    a_downward(f, &ml);
+    mlist_free(&ml);
+}
+
+void orc_afmm_field(const orc_afmm *f, double *H) { memcpy(H, f->H, sizeof(double) * 3 * (size_t)f->n); }
+
+double orc_afmm_energy(const orc_afmm *f)
+{
+    double e = 0.0;
+    for (i64 i = 0; i < f->n; ++i)
+        e += f->mom[3 * i] * f->H[3 * i] + f->mom[3 * i + 1] * f->H[3 * i + 1] +
+             f->mom[3 * i + 2] * f->H[3 * i + 2];
+    return -0.5 * e;
+}
+
+i64 orc_afmm_ncells(const orc_afmm *f) { return f->nc; }
+
+/* level, parent, child0, child1, first point, point count, leaf flag */
+void orc_afmm_cell(const orc_afmm *f, i64 c, i64 out[7])
+{
+    out[0] = f->c[c].level;
+    out[1] = f->c[c].parent;
+    out[2] = f->c[c].child[0];
+    out[3] = f->c[c].child[1];
+    out[4] = f->c[c].p0;
+    out[5] = f->c[c].np;
+    out[6] = a_is_leaf(f, c);
+}
+
+void orc_afmm_perm(const orc_afmm *f, i64 *out) { memcpy(out, f->perm, sizeof(i64) * (size_t)f->n); }
+
+/* (cell, partner) pairs: kind 0 nearPartners of leaves, 1 Partners (far);
+ * returns the count, fills out when non-NULL */
+i64 orc_afmm_pairs(const orc_afmm *f, int kind, i64 *out)
+{
+    i64 k = 0;
+    for (i64 c = 0; c < f->nc; ++c) {
+        const ivec *v = kind ? &f->c[c].farp : &f->c[c].nearp;
+        for (i64 e = 0; e < v->n; ++e) {
+            if (out) {
+                out[2 * k] = c;
+                out[2 * k + 1] = v->v[e];
+            }
+            ++k;
+        }
+    }
+    return k;
+}

@@ -14,6 +14,7 @@ import pytest
 
 import oracle as O
 from paper_0810_0233_gb300 import workloads as W
+import test_oracle_adaptive as A
 import test_oracle_pins as P
 
 SRC = os.path.join(os.path.dirname(O.__file__), "ccfmm_oracle.c")
@@ -64,6 +65,18 @@ MUTANTS = {
     "fmm_ignores_truncation": (
         "m2l_one(&f->F, f->p, f->maxdeg, rel,",
         "m2l_one(&f->F, f->p, 2 * f->p, rel,"),
+    "adaptive_far_descendant_dropped": (
+        "            ivec_push(&f->c[c].farp, b);",
+        "            (void)b;"),
+    "adaptive_coarse_leaf_dropped": (
+        "                a_consider(f, ci, a);",
+        "                (void)ci;"),
+    "adaptive_m2m_offset_reversed": (
+        "for (int a = 0; a < 3; ++a) rel[a] = cc[a] - cen[a];",
+        "for (int a = 0; a < 3; ++a) rel[a] = cen[a] - cc[a];"),
+    "adaptive_splits_at_s": (
+        "if ((double)f->c[c].np <= f->s",
+        "if ((double)f->c[c].np < f->s"),
     "leaf_not_self_near": (
         "ivec_push(&f->nearp[c], c);",
         "(void)0;"),
@@ -86,7 +99,9 @@ PINS = [P.pin_axial_equatorial, P.pin_field_is_minus_grad_potential, P.pin_pair_
         P.pin_p2m_single_dipole, P.pin_p2m_charge_limit, P.pin_multipole_potential,
         P.pin_m2m_exact, P.pin_l2l_l2p, P.pin_l2p_gradient, P.pin_m2l_convergence,
         P.pin_worked_examples, P.pin_eq_so, P.pin_fmm_converges, P.pin_root_moments,
-        P.pin_total_degree_is_taylor, P.pin_fmm_total_degree_brute_force, _c1_checks]
+        P.pin_total_degree_is_taylor, P.pin_fmm_total_degree_brute_force, _c1_checks,
+        A.pin_adaptive_matches_uniform, A.pin_adaptive_coverage, A.pin_adaptive_converges,
+        A.pin_adaptive_all_near_is_direct, A.pin_adaptive_tree]
 
 
 def _run_pins():
