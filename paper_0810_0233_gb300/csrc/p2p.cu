@@ -90,38 +90,61 @@ __device__ __forceinline__ void stripe_range(int len, int S, int stripe, int &j0
 }
 
 // Smooth field (Eq. H, H = -grad V) of one target from its leaf's Taylor
-// coefficients vs[] (multi-indices mi[]), powers x^j / j! kept in pw[i * ps]
-// for i = d * PMAX + j (ps: the caller's stride, so that the lanes of a warp
-// use consecutive words and no bank twice).
-template <typename real>
-__device__ __forceinline__ void l2p_one(int p, int K, const real *vs, const unsigned *mi, real *pw,
-                                        int ps, real x, real y, real z, real &h0, real &h1,
-                                        real &h2)
+// coefficients vs[] (column t - 1 holds the multi-index t), x relative to
+// the leaf centre:  H_a = -sum_{|m| <= p-1} V_{m+e_a} x^m / m!  (returns the
+// three sums; the caller subtracts them).  The order
+// P = p is a template parameter: the loops over m = (mx, my, mz) unroll, the
+// monomial x^m/m! is one product of the per-axis powers' partial products,
+// and each term is three FMAs on broadcast coefficient loads.  The fused
+// near-field epilogue and the standalone L2P kernel both use it, so the two
+// evaluation paths give the same bits.
+template <typename real> struct Sum3 {
+    real x, y, z;
+};
+
+template <typename real, int P>
+__device__ __forceinline__ Sum3<real> l2p_fixed(const real *vs, real x, real y, real z)
 {
-    const real inv[PMAX] = {(real)0, (real)1, (real)0.5, (real)1 / (real)3, (real)0.25,
-                            (real)0.2, (real)1 / (real)6, (real)1 / (real)7};
-    real c[3] = {x, y, z};
+    real px[P], py[P], pz[P];
+    px[0] = py[0] = pz[0] = (real)1;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        real t = (real)1;
-        pw[(d * PMAX) * ps] = t;
+    for (int j = 1; j < P; ++j) {
+        const real inv = (real)1 / (real)j;  // j is a compile-time constant here
+        px[j] = px[j - 1] * x * inv;
+        py[j] = py[j - 1] * y * inv;
+        pz[j] = pz[j - 1] * z * inv;
+    }
+    real s0 = (real)0, s1 = (real)0, s2 = (real)0;
 #pragma unroll
-        for (int j = 1; j < PMAX; ++j) {
-            if (j < p) {
-                t = t * c[d] * inv[j];
-                pw[(d * PMAX + j) * ps] = t;
+    for (int mx = 0; mx < P; ++mx) {
+#pragma unroll
+        for (int my = 0; my < P - mx; ++my) {
+            const real b = px[mx] * py[my];
+#pragma unroll
+            for (int mz = 0; mz < P - mx - my; ++mz) {
+                const real mono = b * pz[mz];
+                s0 += vs[midx(mx + 1, my, mz) - 1] * mono;
+                s1 += vs[midx(mx, my + 1, mz) - 1] * mono;
+                s2 += vs[midx(mx, my, mz + 1) - 1] * mono;
             }
         }
     }
-    for (int k = 0; k < K; ++k) {
-        unsigned n = mi[k];
-        int nx = (int)(n & 31u), ny = (int)((n >> 5) & 31u), nz = (int)((n >> 10) & 31u);
-        real v = vs[k];
-        // loads only inside the branches: there every index is at most p - 1
-        // (|n| <= p and the derivative's component is >= 1)
-        if (nx > 0) h0 -= v * pw[(nx - 1) * ps] * pw[(PMAX + ny) * ps] * pw[(2 * PMAX + nz) * ps];
-        if (ny > 0) h1 -= v * pw[nx * ps] * pw[(PMAX + ny - 1) * ps] * pw[(2 * PMAX + nz) * ps];
-        if (nz > 0) h2 -= v * pw[nx * ps] * pw[(PMAX + ny) * ps] * pw[(2 * PMAX + nz - 1) * ps];
+    return Sum3<real>{s0, s1, s2};
+}
+
+// the sums of l2p_fixed for a run-time order (the field is H - sums)
+template <typename real>
+__device__ __forceinline__ Sum3<real> l2p_eval(int p, const real *vs, real x, real y, real z)
+{
+    switch (p) {
+    case 1: return l2p_fixed<real, 1>(vs, x, y, z);
+    case 2: return l2p_fixed<real, 2>(vs, x, y, z);
+    case 3: return l2p_fixed<real, 3>(vs, x, y, z);
+    case 4: return l2p_fixed<real, 4>(vs, x, y, z);
+    case 5: return l2p_fixed<real, 5>(vs, x, y, z);
+    case 6: return l2p_fixed<real, 6>(vs, x, y, z);
+    case 7: return l2p_fixed<real, 7>(vs, x, y, z);
+    default: return l2p_fixed<real, 8>(vs, x, y, z);
     }
 }
 
@@ -152,7 +175,6 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
     int *est = reinterpret_cast<int *>(esh + P2P_NE);     // [P2P_NE] source start
     int *epf = est + P2P_NE;                              // [P2P_NE + 1] prefix of counts
     real *vs = reinterpret_cast<real *>(epf + P2P_NE + 4);  // [KP]
-    unsigned *mi = reinterpret_cast<unsigned *>(vs + KP);   // [KP]
     __shared__ int wsum[P2P_T / 32];
 
     const long long key = blockIdx.x;
@@ -165,12 +187,7 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
     // V == nullptr: near field only (L2P by k_l2p once V is complete)
     const bool with_l2p = V != nullptr;
     if (with_l2p)
-        for (int c = tid; c < K; c += P2P_T) {
-            vs[c] = (real)V[hid * KP + c];
-            int x, y, z;
-            midx_inv(c + 1, x, y, z);
-            mi[c] = (unsigned)x | ((unsigned)y << 5) | ((unsigned)z << 10);
-        }
+        for (int c = tid; c < K; c += P2P_T) vs[c] = (real)V[hid * KP + c];
     const double wx = g->w[L][0], wy = g->w[L][1], wz = g->w[L][2];
 
     for (int tb = 0; tb < nt; tb += P2P_TPT * P2P_T) {
@@ -298,12 +315,14 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
         }
         __syncthreads();
         if (tid < ngrp) {
-            real *pw = reinterpret_cast<real *>(sp) + tid;  // stride P2P_T
 #pragma unroll
             for (int i = 0; i < P2P_TPT; ++i) {
-                if (with_l2p)
-                    l2p_one<real>(p, K, vs, mi, pw, P2P_T, tx[i][0], tx[i][1], tx[i][2], f[i][0],
-                                  f[i][1], f[i][2]);
+                if (with_l2p) {
+                    const Sum3<real> sl = l2p_eval<real>(p, vs, tx[i][0], tx[i][1], tx[i][2]);
+                    f[i][0] -= sl.x;
+                    f[i][1] -= sl.y;
+                    f[i][2] -= sl.z;
+                }
                 R4 o;
                 o.x = f[i][0];
                 o.y = f[i][1];
@@ -323,9 +342,8 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_sta
 {
     size_t smem = (size_t)P2P_CH * (sizeof(typename vec4<real>::t) + sizeof(typename vec2<real>::t)) +
                   (size_t)P2P_NE * sizeof(typename vec4<real>::t) + (2 * P2P_NE + 4) * sizeof(int) +
-                  (size_t)KP * (sizeof(real) + sizeof(unsigned)) + 64;
-    static_assert(P2P_CH * 4 >= 3 * PMAX * P2P_T && P2P_CH * 4 >= 3 * P2P_TPT * P2P_T,
-                  "the stripe sums and the L2P powers reuse the staging buffer");
+                  (size_t)KP * sizeof(real) + 64;
+    static_assert(P2P_CH * 4 >= 3 * P2P_TPT * P2P_T, "the stripe sums reuse the staging buffer");
     cudaFuncSetAttribute(k_p2p<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
     k_p2p<real><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start, near_start, near,
@@ -337,36 +355,28 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_sta
 // operations in the same order as the fused epilogue.
 constexpr int L2P_W = 4;  // leaves (warps) per block
 
-template <typename real>
-__global__ void __launch_bounds__(32 * L2P_W) k_l2p(int p, int KP, int L, const int *leaf_start,
+template <typename real, int P>
+__global__ void __launch_bounds__(32 * L2P_W) k_l2p(int KP, int L, const int *leaf_start,
                                                     const typename vec4<real>::t *A,
                                                     const double *V, typename vec4<real>::t *H)
 {
     __shared__ real vs[L2P_W][nterms(PMAX)];
-    __shared__ unsigned mi[nterms(PMAX)];
-    __shared__ real pw[L2P_W][3 * PMAX][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int K = nterms(p) - 1;
-    for (int c = threadIdx.x; c < K; c += 32 * L2P_W) {
-        int x, y, z;
-        midx_inv(c + 1, x, y, z);
-        mi[c] = (unsigned)x | ((unsigned)y << 5) | ((unsigned)z << 10);
-    }
+    constexpr int K = nterms(P) - 1;
     const long long key = (long long)blockIdx.x * L2P_W + w;
     const bool live = key < (1ll << L);
     const int t0 = live ? leaf_start[key] : 0, nt = live ? leaf_start[key + 1] - t0 : 0;
     const long long hid = (1ll << L) + key;
     if (nt > 0)
         for (int c = lane; c < K; c += 32) vs[w][c] = (real)V[hid * KP + c];
-    __syncthreads();
+    __syncwarp();
     for (int i = lane; i < nt; i += 32) {
         const typename vec4<real>::t a = A[t0 + i];
         typename vec4<real>::t h = H[t0 + i];
-        real f0 = h.x, f1 = h.y, f2 = h.z;
-        l2p_one<real>(p, K, vs[w], mi, &pw[w][0][lane], 32, a.x, a.y, a.z, f0, f1, f2);
-        h.x = f0;
-        h.y = f1;
-        h.z = f2;
+        const Sum3<real> sl = l2p_fixed<real, P>(vs[w], a.x, a.y, a.z);
+        h.x -= sl.x;
+        h.y -= sl.y;
+        h.z -= sl.z;
         H[t0 + i] = h;
     }
 }
@@ -376,9 +386,15 @@ void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4
                 const double *V, typename vec4<real>::t *H, cudaStream_t s)
 {
     const long long nleaf = 1ll << L;
+    const unsigned nb = (unsigned)((nleaf + L2P_W - 1) / L2P_W);
     note_launch();
-    k_l2p<real><<<(unsigned)((nleaf + L2P_W - 1) / L2P_W), 32 * L2P_W, 0, s>>>(p, KP, L,
-                                                                             leaf_start, A, V, H);
+#define L2PK(PV)                                                                                 \
+    case PV: k_l2p<real, PV><<<nb, 32 * L2P_W, 0, s>>>(KP, L, leaf_start, A, V, H); break;
+    switch (p) {
+        L2PK(1) L2PK(2) L2PK(3) L2PK(4) L2PK(5) L2PK(6) L2PK(7) L2PK(8)
+    default: break;
+    }
+#undef L2PK
 }
 
 // unpermute to input order in FP64 and form per-block partial sums of m.H
