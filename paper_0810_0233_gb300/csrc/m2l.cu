@@ -259,26 +259,32 @@ __global__ void __launch_bounds__(KP * 4) k_m2l_f32(int p, const Tile *tiles, co
 }
 
 // V_n of each field cell = (-1)^|n| h^-(|n|+2) * sum over the tile's items
-// of the partial sums, in FP64 and in item order.
+// of the partial sums, in FP64 and in item order.  A tile's outputs are
+// split over RED_SPLIT blocks (blockIdx.y); each block forms the scale
+// en[n] = (-1)^|n| h^-(|n|+2) by repeated multiplication with 1/h (FP64
+// pow and division are slow on this part: one division per block).
+constexpr int RED_SPLIT = 4;
+
 __global__ void k_m2l_reduce(int p, int KP, const Tile *tiles, const int *tile_item0,
                              const int *tile_nitems, const float *Ps, const Geom *g, double *V)
 {
-    // en[n] = (-1)^|n| h^-(|n|+2) of the tile's level, once per block (FP64
-    // pow is costly; one per coefficient, not one per output)
     extern __shared__ double en[];
     const int tile = blockIdx.x;
     const Tile t = tiles[tile];
     const int K = nterms(p) - 1;
-    const double h = g->h[t.level];
+    const double hinv = 1.0 / g->h[t.level];
     for (int n = threadIdx.x; n < K; n += blockDim.x) {
         int nx, ny, nz;
         midx_inv(n + 1, nx, ny, nz);
         const int kn = nx + ny + nz;
-        en[n] = ((kn & 1) ? -1.0 : 1.0) * pow(h, -(double)(kn + 2));
+        double q = hinv * hinv;
+        for (int d = 0; d < kn; ++d) q *= hinv;
+        en[n] = (kn & 1) ? -q : q;
     }
     __syncthreads();
     const int i0 = tile_item0[tile], ni = tile_nitems[tile];
-    for (int j = threadIdx.x; j < t.nt * K; j += blockDim.x) {
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < t.nt * K;
+         j += gridDim.y * blockDim.x) {
         int ti = j / K, n = j - ti * K;
         double s = 0.0;
         for (int it = 0; it < ni; ++it) s += (double)Ps[((long long)(i0 + it) * TT + ti) * KP + n];
@@ -330,8 +336,8 @@ void launch_m2l_reduce(int p, int KP, const Tile *tiles, int ntiles, const int *
 {
     if (ntiles <= 0) return;
     note_launch();
-    k_m2l_reduce<<<ntiles, 256, sizeof(double) * (nterms(p) - 1), s>>>(p, KP, tiles, tile_item0,
-                                                                     tile_nitems, Ps, g, V);
+    k_m2l_reduce<<<dim3((unsigned)ntiles, RED_SPLIT), 256, sizeof(double) * (nterms(p) - 1), s>>>(
+        p, KP, tiles, tile_item0, tile_nitems, Ps, g, V);
 }
 
 template <typename real, int KP, int KC>
