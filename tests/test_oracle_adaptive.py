@@ -9,7 +9,8 @@ Independent statements it is checked against:
     exactly one far pair (T, S) with T holding i and S holding j;
   * the direct dipole sum: the error falls with p, and with every pair near
     (a tiny opening angle) the method is the direct sum;
-  * the tree's own definition: leaves hold at most s points, split cells more.
+  * the tree's own definition: leaves hold at most s points, split cells more;
+  * symmetry of the near and far relations, which the near test implies.
 """
 import numpy as np
 
@@ -88,6 +89,19 @@ def pin_adaptive_all_near_is_direct():
     return len(f.pairs("far")) == 0 and _rel(H, Hd) < 1e-13
 
 
+def pin_adaptive_symmetry():
+    """The lists are symmetric: (A, B) is a near pair iff (B, A) is, and the
+    same for far pairs, including pairs of unequal levels (both sides stop
+    at the same cell of the other's subtree: the near test is symmetric)."""
+    pos, mom = _clustered(400, 65)
+    f = O.OracleAFMM(pos, mom, 2, 0.5, 4.0)
+    ok = True
+    for kind in ("near", "far"):
+        pr = {tuple(map(int, x)) for x in f.pairs(kind)}
+        ok &= all((b, a) in pr for a, b in pr)
+    return bool(ok)
+
+
 def pin_adaptive_tree():
     """Leaves hold at most s points; split cells more; children partition."""
     pos, mom = _clustered(500, 64)
@@ -120,6 +134,10 @@ def test_adaptive_converges():
 
 def test_adaptive_all_near_is_direct():
     assert pin_adaptive_all_near_is_direct()
+
+
+def test_adaptive_symmetry():
+    assert pin_adaptive_symmetry()
 
 
 def test_adaptive_tree():

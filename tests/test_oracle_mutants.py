@@ -101,7 +101,7 @@ PINS = [P.pin_axial_equatorial, P.pin_field_is_minus_grad_potential, P.pin_pair_
         P.pin_worked_examples, P.pin_eq_so, P.pin_fmm_converges, P.pin_root_moments,
         P.pin_total_degree_is_taylor, P.pin_fmm_total_degree_brute_force, _c1_checks,
         A.pin_adaptive_matches_uniform, A.pin_adaptive_coverage, A.pin_adaptive_converges,
-        A.pin_adaptive_all_near_is_direct, A.pin_adaptive_tree]
+        A.pin_adaptive_all_near_is_direct, A.pin_adaptive_symmetry, A.pin_adaptive_tree]
 
 
 def _run_pins():
