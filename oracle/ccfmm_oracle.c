@@ -620,6 +620,54 @@ static void create_partners(orc_fmm *f, i64 c)
     }
 }
 
+/* The box (given, or the bounding box widened by 2^-20 of its largest
+ * extent) and the split sequence: at each level halve the currently widest
+ * axis, ties x<y<z (Sec. IV examples).  Shared by the complete and the
+ * adaptive tree. */
+static void tree_geometry(i64 n, const double *pos, const double *box, double lo[3], double ext[3],
+                          int axis[ORC_MAXL + 1], int nsplit[ORC_MAXL + 1][3])
+{
+    /* box: given, or the bounding box widened by 2^-20 of the largest extent */
+    if (box) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = box[a];
+            ext[a] = box[3 + a] - box[a];
+        }
+    } else {
+        double blo[3], bhi[3];
+        for (int a = 0; a < 3; ++a) blo[a] = bhi[a] = pos[a];
+        for (i64 i = 1; i < n; ++i)
+            for (int a = 0; a < 3; ++a) {
+                if (pos[3 * i + a] < blo[a]) blo[a] = pos[3 * i + a];
+                if (pos[3 * i + a] > bhi[a]) bhi[a] = pos[3 * i + a];
+            }
+        double m = 0.0;
+        for (int a = 0; a < 3; ++a)
+            if (bhi[a] - blo[a] > m) m = bhi[a] - blo[a];
+        if (m == 0.0) m = 1.0;
+        double pad = m * ipow(0.5, 20);
+        for (int a = 0; a < 3; ++a) {
+            double l0 = blo[a] - pad, h0 = bhi[a] + pad;
+            lo[a] = l0;
+            ext[a] = h0 - l0;
+        }
+    }
+
+    /* split sequence: at each level halve the currently widest axis, ties x<y<z */
+    nsplit[0][0] = nsplit[0][1] = nsplit[0][2] = 0;
+    axis[0] = -1;
+    for (int l = 1; l <= ORC_MAXL; ++l) {
+        double w[3];
+        for (int b = 0; b < 3; ++b) w[b] = ext[b] / ipow(2.0, nsplit[l - 1][b]);
+        int a = 0;
+        if (w[1] > w[a]) a = 1;
+        if (w[2] > w[a]) a = 2;
+        axis[l] = a;
+        for (int b = 0; b < 3; ++b) nsplit[l][b] = nsplit[l - 1][b];
+        nsplit[l][a] += 1;
+    }
+}
+
 orc_fmm *orc_fmm_new(i64 n, const double *pos, const double *mom, int p, double theta,
                      double leaf_size, const double *box)
 {
@@ -635,45 +683,7 @@ orc_fmm *orc_fmm_new(i64 n, const double *pos, const double *mom, int p, double 
     memcpy(f->pos, pos, sizeof(double) * 3 * (size_t)n);
     memcpy(f->mom, mom, sizeof(double) * 3 * (size_t)n);
 
-    /* box: given, or the bounding box widened by 2^-20 of the largest extent */
-    if (box) {
-        for (int a = 0; a < 3; ++a) {
-            f->lo[a] = box[a];
-            f->ext[a] = box[3 + a] - box[a];
-        }
-    } else {
-        double lo[3], hi[3];
-        for (int a = 0; a < 3; ++a) lo[a] = hi[a] = pos[a];
-        for (i64 i = 1; i < n; ++i)
-            for (int a = 0; a < 3; ++a) {
-                if (pos[3 * i + a] < lo[a]) lo[a] = pos[3 * i + a];
-                if (pos[3 * i + a] > hi[a]) hi[a] = pos[3 * i + a];
-            }
-        double m = 0.0;
-        for (int a = 0; a < 3; ++a)
-            if (hi[a] - lo[a] > m) m = hi[a] - lo[a];
-        if (m == 0.0) m = 1.0;
-        double pad = m * ipow(0.5, 20);
-        for (int a = 0; a < 3; ++a) {
-            double l0 = lo[a] - pad, h0 = hi[a] + pad;
-            f->lo[a] = l0;
-            f->ext[a] = h0 - l0;
-        }
-    }
-
-    /* split sequence: at each level halve the currently widest axis, ties x<y<z */
-    f->nsplit[0][0] = f->nsplit[0][1] = f->nsplit[0][2] = 0;
-    f->axis[0] = -1;
-    for (int l = 1; l <= ORC_MAXL; ++l) {
-        double w[3];
-        level_widths(f, l - 1, w);
-        int a = 0;
-        if (w[1] > w[a]) a = 1;
-        if (w[2] > w[a]) a = 2;
-        f->axis[l] = a;
-        for (int b = 0; b < 3; ++b) f->nsplit[l][b] = f->nsplit[l - 1][b];
-        f->nsplit[l][a] += 1;
-    }
+    tree_geometry(n, pos, box, f->lo, f->ext, f->axis, f->nsplit);
 
     /* depth: L minimising |N/nonempty_L - s|; N/nonempty_L never increases with
      * L, so the scan stops at the first L where it is <= s. */
@@ -1227,21 +1237,8 @@ orc_afmm *orc_afmm_new(i64 n, const double *pos, const double *mom, int p, doubl
     f->mom = (double *)malloc(sizeof(double) * 3 * (size_t)n);
     memcpy(f->pos, pos, sizeof(double) * 3 * (size_t)n);
     memcpy(f->mom, mom, sizeof(double) * 3 * (size_t)n);
-    /* the uniform tree's box and split sequence */
-    orc_fmm *u = orc_fmm_new(n, pos, mom, p, theta, s, box);
-    if (!u) {
-        free(f->pos);
-        free(f->mom);
-        free(f);
-        return NULL;
-    }
-    for (int a = 0; a < 3; ++a) {
-        f->lo[a] = u->lo[a];
-        f->ext[a] = u->ext[a];
-    }
-    memcpy(f->axis, u->axis, sizeof(f->axis));
-    memcpy(f->nsplit, u->nsplit, sizeof(f->nsplit));
-    orc_fmm_free(u);
+    /* the complete tree's box and split sequence */
+    tree_geometry(n, pos, box, f->lo, f->ext, f->axis, f->nsplit);
 
     f->perm = (i64 *)malloc(sizeof(i64) * (size_t)n);
     for (i64 i = 0; i < n; ++i) f->perm[i] = i;
