@@ -127,7 +127,7 @@ def workload(name="ferrofluid", n=1_000_000):
     return W.ferrofluid(n, side=100.0 * (n / 1e6) ** (1.0 / 3.0))
 
 
-def describe(name, n, leaf, p, theta):
+def describe(name, n, leaf, p, theta, precision=None, step=None):
     text = {
         "ferrofluid": "ferrofluid: N=%d uniform in [0,100]^3, min separation 0.5, unit moments "
                       "uniform on the sphere (seed 810235)" % n,
@@ -137,8 +137,9 @@ def describe(name, n, leaf, p, theta):
                        "vortex moments (seed 810236)" % n,
     }[name]
     return {"workload": text, "N": n, "p": p, "theta": theta, "leaf_size": leaf,
-            "precision": "FP32 bulk; FP64 D tensors and FP64 local-expansion accumulation",
-            "step": "tree + lists + D tables + field evaluation (P2M..P2P, unpermute)",
+            "precision": precision or "FP32 bulk; FP64 D tensors and FP64 local-expansion "
+                                      "accumulation",
+            "step": step or "tree + lists + D tables + field evaluation (P2M..P2P, unpermute)",
             "l2": "flushed between timed steps by a 256 MB write"}
 
 
@@ -209,19 +210,30 @@ def run_reference(args):
             if it >= args.warmup:
                 times.append(len(pos) / res["value"])
         config = describe_ensemble(len(off) - 1, len(pos), p, theta)
+        config["precision"] = "FP64 throughout (the CPU oracle)"
+        config["step"] = ("FP64 CPU oracle: whole FMM of random samples for about 5 s per step, "
+                          "fields/s over those samples (no rotation)")
+        config["l2"] = "not applicable (CPU)"
     else:
         pos, mom = workload(args.workload)
         for it in range(args.warmup + args.steps):
             res = cpu_oracle_sample(pos, mom, p, theta, nleaves=256, seed=100 + it)
             if it >= args.warmup:
                 times.append(len(pos) / res["value"])
-        config = describe(args.workload, len(pos), 0.74 * p * p, p, theta)
+        config = describe(args.workload, len(pos), 0.74 * p * p, p, theta,
+                          precision="FP64 throughout (the CPU oracle)",
+                          step="FP64 CPU oracle: tree, lists and upward pass over all dipoles, "
+                               "then the downward pass and near field of 256 random occupied "
+                               "leaves; the step time is extrapolated from those leaves to all "
+                               "occupied leaves (not a measured full evaluation)")
+        config["l2"] = "not applicable (CPU)"
     t = float(np.mean(times))
     value = len(pos) / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "fields/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "extrapolated": args.workload != "ensemble",
             "cpu_baseline": {"value": value, "unit": "fields/s", "cores": res["cores"],
                              "kind": "oracle", "sample": res["sample"]},
             "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0,

@@ -345,10 +345,14 @@ ccfmm_status fmm_select(ccfmm_mlp_t m, const double *positions, int64_t N, doubl
  * state.  It computes what ccfmm_direct_field computes (FP64 O(N^2) field,
  * j != i and coincident points skipped) and E = -1/2 sum_i m_i . H_i, and
  * allocates nothing: no cudaMalloc, cudaFree or allocating library call.
- *   positions, moments  N x 3 float64, DEVICE memory of the current device.
+ *   positions, moments  N x 3 float64, DEVICE memory of the current device
+ *                       (or managed memory); memory of another GPU is
+ *                       rejected with CCFMM_ERR_ARG.
  *   N                   1 <= N <= 4,194,304; larger N returns CCFMM_ERR_ARG.
- *   H_out               N x 3 float64, DEVICE memory, caller-owned.
- *   E_out               one float64, host or device memory.
+ *   H_out               N x 3 float64, DEVICE memory of the current device,
+ *                       caller-owned.
+ *   E_out               one float64, host memory or device memory of the
+ *                       current device (another GPU's: CCFMM_ERR_ARG).
  *   stream              cudaStream_t or NULL; the call synchronises it.
  * Scratch: a fixed array of 32,769 doubles (about 256 KB) in the library's
  * device memory, held on every GPU that loads the library until the process
@@ -357,8 +361,9 @@ ccfmm_status fmm_select(ccfmm_mlp_t m, const double *positions, int64_t N, doubl
  * capture.  All calls share the array and it keeps the last call's values;
  * every value a call reads is written earlier in the same call.  Calls whose
  * GPU work overlaps (other streams, other host threads) race on the array:
- * serialise them.  Errors: CCFMM_ERR_ARG for NULL, N out of range or
- * non-device arrays; CCFMM_ERR_CUDA.
+ * serialise them.  Errors: CCFMM_ERR_ARG for NULL, N out of range, or
+ * arrays that are not on the current device (the message names it);
+ * CCFMM_ERR_CUDA.
  * ---------------------------------------------------------------------- */
 ccfmm_status ccfmm_direct_field_energy_noalloc(const double *positions, const double *moments,
                                                int64_t N, double *H_out, double *E_out,

@@ -105,14 +105,22 @@ __global__ void k_direct_energy_final(const double *partial, long long nparts, d
 
 using namespace ccfmm;
 
-static bool na_is_device(const void *p)
+// Where a pointer lives, as this entry point needs it: memory that kernels
+// on device dev can use directly (device memory of dev, or managed memory),
+// memory of another device (never used: without peer access a kernel that
+// touched it could fault), or host memory (any other pointer).
+enum NaWhere { NA_HOST = 0, NA_THIS_DEVICE = 1, NA_OTHER_DEVICE = 2 };
+
+static NaWhere na_where(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return NA_HOST;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return NA_THIS_DEVICE;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? NA_THIS_DEVICE : NA_OTHER_DEVICE;
+    return NA_HOST;
 }
 
 extern "C" {
@@ -131,17 +139,26 @@ ccfmm_status ccfmm_direct_field_energy_noalloc(const double *positions, const do
                        "fixed scratch holds 32768 block sums)");
         return CCFMM_ERR_ARG;
     }
-    if (!na_is_device(positions) || !na_is_device(moments) || !na_is_device(H_out)) {
-        set_last_error("positions, moments and H_out must be device memory of the current "
-                       "device");
-        return CCFMM_ERR_ARG;
-    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
         cudaGetLastError();
         set_last_error("no usable current CUDA device");
         return CCFMM_ERR_CUDA;
+    }
+    if (na_where(positions, dev) != NA_THIS_DEVICE || na_where(moments, dev) != NA_THIS_DEVICE ||
+        na_where(H_out, dev) != NA_THIS_DEVICE) {
+        set_last_error((std::string("positions, moments and H_out must be device memory of the "
+                                    "current device (device ") +
+                        std::to_string(dev) + ")").c_str());
+        return CCFMM_ERR_ARG;
+    }
+    const NaWhere e_where = na_where(E_out, dev);
+    if (e_where == NA_OTHER_DEVICE) {
+        set_last_error((std::string("E_out must be host memory or device memory of the current "
+                                    "device (device ") +
+                        std::to_string(dev) + ")").c_str());
+        return CCFMM_ERR_ARG;
     }
     double *scratch = nullptr;
     {
@@ -170,7 +187,8 @@ ccfmm_status ccfmm_direct_field_energy_noalloc(const double *positions, const do
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(E_out, scratch + NA_MAX_BLOCKS, sizeof(double),
-                            na_is_device(E_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            e_where == NA_THIS_DEVICE ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyDeviceToHost,
                             s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

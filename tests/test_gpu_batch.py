@@ -8,6 +8,8 @@ import oracle as O
 from paper_0810_0233_gb300 import ccfmm as C
 from paper_0810_0233_gb300 import workloads as W
 
+import local_parity as LP
+
 pytestmark = pytest.mark.gpu
 
 
@@ -27,6 +29,22 @@ def _ensemble(ns=5, seed=77):
     return np.concatenate(pos), np.concatenate(mom), off
 
 
+def check_member_local(b, s, H, Href, f, p):
+    """Local bounds of one ensemble member: every dipole, and every cell of
+    levels >= 2 against the oracle's Taylor coefficients."""
+    assert LP.dipole_max_err(H, Href) < LP.DIPOLE_TOL, s
+    L = f.depth
+    lo = f.leaf_of()
+    cells = sorted({(1 << l) + int(k) for l in range(2, L + 1) for k in np.unique(lo >> (L - l))})
+    if not cells:
+        return
+    cols = np.array([O.index(n) for n in C.multi_indices(p)])
+    err = LP.cell_errors(b.sample(s).expansions("V"), f.locals()[:, cols], cells,
+                         C.multi_indices(p), f.box(), f.axes())
+    if err:
+        assert max(err.values()) < LP.CELL_TOL, (s, err)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
 def test_batch_steps_match_oracle(prec, tol):
     pos, mom, off = _ensemble()
@@ -42,8 +60,10 @@ def test_batch_steps_match_oracle(prec, tol):
             assert np.abs(b.moments() - ref_m).max() < 1e-14
             for s in range(b.ns):
                 sl = slice(off[s], off[s + 1])
-                Hr, Er, _ = O.fmm_field(pos[sl], ref_m[sl], p, theta)
+                Hr, Er, f = O.fmm_field(pos[sl], ref_m[sl], p, theta)
                 assert rel(H[sl], Hr) < tol, (prec, step, s)
+                if prec == "mixed":
+                    check_member_local(b, s, H[sl], Hr, f, p)
                 assert abs(E[s] - Er) <= 10 * tol * abs(Er)
         assert b.kernels_per_step() > b.ns
 

@@ -10,6 +10,8 @@ import oracle as O
 from paper_0810_0233_gb300 import ccfmm as C
 from paper_0810_0233_gb300 import workloads as W
 
+import local_parity as LP
+
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
@@ -32,12 +34,21 @@ def _sampled(pos, mom, p, theta, nleaves, seed, precisions=("mixed",)):
     Href = f.field()
     sel = np.isin(leaf_of, pick)
     out = {}
+    # the cells the oracle evaluated: ancestors (levels >= 2) of the picked leaves
+    cells = sorted({(1 << l) + int(k >> (L - l)) for k in pick for l in range(2, L + 1)})
+    cols = np.array([O.index(n) for n in C.multi_indices(p)])
     for prec in precisions:
         with C.FMM(pos, mom, p, theta, 0.0, precision=prec) as g:
             H = g.field()
             st = g.stats()
             assert st["depth"] == L
             assert np.array_equal(g.leaf_of(), leaf_of)
+            if prec == "mixed":
+                # local bounds: every sampled dipole and every evaluated cell
+                assert LP.dipole_max_err(H[sel], Href[sel]) < LP.DIPOLE_TOL
+                err = LP.cell_errors(g.expansions("V"), f.locals()[:, cols], cells,
+                                     C.multi_indices(p), f.box(), f.axes())
+                assert max(err.values()) < LP.CELL_TOL, err
         out[prec] = (H, st)
     ne = np.zeros(1 << (L + 1), dtype=bool)
     for l in range(L + 1):
@@ -102,4 +113,5 @@ def test_ensemble_512_p5():
         sl = slice(off[s], off[s + 1])
         Hr, Er, _ = O.fmm_field(pos[sl], ref_m[sl], p, theta)
         assert rel(H[sl], Hr) < 1e-5, s
+        assert LP.dipole_max_err(H[sl], Hr) < LP.DIPOLE_TOL, s
         assert abs(E[s] - Er) <= 1e-4 * abs(Er), s

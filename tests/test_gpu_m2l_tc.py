@@ -1,5 +1,8 @@
 """The tensor-core M2L (tcgen05, TF32 three-product split) against the FP32
-FMA M2L and the FP64 oracle, for every order it supports (p = 4..7)."""
+FMA M2L and the FP64 oracle, for every order it supports (p = 4..7).  Besides
+the relative RMS, every dipole's field and every cell's Taylor coefficients
+are held to the local bounds of ``local_parity`` against the oracle, so that
+one partner row or one entry run lost at a tile or item boundary fails."""
 import os
 
 import numpy as np
@@ -9,11 +12,29 @@ import oracle as O
 from paper_0810_0233_gb300 import ccfmm as C
 from paper_0810_0233_gb300 import workloads as W
 
+import local_parity as LP
+
 pytestmark = pytest.mark.gpu
 
 
 def rel(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def check_local_vs_oracle(H, V, pos, mom, p, theta):
+    """Per-dipole and per-cell bounds against the oracle FMM (square
+    truncation, all cells)."""
+    Href, _, f = O.fmm_field(pos, mom, p, theta)
+    assert rel(H, Href) < 1e-5
+    assert LP.dipole_max_err(H, Href) < LP.DIPOLE_TOL
+    L = f.depth
+    lo = f.leaf_of()
+    cells = sorted({(1 << l) + int(k) for l in range(2, L + 1) for k in np.unique(lo >> (L - l))})
+    cols = np.array([O.index(n) for n in C.multi_indices(p)])
+    Vo = f.locals()[:, cols]
+    err = LP.cell_errors(V, Vo, cells, C.multi_indices(p), f.box(), f.axes())
+    assert max(err.values()) < LP.CELL_TOL, err
+    return Href
 
 
 def _run(engine, pos, mom, p, theta):
@@ -39,8 +60,7 @@ def test_tensor_core_m2l_matches(p):
     nz = np.abs(Vf).sum(1) > 0
     assert rel(Vt[nz], Vf[nz]) < 2e-5
     assert rel(Ht, Hf) < 2e-6
-    Href = O.fmm_field(pos, mom, p, 0.5)[0]
-    assert rel(Ht, Href) < 1e-5
+    check_local_vs_oracle(Ht, Vt, pos, mom, p, 0.5)
 
 
 @pytest.mark.parametrize("kind", ["clustered", "ring"])
@@ -56,6 +76,7 @@ def test_tensor_core_m2l_irregular(kind):
     nz = np.abs(Vf).sum(1) > 0
     assert rel(Vt[nz], Vf[nz]) < 2e-5
     assert rel(Ht, Hf) < 2e-6
+    check_local_vs_oracle(Ht, Vt, pos, mom, 6, 0.5)
     sub = W.subset(len(pos), 300, 5)
     Hd = C.direct_field(pos, mom, targets=sub)
     assert rel(Ht[sub], Hd) < 1e-4

@@ -4,7 +4,10 @@ Bars: tree, leaf assignment and interaction lists bit-exact (as sets);
 FP64 path within 1e-12 relative RMS of the oracle; mixed path within 1e-5
 (FP32 bulk with FP64 derivative tensors and FP64 local accumulation).  The
 relative RMS is sqrt(sum |H - H_ref|^2 / sum |H_ref|^2) over the compared
-dipoles.  Inputs are the seeded workloads of ``paper_0810_0233_gb300.workloads``.
+dipoles.  The mixed path is also held to the local bounds of
+``local_parity``: every dipole's field error and every cell's Taylor
+coefficients against the oracle's.  Inputs are the seeded workloads of
+``paper_0810_0233_gb300.workloads``.
 """
 import os
 import subprocess
@@ -16,6 +19,8 @@ import pytest
 import oracle as O
 from paper_0810_0233_gb300 import ccfmm as C
 from paper_0810_0233_gb300 import workloads as W
+
+import local_parity as LP
 
 pytestmark = pytest.mark.gpu
 
@@ -80,10 +85,24 @@ def check_full(pos, mom, p, theta, leaf=0.0, box=None, lists=True, expansions=Tr
                     assert rel(ex["V"][rows], Vo[rows]) < TOL64, l
     assert rel(H, Href) < TOL64
     assert abs(E - Eref) <= TOL64 * abs(Eref) + 1e-300
-    Hm, Em, stm, _ = run_gpu(pos, mom, p, theta, leaf, box, "mixed")
+    Hm, Em, stm, exm = run_gpu(pos, mom, p, theta, leaf, box, "mixed")
     assert rel(Hm, Href) < TOLMIX
     assert abs(Em - Eref) <= 10 * TOLMIX * abs(Eref)
+    check_local(Hm, Href, exm["V"], f)
     return Href, H, Hm, st
+
+
+def check_local(Hm, Href, Vm, f):
+    """Mixed path, local bounds: every dipole, and every non-empty cell of
+    levels >= 2 (the levels that receive far interactions) against the
+    oracle's Taylor coefficients."""
+    assert LP.dipole_max_err(Hm, Href) < LP.DIPOLE_TOL
+    L = f.depth
+    Vo = f.locals()[:, lib_to_oracle_cols(f.p)]
+    cells = [c for c in nonempty_cells(f.leaf_of(), L) if c >= 4]
+    if cells and np.abs(Vo[cells]).max() > 0:
+        err = LP.cell_errors(Vm, Vo, cells, C.multi_indices(f.p), f.box(), f.axes())
+        assert max(err.values()) < LP.CELL_TOL, err
 
 
 # ---------------------------------------------------------------- workloads

@@ -1,4 +1,4 @@
-"""The round-end smoke check (__graft_entry__.smoke) and the failure path of
+"""The package smoke check (__graft_entry__.smoke) and the failure path of
 the tensor-core M2L's bounded waits."""
 import numpy as np
 import pytest

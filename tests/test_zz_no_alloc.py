@@ -77,4 +77,7 @@ def test_no_alloc_rejects_out_of_range_and_host_arrays():
     assert b"N out of range" in lib.ccfmm_last_error()
     host = np.zeros((4, 3))
     assert fn(ctypes.c_void_p(host.ctypes.data), ptr, 4, hp, ctypes.byref(E), None) == C.ERR_ARG
+    # the message names the current device, the only one whose memory is used
+    dev = torch.cuda.current_device()
+    assert ("device %d" % dev).encode() in lib.ccfmm_last_error()
     assert fn(ptr, ptr, 0, hp, ctypes.byref(E), None) == C.ERR_ARG
