@@ -143,6 +143,42 @@ def describe(name, n, leaf, p, theta, precision=None, step=None):
             "l2": "flushed between timed steps by a 256 MB write"}
 
 
+def selector_line(C, torch, pos_d, mom_d, H_d, stream, timed, steps, warm, sub, Hd,
+                  headline_s):
+    """FP32 + selector on the same workload: the learned selector's pick for
+    a 1e-4 target (the network trained by the library's kernels, parameters
+    shipped with the package), timed like the headline step, with its error
+    against the FP64 direct sum on the same 10k subset; the rule of thumb
+    (Eq. so with (6, 0.48), Sec. IV) beside it."""
+    from paper_0810_0233_gb300 import selector as S
+    mlp = S.load_trained()
+    if mlp is None:
+        return {"unavailable": "no trained selector parameters in the package"}
+    n = pos_d.shape[0]
+    target = 1e-4
+
+    def measure(p, th, lf):
+        with C.FMM(pos_d, mom_d, p, th, lf, precision="mixed", stream=stream) as g:
+            def step():
+                g.set_positions(pos_d, mom_d)
+                g.field(H_d)
+            t = timed(step, steps, warm)
+            H = H_d.cpu().numpy()
+        err = float(np.sqrt(((H[sub] - Hd) ** 2).sum() / (Hd ** 2).sum()))
+        return {"p": p, "theta": th, "leaf": lf, "value": n * steps / t, "unit": "fields/s",
+                "ms_per_step": 1e3 * t / steps, "rms_vs_direct_10k": err}
+
+    p, th, lf, fb = C.select(mlp, pos_d, target)
+    out = dict(measure(p, th, lf), target=target, fallback=fb)
+    rp, rth = (5, 0.71) if target >= 1e-2 else (6, 0.48)
+    out["rule_of_thumb"] = measure(rp, rth, C.leaf_size_rule(rp))
+    out["speedup_vs_rule"] = out["rule_of_thumb"]["ms_per_step"] / out["ms_per_step"]
+    out["speedup_vs_headline"] = 1e3 * headline_s / out["ms_per_step"]
+    out["note"] = ("selector: the library's MLP (fmm_select) on the library's features; the "
+                   "headline line keeps p = 6, theta = 0.5 and Eq. so leaves")
+    return out
+
+
 def cpu_oracle_sample(pos, mom, p, theta, nleaves=4096, seed=11):
     """The CPU oracle on a bounded sample of the workload: tree, lists and
     upward pass over every dipole, then the downward pass and near field for
@@ -356,6 +392,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-selector", action="store_true",
+                    help="skip the selector object (learned (p, theta, leaf) at 1e-4)")
     ap.add_argument("--profile", action="store_true",
                     help="one warm-up and two steps only (for ncu launch lists and captures)")
     ap.add_argument("--n", type=int, default=1_000_000,
@@ -549,6 +587,10 @@ def main():
                 acc["rms_vs_fp64_fmm"] = float(torch.sqrt(((H_d - H64) ** 2).sum() /
                                                           (H64 ** 2).sum()).item())
         line["accuracy"] = acc
+        if (args.workload == "ferrofluid" and args.precision == "mixed" and n == 1_000_000
+                and not args.no_selector):
+            line["selector"] = selector_line(C, torch, pos_d, mom_d, H_d, stream, timed,
+                                             min(steps, 20), warm, sub, Hd, t_full / steps)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(pos, mom, P, THETA)
         # the same oracle on one host thread, on a smaller sample

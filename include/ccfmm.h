@@ -338,6 +338,40 @@ ccfmm_status fmm_select(ccfmm_mlp_t m, const double *positions, int64_t N, doubl
                         int32_t *p_out, double *theta_out, double *leaf_out, int32_t *fallback_out);
 
 /* ------------------------------------------------------------------------
+ * Lattice FFT comparator (Sec. V: the FFT method the paper compares the
+ * Cartesian FMM with, on the simple-cubic lattice benchmark of Sec. IV).
+ * For dipoles on the lattice r = a (ix, iy, iz), 0 <= ix < nx, ... , the
+ * field of every site, H_i = sum_{j != i} G(r_i - r_j) m_j with
+ * G(r) = (3 r r^T - |r|^2 I) / |r|^5 (Eq. H2 as read), is a discrete
+ * convolution; the library evaluates it exactly (up to rounding) by
+ * zero-padded 3-D FFTs: each axis padded to 2n, so that no wrapped image
+ * overlaps (open boundaries).  The tensor spectra are computed once per
+ * handle.  The FFTs are cuFFT calls (opened at run time); the scatter, the
+ * 3 x 3 spectral product, the gather and the energy are the library's
+ * kernels.
+ *   nx, ny, nz   sites per axis, 1 .. 4096 each.
+ *   spacing      a > 0.
+ *   precision    CCFMM_FP64 (FP64 transforms) or CCFMM_MIXED (FP32
+ *                transforms; tensor built in FP64, energy summed in FP64).
+ *   moments      N x 3 float64 (N = nx ny nz), site (ix, iy, iz) at row
+ *                (ix ny + iy) nz + iz; host or device memory.
+ *   H_out        N x 3 float64, same order, or NULL; host or device.
+ *   E_out        E = -1/2 sum m.H, or NULL; host or device.
+ * fmm_lattice_field synchronises the handle's stream before it returns
+ * (outputs complete).  Errors: CCFMM_ERR_ARG for sizes, spacing or
+ * precision out of range and for non-finite moments (reported after the
+ * evaluation; outputs then undefined); CCFMM_ERR_ALLOC; CCFMM_ERR_CUDA when
+ * cuFFT cannot be opened or a CUDA/cuFFT call fails.
+ * ---------------------------------------------------------------------- */
+typedef struct ccfmm_lattice_s *ccfmm_lattice_t;
+
+ccfmm_status fmm_lattice_create(int32_t nx, int32_t ny, int32_t nz, double spacing,
+                                int32_t precision, void *cuda_stream, ccfmm_lattice_t *out);
+ccfmm_status fmm_lattice_field(ccfmm_lattice_t h, const double *moments, double *H_out,
+                               double *E_out);
+void fmm_lattice_destroy(ccfmm_lattice_t h);
+
+/* ------------------------------------------------------------------------
  * Allocation-free direct field and energy.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc, such as
  * code running inside a host application that owns all GPU memory through

@@ -107,6 +107,10 @@ def load():
             "ccfmm_mlp_predict": (_int, [_vp, _vp, _i64, _vp]),
             "ccfmm_features": (_int, [_vp, _i64, _vp]),
             "fmm_select": (_int, [_vp, _vp, _i64, _dbl, _vp, _vp, _vp, _vp]),
+            "fmm_lattice_create": (_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _dbl,
+                                          ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
+            "fmm_lattice_field": (_int, [_vp, _vp, _vp, _vp]),
+            "fmm_lattice_destroy": (None, [_vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -482,3 +486,45 @@ def select(mlp, positions, target_error):
     _check(load().fmm_select(None if mlp is None else mlp._h, pp, n, float(target_error),
                              ctypes.byref(p), ctypes.byref(th), ctypes.byref(lf), ctypes.byref(fb)))
     return int(p.value), float(th.value), float(lf.value), bool(fb.value)
+
+
+class Lattice:
+    """FFT convolution on a simple-cubic lattice (fmm_lattice_*): the
+    comparator of the paper's Sec. V.  Sites are ordered as
+    ``workloads.lattice`` orders them: (ix ny + iy) nz + iz."""
+
+    def __init__(self, nx, ny=None, nz=None, spacing=1.0, precision="fp64", stream=None):
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        self._lib = load()
+        self.n = int(nx) * int(ny) * int(nz)
+        prec = {"fp64": FP64, "mixed": MIXED, "fp32": MIXED}[precision]
+        h = _vp()
+        _check(self._lib.fmm_lattice_create(int(nx), int(ny), int(nz), float(spacing), prec,
+                                            _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def field_energy(self, moments, out=None):
+        """(H, E); H is written to ``out`` (host or device) when given."""
+        pm, k1 = _ptr(moments, 3 * self.n)
+        if out is None:
+            out = np.zeros((self.n, 3))
+        po, k2 = _ptr(out, 3 * self.n)
+        E = _dbl()
+        _check(self._lib.fmm_lattice_field(self._h, pm, po, ctypes.byref(E)))
+        return out, E.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fmm_lattice_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        self.close()

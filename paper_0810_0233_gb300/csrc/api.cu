@@ -755,6 +755,18 @@ static bool tc_gather_tma()
     return TC_GATHER_TMA_DEFAULT;
 }
 
+// Where the tensor-core M2L keeps its gathered operand: shared memory
+// (cp.async or TMA gather; the default) or tensor memory (filled by
+// tcgen05.st from registers); CCFMM_TC_A=smem|tmem overrides the default.
+constexpr bool TC_A_TMEM_DEFAULT = false;
+static bool tc_a_tmem()
+{
+    const char *e = getenv("CCFMM_TC_A");
+    if (e && !strcmp(e, "smem")) return false;
+    if (e && !strcmp(e, "tmem")) return true;
+    return TC_A_TMEM_DEFAULT;
+}
+
 // Buffers and operators of the tensor-core M2L for the current tree, built
 // on the handle's stream at the first evaluation after a build (ensemble
 // members: before their evaluation is captured).
@@ -849,7 +861,7 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
                       P<int>(h->titem0), P<int>(h->tnitems), P<int>(h->ent_u), P<int>(h->ent_src),
                       P<float>(h->Q), ncellp, P<float>(h->gkt), P<float>(h->Qs),
                       (tc_gather_tma() && h->qmap_ok && h->qmap_for == h->Qs.p) ? h->qmap : nullptr,
-                      P<float>(h->Bop), P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V),
+                      tc_a_tmem(), P<float>(h->Bop), P<Geom>(h->geomd), P<float>(h->Ps), P<double>(h->V),
                       &P<Readback>(h->rb)->eflags, sf);
     else if (sizeof(real) == 4 && m2l_f32_supported(KP, h->ldD))
         launch_m2l_f32(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,

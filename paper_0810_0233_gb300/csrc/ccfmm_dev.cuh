@@ -228,8 +228,8 @@ bool m2l_tc_qmap(void *map, const float *Qs, long long ncell, int KP);
 void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items, int nitems,
                    const int *tile_item0, const int *tile_nitems, const int *ent_u,
                    const int *ent_src, const float *Q, long long ncell, const float *gk,
-                   float *Qs, const void *qmap, const float *Bop, const Geom *g, float *Ps,
-                   double *V, int *flags, cudaStream_t s);
+                   float *Qs, const void *qmap, bool a_tmem, const float *Bop, const Geom *g,
+                   float *Ps, double *V, int *flags, cudaStream_t s);
 template <typename real>
 void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
                 const int *ent_src, const real *Q, const real *D, int ldD, const uint16_t *it,

@@ -20,6 +20,10 @@
 // read once per k-step, which matters because at TF32 the MMAs' operand
 // reads are what bounds shared-memory bandwidth.
 //
+// K is padded to chunks of 32; the k-steps of 8 that lie wholly beyond KP
+// (the last chunk's padding) are skipped, and the gather copies none of
+// their bytes.
+//
 // Shared-memory operands use the 128-byte-swizzled K-major layout: a unit's
 // row of 32 TF32 is one 128-byte line, 8-row atoms of 1024 bytes (stride
 // offset), and the 16-byte chunk j of row r sits in slot j ^ (r mod 8), so
@@ -29,7 +33,8 @@
 //
 // Pipeline, 3 or 4 stages (as many as fit) of one unit = (entry, 32-wide K
 // chunk) each.  Two ways to fill a stage:
-//   TMA gather (default)  producer warp 0 alone: lane 0 posts the stage's
+//   TMA gather (CCFMM_TC_GATHER=tma; measured slower, not the default)
+//              producer warp 0 alone: lane 0 posts the stage's
 //              byte count on its barrier and starts the bulk copy of the
 //              operator chunk; every lane gathers its 4 partner rows of the
 //              hi and the lo plane with one tile::gather4 tensor copy each
@@ -37,7 +42,7 @@
 //              layout by the copy engine; cells without that partner read
 //              row 0, which holds zeros).  The barrier completes when all
 //              bytes have landed, so all stages can be in flight;
-//   cp.async gather  (CCFMM_TC_GATHER=cp) producers (4 or 8 warps) wait for
+//   cp.async gather  (the default) producers (4 or 8 warps) wait for
 //              the stage to be free, gather the 128 partner rows of the
 //              chunk (cp.async, hi and lo; zero rows for cells without that
 //              partner), and thread 0 starts the bulk copy of the operator
@@ -258,8 +263,10 @@ __global__ void k_m2l_ops(int p, const float *D, int ldD, const uint16_t *it_g, 
     }
 }
 
-// Scaled moments split into TF32 pairs: Qs[part][hid][k], rows of KT floats.
-template <int KP>
+// Scaled moments split into TF32 pairs: Qs[part][hid][k], rows of KT floats
+// (SPLIT), or the scaled FP32 moments alone in plane 0 (the kernel that
+// splits them in registers on the way to tensor memory).
+template <int KP, bool SPLIT>
 __global__ void k_q_split(int p, long long ncell, const float *Q, const float *gk, float *Qs)
 {
     typedef TcShape<KP> S;
@@ -280,10 +287,16 @@ __global__ void k_q_split(int p, long long ncell, const float *Q, const float *g
         v[2] = q.z * g.z;
         v[3] = q.w * g.w;
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (k4 + j >= K) v[j] = 0.f;
+    if (!SPLIT) {
+        *reinterpret_cast<float4 *>(Qs + hid * KT + k4) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+    }
     float hi[4], lo[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (k4 + j >= K) v[j] = 0.f;
         hi[j] = to_tf32(v[j]);
         lo[j] = v[j] - hi[j];
     }
@@ -458,14 +471,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                              Bop + ((long long)gid * S::NCH + c) * (2 * S::B_BYTES),
                              2 * S::B_BYTES, bb);
                 }
+                // 16-byte chunks wholly beyond KP feed no MMA (their k-steps are
+                // skipped): not copied
+                if (c * TC_KC + 4 * j < KP) {
 #pragma unroll
-                for (int part = 0; part < 2; ++part) {
-                    const float *qb = Qs + part * qplane + c * TC_KC + 4 * j;
+                    for (int part = 0; part < 2; ++part) {
+                        const float *qb = Qs + part * qplane + c * TC_KC + 4 * j;
 #pragma unroll
-                    for (int m = 0; m < MR; ++m) {
-                        const bool v = src[m] >= 0;
-                        tc_cp16(st + part * S::A_BYTES + dst0 + m * (NW / 2) * TC_SBO,
-                                qb + (v ? (long long)src[m] * S::KT : 0ll), v ? 16 : 0);
+                        for (int m = 0; m < MR; ++m) {
+                            const bool v = src[m] >= 0;
+                            tc_cp16(st + part * S::A_BYTES + dst0 + m * (NW / 2) * TC_SBO,
+                                    qb + (v ? (long long)src[m] * S::KT : 0ll), v ? 16 : 0);
+                        }
                     }
                 }
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -535,8 +552,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = sbase + (uint32_t)(s * S::STAGE), a1 = a0 + S::A_BYTES;
             const uint32_t b0 = a0 + 2 * S::A_BYTES;  // B_hi, then B_lo: 2N rows
+            const int c = u % S::NCH;
 #pragma unroll
             for (int kk = 0; kk < TC_KC / 8; ++kk) {
+                if (c * TC_KC + 8 * kk >= KP) break;  // all-zero K columns
                 const uint32_t o = kk * 32;
                 // [acc_hi | acc_lo] += A_hi [B_hi | B_lo];  acc_hi += A_lo B_hi
                 tc_mma(tmem, umma_desc(a0 + o), umma_desc(b0 + o), idesc2,
@@ -560,6 +579,288 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(S::TMEM_COLS));
+    }
+}
+
+// ------------------------------------------- contraction, A in tensor memory
+// The same contraction with the gathered operand A (partner moments of the
+// tile's 128 cells) in tensor memory instead of shared memory.  Per unit the
+// producers load their cells' 32 scaled FP32 moments straight from global
+// memory into registers (one warp per 32 TMEM lanes and 16 of the 32 K
+// columns, one unit ahead), split them into TF32 hi and lo there, and store
+// both with tcgen05.st into the unit's TMEM stage; only the operator chunk
+// (B) passes through shared memory.  This removes the A writes and the MMA's
+// A reads from shared memory (about half its traffic per unit) and halves
+// the gathered bytes (one FP32 plane instead of two TF32 planes).
+//   TMEM: columns [0, 2N) the accumulator halves [acc_hi | acc_lo]; the
+//   last ST x 64 columns the A stages, each [A_hi (32) | A_lo (32)].
+//   k-steps whose 8 K columns all lie beyond KP are skipped.
+// The shared memory request is at least 116 KB, so that two of these CTAs
+// never share an SM (each allocates all 512 TMEM columns); the rest of the
+// SM's shared memory is left to near-field blocks running concurrently.
+// units whose moments each producer thread keeps in flight
+#ifndef CCFMM_TCT_D
+#define CCFMM_TCT_D 4
+#endif
+constexpr int TCT_D = CCFMM_TCT_D;
+
+template <int KP> struct TctShape {
+    typedef TcShape<KP> S;
+    static constexpr int A_COLS = 2 * TC_KC;
+    static constexpr int ST = (512 - 2 * S::N) / A_COLS > 6 ? 6 : (512 - 2 * S::N) / A_COLS;
+    static constexpr int ACOL0 = 512 - ST * A_COLS;
+    static constexpr int BSTAGE = 2 * S::B_BYTES;
+    static constexpr int SMEM_USE = ST * BSTAGE + 1024;
+    static constexpr int SMEM = SMEM_USE > 116 * 1024 ? SMEM_USE : 116 * 1024;
+    static_assert(ST >= 3 && ACOL0 >= 2 * S::N, "tensor memory plan");
+};
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16};\n" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+// D (tmem) [+]= A (tmem) x B (smem descriptor)
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                          uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+}
+
+template <int KP>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tct(const M2LItem *items, const int *ent_u, const int *ent_src, const float *Qf,
+              const unsigned char *Bop, float *Ps, int *flags, long long spin, int stall)
+{
+    typedef TcShape<KP> S;
+    typedef TctShape<KP> T;
+    constexpr int ST = T::ST;
+    static_assert(TC_PROD == 256, "eight producer warps: two per TMEM lane quarter");
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) unsigned long long bar_full[ST], bar_b[ST], bar_empty[ST];
+    __shared__ __align__(8) unsigned long long bar_done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+    volatile int *abort = &s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const M2LItem item = items[blockIdx.x];
+    const int ne = item.e1 - item.e0;
+    const int nunits = ne * S::NCH;
+    const uint32_t sbase = (smem_u32(smraw) + 1023u) & ~1023u;  // swizzle atoms
+    const uint32_t done = smem_u32(&bar_done);
+
+    if (tid == 0) {
+        *abort = 0;
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), TC_PROD / 32);
+            mbar_init(smem_u32(&bar_b[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    constexpr int MMA_WARP = TC_PROD / 32;
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+            smem_u32(&tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp < MMA_WARP) {
+        // ---------------- producers: warp w owns TMEM lanes 32 (w mod 4) ..
+        // (the tile's cells) and K columns 16 (w / 4) .. of every unit
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = 32 * quad + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(T::ACOL0 + 16 * half);
+        // this thread's 16 moments of a unit (zeros for a cell without the
+        // partner)
+        auto load = [&](int src, int c, float4 (&r)[4]) {
+            if (src >= 0) {
+                const float4 *q = reinterpret_cast<const float4 *>(
+                    Qf + (long long)src * S::KT + c * TC_KC + 16 * half);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) r[j] = __ldg(q + j);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) r[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        // Loads run TCT_D units ahead of the stores, in unit order, through a
+        // ring of register buffers: ld_e / ld_src are the entry and partner
+        // row of the latest load, pf_src the row of entry ld_e + 1 (fetched
+        // one entry ahead, so that no data load waits on its index).
+        int ld_u = 0, ld_e = 0, ld_src = -1, pf_src = -1;
+        if (ne > 0) {
+            ld_src = ent_src[(long long)item.e0 * TT + row];
+            if (ne > 1) pf_src = ent_src[(long long)(item.e0 + 1) * TT + row];
+        }
+        auto issue = [&](float4 (&r)[4]) {
+            if (ld_u < nunits) {
+                const int e = ld_u / S::NCH, c = ld_u - e * S::NCH;
+                if (e != ld_e) {  // the next entry (units advance one at a time)
+                    ld_e = e;
+                    ld_src = pf_src;
+                    pf_src = e + 1 < ne ? ent_src[((long long)item.e0 + e + 1) * TT + row] : -1;
+                }
+                load(ld_src, c, r);
+            }
+            ++ld_u;
+        };
+        // operator class of the current entry and of the next one (thread 0)
+        int gid_cur = 0, gid_nx = 0;
+        if (tid == 0 && ne > 0) {
+            gid_cur = ent_u[item.e0];
+            if (ne > 1) gid_nx = ent_u[item.e0 + 1];
+        }
+        float4 buf[TCT_D][4];
+#pragma unroll
+        for (int d = 0; d < TCT_D; ++d) issue(buf[d]);
+        int issued = 0;
+        bool ok = true;
+        for (int u0 = 0; u0 < nunits && ok; u0 += TCT_D) {
+#pragma unroll
+            for (int d = 0; d < TCT_D; ++d) {
+                const int u = u0 + d;
+                if (u >= nunits) break;
+                const int s = u % ST, r = u / ST;
+                const int e = u / S::NCH, c = u - e * S::NCH;
+                if (tid == 0 && c == 0 && e > 0) {
+                    gid_cur = gid_nx;
+                    gid_nx = e + 1 < ne ? ent_u[item.e0 + e + 1] : 0;
+                }
+                if (r > 0 && !__all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_empty[s]),
+                                                                (r - 1) & 1, abort, spin))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (tid == 0) {
+                    const uint32_t bb = smem_u32(&bar_b[s]);
+                    mbar_expect_tx(bb, T::BSTAGE);
+                    bulk_g2s(sbase + (uint32_t)(s * T::BSTAGE),
+                             Bop + ((long long)gid_cur * S::NCH + c) * T::BSTAGE, T::BSTAGE, bb);
+                }
+                issued = u + 1;
+                float hi[16], lo[16];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float v[4] = {buf[d][j].x, buf[d][j].y, buf[d][j].z, buf[d][j].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        hi[4 * j + q] = to_tf32(v[q]);
+                        lo[4 * j + q] = v[q] - hi[4 * j + q];
+                    }
+                }
+                // unit u + TCT_D into the buffer just consumed
+                issue(buf[d]);
+                const uint32_t ta = tl + (uint32_t)(s * T::A_COLS);
+                tmem_st16(ta, hi);
+                tmem_st16(ta + TC_KC, lo);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bar_full[s]));
+            }
+        }
+        if (!ok) {
+            *abort = 1;
+            atomicOr(flags, FLAG_TIMEOUT);
+        }
+        // operator copies still in flight after a time-out: wait for the
+        // last one issued on each stage (phases of a stage complete in order)
+        if (tid == 0 && *abort) {
+            for (int s = 0; s < ST; ++s) {
+                int last = -1;
+                for (int u = s; u < issued; u += ST) last = u;
+                if (last >= 0) mbar_wait_plain(smem_u32(&bar_b[s]), (last / ST) & 1);
+            }
+        }
+        // ---------------- epilogue: accumulator -> partial sums
+        const bool have = nunits > 0 && mbar_wait(done, 0, abort, spin) && !*abort;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!*abort) {
+            float *out = Ps + ((long long)blockIdx.x * TT + quad * 32 + lane) * KP;
+            const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+#pragma unroll
+            for (int c0 = 16 * half; c0 < S::N; c0 += 32) {
+                uint32_t rh[16], rl2[16];
+                if (have) {
+                    tmem_ld16(trow + (uint32_t)c0, rh);
+                    tmem_ld16(trow + (uint32_t)(S::N + c0), rl2);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) rh[q] = rl2[q] = 0u;
+                }
+#pragma unroll
+                for (int q = 0; q < 16; q += 4)
+                    if (c0 + q < KP)
+                        *reinterpret_cast<float4 *>(out + c0 + q) = make_float4(
+                            __uint_as_float(rh[q]) + __uint_as_float(rl2[q]),
+                            __uint_as_float(rh[q + 1]) + __uint_as_float(rl2[q + 1]),
+                            __uint_as_float(rh[q + 2]) + __uint_as_float(rl2[q + 2]),
+                            __uint_as_float(rh[q + 3]) + __uint_as_float(rl2[q + 3]));
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issue (one thread)
+        const uint32_t idesc2 = (1u << 4) | (2u << 7) | (2u << 10) |
+                                ((uint32_t)(2 * S::N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+        const uint32_t idesc1 = (1u << 4) | (2u << 7) | (2u << 10) |
+                                ((uint32_t)(S::N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+        bool ok = true;
+        for (int u = 0; u < (stall ? 0 : nunits); ++u) {
+            const int s = u % ST, r = u / ST;
+            const int c = u % S::NCH;
+            if (!mbar_wait(smem_u32(&bar_full[s]), r & 1, abort, spin) ||
+                !mbar_wait(smem_u32(&bar_b[s]), r & 1, abort, spin)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = tmem + (uint32_t)(T::ACOL0 + s * T::A_COLS), a1 = a0 + TC_KC;
+            const uint32_t b0 = sbase + (uint32_t)(s * T::BSTAGE);  // B_hi, then B_lo: 2N rows
+#pragma unroll
+            for (int kk = 0; kk < TC_KC / 8; ++kk) {
+                if (c * TC_KC + 8 * kk >= KP) break;  // all-zero K columns
+                // [acc_hi | acc_lo] += A_hi [B_hi | B_lo];  acc_hi += A_lo B_hi
+                tc_mma_ts(tmem, a0 + 8 * kk, umma_desc(b0 + kk * 32), idesc2,
+                          (u == 0 && kk == 0) ? 0u : 1u);
+                tc_mma_ts(tmem, a1 + 8 * kk, umma_desc(b0 + kk * 32), idesc1, 1u);
+            }
+            tc_commit(smem_u32(&bar_empty[s]));
+        }
+        if (!ok) {
+            *abort = 1;
+            atomicOr(flags, FLAG_TIMEOUT);
+        }
+        // arrives once every MMA issued above has completed
+        tc_commit(done);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == MMA_WARP) {
+        if (*abort && lane == 0) mbar_wait_plain(done, 0);
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
     }
 }
 
@@ -655,8 +956,8 @@ bool m2l_tc_qmap(void *map, const float *Qs, long long ncell, int KP)
 void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *items, int nitems,
                    const int *tile_item0, const int *tile_nitems, const int *ent_u,
                    const int *ent_src, const float *Q, long long ncell, const float *gk,
-                   float *Qs, const void *qmap, const float *Bop, const Geom *g, float *Ps,
-                   double *V, int *flags, cudaStream_t s)
+                   float *Qs, const void *qmap, bool a_tmem, const float *Bop, const Geom *g,
+                   float *Ps, double *V, int *flags, cudaStream_t s)
 {
     // qmap (a tensor map from m2l_tc_qmap) selects the TMA gather, nullptr
     // the cp.async gather
@@ -669,13 +970,32 @@ void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *
     const char *sv = getenv("CCFMM_TC_STALL");
     const int stall = (sv && atoi(sv)) ? 1 : 0;
     const long long spin = stall ? (1ll << 12) : TC_SPIN;
-    if (nitems > 0) {
+    if (nitems > 0 && a_tmem) {
+#define M2LTCT(KPV)                                                                             \
+    case KPV: {                                                                                 \
+        typedef TcShape<KPV> S;                                                                 \
+        const long long nq = ncell * (S::KT / 4);                                               \
+        note_launch();                                                                          \
+        k_q_split<KPV, false><<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(p, ncell, Q, gk, Qs); \
+        const int smem = TctShape<KPV>::SMEM;                                                   \
+        cudaFuncSetAttribute(k_m2l_tct<KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        note_launch();                                                                          \
+        k_m2l_tct<KPV><<<nitems, TC_THREADS, smem, s>>>(                                        \
+            items, ent_u, ent_src, Qs, reinterpret_cast<const unsigned char *>(Bop), Ps, flags, \
+            spin, stall);                                                                       \
+    } break;
+        switch (KP) {
+            M2LTCT(40) M2LTCT(56) M2LTCT(88) M2LTCT(120)
+        default: break;
+        }
+#undef M2LTCT
+    } else if (nitems > 0) {
 #define M2LTC(KPV)                                                                              \
     case KPV: {                                                                                 \
         typedef TcShape<KPV> S;                                                                 \
         const long long nq = ncell * (S::KT / 4);                                               \
         note_launch();                                                                          \
-        k_q_split<KPV><<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(p, ncell, Q, gk, Qs);     \
+        k_q_split<KPV, true><<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(p, ncell, Q, gk, Qs); \
         size_t smem = tc_smem<KPV>();                                                           \
         auto kern = qmap ? k_m2l_tc<KPV, true> : k_m2l_tc<KPV, false>;                          \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \

@@ -11,6 +11,10 @@
   every order p with the alpha that meets e, timed on the 32^3 lattice with
   the measured field and energy errors against the direct sum (Table II and
   the optimal-time-versus-accuracy curve of Fig. 3).
+* fft_comparator(): the FFT lattice convolution (the comparator of Sec. V)
+  against the fast method on n^3 lattices: time per evaluation of each (FFT
+  in FP64 and FP32; the fast method at the paper's (5, 0.71) and at
+  (6, 0.5), tree included) and each one's error against the direct sum.
 * truncation(): the square truncation of Eq. taylorcalc against the
   total-degree one (terms |n|+|k| <= p+1) on the ferrofluid workload: field
   error against the direct sum, evaluation time, and the M2L stage time of
@@ -220,12 +224,51 @@ def truncation(n=1_000_000, ps=(4, 5, 6, 7), theta=0.5, nsub=10_000, evals=10, s
     return rows
 
 
+def fft_comparator(sizes=(16, 32, 64, 100, 128), repeats=5, nsub=2000, seed=6):
+    """FFT convolution and the fast method on random-moment n^3 lattices."""
+    import torch
+    run, stream = _timer()
+    rows = []
+    for n in sizes:
+        pos, mom, box = W.lattice(n, seed=810233 + 60 + seed)
+        N = len(pos)
+        pd = torch.from_numpy(pos).cuda()
+        md = torch.from_numpy(mom).cuda()
+        sub = np.random.default_rng(seed).choice(N, min(nsub, N), replace=False)
+        Hd = C.direct_field(pd, md, targets=torch.from_numpy(sub).cuda(), stream=stream)
+        H = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
+        row = {"n": n, "N": N}
+
+        def err():
+            Hs = H.cpu().numpy()[sub]
+            return float(np.sqrt(((Hs - Hd) ** 2).sum() / (Hd ** 2).sum()))
+
+        for prec in ("fp64", "mixed"):
+            with C.Lattice(n, precision=prec, stream=stream) as lat:
+                lat.field_energy(md, out=H)
+                row["fft_%s_ms" % prec] = run(lambda: lat.field_energy(md, out=H), repeats)
+                row["fft_%s_error" % prec] = err()
+        for p, th in ((5, 0.71), (6, 0.5)):
+            with C.FMM(pd, md, p, th, box=box, precision="mixed", stream=stream) as f:
+                f.field(H)
+
+                def step():
+                    f.set_positions(pd, md)
+                    f.field(H)
+
+                row["fmm_p%d_ms" % p] = run(step, repeats)
+                row["fmm_p%d_error" % p] = err()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="fewer sizes (smoke run)")
     ap.add_argument("--part", default="all",
                     choices=["all", "scaling", "leaf_sweep", "optimal_leaf", "error_budget",
-                             "truncation"])
+                             "truncation", "fft"])
     ap.add_argument("--out", default="experiments.json")
     args = ap.parse_args()
     t0 = time.time()
@@ -233,9 +276,10 @@ def main():
              "leaf_sweep": dict(leaves=(4, 8, 16)),
              "optimal_leaf": dict(ps=(3, 5), sizes=(30, 31)),
              "error_budget": dict(n=16, es=(0.05,), ps=(3, 5)),
-             "truncation": dict(n=100_000, ps=(4, 6), evals=3)}
+             "truncation": dict(n=100_000, ps=(4, 6), evals=3),
+             "fft": dict(sizes=(16, 32), repeats=2)}
     parts = {"scaling": scaling, "leaf_sweep": leaf_sweep, "optimal_leaf": optimal_leaf,
-             "error_budget": error_budget, "truncation": truncation}
+             "error_budget": error_budget, "truncation": truncation, "fft": fft_comparator}
     res = {}
     for name, fn in parts.items():
         if args.part not in ("all", name):

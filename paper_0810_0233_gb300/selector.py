@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import os
 import time
 
 import numpy as np
@@ -131,6 +132,18 @@ def train(X, T, epochs=200, batch=256, lr=2e-3, seed=7):
     for ep in range(epochs):
         loss = mlp.train(Xs, Ts, mask, batch=batch, epochs=1, lr=lr * (0.5 ** (ep / (epochs / 3))))
     return mlp, loss
+
+
+TRAINED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_params.npz")
+
+
+def load_trained(path=TRAINED):
+    """The network trained by ``main(--save)`` on the GPU (parameters and
+    input/target normalisation), or None when the file is absent."""
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    return C.MLP(z["params"], z["norm"])
 
 
 def rule_of_thumb(target):

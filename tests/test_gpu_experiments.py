@@ -51,3 +51,13 @@ def test_truncation_small():
         assert r["tc_eval_ms"] > 0 and r["fma_m2l_ms"] > 0
     # fewer far-field terms cannot make the field markedly more accurate
     assert td["rms_field_error"] > 0.5 * sq["rms_field_error"]
+
+
+def test_fft_comparator_small():
+    """FFT and fast method on small lattices: the FFT (FP64) is exact to
+    rounding, the fast method within its truncation error."""
+    rows = X.fft_comparator(sizes=(12, 20), repeats=1, nsub=300)
+    for r in rows:
+        assert r["fft_fp64_error"] < 1e-12 and r["fft_mixed_error"] < 1e-5
+        assert r["fmm_p6_error"] < 1e-3 and r["fmm_p5_error"] < 1e-2
+        assert r["fft_fp64_ms"] > 0 and r["fmm_p5_ms"] > 0

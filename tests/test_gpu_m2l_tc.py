@@ -82,23 +82,27 @@ def test_tensor_core_m2l_irregular(kind):
     assert rel(Ht[sub], Hd) < 1e-4
 
 
-def _run_gather(mode, pos, mom, p, theta):
-    old = os.environ.get("CCFMM_TC_GATHER")
+def _run_gather(mode, pos, mom, p, theta, where="smem"):
+    saved = {k: os.environ.get(k) for k in ("CCFMM_TC_GATHER", "CCFMM_TC_A")}
     os.environ["CCFMM_TC_GATHER"] = mode
+    os.environ["CCFMM_TC_A"] = where
     try:
         return _run("tc", pos, mom, p, theta)
     finally:
-        if old is None:
-            del os.environ["CCFMM_TC_GATHER"]
-        else:
-            os.environ["CCFMM_TC_GATHER"] = old
+        for k, v in saved.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
 
 
 @pytest.mark.parametrize("case", ["p4", "p5", "p6", "p7", "clustered", "ring"])
-def test_tma_gather_is_bitwise(case):
+def test_operand_paths_are_bitwise(case):
     """The TMA row gather (tile::gather4 copies; an absent partner reads the
     zero row 0) fills the operand stages with the same bytes as the cp.async
-    gather, so the MMAs, and the whole field, agree bit for bit."""
+    gather, and the tensor-memory operand (moments split in registers and
+    stored with tcgen05.st) holds the same TF32 pairs, so the MMAs, and the
+    whole field, agree bit for bit on all three paths."""
     if case == "clustered":
         pos, mom = W.clustered(30000, seed=W.BASE_SEED + 41)
         p = 6
@@ -112,3 +116,6 @@ def test_tma_gather_is_bitwise(case):
     Ht, Vt = _run_gather("tma", pos, mom, p, 0.5)
     assert np.array_equal(Vt, Vc)
     assert np.array_equal(Ht, Hc)
+    Hm, Vm = _run_gather("cp", pos, mom, p, 0.5, where="tmem")
+    assert np.array_equal(Vm, Vc)
+    assert np.array_equal(Hm, Hc)
