@@ -166,7 +166,7 @@ struct ccfmm_s {
     DevBuf pos, mom, keys, keys2, keys3, idx, idx2, idx3, sorttemp, scantemp;
     DevBuf geomd, box6, userbox, partial, rb;
     DevBuf leaf_start, A, B, H;
-    DevBuf cube, nsA, nsB, neA, neB, ncnt, fcnt, fstart;
+    DevBuf cube, nl, neA, neB, cflag, crank;
     DevBuf far, far_off, far_num, tiles, tcount, tstart, ent_u, ent_src;
     DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
     DevBuf Hout, epart, items, titem0, tnitems, Ps;
@@ -192,7 +192,8 @@ struct ccfmm_s {
     double *E_dst = nullptr;
     bool quiet = false;
     Readback *hrb = nullptr;  // pinned
-    int *near_start_leaf = nullptr;
+    int2 *near_nl = nullptr;  // leaf near lists: (first entry, count) per leaf
+    size_t near_leaf_bytes = 0;
     NearEnt *near_leaf = nullptr;
     cudaEvent_t evb[EV_NB];
     cudaEvent_t eve[EV_RING][EV_NE];
@@ -509,7 +510,8 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
         launch_sort_points<double>(P<double>(h->pos), P<double>(h->mom), P<int>(h->idx),
                                    P<uint32_t>(h->keys2), N, P<Geom>(h->geomd), L,
                                    P<double4>(h->A), P<double2>(h->B), s);
-    launch_level_counts(P<int>(h->leaf_start), L, drb->ne, s);
+    TRY(ensure(h->cflag, sizeof(int) * ncellp));
+    launch_level_counts(P<int>(h->leaf_start), L, drb->ne, P<int>(h->cflag), s);
     KCHECK();
     if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_BS2], s));
     // the plan needs only the depth and the geometry: the host builds it
@@ -570,25 +572,24 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     }
     if (near_max >= (1ll << 31) || far_sum >= (1ll << 31))
         return fail(CCFMM_ERR_ARG, "interaction lists too large for 32-bit offsets");
-    TRY(ensure(h->nsA, sizeof(int) * (nleaf + 1)));
-    TRY(ensure(h->nsB, sizeof(int) * (nleaf + 1)));
+    TRY(ensure(h->nl, sizeof(int2) * ncellp));
     TRY(ensure(h->neA, sizeof(NearEnt) * near_max));
     TRY(ensure(h->neB, sizeof(NearEnt) * near_max));
-    TRY(ensure(h->ncnt, sizeof(int) * (nleaf + 1)));
-    TRY(ensure(h->fcnt, sizeof(int) * (nleaf + 1)));
-    TRY(ensure(h->fstart, sizeof(int) * (nleaf + 1)));
+    TRY(ensure(h->crank, sizeof(int) * (ncellp + 1)));
     TRY(ensure(h->far, sizeof(FarEnt) * std::max(far_sum, 1ll)));
     TRY(ensure(h->far_off, sizeof(int) * ncellp));
     TRY(ensure(h->far_num, sizeof(int) * ncellp));
-    TRY(ensure(h->scantemp, scan_temp_bytes(std::max(nleaf, 4096ll) * 256)));
+    TRY(ensure(h->scantemp, scan_temp_bytes(std::max(ncellp, 4096ll) * 256)));
     CK(cudaMemsetAsync(h->far_num.p, 0, sizeof(int) * ncellp, s));
     CK(cudaMemsetAsync(h->far_off.p, 0, sizeof(int) * ncellp, s));
-    // level 0: the root is near itself
-    {
-        CK(cudaMemcpyAsync(h->nsA.p, h->h_ns0, sizeof(h->h_ns0), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(h->neA.p, &h->h_e0, sizeof(h->h_e0), cudaMemcpyHostToDevice, s));
-    }
-    DevBuf *nsPrev = &h->nsA, *nsCur = &h->nsB, *nePrev = &h->neA, *neCur = &h->neB;
+    // rank of every non-empty cell among all heap ids; a level's list slots
+    // are indexed by rank within the level
+    scan_exclusive(P<int>(h->cflag), P<int>(h->crank), ncellp, P<int>(h->crank) + ncellp,
+                   h->scantemp.p, s);
+    // level 0: the root is near itself (one entry, offset 0)
+    CK(cudaMemcpyAsync(P<int2>(h->nl) + 1, h->h_ns0, sizeof(h->h_ns0), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->neA.p, &h->h_e0, sizeof(h->h_e0), cudaMemcpyHostToDevice, s));
+    DevBuf *nePrev = &h->neA, *neCur = &h->neB;
     for (int l = 1; l <= L; ++l) {
         LevelPlan &lp = h->plan[l];
         OffsetCube ci;
@@ -596,23 +597,18 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
         ci.R[1] = lp.R[1];
         ci.R[2] = lp.R[2];
         ci.base = lp.cube_base;
-        long long nc = 1ll << l;
-        launch_list_count(l, P<int>(h->leaf_start), L, P<int>(*nsPrev), P<NearEnt>(*nePrev),
-                          P<int>(h->cube), ci, h->geom.axis[l], P<int>(h->ncnt), P<int>(h->fcnt),
+        launch_list_level(l, P<int>(h->leaf_start), L, P<int>(h->crank), P<int2>(h->nl),
+                          P<NearEnt>(*nePrev), P<int>(h->cube), ci, h->geom.axis[l],
+                          (int)lp.nearv.size(), P<NearEnt>(*neCur), lp.far_base,
+                          (int)lp.farv.size(), P<FarEnt>(h->far), P<int>(h->far_off),
+                          P<int>(h->far_num), &drb->near_total[l], &drb->far_total[l],
                           &drb->flags, s);
-        scan_exclusive2(P<int>(h->ncnt), P<int>(*nsCur), P<int>(*nsCur) + nc, P<int>(h->fcnt),
-                        P<int>(h->fstart), P<int>(h->fstart) + nc, nc, h->scantemp.p, s);
-        launch_list_fill_impl(l, P<int>(h->leaf_start), L, P<int>(*nsPrev), P<NearEnt>(*nePrev),
-                              P<int>(h->cube), ci, h->geom.axis[l], P<int>(*nsCur),
-                              P<NearEnt>(*neCur), P<int>(h->fstart), lp.far_base,
-                              P<FarEnt>(h->far), P<int>(h->far_off), P<int>(h->far_num),
-                              &drb->near_total[l], &drb->far_total[l], &drb->flags, s);
-        std::swap(nsPrev, nsCur);
         std::swap(nePrev, neCur);
     }
     KCHECK();
-    h->near_start_leaf = P<int>(*nsPrev);
+    h->near_nl = P<int2>(h->nl) + nleaf;
     h->near_leaf = P<NearEnt>(*nePrev);
+    h->near_leaf_bytes = sizeof(NearEnt) * (size_t)std::max(1ll, h->plan[L].near_bound);
 
     // M2L tiles: TT same-parity cells of one level
     std::vector<Tile> &tiles = h->h_tiles;
@@ -846,7 +842,7 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
         CK(cudaStreamWaitEvent(h->s_far, h->ev_fork, 0));
         // near field only; L2P after the join
         if (ev) CK(cudaEventRecord(evs[EV_P2P0], sn));
-        launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf,
+        launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_nl, h->near_leaf,
                          P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), nullptr, P<R4>(h->H), sn);
         if (ev) CK(cudaEventRecord(evs[EV_P2P1], sn));
     }
@@ -854,7 +850,7 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
     CK(cudaMemsetAsync(h->V.p, 0, sizeof(double) * (size_t)ncellp * KP, sf));
     launch_p2m<real>(p, KP, L, P<int>(h->leaf_start), P<R4>(h->A), P<R2>(h->B), P<real>(h->Q), sf);
     if (ev) CK(cudaEventRecord(evs[EV_P2M], sf));
-    for (int l = L - 1; l >= 0; --l) launch_m2m<real>(p, KP, l, P<Geom>(h->geomd), P<real>(h->Q), sf);
+    launch_m2m_all<real>(p, KP, L, P<Geom>(h->geomd), P<real>(h->Q), sf);
     if (ev) CK(cudaEventRecord(evs[EV_M2M], sf));
     if (tc)
         launch_m2l_tc(p, KP, P<Tile>(h->tiles), h->ntiles, P<M2LItem>(h->items), h->nitems,
@@ -873,8 +869,7 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
                          P<real>(h->Q), P<real>(h->D), h->ldD, P<uint16_t>(h->itab), h->maxdeg,
                          P<Geom>(h->geomd), P<double>(h->V), sf);
     if (ev) CK(cudaEventRecord(evs[EV_M2L], sf));
-    for (int l = 2; l <= L; ++l)
-        launch_l2l(p, KP, l, L, P<Geom>(h->geomd), P<int>(h->leaf_start), P<double>(h->V), sf);
+    launch_l2l_all(p, KP, L, P<Geom>(h->geomd), P<int>(h->leaf_start), P<double>(h->V), sf);
     if (ev) CK(cudaEventRecord(evs[EV_L2L], sf));
     if (ovl) {
         CK(cudaEventRecord(h->ev_join, h->s_far));
@@ -884,7 +879,7 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
                          P<R4>(h->H), s);
     } else {
         if (ev) CK(cudaEventRecord(evs[EV_P2P0], s));
-        launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf,
+        launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_nl, h->near_leaf,
                          P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), P<double>(h->V),
                          P<R4>(h->H), s);
         if (ev) CK(cudaEventRecord(evs[EV_P2P1], s));
@@ -1120,7 +1115,7 @@ ccfmm_status fmm_stats(ccfmm_t h, ccfmm_stats *out)
     Readback *drb = P<Readback>(h->rb);
     if (h->built && !h->pairs_counted) {
         CK(cudaMemsetAsync(&drb->pairs, 0, sizeof(unsigned long long), h->stream));
-        launch_p2p_pair_count(h->L, P<int>(h->leaf_start), h->near_start_leaf, h->near_leaf,
+        launch_p2p_pair_count(h->L, P<int>(h->leaf_start), h->near_nl, h->near_leaf,
                               &drb->pairs, h->stream);
         CK(cudaMemcpyAsync(&h->hrb->pairs, &drb->pairs, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, h->stream));
@@ -1194,7 +1189,7 @@ void fmm_destroy(ccfmm_t h)
     DevBuf *bufs[] = {&h->pos, &h->mom, &h->keys, &h->keys2, &h->keys3, &h->idx, &h->idx2,
                       &h->idx3, &h->sorttemp, &h->scantemp, &h->geomd, &h->box6, &h->userbox,
                       &h->partial, &h->rb, &h->leaf_start, &h->A, &h->B, &h->H, &h->cube,
-                      &h->nsA, &h->nsB, &h->neA, &h->neB, &h->ncnt, &h->fcnt, &h->fstart,
+                      &h->nl, &h->neA, &h->neB, &h->cflag, &h->crank,
                       &h->far, &h->far_off, &h->far_num, &h->tiles, &h->tcount, &h->tstart,
                       &h->ent_u, &h->ent_src, &h->offs, &h->fst, &h->fq, &h->fval, &h->fdense,
                       &h->D, &h->itab, &h->Q, &h->V, &h->Hout, &h->epart, &h->items,
@@ -1253,12 +1248,12 @@ ccfmm_status fmm_get_pairs(ccfmm_t h, int kind, int64_t *pairs, int64_t capacity
     std::vector<int64_t> out;
     if (kind == 0) {
         long long nleaf = 1ll << L;
-        std::vector<int> ns(nleaf + 1);
-        CK(cudaMemcpy(ns.data(), h->near_start_leaf, sizeof(int) * (nleaf + 1), cudaMemcpyDeviceToHost));
-        std::vector<NearEnt> ent(std::max(ns[nleaf], 1));
-        CK(cudaMemcpy(ent.data(), h->near_leaf, sizeof(NearEnt) * ns[nleaf], cudaMemcpyDeviceToHost));
+        std::vector<int2> nl(nleaf);
+        CK(cudaMemcpy(nl.data(), h->near_nl, sizeof(int2) * nleaf, cudaMemcpyDeviceToHost));
+        std::vector<NearEnt> ent(h->near_leaf_bytes / sizeof(NearEnt));
+        CK(cudaMemcpy(ent.data(), h->near_leaf, h->near_leaf_bytes, cudaMemcpyDeviceToHost));
         for (long long k = 0; k < nleaf; ++k)
-            for (int e = ns[k]; e < ns[k + 1]; ++e) {
+            for (int e = nl[k].x; e < nl[k].x + nl[k].y; ++e) {
                 out.push_back(nleaf + k);
                 out.push_back(nleaf + ent[e].src);
             }

@@ -161,20 +161,20 @@ template <typename real>
 void launch_permute_moments(const double *mom, const int *perm, long long n,
                             typename vec4<real>::t *A, typename vec2<real>::t *B,
                             cudaStream_t s);
-void launch_level_counts(const int *leaf_start, int L, int *d_ne, cudaStream_t s);
+// non-empty cells per level (d_ne); with flags != nullptr also flags[hid] =
+// 1 for every non-empty cell, 0 otherwise (flags[0] = 0)
+void launch_level_counts(const int *leaf_start, int L, int *d_ne, int *flags, cudaStream_t s);
 void launch_check_finite(const double *x, long long n, int *d_flags, cudaStream_t s);
 
 // ------------------------------------------------------------------ lists.cu
-void launch_list_count(int level, const int *leaf_start, int L, const int *near_start_prev,
+// one level of the interaction lists in fixed slots (see lists.cu): rank =
+// exclusive prefix of the non-empty flags over all heap ids; nl[hid] = (first
+// near entry, count); near_total / far_total receive the level's totals
+void launch_list_level(int level, const int *leaf_start, int L, const int *rank, int2 *nl,
                        const NearEnt *near_prev, const int *cube, OffsetCube cube_info, int axis,
-                       int *ncnt, int *fcnt, int *d_flags, cudaStream_t s);
-// near_total / far_total: where the level's list totals are copied for the host
-void launch_list_fill_impl(int level, const int *leaf_start, int L, const int *near_start_prev,
-                           const NearEnt *near_prev, const int *cube, OffsetCube cube_info,
-                           int axis, const int *near_start, NearEnt *near_out,
-                           const int *far_start, long long far_base, FarEnt *far_out,
-                           int *far_off, int *far_num, int *near_total, int *far_total,
-                           int *d_flags, cudaStream_t s);
+                       int NB, NearEnt *near_out, long long far_base, int FB, FarEnt *far_out,
+                       int *far_off, int *far_num, int *near_total, int *far_total, int *d_flags,
+                       cudaStream_t s);
 void launch_tile_count(const Tile *tiles, int ntiles, const int *far_off, const int *far_num,
                        const FarEnt *far, int max_bits, int *counts, cudaStream_t s);
 // entries get the D table of their offset class (dmap[class])
@@ -194,10 +194,12 @@ void launch_itable(int p, int KP, int maxdeg, uint16_t *it, cudaStream_t s);
 template <typename real>
 void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, real *Q, cudaStream_t s);
+// M2M over all levels (L-1 .. 0) and L2L over all levels (2 .. L), three
+// levels per launch
 template <typename real>
-void launch_m2m(int p, int KP, int level, const Geom *d_geom, real *Q, cudaStream_t s);
-void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *leaf_start,
-                double *V, cudaStream_t s);
+void launch_m2m_all(int p, int KP, int L, const Geom *d_geom, real *Q, cudaStream_t s);
+void launch_l2l_all(int p, int KP, int L, const Geom *d_geom, const int *leaf_start, double *V,
+                    cudaStream_t s);
 
 // ------------------------------------------------------------------ m2l.cu
 // FP32 M2L work item: a run of at most M2L_EC consecutive entries of a tile
@@ -237,7 +239,7 @@ void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
 
 // ------------------------------------------------------------------ p2p.cu
 template <typename real>
-void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_start,
+void launch_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl,
                 const NearEnt *near, const Geom *d_geom, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
                 cudaStream_t s);
@@ -250,7 +252,7 @@ void launch_finish(const typename vec4<real>::t *H, const int *perm, const doubl
                    long long n, double *H_out, double *partial, double *d_E, cudaStream_t s);
 void launch_direct(const double *pos, const double *mom, long long n, const long long *tgt,
                    long long nt, double *H_out, cudaStream_t s);
-void launch_p2p_pair_count(int L, const int *leaf_start, const int *near_start,
+void launch_p2p_pair_count(int L, const int *leaf_start, const int2 *near_nl,
                            const NearEnt *near, unsigned long long *d_count, cudaStream_t s);
 
 }  // namespace ccfmm

@@ -294,114 +294,159 @@ void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4
 }
 
 // ---------------------------------------------------------------------------
-// M2M (Eq. momentshift) from level l+1 to level l.  The child centre sits at
-// -w/2 (bit 0) or +w/2 (bit 1) along the axis split at level l+1, so only
-// shifts along that axis appear: Q_n += sum_j c^j/j! Q^child_{n - j e_s}.
+// M2M (Eq. momentshift) and L2L (Eq. taylorshift, FP64), several levels per
+// launch.  The child centre sits at -w/2 (bit 0) or +w/2 (bit 1) along the
+// axis split at the child's level, so only shifts along that axis appear:
+//     M2M  Q_n(parent) = sum_children sum_t c^t/t! Q^child_{n - t e_s},
+//     L2L  V^child_n  += sum_t c^t/t! V^parent_{n + t e_s},  |n| + t <= p.
+// A block owns a subtree of depth D <= 3 below a cell of level l0 and
+// carries the expansions of one level of it in shared memory to the next,
+// so that the whole upward pass takes ceil(L / 3) launches (the downward
+// pass ceil((L - 1) / 3)).  The shift factors c^t/t! of the two children are
+// formed once per level by the recurrence f_t = f_(t-1) c / t.
 // ---------------------------------------------------------------------------
-// Block: threadIdx.x = coefficient (KP rounded up to a warp multiple),
-// threadIdx.y = one of SH_C cells; the shift factors c^t/t! of the two
-// children are formed once per block by the same recurrence as per term.
-constexpr int SH_C = 4;
+constexpr int SUB_T = 256;
+constexpr int SUB_D = 3;  // levels per launch
+constexpr int SUB_KP = ((nterms(PMAX) - 1 + 7) / 8) * 8;
 
+// Q of the 2^D descendants at level l0 + D (final) -> Q of levels
+// l0 + D - 1 .. l0 of the subtree rooted at key r (blockIdx.x) of level l0
 template <typename real>
-__global__ void k_m2m(int p, int KP, int l, const Geom *g, real *Q)
+__global__ void __launch_bounds__(SUB_T) k_m2m_sub(int p, int KP, int l0, int D, const Geom *g,
+                                                   real *Q)
 {
+    __shared__ real qs[2][1 << SUB_D][SUB_KP];
     __shared__ real fs[2][PMAX + 1];
-    const int s = g->axis[l + 1];
-    if (threadIdx.y == 0 && threadIdx.x < 2) {
-        const real hw = (real)(0.5 * g->w[l + 1][s]);
-        const real cs = threadIdx.x ? hw : -hw;
-        real f = (real)1;
-        fs[threadIdx.x][0] = f;
-        for (int t = 1; t <= p; ++t) {
-            f = f * cs / (real)t;
-            fs[threadIdx.x][t] = f;
-        }
-    }
-    __syncthreads();
     const int K = nterms(p) - 1;
-    const long long ncell = 1ll << l;
-    const long long key = (long long)blockIdx.x * SH_C + threadIdx.y;
-    const int c = threadIdx.x;
-    if (key >= ncell || c >= KP) return;
-    const long long hid = ncell + key;
-    if (c >= K) {
-        Q[hid * KP + c] = (real)0;
-        return;
+    const long long r = blockIdx.x;
+    int cur = 0;
+    {
+        const int n = 1 << D;
+        const long long hid0 = (1ll << (l0 + D)) + (r << D);
+        for (int i = threadIdx.x; i < n * KP; i += SUB_T)
+            qs[0][i / KP][i % KP] = Q[(hid0 + i / KP) * KP + i % KP];
     }
-    int n[3];
-    midx_inv(c + 1, n[0], n[1], n[2]);
-    real acc = (real)0;
-    for (int b = 0; b < 2; ++b) {
-        const real *Qc = Q + (2 * hid + b) * KP;
-        for (int t = 0; t <= n[s]; ++t) {
-            int m[3] = {n[0], n[1], n[2]};
-            m[s] -= t;
-            if (m[0] + m[1] + m[2] > 0) acc += fs[b][t] * Qc[midx(m[0], m[1], m[2]) - 1];
+    for (int d = D - 1; d >= 0; --d) {
+        const int lp = l0 + d;  // parent level of this step
+        const int sx = g->axis[lp + 1];
+        __syncthreads();  // qs[cur] complete, fs free
+        if (threadIdx.x < 2) {
+            const real hw = (real)(0.5 * g->w[lp + 1][sx]);
+            const real cs = threadIdx.x ? hw : -hw;
+            real f = (real)1;
+            fs[threadIdx.x][0] = f;
+            for (int t = 1; t <= p; ++t) {
+                f = f * cs / (real)t;
+                fs[threadIdx.x][t] = f;
+            }
         }
+        __syncthreads();
+        const int n = 1 << d;
+        const long long hidp = (1ll << lp) + (r << d);
+        for (int i = threadIdx.x; i < n * KP; i += SUB_T) {
+            const int cell = i / KP, c = i - cell * KP;
+            real acc = (real)0;
+            if (c < K) {
+                int nn[3];
+                midx_inv(c + 1, nn[0], nn[1], nn[2]);
+                for (int b = 0; b < 2; ++b) {
+                    const real *Qc = qs[cur][2 * cell + b];
+                    for (int t = 0; t <= nn[sx]; ++t) {
+                        int m[3] = {nn[0], nn[1], nn[2]};
+                        m[sx] -= t;
+                        if (m[0] + m[1] + m[2] > 0) acc += fs[b][t] * Qc[midx(m[0], m[1], m[2]) - 1];
+                    }
+                }
+            }
+            qs[cur ^ 1][cell][c] = acc;
+            Q[(hidp + cell) * KP + c] = acc;
+        }
+        cur ^= 1;
     }
-    Q[hid * KP + c] = acc;
 }
 
 template <typename real>
-void launch_m2m(int p, int KP, int level, const Geom *d_geom, real *Q, cudaStream_t s)
+void launch_m2m_all(int p, int KP, int L, const Geom *d_geom, real *Q, cudaStream_t s)
 {
-    const long long ncell = 1ll << level;
-    const dim3 blk((unsigned)((KP + 31) / 32 * 32), SH_C);
-    note_launch();
-    k_m2m<real><<<(unsigned)((ncell + SH_C - 1) / SH_C), blk, 0, s>>>(p, KP, level, d_geom, Q);
+    for (int cur = L; cur > 0;) {
+        const int D = cur < SUB_D ? cur : SUB_D;
+        const int l0 = cur - D;
+        note_launch();
+        k_m2m_sub<real><<<(unsigned)(1ll << l0), SUB_T, 0, s>>>(p, KP, l0, D, d_geom, Q);
+        cur = l0;
+    }
 }
 
-// ---------------------------------------------------------------------------
-// L2L (Eq. taylorshift) from level l-1 to level l, in FP64:
-// V^child_n += sum_j c^j/j! V^parent_{n + j e_s}, |n| + j <= p.
-// ---------------------------------------------------------------------------
-__global__ void k_l2l(int p, int KP, int l, int L, const Geom *g, const int *leaf_start, double *V)
+// V of the root (key r of level l0, final) and the levels' own M2L
+// contributions -> V of levels l0 + 1 .. l0 + D of the subtree (FP64);
+// empty cells are skipped (their coefficients never reach a field point)
+__global__ void __launch_bounds__(SUB_T) k_l2l_sub(int p, int KP, int l0, int D, int L,
+                                                   const Geom *g, const int *leaf_start, double *V)
 {
-    // fs[side][t] = c^t / t! for the two children, c = -w/2 (lower), +w/2
-    // (upper): 2p FP64 divisions per block instead of one per term
+    __shared__ double vs[2][1 << SUB_D][SUB_KP];
     __shared__ double fs[2][PMAX + 1];
-    const int s = g->axis[l];
-    if (threadIdx.y == 0 && threadIdx.x < 2) {
-        const double cs = threadIdx.x ? 0.5 * g->w[l][s] : -0.5 * g->w[l][s];
-        double f = 1.0;
-        fs[threadIdx.x][0] = 1.0;
-        for (int t = 1; t <= p; ++t) {
-            f = f * cs / (double)t;
-            fs[threadIdx.x][t] = f;
-        }
-    }
-    __syncthreads();
+    __shared__ int full[2][1 << SUB_D];
     const int K = nterms(p) - 1;
-    const long long ncell = 1ll << l;
-    const long long key = (long long)blockIdx.x * SH_C + threadIdx.y;
-    const int c = threadIdx.x;
-    if (key >= ncell || c >= K) return;
-    const int sh = L - l;
-    if (leaf_start[(key + 1) << sh] == leaf_start[key << sh]) return;
-    const long long hid = ncell + key;
-    int n[3];
-    midx_inv(c + 1, n[0], n[1], n[2]);
-    const double *f = fs[key & 1];
-    const double *Vp = V + (hid >> 1) * KP;
-    const int kn = n[0] + n[1] + n[2];
-    double acc = 0.0;
-    for (int t = 0; t <= p - kn; ++t) {
-        int m[3] = {n[0], n[1], n[2]};
-        m[s] += t;
-        acc += f[t] * Vp[midx(m[0], m[1], m[2]) - 1];
+    const long long r = blockIdx.x;
+    int cur = 0;
+    const long long hr = (1ll << l0) + r;
+    for (int c = threadIdx.x; c < KP; c += SUB_T) vs[0][0][c] = V[hr * KP + c];
+    if (threadIdx.x == 0)
+        full[0][0] = leaf_start[(r + 1) << (L - l0)] > leaf_start[r << (L - l0)];
+    for (int d = 1; d <= D; ++d) {
+        const int l = l0 + d;
+        const int sx = g->axis[l];
+        __syncthreads();  // vs[cur], full[cur] complete; fs free
+        if (threadIdx.x < 2) {
+            const double cs = threadIdx.x ? 0.5 * g->w[l][sx] : -0.5 * g->w[l][sx];
+            double f = 1.0;
+            fs[threadIdx.x][0] = 1.0;
+            for (int t = 1; t <= p; ++t) {
+                f = f * cs / (double)t;
+                fs[threadIdx.x][t] = f;
+            }
+        }
+        const int n = 1 << d;
+        const long long key0 = r << d;
+        if (threadIdx.x < n) {
+            const long long key = key0 + threadIdx.x;
+            const int sh = L - l;
+            full[cur ^ 1][threadIdx.x] =
+                full[cur][threadIdx.x >> 1] && leaf_start[(key + 1) << sh] > leaf_start[key << sh];
+        }
+        __syncthreads();
+        const long long hid0 = (1ll << l) + key0;
+        for (int i = threadIdx.x; i < n * KP; i += SUB_T) {
+            const int cell = i / KP, c = i - cell * KP;
+            if (c >= K || !full[cur ^ 1][cell]) continue;
+            int nn[3];
+            midx_inv(c + 1, nn[0], nn[1], nn[2]);
+            const double *f = fs[cell & 1];  // key0 is even: the cell's side is its low bit
+            const double *Vp = vs[cur][cell >> 1];
+            const int kn = nn[0] + nn[1] + nn[2];
+            double acc = 0.0;
+            for (int t = 0; t <= p - kn; ++t) {
+                int m[3] = {nn[0], nn[1], nn[2]};
+                m[sx] += t;
+                acc += f[t] * Vp[midx(m[0], m[1], m[2]) - 1];
+            }
+            const double v = V[(hid0 + cell) * KP + c] + acc;
+            V[(hid0 + cell) * KP + c] = v;
+            vs[cur ^ 1][cell][c] = v;
+        }
+        cur ^= 1;
     }
-    V[hid * KP + c] += acc;
 }
 
-void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *leaf_start,
-                double *V, cudaStream_t s)
+void launch_l2l_all(int p, int KP, int L, const Geom *d_geom, const int *leaf_start, double *V,
+                    cudaStream_t s)
 {
-    const long long ncell = 1ll << level;
-    const dim3 blk((unsigned)((nterms(p) - 1 + 31) / 32 * 32), SH_C);
-    note_launch();
-    k_l2l<<<(unsigned)((ncell + SH_C - 1) / SH_C), blk, 0, s>>>(p, KP, level, L, d_geom,
-                                                               leaf_start, V);
+    for (int cur = 1; cur < L;) {
+        const int D = L - cur < SUB_D ? L - cur : SUB_D;
+        note_launch();
+        k_l2l_sub<<<(unsigned)(1ll << cur), SUB_T, 0, s>>>(p, KP, cur, D, L, d_geom, leaf_start, V);
+        cur += D;
+    }
 }
 
 #define INST(real)                                                                              \
@@ -409,7 +454,7 @@ void launch_l2l(int p, int KP, int level, int L, const Geom *d_geom, const int *
                                        const double4 *, int, real *, int, cudaStream_t);        \
     template void launch_p2m<real>(int, int, int, const int *, const vec4<real>::t *,           \
                                    const vec2<real>::t *, real *, cudaStream_t);                \
-    template void launch_m2m<real>(int, int, int, const Geom *, real *, cudaStream_t);          \
+    template void launch_m2m_all<real>(int, int, int, const Geom *, real *, cudaStream_t);      \
 
 INST(float)
 INST(double)

@@ -38,56 +38,6 @@ __device__ __forceinline__ int cube_class(const int *cube, const OffsetCube &ci,
     return v;
 }
 
-// warp per cell c of level lv: count its near and far candidates; returns
-// (near, far) in every lane
-__device__ __forceinline__ int2 list_count_cell(int lv, long long c, int lane,
-                                                const int *leaf_start, int L,
-                                                const int *nstart_prev, const NearEnt *near_prev,
-                                                const int *cube, const OffsetCube &ci, int axis,
-                                                int *flags)
-{
-    int nn = 0, nf = 0;
-    if (cell_count(leaf_start, L, lv, c) > 0) {
-        long long P = c >> 1;
-        int bc = (int)(c & 1);
-        int e1 = nstart_prev[P + 1];
-        for (int e = nstart_prev[P] + lane; e < e1; e += 32) {
-            NearEnt ne = near_prev[e];
-            for (int ba = 0; ba < 2; ++ba) {
-                long long a = 2ll * ne.src + ba;
-                if (cell_count(leaf_start, L, lv, a) == 0) continue;
-                int o[3] = {ne.ox, ne.oy, ne.oz};
-                o[axis] = 2 * o[axis] + bc - ba;
-                int cls = cube_class(cube, ci, o, flags);
-                if (cls == OFF_NEAR)
-                    ++nn;
-                else if (cls >= 0)
-                    ++nf;
-            }
-        }
-    }
-    for (int o = 16; o; o >>= 1) {
-        nn += __shfl_xor_sync(0xffffffffu, nn, o);
-        nf += __shfl_xor_sync(0xffffffffu, nf, o);
-    }
-    return make_int2(nn, nf);
-}
-
-__global__ void k_list_count(int lv, const int *leaf_start, int L, const int *nstart_prev,
-                             const NearEnt *near_prev, const int *cube, OffsetCube ci, int axis,
-                             int *ncnt, int *fcnt, int *flags)
-{
-    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (c >= (1ll << lv)) return;
-    int2 r = list_count_cell(lv, c, lane, leaf_start, L, nstart_prev, near_prev, cube, ci, axis,
-                             flags);
-    if (lane == 0) {
-        ncnt[c] = r.x;
-        fcnt[c] = r.y;
-    }
-}
-
 __device__ __forceinline__ int warp_excl(int v, int lane, int *total)
 {
     int x = v;
@@ -99,43 +49,55 @@ __device__ __forceinline__ int warp_excl(int v, int lane, int *total)
     return x - v;
 }
 
-// warp per cell: write the candidates in the order (partner entry, child bit)
-__device__ __forceinline__ void list_fill_cell(int lv, long long c, int lane,
-                                               const int *leaf_start, int L,
-                                               const int *nstart_prev, const NearEnt *near_prev,
-                                               const int *cube, const OffsetCube &ci, int axis,
-                                               const int *near_start, NearEnt *near_out,
-                                               const int *far_start, long long far_base,
-                                               FarEnt *far_out, int *far_off, int *far_num,
-                                               int *flags)
+// One level in one pass, warp per cell c.  Lists live in fixed slots: the
+// r-th non-empty cell of the level (r = rank[hid] - rank[2^lv], rank = the
+// exclusive prefix of the non-empty flags over all heap ids) owns NB near and
+// FB far entries, NB / FB = the level's near / far offset classes, which
+// bound the partners a cell can have (each offset at most once).  The cell's
+// near list is nl[hid] = (first slot entry, count); its far list far_off /
+// far_num.  No count pass or scan is needed; the level totals go to
+// near_total / far_total for the statistics.  The order of a cell's entries,
+// (parent entry, child bit), is the same as the oracle's recursion visits
+// them and does not depend on the launch.
+__global__ void k_list_level(int lv, const int *leaf_start, int L, const int *rank, int2 *nl,
+                             const NearEnt *near_prev, const int *cube, OffsetCube ci, int axis,
+                             int NB, NearEnt *near_out, long long far_base, int FB,
+                             FarEnt *far_out, int *far_off, int *far_num, int *near_total,
+                             int *far_total, int *flags)
 {
-    long long hid = (1ll << lv) + c;
-    long long fs = far_base + far_start[c];
-    int fn = far_start[c + 1] - far_start[c];
-    if (lane == 0) {
-        far_off[hid] = (int)fs;
-        far_num[hid] = fn;
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const long long nc = 1ll << lv;
+    if (c >= nc) return;
+    const long long hid = nc + c;
+    if (cell_count(leaf_start, L, lv, c) == 0) {
+        if (lane == 0) {
+            nl[hid] = make_int2(0, 0);
+            far_off[hid] = 0;
+            far_num[hid] = 0;
+        }
+        return;
     }
-    if (cell_count(leaf_start, L, lv, c) == 0) return;
-    long long P = c >> 1;
-    int bc = (int)(c & 1);
-    int e0 = nstart_prev[P], e1 = nstart_prev[P + 1];
-    long long nbase = near_start[c];
-    long long fbase = fs;
-    long long nend = near_start[c + 1], fend = fs + fn;
+    const long long r = rank[hid] - rank[nc];
+    const long long nbase0 = r * NB, fbase0 = far_base + r * FB;
+    const int2 pl = nl[hid >> 1];
+    const int bc = (int)(c & 1);
+    const int e0 = pl.x, e1 = pl.x + pl.y;
+    long long nbase = nbase0, fbase = fbase0;
+    const long long nend = nbase0 + NB, fend = fbase0 + FB;
     for (int eb = e0; eb < e1; eb += 32) {
-        int e = eb + lane;
+        const int e = eb + lane;
         NearEnt out_n[2];
         FarEnt out_f[2];
         int nn = 0, nf = 0;
         if (e < e1) {
-            NearEnt ne = near_prev[e];
+            const NearEnt ne = near_prev[e];
             for (int ba = 0; ba < 2; ++ba) {
-                long long a = 2ll * ne.src + ba;
+                const long long a = 2ll * ne.src + ba;
                 if (cell_count(leaf_start, L, lv, a) == 0) continue;
                 int o[3] = {ne.ox, ne.oy, ne.oz};
                 o[axis] = 2 * o[axis] + bc - ba;
-                int cls = cube_class(cube, ci, o, flags);
+                const int cls = cube_class(cube, ci, o, flags);
                 if (cls == OFF_NEAR) {
                     out_n[nn].src = (int)a;
                     out_n[nn].ox = o[0];
@@ -150,17 +112,17 @@ __device__ __forceinline__ void list_fill_cell(int lv, long long c, int lane,
             }
         }
         int tn, tf;
-        int pn = warp_excl(nn, lane, &tn);
-        int pf = warp_excl(nf, lane, &tf);
+        const int pn = warp_excl(nn, lane, &tn);
+        const int pf = warp_excl(nf, lane, &tf);
         for (int j = 0; j < nn; ++j) {
-            long long at = nbase + pn + j;
+            const long long at = nbase + pn + j;
             if (at < nend)
                 near_out[at] = out_n[j];
             else
                 atomicOr(flags, FLAG_LIST_OVERFLOW);
         }
         for (int j = 0; j < nf; ++j) {
-            long long at = fbase + pf + j;
+            const long long at = fbase + pf + j;
             if (at < fend)
                 far_out[at] = out_f[j];
             else
@@ -169,51 +131,28 @@ __device__ __forceinline__ void list_fill_cell(int lv, long long c, int lane,
         nbase += tn;
         fbase += tf;
     }
-}
-
-// one level; thread 0 also copies the level's list totals (the last entries
-// of the scanned counts) to near_total / far_total for the host
-__global__ void k_list_fill(int lv, const int *leaf_start, int L, const int *nstart_prev,
-                            const NearEnt *near_prev, const int *cube, OffsetCube ci, int axis,
-                            const int *near_start, NearEnt *near_out, const int *far_start,
-                            long long far_base, FarEnt *far_out, int *far_off, int *far_num,
-                            int *near_total, int *far_total, int *flags)
-{
-    long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    const long long nc = 1ll << lv;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *near_total = near_start[nc];
-        *far_total = far_start[nc];
+    if (lane == 0) {
+        const int tn = (int)min(nbase - nbase0, (long long)NB);
+        const int tf = (int)min(fbase - fbase0, (long long)FB);
+        nl[hid] = make_int2((int)nbase0, tn);
+        far_off[hid] = (int)fbase0;
+        far_num[hid] = tf;
+        atomicAdd(near_total, tn);
+        atomicAdd(far_total, tf);
     }
-    if (c >= nc) return;
-    list_fill_cell(lv, c, lane, leaf_start, L, nstart_prev, near_prev, cube, ci, axis, near_start,
-                   near_out, far_start, far_base, far_out, far_off, far_num, flags);
 }
 
-void launch_list_count(int level, const int *leaf_start, int L, const int *near_start_prev,
+void launch_list_level(int level, const int *leaf_start, int L, const int *rank, int2 *nl,
                        const NearEnt *near_prev, const int *cube, OffsetCube cube_info, int axis,
-                       int *ncnt, int *fcnt, int *d_flags, cudaStream_t s)
+                       int NB, NearEnt *near_out, long long far_base, int FB, FarEnt *far_out,
+                       int *far_off, int *far_num, int *near_total, int *far_total, int *d_flags,
+                       cudaStream_t s)
 {
-    long long threads = (1ll << level) * 32;
+    const long long threads = (1ll << level) * 32;
     note_launch();
-    k_list_count<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        level, leaf_start, L, near_start_prev, near_prev, cube, cube_info, axis, ncnt, fcnt,
-        d_flags);
-}
-
-void launch_list_fill_impl(int level, const int *leaf_start, int L, const int *near_start_prev,
-                           const NearEnt *near_prev, const int *cube, OffsetCube cube_info,
-                           int axis, const int *near_start, NearEnt *near_out,
-                           const int *far_start, long long far_base, FarEnt *far_out,
-                           int *far_off, int *far_num, int *near_total, int *far_total,
-                           int *d_flags, cudaStream_t s)
-{
-    long long threads = (1ll << level) * 32;
-    note_launch();
-    k_list_fill<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        level, leaf_start, L, near_start_prev, near_prev, cube, cube_info, axis, near_start,
-        near_out, far_start, far_base, far_out, far_off, far_num, near_total, far_total, d_flags);
+    k_list_level<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        level, leaf_start, L, rank, nl, near_prev, cube, cube_info, axis, NB, near_out, far_base,
+        FB, far_out, far_off, far_num, near_total, far_total, d_flags);
 }
 
 // ---------------------------------------------------------------------------

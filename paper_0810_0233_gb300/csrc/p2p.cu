@@ -161,7 +161,7 @@ __device__ __forceinline__ Sum3<real> l2p_eval(int p, const real *vs, real x, re
 //    no other leaf can hold a point at the target's position.
 template <typename real>
 __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, int L, const int *leaf_start,
-                                               const int *near_start, const NearEnt *near,
+                                               const int2 *near_nl, const NearEnt *near,
                                                const Geom *g, const typename vec4<real>::t *A,
                                                const typename vec2<real>::t *B, const double *V,
                                                typename vec4<real>::t *H)
@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
     const long long key = blockIdx.x;
     const int t0 = leaf_start[key], nt = leaf_start[key + 1] - t0;
     if (nt == 0) return;
-    const int e0 = near_start[key], e1 = near_start[key + 1];
+    const int2 nlk = near_nl[key];  // (first entry, count) of the leaf's near list
+    const int e0 = nlk.x, e1 = nlk.x + nlk.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = nterms(p) - 1;
     const long long hid = (1ll << L) + key;
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
 }
 
 template <typename real>
-void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_start,
+void launch_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl,
                 const NearEnt *near, const Geom *d_geom, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
                 cudaStream_t s)
@@ -346,7 +347,7 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int *near_sta
     static_assert(P2P_CH * 4 >= 3 * P2P_TPT * P2P_T, "the stripe sums reuse the staging buffer");
     cudaFuncSetAttribute(k_p2p<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
-    k_p2p<real><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start, near_start, near,
+    k_p2p<real><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start, near_nl, near,
                                                          d_geom, A, B, V, H);
 }
 
@@ -514,7 +515,7 @@ void launch_direct(const double *pos, const double *mom, long long n, const long
 
 // pairs (i, j), j != i, evaluated by the near field: sum over leaves of
 // nt * (sum of near-leaf counts) - nt
-__global__ void k_pair_count(int L, const int *leaf_start, const int *near_start,
+__global__ void k_pair_count(int L, const int *leaf_start, const int2 *near_nl,
                              const NearEnt *near, unsigned long long *count)
 {
     long long key = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -522,23 +523,24 @@ __global__ void k_pair_count(int L, const int *leaf_start, const int *near_start
     long long nt = leaf_start[key + 1] - leaf_start[key];
     if (!nt) return;
     long long ns = 0;
-    for (int e = near_start[key]; e < near_start[key + 1]; ++e)
+    const int2 nlk = near_nl[key];
+    for (int e = nlk.x; e < nlk.x + nlk.y; ++e)
         ns += leaf_start[near[e].src + 1] - leaf_start[near[e].src];
     atomicAdd(count, (unsigned long long)(nt * ns - nt));
 }
 
-void launch_p2p_pair_count(int L, const int *leaf_start, const int *near_start,
+void launch_p2p_pair_count(int L, const int *leaf_start, const int2 *near_nl,
                            const NearEnt *near, unsigned long long *d_count, cudaStream_t s)
 {
     cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s);
     long long n = 1ll << L;
     note_launch();
-    k_pair_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, leaf_start, near_start, near,
+    k_pair_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, leaf_start, near_nl, near,
                                                             d_count);
 }
 
 #define INST(real)                                                                              \
-    template void launch_p2p<real>(int, int, int, const int *, const int *, const NearEnt *,   \
+    template void launch_p2p<real>(int, int, int, const int *, const int2 *, const NearEnt *,  \
                                    const Geom *, const vec4<real>::t *, const vec2<real>::t *,  \
                                    const double *, vec4<real>::t *, cudaStream_t);              \
     template void launch_finish<real>(const vec4<real>::t *, const int *, const double *,       \

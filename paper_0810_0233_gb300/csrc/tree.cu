@@ -298,7 +298,7 @@ void launch_permute_moments(const double *mom, const int *perm, long long n,
 }
 
 // non-empty cells per level (levels 0..L), from the leaf ranges
-__global__ void k_level_counts(const int *leaf_start, int L, int *ne)
+__global__ void k_level_counts(const int *leaf_start, int L, int *ne, int *flags)
 {
     __shared__ int h[LCAP + 1];
     if (threadIdx.x <= LCAP) h[threadIdx.x] = 0;
@@ -310,20 +310,23 @@ __global__ void k_level_counts(const int *leaf_start, int L, int *ne)
         int l = 63 - __clzll(hid);
         long long key = hid - (1ll << l);
         int sh = L - l;
-        if (leaf_start[(key + 1) << sh] > leaf_start[key << sh]) atomicAdd(&h[l], 1);
+        const bool full = leaf_start[(key + 1) << sh] > leaf_start[key << sh];
+        if (full) atomicAdd(&h[l], 1);
+        if (flags) flags[hid] = full ? 1 : 0;
     }
+    if (flags && blockIdx.x == 0 && threadIdx.x == 0) flags[0] = 0;
     __syncthreads();
     if (threadIdx.x <= LCAP && h[threadIdx.x]) atomicAdd(&ne[threadIdx.x], h[threadIdx.x]);
 }
 
-void launch_level_counts(const int *leaf_start, int L, int *d_ne, cudaStream_t s)
+void launch_level_counts(const int *leaf_start, int L, int *d_ne, int *flags, cudaStream_t s)
 {
     cudaMemsetAsync(d_ne, 0, sizeof(int) * (LCAP + 1), s);
     long long ncell = (1ll << (L + 1)) - 1;
     long long nb = (ncell + 255) / 256;
     if (nb > 4096) nb = 4096;
     note_launch();
-    k_level_counts<<<(unsigned)nb, 256, 0, s>>>(leaf_start, L, d_ne);
+    k_level_counts<<<(unsigned)nb, 256, 0, s>>>(leaf_start, L, d_ne, flags);
 }
 
 __global__ void k_check_finite(const double *x, long long n, int *flags)
