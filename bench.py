@@ -284,7 +284,8 @@ def describe_ensemble(ns, total, p, theta):
             "N": total, "samples": ns, "p": p, "theta": theta,
             "precision": "FP32 bulk; FP64 D tensors and FP64 local-expansion accumulation",
             "step": "rotate every moment (Philox4x64-10, angle U[0, 0.05]) + field and energy "
-                    "of every sample; trees fixed; one CUDA graph launch",
+                    "of every sample; trees fixed; one CUDA graph launch of batched stages "
+                    "(one kernel per stage over all samples)",
             "l2": "inputs (%.0f MB of moments) larger than L2" % (total * 24 / 1e6)}
 
 
@@ -299,8 +300,10 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
     mine, o, rows = R.shard(off, rank, world)
     P_, M_ = R.gather_rows(pos, rows), R.gather_rows(mom, rows)
     total = int(o[-1])
+    t0 = time.perf_counter()
     b = C.Batch(torch.from_numpy(P_).to(dev), torch.from_numpy(M_).to(dev), o, p, theta,
-                precision=args.precision, stream=stream)
+                precision=args.precision, stream=stream, autotune=not args.no_autotune)
+    t_create = time.perf_counter() - t0
     E_d = torch.zeros(len(mine), dtype=torch.float64, device=dev)
     counter = [0]
 
@@ -373,7 +376,14 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
                          "note": "all near-pair and M2L flops of the step over the step time; "
                                  "M2L on the tensor cores in every member"},
             "clocks": clk.summary(),
-            "samples_per_rank": len(mine)}
+            "samples_per_rank": len(mine),
+            "kernels_per_step": b.kernels_per_step(),
+            "autotune": {"classes": [{"n_min": c[0], "leaf": c[1], "m2l_item_len": c[2]}
+                                     for c in b.tuning()],
+                         "create_s": t_create,
+                         "note": "per size class (octave of N) the leaf occupancy and M2L item "
+                                 "length of the fastest timed trial evaluation (library "
+                                 "autotuner, at creation, outside the timed steps)"}}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = oracle_ensemble_sample(pos, mom, off, p, theta)
     b.close()
@@ -392,6 +402,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="ensemble: Eq. so leaves for every sample instead of the autotuner")
     ap.add_argument("--no-selector", action="store_true",
                     help="skip the selector object (learned (p, theta, leaf) at 1e-4)")
     ap.add_argument("--profile", action="store_true",

@@ -208,7 +208,9 @@ ccfmm_status fmm_get_pairs(ccfmm_t h, int kind, int64_t *pairs, int64_t capacity
  * cell shape), ent_u_out (entries: D table id), ent_src_out
  * (entries x 128: partner heap id or -1), tiles_out (tiles x 8 int32:
  * level, first, parity, cells, entry start, entry count, offsets, first
- * offset id).  Any output may be NULL; call with all NULL to get sizes. */
+ * offset id; a tile's cells are the non-empty cells of its level with that
+ * parity of the key, numbers first .. first + cells - 1 of them in key
+ * order).  Any output may be NULL; call with all NULL to get sizes. */
 ccfmm_status fmm_get_m2l_data(ccfmm_t h, int64_t *sizes, double *D_out, int32_t *ent_u_out,
                               int32_t *ent_src_out, int32_t *tiles_out);
 
@@ -249,6 +251,32 @@ ccfmm_status fmm_batch_create(const double *positions, const double *moments,
                               const int64_t *offsets, int nsamples, int p, double theta,
                               double leaf_size, ccfmm_prec prec, void *stream, ccfmm_batch_t *out);
 
+/* Options of fmm_batch_create_ex (fmm_batch_create = all zero).
+ *   autotune  nonzero: the library picks, per sample-size class (the
+ *             octaves of N, floor(log2 N)), the leaf occupancy and the
+ *             M2L work-item length (entries of a tile per tensor-core work
+ *             item) by timed trial evaluations of the class's median-size
+ *             sample: leaf = s x {1/2, 1/sqrt2, 1, sqrt2, 2} with s =
+ *             leaf_size (or Eq. so when leaf_size <= 0), item length 32 or
+ *             64; the fastest mean evaluation time wins.  Trials run on the
+ *             batch's first branch stream at creation.
+ *   trials    timed evaluations per candidate (<= 0: 3). */
+typedef struct {
+    int32_t autotune;
+    int32_t trials;
+} ccfmm_batch_opts;
+
+ccfmm_status fmm_batch_create_ex(const double *positions, const double *moments,
+                                 const int64_t *offsets, int nsamples, int p, double theta,
+                                 double leaf_size, ccfmm_prec prec, const ccfmm_batch_opts *opts,
+                                 void *stream, ccfmm_batch_t *out);
+
+/* The autotuner's choice: nclasses size classes (0 without autotune); for
+ * class i < capacity, the smallest N of the class, its leaf occupancy and
+ * its M2L item length (any output array may be NULL). */
+ccfmm_status fmm_batch_tuning(ccfmm_batch_t b, int32_t *nclasses, int64_t *class_nmin,
+                              double *class_leaf, int32_t *class_item_len, int32_t capacity);
+
 /* One time step: every moment m_i (global row i) is turned about a random
  * axis by a random angle, drawn from Philox4x64-10 (Salmon et al., SC 2011)
  * with key (seed, step) and counter (i, 0, 0, 0): from its outputs x0..x3,
@@ -272,7 +300,10 @@ ccfmm_status fmm_batch_set_moments(ccfmm_batch_t b, const double *moments);
  * for inspection with fmm_stats / fmm_get_* only. */
 ccfmm_status fmm_batch_sample(ccfmm_batch_t b, int i, ccfmm_t *out);
 
-/* Total dipoles and kernels launched by one step's graph. */
+/* Total dipoles and kernels launched by one step's graph.  With the FP32
+ * path and the tensor-core M2L every stage of a step is one launch over all
+ * samples (tens of kernels per step, independent of nsamples); otherwise the
+ * graph holds each sample's own launches on parallel branches. */
 ccfmm_status fmm_batch_info(ccfmm_batch_t b, int64_t *total_n, int64_t *kernels_per_step);
 
 void fmm_batch_destroy(ccfmm_batch_t b);

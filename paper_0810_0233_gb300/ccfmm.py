@@ -87,6 +87,10 @@ def load():
             "ccfmm_kernel_launches": (_i64, []),
             "fmm_batch_create": (_int, [_vp, _vp, _vp, _int, _int, _dbl, _dbl, _int, _vp,
                                         ctypes.POINTER(_vp)]),
+            "fmm_batch_create_ex": (_int, [_vp, _vp, _vp, _int, _int, _dbl, _dbl, _int, _vp,
+                                           _vp, ctypes.POINTER(_vp)]),
+            "fmm_batch_tuning": (_int, [_vp, ctypes.POINTER(ctypes.c_int32), _vp, _vp, _vp,
+                                        ctypes.c_int32]),
             "fmm_batch_step": (_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, _dbl, _vp, _vp]),
             "fmm_batch_evaluate": (_int, [_vp, _vp, _vp]),
             "fmm_batch_get_moments": (_int, [_vp, _vp]),
@@ -323,7 +327,7 @@ class Batch:
     """An ensemble of independent samples stepped together (fmm_batch_*)."""
 
     def __init__(self, positions, moments, offsets, p, theta, leaf_size=0.0, precision="mixed",
-                 stream=None):
+                 stream=None, autotune=False, trials=3):
         lib = load()
         self._lib = lib
         off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
@@ -335,8 +339,11 @@ class Batch:
         prec = {"mixed": MIXED, "fp32": MIXED, "fp64": FP64}[precision]
         h = _vp()
         self._p = int(p)
-        _check(lib.fmm_batch_create(pp, pm, _vp(off.ctypes.data), self.ns, int(p), float(theta),
-                                    float(leaf_size), prec, _stream_ptr(stream), ctypes.byref(h)))
+        opts = (ctypes.c_int32 * 2)(1 if autotune else 0, int(trials))
+        _check(lib.fmm_batch_create_ex(pp, pm, _vp(off.ctypes.data), self.ns, int(p),
+                                       float(theta), float(leaf_size), prec,
+                                       _vp(ctypes.addressof(opts)), _stream_ptr(stream),
+                                       ctypes.byref(h)))
         self._h = h
 
     def close(self):
@@ -387,6 +394,19 @@ class Batch:
         f.p = self._p
         f._borrowed = True
         return f
+
+    def tuning(self):
+        """The autotuner's classes: list of (smallest N, leaf occupancy, M2L
+        item length); empty without autotune."""
+        n = ctypes.c_int32()
+        _check(self._lib.fmm_batch_tuning(self._h, ctypes.byref(n), None, None, None, 0))
+        k = n.value
+        nmin = np.zeros(max(k, 1), np.int64)
+        leaf = np.zeros(max(k, 1))
+        il = np.zeros(max(k, 1), np.int32)
+        _check(self._lib.fmm_batch_tuning(self._h, ctypes.byref(n), _vp(nmin.ctypes.data),
+                                          _vp(leaf.ctypes.data), _vp(il.ctypes.data), k))
+        return [(int(nmin[i]), float(leaf[i]), int(il[i])) for i in range(k)]
 
     def kernels_per_step(self):
         n, k = _i64(), _i64()

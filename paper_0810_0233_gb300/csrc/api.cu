@@ -105,6 +105,7 @@ struct Readback {
     int flags;
     int hist[LCAP + 1];
     int ne[LCAP + 1];
+    int ne_odd[LCAP + 1];  // non-empty cells with an odd key, per level
     int near_total[LCAP + 1];
     int far_total[LCAP + 1];
     int ent_total;
@@ -166,7 +167,7 @@ struct ccfmm_s {
     DevBuf pos, mom, keys, keys2, keys3, idx, idx2, idx3, sorttemp, scantemp;
     DevBuf geomd, box6, userbox, partial, rb;
     DevBuf leaf_start, A, B, H;
-    DevBuf cube, nl, neA, neB, cflag, crank;
+    DevBuf cube, nl, neA, neB, cflag, crank, oflag, orank, tkeys, tseg;
     DevBuf far, far_off, far_num, tiles, tcount, tstart, ent_u, ent_src;
     DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
     DevBuf Hout, epart, items, titem0, tnitems, Ps;
@@ -185,9 +186,11 @@ struct ccfmm_s {
     std::vector<M2LItem> h_items;
     std::vector<Tile> h_tiles;
     int h_ns0[2] = {0, 1};
+    int h_seg[2 * (LCAP + 1)];  // tile key segments per (level, parity)
     NearEnt h_e0 = {0, 0, 0, 0};
     int nitems = 0;
     // batch members: energy input and output redirected, no stage events
+    int item_len = M2L_EC;  // entries per M2L work item (the batch autotuner may change it)
     const double *mom_energy = nullptr;
     double *E_dst = nullptr;
     bool quiet = false;
@@ -511,7 +514,9 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
                                    P<uint32_t>(h->keys2), N, P<Geom>(h->geomd), L,
                                    P<double4>(h->A), P<double2>(h->B), s);
     TRY(ensure(h->cflag, sizeof(int) * ncellp));
-    launch_level_counts(P<int>(h->leaf_start), L, drb->ne, P<int>(h->cflag), s);
+    TRY(ensure(h->oflag, sizeof(int) * ncellp));
+    launch_level_counts(P<int>(h->leaf_start), L, drb->ne, P<int>(h->cflag), P<int>(h->oflag),
+                        drb->ne_odd, s);
     KCHECK();
     if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_BS2], s));
     // the plan needs only the depth and the geometry: the host builds it
@@ -586,6 +591,26 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     // are indexed by rank within the level
     scan_exclusive(P<int>(h->cflag), P<int>(h->crank), ncellp, P<int>(h->crank) + ncellp,
                    h->scantemp.p, s);
+    // the M2L tiles' target cells: non-empty cells per level and parity
+    {
+        long long tot = 0;
+        for (int l = 0; l <= LCAP; ++l) {
+            const int odd = l <= L ? h->hrb->ne_odd[l] : 0;
+            const int even = l <= L ? h->hrb->ne[l] - odd : 0;
+            h->h_seg[2 * l] = (int)tot;
+            tot += l >= 2 ? even : 0;
+            h->h_seg[2 * l + 1] = (int)tot;
+            tot += l >= 2 ? odd : 0;
+        }
+        TRY(ensure(h->orank, sizeof(int) * (ncellp + 1)));
+        TRY(ensure(h->tkeys, sizeof(int) * (size_t)std::max(tot, 1ll)));
+        TRY(ensure(h->tseg, sizeof(h->h_seg)));
+        scan_exclusive(P<int>(h->oflag), P<int>(h->orank), ncellp, P<int>(h->orank) + ncellp,
+                       h->scantemp.p, s);
+        CK(cudaMemcpyAsync(h->tseg.p, h->h_seg, sizeof(h->h_seg), cudaMemcpyHostToDevice, s));
+        launch_tile_keys(L, P<int>(h->cflag), P<int>(h->crank), P<int>(h->orank), P<int>(h->tseg),
+                         P<int>(h->tkeys), s);
+    }
     // level 0: the root is near itself (one entry, offset 0)
     CK(cudaMemcpyAsync(P<int2>(h->nl) + 1, h->h_ns0, sizeof(h->h_ns0), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(h->neA.p, &h->h_e0, sizeof(h->h_e0), cudaMemcpyHostToDevice, s));
@@ -614,22 +639,26 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     std::vector<Tile> &tiles = h->h_tiles;
     tiles.clear();
     h->max_bits = 32;
+    // tiles: TT consecutive non-empty cells of one level and parity (empty
+    // cells have no far partners and no field to receive)
     for (int l = 2; l <= L; ++l) {
         LevelPlan &lp = h->plan[l];
         if (lp.farv.empty()) continue;
-        long long half = 1ll << (l - 1);
-        for (int par = 0; par < 2; ++par)
-            for (long long f = 0; f < half; f += TT) {
+        for (int par = 0; par < 2; ++par) {
+            const int cnt = par ? h->hrb->ne_odd[l] : h->hrb->ne[l] - h->hrb->ne_odd[l];
+            for (int f = 0; f < cnt; f += TT) {
                 Tile t;
                 t.level = l;
-                t.first = (int)f;
+                t.first = f;
                 t.parity = par;
-                t.nt = (int)std::min<long long>(TT, half - f);
+                t.nt = std::min(TT, cnt - f);
                 t.ent_start = t.ent_count = 0;
                 t.nbits = (int)lp.farv.size();
                 t.gid_base = lp.gid_base;
+                t.keys = P<int>(h->tkeys) + h->h_seg[2 * l + par] + f;
                 tiles.push_back(t);
             }
+        }
         h->max_bits = std::max(h->max_bits, (int)lp.farv.size());
     }
     h->ntiles = (int)tiles.size();
@@ -669,11 +698,11 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
         ni.assign(h->ntiles, 0);
         for (int t = 0; t < h->ntiles; ++t) {
             i0[t] = (int)items.size();
-            for (int e = ts[t]; e < ts[t + 1]; e += M2L_EC) {
+            for (int e = ts[t]; e < ts[t + 1]; e += h->item_len) {
                 M2LItem it;
                 it.tile = t;
                 it.e0 = e;
-                it.e1 = std::min(e + M2L_EC, ts[t + 1]);
+                it.e1 = std::min(e + h->item_len, ts[t + 1]);
                 items.push_back(it);
             }
             ni[t] = (int)items.size() - i0[t];
@@ -842,8 +871,12 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
         CK(cudaStreamWaitEvent(h->s_far, h->ev_fork, 0));
         // near field only; L2P after the join
         if (ev) CK(cudaEventRecord(evs[EV_P2P0], sn));
-        launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_nl, h->near_leaf,
-                         P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), nullptr, P<R4>(h->H), sn);
+        if (sizeof(real) == 4 && p2p_symmetric())
+            launch_p2p_sym(L, P<int>(h->leaf_start), h->near_nl, h->near_leaf, P<Geom>(h->geomd),
+                           P<float4>(h->A), P<float2>(h->B), P<float4>(h->H), h->N, sn);
+        else
+            launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_nl, h->near_leaf,
+                             P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), nullptr, P<R4>(h->H), sn);
         if (ev) CK(cudaEventRecord(evs[EV_P2P1], sn));
     }
     // far chain
@@ -879,11 +912,19 @@ static ccfmm_status eval_t(ccfmm_t h, double *Hdev)
                          P<R4>(h->H), s);
     } else {
         if (ev) CK(cudaEventRecord(evs[EV_P2P0], s));
-        launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_nl, h->near_leaf,
-                         P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), P<double>(h->V),
-                         P<R4>(h->H), s);
+        const bool sym = sizeof(real) == 4 && p2p_symmetric();
+        if (sym)
+            launch_p2p_sym(L, P<int>(h->leaf_start), h->near_nl, h->near_leaf, P<Geom>(h->geomd),
+                           P<float4>(h->A), P<float2>(h->B), P<float4>(h->H), h->N, s);
+        else
+            launch_p2p<real>(p, KP, L, P<int>(h->leaf_start), h->near_nl, h->near_leaf,
+                             P<Geom>(h->geomd), P<R4>(h->A), P<R2>(h->B), P<double>(h->V),
+                             P<R4>(h->H), s);
         if (ev) CK(cudaEventRecord(evs[EV_P2P1], s));
         if (ev) CK(cudaEventRecord(evs[EV_JOIN], s));
+        if (sym)
+            launch_l2p<real>(p, KP, L, P<int>(h->leaf_start), P<R4>(h->A), P<double>(h->V),
+                             P<R4>(h->H), s);
     }
     if (ev) CK(cudaEventRecord(evs[EV_L2P], s));
     Readback *drb = P<Readback>(h->rb);
@@ -941,7 +982,8 @@ int64_t ccfmm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 // member: the handle belongs to an ensemble (set before its first build)
 static ccfmm_status create_handle(const double *positions, const double *moments, int64_t N,
                                   int p, double theta, double leaf_size, const double *box,
-                                  ccfmm_prec prec, void *stream, bool member, ccfmm_t *out)
+                                  ccfmm_prec prec, void *stream, bool member, ccfmm_t *out,
+                                  int item_len = M2L_EC)
 {
     g_err.clear();
     if (!out) return fail(CCFMM_ERR_ARG, "out is NULL");
@@ -978,6 +1020,7 @@ static ccfmm_status create_handle(const double *positions, const double *moments
     h->K = nterms(p) - 1;
     h->KP = padded_k(p);
     h->maxdeg = 2 * p;
+    h->item_len = item_len > 0 ? item_len : M2L_EC;
     if (box) {
         h->has_box = true;
         memcpy(h->box_user, box, sizeof(h->box_user));
@@ -1189,7 +1232,8 @@ void fmm_destroy(ccfmm_t h)
     DevBuf *bufs[] = {&h->pos, &h->mom, &h->keys, &h->keys2, &h->keys3, &h->idx, &h->idx2,
                       &h->idx3, &h->sorttemp, &h->scantemp, &h->geomd, &h->box6, &h->userbox,
                       &h->partial, &h->rb, &h->leaf_start, &h->A, &h->B, &h->H, &h->cube,
-                      &h->nl, &h->neA, &h->neB, &h->cflag, &h->crank,
+                      &h->nl, &h->neA, &h->neB, &h->cflag, &h->crank, &h->oflag, &h->orank,
+                      &h->tkeys, &h->tseg,
                       &h->far, &h->far_off, &h->far_num, &h->tiles, &h->tcount, &h->tstart,
                       &h->ent_u, &h->ent_src, &h->offs, &h->fst, &h->fq, &h->fval, &h->fdense,
                       &h->D, &h->itab, &h->Q, &h->V, &h->Hout, &h->epart, &h->items,
@@ -1310,8 +1354,15 @@ ccfmm_status fmm_get_m2l_data(ccfmm_t h, int64_t *sizes, double *D_out, int32_t 
     if (ent_src_out && h->ent_total > 0)
         CK(cudaMemcpy(ent_src_out, h->ent_src.p, sizeof(int) * TT * h->ent_total,
                       cudaMemcpyDeviceToHost));
-    if (tiles_out && h->ntiles > 0)
-        CK(cudaMemcpy(tiles_out, h->tiles.p, sizeof(Tile) * h->ntiles, cudaMemcpyDeviceToHost));
+    if (tiles_out && h->ntiles > 0) {
+        std::vector<Tile> t(h->ntiles);
+        CK(cudaMemcpy(t.data(), h->tiles.p, sizeof(Tile) * h->ntiles, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < h->ntiles; ++i) {
+            const int v[8] = {t[i].level, t[i].first, t[i].parity, t[i].nt,
+                              t[i].ent_start, t[i].ent_count, t[i].nbits, t[i].gid_base};
+            memcpy(tiles_out + 8 * (size_t)i, v, sizeof(v));
+        }
+    }
     return CCFMM_OK;
 }
 
@@ -1455,7 +1506,193 @@ struct ccfmm_batch_s {
     RotateParams *hprm = nullptr;  // pinned
     cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [0] evaluate, [1] rotate + evaluate
     long long graph_kernels[2] = {0, 0};
+    // batched stages: one launch per stage for every member (FP32 path with
+    // the tensor-core M2L); the per-member graph otherwise
+    struct Stage {
+        DevBuf args, bstart;
+        int nblocks = 0;
+    };
+    bool batched = false, planned = false;
+    Stage st_perm, st_p2m, st_qs, st_m2l, st_red, st_p2p, st_l2p, st_fin;
+    cudaEvent_t ev_near0 = nullptr, ev_near1 = nullptr;  // near field on a second branch
+    DevBuf work;  // near-field work list, heaviest leaves first
+    int nwork = 0;
+    std::vector<Stage> st_m2m, st_l2l;
+    DevBuf eflag;  // raised by the batched tensor-core M2L's bounded waits
+    int *heflag = nullptr;
+    bool tuned = false;
+    std::vector<struct TuneClass> tune;
+    std::vector<int> tune_of;
 };
+
+// batched stages are used when every member runs the FP32 path with the
+// tensor-core M2L (CCFMM_BATCH_MODE=graph keeps the per-member graph)
+static bool batch_can_batch(ccfmm_batch_t b)
+{
+    const char *e = getenv("CCFMM_BATCH_MODE");
+    if (e && !strcmp(e, "graph")) return false;
+    for (ccfmm_t hs : b->h)
+        if (hs->prec != CCFMM_MIXED || !m2l_use_tc(hs)) return false;
+    return true;
+}
+
+template <typename A>
+static ccfmm_status stage_upload(ccfmm_batch_s::Stage &st, const std::vector<A> &args,
+                                 const std::vector<int> &blocks)
+{
+    std::vector<int> bs(blocks.size() + 1, 0);
+    for (size_t m = 0; m < blocks.size(); ++m) bs[m + 1] = bs[m] + blocks[m];
+    st.nblocks = bs.back();
+    TRY(ensure(st.args, sizeof(A) * std::max<size_t>(args.size(), 1)));
+    TRY(ensure(st.bstart, sizeof(int) * bs.size()));
+    CK(cudaMemcpy(st.args.p, args.data(), sizeof(A) * args.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(st.bstart.p, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice));
+    return CCFMM_OK;
+}
+
+// Arguments of every batched stage, from the members' buffers (built once;
+// the members' trees and operators are fixed for the batch's life).
+static ccfmm_status batch_plan(ccfmm_batch_t b)
+{
+    const int nm = b->ns;
+    TRY(ensure(b->eflag, sizeof(int)));
+    CK(cudaMemset(b->eflag.p, 0, sizeof(int)));
+    std::vector<PermuteArgs> a_perm(nm);
+    std::vector<P2MArgs> a_p2m(nm);
+    std::vector<QSplitArgs> a_qs(nm);
+    std::vector<M2LTCArgs> a_m2l(nm);
+    std::vector<ReduceArgs> a_red(nm);
+    std::vector<P2PArgs> a_p2p(nm), a_l2p(nm);
+    std::vector<int> b_l2p(nm);
+    std::vector<FinishArgs> a_fin(nm);
+    std::vector<int> b_perm(nm), b_p2m(nm), b_qs(nm), b_m2l(nm), b_red(nm), b_p2p(nm), b_fin(nm);
+    int maxr_m2m = 0, maxr_l2l = 0;
+    for (int m = 0; m < nm; ++m) {
+        int l0[LCAP + 1], D[LCAP + 1];
+        maxr_m2m = std::max(maxr_m2m, m2m_rounds(b->h[m]->L, l0, D));
+        maxr_l2l = std::max(maxr_l2l, l2l_rounds(b->h[m]->L, l0, D));
+    }
+    std::vector<std::vector<M2MArgs>> a_m2m(maxr_m2m, std::vector<M2MArgs>(nm));
+    std::vector<std::vector<L2LArgs>> a_l2l(maxr_l2l, std::vector<L2LArgs>(nm));
+    std::vector<std::vector<int>> b_m2m(maxr_m2m, std::vector<int>(nm, 0)),
+        b_l2l(maxr_l2l, std::vector<int>(nm, 0));
+    for (int m = 0; m < nm; ++m) {
+        ccfmm_t h = b->h[m];
+        const int L = h->L, p = h->p, KP = h->KP;
+        const long long ncellp = 1ll << (L + 1);
+        const Geom *g = P<Geom>(h->geomd);
+        a_perm[m] = PermuteArgs{P<double>(b->mom) + 3 * b->off[m], P<int>(h->idx), h->N,
+                                P<float4>(h->A), P<float2>(h->B), P<double>(h->V), ncellp * KP};
+        b_perm[m] = permute_blocks(h->N);
+        a_p2m[m] = P2MArgs{p, KP, L, P<int>(h->leaf_start), P<float4>(h->A), P<float2>(h->B),
+                           P<float>(h->Q)};
+        b_p2m[m] = p2m_blocks(L);
+        int l0[LCAP + 1], D[LCAP + 1];
+        const int nr = m2m_rounds(L, l0, D);
+        for (int r = 0; r < nr; ++r) {
+            a_m2m[r][m] = M2MArgs{p, KP, l0[r], D[r], g, P<float>(h->Q)};
+            b_m2m[r][m] = (int)(1ll << l0[r]);
+        }
+        a_qs[m] = QSplitArgs{p, ncellp, P<float>(h->Q), P<float>(h->gkt), P<float>(h->Qs)};
+        b_qs[m] = h->nitems > 0 ? q_split_blocks(KP, ncellp) : 0;
+        a_m2l[m] = M2LTCArgs{P<M2LItem>(h->items), P<int>(h->ent_u), P<int>(h->ent_src),
+                             P<float>(h->Qs), ncellp * m2l_tc_kt(KP),
+                             reinterpret_cast<const unsigned char *>(h->Bop.p), P<float>(h->Ps),
+                             P<int>(b->eflag)};
+        b_m2l[m] = h->nitems;
+        a_red[m] = ReduceArgs{p, KP, P<Tile>(h->tiles), P<int>(h->titem0), P<int>(h->tnitems),
+                              P<float>(h->Ps), g, P<double>(h->V)};
+        b_red[m] = h->nitems > 0 ? h->ntiles : 0;
+        const int nl2 = l2l_rounds(L, l0, D);
+        for (int r = 0; r < nl2; ++r) {
+            a_l2l[r][m] = L2LArgs{p, KP, l0[r], D[r], L, g, P<int>(h->leaf_start), P<double>(h->V)};
+            b_l2l[r][m] = (int)(1ll << l0[r]);
+        }
+        // near field alone (it runs beside the far chain), then the smooth field
+        a_p2p[m] = P2PArgs{p, KP, L, P<int>(h->leaf_start), h->near_nl, h->near_leaf, g,
+                           P<float4>(h->A), P<float2>(h->B), nullptr, P<float4>(h->H)};
+        b_p2p[m] = (int)(1ll << L);
+        a_l2p[m] = a_p2p[m];
+        a_l2p[m].V = P<double>(h->V);
+        b_l2p[m] = l2p_blocks(L);
+        a_fin[m] = FinishArgs{P<float4>(h->H), P<int>(h->idx), h->mom_energy, h->N,
+                              P<double>(b->H) + 3 * b->off[m], P<double>(h->epart), h->E_dst};
+        b_fin[m] = finish_blocks(h->N);
+    }
+    TRY(stage_upload(b->st_perm, a_perm, b_perm));
+    TRY(stage_upload(b->st_p2m, a_p2m, b_p2m));
+    b->st_m2m.assign(maxr_m2m, ccfmm_batch_s::Stage());
+    for (int r = 0; r < maxr_m2m; ++r) TRY(stage_upload(b->st_m2m[r], a_m2m[r], b_m2m[r]));
+    TRY(stage_upload(b->st_qs, a_qs, b_qs));
+    TRY(stage_upload(b->st_m2l, a_m2l, b_m2l));
+    TRY(stage_upload(b->st_red, a_red, b_red));
+    b->st_l2l.assign(maxr_l2l, ccfmm_batch_s::Stage());
+    for (int r = 0; r < maxr_l2l; ++r) TRY(stage_upload(b->st_l2l[r], a_l2l[r], b_l2l[r]));
+    TRY(stage_upload(b->st_p2p, a_p2p, b_p2p));
+    TRY(stage_upload(b->st_l2p, a_l2p, b_l2p));
+    {
+        // near-field work list: every (member, leaf), by decreasing cost
+        const int nleaves = b->st_p2p.nblocks;
+        DevBuf cost;
+        TRY(ensure(cost, sizeof(long long) * std::max(nleaves, 1)));
+        launch_leaf_cost((const P2PArgs *)b->st_p2p.args.p, P<int>(b->st_p2p.bstart), nm, nleaves,
+                         P<long long>(cost), b->stream);
+        std::vector<long long> c(nleaves);
+        cudaError_t e = cudaMemcpyAsync(c.data(), cost.p, sizeof(long long) * nleaves,
+                                        cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        cudaFree(cost.p);
+        CK(e);
+        std::vector<int> bs(nm + 1, 0);
+        for (int m = 0; m < nm; ++m) bs[m + 1] = bs[m] + b_p2p[m];
+        std::vector<int2> w;
+        w.reserve(nleaves);
+        for (int m = 0; m < nm; ++m)
+            for (int k = 0; k < b_p2p[m]; ++k)
+                if (c[bs[m] + k] > 0) w.push_back(make_int2(m, k));
+        std::stable_sort(w.begin(), w.end(), [&](const int2 &x, const int2 &y) {
+            return c[bs[x.x] + x.y] > c[bs[y.x] + y.y];
+        });
+        b->nwork = (int)w.size();
+        TRY(ensure(b->work, sizeof(int2) * std::max<size_t>(w.size(), 1)));
+        if (!w.empty())
+            CK(cudaMemcpy(b->work.p, w.data(), sizeof(int2) * w.size(), cudaMemcpyHostToDevice));
+    }
+    if (!b->ev_near0) CK(cudaEventCreateWithFlags(&b->ev_near0, cudaEventDisableTiming));
+    if (!b->ev_near1) CK(cudaEventCreateWithFlags(&b->ev_near1, cudaEventDisableTiming));
+    TRY(stage_upload(b->st_fin, a_fin, b_fin));
+    b->planned = true;
+    return CCFMM_OK;
+}
+
+// the batched stages of one step, in order, on the batch's stream
+static void batch_enqueue(ccfmm_batch_t b, cudaStream_t s)
+{
+    const int nm = b->ns;
+    const int KP = b->h[0]->KP, p = b->h[0]->p;
+    const char *sv = getenv("CCFMM_TC_STALL");
+    const int stall = (sv && atoi(sv)) ? 1 : 0;
+    const long long spin = stall ? (1ll << 12) : (1ll << 22);
+    auto A = [](ccfmm_batch_s::Stage &st) { return st.args.p; };
+    auto B = [](ccfmm_batch_s::Stage &st) { return P<int>(st.bstart); };
+    launch_permute_batch((const PermuteArgs *)A(b->st_perm), B(b->st_perm), nm, b->st_perm.nblocks, s);
+    // the near field of every member on a second branch, beside the far chain
+    cudaStream_t sn = b->br[0];
+    cudaEventRecord(b->ev_near0, s);
+    cudaStreamWaitEvent(sn, b->ev_near0, 0);
+    launch_p2p_ordered((const P2PArgs *)A(b->st_p2p), P<int2>(b->work), b->nwork, KP, sn);
+    cudaEventRecord(b->ev_near1, sn);
+    launch_p2m_batch((const P2MArgs *)A(b->st_p2m), B(b->st_p2m), nm, b->st_p2m.nblocks, s);
+    for (auto &st : b->st_m2m) launch_m2m_batch((const M2MArgs *)A(st), B(st), nm, st.nblocks, s);
+    launch_q_split_batch(KP, (const QSplitArgs *)A(b->st_qs), B(b->st_qs), nm, b->st_qs.nblocks, s);
+    launch_m2l_tc_batch(KP, (const M2LTCArgs *)A(b->st_m2l), B(b->st_m2l), nm, b->st_m2l.nblocks,
+                        spin, stall, s);
+    launch_reduce_batch(p, (const ReduceArgs *)A(b->st_red), B(b->st_red), nm, b->st_red.nblocks, s);
+    for (auto &st : b->st_l2l) launch_l2l_batch((const L2LArgs *)A(st), B(st), nm, st.nblocks, s);
+    cudaStreamWaitEvent(s, b->ev_near1, 0);
+    launch_l2p_batch(p, (const P2PArgs *)A(b->st_l2p), B(b->st_l2p), nm, b->st_l2p.nblocks, s);
+    launch_finish_batch((const FinishArgs *)A(b->st_fin), B(b->st_fin), nm, b->st_fin.nblocks, s);
+}
 
 static ccfmm_status batch_capture(ccfmm_batch_t b, int rotate)
 {
@@ -1470,10 +1707,15 @@ static ccfmm_status batch_capture(ccfmm_batch_t b, int rotate)
         }
     if (prepared)
         for (int r = 0; r < b->nbr; ++r) CK(cudaStreamSynchronize(b->br[r]));
+    if (b->batched && !b->planned) TRY(batch_plan(b));
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     ccfmm_status st = CCFMM_OK;
     do {
         if (rotate) launch_rotate(P<double>(b->mom), b->total, P<RotateParams>(b->prm), s);
+        if (b->batched) {
+            batch_enqueue(b, s);
+            break;
+        }
         if (cudaEventRecord(b->evf, s) != cudaSuccess) { st = fail(CCFMM_ERR_CUDA, "capture fork"); break; }
         for (int r = 0; r < b->nbr; ++r)
             if (cudaStreamWaitEvent(b->br[r], b->evf, 0) != cudaSuccess) st = fail(CCFMM_ERR_CUDA, "capture wait");
@@ -1534,6 +1776,16 @@ static ccfmm_status batch_direct(ccfmm_batch_t b, int rotate)
 {
     cudaStream_t s = b->stream;
     if (rotate) launch_rotate(P<double>(b->mom), b->total, P<RotateParams>(b->prm), s);
+    if (b->batched) {
+        if (!b->planned) {
+            for (ccfmm_t hs : b->h) TRY(tc_prepare(hs));
+            for (int r = 0; r < b->nbr; ++r) CK(cudaStreamSynchronize(b->br[r]));
+            TRY(batch_plan(b));
+        }
+        batch_enqueue(b, s);
+        KCHECK();
+        return CCFMM_OK;
+    }
     CK(cudaEventRecord(b->evf, s));
     for (int r = 0; r < b->nbr; ++r) CK(cudaStreamWaitEvent(b->br[r], b->evf, 0));
     for (int i = 0; i < b->ns; ++i) {
@@ -1566,6 +1818,8 @@ static ccfmm_status batch_run(ccfmm_batch_t b, int rotate, double *H_out, double
         CK(cudaGraphLaunch(b->exec[rotate], b->stream));
         note_launch((int)b->graph_kernels[rotate]);
     }
+    // the batched stages evaluate every member without its own eval_t
+    for (ccfmm_t hs : b->h) hs->evaluated = true;
     if (H_out) {
         cudaMemcpyKind k = is_device_ptr(H_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         CK(cudaMemcpyAsync(H_out, b->H.p, sizeof(double) * 3 * b->total, k, b->stream));
@@ -1574,10 +1828,27 @@ static ccfmm_status batch_run(ccfmm_batch_t b, int rotate, double *H_out, double
         cudaMemcpyKind k = is_device_ptr(E_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         CK(cudaMemcpyAsync(E_out, b->E.p, sizeof(double) * b->ns, k, b->stream));
     }
-    if ((H_out && !is_device_ptr(H_out)) || (E_out && !is_device_ptr(E_out)))
+    const bool sync = (H_out && !is_device_ptr(H_out)) || (E_out && !is_device_ptr(E_out));
+    if (b->batched && b->eflag.p) {
+        // a bounded wait that gave up in a batched launch is reported by the
+        // next call that synchronises
+        CK(cudaMemcpyAsync(b->heflag, b->eflag.p, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    }
+    if (sync) {
         CK(cudaStreamSynchronize(b->stream));
+        if (b->batched && b->eflag.p && *b->heflag) {
+            CK(cudaMemset(b->eflag.p, 0, sizeof(int)));
+            *b->heflag = 0;
+            return fail(CCFMM_ERR_TIMEOUT, "a bounded wait in the tensor-core M2L gave up");
+        }
+    }
     return CCFMM_OK;
 }
+
+static ccfmm_status batch_create(const double *positions, const double *moments,
+                                 const int64_t *offsets, int nsamples, int p, double theta,
+                                 double leaf_size, ccfmm_prec prec, const ccfmm_batch_opts *opts,
+                                 void *stream, ccfmm_batch_t *out, double leaf_all, int il_all);
 
 extern "C" {
 
@@ -1592,18 +1863,168 @@ void fmm_batch_destroy(ccfmm_batch_t b)
     for (cudaStream_t s : b->br) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->evj) cudaEventDestroy(e);
     if (b->evf) cudaEventDestroy(b->evf);
-    DevBuf *bufs[] = {&b->mom, &b->H, &b->E, &b->prm};
+    DevBuf *bufs[] = {&b->mom, &b->H, &b->E, &b->prm, &b->eflag, &b->work};
     for (DevBuf *d : bufs)
         if (d->p) cudaFree(d->p);
+    ccfmm_batch_s::Stage *sts[] = {&b->st_perm, &b->st_p2m, &b->st_qs, &b->st_m2l, &b->st_red,
+                                   &b->st_p2p, &b->st_l2p, &b->st_fin};
+    if (b->ev_near0) cudaEventDestroy(b->ev_near0);
+    if (b->ev_near1) cudaEventDestroy(b->ev_near1);
+    for (auto *st : sts) {
+        if (st->args.p) cudaFree(st->args.p);
+        if (st->bstart.p) cudaFree(st->bstart.p);
+    }
+    for (auto *v : {&b->st_m2m, &b->st_l2l})
+        for (auto &st : *v) {
+            if (st.args.p) cudaFree(st.args.p);
+            if (st.bstart.p) cudaFree(st.bstart.p);
+        }
+    if (b->heflag) cudaFreeHost(b->heflag);
     if (b->hprm) cudaFreeHost(b->hprm);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     cudaGetLastError();
     delete b;
 }
 
+// ------------------------------------------------------------ autotuner
+// Leaf occupancy and M2L item length per sample-size class of an ensemble,
+// chosen by timed trial steps.  Classes are the octaves of N
+// (floor(log2 N)).  Each class is tuned on a sub-ensemble of up to TUNE_SUB
+// of its samples spread over its sizes, run the way the ensemble runs (the
+// batched stages), so that what is timed is throughput, not the latency of
+// one small system: for every candidate (leaf = s x {1/2, 1/sqrt2, 1,
+// sqrt2, 2}, s = the requested occupancy or Eq. so; item length 32 or 64
+// entries on the tensor-core path) the sub-ensemble is built, evaluated
+// once untimed and `trials` times timed with CUDA events; the fastest mean
+// wins.
+struct TuneClass {
+    int octave;
+    long long nmin;
+    double leaf;
+    int item_len;
+};
+constexpr int TUNE_SUB = 16;
+
+static ccfmm_status batch_autotune(const double *positions, const double *moments,
+                                   const std::vector<long long> &off, int p, double theta,
+                                   double leaf_size, ccfmm_prec prec, int trials,
+                                   cudaStream_t s, std::vector<TuneClass> &classes,
+                                   std::vector<int> &class_of)
+{
+    const int ns = (int)off.size() - 1;
+    const double base = leaf_size > 0.0 ? leaf_size : ccfmm_leaf_size_rule(p);
+    const double fac[5] = {0.5, 0.70710678118654752, 1.0, 1.41421356237309505, 2.0};
+    std::map<int, std::vector<int>> by_oct;
+    for (int i = 0; i < ns; ++i) {
+        const long long n = off[i + 1] - off[i];
+        int o = 0;
+        while ((2ll << o) <= n) ++o;
+        by_oct[o].push_back(i);
+    }
+    class_of.assign(ns, 0);
+    classes.clear();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double *dpos = nullptr, *dmom = nullptr;
+    ccfmm_status st = CCFMM_OK;
+    for (auto &kv : by_oct) {
+        std::vector<int> mem = kv.second;
+        std::sort(mem.begin(), mem.end(),
+                  [&](int x, int y) { return off[x + 1] - off[x] < off[y + 1] - off[y]; });
+        // the sub-ensemble: samples spread evenly over the class's sizes
+        std::vector<int> sub;
+        const int k = std::min((int)mem.size(), TUNE_SUB);
+        for (int j = 0; j < k; ++j) sub.push_back(mem[(size_t)j * mem.size() / k]);
+        std::vector<int64_t> so(1, 0);
+        for (int i : sub) so.push_back(so.back() + (off[i + 1] - off[i]));
+        if (cudaMalloc(&dpos, sizeof(double) * 3 * so.back()) != cudaSuccess ||
+            cudaMalloc(&dmom, sizeof(double) * 3 * so.back()) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(CCFMM_ERR_ALLOC, "autotuner: device allocation failed");
+            break;
+        }
+        for (size_t j = 0; j < sub.size() && st == CCFMM_OK; ++j) {
+            const size_t nb = sizeof(double) * 3 * (size_t)(so[j + 1] - so[j]);
+            if (cudaMemcpyAsync(dpos + 3 * so[j], positions + 3 * off[sub[j]], nb, cudaMemcpyDefault, s) != cudaSuccess ||
+                cudaMemcpyAsync(dmom + 3 * so[j], moments + 3 * off[sub[j]], nb, cudaMemcpyDefault, s) != cudaSuccess)
+                st = fail(CCFMM_ERR_CUDA, "autotuner: copy failed");
+        }
+        if (st == CCFMM_OK && cudaStreamSynchronize(s) != cudaSuccess)
+            st = fail(CCFMM_ERR_CUDA, "autotuner: copy failed");
+        TuneClass best{kv.first, off[mem[0] + 1] - off[mem[0]], base, M2L_EC};
+        double best_ms = INFINITY;
+        for (int fi = 0; fi < 5 && st == CCFMM_OK; ++fi)
+            for (int il : {64, 32}) {
+                const double lf = std::max(1.0, base * fac[fi]);
+                ccfmm_batch_t sb = nullptr;
+                st = batch_create(dpos, dmom, so.data(), (int)sub.size(), p, theta, lf, prec,
+                                  nullptr, s, &sb, lf, il);
+                if (st != CCFMM_OK) break;
+                if (!sb->batched && il != 64) {  // the item length matters to the batched M2L only
+                    fmm_batch_destroy(sb);
+                    continue;
+                }
+                st = batch_run(sb, 0, nullptr, nullptr);
+                float t_ms = 0.f;
+                if (st == CCFMM_OK) {
+                    if (cudaStreamSynchronize(s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess)
+                        st = fail(CCFMM_ERR_CUDA, "autotuner: timing failed");
+                    for (int t = 0; t < trials && st == CCFMM_OK; ++t) st = batch_run(sb, 0, nullptr, nullptr);
+                    if (st == CCFMM_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                           cudaEventSynchronize(e1) != cudaSuccess ||
+                                           cudaEventElapsedTime(&t_ms, e0, e1) != cudaSuccess))
+                        st = fail(CCFMM_ERR_CUDA, "autotuner: timing failed");
+                }
+                fmm_batch_destroy(sb);
+                if (st != CCFMM_OK) break;
+                const double ms = t_ms / std::max(trials, 1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best.leaf = lf;
+                    best.item_len = il;
+                }
+            }
+        cudaFree(dpos);
+        cudaFree(dmom);
+        dpos = dmom = nullptr;
+        if (st != CCFMM_OK) break;
+        for (int i : mem) class_of[i] = (int)classes.size();
+        classes.push_back(best);
+    }
+    if (dpos) cudaFree(dpos);
+    if (dmom) cudaFree(dmom);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    return st;
+}
+
 ccfmm_status fmm_batch_create(const double *positions, const double *moments,
                               const int64_t *offsets, int nsamples, int p, double theta,
                               double leaf_size, ccfmm_prec prec, void *stream, ccfmm_batch_t *out)
+{
+    return fmm_batch_create_ex(positions, moments, offsets, nsamples, p, theta, leaf_size, prec,
+                               nullptr, stream, out);
+}
+
+ccfmm_status fmm_batch_create_ex(const double *positions, const double *moments,
+                                 const int64_t *offsets, int nsamples, int p, double theta,
+                                 double leaf_size, ccfmm_prec prec, const ccfmm_batch_opts *opts,
+                                 void *stream, ccfmm_batch_t *out)
+{
+    return batch_create(positions, moments, offsets, nsamples, p, theta, leaf_size, prec, opts,
+                        stream, out, 0.0, 0);
+}
+
+}  // extern "C"
+
+// leaf_all > 0 / il_all > 0: every sample's leaf occupancy and M2L item
+// length (the autotuner's trial sub-ensembles)
+static ccfmm_status batch_create(const double *positions, const double *moments,
+                                 const int64_t *offsets, int nsamples, int p, double theta,
+                                 double leaf_size, ccfmm_prec prec, const ccfmm_batch_opts *opts,
+                                 void *stream, ccfmm_batch_t *out, double leaf_all, int il_all)
 {
     g_err.clear();
     if (!out || !positions || !moments || !offsets) return fail(CCFMM_ERR_ARG, "NULL argument");
@@ -1668,11 +2089,20 @@ ccfmm_status fmm_batch_create(const double *positions, const double *moments,
         BCK(cudaMemcpyAsync(b->mom.p, moments, sizeof(double) * 3 * b->total, k, b->stream));
         BCK(cudaStreamSynchronize(b->stream));
     }
+    if (opts && opts->autotune) {
+        // the positions may be host memory: the trial handles copy them in
+        BTRY(batch_autotune(positions, P<double>(b->mom), b->off, p, theta, leaf_size, prec,
+                            opts->trials > 0 ? opts->trials : 3, b->br[0], b->tune, b->tune_of));
+        b->tuned = true;
+    }
     for (int i = 0; i < nsamples; ++i) {
         ccfmm_t hs = nullptr;
         long long o = b->off[i], n = b->off[i + 1] - o;
-        BTRY(create_handle(positions + 3 * o, P<double>(b->mom) + 3 * o, n, p, theta, leaf_size,
-                           nullptr, prec, b->br[i % b->nbr], true, &hs));
+        const double lf = b->tuned ? b->tune[b->tune_of[i]].leaf
+                                   : (leaf_all > 0.0 ? leaf_all : leaf_size);
+        const int il = b->tuned ? b->tune[b->tune_of[i]].item_len : (il_all > 0 ? il_all : M2L_EC);
+        BTRY(create_handle(positions + 3 * o, P<double>(b->mom) + 3 * o, n, p, theta, lf,
+                           nullptr, prec, b->br[i % b->nbr], true, &hs, il));
         hs->mom_energy = P<double>(b->mom) + 3 * o;
         hs->E_dst = P<double>(b->E) + i;
         b->h.push_back(hs);
@@ -1680,11 +2110,16 @@ ccfmm_status fmm_batch_create(const double *positions, const double *moments,
     // the handles' builds end with kernels still queued on the branch
     // streams; a captured graph would not depend on them
     for (cudaStream_t s : b->br) BCK(cudaStreamSynchronize(s));
+    b->batched = batch_can_batch(b);
+    BCK(cudaMallocHost((void **)&b->heflag, sizeof(int)));
+    *b->heflag = 0;
 #undef BTRY
 #undef BCK
     *out = b;
     return CCFMM_OK;
 }
+
+extern "C" {
 
 ccfmm_status fmm_batch_step(ccfmm_batch_t b, uint64_t seed, uint64_t step, double max_angle,
                             double *H_out, double *E_out)
@@ -1739,6 +2174,20 @@ ccfmm_status fmm_batch_sample(ccfmm_batch_t b, int i, ccfmm_t *out)
     if (!b || !out || i < 0 || i >= b->ns) return fail(CCFMM_ERR_ARG, "bad argument");
     CK(cudaStreamSynchronize(b->stream));
     *out = b->h[i];
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_batch_tuning(ccfmm_batch_t b, int32_t *nclasses, int64_t *class_nmin,
+                              double *class_leaf, int32_t *class_item_len, int32_t capacity)
+{
+    g_err.clear();
+    if (!b || !nclasses) return fail(CCFMM_ERR_ARG, "NULL argument");
+    *nclasses = b->tuned ? (int32_t)b->tune.size() : 0;
+    for (int i = 0; i < *nclasses && i < capacity; ++i) {
+        if (class_nmin) class_nmin[i] = b->tune[i].nmin;
+        if (class_leaf) class_leaf[i] = b->tune[i].leaf;
+        if (class_item_len) class_item_len[i] = b->tune[i].item_len;
+    }
     return CCFMM_OK;
 }
 

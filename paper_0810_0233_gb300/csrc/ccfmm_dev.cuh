@@ -114,7 +114,23 @@ struct Tile {      // M2L work unit
     int ent_count;
     int nbits;     // far offsets of this level (bitmap width)
     int gid_base;  // first global offset id of this level
+    const int *keys;  // device: target i is the level's cell keys[i] (the
+                      // non-empty cells of one parity, in key order)
 };
+
+// Batched launches (ensemble step): one launch covers a stage of every
+// member; bstart[m] .. bstart[m+1] are member m's blocks.  Returns m and
+// sets local to the block's index within its member.
+__device__ __forceinline__ int batch_member(const int *bstart, int nm, int blk, int &local)
+{
+    int lo = 0, hi = nm;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(bstart + mid) <= blk) lo = mid; else hi = mid;
+    }
+    local = blk - __ldg(bstart + lo);
+    return lo;
+}
 
 // Count of kernel launches issued by the library in this process.
 void note_launch(int n = 1);
@@ -163,7 +179,12 @@ void launch_permute_moments(const double *mom, const int *perm, long long n,
                             cudaStream_t s);
 // non-empty cells per level (d_ne); with flags != nullptr also flags[hid] =
 // 1 for every non-empty cell, 0 otherwise (flags[0] = 0)
-void launch_level_counts(const int *leaf_start, int L, int *d_ne, int *flags, cudaStream_t s);
+void launch_level_counts(const int *leaf_start, int L, int *d_ne, int *flags, int *oflags,
+                         int *d_ne_odd, cudaStream_t s);
+// the M2L tiles' target cells: for every level l >= 2 the non-empty cells of
+// each parity in key order, segment (l, parity) at seg[2 l + parity]
+void launch_tile_keys(int L, const int *flags, const int *rank, const int *rank_odd,
+                      const int *seg, int *tkeys, cudaStream_t s);
 void launch_check_finite(const double *x, long long n, int *d_flags, cudaStream_t s);
 
 // ------------------------------------------------------------------ lists.cu
@@ -243,6 +264,12 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl
                 const NearEnt *near, const Geom *d_geom, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
                 cudaStream_t s);
+// symmetric near field (CCFMM_P2P=sym): zeroes H, adds the near field with
+// global reductions; the smooth field is added by launch_l2p
+bool p2p_symmetric();
+void launch_p2p_sym(int L, const int *leaf_start, const int2 *near_nl, const NearEnt *near,
+                    const Geom *d_geom, const float4 *A, const float2 *B, float4 *H,
+                    long long N, cudaStream_t s);
 // V == nullptr: near field only; launch_l2p then adds the smooth field
 template <typename real>
 void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
@@ -254,5 +281,109 @@ void launch_direct(const double *pos, const double *mom, long long n, const long
                    long long nt, double *H_out, cudaStream_t s);
 void launch_p2p_pair_count(int L, const int *leaf_start, const int2 *near_nl,
                            const NearEnt *near, unsigned long long *d_count, cudaStream_t s);
+
+// ------------------------------------------------ batched ensemble stages
+// One launch per stage covers every member of an ensemble (FP32 path,
+// tensor-core M2L): the arguments of each member's launch in device
+// memory, and bstart (nm + 1 block offsets) mapping blocks to members.
+struct PermuteArgs {
+    const double *mom;
+    const int *perm;
+    long long n;
+    float4 *A;
+    float2 *B;
+    double *V;        // zeroed by the same launch
+    long long nV;     // doubles of V
+};
+struct P2MArgs {
+    int p, KP, L;
+    const int *leaf_start;
+    const float4 *A;
+    const float2 *B;
+    float *Q;
+};
+struct M2MArgs {   // one round: levels l0 + D - 1 .. l0 from l0 + D
+    int p, KP, l0, D;
+    const Geom *g;
+    float *Q;
+};
+struct QSplitArgs {
+    int p;
+    long long ncell;
+    const float *Q, *gk;
+    float *Qs;
+};
+struct M2LTCArgs {
+    const M2LItem *items;
+    const int *ent_u, *ent_src;
+    const float *Qs;
+    long long qplane;
+    const unsigned char *Bop;
+    float *Ps;
+    int *flags;
+};
+struct ReduceArgs {
+    int p, KP;
+    const Tile *tiles;
+    const int *tile_item0, *tile_nitems;
+    const float *Ps;
+    const Geom *g;
+    double *V;
+};
+struct L2LArgs {   // one round: levels l0 + 1 .. l0 + D from l0
+    int p, KP, l0, D, L;
+    const Geom *g;
+    const int *leaf_start;
+    double *V;
+};
+struct P2PArgs {   // near field with the fused smooth field
+    int p, KP, L;
+    const int *leaf_start;
+    const int2 *near_nl;
+    const NearEnt *near;
+    const Geom *g;
+    const float4 *A;
+    const float2 *B;
+    const double *V;
+    float4 *H;
+};
+struct FinishArgs {
+    const float4 *H;
+    const int *perm;
+    const double *mom;
+    long long n;
+    double *Hout, *partial, *E;
+};
+int permute_blocks(long long n);
+int p2m_blocks(int L);
+int q_split_blocks(int KP, long long ncell);
+int finish_blocks(long long n);
+void launch_permute_batch(const PermuteArgs *a, const int *bstart, int nm, int nblocks,
+                          cudaStream_t s);
+void launch_p2m_batch(const P2MArgs *a, const int *bstart, int nm, int nblocks, cudaStream_t s);
+void launch_m2m_batch(const M2MArgs *a, const int *bstart, int nm, int nblocks, cudaStream_t s);
+void launch_l2l_batch(const L2LArgs *a, const int *bstart, int nm, int nblocks, cudaStream_t s);
+void launch_q_split_batch(int KP, const QSplitArgs *a, const int *bstart, int nm, int nblocks,
+                          cudaStream_t s);
+void launch_m2l_tc_batch(int KP, const M2LTCArgs *a, const int *bstart, int nm, int nblocks,
+                         long long spin, int stall, cudaStream_t s);
+void launch_reduce_batch(int p, const ReduceArgs *a, const int *bstart, int nm, int nblocks,
+                         cudaStream_t s);
+void launch_p2p_batch(const P2PArgs *a, const int *bstart, int nm, int nblocks, int KP,
+                      cudaStream_t s);
+// near field over a (member, leaf) work list, block b = item b, and the
+// cost of every (member, leaf) to order that list
+void launch_p2p_ordered(const P2PArgs *a, const int2 *work, int nwork, int KP, cudaStream_t s);
+void launch_leaf_cost(const P2PArgs *a, const int *bstart, int nm, int nleaves, long long *cost,
+                      cudaStream_t s);
+void launch_finish_batch(const FinishArgs *a, const int *bstart, int nm, int nblocks,
+                         cudaStream_t s);
+// smooth field added to the near field (P2PArgs with V set), every member
+int l2p_blocks(int L);
+void launch_l2p_batch(int p, const P2PArgs *a, const int *bstart, int nm, int nblocks,
+                      cudaStream_t s);
+// the M2M and L2L rounds of a tree of depth L: (l0, D) per round
+int m2m_rounds(int L, int *l0, int *D);
+int l2l_rounds(int L, int *l0, int *D);
 
 }  // namespace ccfmm

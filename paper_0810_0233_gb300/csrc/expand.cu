@@ -215,9 +215,9 @@ constexpr int P2M_W = 4;
 constexpr int P2M_R = (nterms(PMAX) - 1 + 31) / 32;  // coefficient rounds per lane
 
 template <typename real>
-__global__ void __launch_bounds__(32 * P2M_W) k_p2m(int p, int KP, int L, const int *leaf_start,
-                                                    const typename vec4<real>::t *A,
-                                                    const typename vec2<real>::t *B, real *Q)
+__device__ __forceinline__ void p2m_body(int p, int KP, int L, const int *leaf_start,
+                                         const typename vec4<real>::t *A,
+                                         const typename vec2<real>::t *B, real *Q, long long blk)
 {
     __shared__ real pw[P2M_W][32][3][PMAX];
     __shared__ real mm[P2M_W][32][3];
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(32 * P2M_W) k_p2m(int p, int KP, int L, const 
     fill_mi(mi, K);
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long key = (long long)blockIdx.x * P2M_W + w;
+    const long long key = blk * P2M_W + w;
     if (key >= (1ll << L)) return;
     const int s0 = leaf_start[key], s1 = leaf_start[key + 1];
     real acc[P2M_R];
@@ -284,6 +284,31 @@ __global__ void __launch_bounds__(32 * P2M_W) k_p2m(int p, int KP, int L, const 
 }
 
 template <typename real>
+__global__ void __launch_bounds__(32 * P2M_W) k_p2m(int p, int KP, int L, const int *leaf_start,
+                                                    const typename vec4<real>::t *A,
+                                                    const typename vec2<real>::t *B, real *Q)
+{
+    p2m_body<real>(p, KP, L, leaf_start, A, B, Q, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(32 * P2M_W) k_p2m_batch(const P2MArgs *a, const int *bstart,
+                                                          int nm)
+{
+    int blk;
+    const P2MArgs &x = a[batch_member(bstart, nm, blockIdx.x, blk)];
+    p2m_body<float>(x.p, x.KP, x.L, x.leaf_start, x.A, x.B, x.Q, blk);
+}
+
+int p2m_blocks(int L) { return (int)(((1ll << L) + P2M_W - 1) / P2M_W); }
+
+void launch_p2m_batch(const P2MArgs *a, const int *bstart, int nm, int nblocks, cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    note_launch();
+    k_p2m_batch<<<(unsigned)nblocks, 32 * P2M_W, 0, s>>>(a, bstart, nm);
+}
+
+template <typename real>
 void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, real *Q, cudaStream_t s)
 {
@@ -312,13 +337,12 @@ constexpr int SUB_KP = ((nterms(PMAX) - 1 + 7) / 8) * 8;
 // Q of the 2^D descendants at level l0 + D (final) -> Q of levels
 // l0 + D - 1 .. l0 of the subtree rooted at key r (blockIdx.x) of level l0
 template <typename real>
-__global__ void __launch_bounds__(SUB_T) k_m2m_sub(int p, int KP, int l0, int D, const Geom *g,
-                                                   real *Q)
+__device__ __forceinline__ void m2m_sub_body(int p, int KP, int l0, int D, const Geom *g, real *Q,
+                                             long long r)
 {
     __shared__ real qs[2][1 << SUB_D][SUB_KP];
     __shared__ real fs[2][PMAX + 1];
     const int K = nterms(p) - 1;
-    const long long r = blockIdx.x;
     int cur = 0;
     {
         const int n = 1 << D;
@@ -366,28 +390,69 @@ __global__ void __launch_bounds__(SUB_T) k_m2m_sub(int p, int KP, int l0, int D,
 }
 
 template <typename real>
+__global__ void __launch_bounds__(SUB_T) k_m2m_sub(int p, int KP, int l0, int D, const Geom *g,
+                                                   real *Q)
+{
+    m2m_sub_body<real>(p, KP, l0, D, g, Q, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(SUB_T) k_m2m_batch(const M2MArgs *a, const int *bstart, int nm)
+{
+    int r;
+    const M2MArgs &x = a[batch_member(bstart, nm, blockIdx.x, r)];
+    m2m_sub_body<float>(x.p, x.KP, x.l0, x.D, x.g, x.Q, r);
+}
+
+int m2m_rounds(int L, int *l0, int *D)
+{
+    int n = 0;
+    for (int cur = L; cur > 0; ++n) {
+        D[n] = cur < SUB_D ? cur : SUB_D;
+        l0[n] = cur - D[n];
+        cur = l0[n];
+    }
+    return n;
+}
+
+int l2l_rounds(int L, int *l0, int *D)
+{
+    int n = 0;
+    for (int cur = 1; cur < L; ++n) {
+        l0[n] = cur;
+        D[n] = L - cur < SUB_D ? L - cur : SUB_D;
+        cur += D[n];
+    }
+    return n;
+}
+
+template <typename real>
 void launch_m2m_all(int p, int KP, int L, const Geom *d_geom, real *Q, cudaStream_t s)
 {
-    for (int cur = L; cur > 0;) {
-        const int D = cur < SUB_D ? cur : SUB_D;
-        const int l0 = cur - D;
+    int l0[LCAP + 1], D[LCAP + 1];
+    const int n = m2m_rounds(L, l0, D);
+    for (int r = 0; r < n; ++r) {
         note_launch();
-        k_m2m_sub<real><<<(unsigned)(1ll << l0), SUB_T, 0, s>>>(p, KP, l0, D, d_geom, Q);
-        cur = l0;
+        k_m2m_sub<real><<<(unsigned)(1ll << l0[r]), SUB_T, 0, s>>>(p, KP, l0[r], D[r], d_geom, Q);
     }
+}
+
+void launch_m2m_batch(const M2MArgs *a, const int *bstart, int nm, int nblocks, cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    note_launch();
+    k_m2m_batch<<<(unsigned)nblocks, SUB_T, 0, s>>>(a, bstart, nm);
 }
 
 // V of the root (key r of level l0, final) and the levels' own M2L
 // contributions -> V of levels l0 + 1 .. l0 + D of the subtree (FP64);
 // empty cells are skipped (their coefficients never reach a field point)
-__global__ void __launch_bounds__(SUB_T) k_l2l_sub(int p, int KP, int l0, int D, int L,
-                                                   const Geom *g, const int *leaf_start, double *V)
+__device__ __forceinline__ void l2l_sub_body(int p, int KP, int l0, int D, int L, const Geom *g,
+                                             const int *leaf_start, double *V, long long r)
 {
     __shared__ double vs[2][1 << SUB_D][SUB_KP];
     __shared__ double fs[2][PMAX + 1];
     __shared__ int full[2][1 << SUB_D];
     const int K = nterms(p) - 1;
-    const long long r = blockIdx.x;
     int cur = 0;
     const long long hr = (1ll << l0) + r;
     for (int c = threadIdx.x; c < KP; c += SUB_T) vs[0][0][c] = V[hr * KP + c];
@@ -438,15 +503,36 @@ __global__ void __launch_bounds__(SUB_T) k_l2l_sub(int p, int KP, int l0, int D,
     }
 }
 
+__global__ void __launch_bounds__(SUB_T) k_l2l_sub(int p, int KP, int l0, int D, int L,
+                                                   const Geom *g, const int *leaf_start, double *V)
+{
+    l2l_sub_body(p, KP, l0, D, L, g, leaf_start, V, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(SUB_T) k_l2l_batch(const L2LArgs *a, const int *bstart, int nm)
+{
+    int r;
+    const L2LArgs &x = a[batch_member(bstart, nm, blockIdx.x, r)];
+    l2l_sub_body(x.p, x.KP, x.l0, x.D, x.L, x.g, x.leaf_start, x.V, r);
+}
+
 void launch_l2l_all(int p, int KP, int L, const Geom *d_geom, const int *leaf_start, double *V,
                     cudaStream_t s)
 {
-    for (int cur = 1; cur < L;) {
-        const int D = L - cur < SUB_D ? L - cur : SUB_D;
+    int l0[LCAP + 1], D[LCAP + 1];
+    const int n = l2l_rounds(L, l0, D);
+    for (int r = 0; r < n; ++r) {
         note_launch();
-        k_l2l_sub<<<(unsigned)(1ll << cur), SUB_T, 0, s>>>(p, KP, cur, D, L, d_geom, leaf_start, V);
-        cur += D;
+        k_l2l_sub<<<(unsigned)(1ll << l0[r]), SUB_T, 0, s>>>(p, KP, l0[r], D[r], L, d_geom,
+                                                              leaf_start, V);
     }
+}
+
+void launch_l2l_batch(const L2LArgs *a, const int *bstart, int nm, int nblocks, cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    note_launch();
+    k_l2l_batch<<<(unsigned)nblocks, SUB_T, 0, s>>>(a, bstart, nm);
 }
 
 #define INST(real)                                                                              \

@@ -169,7 +169,7 @@ __device__ __forceinline__ void tile_bitmap(const Tile &t, const int *far_off, c
     __syncthreads();
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int i = warp; i < t.nt; i += nw) {
-        long long hid = (1ll << t.level) + 2ll * (t.first + i) + t.parity;
+        long long hid = (1ll << t.level) + t.keys[i];
         int e0 = far_off[hid], n = far_num[hid];
         for (int e = lane; e < n; e += 32) {
             int u = far[e0 + e].gid - t.gid_base;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(TL_T) k_tile_fill(const Tile *tiles, const int
     __syncthreads();
     int nw = blockDim.x >> 5;
     for (int i = warp; i < t.nt; i += nw) {
-        long long hid = (1ll << t.level) + 2ll * (t.first + i) + t.parity;
+        long long hid = (1ll << t.level) + t.keys[i];
         int e0 = far_off[hid], n = far_num[hid];
         for (int e = lane; e < n; e += 32) {
             FarEnt fe = far[e0 + e];

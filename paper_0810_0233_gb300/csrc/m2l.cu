@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(KP * 4) k_m2l(int p, const Tile *tiles, const 
     for (int i = 0; i < 4; ++i) {
         int ti = 4 * lane + i;
         if (ti >= t.nt) continue;
-        long long hid = (1ll << t.level) + 2ll * (t.first + ti) + t.parity;
+        long long hid = (1ll << t.level) + t.keys[ti];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             int n = 8 * warp + j;
@@ -265,11 +265,12 @@ __global__ void __launch_bounds__(KP * 4) k_m2l_f32(int p, const Tile *tiles, co
 // pow and division are slow on this part: one division per block).
 constexpr int RED_SPLIT = 4;
 
-__global__ void k_m2l_reduce(int p, int KP, const Tile *tiles, const int *tile_item0,
-                             const int *tile_nitems, const float *Ps, const Geom *g, double *V)
+__device__ __forceinline__ void m2l_reduce_body(int p, int KP, const Tile *tiles,
+                                                const int *tile_item0, const int *tile_nitems,
+                                                const float *Ps, const Geom *g, double *V,
+                                                int tile)
 {
     extern __shared__ double en[];
-    const int tile = blockIdx.x;
     const Tile t = tiles[tile];
     const int K = nterms(p) - 1;
     const double hinv = 1.0 / g->h[t.level];
@@ -288,9 +289,32 @@ __global__ void k_m2l_reduce(int p, int KP, const Tile *tiles, const int *tile_i
         int ti = j / K, n = j - ti * K;
         double s = 0.0;
         for (int it = 0; it < ni; ++it) s += (double)Ps[((long long)(i0 + it) * TT + ti) * KP + n];
-        long long hid = (1ll << t.level) + 2ll * (t.first + ti) + t.parity;
+        long long hid = (1ll << t.level) + t.keys[ti];
         V[hid * KP + n] = s * en[n];
     }
+}
+
+__global__ void k_m2l_reduce(int p, int KP, const Tile *tiles, const int *tile_item0,
+                             const int *tile_nitems, const float *Ps, const Geom *g, double *V)
+{
+    m2l_reduce_body(p, KP, tiles, tile_item0, tile_nitems, Ps, g, V, blockIdx.x);
+}
+
+// every member's tiles in one launch (ensemble step)
+__global__ void k_m2l_reduce_batch(const ReduceArgs *a, const int *bstart, int nm)
+{
+    int tile;
+    const ReduceArgs &x = a[batch_member(bstart, nm, blockIdx.x, tile)];
+    m2l_reduce_body(x.p, x.KP, x.tiles, x.tile_item0, x.tile_nitems, x.Ps, x.g, x.V, tile);
+}
+
+void launch_reduce_batch(int p, const ReduceArgs *a, const int *bstart, int nm, int nblocks,
+                         cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    note_launch();
+    k_m2l_reduce_batch<<<dim3((unsigned)nblocks, RED_SPLIT), 256,
+                         sizeof(double) * (nterms(p) - 1), s>>>(a, bstart, nm);
 }
 
 size_t m2l_f32_smem(int KP, int ldD)

@@ -267,12 +267,13 @@ __global__ void k_m2l_ops(int p, const float *D, int ldD, const uint16_t *it_g, 
 // (SPLIT), or the scaled FP32 moments alone in plane 0 (the kernel that
 // splits them in registers on the way to tensor memory).
 template <int KP, bool SPLIT>
-__global__ void k_q_split(int p, long long ncell, const float *Q, const float *gk, float *Qs)
+__device__ __forceinline__ void q_split_body(int p, long long ncell, const float *Q,
+                                             const float *gk, float *Qs, long long blk)
 {
     typedef TcShape<KP> S;
     constexpr int KT = S::KT;
     const int K = nterms(p) - 1;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = blk * blockDim.x + threadIdx.x;
     if (i >= ncell * (KT / 4)) return;
     const long long hid = i / (KT / 4);
     const int k4 = (int)(i - hid * (KT / 4)) * 4;
@@ -305,6 +306,20 @@ __global__ void k_q_split(int p, long long ncell, const float *Q, const float *g
         make_float4(lo[0], lo[1], lo[2], lo[3]);
 }
 
+template <int KP, bool SPLIT>
+__global__ void k_q_split(int p, long long ncell, const float *Q, const float *gk, float *Qs)
+{
+    q_split_body<KP, SPLIT>(p, ncell, Q, gk, Qs, blockIdx.x);
+}
+
+template <int KP>
+__global__ void k_q_split_batch(const QSplitArgs *a, const int *bstart, int nm)
+{
+    int blk;
+    const QSplitArgs &x = a[batch_member(bstart, nm, blockIdx.x, blk)];
+    q_split_body<KP, true>(x.p, x.ncell, x.Q, x.gk, x.Qs, blk);
+}
+
 // 16 consecutive accumulator columns of this warp's 32 TMEM lanes
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 {
@@ -319,10 +334,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 
 // ------------------------------------------------------------ contraction
 template <int KP, bool TMA>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_m2l_tc(const M2LItem *items, const int *ent_u, const int *ent_src, const float *Qs,
-             long long qplane, const __grid_constant__ CUtensorMap qmap, int ncell,
-             const unsigned char *Bop, float *Ps, int *flags, long long spin, int stall)
+__device__ __forceinline__ void m2l_tc_body(const M2LItem *items, const int *ent_u,
+                                            const int *ent_src, const float *Qs, long long qplane,
+                                            const CUtensorMap *qmap, int ncell,
+                                            const unsigned char *Bop, float *Ps, int *flags,
+                                            long long spin, int stall, int itx)
 {
     typedef TcShape<KP> S;
     extern __shared__ __align__(1024) unsigned char smraw[];
@@ -334,7 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     volatile int *abort = &s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const M2LItem item = items[blockIdx.x];
+    const M2LItem item = items[itx];
     const int ne = item.e1 - item.e0;
     const int nunits = ne * S::NCH;
     const uint32_t sbase = (smem_u32(smraw) + 1023u) & ~1023u;  // swizzle atoms
@@ -407,8 +423,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     // a cell without this partner reads row 0 (zeros)
                     const int4 q = make_int4(rw.x >= 0 ? rw.x : 0, rw.y >= 0 ? rw.y : 0,
                                              rw.z >= 0 ? rw.z : 0, rw.w >= 0 ? rw.w : 0);
-                    tma_gather4(st + dsta, &qmap, c * TC_KC, q, bb);
-                    tma_gather4(st + S::A_BYTES + dsta, &qmap, c * TC_KC,
+                    tma_gather4(st + dsta, qmap, c * TC_KC, q, bb);
+                    tma_gather4(st + S::A_BYTES + dsta, qmap, c * TC_KC,
                                 make_int4(q.x + ncell, q.y + ncell, q.z + ncell, q.w + ncell), bb);
                     issued = u + 1;
                 }
@@ -510,7 +526,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (!*abort) {
             const int quad = warp & 3, half = warp >> 2;
-            float *out = Ps + ((long long)blockIdx.x * TT + quad * 32 + lane) * KP;
+            float *out = Ps + ((long long)itx * TT + quad * 32 + lane) * KP;
             const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
 #pragma unroll
             for (int c0 = 16 * half; c0 < S::N; c0 += 16 * (TC_PROD / 128)) {
@@ -580,6 +596,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(S::TMEM_COLS));
     }
+}
+
+template <int KP, bool TMA>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tc(const M2LItem *items, const int *ent_u, const int *ent_src, const float *Qs,
+             long long qplane, const __grid_constant__ CUtensorMap qmap, int ncell,
+             const unsigned char *Bop, float *Ps, int *flags, long long spin, int stall)
+{
+    m2l_tc_body<KP, TMA>(items, ent_u, ent_src, Qs, qplane, &qmap, ncell, Bop, Ps, flags, spin,
+                         stall, blockIdx.x);
+}
+
+// every member's items in one launch (ensemble step; cp.async gather)
+template <int KP>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tc_batch(const M2LTCArgs *a, const int *bstart, int nm, long long spin, int stall)
+{
+    int itx;
+    const M2LTCArgs &x = a[batch_member(bstart, nm, blockIdx.x, itx)];
+    m2l_tc_body<KP, false>(x.items, x.ent_u, x.ent_src, x.Qs, x.qplane, nullptr, 0, x.Bop, x.Ps,
+                           x.flags, spin, stall, itx);
 }
 
 // ------------------------------------------- contraction, A in tensor memory
@@ -867,6 +904,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 template <int KP> static size_t tc_smem()
 {
     return (size_t)TcShape<KP>::ST * TcShape<KP>::STAGE + 1024;
+}
+
+int q_split_blocks(int KP, long long ncell) { return (int)((ncell * (m2l_tc_kt(KP) / 4) + 255) / 256); }
+
+void launch_q_split_batch(int KP, const QSplitArgs *a, const int *bstart, int nm, int nblocks,
+                          cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    note_launch();
+    switch (KP) {
+    case 40: k_q_split_batch<40><<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm); break;
+    case 56: k_q_split_batch<56><<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm); break;
+    case 88: k_q_split_batch<88><<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm); break;
+    case 120: k_q_split_batch<120><<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm); break;
+    default: break;
+    }
+}
+
+template <int KP> static size_t tc_smem();
+
+void launch_m2l_tc_batch(int KP, const M2LTCArgs *a, const int *bstart, int nm, int nblocks,
+                         long long spin, int stall, cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+#define M2LTCB(KPV)                                                                             \
+    case KPV: {                                                                                 \
+        const int smem = (int)tc_smem<KPV>();                                                   \
+        cudaFuncSetAttribute(k_m2l_tc_batch<KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             smem);                                                             \
+        note_launch();                                                                          \
+        k_m2l_tc_batch<KPV><<<(unsigned)nblocks, TC_THREADS, smem, s>>>(a, bstart, nm, spin,     \
+                                                                        stall);                 \
+    } break;
+    switch (KP) {
+        M2LTCB(40) M2LTCB(56) M2LTCB(88) M2LTCB(120)
+    default: break;
+    }
+#undef M2LTCB
 }
 
 bool m2l_tc_supported(int KP)

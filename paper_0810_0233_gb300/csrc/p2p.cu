@@ -4,6 +4,11 @@
 // FP64 direct sum used to measure the error of the fast method.
 #include "ccfmm_dev.cuh"
 
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
 namespace ccfmm {
 
 // sources staged per batch and resident blocks per SM (the register budget);
@@ -160,11 +165,11 @@ __device__ __forceinline__ Sum3<real> l2p_eval(int p, const real *vs, real x, re
 //    source on the field point contributes nothing, Appendix updateField);
 //    no other leaf can hold a point at the target's position.
 template <typename real>
-__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, int L, const int *leaf_start,
-                                               const int2 *near_nl, const NearEnt *near,
-                                               const Geom *g, const typename vec4<real>::t *A,
-                                               const typename vec2<real>::t *B, const double *V,
-                                               typename vec4<real>::t *H)
+__device__ __forceinline__ void p2p_body(int p, int KP, int L, const int *leaf_start,
+                                         const int2 *near_nl, const NearEnt *near, const Geom *g,
+                                         const typename vec4<real>::t *A,
+                                         const typename vec2<real>::t *B, const double *V,
+                                         typename vec4<real>::t *H, long long key)
 {
     typedef typename vec4<real>::t R4;
     typedef typename vec2<real>::t R2;
@@ -177,7 +182,6 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
     real *vs = reinterpret_cast<real *>(epf + P2P_NE + 4);  // [KP]
     __shared__ int wsum[P2P_T / 32];
 
-    const long long key = blockIdx.x;
     const int t0 = leaf_start[key], nt = leaf_start[key + 1] - t0;
     if (nt == 0) return;
     const int2 nlk = near_nl[key];  // (first entry, count) of the leaf's near list
@@ -336,6 +340,319 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB) k_p2p(int p, int KP, in
 }
 
 template <typename real>
+__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+    k_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl, const NearEnt *near,
+          const Geom *g, const typename vec4<real>::t *A, const typename vec2<real>::t *B,
+          const double *V, typename vec4<real>::t *H)
+{
+    p2p_body<real>(p, KP, L, leaf_start, near_nl, near, g, A, B, V, H, blockIdx.x);
+}
+
+// every member's leaves in one launch (ensemble step)
+__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+    k_p2p_batch(const P2PArgs *a, const int *bstart, int nm)
+{
+    int key;
+    const P2PArgs &x = a[batch_member(bstart, nm, blockIdx.x, key)];
+    p2p_body<float>(x.p, x.KP, x.L, x.leaf_start, x.near_nl, x.near, x.g, x.A, x.B, x.V, x.H,
+                    key);
+}
+
+// Ordered form: block b takes the b-th (member, leaf) of a list sorted by
+// decreasing cost (target dipoles x near-field sources).  Blocks are
+// dispatched roughly in index order, so the heaviest leaves of crowded
+// samples start first and the tail of the launch is short, while blocks
+// still end one by one and leave room for the far chain running beside.
+__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+    k_p2p_ordered(const P2PArgs *a, const int2 *work)
+{
+    const int2 it = work[blockIdx.x];
+    const P2PArgs &x = a[it.x];
+    p2p_body<float>(x.p, x.KP, x.L, x.leaf_start, x.near_nl, x.near, x.g, x.A, x.B, x.V, x.H,
+                    it.y);
+}
+
+void launch_p2p_ordered(const P2PArgs *d_args, const int2 *work, int nwork, int KP, cudaStream_t s)
+{
+    if (nwork <= 0) return;
+    const size_t smem = (size_t)P2P_CH * (sizeof(float4) + sizeof(float2)) +
+                        (size_t)P2P_NE * sizeof(float4) + (2 * P2P_NE + 4) * sizeof(int) +
+                        (size_t)KP * sizeof(float) + 64;
+    cudaFuncSetAttribute(k_p2p_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
+    k_p2p_ordered<<<(unsigned)nwork, P2P_T, smem, s>>>(d_args, work);
+}
+
+// near-field cost of every leaf of every member: target dipoles x sources
+// over its near list (the P2P work of the leaf)
+__global__ void k_leaf_cost(const P2PArgs *a, const int *bstart, int nm, long long *cost)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= __ldg(bstart + nm)) return;
+    int lo = 0, hi = nm;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bstart[mid] <= g) lo = mid; else hi = mid;
+    }
+    const P2PArgs &x = a[lo];
+    const int key = g - bstart[lo];
+    const long long nt = x.leaf_start[key + 1] - x.leaf_start[key];
+    long long ns = 0;
+    if (nt > 0) {
+        const int2 nl = x.near_nl[key];
+        for (int e = nl.x; e < nl.x + nl.y; ++e)
+            ns += x.leaf_start[x.near[e].src + 1] - x.leaf_start[x.near[e].src];
+    }
+    cost[g] = nt * ns;
+}
+
+void launch_leaf_cost(const P2PArgs *d_args, const int *d_bstart, int nm, int nleaves,
+                      long long *cost, cudaStream_t s)
+{
+    if (nleaves <= 0) return;
+    note_launch();
+    k_leaf_cost<<<(unsigned)((nleaves + 255) / 256), 256, 0, s>>>(d_args, d_bstart, nm, cost);
+}
+
+void launch_p2p_batch(const P2PArgs *d_args, const int *d_bstart, int nm, int nblocks, int KP,
+                      cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    const size_t smem = (size_t)P2P_CH * (sizeof(float4) + sizeof(float2)) +
+                        (size_t)P2P_NE * sizeof(float4) + (2 * P2P_NE + 4) * sizeof(int) +
+                        (size_t)KP * sizeof(float) + 64;
+    cudaFuncSetAttribute(k_p2p_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
+    k_p2p_batch<<<(unsigned)nblocks, P2P_T, smem, s>>>(d_args, d_bstart, nm);
+}
+
+// ------------------------------------------- symmetric near field (variant)
+// Newton's third law: the pair (i, j) of leaves A and B gives the field of j
+// at i and of i at j (Eq. H2 as read is symmetric in that sense:
+// r -> -r leaves [3 (m.u) u - m] / r^3 unchanged), and the offset, r^2,
+// the rsqrt and r^-3 are shared by both directions.  The block of leaf A
+// takes its own leaf one-sided (as k_p2p) and every near leaf B with a
+// larger key both ways; the leaves with smaller keys reach A through their
+// own blocks.  The field at B's dipoles is summed per staged source in
+// shared memory (shared atomics; within a stripe the threads of different
+// target groups visit the sources in rotated order, so that they seldom
+// meet on one source) and then added to H with one vector global reduction
+// per source; A's own fields are added the same way.  H must be zero before
+// the launch, the smooth field is added afterwards (k_l2p), and the order of
+// the global additions is not fixed: results vary in the last bits from run
+// to run.  Selected by CCFMM_P2P=sym (FP32, near/far overlap on).
+#ifndef CCFMM_P2PS_CH
+#define CCFMM_P2PS_CH 1024
+#endif
+constexpr int P2PS_CH = CCFMM_P2PS_CH;
+
+__device__ __forceinline__ void red_add4(float4 *p, float a, float b, float c)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+                 "f"(0.f)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+    k_p2p_sym(int L, const int *leaf_start, const int2 *near_nl, const NearEnt *near,
+              const Geom *g, const float4 *A, const float2 *B, float4 *H)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float4 *sp = reinterpret_cast<float4 *>(smraw);              // [P2PS_CH]
+    float2 *sm = reinterpret_cast<float2 *>(sp + P2PS_CH);       // [P2PS_CH]
+    float *acc = reinterpret_cast<float *>(sm + P2PS_CH);        // [3 P2PS_CH]
+    int *sidx = reinterpret_cast<int *>(acc + 3 * P2PS_CH);      // [P2PS_CH]
+    float4 *esh = reinterpret_cast<float4 *>(sidx + P2PS_CH);    // [P2P_NE]
+    int *est = reinterpret_cast<int *>(esh + P2P_NE);            // [P2P_NE]
+    int *epf = est + P2P_NE;                                     // [P2P_NE + 1]
+    __shared__ int wsum[P2P_T / 32];
+
+    const long long key = blockIdx.x;
+    const int t0 = leaf_start[key], nt = leaf_start[key + 1] - t0;
+    if (nt == 0) return;
+    const int2 nlk = near_nl[key];
+    const int e0 = nlk.x, e1 = nlk.x + nlk.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double wx = g->w[L][0], wy = g->w[L][1], wz = g->w[L][2];
+
+    for (int tb = 0; tb < nt; tb += 2 * P2P_T) {
+        const int ntc = min(nt - tb, 2 * P2P_T);
+        const int ngrp = (ntc + 1) / 2;
+        const int S = max(1, P2P_T / ngrp);
+        const int q = tid % ngrp, stripe = tid / ngrp;
+        const bool active = stripe < S;
+        const int i0 = tb + 2 * q;
+        // a padded second target (odd ntc) repeats the first with zero moment,
+        // so that it adds nothing to the sources
+        const bool two = i0 + 1 < tb + ntc;
+        float tx[2][3], tm[2][3], hs[2][3];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int ti = t0 + min(i0 + i, tb + ntc - 1);
+            const float4 a = A[ti];
+            const float2 b = B[ti];
+            const bool live = i == 0 || two;
+            tx[i][0] = a.x;
+            tx[i][1] = a.y;
+            tx[i][2] = a.z;
+            tm[i][0] = live ? a.w : 0.f;
+            tm[i][1] = live ? b.x : 0.f;
+            tm[i][2] = live ? b.y : 0.f;
+            hs[i][0] = hs[i][1] = hs[i][2] = 0.f;
+        }
+        // 1) the leaf's own dipoles, one-sided, r = 0 possible
+        for (int b0 = 0; b0 < nt; b0 += P2PS_CH) {
+            const int len = min(P2PS_CH, nt - b0);
+            __syncthreads();
+            for (int v = tid; v < len; v += P2P_T) {
+                sp[v] = A[t0 + b0 + v];
+                sm[v] = B[t0 + b0 + v];
+            }
+            __syncthreads();
+            if (active) {
+                int j0, j1;
+                stripe_range(len, S, stripe, j0, j1);
+                p2p_range<float, true>(sp, sm, j0, j1, tx, hs);
+            }
+        }
+        // 2) near leaves with a larger key, both directions
+        for (int ec = e0; ec < e1; ec += P2P_NE) {
+            const int nec = min(P2P_NE, e1 - ec);
+            __syncthreads();
+            int c0 = 0, c1 = 0;
+            for (int r = 0; r < 2; ++r) {
+                const int e = 2 * tid + r;
+                int cnt = 0;
+                if (e < nec) {
+                    const NearEnt x = near[ec + e];
+                    const int st = leaf_start[x.src];
+                    cnt = (x.src > (int)key) ? leaf_start[x.src + 1] - st : 0;
+                    est[e] = st;
+                    esh[e] = make_float4((float)((double)x.ox * wx), (float)((double)x.oy * wy),
+                                         (float)((double)x.oz * wz), 0.f);
+                }
+                if (r == 0) c0 = cnt; else c1 = cnt;
+            }
+            const int v = c0 + c1;
+            int x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
+            __syncthreads();
+            int base = 0;
+            for (int w = 0; w < warp; ++w) base += wsum[w];
+            const int ex = base + x - v;
+            if (2 * tid < nec) epf[2 * tid] = ex;
+            if (2 * tid + 1 < nec) epf[2 * tid + 1] = ex + c0;
+            if (tid == 0) {
+                int tot = 0;
+                for (int w = 0; w < P2P_T / 32; ++w) tot += wsum[w];
+                epf[nec] = tot;
+            }
+            __syncthreads();
+            const int total = epf[nec];
+            for (int b0 = 0; b0 < total; b0 += P2PS_CH) {
+                const int len = min(P2PS_CH, total - b0);
+                if (b0) __syncthreads();
+                for (int e = warp; e < nec; e += P2P_T / 32) {
+                    const int lo = max(epf[e], b0), hi = min(epf[e + 1], b0 + len);
+                    if (lo >= hi) continue;
+                    const int off = est[e] - epf[e];
+                    const float4 sh = esh[e];
+                    for (int gv = lo + lane; gv < hi; gv += 32) {
+                        const float4 a = A[off + gv];
+                        sp[gv - b0] = make_float4(a.x - sh.x, a.y - sh.y, a.z - sh.z, a.w);
+                        sm[gv - b0] = B[off + gv];
+                        sidx[gv - b0] = off + gv;
+                        acc[3 * (gv - b0)] = acc[3 * (gv - b0) + 1] = acc[3 * (gv - b0) + 2] = 0.f;
+                    }
+                }
+                __syncthreads();
+                if (active) {
+                    int j0, j1;
+                    stripe_range(len, S, stripe, j0, j1);
+                    const int ls = j1 - j0;
+                    int j = ls > 0 ? j0 + q % ls : j0;
+                    for (int k = 0; k < ls; ++k) {
+                        const float4 s4 = sp[j];
+                        const float2 m2 = sm[j];
+                        float rv0 = 0.f, rv1 = 0.f, rv2 = 0.f;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const float rx = tx[i][0] - s4.x, ry = tx[i][1] - s4.y,
+                                        rz = tx[i][2] - s4.z;
+                            const float r2 = rx * rx + ry * ry + rz * rz;
+                            const float ri = rsq<float>(r2);
+                            const float ri2 = ri * ri, ri3 = ri2 * ri;
+                            // field of j at target i
+                            const float t = 3.f * (s4.w * rx + m2.x * ry + m2.y * rz) * ri2;
+                            hs[i][0] += ri3 * (t * rx - s4.w);
+                            hs[i][1] += ri3 * (t * ry - m2.x);
+                            hs[i][2] += ri3 * (t * rz - m2.y);
+                            // field of target i at j (the same expression in -r)
+                            const float u = 3.f * (tm[i][0] * rx + tm[i][1] * ry + tm[i][2] * rz) * ri2;
+                            rv0 += ri3 * (u * rx - tm[i][0]);
+                            rv1 += ri3 * (u * ry - tm[i][1]);
+                            rv2 += ri3 * (u * rz - tm[i][2]);
+                        }
+                        atomicAdd(&acc[3 * j], rv0);
+                        atomicAdd(&acc[3 * j + 1], rv1);
+                        atomicAdd(&acc[3 * j + 2], rv2);
+                        j = (j + 1 == j1) ? j0 : j + 1;
+                    }
+                }
+                __syncthreads();
+                for (int v2 = tid; v2 < len; v2 += P2P_T)
+                    red_add4(H + sidx[v2], acc[3 * v2], acc[3 * v2 + 1], acc[3 * v2 + 2]);
+                __syncthreads();
+            }
+        }
+        // 3) reduce the stripes; add the targets' fields to H
+        __syncthreads();
+        float *red = reinterpret_cast<float *>(sp);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) red[6 * tid + 3 * i + k] = hs[i][k];
+        __syncthreads();
+        if (tid < ngrp) {
+            float f[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            for (int st = 0; st < S; ++st) {
+                const float *rr = red + 6 * (st * ngrp + tid);
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) f[i][k] += rr[3 * i + k];
+            }
+            red_add4(H + t0 + i0, f[0][0], f[0][1], f[0][2]);
+            if (two) red_add4(H + t0 + i0 + 1, f[1][0], f[1][1], f[1][2]);
+        }
+    }
+}
+
+bool p2p_symmetric()
+{
+    const char *e = getenv("CCFMM_P2P");
+    return e && !strcmp(e, "sym");
+}
+
+void launch_p2p_sym(int L, const int *leaf_start, const int2 *near_nl, const NearEnt *near,
+                    const Geom *d_geom, const float4 *A, const float2 *B, float4 *H,
+                    long long N, cudaStream_t s)
+{
+    const size_t smem = (size_t)P2PS_CH * (16 + 8 + 12 + 4) + (size_t)P2P_NE * 16 +
+                        (2 * P2P_NE + 4) * sizeof(int) + 64;
+    static_assert(P2PS_CH * 4 >= 6 * P2P_T, "the stripe sums reuse the staging buffer");
+    cudaMemsetAsync(H, 0, sizeof(float4) * (size_t)N, s);
+    cudaFuncSetAttribute(k_p2p_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
+    k_p2p_sym<<<(unsigned)(1ll << L), P2P_T, smem, s>>>(L, leaf_start, near_nl, near, d_geom, A,
+                                                         B, H);
+}
+
+template <typename real>
 void launch_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl,
                 const NearEnt *near, const Geom *d_geom, const typename vec4<real>::t *A,
                 const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
@@ -357,14 +674,14 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl
 constexpr int L2P_W = 4;  // leaves (warps) per block
 
 template <typename real, int P>
-__global__ void __launch_bounds__(32 * L2P_W) k_l2p(int KP, int L, const int *leaf_start,
-                                                    const typename vec4<real>::t *A,
-                                                    const double *V, typename vec4<real>::t *H)
+__device__ __forceinline__ void l2p_body(int KP, int L, const int *leaf_start,
+                                         const typename vec4<real>::t *A, const double *V,
+                                         typename vec4<real>::t *H, long long blk)
 {
     __shared__ real vs[L2P_W][nterms(PMAX)];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int K = nterms(P) - 1;
-    const long long key = (long long)blockIdx.x * L2P_W + w;
+    const long long key = blk * L2P_W + w;
     const bool live = key < (1ll << L);
     const int t0 = live ? leaf_start[key] : 0, nt = live ? leaf_start[key + 1] - t0 : 0;
     const long long hid = (1ll << L) + key;
@@ -380,6 +697,40 @@ __global__ void __launch_bounds__(32 * L2P_W) k_l2p(int KP, int L, const int *le
         h.z -= sl.z;
         H[t0 + i] = h;
     }
+}
+
+template <typename real, int P>
+__global__ void __launch_bounds__(32 * L2P_W) k_l2p(int KP, int L, const int *leaf_start,
+                                                    const typename vec4<real>::t *A,
+                                                    const double *V, typename vec4<real>::t *H)
+{
+    l2p_body<real, P>(KP, L, leaf_start, A, V, H, blockIdx.x);
+}
+
+// every member's smooth field in one launch (ensemble step)
+template <int P>
+__global__ void __launch_bounds__(32 * L2P_W) k_l2p_batch(const P2PArgs *a, const int *bstart,
+                                                          int nm)
+{
+    int blk;
+    const P2PArgs &x = a[batch_member(bstart, nm, blockIdx.x, blk)];
+    l2p_body<float, P>(x.KP, x.L, x.leaf_start, x.A, x.V, x.H, blk);
+}
+
+int l2p_blocks(int L) { return (int)(((1ll << L) + L2P_W - 1) / L2P_W); }
+
+void launch_l2p_batch(int p, const P2PArgs *a, const int *bstart, int nm, int nblocks,
+                      cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    note_launch();
+#define L2PB(PV)                                                                                 \
+    case PV: k_l2p_batch<PV><<<(unsigned)nblocks, 32 * L2P_W, 0, s>>>(a, bstart, nm); break;
+    switch (p) {
+        L2PB(1) L2PB(2) L2PB(3) L2PB(4) L2PB(5) L2PB(6) L2PB(7) L2PB(8)
+    default: break;
+    }
+#undef L2PB
 }
 
 template <typename real>
@@ -402,13 +753,13 @@ void launch_l2p(int p, int KP, int L, const int *leaf_start, const typename vec4
 constexpr int FIN_T = 256;
 
 template <typename real>
-__global__ void __launch_bounds__(FIN_T) k_finish(const typename vec4<real>::t *H, const int *perm,
-                                                  const double *mom, long long n, double *Hout,
-                                                  double *partial)
+__device__ __forceinline__ void finish_body(const typename vec4<real>::t *H, const int *perm,
+                                            const double *mom, long long n, double *Hout,
+                                            double *partial, long long blk)
 {
     __shared__ double red[FIN_T / 32];
     double e = 0.0;
-    long long s = (long long)blockIdx.x * FIN_T + threadIdx.x;
+    long long s = blk * FIN_T + threadIdx.x;
     if (s < n) {
         long long i = perm[s];
         typename vec4<real>::t h = H[s];
@@ -426,12 +777,20 @@ __global__ void __launch_bounds__(FIN_T) k_finish(const typename vec4<real>::t *
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < FIN_T / 32; ++w) t += red[w];
-        partial[blockIdx.x] = t;
+        partial[blk] = t;
     }
 }
 
+template <typename real>
+__global__ void __launch_bounds__(FIN_T) k_finish(const typename vec4<real>::t *H, const int *perm,
+                                                  const double *mom, long long n, double *Hout,
+                                                  double *partial)
+{
+    finish_body<real>(H, perm, mom, n, Hout, partial, blockIdx.x);
+}
+
 // E = -1/2 sum of the partials, summed in a fixed order
-__global__ void k_energy_final(const double *partial, long long nparts, double *E)
+__device__ __forceinline__ void energy_body(const double *partial, long long nparts, double *E)
 {
     __shared__ double red[256];
     double t = 0.0;
@@ -444,6 +803,37 @@ __global__ void k_energy_final(const double *partial, long long nparts, double *
     }
     if (threadIdx.x == 0) *E = -0.5 * red[0];
 }
+
+__global__ void k_energy_final(const double *partial, long long nparts, double *E)
+{
+    energy_body(partial, nparts, E);
+}
+
+// every member's unpermute + energy partials, then every member's energy
+__global__ void __launch_bounds__(FIN_T) k_finish_batch(const FinishArgs *a, const int *bstart,
+                                                        int nm)
+{
+    int blk;
+    const FinishArgs &x = a[batch_member(bstart, nm, blockIdx.x, blk)];
+    finish_body<float>(x.H, x.perm, x.mom, x.n, x.Hout, x.partial, blk);
+}
+
+__global__ void k_energy_batch(const FinishArgs *a)
+{
+    const FinishArgs &x = a[blockIdx.x];
+    energy_body(x.partial, (x.n + FIN_T - 1) / FIN_T, x.E);
+}
+
+void launch_finish_batch(const FinishArgs *d_args, const int *d_bstart, int nm, int nblocks,
+                         cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    note_launch(2);
+    k_finish_batch<<<(unsigned)nblocks, FIN_T, 0, s>>>(d_args, d_bstart, nm);
+    k_energy_batch<<<(unsigned)nm, 256, 0, s>>>(d_args);
+}
+
+int finish_blocks(long long n) { return (int)((n + FIN_T - 1) / FIN_T); }
 
 template <typename real>
 void launch_finish(const typename vec4<real>::t *H, const int *perm, const double *mom,

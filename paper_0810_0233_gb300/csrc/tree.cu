@@ -297,11 +297,39 @@ void launch_permute_moments(const double *mom, const int *perm, long long n,
     k_permute_moments<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mom, perm, n, A, B);
 }
 
-// non-empty cells per level (levels 0..L), from the leaf ranges
-__global__ void k_level_counts(const int *leaf_start, int L, int *ne, int *flags)
+// every member's moments into its sorted arrays, and its Taylor
+// coefficients zeroed, in one launch (ensemble step)
+__global__ void k_permute_batch(const PermuteArgs *a, const int *bstart, int nm)
 {
-    __shared__ int h[LCAP + 1];
-    if (threadIdx.x <= LCAP) h[threadIdx.x] = 0;
+    int blk;
+    const int m = batch_member(bstart, nm, blockIdx.x, blk);
+    const PermuteArgs &x = a[m];
+    const long long s = (long long)blk * 256 + threadIdx.x;
+    if (s < x.n) {
+        const long long i = x.perm[s];
+        x.A[s].w = (float)x.mom[3 * i];
+        x.B[s] = make_float2((float)x.mom[3 * i + 1], (float)x.mom[3 * i + 2]);
+    }
+    const long long nth = (long long)(bstart[m + 1] - bstart[m]) * 256;
+    for (long long j = s; j < x.nV; j += nth) x.V[j] = 0.0;
+}
+
+int permute_blocks(long long n) { return (int)((n + 255) / 256); }
+
+void launch_permute_batch(const PermuteArgs *a, const int *bstart, int nm, int nblocks,
+                          cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    note_launch();
+    k_permute_batch<<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm);
+}
+
+// non-empty cells per level (levels 0..L), from the leaf ranges
+__global__ void k_level_counts(const int *leaf_start, int L, int *ne, int *flags, int *oflags,
+                               int *ne_odd)
+{
+    __shared__ int h[LCAP + 1], ho[LCAP + 1];
+    if (threadIdx.x <= LCAP) h[threadIdx.x] = ho[threadIdx.x] = 0;
     __syncthreads();
     long long ncell = (1ll << (L + 1)) - 1;
     for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < ncell;
@@ -311,22 +339,59 @@ __global__ void k_level_counts(const int *leaf_start, int L, int *ne, int *flags
         long long key = hid - (1ll << l);
         int sh = L - l;
         const bool full = leaf_start[(key + 1) << sh] > leaf_start[key << sh];
+        const bool odd = full && (key & 1);
         if (full) atomicAdd(&h[l], 1);
+        if (odd) atomicAdd(&ho[l], 1);
         if (flags) flags[hid] = full ? 1 : 0;
+        if (oflags) oflags[hid] = odd ? 1 : 0;
     }
     if (flags && blockIdx.x == 0 && threadIdx.x == 0) flags[0] = 0;
+    if (oflags && blockIdx.x == 0 && threadIdx.x == 0) oflags[0] = 0;
     __syncthreads();
     if (threadIdx.x <= LCAP && h[threadIdx.x]) atomicAdd(&ne[threadIdx.x], h[threadIdx.x]);
+    if (ne_odd && threadIdx.x <= LCAP && ho[threadIdx.x])
+        atomicAdd(&ne_odd[threadIdx.x], ho[threadIdx.x]);
 }
 
-void launch_level_counts(const int *leaf_start, int L, int *d_ne, int *flags, cudaStream_t s)
+void launch_level_counts(const int *leaf_start, int L, int *d_ne, int *flags, int *oflags,
+                         int *d_ne_odd, cudaStream_t s)
 {
     cudaMemsetAsync(d_ne, 0, sizeof(int) * (LCAP + 1), s);
+    if (d_ne_odd) cudaMemsetAsync(d_ne_odd, 0, sizeof(int) * (LCAP + 1), s);
     long long ncell = (1ll << (L + 1)) - 1;
     long long nb = (ncell + 255) / 256;
     if (nb > 4096) nb = 4096;
     note_launch();
-    k_level_counts<<<(unsigned)nb, 256, 0, s>>>(leaf_start, L, d_ne, flags);
+    k_level_counts<<<(unsigned)nb, 256, 0, s>>>(leaf_start, L, d_ne, flags, oflags, d_ne_odd);
+}
+
+// target cells of the M2L tiles: the non-empty cells of each level l >= 2
+// and parity, in key order, at seg[2 l + parity]
+__global__ void k_tile_keys(int L, const int *flags, const int *rank, const int *rank_odd,
+                            const int *seg, int *tkeys)
+{
+    const long long ncell = 1ll << (L + 1);
+    for (long long hid = 4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; hid < ncell;
+         hid += (long long)gridDim.x * blockDim.x) {
+        if (!flags[hid]) continue;
+        const int l = 63 - __clzll(hid);
+        const long long l0 = 1ll << l;
+        const int key = (int)(hid - l0);
+        const int rl = rank[hid] - rank[l0], ro = rank_odd[hid] - rank_odd[l0];
+        const int par = key & 1;
+        tkeys[seg[2 * l + par] + (par ? ro : rl - ro)] = key;
+    }
+}
+
+void launch_tile_keys(int L, const int *flags, const int *rank, const int *rank_odd,
+                      const int *seg, int *tkeys, cudaStream_t s)
+{
+    if (L < 2) return;
+    const long long n = (1ll << (L + 1)) - 4;
+    long long nb = (n + 255) / 256;
+    if (nb > 4096) nb = 4096;
+    note_launch();
+    k_tile_keys<<<(unsigned)nb, 256, 0, s>>>(L, flags, rank, rank_odd, seg, tkeys);
 }
 
 __global__ void k_check_finite(const double *x, long long n, int *flags)

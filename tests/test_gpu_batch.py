@@ -65,7 +65,11 @@ def test_batch_steps_match_oracle(prec, tol):
                 if prec == "mixed":
                     check_member_local(b, s, H[sl], Hr, f, p)
                 assert abs(E[s] - Er) <= 10 * tol * abs(Er)
-        assert b.kernels_per_step() > b.ns
+        if prec == "mixed":
+            # one launch per stage over every sample (tensor-core M2L path)
+            assert 5 < b.kernels_per_step() < 40
+        else:
+            assert b.kernels_per_step() > b.ns
 
 
 @pytest.mark.parametrize("engine", ["fma", "tc"])
@@ -112,3 +116,59 @@ def test_fp64_pair_with_levels_without_m2l_entries():
         sl = slice(o[s], o[s + 1])
         with C.FMM(P[sl], M[sl], 5, 0.5, precision="fp64") as f:
             assert rel(H[sl], f.field()) < 1e-13
+
+
+@pytest.mark.parametrize("mode", ["batched", "graph"])
+def test_batched_stages_equal_member_graph_bitwise(monkeypatch, mode):
+    """The batched stages (one launch per stage over all samples) run each
+    sample's arithmetic unchanged: the same bits as the graph of per-sample
+    launches (CCFMM_BATCH_MODE=graph) and as standalone handles."""
+    pos, mom, off = _ensemble(ns=6, seed=79)
+    monkeypatch.delenv("CCFMM_M2L", raising=False)
+    if mode == "graph":
+        monkeypatch.setenv("CCFMM_BATCH_MODE", "graph")
+    with C.Batch(pos, mom, off, 5, 0.5) as b:
+        H = np.zeros((b.total, 3))
+        E = np.zeros(b.ns)
+        b.step(seed=5, step=0, max_angle=0.05, H_out=H, E_out=E)
+        M = b.moments()
+        k = b.kernels_per_step()
+    assert (k < 40) == (mode == "batched")
+    for s in range(b.ns):
+        sl = slice(off[s], off[s + 1])
+        with C.FMM(pos[sl], M[sl], 5, 0.5) as f:
+            Hs, Es = f.field_energy()
+        assert np.array_equal(Hs, H[sl]), s
+        assert Es == E[s], s
+
+
+def test_autotuner_picks_per_class_and_stays_exact():
+    """fmm_batch_create_ex with autotune: one (leaf, item length) per size
+    class, chosen from the candidates; the tuned ensemble still matches the
+    oracle."""
+    rng = np.random.default_rng(81)
+    sizes = [900, 1100, 3000, 3500, 9000]
+    pos, mom = [], []
+    for i, n in enumerate(sizes):
+        p_, m_ = W.clustered(n, seed=8100 + i)
+        pos.append(p_)
+        mom.append(m_)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pos, mom = np.concatenate(pos), np.concatenate(mom)
+    rule = C.leaf_size_rule(5)
+    with C.Batch(pos, mom, off, 5, 0.5, autotune=True, trials=2) as b:
+        tun = b.tuning()
+        H = np.zeros((b.total, 3))
+        b.evaluate(H_out=H)
+    octaves = sorted({int(np.floor(np.log2(n))) for n in sizes})
+    assert len(tun) == len(octaves)
+    for nmin, leaf, il in tun:
+        assert il in (32, 64)
+        assert any(abs(leaf - max(1.0, rule * f)) < 1e-9
+                   for f in (0.5, 2 ** -0.5, 1.0, 2 ** 0.5, 2.0))
+    leaf_of_octave = {int(np.floor(np.log2(nmin))): leaf for nmin, leaf, _ in tun}
+    for s, n in enumerate(sizes):
+        sl = slice(off[s], off[s + 1])
+        leaf = leaf_of_octave[int(np.floor(np.log2(n)))]
+        Hr = O.fmm_field(pos[sl], mom[sl], 5, 0.5, leaf)[0]
+        assert rel(H[sl], Hr) < 1e-5, (s, leaf)

@@ -301,3 +301,31 @@ def test_near_pair_count_from_the_lists():
             cnt = np.bincount(f.leaf_of(), minlength=1 << L)
             pr = f.pairs("near") - (1 << L)
             assert st["p2p_pairs"] == int((cnt[pr[:, 0]] * cnt[pr[:, 1]]).sum()) - len(pos)
+
+
+@pytest.mark.parametrize("kind", ["ferrofluid", "clustered", "lattice"])
+@pytest.mark.parametrize("overlap", ["1", "0"])
+def test_symmetric_near_field_variant(monkeypatch, kind, overlap):
+    """The symmetric near field (CCFMM_P2P=sym: each pair of near leaves
+    once, both directions, Newton's third law) against the oracle and the
+    default one-sided kernel: the same sums in another order, so FP32
+    rounding apart they agree; the global reductions are unordered, so
+    repeated evaluations agree only to rounding."""
+    if kind == "ferrofluid":
+        pos, mom = W.ferrofluid(20000, side=100.0 * 0.02 ** (1 / 3), seed=W.BASE_SEED + 18)
+        box = None
+    elif kind == "clustered":
+        pos, mom = W.clustered(12000, seed=W.BASE_SEED + 19)
+        box = None
+    else:
+        pos, mom, box = W.lattice(17, 13, 11, seed=W.BASE_SEED + 20)
+    monkeypatch.setenv("CCFMM_OVERLAP", overlap)
+    Href, Eref, f = O.fmm_field(pos, mom, 6, 0.5, box=box)
+    monkeypatch.delenv("CCFMM_P2P", raising=False)
+    H0, E0, _, _ = run_gpu(pos, mom, 6, 0.5, box=box, prec="mixed")
+    monkeypatch.setenv("CCFMM_P2P", "sym")
+    H1, E1, st, ex = run_gpu(pos, mom, 6, 0.5, box=box, prec="mixed")
+    assert rel(H1, Href) < TOLMIX
+    assert abs(E1 - Eref) <= 10 * TOLMIX * abs(Eref)
+    check_local(H1, Href, ex["V"], f)
+    assert rel(H1, H0) < 2e-6

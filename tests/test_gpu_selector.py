@@ -64,10 +64,17 @@ def test_features_distinguish_sets():
     assert abs(fl[7] - 1) < 1e-6 and abs(fl[8] - 1) < 1e-6
 
 
+def _mean_ns(runner, p, theta, leaf, repeats=5):
+    """Mean time per dipole (ns) over several timed runs (each the best of
+    three), so that one slow run on a shared machine decides nothing."""
+    return float(np.mean([runner.run(p, theta, leaf, repeats=3)[0] for _ in range(repeats)]))
+
+
 def test_selector_beats_rule_of_thumb():
     """Small sweep and training; on a held-out instance at target 1e-4 the
     selected configuration meets the target and is faster than the rule of
-    thumb (which is far more accurate than needed)."""
+    thumb (which is far more accurate than needed): the mean of repeated
+    timings must be at least 10 % below the rule's."""
     X, T = S.sweep(n_runs=1200, per_instance=40, n_lo=3000, n_hi=40000, seed=11)
     mlp, loss = S.train(X, T, epochs=60)
     pos, mom = S.instance("uniform", 120000, seed=4242)
@@ -75,4 +82,23 @@ def test_selector_beats_rule_of_thumb():
     sel, rule = res["selector"], res["rule_of_thumb"]
     assert sel["error"] <= 1e-4, res
     assert rule["error"] <= 1e-4
-    assert sel["ns_per_dipole"] < rule["ns_per_dipole"], res
+    r = S.Runner(pos, mom, n_err=64, seed=3)
+    t_sel = _mean_ns(r, sel["p"], sel["theta"], sel["leaf"])
+    t_rule = _mean_ns(r, rule["p"], rule["theta"], rule["leaf"])
+    assert t_sel < 0.9 * t_rule, (t_sel, t_rule, res)
+
+
+def test_shipped_selector_parameters():
+    """The network trained on the GPU by the library's own kernels ships with
+    the package (selector_params.npz): it loads, and on a 2 x 10^5 ferrofluid
+    (the density of the 10^6 workload) at target 1e-4 it chooses, without
+    falling back, a configuration that meets the target against the FP64
+    direct sum."""
+    mlp = S.load_trained()
+    assert mlp is not None
+    pos, mom = W.ferrofluid(200_000, side=100.0 * 0.2 ** (1 / 3), seed=W.BASE_SEED + 90)
+    p, th, lf, fb = C.select(mlp, pos, 1e-4)
+    assert not fb and 2 <= p <= 8 and 0.3 <= th <= 0.7 and 4 <= lf <= 64
+    r = S.Runner(pos, mom, n_err=1000, seed=4)
+    ns, err = r.run(p, th, lf)
+    assert err <= 1e-4, (p, th, lf, err)
