@@ -1515,8 +1515,8 @@ struct ccfmm_batch_s {
     bool batched = false, planned = false;
     Stage st_perm, st_p2m, st_qs, st_m2l, st_red, st_p2p, st_l2p, st_fin;
     cudaEvent_t ev_near0 = nullptr, ev_near1 = nullptr;  // near field on a second branch
-    DevBuf work;  // near-field work list, heaviest leaves first
-    int nwork = 0;
+    cudaStream_t s_hi = nullptr;  // the far chain, at the highest stream priority
+    cudaEvent_t ev_far1 = nullptr;
     std::vector<Stage> st_m2m, st_l2l;
     DevBuf eflag;  // raised by the batched tensor-core M2L's bounded waits
     int *heflag = nullptr;
@@ -1628,38 +1628,30 @@ static ccfmm_status batch_plan(ccfmm_batch_t b)
     TRY(stage_upload(b->st_red, a_red, b_red));
     b->st_l2l.assign(maxr_l2l, ccfmm_batch_s::Stage());
     for (int r = 0; r < maxr_l2l; ++r) TRY(stage_upload(b->st_l2l[r], a_l2l[r], b_l2l[r]));
-    TRY(stage_upload(b->st_p2p, a_p2p, b_p2p));
-    TRY(stage_upload(b->st_l2p, a_l2p, b_l2p));
     {
-        // near-field work list: every (member, leaf), by decreasing cost
-        const int nleaves = b->st_p2p.nblocks;
-        DevBuf cost;
-        TRY(ensure(cost, sizeof(long long) * std::max(nleaves, 1)));
-        launch_leaf_cost((const P2PArgs *)b->st_p2p.args.p, P<int>(b->st_p2p.bstart), nm, nleaves,
-                         P<long long>(cost), b->stream);
-        std::vector<long long> c(nleaves);
-        cudaError_t e = cudaMemcpyAsync(c.data(), cost.p, sizeof(long long) * nleaves,
-                                        cudaMemcpyDeviceToHost, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        cudaFree(cost.p);
-        CK(e);
-        std::vector<int> bs(nm + 1, 0);
-        for (int m = 0; m < nm; ++m) bs[m + 1] = bs[m] + b_p2p[m];
-        std::vector<int2> w;
-        w.reserve(nleaves);
-        for (int m = 0; m < nm; ++m)
-            for (int k = 0; k < b_p2p[m]; ++k)
-                if (c[bs[m] + k] > 0) w.push_back(make_int2(m, k));
-        std::stable_sort(w.begin(), w.end(), [&](const int2 &x, const int2 &y) {
-            return c[bs[x.x] + x.y] > c[bs[y.x] + y.y];
-        });
-        b->nwork = (int)w.size();
-        TRY(ensure(b->work, sizeof(int2) * std::max<size_t>(w.size(), 1)));
-        if (!w.empty())
-            CK(cudaMemcpy(b->work.p, w.data(), sizeof(int2) * w.size(), cudaMemcpyHostToDevice));
+        // the near field takes the largest samples first (their leaves stay
+        // together, in key order), so that the launch ends on small ones
+        std::vector<int> ord(nm);
+        for (int m = 0; m < nm; ++m) ord[m] = m;
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int x, int y) { return b->h[x]->N > b->h[y]->N; });
+        std::vector<P2PArgs> a2(nm);
+        std::vector<int> b2(nm);
+        for (int m = 0; m < nm; ++m) {
+            a2[m] = a_p2p[ord[m]];
+            b2[m] = b_p2p[ord[m]];
+        }
+        TRY(stage_upload(b->st_p2p, a2, b2));
     }
+    TRY(stage_upload(b->st_l2p, a_l2p, b_l2p));
     if (!b->ev_near0) CK(cudaEventCreateWithFlags(&b->ev_near0, cudaEventDisableTiming));
     if (!b->ev_near1) CK(cudaEventCreateWithFlags(&b->ev_near1, cudaEventDisableTiming));
+    if (!b->ev_far1) CK(cudaEventCreateWithFlags(&b->ev_far1, cudaEventDisableTiming));
+    if (!b->s_hi) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&b->s_hi, cudaStreamNonBlocking, greatest));
+    }
     TRY(stage_upload(b->st_fin, a_fin, b_fin));
     b->planned = true;
     return CCFMM_OK;
@@ -1680,15 +1672,21 @@ static void batch_enqueue(ccfmm_batch_t b, cudaStream_t s)
     cudaStream_t sn = b->br[0];
     cudaEventRecord(b->ev_near0, s);
     cudaStreamWaitEvent(sn, b->ev_near0, 0);
-    launch_p2p_ordered((const P2PArgs *)A(b->st_p2p), P<int2>(b->work), b->nwork, KP, sn);
+    launch_p2p_batch((const P2PArgs *)A(b->st_p2p), B(b->st_p2p), nm, b->st_p2p.nblocks, KP, sn);
     cudaEventRecord(b->ev_near1, sn);
-    launch_p2m_batch((const P2MArgs *)A(b->st_p2m), B(b->st_p2m), nm, b->st_p2m.nblocks, s);
-    for (auto &st : b->st_m2m) launch_m2m_batch((const M2MArgs *)A(st), B(st), nm, st.nblocks, s);
-    launch_q_split_batch(KP, (const QSplitArgs *)A(b->st_qs), B(b->st_qs), nm, b->st_qs.nblocks, s);
+    // the far chain on a high-priority stream: its blocks are dispatched
+    // first whenever near-field blocks retire
+    cudaStream_t sf = b->s_hi;
+    cudaStreamWaitEvent(sf, b->ev_near0, 0);
+    launch_p2m_batch((const P2MArgs *)A(b->st_p2m), B(b->st_p2m), nm, b->st_p2m.nblocks, sf);
+    for (auto &st : b->st_m2m) launch_m2m_batch((const M2MArgs *)A(st), B(st), nm, st.nblocks, sf);
+    launch_q_split_batch(KP, (const QSplitArgs *)A(b->st_qs), B(b->st_qs), nm, b->st_qs.nblocks, sf);
     launch_m2l_tc_batch(KP, (const M2LTCArgs *)A(b->st_m2l), B(b->st_m2l), nm, b->st_m2l.nblocks,
-                        spin, stall, s);
-    launch_reduce_batch(p, (const ReduceArgs *)A(b->st_red), B(b->st_red), nm, b->st_red.nblocks, s);
-    for (auto &st : b->st_l2l) launch_l2l_batch((const L2LArgs *)A(st), B(st), nm, st.nblocks, s);
+                        spin, stall, sf);
+    launch_reduce_batch(p, (const ReduceArgs *)A(b->st_red), B(b->st_red), nm, b->st_red.nblocks, sf);
+    for (auto &st : b->st_l2l) launch_l2l_batch((const L2LArgs *)A(st), B(st), nm, st.nblocks, sf);
+    cudaEventRecord(b->ev_far1, sf);
+    cudaStreamWaitEvent(s, b->ev_far1, 0);
     cudaStreamWaitEvent(s, b->ev_near1, 0);
     launch_l2p_batch(p, (const P2PArgs *)A(b->st_l2p), B(b->st_l2p), nm, b->st_l2p.nblocks, s);
     launch_finish_batch((const FinishArgs *)A(b->st_fin), B(b->st_fin), nm, b->st_fin.nblocks, s);
@@ -1760,7 +1758,8 @@ static ccfmm_status batch_capture(ccfmm_batch_t b, int rotate)
         if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nk;
     }
     b->graph_kernels[rotate] = nk;
-    e = cudaGraphInstantiate(&b->exec[rotate], g, 0);
+    // node priorities from the capturing streams (the far chain's is higher)
+    e = cudaGraphInstantiateWithFlags(&b->exec[rotate], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1863,13 +1862,15 @@ void fmm_batch_destroy(ccfmm_batch_t b)
     for (cudaStream_t s : b->br) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->evj) cudaEventDestroy(e);
     if (b->evf) cudaEventDestroy(b->evf);
-    DevBuf *bufs[] = {&b->mom, &b->H, &b->E, &b->prm, &b->eflag, &b->work};
+    DevBuf *bufs[] = {&b->mom, &b->H, &b->E, &b->prm, &b->eflag};
     for (DevBuf *d : bufs)
         if (d->p) cudaFree(d->p);
     ccfmm_batch_s::Stage *sts[] = {&b->st_perm, &b->st_p2m, &b->st_qs, &b->st_m2l, &b->st_red,
                                    &b->st_p2p, &b->st_l2p, &b->st_fin};
     if (b->ev_near0) cudaEventDestroy(b->ev_near0);
     if (b->ev_near1) cudaEventDestroy(b->ev_near1);
+    if (b->ev_far1) cudaEventDestroy(b->ev_far1);
+    if (b->s_hi) cudaStreamDestroy(b->s_hi);
     for (auto *st : sts) {
         if (st->args.p) cudaFree(st->args.p);
         if (st->bstart.p) cudaFree(st->bstart.p);

@@ -371,11 +371,6 @@ void launch_reduce_batch(int p, const ReduceArgs *a, const int *bstart, int nm, 
                          cudaStream_t s);
 void launch_p2p_batch(const P2PArgs *a, const int *bstart, int nm, int nblocks, int KP,
                       cudaStream_t s);
-// near field over a (member, leaf) work list, block b = item b, and the
-// cost of every (member, leaf) to order that list
-void launch_p2p_ordered(const P2PArgs *a, const int2 *work, int nwork, int KP, cudaStream_t s);
-void launch_leaf_cost(const P2PArgs *a, const int *bstart, int nm, int nleaves, long long *cost,
-                      cudaStream_t s);
 void launch_finish_batch(const FinishArgs *a, const int *bstart, int nm, int nblocks,
                          cudaStream_t s);
 // smooth field added to the near field (P2PArgs with V set), every member

@@ -358,62 +358,6 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
                     key);
 }
 
-// Ordered form: block b takes the b-th (member, leaf) of a list sorted by
-// decreasing cost (target dipoles x near-field sources).  Blocks are
-// dispatched roughly in index order, so the heaviest leaves of crowded
-// samples start first and the tail of the launch is short, while blocks
-// still end one by one and leave room for the far chain running beside.
-__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
-    k_p2p_ordered(const P2PArgs *a, const int2 *work)
-{
-    const int2 it = work[blockIdx.x];
-    const P2PArgs &x = a[it.x];
-    p2p_body<float>(x.p, x.KP, x.L, x.leaf_start, x.near_nl, x.near, x.g, x.A, x.B, x.V, x.H,
-                    it.y);
-}
-
-void launch_p2p_ordered(const P2PArgs *d_args, const int2 *work, int nwork, int KP, cudaStream_t s)
-{
-    if (nwork <= 0) return;
-    const size_t smem = (size_t)P2P_CH * (sizeof(float4) + sizeof(float2)) +
-                        (size_t)P2P_NE * sizeof(float4) + (2 * P2P_NE + 4) * sizeof(int) +
-                        (size_t)KP * sizeof(float) + 64;
-    cudaFuncSetAttribute(k_p2p_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    note_launch();
-    k_p2p_ordered<<<(unsigned)nwork, P2P_T, smem, s>>>(d_args, work);
-}
-
-// near-field cost of every leaf of every member: target dipoles x sources
-// over its near list (the P2P work of the leaf)
-__global__ void k_leaf_cost(const P2PArgs *a, const int *bstart, int nm, long long *cost)
-{
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= __ldg(bstart + nm)) return;
-    int lo = 0, hi = nm;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (bstart[mid] <= g) lo = mid; else hi = mid;
-    }
-    const P2PArgs &x = a[lo];
-    const int key = g - bstart[lo];
-    const long long nt = x.leaf_start[key + 1] - x.leaf_start[key];
-    long long ns = 0;
-    if (nt > 0) {
-        const int2 nl = x.near_nl[key];
-        for (int e = nl.x; e < nl.x + nl.y; ++e)
-            ns += x.leaf_start[x.near[e].src + 1] - x.leaf_start[x.near[e].src];
-    }
-    cost[g] = nt * ns;
-}
-
-void launch_leaf_cost(const P2PArgs *d_args, const int *d_bstart, int nm, int nleaves,
-                      long long *cost, cudaStream_t s)
-{
-    if (nleaves <= 0) return;
-    note_launch();
-    k_leaf_cost<<<(unsigned)((nleaves + 255) / 256), 256, 0, s>>>(d_args, d_bstart, nm, cost);
-}
-
 void launch_p2p_batch(const P2PArgs *d_args, const int *d_bstart, int nm, int nblocks, int KP,
                       cudaStream_t s)
 {
