@@ -305,12 +305,12 @@ def test_near_pair_count_from_the_lists():
 
 @pytest.mark.parametrize("kind", ["ferrofluid", "clustered", "lattice"])
 @pytest.mark.parametrize("overlap", ["1", "0"])
-def test_symmetric_near_field_variant(monkeypatch, kind, overlap):
+@pytest.mark.parametrize("mode", ["sym"])
+def test_near_field_variants(monkeypatch, kind, overlap, mode):
     """The symmetric near field (CCFMM_P2P=sym: each pair of near leaves
-    once, both directions, Newton's third law) against the oracle and the
-    default one-sided kernel: the same sums in another order, so FP32
-    rounding apart they agree; the global reductions are unordered, so
-    repeated evaluations agree only to rounding."""
+    once, both directions, Newton's third law; unordered global reductions)
+    against the oracle and the default one-sided kernel: the same sums in
+    another order, so FP32 rounding apart they agree."""
     if kind == "ferrofluid":
         pos, mom = W.ferrofluid(20000, side=100.0 * 0.02 ** (1 / 3), seed=W.BASE_SEED + 18)
         box = None
@@ -323,9 +323,10 @@ def test_symmetric_near_field_variant(monkeypatch, kind, overlap):
     Href, Eref, f = O.fmm_field(pos, mom, 6, 0.5, box=box)
     monkeypatch.delenv("CCFMM_P2P", raising=False)
     H0, E0, _, _ = run_gpu(pos, mom, 6, 0.5, box=box, prec="mixed")
-    monkeypatch.setenv("CCFMM_P2P", "sym")
+    monkeypatch.setenv("CCFMM_P2P", mode)
     H1, E1, st, ex = run_gpu(pos, mom, 6, 0.5, box=box, prec="mixed")
     assert rel(H1, Href) < TOLMIX
     assert abs(E1 - Eref) <= 10 * TOLMIX * abs(Eref)
     check_local(H1, Href, ex["V"], f)
     assert rel(H1, H0) < 2e-6
+
