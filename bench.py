@@ -528,6 +528,9 @@ def main():
     src = {"p2p": "p2p.cu", "m2l": "m2l_tc.cu" if tc else "m2l.cu"}
 
     def traffic(k):
+        # the capture is of the 10^6-dipole ferrofluid: other workloads have none
+        if getattr(args, "workload", "ferrofluid") != "ferrofluid" or args.n != 1_000_000:
+            return None
         tr = NCU_TRAFFIC.get(k)
         return tr["bytes"] if tr and tr.get("src") == _src_hash(src[k]) else None
 

@@ -93,27 +93,35 @@ __global__ void __launch_bounds__(256) k_bbox_final(const double *partial, int n
 }
 
 // split sequence: at every level halve the currently widest axis, ties x<y<z
+// Box, split sequence and cell sizes of every level.  One thread; the
+// running widths and split counts stay in registers (the stores to g are
+// never read back here, so no step waits on a global-memory round trip).
 __global__ void k_geom(const double *box6, Geom *g)
 {
     if (threadIdx.x != 0) return;
+    double ext[3], w[3];
+    int ns[3] = {0, 0, 0};
     for (int a = 0; a < 3; ++a) {
+        ext[a] = box6[3 + a] - box6[a];
+        w[a] = ext[a];
         g->lo[a] = box6[a];
-        g->ext[a] = box6[3 + a] - box6[a];
+        g->ext[a] = ext[a];
         g->nsplit[0][a] = 0;
-        g->w[0][a] = g->ext[a];
+        g->w[0][a] = w[a];
     }
     g->axis[0] = -1;
+    g->h[0] = 0.5 * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     for (int l = 1; l <= LCAP; ++l) {
-        const double *w = g->w[l - 1];
         int a = 0;
         if (w[1] > w[a]) a = 1;
         if (w[2] > w[a]) a = 2;
         g->axis[l] = a;
-        for (int b = 0; b < 3; ++b) g->nsplit[l][b] = g->nsplit[l - 1][b] + (b == a);
-        for (int b = 0; b < 3; ++b) g->w[l][b] = ldexp(g->ext[b], -g->nsplit[l][b]);
-    }
-    for (int l = 0; l <= LCAP; ++l) {
-        const double *w = g->w[l];
+        ns[a] += 1;
+        for (int b = 0; b < 3; ++b) {
+            w[b] = ldexp(ext[b], -ns[b]);
+            g->nsplit[l][b] = ns[b];
+            g->w[l][b] = w[b];
+        }
         g->h[l] = 0.5 * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     }
     g->L = -1;
