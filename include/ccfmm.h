@@ -441,6 +441,108 @@ int64_t ccfmm_kernel_launches(void);
 /* Eq. so: rule-of-thumb leaf occupancy for order p (8 for p <= 3, else 0.74 p^2). */
 double ccfmm_leaf_size_rule(int p);
 
+/* ------------------------------------------------------------------------
+ * Adaptive-depth tree (a project addition: the paper's tree is complete,
+ * every leaf at one depth, Sec. II).  The complete tree's box, split
+ * sequence (halve the widest axis, ties x < y < z) and point membership, but
+ * a cell splits only while it holds more than s dipoles (to level 40 at
+ * most) and empty children are not created.  Cells A and B of different
+ * levels are near when (r_A + r_B) / d > theta, r = half the cell diagonal,
+ * d = distance of the centres; for equal levels this is the paper's
+ * 2r/d > alpha_m (Sec. II).  The interaction lists extend the Appendix's
+ * createPartners to unequal levels: a child takes as near candidates the
+ * children of the internal cells of its parent's near set and that set's
+ * leaves as they are; far candidates are its Partners (M2L sources, any
+ * level); at a leaf, near leaves are nearPartners (Eq. H2) and a near
+ * internal cell is refined against the leaf (far descendants -> Partners,
+ * near leaves -> nearPartners).  The expansions are those of Sec. III
+ * (P2M Eq. multipolemoments, M2M Eq. momentshift, M2L Eq. taylorcalc at any
+ * pair of levels, L2L Eq. taylorshift, L2P Eq. H).
+ *
+ * Several independent samples may share one handle (an ensemble): each gets
+ * its own box and tree; one evaluation covers all of them.
+ *   positions, moments  concatenated samples, total x 3 float64, host or
+ *                       device; sample i is rows offsets[i] .. offsets[i+1].
+ *   offsets             nsamples + 1 host int64, offsets[0] = 0, strictly
+ *                       increasing (every sample holds a dipole).
+ *   p                   1 .. 8; theta in (0, 1).
+ *   split               nsamples thresholds s >= 1 (host), or NULL for
+ *                       Eq. so: s = 0.74 p^2 (p > 3), else 8.
+ *   box                 NULL (bounding box widened by 2^-20 of its largest
+ *                       extent) or, for one sample only, 6 host doubles
+ *                       (lo, hi); points outside are clamped to it.
+ *   prec                CCFMM_FP64: every stage in FP64 with FP64 atomic
+ *                       M2L accumulation; CCFMM_MIXED: FP32 P2M/M2M/M2L/P2P
+ *                       with FP64 D tensors, M2L accumulated in FP32 per
+ *                       cell and L2L in FP64.
+ * Creation builds the trees, lists and D tensors on the handle's stream and
+ * synchronises it.  M2L contributions are added with atomics, so results
+ * may vary in the last bits from run to run.  Errors: CCFMM_ERR_ARG (bad
+ * arguments, non-finite positions, a tree deeper or a box more elongated
+ * than the 40-level keys and 30-bit cell coordinates allow, lists beyond
+ * 2^31 entries), CCFMM_ERR_ALLOC, CCFMM_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct ccfmm_adaptive_s *ccfmm_adaptive_t;
+
+typedef struct {
+    int64_t n;                /* dipoles over all samples */
+    int32_t nsamples, p;
+    double theta;
+    int64_t ncells, nleaves;  /* over all samples */
+    int32_t max_level, pad;
+    int64_t far_pairs;        /* (cell, Partner) pairs */
+    int64_t near_entries;     /* (leaf, nearPartner) pairs, the leaf itself included */
+    int64_t near_pairs;       /* dipole pairs of the near field, sum n_leaf n_partner */
+    int64_t d_rows;           /* distinct separations (one D tensor each) */
+    int64_t m2l_items;        /* M2L work items */
+    int64_t kernels_per_eval; /* kernels of one evaluation */
+    double ms_build;          /* wall time of the build */
+} ccfmm_adaptive_stats;
+
+ccfmm_status fmm_adaptive_create(const double *positions, const double *moments,
+                                 const int64_t *offsets, int nsamples, int p, double theta,
+                                 const double *split, const double *box, ccfmm_prec prec,
+                                 void *stream, ccfmm_adaptive_t *out);
+
+/* Field at every dipole and the energy of every sample for the current
+ * moments (one CUDA graph launch; synchronises).
+ *   H_out  total x 3 float64 in input order (host, device or NULL).
+ *   E_out  nsamples float64, E = -1/2 sum m.H per sample (host, device or
+ *          NULL). */
+ccfmm_status fmm_adaptive_evaluate(ccfmm_adaptive_t a, double *H_out, double *E_out);
+
+/* The ensemble time step of fmm_batch_step (the same Philox4x64-10 rotation
+ * of every moment, key (seed, step), counter (row, 0, 0, 0)), then an
+ * evaluation. */
+ccfmm_status fmm_adaptive_step(ccfmm_adaptive_t a, uint64_t seed, uint64_t step,
+                               double max_angle, double *H_out, double *E_out);
+
+ccfmm_status fmm_adaptive_set_moments(ccfmm_adaptive_t a, const double *moments);
+ccfmm_status fmm_adaptive_get_moments(ccfmm_adaptive_t a, double *out);
+ccfmm_status fmm_adaptive_info(ccfmm_adaptive_t a, ccfmm_adaptive_stats *out);
+
+/* Cells in creation order (each sample's root, then depth first, lower
+ * child first), 8 int64 per cell: level, parent, child0, child1 (-1 when
+ * absent), first sorted dipole, dipole count, leaf flag, sample. */
+ccfmm_status fmm_adaptive_cells(ccfmm_adaptive_t a, int64_t *out);
+
+/* Sorted dipole order: out[i] = input row of the i-th sorted dipole (the
+ * dipoles of a cell are rows first .. first + count - 1 of it). */
+ccfmm_status fmm_adaptive_perm(ccfmm_adaptive_t a, int64_t *out);
+
+/* Interaction pairs (cell, partner) as cell numbers: kind 0 nearPartners of
+ * the leaves, kind 1 Partners (far).  *count receives the number; out
+ * (2 x count int64, host) may be NULL to query it; capacity in pairs. */
+ccfmm_status fmm_adaptive_pairs(ccfmm_adaptive_t a, int kind, int64_t *out, int64_t capacity,
+                                int64_t *count);
+
+/* Multipole moments Q and Taylor coefficients V of every cell after an
+ * evaluation, ncells x (T(p) - 1) float64 each in the library's
+ * multi-index order (host; either may be NULL). */
+ccfmm_status fmm_adaptive_expansions(ccfmm_adaptive_t a, double *Q_out, double *V_out);
+
+void fmm_adaptive_destroy(ccfmm_adaptive_t a);
+
 #ifdef __cplusplus
 }
 #endif

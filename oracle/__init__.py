@@ -96,6 +96,10 @@ def _bind(path):
         "orc_afmm_cell": (None, [ctypes.c_void_p, _i64, _lp]),
         "orc_afmm_perm": (None, [ctypes.c_void_p, _lp]),
         "orc_afmm_pairs": (_i64, [ctypes.c_void_p, ctypes.c_int, _lp]),
+        "orc_afmm_moments": (None, [ctypes.c_void_p, _dp]),
+        "orc_afmm_locals": (None, [ctypes.c_void_p, _dp]),
+        "orc_afmm_box": (None, [ctypes.c_void_p, _dp]),
+        "orc_afmm_widths": (None, [ctypes.c_void_p, _dp]),
         "orc_philox4x64": (None, [_u64p, _u64p, _u64p]),
         "orc_rotate_moments": (None, [_i64, _dp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
                                       _i64]),
@@ -462,6 +466,29 @@ class OracleAFMM:
     def perm(self) -> np.ndarray:
         out = np.zeros(self.n, dtype=np.int64)
         self._lib.orc_afmm_perm(self._h, out.ctypes.data_as(_lp))
+        return out
+
+    def moments(self) -> np.ndarray:
+        """Q of every cell (ncells x T(p), oracle multi-index order), after run()."""
+        out = np.zeros((self._lib.orc_afmm_ncells(self._h), nterms(self.p)))
+        self._lib.orc_afmm_moments(self._h, _d(out))
+        return out
+
+    def locals(self) -> np.ndarray:
+        """V of every cell (ncells x T(p), oracle multi-index order), after run()."""
+        out = np.zeros((self._lib.orc_afmm_ncells(self._h), nterms(self.p)))
+        self._lib.orc_afmm_locals(self._h, _d(out))
+        return out
+
+    def box(self) -> np.ndarray:
+        out = np.zeros(6)
+        self._lib.orc_afmm_box(self._h, _d(out))
+        return out
+
+    def widths(self) -> np.ndarray:
+        """Cell widths of every level 0..40 (41 x 3)."""
+        out = np.zeros((41, 3))
+        self._lib.orc_afmm_widths(self._h, _d(out))
         return out
 
     def pairs(self, kind: str) -> np.ndarray:

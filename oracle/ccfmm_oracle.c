@@ -1376,6 +1376,32 @@ double orc_afmm_energy(const orc_afmm *f)
 
 i64 orc_afmm_ncells(const orc_afmm *f) { return f->nc; }
 
+/* multipole moments Q and Taylor coefficients V of every cell (nc x T(p),
+ * the oracle's multi-index order), after orc_afmm_run */
+void orc_afmm_moments(const orc_afmm *f, double *out)
+{
+    memcpy(out, f->Q, sizeof(double) * (size_t)f->nc * orc_nterms(f->p));
+}
+
+void orc_afmm_locals(const orc_afmm *f, double *out)
+{
+    memcpy(out, f->V, sizeof(double) * (size_t)f->nc * orc_nterms(f->p));
+}
+
+/* the box (lo, hi) and the level widths w[l][a], l = 0 .. ORC_MAXL */
+void orc_afmm_box(const orc_afmm *f, double out[6])
+{
+    for (int a = 0; a < 3; ++a) {
+        out[a] = f->lo[a];
+        out[3 + a] = f->lo[a] + f->ext[a];
+    }
+}
+
+void orc_afmm_widths(const orc_afmm *f, double *out)
+{
+    for (int l = 0; l <= ORC_MAXL; ++l) a_widths(f, l, &out[3 * l]);
+}
+
 /* level, parent, child0, child1, first point, point count, leaf flag */
 void orc_afmm_cell(const orc_afmm *f, i64 c, i64 out[7])
 {

@@ -46,6 +46,16 @@ class Stats(ctypes.Structure):
         return d
 
 
+class AdaptiveStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nsamples", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("theta", ctypes.c_double), ("ncells", ctypes.c_int64),
+                ("nleaves", ctypes.c_int64), ("max_level", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("far_pairs", ctypes.c_int64),
+                ("near_entries", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
+                ("d_rows", ctypes.c_int64), ("m2l_items", ctypes.c_int64),
+                ("kernels_per_eval", ctypes.c_int64), ("ms_build", ctypes.c_double)]
+
+
 class CCFMMError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("libccfmm status %d: %s" % (status, msg))
@@ -115,6 +125,18 @@ def load():
                                           ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
             "fmm_lattice_field": (_int, [_vp, _vp, _vp, _vp]),
             "fmm_lattice_destroy": (None, [_vp]),
+            "fmm_adaptive_create": (_int, [_vp, _vp, _vp, _int, _int, _dbl, _vp, _vp, _int, _vp,
+                                           ctypes.POINTER(_vp)]),
+            "fmm_adaptive_evaluate": (_int, [_vp, _vp, _vp]),
+            "fmm_adaptive_step": (_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, _dbl, _vp, _vp]),
+            "fmm_adaptive_set_moments": (_int, [_vp, _vp]),
+            "fmm_adaptive_get_moments": (_int, [_vp, _vp]),
+            "fmm_adaptive_info": (_int, [_vp, ctypes.POINTER(AdaptiveStats)]),
+            "fmm_adaptive_cells": (_int, [_vp, _vp]),
+            "fmm_adaptive_perm": (_int, [_vp, _vp]),
+            "fmm_adaptive_pairs": (_int, [_vp, _int, _vp, _i64, ctypes.POINTER(_i64)]),
+            "fmm_adaptive_expansions": (_int, [_vp, _vp, _vp]),
+            "fmm_adaptive_destroy": (None, [_vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -548,3 +570,121 @@ class Lattice:
 
     def __del__(self):
         self.close()
+
+
+class Adaptive:
+    """Adaptive-depth tree (fmm_adaptive_*): one system, or an ensemble of
+    independent samples (``offsets``) evaluated together."""
+
+    def __init__(self, positions, moments, p, theta, split=None, offsets=None, box=None,
+                 precision="mixed", stream=None):
+        lib = load()
+        self._lib = lib
+        if offsets is None:
+            n = int(np.asarray(positions).size // 3) if not hasattr(positions, "numel") \
+                else int(positions.numel() // 3)
+            offsets = [0, n]
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.offsets = off
+        self.ns = len(off) - 1
+        self.n = int(off[-1])
+        pp, k1 = _ptr(positions, 3 * self.n)
+        pm, k2 = _ptr(moments, 3 * self.n)
+        sp = None
+        if split is not None:
+            sa = np.ascontiguousarray(np.broadcast_to(np.asarray(split, np.float64), (self.ns,)))
+            self._split = sa
+            sp = _vp(sa.ctypes.data)
+        bp = None
+        if box is not None:
+            self._box = np.ascontiguousarray(np.asarray(box, np.float64).reshape(6))
+            bp = _vp(self._box.ctypes.data)
+        prec = {"mixed": MIXED, "fp32": MIXED, "fp64": FP64}[precision]
+        self.p = int(p)
+        h = _vp()
+        _check(lib.fmm_adaptive_create(pp, pm, _vp(off.ctypes.data), self.ns, int(p),
+                                       float(theta), sp, bp, prec, _stream_ptr(stream),
+                                       ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fmm_adaptive_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _outs(self, H_out, E_out):
+        if H_out is None:
+            H_out = np.zeros((self.n, 3))
+        if E_out is None:
+            E_out = np.zeros(self.ns)
+        ph, k1 = _ptr(H_out, 3 * self.n)
+        pe, k2 = _ptr(E_out, self.ns)
+        return H_out, E_out, ph, pe, (k1, k2)
+
+    def evaluate(self, H_out=None, E_out=None):
+        """(H, E): fields in input order and the energy of every sample."""
+        H_out, E_out, ph, pe, keep = self._outs(H_out, E_out)
+        _check(self._lib.fmm_adaptive_evaluate(self._h, ph, pe))
+        return H_out, E_out
+
+    def step(self, seed, step, max_angle, H_out=None, E_out=None):
+        """Rotate every moment (Philox(seed, step)) and evaluate."""
+        H_out, E_out, ph, pe, keep = self._outs(H_out, E_out)
+        _check(self._lib.fmm_adaptive_step(self._h, int(seed), int(step), float(max_angle), ph, pe))
+        return H_out, E_out
+
+    def set_moments(self, moments):
+        pm, k = _ptr(moments, 3 * self.n)
+        _check(self._lib.fmm_adaptive_set_moments(self._h, pm))
+
+    def moments(self):
+        out = np.zeros((self.n, 3))
+        _check(self._lib.fmm_adaptive_get_moments(self._h, _vp(out.ctypes.data)))
+        return out
+
+    def stats(self) -> dict:
+        st = AdaptiveStats()
+        _check(self._lib.fmm_adaptive_info(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in AdaptiveStats._fields_ if k != "pad"}
+
+    def cells(self) -> np.ndarray:
+        """ncells x 8: level, parent, child0, child1, first, count, leaf, sample."""
+        out = np.zeros((self.stats()["ncells"], 8), np.int64)
+        _check(self._lib.fmm_adaptive_cells(self._h, _vp(out.ctypes.data)))
+        return out
+
+    def perm(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int64)
+        _check(self._lib.fmm_adaptive_perm(self._h, _vp(out.ctypes.data)))
+        return out
+
+    def pairs(self, kind: str) -> np.ndarray:
+        """(cell, partner) pairs: kind "near" or "far"."""
+        k = {"near": 0, "far": 1}[kind]
+        cnt = _i64()
+        _check(self._lib.fmm_adaptive_pairs(self._h, k, None, 0, ctypes.byref(cnt)))
+        out = np.zeros((max(cnt.value, 1), 2), np.int64)
+        _check(self._lib.fmm_adaptive_pairs(self._h, k, _vp(out.ctypes.data), cnt.value,
+                                            ctypes.byref(cnt)))
+        return out[:cnt.value]
+
+    def expansions(self):
+        """(Q, V): ncells x (T(p) - 1) each, library multi-index order."""
+        nc = self.stats()["ncells"]
+        K = (self.p + 1) * (self.p + 2) * (self.p + 3) // 6 - 1
+        Q = np.zeros((nc, K))
+        V = np.zeros((nc, K))
+        _check(self._lib.fmm_adaptive_expansions(self._h, _vp(Q.ctypes.data), _vp(V.ctypes.data)))
+        return Q, V

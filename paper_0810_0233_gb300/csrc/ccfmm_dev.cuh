@@ -377,6 +377,26 @@ void launch_finish_batch(const FinishArgs *a, const int *bstart, int nm, int nbl
 int l2p_blocks(int L);
 void launch_l2p_batch(int p, const P2PArgs *a, const int *bstart, int nm, int nblocks,
                       cudaStream_t s);
+// ------------------------------------------------ adaptive-depth tree
+// P2M of every leaf cell (any level) about its centre
+template <typename real>
+void launch_ap2m(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
+                 const typename vec4<real>::t *A, const typename vec2<real>::t *B, real *Q,
+                 cudaStream_t s);
+// M2L grouped by D row: items (first pair, count <= ap, D row) over the
+// sorted pair arrays pt/ps; accumulates into VF with atomics (ap = 16 or 64)
+template <typename real>
+void launch_am2l(int p, int KP, const int4 *items, int nitems, int ap, const int *pt,
+                 const int *ps, const double4 *sep, const real *D, int ldD, const uint16_t *it,
+                 int maxdeg, const real *Q, real *VF, cudaStream_t s);
+// near field + smooth field of every leaf cell
+template <typename real>
+void launch_ap2p(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
+                 const int *near_first, const int *near_num, const int *near_src,
+                 const double4 *cen, const typename vec4<real>::t *A,
+                 const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
+                 cudaStream_t s);
+
 // the M2M and L2L rounds of a tree of depth L: (l0, D) per round
 int m2m_rounds(int L, int *l0, int *D);
 int l2l_rounds(int L, int *l0, int *D);

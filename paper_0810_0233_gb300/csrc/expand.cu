@@ -214,10 +214,14 @@ void launch_itable(int p, int KP, int maxdeg, uint16_t *it, cudaStream_t s)
 constexpr int P2M_W = 4;
 constexpr int P2M_R = (nterms(PMAX) - 1 + 31) / 32;  // coefficient rounds per lane
 
+// P2M of the dipoles s0..s1 (coordinates relative to the leaf centre) into
+// Qrow[0..KP) by warp w of the block; every thread of the block calls it
+// (the multi-index table is filled block-wide), live = false for warps
+// without a leaf.
 template <typename real>
-__device__ __forceinline__ void p2m_body(int p, int KP, int L, const int *leaf_start,
-                                         const typename vec4<real>::t *A,
-                                         const typename vec2<real>::t *B, real *Q, long long blk)
+__device__ __forceinline__ void p2m_run(int p, int KP, bool live, int s0, int s1,
+                                        const typename vec4<real>::t *A,
+                                        const typename vec2<real>::t *B, real *Qrow)
 {
     __shared__ real pw[P2M_W][32][3][PMAX];
     __shared__ real mm[P2M_W][32][3];
@@ -227,10 +231,8 @@ __device__ __forceinline__ void p2m_body(int p, int KP, int L, const int *leaf_s
     const int K = nterms(p) - 1;
     fill_mi(mi, K);
     __syncthreads();
+    if (!live) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long key = blk * P2M_W + w;
-    if (key >= (1ll << L)) return;
-    const int s0 = leaf_start[key], s1 = leaf_start[key + 1];
     real acc[P2M_R];
 #pragma unroll
     for (int r = 0; r < P2M_R; ++r) acc[r] = (real)0;
@@ -275,12 +277,24 @@ __device__ __forceinline__ void p2m_body(int p, int KP, int L, const int *leaf_s
             }
         }
     }
-    const long long hid = (1ll << L) + key;
 #pragma unroll
     for (int r = 0; r < P2M_R; ++r) {
         const int c = lane + 32 * r;
-        if (c < KP) Q[hid * KP + c] = c < K ? acc[r] : (real)0;
+        if (c < KP) Qrow[c] = c < K ? acc[r] : (real)0;
     }
+}
+
+template <typename real>
+__device__ __forceinline__ void p2m_body(int p, int KP, int L, const int *leaf_start,
+                                         const typename vec4<real>::t *A,
+                                         const typename vec2<real>::t *B, real *Q, long long blk)
+{
+    const int w = threadIdx.x >> 5;
+    const long long key = blk * P2M_W + w;
+    const bool live = key < (1ll << L);
+    const int s0 = live ? leaf_start[key] : 0, s1 = live ? leaf_start[key + 1] : 0;
+    const long long hid = (1ll << L) + key;
+    p2m_run<real>(p, KP, live, s0, s1, A, B, live ? Q + hid * KP : Q);
 }
 
 template <typename real>
@@ -316,6 +330,32 @@ void launch_p2m(int p, int KP, int L, const int *leaf_start, const typename vec4
     note_launch();
     k_p2m<real><<<(unsigned)((nleaf + P2M_W - 1) / P2M_W), 32 * P2M_W, 0, s>>>(p, KP, L,
                                                                              leaf_start, A, B, Q);
+}
+
+// P2M of the adaptive-depth tree: one warp per leaf cell (any level), the
+// dipoles' coordinates relative to that leaf's centre.
+template <typename real>
+__global__ void __launch_bounds__(32 * P2M_W) k_ap2m(int p, int KP, int nleaf, const int *leaves,
+                                                     const int *p0, const int *np,
+                                                     const typename vec4<real>::t *A,
+                                                     const typename vec2<real>::t *B, real *Q)
+{
+    const long long li = (long long)blockIdx.x * P2M_W + (threadIdx.x >> 5);
+    const bool live = li < nleaf;
+    const int c = live ? leaves[li] : 0;
+    const int s0 = live ? p0[c] : 0, s1 = live ? s0 + np[c] : 0;
+    p2m_run<real>(p, KP, live, s0, s1, A, B, Q + (long long)c * KP);
+}
+
+template <typename real>
+void launch_ap2m(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
+                 const typename vec4<real>::t *A, const typename vec2<real>::t *B, real *Q,
+                 cudaStream_t s)
+{
+    if (nleaf <= 0) return;
+    note_launch();
+    k_ap2m<real><<<(unsigned)((nleaf + P2M_W - 1) / P2M_W), 32 * P2M_W, 0, s>>>(p, KP, nleaf, leaves,
+                                                                              p0, np, A, B, Q);
 }
 
 // ---------------------------------------------------------------------------
@@ -541,6 +581,9 @@ void launch_l2l_batch(const L2LArgs *a, const int *bstart, int nm, int nblocks, 
     template void launch_p2m<real>(int, int, int, const int *, const vec4<real>::t *,           \
                                    const vec2<real>::t *, real *, cudaStream_t);                \
     template void launch_m2m_all<real>(int, int, int, const Geom *, real *, cudaStream_t);      \
+    template void launch_ap2m<real>(int, int, int, const int *, const int *, const int *,       \
+                                    const vec4<real>::t *, const vec2<real>::t *, real *,       \
+                                    cudaStream_t);                                              \
 
 INST(float)
 INST(double)

@@ -403,6 +403,208 @@ void launch_m2l(int p, int KP, const Tile *tiles, int ntiles, const int *ent_u,
     }
 }
 
+// ---------------------------------------------------------------------------
+// M2L of the adaptive-depth tree, grouped by derivative tensor.  The far
+// pairs (target cell, source cell) are sorted so that pairs with the same
+// separation c = target centre - source centre (one D row) are contiguous;
+// a work item is a run of pairs of one such group, (first pair, count, D
+// row).  Per item the block forms M[k][n] = D~_{n+k} (once, when the
+// coefficient columns fit one chunk) and then, for AP pairs at a time,
+//     acc[pair][n] = sum_k M[k][n] Qs[k][pair],   Qs[k] = rho^-|k| Q_k(source),
+// with D~ = D(c / rho), rho = |c| (the D row is computed at the unit vector,
+// so every operand is O(1) for any pair of levels); the epilogue applies
+// (-1)^|n| rho^-(|n|+1) and adds the result to the target's accumulator VF
+// with vector atomics (FP32) or FP64 atomics: the order of the additions
+// into one target is not fixed.  The powers of 1/rho are formed once per
+// item by repeated multiplication (FP64, then rounded for FP32 operands).
+// Thread layout: pair group pg (4 pairs) x column group ng (8 columns), so
+// each thread keeps a 4 x 8 accumulator tile; columns are consumed in chunks
+// of KC.
+// ---------------------------------------------------------------------------
+template <typename real> __device__ __forceinline__ void vf_add8(real *dst, const real (&o)[8]);
+template <> __device__ __forceinline__ void vf_add8<float>(float *dst, const float (&o)[8])
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(o[0]), "f"(o[1]),
+                 "f"(o[2]), "f"(o[3])
+                 : "memory");
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4), "f"(o[4]),
+                 "f"(o[5]), "f"(o[6]), "f"(o[7])
+                 : "memory");
+}
+template <> __device__ __forceinline__ void vf_add8<double>(double *dst, const double (&o)[8])
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j) atomicAdd(dst + j, o[j]);
+}
+
+template <typename real, int AP> struct am2l_shape {
+    static constexpr int QSTR = AP + (sizeof(real) == 4 ? 4 : 2);  // Qs row stride
+};
+
+template <typename real, int KP, int AP, int KC>
+__global__ void __launch_bounds__(((KP / 8) * (AP / 4) + 31) / 32 * 32)
+    k_am2l(int p, const int4 *items, const int *pt, const int *ps, const double4 *sep,
+           const real *D, int ldD, const uint16_t *it, int maxdeg, const real *Q, real *VF)
+{
+    constexpr int NG = KP / 8, PG = AP / 4, NT = NG * PG;
+    constexpr int QSTR = am2l_shape<real, AP>::QSTR;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    real *Ms = reinterpret_cast<real *>(smraw);  // [KC][KP]
+    real *Qs = Ms + KC * KP;                     // [KC][QSTR]
+    real *Dl = Qs + KC * QSTR;                   // [ldD]
+    real *gk = Dl + ldD;                         // [KP] rho^-|k|
+    real *en = gk + KP;                          // [KP] (-1)^|n| rho^-(|n|+1)
+    real *pw = en + KP;                          // [PMAX + 4] rho^-d
+    int *tg = reinterpret_cast<int *>(pw + PMAX + 4);  // [AP]
+    int *sr = tg + AP;                                 // [AP]
+
+    const int4 item = items[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int K = nterms(p) - 1;
+    if (tid == 0) {
+        const double ri = 1.0 / sep[item.z].w;
+        double v = 1.0;
+        for (int d = 0; d <= p + 1; ++d) {
+            pw[d] = (real)v;
+            v *= ri;
+        }
+    }
+    const real *Drow = D + (long long)item.z * ldD;
+    for (int i = tid; i < ldD; i += blockDim.x) Dl[i] = Drow[i];
+    __syncthreads();
+    for (int c = tid; c < KP; c += blockDim.x) {
+        real gv = (real)0, ev = (real)0;
+        if (c < K) {
+            int d = 1;
+            while (nterms(d) <= c + 1) ++d;  // degree of multi-index c + 1
+            gv = pw[d];
+            ev = (d & 1) ? -pw[d + 1] : pw[d + 1];
+        }
+        gk[c] = gv;
+        en[c] = ev;
+    }
+    const int pg = tid % PG, ng = tid / PG;
+    const bool act = tid < NT;
+    const int kend = act ? m2l_kend(p, maxdeg, 8 * ng) : 0;
+    constexpr bool ONE = KC >= KP;  // M built once per item
+    if (ONE) {
+        for (int idx = tid; idx < KP * KP; idx += blockDim.x) Ms[idx] = Dl[it[idx]];
+    }
+    for (int c0 = 0; c0 < item.y; c0 += AP) {
+        const int cnt = min(AP, item.y - c0);
+        __syncthreads();  // scale tables and M ready; the previous chunk's reads done
+        for (int i = tid; i < AP; i += blockDim.x) {
+            const bool v = i < cnt;
+            tg[i] = v ? pt[item.x + c0 + i] : -1;
+            sr[i] = v ? ps[item.x + c0 + i] : -1;
+        }
+        __syncthreads();
+        real acc[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = (real)0;
+        for (int k0 = 0; k0 < KP; k0 += KC) {
+            if (k0) __syncthreads();
+            // moments of the chunk's sources, a row per pair read along k
+            for (int idx = tid; idx < KC * AP; idx += blockDim.x) {
+                const int i = idx / KC, kk = idx - i * KC, col = k0 + kk;
+                const int sidx = sr[i];
+                real v = (real)0;
+                if (sidx >= 0 && col < K) v = Q[(long long)sidx * KP + col] * gk[col];
+                Qs[kk * QSTR + i] = v;
+            }
+            if (!ONE)
+                for (int idx = tid; idx < KC * KP; idx += blockDim.x) {
+                    const int kk = idx / KP, n = idx - kk * KP;
+                    Ms[idx] = (k0 + kk < KP) ? Dl[it[(k0 + kk) * KP + n]] : (real)0;
+                }
+            __syncthreads();
+            if (act) {
+                const int kc = min(KC, kend - k0);
+                const real *Mk = ONE ? Ms + k0 * KP : Ms;
+#pragma unroll 4
+                for (int kk = 0; kk < kc; ++kk) {
+                    real q[4], m0[4], m1[4];
+                    v4<real>::ld(Qs + kk * QSTR + 4 * pg, q);
+                    v4<real>::ld(Mk + kk * KP + 8 * ng, m0);
+                    v4<real>::ld(Mk + kk * KP + 8 * ng + 4, m1);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            acc[i][j] += q[i] * m0[j];
+                            acc[i][4 + j] += q[i] * m1[j];
+                        }
+                    }
+                }
+            }
+        }
+        if (act) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int t = tg[4 * pg + i];
+                if (t < 0) continue;
+                real o[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) o[j] = acc[i][j] * en[8 * ng + j];
+                vf_add8<real>(VF + (long long)t * KP + 8 * ng, o);
+            }
+        }
+    }
+}
+
+template <typename real, int KP, int AP, int KC>
+static void run_am2l(int p, const int4 *items, int nitems, const int *pt, const int *ps,
+                     const double4 *sep, const real *D, int ldD, const uint16_t *it, int maxdeg,
+                     const real *Q, real *VF, cudaStream_t s)
+{
+    constexpr int NT = ((KP / 8) * (AP / 4) + 31) / 32 * 32;
+    const size_t smem = sizeof(real) * ((size_t)KC * KP + (size_t)KC * am2l_shape<real, AP>::QSTR +
+                                        ldD + 2 * KP + PMAX + 4) +
+                        sizeof(int) * 2 * AP + 64;
+    auto kern = k_am2l<real, KP, AP, KC>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
+    kern<<<(unsigned)nitems, NT, smem, s>>>(p, items, pt, ps, sep, D, ldD, it, maxdeg, Q, VF);
+}
+
+template <typename real, int AP>
+static void am2l_dispatch(int p, int KP, const int4 *items, int nitems, const int *pt,
+                          const int *ps, const double4 *sep, const real *D, int ldD,
+                          const uint16_t *it, int maxdeg, const real *Q, real *VF, cudaStream_t s)
+{
+#define AM2L(KPV, KCV)                                                                           \
+    case KPV:                                                                                    \
+        run_am2l<real, KPV, AP, KCV>(p, items, nitems, pt, ps, sep, D, ldD, it, maxdeg, Q, VF, s); \
+        break;
+    switch (KP) {
+        AM2L(8, 8) AM2L(16, 16) AM2L(24, 24) AM2L(40, 40) AM2L(56, 56) AM2L(88, 88)
+        AM2L(120, 40) AM2L(168, 56)
+    default: break;
+    }
+#undef AM2L
+}
+
+template <typename real>
+void launch_am2l(int p, int KP, const int4 *items, int nitems, int ap, const int *pt,
+                 const int *ps, const double4 *sep, const real *D, int ldD, const uint16_t *it,
+                 int maxdeg, const real *Q, real *VF, cudaStream_t s)
+{
+    if (nitems <= 0) return;
+    if (ap == 64)
+        am2l_dispatch<real, 64>(p, KP, items, nitems, pt, ps, sep, D, ldD, it, maxdeg, Q, VF, s);
+    else
+        am2l_dispatch<real, 16>(p, KP, items, nitems, pt, ps, sep, D, ldD, it, maxdeg, Q, VF, s);
+}
+
+template void launch_am2l<float>(int, int, const int4 *, int, int, const int *, const int *,
+                                 const double4 *, const float *, int, const uint16_t *, int,
+                                 const float *, float *, cudaStream_t);
+template void launch_am2l<double>(int, int, const int4 *, int, int, const int *, const int *,
+                                  const double4 *, const double *, int, const uint16_t *, int,
+                                  const double *, double *, cudaStream_t);
+
 template void launch_m2l<float>(int, int, const Tile *, int, const int *, const int *,
                                 const float *, const float *, int, const uint16_t *, int, const Geom *,
                                 double *, cudaStream_t);

@@ -164,12 +164,56 @@ __device__ __forceinline__ Sum3<real> l2p_eval(int p, const real *vs, real x, re
 //  * The leaf's own dipoles are processed first, with the r = 0 test (a
 //    source on the field point contributes nothing, Appendix updateField);
 //    no other leaf can hold a point at the target's position.
+// Near entries of the complete tree: a partner leaf key at the same level
+// and its integer cell offset; the shift is the offset times the leaf widths.
+struct UniEnts {
+    const int *leaf_start;
+    const NearEnt *near;
+    double wx, wy, wz;
+    int self;
+    template <typename R4>
+    __device__ __forceinline__ int get(int e, int &st, R4 &sh) const
+    {
+        NearEnt x = near[e];
+        st = leaf_start[x.src];
+        sh.x = (decltype(sh.x))((double)x.ox * wx);
+        sh.y = (decltype(sh.x))((double)x.oy * wy);
+        sh.z = (decltype(sh.x))((double)x.oz * wz);
+        sh.w = (decltype(sh.x))0;
+        return (x.src == self) ? 0 : leaf_start[x.src + 1] - st;
+    }
+};
+
+template <typename real, typename Ents>
+__device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, const Ents &ents,
+                                         const double *Vrow, const typename vec4<real>::t *A,
+                                         const typename vec2<real>::t *B,
+                                         typename vec4<real>::t *H);
+
 template <typename real>
 __device__ __forceinline__ void p2p_body(int p, int KP, int L, const int *leaf_start,
                                          const int2 *near_nl, const NearEnt *near, const Geom *g,
                                          const typename vec4<real>::t *A,
                                          const typename vec2<real>::t *B, const double *V,
                                          typename vec4<real>::t *H, long long key)
+{
+    const int t0 = leaf_start[key], nt = leaf_start[key + 1] - t0;
+    if (nt == 0) return;
+    const int2 nlk = near_nl[key];  // (first entry, count) of the leaf's near list
+    const long long hid = (1ll << L) + key;
+    UniEnts ents{leaf_start, near, g->w[L][0], g->w[L][1], g->w[L][2], (int)key};
+    // V == nullptr: near field only (L2P by k_l2p once V is complete)
+    p2p_leaf<real>(p, t0, nt, nlk.x, nlk.x + nlk.y, ents, V ? V + hid * KP : nullptr, A, B, H);
+}
+
+// The near field (and, with Vrow, the smooth field) of one leaf's nt dipoles
+// at t0..: its own dipoles first, then the entries e0..e1 of its near list,
+// each giving a source range and the shift (target centre - source centre).
+template <typename real, typename Ents>
+__device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, const Ents &ents,
+                                         const double *Vrow, const typename vec4<real>::t *A,
+                                         const typename vec2<real>::t *B,
+                                         typename vec4<real>::t *H)
 {
     typedef typename vec4<real>::t R4;
     typedef typename vec2<real>::t R2;
@@ -182,18 +226,11 @@ __device__ __forceinline__ void p2p_body(int p, int KP, int L, const int *leaf_s
     real *vs = reinterpret_cast<real *>(epf + P2P_NE + 4);  // [KP]
     __shared__ int wsum[P2P_T / 32];
 
-    const int t0 = leaf_start[key], nt = leaf_start[key + 1] - t0;
-    if (nt == 0) return;
-    const int2 nlk = near_nl[key];  // (first entry, count) of the leaf's near list
-    const int e0 = nlk.x, e1 = nlk.x + nlk.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = nterms(p) - 1;
-    const long long hid = (1ll << L) + key;
-    // V == nullptr: near field only (L2P by k_l2p once V is complete)
-    const bool with_l2p = V != nullptr;
+    const bool with_l2p = Vrow != nullptr;
     if (with_l2p)
-        for (int c = tid; c < K; c += P2P_T) vs[c] = (real)V[hid * KP + c];
-    const double wx = g->w[L][0], wy = g->w[L][1], wz = g->w[L][2];
+        for (int c = tid; c < K; c += P2P_T) vs[c] = (real)Vrow[c];
 
     for (int tb = 0; tb < nt; tb += P2P_TPT * P2P_T) {
         const int ntc = min(nt - tb, P2P_TPT * P2P_T);
@@ -237,15 +274,10 @@ __device__ __forceinline__ void p2p_body(int p, int KP, int L, const int *leaf_s
                 int e = 2 * tid + r;
                 int cnt = 0;
                 if (e < nec) {
-                    NearEnt x = near[ec + e];
-                    int st = leaf_start[x.src];
-                    cnt = (x.src == (int)key) ? 0 : leaf_start[x.src + 1] - st;
-                    est[e] = st;
+                    int st;
                     R4 sh;
-                    sh.x = (real)((double)x.ox * wx);
-                    sh.y = (real)((double)x.oy * wy);
-                    sh.z = (real)((double)x.oz * wz);
-                    sh.w = (real)0;
+                    cnt = ents.get(ec + e, st, sh);
+                    est[e] = st;
                     esh[e] = sh;
                 }
                 if (r == 0) c0 = cnt; else c1 = cnt;
@@ -347,6 +379,67 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
 {
     p2p_body<real>(p, KP, L, leaf_start, near_nl, near, g, A, B, V, H, blockIdx.x);
 }
+
+// Near entries of the adaptive-depth tree: a partner leaf cell of any
+// level; the shift is the difference of the two cells' centres, in FP64.
+struct AdaEnts {
+    const int *p0, *np, *src;
+    const double4 *cen;
+    double cx, cy, cz;
+    int self;
+    template <typename R4>
+    __device__ __forceinline__ int get(int e, int &st, R4 &sh) const
+    {
+        const int b = src[e];
+        const double4 c = cen[b];
+        st = p0[b];
+        sh.x = (decltype(sh.x))(cx - c.x);
+        sh.y = (decltype(sh.x))(cy - c.y);
+        sh.z = (decltype(sh.x))(cz - c.z);
+        sh.w = (decltype(sh.x))0;
+        return b == self ? 0 : np[b];
+    }
+};
+
+// near field + smooth field of the adaptive tree's leaves, one block per leaf
+template <typename real>
+__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+    k_ap2p(int p, int KP, const int *leaves, const int *p0, const int *np, const int *near_first,
+           const int *near_num, const int *near_src, const double4 *cen,
+           const typename vec4<real>::t *A, const typename vec2<real>::t *B, const double *V,
+           typename vec4<real>::t *H)
+{
+    const int c = leaves[blockIdx.x];
+    const double4 cc = cen[c];
+    const AdaEnts ents{p0, np, near_src, cen, cc.x, cc.y, cc.z, c};
+    const int e0 = near_first[c];
+    p2p_leaf<real>(p, p0[c], np[c], e0, e0 + near_num[c], ents, V + (long long)c * KP, A, B, H);
+}
+
+template <typename real>
+void launch_ap2p(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
+                 const int *near_first, const int *near_num, const int *near_src,
+                 const double4 *cen, const typename vec4<real>::t *A,
+                 const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
+                 cudaStream_t s)
+{
+    if (nleaf <= 0) return;
+    const size_t smem = (size_t)P2P_CH * (sizeof(typename vec4<real>::t) + sizeof(typename vec2<real>::t)) +
+                        (size_t)P2P_NE * sizeof(typename vec4<real>::t) + (2 * P2P_NE + 4) * sizeof(int) +
+                        (size_t)KP * sizeof(real) + 64;
+    cudaFuncSetAttribute(k_ap2p<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
+    k_ap2p<real><<<(unsigned)nleaf, P2P_T, smem, s>>>(p, KP, leaves, p0, np, near_first, near_num,
+                                                      near_src, cen, A, B, V, H);
+}
+
+template void launch_ap2p<float>(int, int, int, const int *, const int *, const int *, const int *,
+                                 const int *, const int *, const double4 *, const float4 *,
+                                 const float2 *, const double *, float4 *, cudaStream_t);
+template void launch_ap2p<double>(int, int, int, const int *, const int *, const int *,
+                                  const int *, const int *, const int *, const double4 *,
+                                  const double4 *, const double2 *, const double *, double4 *,
+                                  cudaStream_t);
 
 // every member's leaves in one launch (ensemble step)
 __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)

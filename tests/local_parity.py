@@ -87,3 +87,22 @@ def cell_errors(V, Vref, cells, mi, box, axes):
 def cell_max_err(V, Vref, cells, mi, box, axes):
     e = cell_errors(V, Vref, cells, mi, box, axes)
     return max(e.values()) if e else 0.0
+
+
+def cell_errors_levels(V, Vref, rows, levels, rho, mi):
+    """cell_errors for trees whose cells are not heap-numbered (the adaptive
+    tree): rows are cell numbers, levels their levels, rho[l] the half
+    diagonal of level l; returns {level: max error}."""
+    rows = np.asarray(rows, dtype=np.int64)
+    levels = np.asarray(levels, dtype=np.int64)
+    out = {}
+    for l in np.unique(levels):
+        r = rows[levels == l]
+        w = term_weights(mi, rho[int(l)])
+        ref = Vref[r] * w
+        scale = math.sqrt(float((ref ** 2).sum(1).mean()))
+        if scale == 0.0:
+            continue
+        d = (V[r] - Vref[r]) * w
+        out[int(l)] = float(np.sqrt((d ** 2).sum(1)).max() / scale)
+    return out
