@@ -18,6 +18,9 @@
 // cells 4*lane..4*lane+3, so each thread keeps a 4 x 8 accumulator tile.
 #include "ccfmm_dev.cuh"
 
+#include <stdlib.h>
+#include <string.h>
+
 namespace ccfmm {
 
 template <typename real> struct v4;
@@ -586,12 +589,250 @@ static void am2l_dispatch(int p, int KP, const int4 *items, int nitems, const in
 #undef AM2L
 }
 
+// ---------------------------------------------------------------------------
+// The same contraction on the tensor cores, FP32 path (3xTF32: each operand
+// x = hi + lo with hi = tf32(x), lo = tf32(x - hi); A B ~ Alo Bhi + Ahi Blo +
+// Ahi Bhi with FP32 accumulation).  The operator of an item is built from
+// its D row for 16-row tiles, which the warp-level MMA (mma.sync m16n8k8,
+// TF32) takes directly from registers: a warp owns 16 pairs (rows) x all
+// KP columns, K in steps of 8; its A fragments are the scaled moments of the
+// 16 sources read from global memory, its B fragments M[k][n] = D~_{n+k}.
+//   BIG:   one item per block (groups of more than 16 pairs, items of at
+//          most 512): the block first stores every B fragment of the item's
+//          operator, split, in shared memory (fragment order), then its four
+//          warps take the item's 16-pair chunks in turn.
+//   SMALL: one item per warp (groups of at most 16 pairs): B fragments are
+//          formed from the D row as they are used.
+// Fragment layouts (PTX ISA, mma.m16n8k8 with .tf32): g = lane / 4,
+// t = lane % 4; A: a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4);
+// B: b0 (k = t, n = g), b1 (k = t + 4, n = g); C: c0 (g, 2t), c1 (g, 2t + 1),
+// c2 (g + 8, 2t), c3 (g + 8, 2t + 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
+{
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void red_add2(float *p, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
+// scale tables of one item: pw[d] = rho^-d, gk[c] = rho^-|k|,
+// en[c] = (-1)^|n| rho^-(|n|+1) (zero beyond K); threads tid0.. step nth
+__device__ __forceinline__ void am2l_scales(int p, int KP, double rho, float *pw, float *gk,
+                                            float *en, int tid0, int nth, bool sync_block)
+{
+    if (tid0 == 0) {
+        const double ri = 1.0 / rho;
+        double v = 1.0;
+        for (int d = 0; d <= p + 1; ++d) {
+            pw[d] = (float)v;
+            v *= ri;
+        }
+    }
+    if (sync_block) __syncthreads(); else __syncwarp();
+    const int K = nterms(p) - 1;
+    for (int c = tid0; c < KP; c += nth) {
+        float gv = 0.f, ev = 0.f;
+        if (c < K) {
+            int d = 1;
+            while (nterms(d) <= c + 1) ++d;
+            gv = pw[d];
+            ev = (d & 1) ? -pw[d + 1] : pw[d + 1];
+        }
+        gk[c] = gv;
+        en[c] = ev;
+    }
+}
+
+// 16 pairs (rows) from pair c0 of the item: A from the sources' moments,
+// B from bfrag (BIG, fragment order in shared memory) or from Dl and the
+// index table; the results added to the targets' accumulators
+template <int KP, bool BIG>
+__device__ __forceinline__ void am2l_mma_chunk(const int4 &item, int c0, const int *pt,
+                                               const int *ps, const float *Q, const float *gk,
+                                               const float *en, const float4 *bfrag,
+                                               const float *Dl, const uint16_t *it, float *VF)
+{
+    constexpr int KS = KP / 8;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int r0 = c0 + g, r1 = c0 + g + 8;
+    const bool v0 = r0 < item.y, v1 = r1 < item.y;
+    const float *q0 = Q + (long long)(v0 ? ps[item.x + r0] : 0) * KP;
+    const float *q1 = Q + (long long)(v1 ? ps[item.x + r1] : 0) * KP;
+    float c[KS][4];
+#pragma unroll
+    for (int n = 0; n < KS; ++n) c[n][0] = c[n][1] = c[n][2] = c[n][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+        const int col = 8 * ks + t;
+        const float x0 = v0 ? q0[col] * gk[col] : 0.f;
+        const float x1 = v1 ? q1[col] * gk[col] : 0.f;
+        const float x2 = v0 ? q0[col + 4] * gk[col + 4] : 0.f;
+        const float x3 = v1 ? q1[col + 4] * gk[col + 4] : 0.f;
+        uint32_t ah[4], al[4];
+        tf32_split(x0, ah[0], al[0]);
+        tf32_split(x1, ah[1], al[1]);
+        tf32_split(x2, ah[2], al[2]);
+        tf32_split(x3, ah[3], al[3]);
+#pragma unroll
+        for (int nt = 0; nt < KS; ++nt) {
+            uint32_t bh0, bh1, bl0, bl1;
+            if (BIG) {
+                const float4 b = bfrag[(ks * KS + nt) * 32 + lane];
+                bh0 = __float_as_uint(b.x);
+                bh1 = __float_as_uint(b.y);
+                bl0 = __float_as_uint(b.z);
+                bl1 = __float_as_uint(b.w);
+            } else {
+                const int k = 8 * ks + t, n = 8 * nt + g;
+                tf32_split(Dl[it[k * KP + n]], bh0, bl0);
+                tf32_split(Dl[it[(k + 4) * KP + n]], bh1, bl1);
+            }
+            mma_tf32(c[nt], al, bh0, bh1);
+            mma_tf32(c[nt], ah, bl0, bl1);
+            mma_tf32(c[nt], ah, bh0, bh1);
+        }
+    }
+    const int t0 = v0 ? pt[item.x + r0] : -1, t1 = v1 ? pt[item.x + r1] : -1;
+#pragma unroll
+    for (int nt = 0; nt < KS; ++nt) {
+        const int col = 8 * nt + 2 * t;
+        const float e0 = en[col], e1 = en[col + 1];
+        if (t0 >= 0) red_add2(VF + (long long)t0 * KP + col, c[nt][0] * e0, c[nt][1] * e1);
+        if (t1 >= 0) red_add2(VF + (long long)t1 * KP + col, c[nt][2] * e0, c[nt][3] * e1);
+    }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(128) k_am2l_mma_big(int p, const int4 *items, const int *pt,
+                                                      const int *ps, const double4 *sep,
+                                                      const float *D, int ldD,
+                                                      const uint16_t *it, const float *Q,
+                                                      float *VF)
+{
+    constexpr int KS = KP / 8;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float4 *bfrag = reinterpret_cast<float4 *>(smraw);  // [KS * KS * 32]
+    float *Dl = reinterpret_cast<float *>(bfrag + KS * KS * 32);  // [ldD]
+    float *gk = Dl + ldD, *en = gk + KP, *pw = en + KP;  // [KP], [KP], [PMAX + 4]
+    const int4 item = items[blockIdx.x];
+    const int tid = threadIdx.x;
+    const float *Drow = D + (long long)item.z * ldD;
+    for (int i = tid; i < ldD; i += blockDim.x) Dl[i] = Drow[i];
+    am2l_scales(p, KP, sep[item.z].w, pw, gk, en, tid, blockDim.x, true);
+    for (int idx = tid; idx < KS * KS * 32; idx += blockDim.x) {
+        const int tile = idx >> 5, ln = idx & 31;
+        const int ks = tile / KS, nt = tile - ks * KS;
+        const int k = 8 * ks + (ln & 3), n = 8 * nt + (ln >> 2);
+        uint32_t h0, l0, h1, l1;
+        tf32_split(Dl[it[k * KP + n]], h0, l0);
+        tf32_split(Dl[it[(k + 4) * KP + n]], h1, l1);
+        bfrag[idx] = make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(l0),
+                                 __uint_as_float(l1));
+    }
+    __syncthreads();
+    const int warp = tid >> 5;
+    for (int c0 = 16 * warp; c0 < item.y; c0 += 64)
+        am2l_mma_chunk<KP, true>(item, c0, pt, ps, Q, gk, en, bfrag, Dl, it, VF);
+}
+
+template <int KP>
+__global__ void __launch_bounds__(128) k_am2l_mma_small(int p, const int4 *items, int nitems,
+                                                        const int *pt, const int *ps,
+                                                        const double4 *sep, const float *D,
+                                                        int ldD, const uint16_t *it,
+                                                        const float *Q, float *VF)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per = ((ldD + 2 * KP + PMAX + 4) + 3) & ~3;  // floats per warp
+    float *Dl = reinterpret_cast<float *>(smraw) + warp * per;
+    float *gk = Dl + ldD, *en = gk + KP, *pw = en + KP;
+    const int ii = blockIdx.x * 4 + warp;
+    if (ii >= nitems) return;
+    const int4 item = items[ii];
+    const float *Drow = D + (long long)item.z * ldD;
+    for (int i = lane; i < ldD; i += 32) Dl[i] = Drow[i];
+    am2l_scales(p, KP, sep[item.z].w, pw, gk, en, lane, 32, false);
+    __syncwarp();
+    for (int c0 = 0; c0 < item.y; c0 += 16)
+        am2l_mma_chunk<KP, false>(item, c0, pt, ps, Q, gk, en, nullptr, Dl, it, VF);
+}
+
+template <int KP>
+static void run_am2l_mma(int p, const int4 *items, int nitems, bool big, const int *pt,
+                         const int *ps, const double4 *sep, const float *D, int ldD,
+                         const uint16_t *it, const float *Q, float *VF, cudaStream_t s)
+{
+    constexpr int KS = KP / 8;
+    note_launch();
+    if (big) {
+        const size_t smem = (size_t)KS * KS * 32 * sizeof(float4) +
+                            sizeof(float) * (ldD + 2 * KP + PMAX + 4) + 16;
+        cudaFuncSetAttribute(k_am2l_mma_big<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_am2l_mma_big<KP><<<(unsigned)nitems, 128, smem, s>>>(p, items, pt, ps, sep, D, ldD, it,
+                                                                Q, VF);
+    } else {
+        const int per = ((ldD + 2 * KP + PMAX + 4) + 3) & ~3;
+        const size_t smem = sizeof(float) * 4 * per + 16;
+        cudaFuncSetAttribute(k_am2l_mma_small<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_am2l_mma_small<KP><<<(unsigned)((nitems + 3) / 4), 128, smem, s>>>(
+            p, items, nitems, pt, ps, sep, D, ldD, it, Q, VF);
+    }
+}
+
+// the tensor-core form serves the FP32 path for p <= 6 (the split operator
+// of one item fits shared memory) unless CCFMM_AM2L=fma
+static bool am2l_use_mma(int KP)
+{
+    static int env = -1;
+    if (env < 0) {
+        const char *e = getenv("CCFMM_AM2L");
+        env = (e && strcmp(e, "fma") == 0) ? 0 : 1;
+    }
+    return env == 1 && KP <= 88;
+}
+
 template <typename real>
 void launch_am2l(int p, int KP, const int4 *items, int nitems, int ap, const int *pt,
                  const int *ps, const double4 *sep, const real *D, int ldD, const uint16_t *it,
                  int maxdeg, const real *Q, real *VF, cudaStream_t s)
 {
     if (nitems <= 0) return;
+    if (sizeof(real) == 4 && maxdeg >= 2 * p && am2l_use_mma(KP)) {
+        const float *Df = reinterpret_cast<const float *>(D);
+        const float *Qf = reinterpret_cast<const float *>(Q);
+        float *Vf = reinterpret_cast<float *>(VF);
+        const bool big = ap == 64;
+        switch (KP) {
+        case 8: run_am2l_mma<8>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
+        case 16: run_am2l_mma<16>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
+        case 24: run_am2l_mma<24>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
+        case 40: run_am2l_mma<40>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
+        case 56: run_am2l_mma<56>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
+        case 88: run_am2l_mma<88>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
+        default: break;
+        }
+    }
     if (ap == 64)
         am2l_dispatch<real, 64>(p, KP, items, nitems, pt, ps, sep, D, ldD, it, maxdeg, Q, VF, s);
     else
