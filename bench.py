@@ -209,9 +209,11 @@ def cpu_oracle_sample(pos, mom, p, theta, nleaves=4096, seed=11):
             "seconds": t_setup + t_sample}
 
 
-def oracle_ensemble_sample(pos, mom, off, p, theta, budget_s=15.0, seed=12):
+def oracle_ensemble_sample(pos, mom, off, p, theta, budget_s=15.0, seed=12, tree="adaptive"):
     """The CPU oracle over whole samples of the ensemble, drawn at random
-    until about budget_s seconds of work; fields/s over those samples."""
+    until about budget_s seconds of work; fields/s over those samples.  With
+    the adaptive tree the oracle's adaptive mode runs at s = 2 x Eq. so (the
+    middle of the autotuner's candidates)."""
     import oracle as O
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(off) - 1)
@@ -219,15 +221,19 @@ def oracle_ensemble_sample(pos, mom, off, p, theta, budget_s=15.0, seed=12):
     done = fields = 0
     for i in order:
         sl = slice(int(off[i]), int(off[i + 1]))
-        O.fmm_field(pos[sl], mom[sl], p, theta)
+        if tree == "adaptive":
+            O.afmm_field(pos[sl], mom[sl], p, theta, 2.0 * O.leaf_size_rule(p))
+        else:
+            O.fmm_field(pos[sl], mom[sl], p, theta)
         done += 1
         fields += sl.stop - sl.start
         if time.perf_counter() - t0 > budget_s:
             break
     t = time.perf_counter() - t0
     return {"value": fields / t, "unit": "fields/s", "cores": O.threads(), "kind": "oracle",
-            "sample": "FP64 CPU oracle, full FMM (tree, lists, all passes) of %d random samples "
-                      "of the ensemble, %d fields in %.1f s" % (done, fields, t),
+            "sample": "FP64 CPU oracle (%s tree), full FMM (tree, lists, all passes) of %d "
+                      "random samples of the ensemble, %d fields in %.1f s"
+                      % (tree, done, fields, t),
             "seconds": t}
 
 
@@ -242,10 +248,11 @@ def run_reference(args):
         from paper_0810_0233_gb300 import workloads as W
         pos, mom, off = W.ensemble()
         for it in range(args.warmup + args.steps):
-            res = oracle_ensemble_sample(pos, mom, off, p, theta, budget_s=5.0, seed=100 + it)
+            res = oracle_ensemble_sample(pos, mom, off, p, theta, budget_s=5.0, seed=100 + it,
+                                         tree=args.tree)
             if it >= args.warmup:
                 times.append(len(pos) / res["value"])
-        config = describe_ensemble(len(off) - 1, len(pos), p, theta)
+        config = describe_ensemble(len(off) - 1, len(pos), p, theta, args.tree)
         config["precision"] = "FP64 throughout (the CPU oracle)"
         config["step"] = ("FP64 CPU oracle: whole FMM of random samples for about 5 s per step, "
                           "fields/s over those samples (no rotation)")
@@ -277,15 +284,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def describe_ensemble(ns, total, p, theta):
+def describe_ensemble(ns, total, p, theta, tree="adaptive"):
+    if tree == "adaptive":
+        how = ("adaptive-depth trees (a cell splits while it holds more than s dipoles, s per "
+               "size class by the library's autotuner); one CUDA graph launch, one kernel per "
+               "stage over all samples (per level for M2M and L2L)")
+        prec = ("FP32 bulk, M2L on 3xTF32 warp-level MMA; FP64 D tensors; per-cell M2L sums "
+                "in FP32, L2L in FP64")
+    else:
+        how = ("complete trees at the Eq. so depth; one CUDA graph launch of batched stages "
+               "(one kernel per stage over all samples)")
+        prec = "FP32 bulk; FP64 D tensors and FP64 local-expansion accumulation"
     return {"workload": "ensemble: %d clustered samples (80%% Gaussian blobs sigma 3 of 500, 20%% "
                         "chains of 20), N log-uniform in [1e3, 2e5], sum N = %d (seed 810237)"
                         % (ns, total),
-            "N": total, "samples": ns, "p": p, "theta": theta,
-            "precision": "FP32 bulk; FP64 D tensors and FP64 local-expansion accumulation",
+            "N": total, "samples": ns, "p": p, "theta": theta, "tree": tree,
+            "precision": prec,
             "step": "rotate every moment (Philox4x64-10, angle U[0, 0.05]) + field and energy "
-                    "of every sample; trees fixed; one CUDA graph launch of batched stages "
-                    "(one kernel per stage over all samples)",
+                    "of every sample; trees fixed; " + how,
             "l2": "inputs (%.0f MB of moments) larger than L2" % (total * 24 / 1e6)}
 
 
@@ -301,8 +317,14 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
     P_, M_ = R.gather_rows(pos, rows), R.gather_rows(mom, rows)
     total = int(o[-1])
     t0 = time.perf_counter()
-    b = C.Batch(torch.from_numpy(P_).to(dev), torch.from_numpy(M_).to(dev), o, p, theta,
-                precision=args.precision, stream=stream, autotune=not args.no_autotune)
+    adaptive = args.tree == "adaptive"
+    if adaptive:
+        b = C.Adaptive(torch.from_numpy(P_).to(dev), torch.from_numpy(M_).to(dev), p, theta,
+                       offsets=o, precision=args.precision, stream=stream,
+                       autotune=not args.no_autotune)
+    else:
+        b = C.Batch(torch.from_numpy(P_).to(dev), torch.from_numpy(M_).to(dev), o, p, theta,
+                    precision=args.precision, stream=stream, autotune=not args.no_autotune)
     t_create = time.perf_counter() - t0
     E_d = torch.zeros(len(mine), dtype=torch.float64, device=dev)
     counter = [0]
@@ -347,10 +369,14 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
     # algorithmic work of one step, summed over this rank's samples
     K = (p + 1) * (p + 2) * (p + 3) // 6 - 1
     pairs = far = 0
-    for i in range(len(mine)):
-        st = b.sample(i).stats()
-        pairs += st["p2p_pairs"]
-        far += st["far_pairs"]
+    if adaptive:
+        ast = b.stats()
+        pairs, far = ast["near_pairs"], ast["far_pairs"]
+    else:
+        for i in range(len(mine)):
+            st = b.sample(i).stats()
+            pairs += st["p2p_pairs"]
+            far += st["far_pairs"]
     peaks = _peaks()
     clock = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
@@ -361,7 +387,7 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
             "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": describe_ensemble(ns, len(pos), p, theta),
+            "config": describe_ensemble(ns, len(pos), p, theta, args.tree),
             "e2e": {"value": all_total * args.steps / t_e2e, "unit": "fields/s",
                     "ms_per_step": 1e3 * t_e2e / args.steps, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(total * 24 + len(mine) * 8),
@@ -374,18 +400,30 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
                          "algorithmic": {"p2p_pairs": pairs, "far_pairs": far,
                                          "flop": flops},
                          "note": "all near-pair and M2L flops of the step over the step time; "
-                                 "M2L on the tensor cores in every member"},
+                                 "M2L on the tensor cores"},
             "clocks": clk.summary(),
-            "samples_per_rank": len(mine),
-            "kernels_per_step": b.kernels_per_step(),
-            "autotune": {"classes": [{"n_min": c[0], "leaf": c[1], "m2l_item_len": c[2]}
-                                     for c in b.tuning()],
-                         "create_s": t_create,
-                         "note": "per size class (octave of N) the leaf occupancy and M2L item "
-                                 "length of the fastest timed trial evaluation (library "
-                                 "autotuner, at creation, outside the timed steps)"}}
+            "samples_per_rank": len(mine)}
+    if adaptive:
+        ast = b.stats()
+        line["kernels_per_step"] = int(ast["kernels_per_eval"]) + 1
+        line["adaptive_tree"] = {k: ast[k] for k in ("ncells", "nleaves", "max_level",
+                                                     "far_pairs", "near_pairs", "d_rows",
+                                                     "m2l_items", "ms_build")}
+        line["autotune"] = {"classes": [{"n_min": c[0], "split": c[1]} for c in b.tuning()],
+                            "create_s": t_create,
+                            "note": "per size class (octave of N) the split threshold of the "
+                                    "fastest timed trial evaluation (library autotuner, at "
+                                    "creation, outside the timed steps)"}
+    else:
+        line["kernels_per_step"] = b.kernels_per_step()
+        line["autotune"] = {"classes": [{"n_min": c[0], "leaf": c[1], "m2l_item_len": c[2]}
+                                        for c in b.tuning()],
+                            "create_s": t_create,
+                            "note": "per size class (octave of N) the leaf occupancy and M2L "
+                                    "item length of the fastest timed trial evaluation (library "
+                                    "autotuner, at creation, outside the timed steps)"}
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = oracle_ensemble_sample(pos, mom, off, p, theta)
+        line["cpu_baseline"] = oracle_ensemble_sample(pos, mom, off, p, theta, tree=args.tree)
     b.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -403,7 +441,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="ensemble: Eq. so leaves for every sample instead of the autotuner")
+                    help="ensemble: Eq. so leaves (splits) for every sample instead of the "
+                         "autotuner")
+    ap.add_argument("--tree", default="adaptive", choices=["adaptive", "uniform"],
+                    help="ensemble: adaptive-depth trees (default) or complete trees")
     ap.add_argument("--no-selector", action="store_true",
                     help="skip the selector object (learned (p, theta, leaf) at 1e-4)")
     ap.add_argument("--profile", action="store_true",

@@ -504,6 +504,33 @@ ccfmm_status fmm_adaptive_create(const double *positions, const double *moments,
                                  const double *split, const double *box, ccfmm_prec prec,
                                  void *stream, ccfmm_adaptive_t *out);
 
+/* Options of fmm_adaptive_create_ex (fmm_adaptive_create = autotune off).
+ *   autotune  nonzero: the library picks the split threshold per sample-size
+ *             class (floor(log2 N)): for each class, up to 16 of its samples
+ *             (spread over its sizes) are built and evaluated as a trial
+ *             forest for s = s0 x {1, sqrt2, 2, 2 sqrt2, 4} (s0: the given
+ *             threshold of the class's median sample, or Eq. so), and the
+ *             fastest mean evaluation time over `trials` timed evaluations
+ *             (after one warm-up) wins.  Trials run on the handle's stream
+ *             at creation.
+ *   trials    timed evaluations per candidate (<= 0: 3). */
+typedef struct {
+    int32_t autotune;
+    int32_t trials;
+} ccfmm_adaptive_opts;
+
+ccfmm_status fmm_adaptive_create_ex(const double *positions, const double *moments,
+                                    const int64_t *offsets, int nsamples, int p, double theta,
+                                    const double *split, const double *box, ccfmm_prec prec,
+                                    const ccfmm_adaptive_opts *opts, void *stream,
+                                    ccfmm_adaptive_t *out);
+
+/* The autotuner's choice: nclasses size classes (0 without autotune); for
+ * class i < capacity its smallest N and its split threshold (either output
+ * array may be NULL). */
+ccfmm_status fmm_adaptive_tuning(ccfmm_adaptive_t a, int32_t *nclasses, int64_t *class_nmin,
+                                 double *class_split, int32_t capacity);
+
 /* Field at every dipole and the energy of every sample for the current
  * moments (one CUDA graph launch; synchronises).
  *   H_out  total x 3 float64 in input order (host, device or NULL).

@@ -127,6 +127,10 @@ def load():
             "fmm_lattice_destroy": (None, [_vp]),
             "fmm_adaptive_create": (_int, [_vp, _vp, _vp, _int, _int, _dbl, _vp, _vp, _int, _vp,
                                            ctypes.POINTER(_vp)]),
+            "fmm_adaptive_create_ex": (_int, [_vp, _vp, _vp, _int, _int, _dbl, _vp, _vp, _int,
+                                              _vp, _vp, ctypes.POINTER(_vp)]),
+            "fmm_adaptive_tuning": (_int, [_vp, ctypes.POINTER(ctypes.c_int32), _vp, _vp,
+                                           ctypes.c_int32]),
             "fmm_adaptive_evaluate": (_int, [_vp, _vp, _vp]),
             "fmm_adaptive_step": (_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, _dbl, _vp, _vp]),
             "fmm_adaptive_set_moments": (_int, [_vp, _vp]),
@@ -577,7 +581,7 @@ class Adaptive:
     independent samples (``offsets``) evaluated together."""
 
     def __init__(self, positions, moments, p, theta, split=None, offsets=None, box=None,
-                 precision="mixed", stream=None):
+                 precision="mixed", stream=None, autotune=False, trials=3):
         lib = load()
         self._lib = lib
         if offsets is None:
@@ -602,10 +606,23 @@ class Adaptive:
         prec = {"mixed": MIXED, "fp32": MIXED, "fp64": FP64}[precision]
         self.p = int(p)
         h = _vp()
-        _check(lib.fmm_adaptive_create(pp, pm, _vp(off.ctypes.data), self.ns, int(p),
-                                       float(theta), sp, bp, prec, _stream_ptr(stream),
-                                       ctypes.byref(h)))
+        opts = (ctypes.c_int32 * 2)(1 if autotune else 0, int(trials))
+        _check(lib.fmm_adaptive_create_ex(pp, pm, _vp(off.ctypes.data), self.ns, int(p),
+                                          float(theta), sp, bp, prec,
+                                          _vp(ctypes.addressof(opts)), _stream_ptr(stream),
+                                          ctypes.byref(h)))
         self._h = h
+
+    def tuning(self):
+        """The autotuner's classes: list of (smallest N, split threshold)."""
+        n = ctypes.c_int32()
+        _check(self._lib.fmm_adaptive_tuning(self._h, ctypes.byref(n), None, None, 0))
+        k = n.value
+        nmin = np.zeros(max(k, 1), np.int64)
+        spl = np.zeros(max(k, 1))
+        _check(self._lib.fmm_adaptive_tuning(self._h, ctypes.byref(n), _vp(nmin.ctypes.data),
+                                             _vp(spl.ctypes.data), k))
+        return [(int(nmin[i]), float(spl[i])) for i in range(k)]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -625,12 +642,13 @@ class Adaptive:
         self.close()
 
     def _outs(self, H_out, E_out):
-        if H_out is None:
+        # neither given: both returned as new host arrays; otherwise only the
+        # given ones are written (the other is not copied out)
+        if H_out is None and E_out is None:
             H_out = np.zeros((self.n, 3))
-        if E_out is None:
             E_out = np.zeros(self.ns)
-        ph, k1 = _ptr(H_out, 3 * self.n)
-        pe, k2 = _ptr(E_out, self.ns)
+        ph, k1 = _ptr(H_out, 3 * self.n) if H_out is not None else (None, None)
+        pe, k2 = _ptr(E_out, self.ns) if E_out is not None else (None, None)
         return H_out, E_out, ph, pe, (k1, k2)
 
     def evaluate(self, H_out=None, E_out=None):

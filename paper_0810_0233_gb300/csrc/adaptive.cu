@@ -700,13 +700,50 @@ __global__ void k_item_fill(int nd, const int *gstart, long long nf, const int *
 }
 
 // ---------------------------------------------------------------- upward / downward
+// Shift tables of the one-axis translations: for coefficient column c
+// (multi-index n = c + 1) and axis s, the columns of n - t e_s (M2M, t = 0 ..
+// n_s, the zero multi-index left out) and of n + t e_s (L2L, t = 0 .. p - |n|),
+// in order of t.
+constexpr int KPMAX = ((nterms(PMAX) - 1 + 7) / 8) * 8;
+struct ShiftTab {
+    uint8_t m2m_n[3][KPMAX], l2l_n[3][KPMAX];
+    uint8_t m2m_c[3][KPMAX][PMAX + 1], l2l_c[3][KPMAX][PMAX + 1];
+};
+
+__global__ void k_shift_tab(int p, ShiftTab *tb)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= KPMAX) return;
+    const int K = nterms(p) - 1;
+    for (int sx = 0; sx < 3; ++sx) {
+        int nm = 0, nl = 0;
+        if (c < K) {
+            int nn[3];
+            midx_inv(c + 1, nn[0], nn[1], nn[2]);
+            const int kn = nn[0] + nn[1] + nn[2];
+            for (int t = 0; t <= nn[sx]; ++t) {
+                int m[3] = {nn[0], nn[1], nn[2]};
+                m[sx] -= t;
+                if (m[0] + m[1] + m[2] > 0) tb->m2m_c[sx][c][nm++] = (uint8_t)(midx(m[0], m[1], m[2]) - 1);
+            }
+            for (int t = 0; t <= p - kn; ++t) {
+                int m[3] = {nn[0], nn[1], nn[2]};
+                m[sx] += t;
+                tb->l2l_c[sx][c][nl++] = (uint8_t)(midx(m[0], m[1], m[2]) - 1);
+            }
+        }
+        tb->m2m_n[sx][c] = (uint8_t)nm;
+        tb->l2l_n[sx][c] = (uint8_t)nl;
+    }
+}
+
 // M2M (Eq. momentshift) into every internal cell of one level, one warp per
 // cell: the children sit at -/+ half their width along the axis split at
 // their level.
 template <typename real>
 __global__ void __launch_bounds__(32 * AW) k_am2m(int p, int KP, const int *cells, int ncl,
                                                   const int *smp, const int *lev, const int *ch,
-                                                  const AGeom *geo, real *Q)
+                                                  const AGeom *geo, const ShiftTab *tb, real *Q)
 {
     __shared__ real fs[AW][2][PMAX + 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -728,22 +765,15 @@ __global__ void __launch_bounds__(32 * AW) k_am2m(int p, int KP, const int *cell
         }
     }
     __syncwarp();
-    const int K = nterms(p) - 1;
     for (int col = lane; col < KP; col += 32) {
         real acc = (real)0;
-        if (col < K) {
-            int nn[3];
-            midx_inv(col + 1, nn[0], nn[1], nn[2]);
-            for (int b = 0; b < 2; ++b) {
-                const int chb = b ? b1 : b0;
-                if (chb < 0) continue;
-                const real *Qc = Q + (long long)chb * KP;
-                for (int t = 0; t <= nn[sx]; ++t) {
-                    int m[3] = {nn[0], nn[1], nn[2]};
-                    m[sx] -= t;
-                    if (m[0] + m[1] + m[2] > 0) acc += fs[w][b][t] * Qc[midx(m[0], m[1], m[2]) - 1];
-                }
-            }
+        const int n = tb->m2m_n[sx][col];
+        const uint8_t *cl = tb->m2m_c[sx][col];
+        for (int b = 0; b < 2; ++b) {
+            const int chb = b ? b1 : b0;
+            if (chb < 0) continue;
+            const real *Qc = Q + (long long)chb * KP;
+            for (int t = 0; t < n; ++t) acc += fs[w][b][t] * Qc[cl[t]];
         }
         Q[(long long)c * KP + col] = acc;
     }
@@ -755,7 +785,7 @@ template <typename acc_t>
 __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, const int *cells, int ncl,
                                                   const int *smp, const int *lev, const int *par,
                                                   const int4 *ic, const AGeom *geo,
-                                                  const acc_t *VF, double *V)
+                                                  const ShiftTab *tb, const acc_t *VF, double *V)
 {
     __shared__ double fs[AW][PMAX + 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -787,15 +817,10 @@ __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, const int *cell
             V[row + col] = 0.0;
             continue;
         }
-        int nn[3];
-        midx_inv(col + 1, nn[0], nn[1], nn[2]);
-        const int kn = nn[0] + nn[1] + nn[2];
+        const int n = tb->l2l_n[sx][col];
+        const uint8_t *cl = tb->l2l_c[sx][col];
         double acc = 0.0;
-        for (int t = 0; t <= p - kn; ++t) {
-            int m[3] = {nn[0], nn[1], nn[2]};
-            m[sx] += t;
-            acc += fs[w][t] * Vp[midx(m[0], m[1], m[2]) - 1];
-        }
+        for (int t = 0; t < n; ++t) acc += fs[w][t] * Vp[cl[t]];
         V[row + col] = (double)VF[row + col] + acc;
     }
 }
@@ -938,6 +963,9 @@ struct ccfmm_adaptive_s {
     double theta = 0.0;
     bool dbl = false;
     std::vector<long long> off;
+    // autotuner: per size class (floor(log2 N)) its smallest N and split
+    std::vector<long long> tune_nmin;
+    std::vector<double> tune_split;
     ABuf offd, pos, mom, geo, perm, A, B, H, Hd, E, flags, tmp;
     // cells
     int nc = 0, nleaf = 0, maxL = 0;
@@ -950,7 +978,7 @@ struct ccfmm_adaptive_s {
     // M2L groups
     int nd = 0, n64 = 0, n16 = 0;
     ABuf pt, ps, sep, D, it64, it16, fdense, fst, fq, fval, itab;
-    ABuf Q, VF, V;
+    ABuf Q, VF, V, shift;
     // ensemble step
     ABuf prm;
     RotateParams *hprm = nullptr;
@@ -1274,6 +1302,9 @@ template <typename real> ccfmm_status build_m2l(ccfmm_adaptive_t h, ABuf &stemp)
         ACK(cudaGetLastError());
         ACK(cudaStreamSynchronize(s));
     }
+    ATRY(aalloc(h->shift, sizeof(ShiftTab)));
+    note_launch();
+    k_shift_tab<<<1, KPMAX, 0, s>>>(h->p, AP<ShiftTab>(h->shift));
     const size_t cells = (size_t)h->nc * h->KP;
     ATRY(aalloc(h->Q, sizeof(real) * cells));
     ATRY(aalloc(h->VF, sizeof(real) * cells));
@@ -1313,7 +1344,8 @@ template <typename real> void enqueue_eval(ccfmm_adaptive_t h, bool rotate)
         note_launch();
         k_am2m<real><<<nblk(ncl, AW), 32 * AW, 0, s>>>(
             h->p, h->KP, AP<int>(h->lvl_cells) + h->lvl_off[l], ncl, AP<int>(h->smp),
-            AP<int>(h->lev), AP<int>(h->ch), AP<AGeom>(h->geo), AP<real>(h->Q));
+            AP<int>(h->lev), AP<int>(h->ch), AP<AGeom>(h->geo), AP<ShiftTab>(h->shift),
+            AP<real>(h->Q));
         ++k;
     }
     cudaMemsetAsync(h->VF.p, 0, sizeof(real) * (size_t)h->nc * h->KP, s);
@@ -1330,8 +1362,8 @@ template <typename real> void enqueue_eval(ccfmm_adaptive_t h, bool rotate)
         note_launch();
         k_al2l<real><<<nblk(ncl, AW), 32 * AW, 0, s>>>(
             h->p, h->KP, AP<int>(h->lvl_cells) + h->lvl_off[l], ncl, AP<int>(h->smp),
-            AP<int>(h->lev), AP<int>(h->par), AP<int4>(h->ic), AP<AGeom>(h->geo), AP<real>(h->VF),
-            AP<double>(h->V));
+            AP<int>(h->lev), AP<int>(h->par), AP<int4>(h->ic), AP<AGeom>(h->geo),
+            AP<ShiftTab>(h->shift), AP<real>(h->VF), AP<double>(h->V));
         ++k;
     }
     launch_ap2p<real>(h->p, h->KP, h->nleaf, AP<int>(h->leaves), AP<int>(h->p0), AP<int>(h->np),
@@ -1402,17 +1434,17 @@ void fmm_adaptive_destroy(ccfmm_adaptive_t h)
                     &h->ic, &h->cen, &h->leaves, &h->lvl_cells, &h->near_first, &h->near_num,
                     &h->near_src, &h->far_t, &h->far_s, &h->pt, &h->ps, &h->sep, &h->D, &h->it64,
                     &h->it16, &h->fdense, &h->fst, &h->fq, &h->fval, &h->itab, &h->Q, &h->VF,
-                    &h->V, &h->prm};
+                    &h->V, &h->shift, &h->prm};
     for (ABuf *b : bufs) afree(*b);
     if (h->hprm) cudaFreeHost(h->hprm);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
 
-ccfmm_status fmm_adaptive_create(const double *positions, const double *moments,
-                                 const int64_t *offsets, int nsamples, int p, double theta,
-                                 const double *split, const double *box, ccfmm_prec prec,
-                                 void *stream, ccfmm_adaptive_t *out)
+static ccfmm_status adaptive_create(const double *positions, const double *moments,
+                                    const int64_t *offsets, int nsamples, int p, double theta,
+                                    const double *split, const double *box, ccfmm_prec prec,
+                                    void *stream, ccfmm_adaptive_t *out)
 {
     set_last_error("");
     if (!out) return afail(CCFMM_ERR_ARG, "out is NULL");
@@ -1508,6 +1540,134 @@ ccfmm_status fmm_adaptive_create(const double *positions, const double *moments,
 #undef BTRY
     h->ms_build = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h;
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_adaptive_create(const double *positions, const double *moments,
+                                 const int64_t *offsets, int nsamples, int p, double theta,
+                                 const double *split, const double *box, ccfmm_prec prec,
+                                 void *stream, ccfmm_adaptive_t *out)
+{
+    return adaptive_create(positions, moments, offsets, nsamples, p, theta, split, box, prec,
+                           stream, out);
+}
+
+// Autotuner of the split threshold: samples are grouped by floor(log2 N);
+// for each class, up to 16 of its samples (spread over its sizes) form a
+// trial forest for every candidate s = s0 x {1, sqrt2, 2, 2 sqrt2, 4}
+// (s0 = the given split, or Eq. so), timed over `trials` evaluations after
+// one warm-up; the fastest mean wins, and the final forest takes each
+// sample's class threshold.
+ccfmm_status fmm_adaptive_create_ex(const double *positions, const double *moments,
+                                    const int64_t *offsets, int nsamples, int p, double theta,
+                                    const double *split, const double *box, ccfmm_prec prec,
+                                    const ccfmm_adaptive_opts *opts, void *stream,
+                                    ccfmm_adaptive_t *out)
+{
+    if (!opts || !opts->autotune)
+        return adaptive_create(positions, moments, offsets, nsamples, p, theta, split, box, prec,
+                               stream, out);
+    set_last_error("");
+    if (!out || !positions || !moments || !offsets || nsamples < 1)
+        return afail(CCFMM_ERR_ARG, "bad argument");
+    if (p < 1 || p > PMAX) return afail(CCFMM_ERR_ARG, "p must be in 1..%d", PMAX);
+    for (int i = 0; i < nsamples; ++i)
+        if (offsets[i + 1] <= offsets[i]) return afail(CCFMM_ERR_ARG, "every sample needs a dipole");
+    const int trials = opts->trials > 0 ? opts->trials : 3;
+    const double s0 = p > 3 ? 0.74 * (double)p * (double)p : 8.0;
+    const double mult[5] = {1.0, 1.4142135623730951, 2.0, 2.8284271247461903, 4.0};
+    std::vector<int> cls(nsamples);
+    int ncls = 0;
+    for (int i = 0; i < nsamples; ++i) {
+        long long n = offsets[i + 1] - offsets[i];
+        int c = 0;
+        while ((2ll << c) <= n) ++c;
+        cls[i] = c;
+        ncls = std::max(ncls, c + 1);
+    }
+    std::vector<double> best(ncls, 0.0);
+    std::vector<long long> nmin(ncls, -1);
+    for (int c = 0; c < ncls; ++c) {
+        std::vector<int> mem;
+        for (int i = 0; i < nsamples; ++i)
+            if (cls[i] == c) mem.push_back(i);
+        if (mem.empty()) continue;
+        std::sort(mem.begin(), mem.end(), [&](int a, int b) {
+            return offsets[a + 1] - offsets[a] < offsets[b + 1] - offsets[b];
+        });
+        nmin[c] = offsets[mem[0] + 1] - offsets[mem[0]];
+        std::vector<int> pick;
+        const int take = std::min<int>((int)mem.size(), 16);
+        for (int j = 0; j < take; ++j) pick.push_back(mem[(size_t)j * mem.size() / take]);
+        std::vector<int64_t> toff(1, 0);
+        for (int i : pick) toff.push_back(toff.back() + offsets[i + 1] - offsets[i]);
+        double *tpos = nullptr, *tmom = nullptr;
+        if (cudaMalloc(&tpos, sizeof(double) * 3 * toff.back()) != cudaSuccess ||
+            cudaMalloc(&tmom, sizeof(double) * 3 * toff.back()) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(tpos);
+            return afail(CCFMM_ERR_ALLOC, "autotuner allocation failed");
+        }
+        for (size_t j = 0; j < pick.size(); ++j) {
+            const size_t nb = sizeof(double) * 3 * (offsets[pick[j] + 1] - offsets[pick[j]]);
+            cudaMemcpy(tpos + 3 * toff[j], positions + 3 * offsets[pick[j]], nb, cudaMemcpyDefault);
+            cudaMemcpy(tmom + 3 * toff[j], moments + 3 * offsets[pick[j]], nb, cudaMemcpyDefault);
+        }
+        const double base = split ? split[mem[mem.size() / 2]] : s0;
+        double tbest = 1e300;
+        for (double m : mult) {
+            const double sv = base * m;
+            std::vector<double> sp(pick.size(), sv);
+            ccfmm_adaptive_t t = nullptr;
+            ccfmm_status st = adaptive_create(tpos, tmom, toff.data(), (int)pick.size(), p, theta,
+                                              sp.data(), nullptr, prec, stream, &t);
+            if (st != CCFMM_OK) {
+                cudaFree(tpos);
+                cudaFree(tmom);
+                return st;
+            }
+            st = run(t, 0, nullptr, nullptr);
+            const auto a0 = std::chrono::steady_clock::now();
+            for (int r = 0; r < trials && st == CCFMM_OK; ++r) st = run(t, 0, nullptr, nullptr);
+            const double ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a0).count() / trials;
+            fmm_adaptive_destroy(t);
+            if (st != CCFMM_OK) {
+                cudaFree(tpos);
+                cudaFree(tmom);
+                return st;
+            }
+            if (ms < tbest) {
+                tbest = ms;
+                best[c] = sv;
+            }
+        }
+        cudaFree(tpos);
+        cudaFree(tmom);
+    }
+    std::vector<double> sp(nsamples);
+    for (int i = 0; i < nsamples; ++i) sp[i] = best[cls[i]];
+    ccfmm_status st = adaptive_create(positions, moments, offsets, nsamples, p, theta, sp.data(),
+                                      box, prec, stream, out);
+    if (st != CCFMM_OK) return st;
+    for (int c = 0; c < ncls; ++c)
+        if (nmin[c] >= 0) {
+            (*out)->tune_nmin.push_back(nmin[c]);
+            (*out)->tune_split.push_back(best[c]);
+        }
+    return CCFMM_OK;
+}
+
+ccfmm_status fmm_adaptive_tuning(ccfmm_adaptive_t h, int32_t *nclasses, int64_t *class_nmin,
+                                 double *class_split, int32_t capacity)
+{
+    set_last_error("");
+    if (!h || !nclasses) return afail(CCFMM_ERR_ARG, "NULL argument");
+    *nclasses = (int32_t)h->tune_nmin.size();
+    for (int i = 0; i < (int)h->tune_nmin.size() && i < capacity; ++i) {
+        if (class_nmin) class_nmin[i] = h->tune_nmin[i];
+        if (class_split) class_split[i] = h->tune_split[i];
+    }
     return CCFMM_OK;
 }
 

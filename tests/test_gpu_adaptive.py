@@ -239,3 +239,35 @@ def test_near_pair_cut_on_clustered_sample():
     Hd = O.direct_field(pos, mom, targets=idx)
     eu, ea = rel(Hu[idx], Hd), rel(Ha[idx], Hd)
     assert ea < 1e-4 and eu < 1e-4, (eu, ea)
+
+
+def test_autotuner_picks_per_class_and_stays_exact():
+    """The library's split autotuner: one threshold per size class from the
+    candidate set, and the forest it builds agrees with the oracle run at
+    each sample's chosen threshold (mixed bounds)."""
+    sizes = [600, 700, 2500, 3100, 9000]
+    ps, ms = [], []
+    for i, n in enumerate(sizes):
+        pos, mom = W.clustered(n, seed=300 + i)
+        ps.append(pos)
+        ms.append(mom)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    pos, mom = np.concatenate(ps), np.concatenate(ms)
+    p, theta = 5, 0.5
+    s0 = O.leaf_size_rule(p)
+    cand = [s0 * m for m in (1.0, math.sqrt(2), 2.0, 2 * math.sqrt(2), 4.0)]
+    with C.Adaptive(pos, mom, p, theta, offsets=off, autotune=True, trials=1) as g:
+        tune = g.tuning()
+        assert [c[0] for c in tune] == [600, 2500, 9000]
+        for _, sv in tune:
+            assert min(abs(sv - c) for c in cand) < 1e-9 * sv
+        H, E = g.evaluate()
+        Q, V = g.expansions()
+        c0 = 0
+        for i, n in enumerate(sizes):
+            sv = [sv for nmin, sv in tune if nmin <= n][-1]
+            f = O.OracleAFMM(ps[i], ms[i], p, theta, sv)
+            f.run()
+            nc = len(f.cells())
+            check_mixed(H[off[i]:off[i + 1]], E[i], V[c0:c0 + nc], f, p)
+            c0 += nc
