@@ -38,6 +38,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -58,6 +59,7 @@ struct AGeom {               // one sample's tree geometry
     double w[AMAXL + 1][3];       // cell widths of level l
     double w2[AMAXL + 1];         // squared diagonal, (w0^2 + w1^2) + w2^2
     double rad[AMAXL + 1];        // half diagonal, 0.5 sqrt(w2)
+    double sh[AMAXL + 1][PMAX + 1];  // (w_l / 2)^t / t! along the axis split at level l
     double s;                     // split while a cell holds more than s
 };
 
@@ -144,6 +146,15 @@ __global__ void __launch_bounds__(256) k_ageom(const double *pos, const long lon
         g.w2[l] = __dadd_rn(__dadd_rn(__dmul_rn(g.w[l][0], g.w[l][0]), __dmul_rn(g.w[l][1], g.w[l][1])),
                             __dmul_rn(g.w[l][2], g.w[l][2]));
         g.rad[l] = 0.5 * sqrt(g.w2[l]);
+        // shift factors of the one-axis translations between level l - 1
+        // and level l (the child centre is at +/- w_l / 2 along axis[l])
+        const double hw = l ? 0.5 * g.w[l][g.axis[l]] : 0.0;
+        double f = 1.0;
+        g.sh[l][0] = 1.0;
+        for (int t = 1; t <= PMAX; ++t) {
+            f = f * hw / (double)t;
+            g.sh[l][t] = f;
+        }
     }
     g.s = sarr ? sarr[smp] : s_default;
     geo[smp] = g;
@@ -643,8 +654,9 @@ __global__ void k_group_flags(long long nf, const int *perm, const uint32_t *klo
 
 // group starts, the D rows' separations (unit vector, length), and the
 // number of 64- and 16-pair work items of each group
-__global__ void k_group_sep(long long nf, const int *gflag, const int *grank, const int *pt,
-                            const int *ps, const double4 *cen, int *gstart, double4 *sep)
+__global__ void k_group_sep(long long nf, int p, const int *gflag, const int *grank,
+                            const int *pt, const int *ps, const double4 *cen, int *gstart,
+                            double4 *sep, float *rpow)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf || !gflag[i]) return;
@@ -654,6 +666,12 @@ __global__ void k_group_sep(long long nf, const int *gflag, const int *grank, co
     const double x = a.x - b.x, y = a.y - b.y, z = a.z - b.z;
     const double r = sqrt(x * x + y * y + z * z);
     sep[d] = make_double4(x / r, y / r, z / r, r);
+    const double ri = 1.0 / r;
+    double v = 1.0;
+    for (int k = 0; k < PMAX + 2; ++k) {
+        rpow[(long long)d * (PMAX + 2) + k] = k <= p + 1 ? (float)v : 0.f;
+        v *= ri;
+    }
 }
 
 // work items of a group of n pairs: groups of more than 16 pairs go to the
@@ -746,12 +764,17 @@ __global__ void __launch_bounds__(32 * AW) k_am2m(int p, int KP, const int *cell
                                                   const AGeom *geo, const ShiftTab *tb, real *Q)
 {
     __shared__ real fs[AW][2][PMAX + 1];
+    __shared__ real qs[AW][2][KPMAX];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int idx = blockIdx.x * AW + w;
     if (idx >= ncl) return;
     const int c = cells[idx];
     const int b0 = ch[2 * c], b1 = ch[2 * c + 1];
     if (b0 < 0 && b1 < 0) return;  // a leaf: P2M wrote its moments
+    for (int col = lane; col < KP; col += 32) {
+        qs[w][0][col] = b0 >= 0 ? Q[(long long)b0 * KP + col] : (real)0;
+        qs[w][1][col] = b1 >= 0 ? Q[(long long)b1 * KP + col] : (real)0;
+    }
     const AGeom &g = geo[smp[c]];
     const int l = lev[c], sx = g.axis[l + 1];
     if (lane < 2) {
@@ -770,10 +793,8 @@ __global__ void __launch_bounds__(32 * AW) k_am2m(int p, int KP, const int *cell
         const int n = tb->m2m_n[sx][col];
         const uint8_t *cl = tb->m2m_c[sx][col];
         for (int b = 0; b < 2; ++b) {
-            const int chb = b ? b1 : b0;
-            if (chb < 0) continue;
-            const real *Qc = Q + (long long)chb * KP;
-            for (int t = 0; t < n; ++t) acc += fs[w][b][t] * Qc[cl[t]];
+            if ((b ? b1 : b0) < 0) continue;
+            for (int t = 0; t < n; ++t) acc += fs[w][b][t] * qs[w][b][cl[t]];
         }
         Q[(long long)c * KP + col] = acc;
     }
@@ -788,6 +809,7 @@ __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, const int *cell
                                                   const ShiftTab *tb, const acc_t *VF, double *V)
 {
     __shared__ double fs[AW][PMAX + 1];
+    __shared__ double vp[AW][KPMAX];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int idx = blockIdx.x * AW + w;
     if (idx >= ncl) return;
@@ -801,17 +823,12 @@ __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, const int *cell
     }
     const AGeom &g = geo[smp[c]];
     const int l = lev[c], sx = g.axis[l];
-    if (lane == 0) {
-        const double cs = ic[c].w ? 0.5 * g.w[l][sx] : -0.5 * g.w[l][sx];
-        double f = 1.0;
-        fs[w][0] = 1.0;
-        for (int t = 1; t <= p; ++t) {
-            f = f * cs / (double)t;
-            fs[w][t] = f;
-        }
+    if (lane <= p) {
+        const double f = g.sh[l][lane];
+        fs[w][lane] = (ic[c].w || !(lane & 1)) ? f : -f;
     }
+    for (int col = lane; col < KP; col += 32) vp[w][col] = V[(long long)pr * KP + col];
     __syncwarp();
-    const double *Vp = V + (long long)pr * KP;
     for (int col = lane; col < KP; col += 32) {
         if (col >= K) {
             V[row + col] = 0.0;
@@ -820,7 +837,7 @@ __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, const int *cell
         const int n = tb->l2l_n[sx][col];
         const uint8_t *cl = tb->l2l_c[sx][col];
         double acc = 0.0;
-        for (int t = 0; t < n; ++t) acc += fs[w][t] * Vp[cl[t]];
+        for (int t = 0; t < n; ++t) acc += fs[w][t] * vp[w][cl[t]];
         V[row + col] = (double)VF[row + col] + acc;
     }
 }
@@ -977,12 +994,17 @@ struct ccfmm_adaptive_s {
     ABuf near_first, near_num, near_src, far_t, far_s;
     // M2L groups
     int nd = 0, n64 = 0, n16 = 0;
-    ABuf pt, ps, sep, D, it64, it16, fdense, fst, fq, fval, itab;
+    ABuf pt, ps, sep, rpow, D, it64, it16, fdense, fst, fq, fval, itab;
     ABuf Q, VF, V, shift;
     // ensemble step
     ABuf prm;
     RotateParams *hprm = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // evaluation, rotation + evaluation
+    // the far chain (P2M .. L2L) runs on s_far (highest priority) beside the
+    // near field on the handle's stream; off with CCFMM_OVERLAP=0
+    bool overlap = true;
+    cudaStream_t s_far = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     long long kernels_per_eval = 0;
     double ms_build = 0.0;
     bool evaluated = false;
@@ -1275,11 +1297,12 @@ template <typename real> ccfmm_status build_m2l(ccfmm_adaptive_t h, ABuf &stemp)
         ABuf gstart, c64, c16, o64, o16;
         for (ABuf *b : {&gstart, &c64, &c16, &o64, &o16}) ATRY(aalloc(*b, 4 * (size_t)nd));
         ATRY(aalloc(h->sep, sizeof(double4) * (size_t)nd));
+        ATRY(aalloc(h->rpow, sizeof(float) * (PMAX + 2) * (size_t)nd));
         note_launch();
-        k_group_sep<<<nblk(nf, 256), 256, 0, s>>>(nf, AP<int>(gflag), AP<int>(grank),
+        k_group_sep<<<nblk(nf, 256), 256, 0, s>>>(nf, h->p, AP<int>(gflag), AP<int>(grank),
                                                   AP<int>(h->pt), AP<int>(h->ps),
                                                   AP<double4>(h->cen), AP<int>(gstart),
-                                                  AP<double4>(h->sep));
+                                                  AP<double4>(h->sep), AP<float>(h->rpow));
         note_launch();
         k_item_count<<<nblk(nd, 256), 256, 0, s>>>(nd, AP<int>(gstart), nf, AP<int>(c64),
                                                    AP<int>(c16));
@@ -1322,12 +1345,16 @@ template <typename real> ccfmm_status build_m2l(ccfmm_adaptive_t h, ABuf &stemp)
     return CCFMM_OK;
 }
 
-// one evaluation (with the ensemble rotation first when rotate)
+// one evaluation (with the ensemble rotation first when rotate).  With the
+// overlap on, the near field (without the smooth field) runs on the handle's
+// stream while P2M, M2M, M2L and L2L run on the high-priority stream; the
+// smooth field is added after the join.
 template <typename real> void enqueue_eval(ccfmm_adaptive_t h, bool rotate)
 {
     typedef typename vec4<real>::t R4;
     typedef typename vec2<real>::t R2;
     const cudaStream_t s = h->stream;
+    const cudaStream_t sf = h->overlap ? h->s_far : s;
     long long k = 0;
     if (rotate) {
         launch_rotate(AP<double>(h->mom), h->N, AP<RotateParams>(h->prm), s);
@@ -1335,47 +1362,67 @@ template <typename real> void enqueue_eval(ccfmm_adaptive_t h, bool rotate)
     }
     launch_permute_moments<real>(AP<double>(h->mom), AP<int>(h->perm), h->N, AP<R4>(h->A),
                                  AP<R2>(h->B), s);
+    ++k;
+    if (h->overlap) {
+        cudaEventRecord(h->ev_fork, s);
+        cudaStreamWaitEvent(sf, h->ev_fork, 0);
+        launch_ap2p<real>(h->p, h->KP, h->nleaf, AP<int>(h->leaves), AP<int>(h->p0),
+                          AP<int>(h->np), AP<int>(h->near_first), AP<int>(h->near_num),
+                          AP<int>(h->near_src), AP<double4>(h->cen), AP<R4>(h->A), AP<R2>(h->B),
+                          nullptr, AP<R4>(h->H), s);
+        ++k;
+    }
     launch_ap2m<real>(h->p, h->KP, h->nleaf, AP<int>(h->leaves), AP<int>(h->p0), AP<int>(h->np),
-                      AP<R4>(h->A), AP<R2>(h->B), AP<real>(h->Q), s);
-    k += 2;
+                      AP<R4>(h->A), AP<R2>(h->B), AP<real>(h->Q), sf);
+    ++k;
     for (int l = h->maxL - 1; l >= 0; --l) {
         const int ncl = h->lvl_off[l + 1] - h->lvl_off[l];
         if (ncl == 0) continue;
         note_launch();
-        k_am2m<real><<<nblk(ncl, AW), 32 * AW, 0, s>>>(
+        k_am2m<real><<<nblk(ncl, AW), 32 * AW, 0, sf>>>(
             h->p, h->KP, AP<int>(h->lvl_cells) + h->lvl_off[l], ncl, AP<int>(h->smp),
             AP<int>(h->lev), AP<int>(h->ch), AP<AGeom>(h->geo), AP<ShiftTab>(h->shift),
             AP<real>(h->Q));
         ++k;
     }
-    cudaMemsetAsync(h->VF.p, 0, sizeof(real) * (size_t)h->nc * h->KP, s);
+    cudaMemsetAsync(h->VF.p, 0, sizeof(real) * (size_t)h->nc * h->KP, sf);
     launch_am2l<real>(h->p, h->KP, AP<int4>(h->it64), h->n64, 64, AP<int>(h->pt), AP<int>(h->ps),
-                      AP<double4>(h->sep), AP<real>(h->D), h->ldD, AP<uint16_t>(h->itab),
-                      h->maxdeg, AP<real>(h->Q), AP<real>(h->VF), s);
+                      AP<double4>(h->sep), AP<float>(h->rpow), AP<real>(h->D), h->ldD,
+                      AP<uint16_t>(h->itab),
+                      h->maxdeg, AP<real>(h->Q), AP<real>(h->VF), sf);
     launch_am2l<real>(h->p, h->KP, AP<int4>(h->it16), h->n16, 16, AP<int>(h->pt), AP<int>(h->ps),
-                      AP<double4>(h->sep), AP<real>(h->D), h->ldD, AP<uint16_t>(h->itab),
-                      h->maxdeg, AP<real>(h->Q), AP<real>(h->VF), s);
+                      AP<double4>(h->sep), AP<float>(h->rpow), AP<real>(h->D), h->ldD,
+                      AP<uint16_t>(h->itab),
+                      h->maxdeg, AP<real>(h->Q), AP<real>(h->VF), sf);
     k += (h->n64 > 0) + (h->n16 > 0);
     for (int l = 0; l <= h->maxL; ++l) {
         const int ncl = h->lvl_off[l + 1] - h->lvl_off[l];
         if (ncl == 0) continue;
         note_launch();
-        k_al2l<real><<<nblk(ncl, AW), 32 * AW, 0, s>>>(
+        k_al2l<real><<<nblk(ncl, AW), 32 * AW, 0, sf>>>(
             h->p, h->KP, AP<int>(h->lvl_cells) + h->lvl_off[l], ncl, AP<int>(h->smp),
             AP<int>(h->lev), AP<int>(h->par), AP<int4>(h->ic), AP<AGeom>(h->geo),
             AP<ShiftTab>(h->shift), AP<real>(h->VF), AP<double>(h->V));
         ++k;
     }
-    launch_ap2p<real>(h->p, h->KP, h->nleaf, AP<int>(h->leaves), AP<int>(h->p0), AP<int>(h->np),
-                      AP<int>(h->near_first), AP<int>(h->near_num), AP<int>(h->near_src),
-                      AP<double4>(h->cen), AP<R4>(h->A), AP<R2>(h->B), AP<double>(h->V),
-                      AP<R4>(h->H), s);
+    if (h->overlap) {
+        cudaEventRecord(h->ev_join, sf);
+        cudaStreamWaitEvent(s, h->ev_join, 0);
+        launch_al2p<real>(h->p, h->KP, h->nleaf, AP<int>(h->leaves), AP<int>(h->p0),
+                          AP<int>(h->np), AP<R4>(h->A), AP<double>(h->V), AP<R4>(h->H), s);
+    } else {
+        launch_ap2p<real>(h->p, h->KP, h->nleaf, AP<int>(h->leaves), AP<int>(h->p0),
+                          AP<int>(h->np), AP<int>(h->near_first), AP<int>(h->near_num),
+                          AP<int>(h->near_src), AP<double4>(h->cen), AP<R4>(h->A), AP<R2>(h->B),
+                          AP<double>(h->V), AP<R4>(h->H), s);
+    }
+    ++k;
     note_launch(2);
     k_aunperm<real><<<nblk(h->N, 256), 256, 0, s>>>(h->N, AP<int>(h->perm), AP<R4>(h->H),
                                                     AP<double>(h->Hd));
     k_aenergy<<<h->ns, 256, 0, s>>>(AP<long long>(h->offd), AP<double>(h->mom), AP<double>(h->Hd),
                                     AP<double>(h->E));
-    k += 3;
+    k += 2;
     h->kernels_per_eval = k - (rotate ? 1 : 0);
 }
 
@@ -1432,11 +1479,14 @@ void fmm_adaptive_destroy(ccfmm_adaptive_t h)
     ABuf *bufs[] = {&h->offd, &h->pos, &h->mom, &h->geo, &h->perm, &h->A, &h->B, &h->H, &h->Hd,
                     &h->E, &h->flags, &h->tmp, &h->lev, &h->smp, &h->p0, &h->np, &h->par, &h->ch,
                     &h->ic, &h->cen, &h->leaves, &h->lvl_cells, &h->near_first, &h->near_num,
-                    &h->near_src, &h->far_t, &h->far_s, &h->pt, &h->ps, &h->sep, &h->D, &h->it64,
+                    &h->near_src, &h->far_t, &h->far_s, &h->pt, &h->ps, &h->sep, &h->rpow, &h->D, &h->it64,
                     &h->it16, &h->fdense, &h->fst, &h->fq, &h->fval, &h->itab, &h->Q, &h->VF,
                     &h->V, &h->shift, &h->prm};
     for (ABuf *b : bufs) afree(*b);
     if (h->hprm) cudaFreeHost(h->hprm);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->s_far) cudaStreamDestroy(h->s_far);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -1483,6 +1533,19 @@ static ccfmm_status adaptive_create(const double *positions, const double *momen
             return afail(CCFMM_ERR_CUDA, "stream creation failed");
         }
         h->own_stream = true;
+    }
+    {
+        const char *e = getenv("CCFMM_OVERLAP");
+        h->overlap = !(e && strcmp(e, "0") == 0);
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&h->s_far, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            afail(CCFMM_ERR_CUDA, "stream or event creation failed");
+            return bail(CCFMM_ERR_CUDA);
+        }
     }
     h->ns = nsamples;
     h->N = N;

@@ -383,13 +383,20 @@ template <typename real>
 void launch_ap2m(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
                  const typename vec4<real>::t *A, const typename vec2<real>::t *B, real *Q,
                  cudaStream_t s);
-// M2L grouped by D row: items (first pair, count <= ap, D row) over the
-// sorted pair arrays pt/ps; accumulates into VF with atomics (ap = 16 or 64)
+// M2L grouped by D row: items (first pair, count, D row) over the sorted
+// pair arrays pt/ps; accumulates into VF with atomics.  ap = 64: groups of
+// more than 16 pairs, 16: the others.  rpow: per D row rho^-d, d = 0 .. p+1
+// (PMAX + 2 floats a row; FP32 tensor-core form), or null.
 template <typename real>
 void launch_am2l(int p, int KP, const int4 *items, int nitems, int ap, const int *pt,
-                 const int *ps, const double4 *sep, const real *D, int ldD, const uint16_t *it,
-                 int maxdeg, const real *Q, real *VF, cudaStream_t s);
-// near field + smooth field of every leaf cell
+                 const int *ps, const double4 *sep, const float *rpow, const real *D, int ldD,
+                 const uint16_t *it, int maxdeg, const real *Q, real *VF, cudaStream_t s);
+// smooth field of every leaf cell added to H (after launch_ap2p with V null)
+template <typename real>
+void launch_al2p(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
+                 const typename vec4<real>::t *A, const double *V, typename vec4<real>::t *H,
+                 cudaStream_t s);
+// near field of every leaf cell, with the smooth field fused when V is not null
 template <typename real>
 void launch_ap2p(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
                  const int *near_first, const int *near_num, const int *near_src,

@@ -622,8 +622,7 @@ __device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
                                          uint32_t b1)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
         "{%8,%9}, {%0,%1,%2,%3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -633,20 +632,12 @@ __device__ __forceinline__ void red_add2(float *p, float a, float b)
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
 
-// scale tables of one item: pw[d] = rho^-d, gk[c] = rho^-|k|,
-// en[c] = (-1)^|n| rho^-(|n|+1) (zero beyond K); threads tid0.. step nth
-__device__ __forceinline__ void am2l_scales(int p, int KP, double rho, float *pw, float *gk,
-                                            float *en, int tid0, int nth, bool sync_block)
+// scale tables of one item from its row of rho^-d (d = 0 .. p + 1, formed in
+// FP64 at the build): gk[c] = rho^-|k|, en[c] = (-1)^|n| rho^-(|n|+1) (zero
+// beyond K); threads tid0.. step nth
+__device__ __forceinline__ void am2l_scales(int p, int KP, const float *pw, float *gk,
+                                            float *en, int tid0, int nth)
 {
-    if (tid0 == 0) {
-        const double ri = 1.0 / rho;
-        double v = 1.0;
-        for (int d = 0; d <= p + 1; ++d) {
-            pw[d] = (float)v;
-            v *= ri;
-        }
-    }
-    if (sync_block) __syncthreads(); else __syncwarp();
     const int K = nterms(p) - 1;
     for (int c = tid0; c < KP; c += nth) {
         float gv = 0.f, ev = 0.f;
@@ -664,11 +655,39 @@ __device__ __forceinline__ void am2l_scales(int p, int KP, double rho, float *pw
 // 16 pairs (rows) from pair c0 of the item: A from the sources' moments,
 // B from bfrag (BIG, fragment order in shared memory) or from Dl and the
 // index table; the results added to the targets' accumulators
+// compile-time choice of the chunk's instruction order: 0 (default) forms the
+// A fragments of one k-step at a time and issues the three passes of each
+// column tile together; 1 loads every A element first and issues the passes
+// over all column tiles in turn (more registers)
+#ifndef CCFMM_AM2L_PRELOAD
+#define CCFMM_AM2L_PRELOAD 0
+#endif
+
+template <int KP, bool BIG>
+__device__ __forceinline__ void am2l_bfrag(int ks, int nt, const float4 *bfrag, const float *Dl,
+                                           const uint16_t *its, uint32_t &bh0, uint32_t &bh1,
+                                           uint32_t &bl0, uint32_t &bl1)
+{
+    constexpr int KS = KP / 8;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    if (BIG) {
+        const float4 b = bfrag[(ks * KS + nt) * 32 + lane];
+        bh0 = __float_as_uint(b.x);
+        bh1 = __float_as_uint(b.y);
+        bl0 = __float_as_uint(b.z);
+        bl1 = __float_as_uint(b.w);
+    } else {
+        const int k = 8 * ks + t, n = 8 * nt + g;
+        tf32_split(Dl[its[k * KP + n]], bh0, bl0);
+        tf32_split(Dl[its[(k + 4) * KP + n]], bh1, bl1);
+    }
+}
+
 template <int KP, bool BIG>
 __device__ __forceinline__ void am2l_mma_chunk(const int4 &item, int c0, const int *pt,
                                                const int *ps, const float *Q, const float *gk,
                                                const float *en, const float4 *bfrag,
-                                               const float *Dl, const uint16_t *it, float *VF)
+                                               const float *Dl, const uint16_t *its, float *VF)
 {
     constexpr int KS = KP / 8;
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -679,36 +698,53 @@ __device__ __forceinline__ void am2l_mma_chunk(const int4 &item, int c0, const i
     float c[KS][4];
 #pragma unroll
     for (int n = 0; n < KS; ++n) c[n][0] = c[n][1] = c[n][2] = c[n][3] = 0.f;
+#if CCFMM_AM2L_PRELOAD
+    float x[KS][4];
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
         const int col = 8 * ks + t;
-        const float x0 = v0 ? q0[col] * gk[col] : 0.f;
-        const float x1 = v1 ? q1[col] * gk[col] : 0.f;
-        const float x2 = v0 ? q0[col + 4] * gk[col + 4] : 0.f;
-        const float x3 = v1 ? q1[col + 4] * gk[col + 4] : 0.f;
+        x[ks][0] = v0 ? q0[col] : 0.f;
+        x[ks][1] = v1 ? q1[col] : 0.f;
+        x[ks][2] = v0 ? q0[col + 4] : 0.f;
+        x[ks][3] = v1 ? q1[col + 4] : 0.f;
+    }
+#endif
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+        const int col = 8 * ks + t;
+        const float g0 = gk[col], g4 = gk[col + 4];
+#if CCFMM_AM2L_PRELOAD
+        const float y0 = x[ks][0], y1 = x[ks][1], y2 = x[ks][2], y3 = x[ks][3];
+#else
+        const float y0 = v0 ? q0[col] : 0.f, y1 = v1 ? q1[col] : 0.f;
+        const float y2 = v0 ? q0[col + 4] : 0.f, y3 = v1 ? q1[col + 4] : 0.f;
+#endif
         uint32_t ah[4], al[4];
-        tf32_split(x0, ah[0], al[0]);
-        tf32_split(x1, ah[1], al[1]);
-        tf32_split(x2, ah[2], al[2]);
-        tf32_split(x3, ah[3], al[3]);
+        tf32_split(y0 * g0, ah[0], al[0]);
+        tf32_split(y1 * g0, ah[1], al[1]);
+        tf32_split(y2 * g4, ah[2], al[2]);
+        tf32_split(y3 * g4, ah[3], al[3]);
+#if CCFMM_AM2L_PRELOAD
+        uint32_t bh0[KS], bh1[KS], bl0[KS], bl1[KS];
+#pragma unroll
+        for (int nt = 0; nt < KS; ++nt)
+            am2l_bfrag<KP, BIG>(ks, nt, bfrag, Dl, its, bh0[nt], bh1[nt], bl0[nt], bl1[nt]);
+#pragma unroll
+        for (int nt = 0; nt < KS; ++nt) mma_tf32(c[nt], al, bh0[nt], bh1[nt]);
+#pragma unroll
+        for (int nt = 0; nt < KS; ++nt) mma_tf32(c[nt], ah, bl0[nt], bl1[nt]);
+#pragma unroll
+        for (int nt = 0; nt < KS; ++nt) mma_tf32(c[nt], ah, bh0[nt], bh1[nt]);
+#else
 #pragma unroll
         for (int nt = 0; nt < KS; ++nt) {
             uint32_t bh0, bh1, bl0, bl1;
-            if (BIG) {
-                const float4 b = bfrag[(ks * KS + nt) * 32 + lane];
-                bh0 = __float_as_uint(b.x);
-                bh1 = __float_as_uint(b.y);
-                bl0 = __float_as_uint(b.z);
-                bl1 = __float_as_uint(b.w);
-            } else {
-                const int k = 8 * ks + t, n = 8 * nt + g;
-                tf32_split(Dl[it[k * KP + n]], bh0, bl0);
-                tf32_split(Dl[it[(k + 4) * KP + n]], bh1, bl1);
-            }
+            am2l_bfrag<KP, BIG>(ks, nt, bfrag, Dl, its, bh0, bh1, bl0, bl1);
             mma_tf32(c[nt], al, bh0, bh1);
             mma_tf32(c[nt], ah, bl0, bl1);
             mma_tf32(c[nt], ah, bh0, bh1);
         }
+#endif
     }
     const int t0 = v0 ? pt[item.x + r0] : -1, t1 = v1 ? pt[item.x + r1] : -1;
 #pragma unroll
@@ -722,7 +758,7 @@ __device__ __forceinline__ void am2l_mma_chunk(const int4 &item, int c0, const i
 
 template <int KP>
 __global__ void __launch_bounds__(128) k_am2l_mma_big(int p, const int4 *items, const int *pt,
-                                                      const int *ps, const double4 *sep,
+                                                      const int *ps, const float *rpow,
                                                       const float *D, int ldD,
                                                       const uint16_t *it, const float *Q,
                                                       float *VF)
@@ -731,12 +767,13 @@ __global__ void __launch_bounds__(128) k_am2l_mma_big(int p, const int4 *items, 
     extern __shared__ __align__(16) unsigned char smraw[];
     float4 *bfrag = reinterpret_cast<float4 *>(smraw);  // [KS * KS * 32]
     float *Dl = reinterpret_cast<float *>(bfrag + KS * KS * 32);  // [ldD]
-    float *gk = Dl + ldD, *en = gk + KP, *pw = en + KP;  // [KP], [KP], [PMAX + 4]
+    float *gk = Dl + ldD, *en = gk + KP;                          // [KP], [KP]
     const int4 item = items[blockIdx.x];
     const int tid = threadIdx.x;
     const float *Drow = D + (long long)item.z * ldD;
     for (int i = tid; i < ldD; i += blockDim.x) Dl[i] = Drow[i];
-    am2l_scales(p, KP, sep[item.z].w, pw, gk, en, tid, blockDim.x, true);
+    am2l_scales(p, KP, rpow + (long long)item.z * (PMAX + 2), gk, en, tid, blockDim.x);
+    __syncthreads();
     for (int idx = tid; idx < KS * KS * 32; idx += blockDim.x) {
         const int tile = idx >> 5, ln = idx & 31;
         const int ks = tile / KS, nt = tile - ks * KS;
@@ -756,47 +793,51 @@ __global__ void __launch_bounds__(128) k_am2l_mma_big(int p, const int4 *items, 
 template <int KP>
 __global__ void __launch_bounds__(128) k_am2l_mma_small(int p, const int4 *items, int nitems,
                                                         const int *pt, const int *ps,
-                                                        const double4 *sep, const float *D,
+                                                        const float *rpow, const float *D,
                                                         int ldD, const uint16_t *it,
                                                         const float *Q, float *VF)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
+    uint16_t *its = reinterpret_cast<uint16_t *>(smraw);  // [KP * KP] index table
+    float *wbase = reinterpret_cast<float *>(smraw + ((KP * KP * 2 + 15) & ~15));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per = ((ldD + 2 * KP + PMAX + 4) + 3) & ~3;  // floats per warp
-    float *Dl = reinterpret_cast<float *>(smraw) + warp * per;
-    float *gk = Dl + ldD, *en = gk + KP, *pw = en + KP;
+    const int per = ((ldD + 2 * KP) + 3) & ~3;  // floats per warp
+    float *Dl = wbase + warp * per;
+    float *gk = Dl + ldD, *en = gk + KP;
+    for (int i = threadIdx.x; i < KP * KP; i += blockDim.x) its[i] = it[i];
+    __syncthreads();
     const int ii = blockIdx.x * 4 + warp;
     if (ii >= nitems) return;
     const int4 item = items[ii];
     const float *Drow = D + (long long)item.z * ldD;
     for (int i = lane; i < ldD; i += 32) Dl[i] = Drow[i];
-    am2l_scales(p, KP, sep[item.z].w, pw, gk, en, lane, 32, false);
+    am2l_scales(p, KP, rpow + (long long)item.z * (PMAX + 2), gk, en, lane, 32);
     __syncwarp();
     for (int c0 = 0; c0 < item.y; c0 += 16)
-        am2l_mma_chunk<KP, false>(item, c0, pt, ps, Q, gk, en, nullptr, Dl, it, VF);
+        am2l_mma_chunk<KP, false>(item, c0, pt, ps, Q, gk, en, nullptr, Dl, its, VF);
 }
 
 template <int KP>
 static void run_am2l_mma(int p, const int4 *items, int nitems, bool big, const int *pt,
-                         const int *ps, const double4 *sep, const float *D, int ldD,
+                         const int *ps, const float *rpow, const float *D, int ldD,
                          const uint16_t *it, const float *Q, float *VF, cudaStream_t s)
 {
     constexpr int KS = KP / 8;
     note_launch();
     if (big) {
         const size_t smem = (size_t)KS * KS * 32 * sizeof(float4) +
-                            sizeof(float) * (ldD + 2 * KP + PMAX + 4) + 16;
+                            sizeof(float) * (ldD + 2 * KP) + 16;
         cudaFuncSetAttribute(k_am2l_mma_big<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        k_am2l_mma_big<KP><<<(unsigned)nitems, 128, smem, s>>>(p, items, pt, ps, sep, D, ldD, it,
-                                                                Q, VF);
+        k_am2l_mma_big<KP><<<(unsigned)nitems, 128, smem, s>>>(p, items, pt, ps, rpow, D, ldD,
+                                                                it, Q, VF);
     } else {
-        const int per = ((ldD + 2 * KP + PMAX + 4) + 3) & ~3;
-        const size_t smem = sizeof(float) * 4 * per + 16;
+        const int per = ((ldD + 2 * KP) + 3) & ~3;
+        const size_t smem = ((KP * KP * 2 + 15) & ~15) + sizeof(float) * 4 * per + 16;
         cudaFuncSetAttribute(k_am2l_mma_small<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         k_am2l_mma_small<KP><<<(unsigned)((nitems + 3) / 4), 128, smem, s>>>(
-            p, items, nitems, pt, ps, sep, D, ldD, it, Q, VF);
+            p, items, nitems, pt, ps, rpow, D, ldD, it, Q, VF);
     }
 }
 
@@ -814,22 +855,22 @@ static bool am2l_use_mma(int KP)
 
 template <typename real>
 void launch_am2l(int p, int KP, const int4 *items, int nitems, int ap, const int *pt,
-                 const int *ps, const double4 *sep, const real *D, int ldD, const uint16_t *it,
-                 int maxdeg, const real *Q, real *VF, cudaStream_t s)
+                 const int *ps, const double4 *sep, const float *rpow, const real *D, int ldD,
+                 const uint16_t *it, int maxdeg, const real *Q, real *VF, cudaStream_t s)
 {
     if (nitems <= 0) return;
-    if (sizeof(real) == 4 && maxdeg >= 2 * p && am2l_use_mma(KP)) {
+    if (sizeof(real) == 4 && rpow && maxdeg >= 2 * p && am2l_use_mma(KP)) {
         const float *Df = reinterpret_cast<const float *>(D);
         const float *Qf = reinterpret_cast<const float *>(Q);
         float *Vf = reinterpret_cast<float *>(VF);
         const bool big = ap == 64;
         switch (KP) {
-        case 8: run_am2l_mma<8>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
-        case 16: run_am2l_mma<16>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
-        case 24: run_am2l_mma<24>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
-        case 40: run_am2l_mma<40>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
-        case 56: run_am2l_mma<56>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
-        case 88: run_am2l_mma<88>(p, items, nitems, big, pt, ps, sep, Df, ldD, it, Qf, Vf, s); return;
+        case 8: run_am2l_mma<8>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
+        case 16: run_am2l_mma<16>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
+        case 24: run_am2l_mma<24>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
+        case 40: run_am2l_mma<40>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
+        case 56: run_am2l_mma<56>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
+        case 88: run_am2l_mma<88>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
         default: break;
         }
     }
@@ -840,11 +881,11 @@ void launch_am2l(int p, int KP, const int4 *items, int nitems, int ap, const int
 }
 
 template void launch_am2l<float>(int, int, const int4 *, int, int, const int *, const int *,
-                                 const double4 *, const float *, int, const uint16_t *, int,
-                                 const float *, float *, cudaStream_t);
+                                 const double4 *, const float *, const float *, int,
+                                 const uint16_t *, int, const float *, float *, cudaStream_t);
 template void launch_am2l<double>(int, int, const int4 *, int, int, const int *, const int *,
-                                  const double4 *, const double *, int, const uint16_t *, int,
-                                  const double *, double *, cudaStream_t);
+                                  const double4 *, const float *, const double *, int,
+                                  const uint16_t *, int, const double *, double *, cudaStream_t);
 
 template void launch_m2l<float>(int, int, const Tile *, int, const int *, const int *,
                                 const float *, const float *, int, const uint16_t *, int, const Geom *,

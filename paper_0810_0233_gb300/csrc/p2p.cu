@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
     const double4 cc = cen[c];
     const AdaEnts ents{p0, np, near_src, cen, cc.x, cc.y, cc.z, c};
     const int e0 = near_first[c];
-    p2p_leaf<real>(p, p0[c], np[c], e0, e0 + near_num[c], ents, V + (long long)c * KP, A, B, H);
+    p2p_leaf<real>(p, p0[c], np[c], e0, e0 + near_num[c], ents,
+                   V ? V + (long long)c * KP : nullptr, A, B, H);
 }
 
 template <typename real>
@@ -743,6 +744,56 @@ __global__ void __launch_bounds__(32 * L2P_W) k_l2p(int KP, int L, const int *le
 {
     l2p_body<real, P>(KP, L, leaf_start, A, V, H, blockIdx.x);
 }
+
+// L2P of the adaptive tree's leaf cells (one warp per leaf), added to the
+// near field that k_ap2p stored without the smooth field
+template <typename real, int P>
+__global__ void __launch_bounds__(32 * L2P_W) k_al2p(int KP, int nleaf, const int *leaves,
+                                                     const int *p0, const int *np,
+                                                     const typename vec4<real>::t *A,
+                                                     const double *V, typename vec4<real>::t *H)
+{
+    __shared__ real vs[L2P_W][nterms(PMAX)];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int K = nterms(P) - 1;
+    const int li = blockIdx.x * L2P_W + w;
+    if (li >= nleaf) return;
+    const int c = leaves[li];
+    const int t0 = p0[c], nt = np[c];
+    for (int k = lane; k < K; k += 32) vs[w][k] = (real)V[(long long)c * KP + k];
+    __syncwarp();
+    for (int i = lane; i < nt; i += 32) {
+        const typename vec4<real>::t a = A[t0 + i];
+        typename vec4<real>::t h = H[t0 + i];
+        const Sum3<real> sl = l2p_fixed<real, P>(vs[w], a.x, a.y, a.z);
+        h.x -= sl.x;
+        h.y -= sl.y;
+        h.z -= sl.z;
+        H[t0 + i] = h;
+    }
+}
+
+template <typename real>
+void launch_al2p(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
+                 const typename vec4<real>::t *A, const double *V, typename vec4<real>::t *H,
+                 cudaStream_t s)
+{
+    if (nleaf <= 0) return;
+    const unsigned nb = (unsigned)((nleaf + L2P_W - 1) / L2P_W);
+    note_launch();
+#define AL2P(PV)                                                                                 \
+    case PV: k_al2p<real, PV><<<nb, 32 * L2P_W, 0, s>>>(KP, nleaf, leaves, p0, np, A, V, H); break;
+    switch (p) {
+        AL2P(1) AL2P(2) AL2P(3) AL2P(4) AL2P(5) AL2P(6) AL2P(7) AL2P(8)
+    default: break;
+    }
+#undef AL2P
+}
+
+template void launch_al2p<float>(int, int, int, const int *, const int *, const int *,
+                                 const float4 *, const double *, float4 *, cudaStream_t);
+template void launch_al2p<double>(int, int, int, const int *, const int *, const int *,
+                                  const double4 *, const double *, double4 *, cudaStream_t);
 
 // every member's smooth field in one launch (ensemble step)
 template <int P>
