@@ -1683,7 +1683,8 @@ static void batch_enqueue(ccfmm_batch_t b, cudaStream_t s)
     launch_q_split_batch(KP, (const QSplitArgs *)A(b->st_qs), B(b->st_qs), nm, b->st_qs.nblocks, sf);
     launch_m2l_tc_batch(KP, (const M2LTCArgs *)A(b->st_m2l), B(b->st_m2l), nm, b->st_m2l.nblocks,
                         spin, stall, sf);
-    launch_reduce_batch(p, (const ReduceArgs *)A(b->st_red), B(b->st_red), nm, b->st_red.nblocks, sf);
+    launch_reduce_h_batch(p, KP, (const ReduceArgs *)A(b->st_red), B(b->st_red), nm,
+                          b->st_red.nblocks, sf);
     for (auto &st : b->st_l2l) launch_l2l_batch((const L2LArgs *)A(st), B(st), nm, st.nblocks, sf);
     cudaEventRecord(b->ev_far1, sf);
     cudaStreamWaitEvent(s, b->ev_far1, 0);

@@ -369,6 +369,10 @@ void launch_m2l_tc_batch(int KP, const M2LTCArgs *a, const int *bstart, int nm, 
                          long long spin, int stall, cudaStream_t s);
 void launch_reduce_batch(int p, const ReduceArgs *a, const int *bstart, int nm, int nblocks,
                          cudaStream_t s);
+// the tensor-core path's reduce (harmonic reduction: reduced partial sums,
+// then the full V); KPF the full coefficient width
+void launch_reduce_h_batch(int p, int KPF, const ReduceArgs *a, const int *bstart, int nm,
+                           int nblocks, cudaStream_t s);
 void launch_p2p_batch(const P2PArgs *a, const int *bstart, int nm, int nblocks, int KP,
                       cudaStream_t s);
 void launch_finish_batch(const FinishArgs *a, const int *bstart, int nm, int nblocks,

@@ -99,6 +99,34 @@ template <int KP> struct TcShape {
     static constexpr int TMEM_COLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256);
 };
 
+// Harmonic reduction of the contraction.  D_m is a derivative of 1/r, so
+// sum_a D_{m+2e_a} = 0 (Laplace): a moment Q_k with k_z >= 2 folds into
+// Q_{k-2e_z+2e_x} and Q_{k-2e_z+2e_y} (with a minus sign) without changing
+// any V_n, leaving per order k the 2k + 1 moments with k_z <= 1; and V_n
+// with n_z >= 2 follows from V_{n-2e_z+2e_x} + V_{n-2e_z+2e_y} = -V_n by the
+// same identity.  So the MMA contracts (p+1)^2 - 1 coefficients on either
+// side instead of T(p) - 1 (48 instead of 83 at p = 6).  In the library's
+// order the k_z <= 1 multi-indices are the first 2k + 1 of each order: the
+// reduced column r of order k (k^2 - 1 <= r < (k+1)^2 - 1) is the full
+// column T(k-1) - 1 + r - (k^2 - 1).  The kernels below are instantiated on
+// the reduced width (padded to 8) of each full width KP.
+constexpr int tc_red_kp(int KP)
+{
+    return KP == 40 ? 24 : KP == 56 ? 40 : KP == 88 ? 48 : KP == 120 ? 64 : 0;
+}
+__host__ __device__ constexpr int red_count(int p) { return (p + 1) * (p + 1) - 1; }
+__device__ __forceinline__ int red_order(int r)
+{
+    int k = 1;
+    while ((k + 1) * (k + 1) - 1 <= r) ++k;
+    return k;
+}
+__device__ __forceinline__ int red_full(int r)
+{
+    const int k = red_order(r);
+    return nterms(k - 1) - 1 + r - (k * k - 1);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -225,14 +253,10 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
 __global__ void k_tc_scale(int p, int KT, int L, const Geom *g, float *gk)
 {
     const int l = blockIdx.x;
-    const int K = nterms(p) - 1;
+    const int KR = red_count(p);
     for (int k = threadIdx.x; k < KT; k += blockDim.x) {
         float v = 0.f;
-        if (k < K && l <= L) {
-            int nx, ny, nz;
-            midx_inv(k + 1, nx, ny, nz);
-            v = (float)pow(g->h[l], (double)(1 - (nx + ny + nz)));
-        }
+        if (k < KR && l <= L) v = (float)pow(g->h[l], (double)(1 - red_order(k)));
         gk[l * KT + k] = v;
     }
 }
@@ -240,11 +264,12 @@ __global__ void k_tc_scale(int p, int KT, int L, const Geom *g, float *gk)
 // Operator chunks of every far offset class: for chunk c and part (hi, lo),
 // the N x 32 block M[n][k] = D~_{n+k}, k = 32c + kl, in canonical layout.
 template <int KP>
-__global__ void k_m2l_ops(int p, const float *D, int ldD, const uint16_t *it_g, float *Bop)
+__global__ void k_m2l_ops(int p, int KPF, const float *D, int ldD, const uint16_t *it_g,
+                          float *Bop)
 {
     typedef TcShape<KP> S;
     extern __shared__ float Dl[];
-    const int K = nterms(p) - 1;
+    const int K = red_count(p);
     const long long gid = blockIdx.x;
     for (int i = threadIdx.x; i < ldD; i += blockDim.x) Dl[i] = D[gid * ldD + i];
     __syncthreads();
@@ -256,68 +281,171 @@ __global__ void k_m2l_ops(int p, const float *D, int ldD, const uint16_t *it_g, 
         const int n = ((q >> 5) & 7) | ((q >> 8) << 3);
         const int kl = (q & 3) | ((((q >> 2) & 7) ^ (n & 7)) << 2);
         const int k = c * TC_KC + kl;
-        const float v = (n < K && k < K) ? Dl[it_g[k * KP + n]] : 0.f;
+        const float v = (n < K && k < K) ? Dl[it_g[red_full(k) * KPF + red_full(n)]] : 0.f;
         const float hi = to_tf32(v);
         out[c * 2 * PER + q] = hi;
         out[c * 2 * PER + PER + q] = v - hi;
     }
 }
 
-// Scaled moments split into TF32 pairs: Qs[part][hid][k], rows of KT floats
-// (SPLIT), or the scaled FP32 moments alone in plane 0 (the kernel that
-// splits them in registers on the way to tensor memory).
+// Scaled, folded moments split into TF32 pairs: Qs[part][hid][r], rows of
+// KT floats over the reduced columns r (SPLIT), or the scaled FP32 values
+// alone in plane 0 (the kernel that splits them in registers on the way to
+// tensor memory).  One warp per cell: the full row into shared memory, lane
+// k - 1 folds order k (k_z from high to low, in FP32), then the reduced
+// columns are scaled by h^(1-|k|) and split.
+constexpr int QF_W = 8;  // cells (warps) per block
+constexpr int QF_ROW = ((nterms(PMAX) - 1 + 7) / 8) * 8;
+
 template <int KP, bool SPLIT>
-__device__ __forceinline__ void q_split_body(int p, long long ncell, const float *Q,
-                                             const float *gk, float *Qs, long long blk)
+__device__ __forceinline__ void q_fold_body(int p, int KPF, long long ncell, const float *Q,
+                                            const float *gk, float *Qs, long long blk)
 {
     typedef TcShape<KP> S;
     constexpr int KT = S::KT;
-    const int K = nterms(p) - 1;
-    const long long i = blk * blockDim.x + threadIdx.x;
-    if (i >= ncell * (KT / 4)) return;
-    const long long hid = i / (KT / 4);
-    const int k4 = (int)(i - hid * (KT / 4)) * 4;
-    const int level = hid > 0 ? 63 - __clzll(hid) : 0;
-    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    __shared__ float row[QF_W][QF_ROW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long hid = blk * QF_W + w;
+    if (hid >= ncell) return;
+    const int K = nterms(p) - 1, KR = red_count(p);
     // heap id 0 is no cell: its row stays zero (the gather's empty partner)
-    if (k4 < KP && hid > 0) {
-        const float4 q = *reinterpret_cast<const float4 *>(Q + hid * KP + k4);
-        const float4 g = *reinterpret_cast<const float4 *>(gk + level * KT + k4);
-        v[0] = q.x * g.x;
-        v[1] = q.y * g.y;
-        v[2] = q.z * g.z;
-        v[3] = q.w * g.w;
+    for (int c = lane; c < K; c += 32) row[w][c] = hid > 0 ? Q[hid * KPF + c] : 0.f;
+    __syncwarp();
+    if (lane >= 1 && lane < p) {
+        const int k = lane + 1, base = nterms(k - 1) - 1;
+        for (int z = k; z >= 2; --z)
+            for (int y = 0; y <= k - z; ++y) {
+                const int x = k - z - y;
+                const float v = row[w][base + z * (2 * k + 3 - z) / 2 + y];
+                const int zt = z - 2, lt = base + zt * (2 * k + 3 - zt) / 2;
+                row[w][lt + y] -= v;       // (x + 2, y, z - 2)
+                row[w][lt + y + 2] -= v;   // (x, y + 2, z - 2)
+                (void)x;
+            }
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (k4 + j >= K) v[j] = 0.f;
-    if (!SPLIT) {
-        *reinterpret_cast<float4 *>(Qs + hid * KT + k4) = make_float4(v[0], v[1], v[2], v[3]);
-        return;
+    __syncwarp();
+    const int level = hid > 0 ? 63 - __clzll(hid) : 0;
+    for (int r = lane; r < KT; r += 32) {
+        const float v = (r < KR && hid > 0) ? row[w][red_full(r)] * gk[level * KT + r] : 0.f;
+        if (!SPLIT) {
+            Qs[hid * KT + r] = v;
+        } else {
+            const float hi = to_tf32(v);
+            Qs[hid * KT + r] = hi;
+            Qs[(ncell + hid) * KT + r] = v - hi;
+        }
     }
-    float hi[4], lo[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        hi[j] = to_tf32(v[j]);
-        lo[j] = v[j] - hi[j];
-    }
-    *reinterpret_cast<float4 *>(Qs + hid * KT + k4) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<float4 *>(Qs + (ncell + hid) * KT + k4) =
-        make_float4(lo[0], lo[1], lo[2], lo[3]);
 }
 
 template <int KP, bool SPLIT>
-__global__ void k_q_split(int p, long long ncell, const float *Q, const float *gk, float *Qs)
+__global__ void __launch_bounds__(32 * QF_W) k_q_fold(int p, int KPF, long long ncell,
+                                                      const float *Q, const float *gk, float *Qs)
 {
-    q_split_body<KP, SPLIT>(p, ncell, Q, gk, Qs, blockIdx.x);
+    q_fold_body<KP, SPLIT>(p, KPF, ncell, Q, gk, Qs, blockIdx.x);
 }
 
 template <int KP>
-__global__ void k_q_split_batch(const QSplitArgs *a, const int *bstart, int nm)
+__global__ void __launch_bounds__(32 * QF_W) k_q_fold_batch(int KPF, const QSplitArgs *a,
+                                                            const int *bstart, int nm)
 {
     int blk;
     const QSplitArgs &x = a[batch_member(bstart, nm, blockIdx.x, blk)];
-    q_split_body<KP, true>(x.p, x.ncell, x.Q, x.gk, x.Qs, blk);
+    q_fold_body<KP, true>(x.p, KPF, x.ncell, x.Q, x.gk, x.Qs, blk);
+}
+
+// V of each field cell from the tile's partial sums over the reduced
+// columns: FP64 sums in item order times (-1)^|n| h^-(|n|+2), then the
+// columns with n_z >= 2 by -V_{n-2e_z+2e_x} - V_{n-2e_z+2e_y} in the library's
+// order (within an order by increasing n_z, so both are known).  A tile's
+// cells are split over RED_H blocks (blockIdx.y), 128 / RED_H cells each.
+constexpr int RED_H = 4, RED_HC = TT / RED_H;
+
+__device__ __forceinline__ void m2l_reduce_h_body(int p, int KPF, int KRP, const Tile *tiles,
+                                                  const int *tile_item0, const int *tile_nitems,
+                                                  const float *Ps, const Geom *g, double *V,
+                                                  int tile)
+{
+    extern __shared__ double smd[];
+    const int K = nterms(p) - 1, KR = red_count(p);
+    double *en = smd;              // [KR]
+    double *rows = smd + KR;       // [RED_HC][K]
+    const Tile t = tiles[tile];
+    const double hinv = 1.0 / g->h[t.level];
+    for (int r = threadIdx.x; r < KR; r += blockDim.x) {
+        const int kn = red_order(r);
+        double q = hinv * hinv;
+        for (int d = 0; d < kn; ++d) q *= hinv;
+        en[r] = (kn & 1) ? -q : q;
+    }
+    __syncthreads();
+    const int i0 = tile_item0[tile], ni = tile_nitems[tile];
+    const int tb = blockIdx.y * RED_HC;
+    const int nc = min(RED_HC, t.nt - tb);
+    for (int j = threadIdx.x; j < nc * KR; j += blockDim.x) {
+        const int ci = j / KR, r = j - ci * KR;
+        double s = 0.0;
+        for (int it = 0; it < ni; ++it)
+            s += (double)Ps[((long long)(i0 + it) * TT + tb + ci) * KRP + r];
+        rows[ci * K + red_full(r)] = s * en[r];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nc) {
+        double *v = rows + threadIdx.x * K;
+        for (int c = 0; c < K; ++c) {
+            int nx, ny, nz;
+            midx_inv(c + 1, nx, ny, nz);
+            if (nz < 2) continue;
+            v[c] = -v[midx(nx + 2, ny, nz - 2) - 1] - v[midx(nx, ny + 2, nz - 2) - 1];
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc * K; j += blockDim.x) {
+        const int ci = j / K, c = j - ci * K;
+        const long long hid = (1ll << t.level) + t.keys[tb + ci];
+        V[hid * KPF + c] = rows[j];
+    }
+}
+
+__global__ void k_m2l_reduce_h(int p, int KPF, int KRP, const Tile *tiles, const int *tile_item0,
+                               const int *tile_nitems, const float *Ps, const Geom *g, double *V)
+{
+    m2l_reduce_h_body(p, KPF, KRP, tiles, tile_item0, tile_nitems, Ps, g, V, blockIdx.x);
+}
+
+__global__ void k_m2l_reduce_h_batch(int KRP, const ReduceArgs *a, const int *bstart, int nm)
+{
+    int tile;
+    const ReduceArgs &x = a[batch_member(bstart, nm, blockIdx.x, tile)];
+    m2l_reduce_h_body(x.p, x.KP, KRP, x.tiles, x.tile_item0, x.tile_nitems, x.Ps, x.g, x.V, tile);
+}
+
+static size_t reduce_h_smem(int p)
+{
+    return sizeof(double) * ((size_t)red_count(p) + (size_t)RED_HC * (nterms(p) - 1));
+}
+
+void launch_reduce_h(int p, int KPF, const Tile *tiles, int ntiles, const int *tile_item0,
+                     const int *tile_nitems, const float *Ps, const Geom *g, double *V,
+                     cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    const size_t smem = reduce_h_smem(p);
+    cudaFuncSetAttribute(k_m2l_reduce_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
+    k_m2l_reduce_h<<<dim3((unsigned)ntiles, RED_H), 256, smem, s>>>(
+        p, KPF, tc_red_kp(KPF), tiles, tile_item0, tile_nitems, Ps, g, V);
+}
+
+void launch_reduce_h_batch(int p, int KPF, const ReduceArgs *a, const int *bstart, int nm,
+                           int nblocks, cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    const size_t smem = reduce_h_smem(p);
+    cudaFuncSetAttribute(k_m2l_reduce_h_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    note_launch();
+    k_m2l_reduce_h_batch<<<dim3((unsigned)nblocks, RED_H), 256, smem, s>>>(tc_red_kp(KPF), a,
+                                                                           bstart, nm);
 }
 
 // 16 consecutive accumulator columns of this warp's 32 TMEM lanes
@@ -906,7 +1034,12 @@ template <int KP> static size_t tc_smem()
     return (size_t)TcShape<KP>::ST * TcShape<KP>::STAGE + 1024;
 }
 
-int q_split_blocks(int KP, long long ncell) { return (int)((ncell * (m2l_tc_kt(KP) / 4) + 255) / 256); }
+// blocks of the fold for ncell cells (full width KP)
+int q_split_blocks(int KP, long long ncell)
+{
+    (void)KP;
+    return (int)((ncell + QF_W - 1) / QF_W);
+}
 
 void launch_q_split_batch(int KP, const QSplitArgs *a, const int *bstart, int nm, int nblocks,
                           cudaStream_t s)
@@ -914,31 +1047,29 @@ void launch_q_split_batch(int KP, const QSplitArgs *a, const int *bstart, int nm
     if (nblocks <= 0) return;
     note_launch();
     switch (KP) {
-    case 40: k_q_split_batch<40><<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm); break;
-    case 56: k_q_split_batch<56><<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm); break;
-    case 88: k_q_split_batch<88><<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm); break;
-    case 120: k_q_split_batch<120><<<(unsigned)nblocks, 256, 0, s>>>(a, bstart, nm); break;
+    case 40: k_q_fold_batch<24><<<(unsigned)nblocks, 32 * QF_W, 0, s>>>(KP, a, bstart, nm); break;
+    case 56: k_q_fold_batch<40><<<(unsigned)nblocks, 32 * QF_W, 0, s>>>(KP, a, bstart, nm); break;
+    case 88: k_q_fold_batch<48><<<(unsigned)nblocks, 32 * QF_W, 0, s>>>(KP, a, bstart, nm); break;
+    case 120: k_q_fold_batch<64><<<(unsigned)nblocks, 32 * QF_W, 0, s>>>(KP, a, bstart, nm); break;
     default: break;
     }
 }
-
-template <int KP> static size_t tc_smem();
 
 void launch_m2l_tc_batch(int KP, const M2LTCArgs *a, const int *bstart, int nm, int nblocks,
                          long long spin, int stall, cudaStream_t s)
 {
     if (nblocks <= 0) return;
-#define M2LTCB(KPV)                                                                             \
+#define M2LTCB(KPV, KRV)                                                                        \
     case KPV: {                                                                                 \
-        const int smem = (int)tc_smem<KPV>();                                                   \
-        cudaFuncSetAttribute(k_m2l_tc_batch<KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+        const int smem = (int)tc_smem<KRV>();                                                   \
+        cudaFuncSetAttribute(k_m2l_tc_batch<KRV>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                              smem);                                                             \
         note_launch();                                                                          \
-        k_m2l_tc_batch<KPV><<<(unsigned)nblocks, TC_THREADS, smem, s>>>(a, bstart, nm, spin,     \
+        k_m2l_tc_batch<KRV><<<(unsigned)nblocks, TC_THREADS, smem, s>>>(a, bstart, nm, spin,     \
                                                                         stall);                 \
     } break;
     switch (KP) {
-        M2LTCB(40) M2LTCB(56) M2LTCB(88) M2LTCB(120)
+        M2LTCB(40, 24) M2LTCB(56, 40) M2LTCB(88, 48) M2LTCB(120, 64)
     default: break;
     }
 #undef M2LTCB
@@ -947,10 +1078,10 @@ void launch_m2l_tc_batch(int KP, const M2LTCArgs *a, const int *bstart, int nm, 
 bool m2l_tc_supported(int KP)
 {
     switch (KP) {
-    case 40: return tc_smem<40>() <= 227 * 1024;
-    case 56: return tc_smem<56>() <= 227 * 1024;
-    case 88: return tc_smem<88>() <= 227 * 1024;
-    case 120: return tc_smem<120>() <= 227 * 1024;
+    case 40: return tc_smem<24>() <= 227 * 1024;
+    case 56: return tc_smem<40>() <= 227 * 1024;
+    case 88: return tc_smem<48>() <= 227 * 1024;
+    case 120: return tc_smem<64>() <= 227 * 1024;
     default: return false;
     }
 }
@@ -958,10 +1089,10 @@ bool m2l_tc_supported(int KP)
 size_t m2l_tc_op_bytes(int KP)
 {
     switch (KP) {
-    case 40: return TcShape<40>::OP_BYTES;
-    case 56: return TcShape<56>::OP_BYTES;
-    case 88: return TcShape<88>::OP_BYTES;
-    case 120: return TcShape<120>::OP_BYTES;
+    case 40: return TcShape<24>::OP_BYTES;
+    case 56: return TcShape<40>::OP_BYTES;
+    case 88: return TcShape<48>::OP_BYTES;
+    case 120: return TcShape<64>::OP_BYTES;
     default: return 0;
     }
 }
@@ -969,10 +1100,10 @@ size_t m2l_tc_op_bytes(int KP)
 int m2l_tc_kt(int KP)
 {
     switch (KP) {
-    case 40: return TcShape<40>::KT;
-    case 56: return TcShape<56>::KT;
-    case 88: return TcShape<88>::KT;
-    case 120: return TcShape<120>::KT;
+    case 40: return TcShape<24>::KT;
+    case 56: return TcShape<40>::KT;
+    case 88: return TcShape<48>::KT;
+    case 120: return TcShape<64>::KT;
     default: return 0;
     }
 }
@@ -985,13 +1116,13 @@ void launch_m2l_tc_ops(int p, int KP, int L, int n_off, const Geom *g, const flo
     k_tc_scale<<<LCAP + 1, 128, 0, s>>>(p, KT, L, g, gk);
     if (n_off <= 0) return;
     const size_t smem = sizeof(float) * (size_t)ldD;
-#define M2LOPS(KPV)                                                                            \
+#define M2LOPS(KPV, KRV)                                                                       \
     case KPV:                                                                                  \
         note_launch();                                                                         \
-        k_m2l_ops<KPV><<<n_off, 256, smem, s>>>(p, D, ldD, it, Bop);                           \
+        k_m2l_ops<KRV><<<n_off, 256, smem, s>>>(p, KPV, D, ldD, it, Bop);                      \
         break;
     switch (KP) {
-        M2LOPS(40) M2LOPS(56) M2LOPS(88) M2LOPS(120)
+        M2LOPS(40, 24) M2LOPS(56, 40) M2LOPS(88, 48) M2LOPS(120, 64)
     default: break;
     }
 #undef M2LOPS
@@ -1046,33 +1177,32 @@ void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *
     const int stall = (sv && atoi(sv)) ? 1 : 0;
     const long long spin = stall ? (1ll << 12) : TC_SPIN;
     if (nitems > 0 && a_tmem) {
-#define M2LTCT(KPV)                                                                             \
+#define M2LTCT(KPV, KRV)                                                                        \
     case KPV: {                                                                                 \
-        typedef TcShape<KPV> S;                                                                 \
-        const long long nq = ncell * (S::KT / 4);                                               \
         note_launch();                                                                          \
-        k_q_split<KPV, false><<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(p, ncell, Q, gk, Qs); \
-        const int smem = TctShape<KPV>::SMEM;                                                   \
-        cudaFuncSetAttribute(k_m2l_tct<KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        k_q_fold<KRV, false><<<(unsigned)((ncell + QF_W - 1) / QF_W), 32 * QF_W, 0, s>>>(        \
+            p, KPV, ncell, Q, gk, Qs);                                                          \
+        const int smem = TctShape<KRV>::SMEM;                                                   \
+        cudaFuncSetAttribute(k_m2l_tct<KRV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
         note_launch();                                                                          \
-        k_m2l_tct<KPV><<<nitems, TC_THREADS, smem, s>>>(                                        \
+        k_m2l_tct<KRV><<<nitems, TC_THREADS, smem, s>>>(                                        \
             items, ent_u, ent_src, Qs, reinterpret_cast<const unsigned char *>(Bop), Ps, flags, \
             spin, stall);                                                                       \
     } break;
         switch (KP) {
-            M2LTCT(40) M2LTCT(56) M2LTCT(88) M2LTCT(120)
+            M2LTCT(40, 24) M2LTCT(56, 40) M2LTCT(88, 48) M2LTCT(120, 64)
         default: break;
         }
 #undef M2LTCT
     } else if (nitems > 0) {
-#define M2LTC(KPV)                                                                              \
+#define M2LTC(KPV, KRV)                                                                         \
     case KPV: {                                                                                 \
-        typedef TcShape<KPV> S;                                                                 \
-        const long long nq = ncell * (S::KT / 4);                                               \
+        typedef TcShape<KRV> S;                                                                 \
         note_launch();                                                                          \
-        k_q_split<KPV, true><<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(p, ncell, Q, gk, Qs); \
-        size_t smem = tc_smem<KPV>();                                                           \
-        auto kern = qmap ? k_m2l_tc<KPV, true> : k_m2l_tc<KPV, false>;                          \
+        k_q_fold<KRV, true><<<(unsigned)((ncell + QF_W - 1) / QF_W), 32 * QF_W, 0, s>>>(         \
+            p, KPV, ncell, Q, gk, Qs);                                                          \
+        size_t smem = tc_smem<KRV>();                                                           \
+        auto kern = qmap ? k_m2l_tc<KRV, true> : k_m2l_tc<KRV, false>;                          \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
         note_launch();                                                                          \
         kern<<<nitems, TC_THREADS, smem, s>>>(                                                  \
@@ -1080,12 +1210,12 @@ void launch_m2l_tc(int p, int KP, const Tile *tiles, int ntiles, const M2LItem *
             reinterpret_cast<const unsigned char *>(Bop), Ps, flags, spin, stall);              \
     } break;
         switch (KP) {
-            M2LTC(40) M2LTC(56) M2LTC(88) M2LTC(120)
+            M2LTC(40, 24) M2LTC(56, 40) M2LTC(88, 48) M2LTC(120, 64)
         default: break;
         }
 #undef M2LTC
     }
-    launch_m2l_reduce(p, KP, tiles, ntiles, tile_item0, tile_nitems, Ps, g, V, s);
+    launch_reduce_h(p, KP, tiles, ntiles, tile_item0, tile_nitems, Ps, g, V, s);
 }
 
 }  // namespace ccfmm
