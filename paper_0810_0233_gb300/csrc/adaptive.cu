@@ -800,16 +800,52 @@ __global__ void __launch_bounds__(32 * AW) k_am2m(int p, int KP, const int *cell
     }
 }
 
+// Completion of the harmonic reduction: for full column c the reduced
+// column (or -1), n_z, and for n_z >= 2 the full columns of n - 2e_z + 2e_x
+// and n - 2e_z + 2e_y (V_n = -V of those two).
+struct HarmTab {
+    int8_t red[KPMAX];
+    uint8_t nz[KPMAX], s1[KPMAX], s2[KPMAX];
+};
+
+__global__ void k_harm_tab(int p, HarmTab *ht)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= KPMAX) return;
+    const int K = nterms(p) - 1;
+    int r = -1, z = 0, a = 0, b = 0;
+    if (c < K) {
+        int nx, ny, nz;
+        midx_inv(c + 1, nx, ny, nz);
+        const int k = nx + ny + nz;
+        z = nz;
+        if (nz <= 1) {
+            r = k * k - 1 + nz * (2 * k + 3 - nz) / 2 + ny;
+        } else {
+            a = midx(nx + 2, ny, nz - 2) - 1;
+            b = midx(nx, ny + 2, nz - 2) - 1;
+        }
+    }
+    ht->red[c] = (int8_t)r;
+    ht->nz[c] = (uint8_t)z;
+    ht->s1[c] = (uint8_t)a;
+    ht->s2[c] = (uint8_t)b;
+}
+
 // L2L (Eq. taylorshift, FP64) into every cell of one level, one warp per
-// cell: V = the cell's own M2L sum + the parent's V shifted to the cell
-template <typename acc_t>
-__global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, const int *cells, int ncl,
-                                                  const int *smp, const int *lev, const int *par,
-                                                  const int4 *ic, const AGeom *geo,
-                                                  const ShiftTab *tb, const acc_t *VF, double *V)
+// cell: V = the cell's own M2L sum + the parent's V shifted to the cell.
+// RED: the M2L sum is the reduced accumulator (rows of KRP), completed to
+// all columns first.
+template <typename acc_t, bool RED>
+__global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, int KRP, const int *cells,
+                                                  int ncl, const int *smp, const int *lev,
+                                                  const int *par, const int4 *ic,
+                                                  const AGeom *geo, const ShiftTab *tb,
+                                                  const HarmTab *ht, const acc_t *VF, double *V)
 {
     __shared__ double fs[AW][PMAX + 1];
     __shared__ double vp[AW][KPMAX];
+    __shared__ double vm[AW][RED ? KPMAX : 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int idx = blockIdx.x * AW + w;
     if (idx >= ncl) return;
@@ -817,8 +853,21 @@ __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, const int *cell
     const int pr = par[c];
     const int K = nterms(p) - 1;
     const long long row = (long long)c * KP;
+    if (RED) {
+        for (int col = lane; col < K; col += 32) {
+            const int r = ht->red[col];
+            vm[w][col] = r >= 0 ? (double)VF[(long long)c * KRP + r] : 0.0;
+        }
+        __syncwarp();
+        for (int z = 2; z <= p; ++z) {
+            for (int col = lane; col < K; col += 32)
+                if (ht->nz[col] == z) vm[w][col] = -vm[w][ht->s1[col]] - vm[w][ht->s2[col]];
+            __syncwarp();
+        }
+    }
+    auto m2l = [&](int col) -> double { return RED ? vm[w][col] : (double)VF[row + col]; };
     if (pr < 0) {
-        for (int col = lane; col < KP; col += 32) V[row + col] = col < K ? (double)VF[row + col] : 0.0;
+        for (int col = lane; col < KP; col += 32) V[row + col] = col < K ? m2l(col) : 0.0;
         return;
     }
     const AGeom &g = geo[smp[c]];
@@ -838,7 +887,7 @@ __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, const int *cell
         const uint8_t *cl = tb->l2l_c[sx][col];
         double acc = 0.0;
         for (int t = 0; t < n; ++t) acc += fs[w][t] * vp[w][cl[t]];
-        V[row + col] = (double)VF[row + col] + acc;
+        V[row + col] = m2l(col) + acc;
     }
 }
 
@@ -996,6 +1045,10 @@ struct ccfmm_adaptive_s {
     int nd = 0, n64 = 0, n16 = 0;
     ABuf pt, ps, sep, rpow, D, it64, it16, fdense, fst, fq, fval, itab;
     ABuf Q, VF, V, shift;
+    // harmonic reduction of the FP32 tensor-core M2L
+    bool red = false;
+    int KRP = 0;
+    ABuf Qr, VFr, itr, harm;
     // ensemble step
     ABuf prm;
     RotateParams *hprm = nullptr;
@@ -1328,6 +1381,17 @@ template <typename real> ccfmm_status build_m2l(ccfmm_adaptive_t h, ABuf &stemp)
     ATRY(aalloc(h->shift, sizeof(ShiftTab)));
     note_launch();
     k_shift_tab<<<1, KPMAX, 0, s>>>(h->p, AP<ShiftTab>(h->shift));
+    h->red = sizeof(real) == 4 && h->maxdeg >= 2 * h->p && am2l_mma_ok(h->p);
+    ATRY(aalloc(h->harm, sizeof(HarmTab)));
+    note_launch();
+    k_harm_tab<<<1, KPMAX, 0, s>>>(h->p, AP<HarmTab>(h->harm));
+    if (h->red) {
+        h->KRP = red_padded(h->p);
+        ATRY(aalloc(h->itr, sizeof(uint16_t) * h->KRP * h->KRP));
+        launch_itable_red(h->p, h->KP, h->KRP, AP<uint16_t>(h->itab), AP<uint16_t>(h->itr), s);
+        ATRY(aalloc(h->Qr, sizeof(float) * (size_t)h->nc * h->KRP));
+        ATRY(aalloc(h->VFr, sizeof(float) * (size_t)h->nc * h->KRP));
+    }
     const size_t cells = (size_t)h->nc * h->KP;
     ATRY(aalloc(h->Q, sizeof(real) * cells));
     ATRY(aalloc(h->VF, sizeof(real) * cells));
@@ -1385,24 +1449,42 @@ template <typename real> void enqueue_eval(ccfmm_adaptive_t h, bool rotate)
             AP<real>(h->Q));
         ++k;
     }
-    cudaMemsetAsync(h->VF.p, 0, sizeof(real) * (size_t)h->nc * h->KP, sf);
-    launch_am2l<real>(h->p, h->KP, AP<int4>(h->it64), h->n64, 64, AP<int>(h->pt), AP<int>(h->ps),
-                      AP<double4>(h->sep), AP<float>(h->rpow), AP<real>(h->D), h->ldD,
-                      AP<uint16_t>(h->itab),
-                      h->maxdeg, AP<real>(h->Q), AP<real>(h->VF), sf);
-    launch_am2l<real>(h->p, h->KP, AP<int4>(h->it16), h->n16, 16, AP<int>(h->pt), AP<int>(h->ps),
-                      AP<double4>(h->sep), AP<float>(h->rpow), AP<real>(h->D), h->ldD,
-                      AP<uint16_t>(h->itab),
-                      h->maxdeg, AP<real>(h->Q), AP<real>(h->VF), sf);
+    if (h->red) {
+        launch_afold(h->p, h->KP, h->KRP, h->nc, AP<float>(h->Q), AP<float>(h->Qr), sf);
+        ++k;
+        cudaMemsetAsync(h->VFr.p, 0, sizeof(float) * (size_t)h->nc * h->KRP, sf);
+        launch_am2l_red(h->p, h->KRP, AP<int4>(h->it64), h->n64, 64, AP<int>(h->pt),
+                        AP<int>(h->ps), AP<float>(h->rpow), AP<float>(h->D), h->ldD,
+                        AP<uint16_t>(h->itr), AP<float>(h->Qr), AP<float>(h->VFr), sf);
+        launch_am2l_red(h->p, h->KRP, AP<int4>(h->it16), h->n16, 16, AP<int>(h->pt),
+                        AP<int>(h->ps), AP<float>(h->rpow), AP<float>(h->D), h->ldD,
+                        AP<uint16_t>(h->itr), AP<float>(h->Qr), AP<float>(h->VFr), sf);
+    } else {
+        cudaMemsetAsync(h->VF.p, 0, sizeof(real) * (size_t)h->nc * h->KP, sf);
+        launch_am2l<real>(h->p, h->KP, AP<int4>(h->it64), h->n64, 64, AP<int>(h->pt),
+                          AP<int>(h->ps), AP<double4>(h->sep), AP<float>(h->rpow), AP<real>(h->D),
+                          h->ldD, AP<uint16_t>(h->itab), h->maxdeg, AP<real>(h->Q),
+                          AP<real>(h->VF), sf);
+        launch_am2l<real>(h->p, h->KP, AP<int4>(h->it16), h->n16, 16, AP<int>(h->pt),
+                          AP<int>(h->ps), AP<double4>(h->sep), AP<float>(h->rpow), AP<real>(h->D),
+                          h->ldD, AP<uint16_t>(h->itab), h->maxdeg, AP<real>(h->Q),
+                          AP<real>(h->VF), sf);
+    }
     k += (h->n64 > 0) + (h->n16 > 0);
     for (int l = 0; l <= h->maxL; ++l) {
         const int ncl = h->lvl_off[l + 1] - h->lvl_off[l];
         if (ncl == 0) continue;
         note_launch();
-        k_al2l<real><<<nblk(ncl, AW), 32 * AW, 0, sf>>>(
-            h->p, h->KP, AP<int>(h->lvl_cells) + h->lvl_off[l], ncl, AP<int>(h->smp),
-            AP<int>(h->lev), AP<int>(h->par), AP<int4>(h->ic), AP<AGeom>(h->geo),
-            AP<ShiftTab>(h->shift), AP<real>(h->VF), AP<double>(h->V));
+        if (h->red)
+            k_al2l<float, true><<<nblk(ncl, AW), 32 * AW, 0, sf>>>(
+                h->p, h->KP, h->KRP, AP<int>(h->lvl_cells) + h->lvl_off[l], ncl, AP<int>(h->smp),
+                AP<int>(h->lev), AP<int>(h->par), AP<int4>(h->ic), AP<AGeom>(h->geo),
+                AP<ShiftTab>(h->shift), AP<HarmTab>(h->harm), AP<float>(h->VFr), AP<double>(h->V));
+        else
+            k_al2l<real, false><<<nblk(ncl, AW), 32 * AW, 0, sf>>>(
+                h->p, h->KP, h->KP, AP<int>(h->lvl_cells) + h->lvl_off[l], ncl, AP<int>(h->smp),
+                AP<int>(h->lev), AP<int>(h->par), AP<int4>(h->ic), AP<AGeom>(h->geo),
+                AP<ShiftTab>(h->shift), AP<HarmTab>(h->harm), AP<real>(h->VF), AP<double>(h->V));
         ++k;
     }
     if (h->overlap) {
@@ -1481,7 +1563,7 @@ void fmm_adaptive_destroy(ccfmm_adaptive_t h)
                     &h->ic, &h->cen, &h->leaves, &h->lvl_cells, &h->near_first, &h->near_num,
                     &h->near_src, &h->far_t, &h->far_s, &h->pt, &h->ps, &h->sep, &h->rpow, &h->D, &h->it64,
                     &h->it16, &h->fdense, &h->fst, &h->fq, &h->fval, &h->itab, &h->Q, &h->VF,
-                    &h->V, &h->shift, &h->prm};
+                    &h->V, &h->shift, &h->Qr, &h->VFr, &h->itr, &h->harm, &h->prm};
     for (ABuf *b : bufs) afree(*b);
     if (h->hprm) cudaFreeHost(h->hprm);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);

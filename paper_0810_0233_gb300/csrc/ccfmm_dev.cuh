@@ -56,6 +56,24 @@ __host__ __device__ inline int m2l_kend(int p, int maxdeg, int n)
     return r >= p ? K : nterms(r) - 1;
 }
 
+// Harmonic reduction of the M2L contraction (the D tensors satisfy Laplace's
+// equation): per order k the 2k + 1 multi-indices with n_z <= 1, the first
+// 2k + 1 of the order in the library's order; reduced column r of order k
+// (k^2 - 1 <= r < (k+1)^2 - 1) is full column T(k-1) - 1 + r - (k^2 - 1).
+__host__ __device__ constexpr int red_count(int p) { return (p + 1) * (p + 1) - 1; }
+inline int red_padded(int p) { return ((red_count(p) + 7) / 8) * 8; }
+__host__ __device__ inline int red_order(int r)
+{
+    int k = 1;
+    while ((k + 1) * (k + 1) - 1 <= r) ++k;
+    return k;
+}
+__host__ __device__ inline int red_full(int r)
+{
+    const int k = red_order(r);
+    return nterms(k - 1) - 1 + r - (k * k - 1);
+}
+
 template <typename T> struct vec4;
 template <> struct vec4<float> { typedef float4 t; };
 template <> struct vec4<double> { typedef double4 t; };
@@ -395,6 +413,17 @@ template <typename real>
 void launch_am2l(int p, int KP, const int4 *items, int nitems, int ap, const int *pt,
                  const int *ps, const double4 *sep, const float *rpow, const real *D, int ldD,
                  const uint16_t *it, int maxdeg, const real *Q, real *VF, cudaStream_t s);
+// adaptive M2L over the harmonic reduction (FP32, p <= 6, tensor cores):
+// moments folded into reduced rows (KRP = red_padded(p) floats), the reduced
+// index table from the full one, and the contraction into a reduced
+// accumulator VFr[cell][KRP]
+bool am2l_mma_ok(int p);
+void launch_afold(int p, int KPF, int KRP, int nc, const float *Q, float *Qr, cudaStream_t s);
+void launch_itable_red(int p, int KPF, int KRP, const uint16_t *it, uint16_t *itr,
+                       cudaStream_t s);
+void launch_am2l_red(int p, int KRP, const int4 *items, int nitems, int ap, const int *pt,
+                     const int *ps, const float *rpow, const float *D, int ldD,
+                     const uint16_t *itr, const float *Qr, float *VFr, cudaStream_t s);
 // smooth field of every leaf cell added to H (after launch_ap2p with V null)
 template <typename real>
 void launch_al2p(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,

@@ -603,6 +603,9 @@ static void am2l_dispatch(int p, int KP, const int4 *items, int nitems, const in
 //          warps take the item's 16-pair chunks in turn.
 //   SMALL: one item per warp (groups of at most 16 pairs): B fragments are
 //          formed from the D row as they are used.
+// The contraction runs over the harmonic reduction (moments folded by the
+// Laplace identity of the D tensors, (p+1)^2 - 1 columns on either side):
+// Q rows, the index table and the accumulator VF are the reduced ones.
 // Fragment layouts (PTX ISA, mma.m16n8k8 with .tf32): g = lane / 4,
 // t = lane % 4; A: a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4);
 // B: b0 (k = t, n = g), b1 (k = t + 4, n = g); C: c0 (g, 2t), c1 (g, 2t + 1),
@@ -633,17 +636,17 @@ __device__ __forceinline__ void red_add2(float *p, float a, float b)
 }
 
 // scale tables of one item from its row of rho^-d (d = 0 .. p + 1, formed in
-// FP64 at the build): gk[c] = rho^-|k|, en[c] = (-1)^|n| rho^-(|n|+1) (zero
-// beyond K); threads tid0.. step nth
+// FP64 at the build), over the reduced columns: gk[c] = rho^-|k|,
+// en[c] = (-1)^|n| rho^-(|n|+1) (zero beyond the reduced count); threads
+// tid0.. step nth
 __device__ __forceinline__ void am2l_scales(int p, int KP, const float *pw, float *gk,
                                             float *en, int tid0, int nth)
 {
-    const int K = nterms(p) - 1;
+    const int K = red_count(p);
     for (int c = tid0; c < KP; c += nth) {
         float gv = 0.f, ev = 0.f;
         if (c < K) {
-            int d = 1;
-            while (nterms(d) <= c + 1) ++d;
+            const int d = red_order(c);
             gv = pw[d];
             ev = (d & 1) ? -pw[d + 1] : pw[d + 1];
         }
@@ -843,14 +846,81 @@ static void run_am2l_mma(int p, const int4 *items, int nitems, bool big, const i
 
 // the tensor-core form serves the FP32 path for p <= 6 (the split operator
 // of one item fits shared memory) unless CCFMM_AM2L=fma
-static bool am2l_use_mma(int KP)
+bool am2l_mma_ok(int p)
 {
     static int env = -1;
     if (env < 0) {
         const char *e = getenv("CCFMM_AM2L");
         env = (e && strcmp(e, "fma") == 0) ? 0 : 1;
     }
-    return env == 1 && KP <= 88;
+    return env == 1 && p <= 6;
+}
+
+// folds every cell's moments (rows of KPF floats) into the reduced rows of
+// KRP floats (zero padding), one warp per cell
+constexpr int AF_W = 8;
+__global__ void __launch_bounds__(32 * AF_W) k_afold(int p, int KPF, int KRP, int nc,
+                                                     const float *Q, float *Qr)
+{
+    __shared__ float row[AF_W][((nterms(PMAX) - 1 + 7) / 8) * 8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long c = (long long)blockIdx.x * AF_W + w;
+    if (c >= nc) return;
+    const int K = nterms(p) - 1, KR = red_count(p);
+    for (int j = lane; j < K; j += 32) row[w][j] = Q[c * KPF + j];
+    __syncwarp();
+    if (lane >= 1 && lane < p) {
+        const int k = lane + 1, base = nterms(k - 1) - 1;
+        for (int z = k; z >= 2; --z)
+            for (int y = 0; y <= k - z; ++y) {
+                const float v = row[w][base + z * (2 * k + 3 - z) / 2 + y];
+                const int zt = z - 2, lt = base + zt * (2 * k + 3 - zt) / 2;
+                row[w][lt + y] -= v;      // (x + 2, y, z - 2)
+                row[w][lt + y + 2] -= v;  // (x, y + 2, z - 2)
+            }
+    }
+    __syncwarp();
+    for (int r = lane; r < KRP; r += 32) Qr[c * KRP + r] = r < KR ? row[w][red_full(r)] : 0.f;
+}
+
+// the reduced index table from the full one: itr[k][n] = it[full k][full n]
+// (the zero column beyond the reduced count)
+__global__ void k_itable_red(int p, int KPF, int KRP, const uint16_t *it, uint16_t *itr)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= KRP * KRP) return;
+    const int k = j / KRP, n = j - k * KRP, KR = red_count(p);
+    itr[j] = (k < KR && n < KR) ? it[red_full(k) * KPF + red_full(n)] : it[(KPF - 1) * KPF + KPF - 1];
+}
+
+void launch_afold(int p, int KPF, int KRP, int nc, const float *Q, float *Qr, cudaStream_t s)
+{
+    if (nc <= 0) return;
+    note_launch();
+    k_afold<<<(unsigned)((nc + AF_W - 1) / AF_W), 32 * AF_W, 0, s>>>(p, KPF, KRP, nc, Q, Qr);
+}
+
+void launch_itable_red(int p, int KPF, int KRP, const uint16_t *it, uint16_t *itr, cudaStream_t s)
+{
+    note_launch();
+    k_itable_red<<<(KRP * KRP + 255) / 256, 256, 0, s>>>(p, KPF, KRP, it, itr);
+}
+
+// reduced contraction on the tensor cores (FP32): KRP the reduced width
+void launch_am2l_red(int p, int KRP, const int4 *items, int nitems, int ap, const int *pt,
+                     const int *ps, const float *rpow, const float *D, int ldD,
+                     const uint16_t *itr, const float *Qr, float *VFr, cudaStream_t s)
+{
+    if (nitems <= 0) return;
+    const bool big = ap == 64;
+    switch (KRP) {
+    case 8: run_am2l_mma<8>(p, items, nitems, big, pt, ps, rpow, D, ldD, itr, Qr, VFr, s); break;
+    case 16: run_am2l_mma<16>(p, items, nitems, big, pt, ps, rpow, D, ldD, itr, Qr, VFr, s); break;
+    case 24: run_am2l_mma<24>(p, items, nitems, big, pt, ps, rpow, D, ldD, itr, Qr, VFr, s); break;
+    case 40: run_am2l_mma<40>(p, items, nitems, big, pt, ps, rpow, D, ldD, itr, Qr, VFr, s); break;
+    case 48: run_am2l_mma<48>(p, items, nitems, big, pt, ps, rpow, D, ldD, itr, Qr, VFr, s); break;
+    default: break;
+    }
 }
 
 template <typename real>
@@ -858,22 +928,8 @@ void launch_am2l(int p, int KP, const int4 *items, int nitems, int ap, const int
                  const int *ps, const double4 *sep, const float *rpow, const real *D, int ldD,
                  const uint16_t *it, int maxdeg, const real *Q, real *VF, cudaStream_t s)
 {
+    (void)rpow;
     if (nitems <= 0) return;
-    if (sizeof(real) == 4 && rpow && maxdeg >= 2 * p && am2l_use_mma(KP)) {
-        const float *Df = reinterpret_cast<const float *>(D);
-        const float *Qf = reinterpret_cast<const float *>(Q);
-        float *Vf = reinterpret_cast<float *>(VF);
-        const bool big = ap == 64;
-        switch (KP) {
-        case 8: run_am2l_mma<8>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
-        case 16: run_am2l_mma<16>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
-        case 24: run_am2l_mma<24>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
-        case 40: run_am2l_mma<40>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
-        case 56: run_am2l_mma<56>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
-        case 88: run_am2l_mma<88>(p, items, nitems, big, pt, ps, rpow, Df, ldD, it, Qf, Vf, s); return;
-        default: break;
-        }
-    }
     if (ap == 64)
         am2l_dispatch<real, 64>(p, KP, items, nitems, pt, ps, sep, D, ldD, it, maxdeg, Q, VF, s);
     else

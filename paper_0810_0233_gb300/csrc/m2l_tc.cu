@@ -70,8 +70,8 @@ namespace ccfmm {
 constexpr int TC_M = 128;       // field cells per tile (MMA M = TMEM lanes)
 constexpr int TC_KC = 32;       // K per unit: 4 MMA k-steps of 8
 constexpr int TC_SMEM = 227 * 1024;
-// at most this many pipeline stages (3 leaves room on the SM for a block of
-// the near-field kernel running concurrently)
+// at most this many pipeline stages (as many as fit, 3 at least; 3 leaves
+// room on the SM for a block of the near-field kernel running concurrently)
 #ifndef CCFMM_TC_MAXST
 #define CCFMM_TC_MAXST 4
 #endif
@@ -94,7 +94,8 @@ template <int KP> struct TcShape {
     static constexpr int OP_BYTES = NCH * 2 * B_BYTES;            // one offset class
     // pipeline stages that fit (at most 4), and how many units a producer
     // keeps in flight before marking the oldest one full
-    static constexpr int ST = (TC_SMEM - 2048) / STAGE >= 4 && CCFMM_TC_MAXST >= 4 ? 4 : 3;
+    static constexpr int FIT = (TC_SMEM - 2048) / STAGE;
+    static constexpr int ST = FIT < CCFMM_TC_MAXST ? (FIT < 3 ? 3 : FIT) : CCFMM_TC_MAXST;
     static constexpr int LAG = ST - 1;
     static constexpr int TMEM_COLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256);
 };
@@ -113,18 +114,6 @@ template <int KP> struct TcShape {
 constexpr int tc_red_kp(int KP)
 {
     return KP == 40 ? 24 : KP == 56 ? 40 : KP == 88 ? 48 : KP == 120 ? 64 : 0;
-}
-__host__ __device__ constexpr int red_count(int p) { return (p + 1) * (p + 1) - 1; }
-__device__ __forceinline__ int red_order(int r)
-{
-    int k = 1;
-    while ((k + 1) * (k + 1) - 1 <= r) ++k;
-    return k;
-}
-__device__ __forceinline__ int red_full(int r)
-{
-    const int k = red_order(r);
-    return nterms(k - 1) - 1 + r - (k * k - 1);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -471,7 +460,7 @@ __device__ __forceinline__ void m2l_tc_body(const M2LItem *items, const int *ent
     typedef TcShape<KP> S;
     extern __shared__ __align__(1024) unsigned char smraw[];
     constexpr int TC_ST = S::ST;
-    __shared__ __align__(8) unsigned long long bar_full[4], bar_b[4], bar_empty[4];
+    __shared__ __align__(8) unsigned long long bar_full[TC_ST], bar_b[TC_ST], bar_empty[TC_ST];
     __shared__ __align__(8) unsigned long long bar_done;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
