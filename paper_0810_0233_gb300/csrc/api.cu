@@ -168,7 +168,7 @@ struct ccfmm_s {
     DevBuf geomd, box6, userbox, partial, rb;
     DevBuf leaf_start, A, B, H;
     DevBuf cube, nl, neA, neB, cflag, crank, oflag, orank, tkeys, tseg;
-    DevBuf far, far_off, far_num, tiles, tcount, tstart, ent_u, ent_src;
+    DevBuf far, far_off, far_num, tiles, tcount, tstart, ent_u, ent_src, tbm, twp;
     DevBuf offs, fst, fq, fval, fdense, D, itab, Q, V;
     DevBuf Hout, epart, items, titem0, tnitems, Ps;
     DevBuf Qs, Bop, gkt;  // tensor-core M2L: split moments, operators, level scales
@@ -668,8 +668,12 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     if (h->ntiles) {
         CK(cudaMemcpyAsync(h->tiles.p, tiles.data(), sizeof(Tile) * tiles.size(),
                            cudaMemcpyHostToDevice, s));
+        const size_t tw = (size_t)h->ntiles * ((h->max_bits + 31) / 32);
+        TRY(ensure(h->tbm, sizeof(unsigned) * tw));
+        TRY(ensure(h->twp, sizeof(unsigned) * tw));
         launch_tile_count(P<Tile>(h->tiles), h->ntiles, P<int>(h->far_off), P<int>(h->far_num),
-                          P<FarEnt>(h->far), h->max_bits, P<int>(h->tcount), s);
+                          P<FarEnt>(h->far), h->max_bits, P<unsigned>(h->tbm),
+                          P<unsigned>(h->twp), P<int>(h->tcount), s);
         scan_exclusive(P<int>(h->tcount), P<int>(h->tstart), h->ntiles, &drb->ent_total,
                        h->scantemp.p, s);
         CK(cudaMemcpyAsync(P<int>(h->tstart) + h->ntiles, &drb->ent_total, sizeof(int),
@@ -733,9 +737,13 @@ static ccfmm_status build(ccfmm_t h, const double *positions, const double *mome
     if (h->ev_ok) CK(cudaEventRecord(h->evb[EV_BS4], s));
     TRY(ensure(h->ent_u, sizeof(int) * std::max(h->ent_total, 1ll)));
     TRY(ensure(h->ent_src, sizeof(int) * (size_t)TT * std::max(h->ent_total, 1ll)));
+    // every partner slot starts as -1 (no partner): one memset at full bandwidth
+    if (h->ent_total > 0)
+        CK(cudaMemsetAsync(h->ent_src.p, 0xff, sizeof(int) * (size_t)TT * h->ent_total, s));
     if (h->ntiles)
         launch_tile_fill(P<Tile>(h->tiles), h->ntiles, P<int>(h->tstart), P<int>(h->far_off),
-                         P<int>(h->far_num), P<FarEnt>(h->far), h->max_bits, P<int>(h->dmap),
+                         P<int>(h->far_num), P<FarEnt>(h->far), h->max_bits,
+                         P<unsigned>(h->tbm), P<unsigned>(h->twp), P<int>(h->dmap),
                          P<int>(h->ent_u), P<int>(h->ent_src), s);
 
     TRY(ensure(h->Q, rs * (size_t)ncellp * h->KP));
@@ -1234,7 +1242,7 @@ void fmm_destroy(ccfmm_t h)
                       &h->partial, &h->rb, &h->leaf_start, &h->A, &h->B, &h->H, &h->cube,
                       &h->nl, &h->neA, &h->neB, &h->cflag, &h->crank, &h->oflag, &h->orank,
                       &h->tkeys, &h->tseg,
-                      &h->far, &h->far_off, &h->far_num, &h->tiles, &h->tcount, &h->tstart,
+                      &h->far, &h->far_off, &h->far_num, &h->tiles, &h->tcount, &h->tstart, &h->tbm, &h->twp,
                       &h->ent_u, &h->ent_src, &h->offs, &h->fst, &h->fq, &h->fval, &h->fdense,
                       &h->D, &h->itab, &h->Q, &h->V, &h->Hout, &h->epart, &h->items,
                       &h->titem0, &h->tnitems, &h->Ps, &h->Qs, &h->Bop, &h->gkt, &h->dmap,

@@ -214,12 +214,18 @@ void launch_list_level(int level, const int *leaf_start, int L, const int *rank,
                        int NB, NearEnt *near_out, long long far_base, int FB, FarEnt *far_out,
                        int *far_off, int *far_num, int *near_total, int *far_total, int *d_flags,
                        cudaStream_t s);
+// per tile: the number of distinct far offsets; its offset bitmap and the
+// prefix of the bitmap words' popcounts are stored (nwmax = (max_bits + 31)
+// / 32 words a tile) for the fill
 void launch_tile_count(const Tile *tiles, int ntiles, const int *far_off, const int *far_num,
-                       const FarEnt *far, int max_bits, int *counts, cudaStream_t s);
-// entries get the D table of their offset class (dmap[class])
+                       const FarEnt *far, int max_bits, unsigned *gbm, unsigned *gwp, int *counts,
+                       cudaStream_t s);
+// entries get the D table of their offset class (dmap[class]); ent_src must
+// hold -1 in every slot beforehand
 void launch_tile_fill(Tile *tiles, int ntiles, const int *ent_start, const int *far_off,
-                      const int *far_num, const FarEnt *far, int max_bits, const int *dmap,
-                      int *ent_u, int *ent_src, cudaStream_t s);
+                      const int *far_num, const FarEnt *far, int max_bits, const unsigned *gbm,
+                      const unsigned *gwp, const int *dmap, int *ent_u, int *ent_src,
+                      cudaStream_t s);
 
 // ------------------------------------------------------------------ expand.cu
 size_t ftable_scratch_bytes(int order);

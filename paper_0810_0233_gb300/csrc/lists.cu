@@ -59,86 +59,101 @@ __device__ __forceinline__ int warp_excl(int v, int lane, int *total)
 // near_total / far_total for the statistics.  The order of a cell's entries,
 // (parent entry, child bit), is the same as the oracle's recursion visits
 // them and does not depend on the launch.
-__global__ void k_list_level(int lv, const int *leaf_start, int L, const int *rank, int2 *nl,
-                             const NearEnt *near_prev, const int *cube, OffsetCube ci, int axis,
-                             int NB, NearEnt *near_out, long long far_base, int FB,
-                             FarEnt *far_out, int *far_off, int *far_num, int *near_total,
-                             int *far_total, int *flags)
+__global__ void __launch_bounds__(256) k_list_level(
+    int lv, const int *leaf_start, int L, const int *rank, int2 *nl, const NearEnt *near_prev,
+    const int *cube, OffsetCube ci, int axis, int NB, NearEnt *near_out, long long far_base,
+    int FB, FarEnt *far_out, int *far_off, int *far_num, int *near_total, int *far_total,
+    int *flags)
 {
+    __shared__ int s_tot[2];
+    if (threadIdx.x < 2) s_tot[threadIdx.x] = 0;
+    __syncthreads();
     const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const long long nc = 1ll << lv;
-    if (c >= nc) return;
     const long long hid = nc + c;
-    if (cell_count(leaf_start, L, lv, c) == 0) {
+    if (c < nc && cell_count(leaf_start, L, lv, c) == 0) {
         if (lane == 0) {
             nl[hid] = make_int2(0, 0);
             far_off[hid] = 0;
             far_num[hid] = 0;
         }
-        return;
-    }
-    const long long r = rank[hid] - rank[nc];
-    const long long nbase0 = r * NB, fbase0 = far_base + r * FB;
-    const int2 pl = nl[hid >> 1];
-    const int bc = (int)(c & 1);
-    const int e0 = pl.x, e1 = pl.x + pl.y;
-    long long nbase = nbase0, fbase = fbase0;
-    const long long nend = nbase0 + NB, fend = fbase0 + FB;
-    for (int eb = e0; eb < e1; eb += 32) {
-        const int e = eb + lane;
-        NearEnt out_n[2];
-        FarEnt out_f[2];
-        int nn = 0, nf = 0;
-        if (e < e1) {
-            const NearEnt ne = near_prev[e];
-            for (int ba = 0; ba < 2; ++ba) {
-                const long long a = 2ll * ne.src + ba;
-                if (cell_count(leaf_start, L, lv, a) == 0) continue;
-                int o[3] = {ne.ox, ne.oy, ne.oz};
-                o[axis] = 2 * o[axis] + bc - ba;
-                const int cls = cube_class(cube, ci, o, flags);
-                if (cls == OFF_NEAR) {
-                    out_n[nn].src = (int)a;
-                    out_n[nn].ox = o[0];
-                    out_n[nn].oy = o[1];
-                    out_n[nn].oz = o[2];
-                    ++nn;
-                } else if (cls >= 0) {
-                    out_f[nf].src = (int)a;
-                    out_f[nf].gid = cls;
-                    ++nf;
+    } else if (c < nc) {
+        const long long r = rank[hid] - rank[nc];
+        const long long nbase0 = r * NB, fbase0 = far_base + r * FB;
+        const int2 pl = nl[hid >> 1];
+        const int bc = (int)(c & 1);
+        const int e0 = pl.x, e1 = pl.x + pl.y;
+        long long nbase = nbase0, fbase = fbase0;
+        const long long nend = nbase0 + NB, fend = fbase0 + FB;
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int e = eb + lane;
+            // up to two near and two far results per lane, in registers
+            NearEnt n0{}, n1{};
+            FarEnt f0{}, f1{};
+            int nn = 0, nf = 0;
+            if (e < e1) {
+                const NearEnt ne = near_prev[e];
+#pragma unroll
+                for (int ba = 0; ba < 2; ++ba) {
+                    const long long a = 2ll * ne.src + ba;
+                    if (cell_count(leaf_start, L, lv, a) == 0) continue;
+                    int o[3] = {ne.ox, ne.oy, ne.oz};
+                    const int d = bc - ba;
+                    o[0] = axis == 0 ? 2 * o[0] + d : o[0];
+                    o[1] = axis == 1 ? 2 * o[1] + d : o[1];
+                    o[2] = axis == 2 ? 2 * o[2] + d : o[2];
+                    const int cls = cube_class(cube, ci, o, flags);
+                    if (cls == OFF_NEAR) {
+                        const NearEnt x{(int)a, o[0], o[1], o[2]};
+                        if (nn == 0) n0 = x; else n1 = x;
+                        ++nn;
+                    } else if (cls >= 0) {
+                        const FarEnt x{(int)a, cls};
+                        if (nf == 0) f0 = x; else f1 = x;
+                        ++nf;
+                    }
                 }
             }
+            int tn, tf;
+            const int pn = warp_excl(nn, lane, &tn);
+            const int pf = warp_excl(nf, lane, &tf);
+            if (nn > 0) {
+                const long long at = nbase + pn;
+                if (at + nn <= nend) {
+                    near_out[at] = n0;
+                    if (nn > 1) near_out[at + 1] = n1;
+                } else {
+                    atomicOr(flags, FLAG_LIST_OVERFLOW);
+                }
+            }
+            if (nf > 0) {
+                const long long at = fbase + pf;
+                if (at + nf <= fend) {
+                    far_out[at] = f0;
+                    if (nf > 1) far_out[at + 1] = f1;
+                } else {
+                    atomicOr(flags, FLAG_LIST_OVERFLOW);
+                }
+            }
+            nbase += tn;
+            fbase += tf;
         }
-        int tn, tf;
-        const int pn = warp_excl(nn, lane, &tn);
-        const int pf = warp_excl(nf, lane, &tf);
-        for (int j = 0; j < nn; ++j) {
-            const long long at = nbase + pn + j;
-            if (at < nend)
-                near_out[at] = out_n[j];
-            else
-                atomicOr(flags, FLAG_LIST_OVERFLOW);
+        if (lane == 0) {
+            const int tn = (int)min(nbase - nbase0, (long long)NB);
+            const int tf = (int)min(fbase - fbase0, (long long)FB);
+            nl[hid] = make_int2((int)nbase0, tn);
+            far_off[hid] = (int)fbase0;
+            far_num[hid] = tf;
+            atomicAdd(&s_tot[0], tn);
+            atomicAdd(&s_tot[1], tf);
         }
-        for (int j = 0; j < nf; ++j) {
-            const long long at = fbase + pf + j;
-            if (at < fend)
-                far_out[at] = out_f[j];
-            else
-                atomicOr(flags, FLAG_LIST_OVERFLOW);
-        }
-        nbase += tn;
-        fbase += tf;
     }
-    if (lane == 0) {
-        const int tn = (int)min(nbase - nbase0, (long long)NB);
-        const int tf = (int)min(fbase - fbase0, (long long)FB);
-        nl[hid] = make_int2((int)nbase0, tn);
-        far_off[hid] = (int)fbase0;
-        far_num[hid] = tf;
-        atomicAdd(near_total, tn);
-        atomicAdd(far_total, tf);
+    // one global addition per block for the level totals
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_tot[0]) atomicAdd(near_total, s_tot[0]);
+        if (s_tot[1]) atomicAdd(far_total, s_tot[1]);
     }
 }
 
@@ -179,44 +194,24 @@ __device__ __forceinline__ void tile_bitmap(const Tile &t, const int *far_off, c
     __syncthreads();
 }
 
+// counts[tile] = distinct far offsets among the tile's targets; the tile's
+// offset bitmap and the exclusive prefix of its words' popcounts go to
+// gbm / gwp (nwmax words a tile) for the fill
 __global__ void __launch_bounds__(TL_T) k_tile_count(const Tile *tiles, const int *far_off,
                                                      const int *far_num, const FarEnt *far,
+                                                     int nwmax, unsigned *gbm, unsigned *gwp,
                                                      int *counts)
-{
-    extern __shared__ unsigned bm[];
-    __shared__ int red[TL_T / 32];
-    Tile t = tiles[blockIdx.x];
-    int nwords = (t.nbits + 31) / 32;
-    tile_bitmap(t, far_off, far_num, far, bm, nwords);
-    int c = 0;
-    for (int w = threadIdx.x; w < nwords; w += blockDim.x) c += __popc(bm[w]);
-    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int w = 0; w < TL_T / 32; ++w) s += red[w];
-        counts[blockIdx.x] = s;
-    }
-}
-
-__global__ void __launch_bounds__(TL_T) k_tile_fill(const Tile *tiles, const int *ent_start,
-                                                    const int *far_off, const int *far_num,
-                                                    const FarEnt *far, const int *dmap, int *ent_u,
-                                                    int *ent_src)
 {
     extern __shared__ unsigned bm[];
     __shared__ int sm[32];
     Tile t = tiles[blockIdx.x];
-    int nwords = (t.nbits + 31) / 32;
-    unsigned *wpre = bm + nwords;
+    const int nwords = (t.nbits + 31) / 32;
     tile_bitmap(t, far_off, far_num, far, bm, nwords);
-    // exclusive prefix of the popcounts over the bitmap words
-    int per = (nwords + TL_T - 1) / TL_T;
-    int w0 = threadIdx.x * per;
+    const int per = (nwords + TL_T - 1) / TL_T;
+    const int w0 = threadIdx.x * per;
     int local = 0;
     for (int w = w0; w < w0 + per && w < nwords; ++w) local += __popc(bm[w]);
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int x = local;
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -234,60 +229,80 @@ __global__ void __launch_bounds__(TL_T) k_tile_fill(const Tile *tiles, const int
     }
     __syncthreads();
     int run = (warp ? sm[warp - 1] : 0) + x - local;
+    unsigned *obm = gbm + (long long)blockIdx.x * nwmax, *owp = gwp + (long long)blockIdx.x * nwmax;
     for (int w = w0; w < w0 + per && w < nwords; ++w) {
-        wpre[w] = (unsigned)run;
+        obm[w] = bm[w];
+        owp[w] = (unsigned)run;
         run += __popc(bm[w]);
     }
-    __syncthreads();
-    int start = ent_start[blockIdx.x];
-    int count = ent_start[blockIdx.x + 1] - start;
-    for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
-        unsigned b = bm[w];
-        int r = (int)wpre[w];
-        while (b) {
-            int bit = __ffs(b) - 1;
-            ent_u[start + r] = dmap[t.gid_base + w * 32 + bit];  // D table of the class
-            ++r;
-            b &= b - 1;
+    if (threadIdx.x == 0) counts[blockIdx.x] = sm[TL_T / 32 - 1];
+}
+
+// Entries of every tile from its stored bitmap: entry j of the tile is its
+// j-th present offset (D table ent_u) with the partner of each target
+// (ent_src, -1 beforehand); blockIdx.y takes targets 32 y .. 32 y + 31
+constexpr int TF_SPLIT = TT / 32;
+__global__ void __launch_bounds__(TL_T) k_tile_fill(const Tile *tiles, const int *ent_start,
+                                                    const int *far_off, const int *far_num,
+                                                    const FarEnt *far, int nwmax,
+                                                    const unsigned *gbm, const unsigned *gwp,
+                                                    const int *dmap, int *ent_u, int *ent_src)
+{
+    const Tile t = tiles[blockIdx.x];
+    const unsigned *bm = gbm + (long long)blockIdx.x * nwmax;
+    const unsigned *wpre = gwp + (long long)blockIdx.x * nwmax;
+    const int start = ent_start[blockIdx.x];
+    if (blockIdx.y == 0) {
+        const int nwords = (t.nbits + 31) / 32;
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+            unsigned b = bm[w];
+            int r = (int)wpre[w];
+            while (b) {
+                const int bit = __ffs(b) - 1;
+                ent_u[start + r] = dmap[t.gid_base + w * 32 + bit];  // D table of the class
+                ++r;
+                b &= b - 1;
+            }
         }
     }
-    for (long long j = threadIdx.x; j < (long long)count * TT; j += blockDim.x)
-        ent_src[(long long)start * TT + j] = -1;
-    __syncthreads();
-    int nw = blockDim.x >> 5;
-    for (int i = warp; i < t.nt; i += nw) {
-        long long hid = (1ll << t.level) + t.keys[i];
-        int e0 = far_off[hid], n = far_num[hid];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int i1 = min(t.nt, 32 * ((int)blockIdx.y + 1));
+    for (int i = 32 * blockIdx.y + warp; i < i1; i += nw) {
+        const long long hid = (1ll << t.level) + t.keys[i];
+        const int e0 = far_off[hid], n = far_num[hid];
         for (int e = lane; e < n; e += 32) {
-            FarEnt fe = far[e0 + e];
-            int u = fe.gid - t.gid_base;
-            int pos = (int)wpre[u >> 5] + __popc(bm[u >> 5] & ((1u << (u & 31)) - 1u));
+            const FarEnt fe = far[e0 + e];
+            const int u = fe.gid - t.gid_base;
+            const int pos = (int)__ldg(wpre + (u >> 5)) +
+                            __popc(__ldg(bm + (u >> 5)) & ((1u << (u & 31)) - 1u));
             ent_src[((long long)start + pos) * TT + i] = (1 << t.level) + fe.src;
         }
     }
 }
 
 void launch_tile_count(const Tile *tiles, int ntiles, const int *far_off, const int *far_num,
-                       const FarEnt *far, int max_bits, int *counts, cudaStream_t s)
+                       const FarEnt *far, int max_bits, unsigned *gbm, unsigned *gwp, int *counts,
+                       cudaStream_t s)
 {
     if (ntiles <= 0) return;
-    size_t smem = (size_t)((max_bits + 31) / 32) * sizeof(unsigned);
+    const int nwmax = (max_bits + 31) / 32;
+    size_t smem = (size_t)nwmax * sizeof(unsigned);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_tile_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
-    k_tile_count<<<ntiles, TL_T, smem, s>>>(tiles, far_off, far_num, far, counts);
+    k_tile_count<<<ntiles, TL_T, smem, s>>>(tiles, far_off, far_num, far, nwmax, gbm, gwp, counts);
 }
 
 void launch_tile_fill(Tile *tiles, int ntiles, const int *ent_start, const int *far_off,
-                      const int *far_num, const FarEnt *far, int max_bits, const int *dmap, int *ent_u,
-                      int *ent_src, cudaStream_t s)
+                      const int *far_num, const FarEnt *far, int max_bits, const unsigned *gbm,
+                      const unsigned *gwp, const int *dmap, int *ent_u, int *ent_src,
+                      cudaStream_t s)
 {
     if (ntiles <= 0) return;
-    size_t smem = 2 * (size_t)((max_bits + 31) / 32) * sizeof(unsigned);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_tile_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
-    k_tile_fill<<<ntiles, TL_T, smem, s>>>(tiles, ent_start, far_off, far_num, far, dmap, ent_u, ent_src);
+    k_tile_fill<<<dim3((unsigned)ntiles, TF_SPLIT), TL_T, 0, s>>>(
+        tiles, ent_start, far_off, far_num, far, (max_bits + 31) / 32, gbm, gwp, dmap, ent_u,
+        ent_src);
 }
 
 }  // namespace ccfmm

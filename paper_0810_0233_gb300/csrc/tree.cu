@@ -96,35 +96,44 @@ __global__ void __launch_bounds__(256) k_bbox_final(const double *partial, int n
 // Box, split sequence and cell sizes of every level.  One thread; the
 // running widths and split counts stay in registers (the stores to g are
 // never read back here, so no step waits on a global-memory round trip).
+// The split sequence (one thread: halve the widest axis, ties x < y < z),
+// then the widths and radii of every level (one thread per level).
 __global__ void k_geom(const double *box6, Geom *g)
 {
-    if (threadIdx.x != 0) return;
-    double ext[3], w[3];
-    int ns[3] = {0, 0, 0};
-    for (int a = 0; a < 3; ++a) {
-        ext[a] = box6[3 + a] - box6[a];
-        w[a] = ext[a];
-        g->lo[a] = box6[a];
-        g->ext[a] = ext[a];
-        g->nsplit[0][a] = 0;
-        g->w[0][a] = w[a];
+    __shared__ int s_ns[LCAP + 1][3];
+    const int t = threadIdx.x;
+    double ext[3];
+    for (int a = 0; a < 3; ++a) ext[a] = box6[3 + a] - box6[a];
+    if (t == 0) {
+        int ns[3] = {0, 0, 0};
+        double w[3] = {ext[0], ext[1], ext[2]};
+        for (int a = 0; a < 3; ++a) {
+            g->lo[a] = box6[a];
+            g->ext[a] = ext[a];
+            s_ns[0][a] = 0;
+        }
+        g->axis[0] = -1;
+        for (int l = 1; l <= LCAP; ++l) {
+            int a = 0;
+            if (w[1] > w[a]) a = 1;
+            if (w[2] > w[a]) a = 2;
+            g->axis[l] = a;
+            ns[a] += 1;
+            w[a] = ldexp(ext[a], -ns[a]);
+            for (int b = 0; b < 3; ++b) s_ns[l][b] = ns[b];
+        }
+        g->L = -1;
     }
-    g->axis[0] = -1;
-    g->h[0] = 0.5 * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-    for (int l = 1; l <= LCAP; ++l) {
-        int a = 0;
-        if (w[1] > w[a]) a = 1;
-        if (w[2] > w[a]) a = 2;
-        g->axis[l] = a;
-        ns[a] += 1;
+    __syncthreads();
+    for (int l = t; l <= LCAP; l += blockDim.x) {
+        double w[3];
         for (int b = 0; b < 3; ++b) {
-            w[b] = ldexp(ext[b], -ns[b]);
-            g->nsplit[l][b] = ns[b];
+            w[b] = ldexp(ext[b], -s_ns[l][b]);
+            g->nsplit[l][b] = s_ns[l][b];
             g->w[l][b] = w[b];
         }
         g->h[l] = 0.5 * sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     }
-    g->L = -1;
 }
 
 void launch_bbox(const double *pos, long long n, const double *user_box, double *d_box6,
@@ -165,13 +174,15 @@ __global__ void k_keys(const double *pos, long long n, const Geom *g, uint32_t *
         if (ca < 0) ca = 0;
         c[a] = ca;
     }
+    // level j takes the next bit (from the top) of the coordinate along the
+    // axis split at j: bit nsplit[LCAP][a] - nsplit[j][a] of c[a]
     uint32_t key = 0;
-    int used[3] = {0, 0, 0};
+#pragma unroll
     for (int j = 1; j <= LCAP; ++j) {
-        int a = g->axis[j];
-        uint32_t bit = (uint32_t)((c[a] >> (nb[a] - 1 - used[a])) & 1);
-        used[a]++;
-        key = (key << 1) | bit;
+        const int a = g->axis[j];
+        const long long ca = a == 0 ? c[0] : (a == 1 ? c[1] : c[2]);
+        const int sh = (a == 0 ? nb[0] : (a == 1 ? nb[1] : nb[2])) - g->nsplit[j][a];
+        key = (key << 1) | (uint32_t)((ca >> sh) & 1);
     }
     keys[i] = key;
     idx[i] = (int)i;
