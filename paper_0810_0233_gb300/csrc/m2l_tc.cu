@@ -70,10 +70,10 @@ namespace ccfmm {
 constexpr int TC_M = 128;       // field cells per tile (MMA M = TMEM lanes)
 constexpr int TC_KC = 32;       // K per unit: 4 MMA k-steps of 8
 constexpr int TC_SMEM = 227 * 1024;
-// at most this many pipeline stages (as many as fit, 3 at least; 3 leaves
-// room on the SM for a block of the near-field kernel running concurrently)
+// at most this many pipeline stages (as many as fit, 2 at least; fewer
+// stages leave room on the SM for a second CTA or near-field blocks)
 #ifndef CCFMM_TC_MAXST
-#define CCFMM_TC_MAXST 4
+#define CCFMM_TC_MAXST 2
 #endif
 #ifndef CCFMM_TC_PROD
 #define CCFMM_TC_PROD 256
@@ -95,7 +95,7 @@ template <int KP> struct TcShape {
     // pipeline stages that fit (at most 4), and how many units a producer
     // keeps in flight before marking the oldest one full
     static constexpr int FIT = (TC_SMEM - 2048) / STAGE;
-    static constexpr int ST = FIT < CCFMM_TC_MAXST ? (FIT < 3 ? 3 : FIT) : CCFMM_TC_MAXST;
+    static constexpr int ST = FIT < CCFMM_TC_MAXST ? (FIT < 2 ? 2 : FIT) : CCFMM_TC_MAXST;
     static constexpr int LAG = ST - 1;
     static constexpr int TMEM_COLS = 2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256);
 };
