@@ -422,8 +422,9 @@ void fmm_lattice_destroy(ccfmm_lattice_t h);
  * Scratch: a fixed array of 32,769 doubles (about 256 KB) in the library's
  * device memory, held on every GPU that loads the library until the process
  * exits.  Its device address is looked up on the first call on each device
- * (with that device current), so make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's values;
+ * (with that device current).  The call synchronises its stream, so it
+ * cannot be made while that stream is being captured (CCFMM_ERR_ARG).  All
+ * calls share the array and it keeps the last call's values;
  * every value a call reads is written earlier in the same call.  Calls whose
  * GPU work overlaps (other streams, other host threads) race on the array:
  * serialise them.  Errors: CCFMM_ERR_ARG for NULL, N out of range, or

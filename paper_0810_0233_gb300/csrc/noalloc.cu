@@ -146,6 +146,19 @@ ccfmm_status ccfmm_direct_field_energy_noalloc(const double *positions, const do
         set_last_error("no usable current CUDA device");
         return CCFMM_ERR_CUDA;
     }
+    // the call synchronises its stream, which a capturing stream forbids
+    if (stream) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            set_last_error("stream query failed");
+            return CCFMM_ERR_CUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) {
+            set_last_error("the stream is being captured: this call synchronises its stream");
+            return CCFMM_ERR_ARG;
+        }
+    }
     if (na_where(positions, dev) != NA_THIS_DEVICE || na_where(moments, dev) != NA_THIS_DEVICE ||
         na_where(H_out, dev) != NA_THIS_DEVICE) {
         set_last_error((std::string("positions, moments and H_out must be device memory of the "
