@@ -81,3 +81,29 @@ def test_no_alloc_rejects_out_of_range_and_host_arrays():
     dev = torch.cuda.current_device()
     assert ("device %d" % dev).encode() in lib.ccfmm_last_error()
     assert fn(ptr, ptr, 0, hp, ctypes.byref(E), None) == C.ERR_ARG
+
+
+def test_no_alloc_refuses_a_capturing_stream():
+    """The call synchronises its stream, so on a stream under capture it must
+    refuse (CCFMM_ERR_ARG) without touching the capture; the capture then
+    ends normally and the stream works afterwards."""
+    torch = pytest.importorskip("torch")
+    lib, fn = _fns()
+    pos = torch.rand(100, 3, dtype=torch.float64, device="cuda") * 10
+    mom = torch.randn(100, 3, dtype=torch.float64, device="cuda")
+    H = torch.zeros(100, 3, dtype=torch.float64, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            st = fn(pos.data_ptr(), mom.data_ptr(), 100, H.data_ptr(), E.data_ptr(),
+                    ctypes.c_void_p(s.cuda_stream))
+            H.add_(0.0)
+    assert st == C.ERR_ARG
+    assert b"captured" in lib.ccfmm_last_error()
+    st = fn(pos.data_ptr(), mom.data_ptr(), 100, H.data_ptr(), E.data_ptr(),
+            ctypes.c_void_p(s.cuda_stream))
+    assert st == C.OK
+    torch.cuda.synchronize()
+    assert torch.isfinite(H).all()
