@@ -91,6 +91,8 @@ CASES = [
     ("ferrofluid", 5000, 5, 0.5, 20.0),
     ("ring", 0, 4, 0.5, 10.0),
     ("lattice", 0, 3, 0.5, 8.0),
+    ("clustered", 2500, 7, 0.5, 20.0),  # FP32 FMA contraction (no tensor-core form at p = 7)
+    ("clustered", 1500, 8, 0.6, 16.0),
 ]
 
 
