@@ -33,14 +33,17 @@ __global__ void k_rotate(double *mom, long long n, const RotateParams *prm)
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double two53 = 1.0 / 9007199254740992.0;
-    const double pi = 3.14159265358979323846;
     unsigned long long x[4] = {(unsigned long long)i, 0ull, 0ull, 0ull};
     philox4x64(x, prm->seed, prm->step);
     double u0 = (double)(x[0] >> 11) * two53, u1 = (double)(x[1] >> 11) * two53;
     double u2 = (double)(x[2] >> 11) * two53;
-    double z = 1.0 - 2.0 * u0, phi = 2.0 * pi * u1, s = sqrt(1.0 - z * z);
-    double k[3] = {s * cos(phi), s * sin(phi), z};
-    double a = prm->max_angle * u2, ca = cos(a), sa = sin(a);
+    // phi = 2 pi u1 by sincospi(2 u1) (no argument reduction by pi), the
+    // angle's sine and cosine from one sincos
+    double z = 1.0 - 2.0 * u0, s = sqrt(1.0 - z * z), sp, cp;
+    sincospi(2.0 * u1, &sp, &cp);
+    double k[3] = {s * cp, s * sp, z};
+    double a = prm->max_angle * u2, ca, sa;
+    sincos(a, &sa, &ca);
     double m[3] = {mom[3 * i], mom[3 * i + 1], mom[3 * i + 2]};
     double kxm[3] = {k[1] * m[2] - k[2] * m[1], k[2] * m[0] - k[0] * m[2], k[0] * m[1] - k[1] * m[0]};
     double km = k[0] * m[0] + k[1] * m[1] + k[2] * m[2];
