@@ -382,7 +382,9 @@ __device__ __forceinline__ void m2m_sub_body(int p, int KP, int l0, int D, const
 {
     __shared__ real qs[2][1 << SUB_D][SUB_KP];
     __shared__ real fs[2][PMAX + 1];
+    __shared__ unsigned mi[SUB_KP];
     const int K = nterms(p) - 1;
+    fill_mi(mi, K);  // read after the first barrier below
     int cur = 0;
     {
         const int n = 1 << D;
@@ -411,8 +413,8 @@ __device__ __forceinline__ void m2m_sub_body(int p, int KP, int l0, int D, const
             const int cell = i / KP, c = i - cell * KP;
             real acc = (real)0;
             if (c < K) {
-                int nn[3];
-                midx_inv(c + 1, nn[0], nn[1], nn[2]);
+                const unsigned mc = mi[c];
+                const int nn[3] = {px(mc), py(mc), pz(mc)};
                 for (int b = 0; b < 2; ++b) {
                     const real *Qc = qs[cur][2 * cell + b];
                     for (int t = 0; t <= nn[sx]; ++t) {
@@ -492,7 +494,9 @@ __device__ __forceinline__ void l2l_sub_body(int p, int KP, int l0, int D, int L
     __shared__ double vs[2][1 << SUB_D][SUB_KP];
     __shared__ double fs[2][PMAX + 1];
     __shared__ int full[2][1 << SUB_D];
+    __shared__ unsigned mi[SUB_KP];
     const int K = nterms(p) - 1;
+    fill_mi(mi, K);  // read after the first barrier below
     int cur = 0;
     const long long hr = (1ll << l0) + r;
     for (int c = threadIdx.x; c < KP; c += SUB_T) vs[0][0][c] = V[hr * KP + c];
@@ -524,8 +528,8 @@ __device__ __forceinline__ void l2l_sub_body(int p, int KP, int l0, int D, int L
         for (int i = threadIdx.x; i < n * KP; i += SUB_T) {
             const int cell = i / KP, c = i - cell * KP;
             if (c >= K || !full[cur ^ 1][cell]) continue;
-            int nn[3];
-            midx_inv(c + 1, nn[0], nn[1], nn[2]);
+            const unsigned mc = mi[c];
+            const int nn[3] = {px(mc), py(mc), pz(mc)};
             const double *f = fs[cell & 1];  // key0 is even: the cell's side is its low bit
             const double *Vp = vs[cur][cell >> 1];
             const int kn = nn[0] + nn[1] + nn[2];

@@ -358,6 +358,9 @@ __device__ __forceinline__ void m2l_reduce_h_body(int p, int KPF, int KRP, const
     const int K = nterms(p) - 1, KR = red_count(p);
     double *en = smd;              // [KR]
     double *rows = smd + KR;       // [RED_HC][K]
+    // completion table: for full column c with n_z >= 2 its n_z and the full
+    // columns of n - 2e_z + 2e_x and n - 2e_z + 2e_y
+    __shared__ unsigned char cz[QF_ROW], cs1[QF_ROW], cs2[QF_ROW];
     const Tile t = tiles[tile];
     const double hinv = 1.0 / g->h[t.level];
     for (int r = threadIdx.x; r < KR; r += blockDim.x) {
@@ -365,6 +368,13 @@ __device__ __forceinline__ void m2l_reduce_h_body(int p, int KPF, int KRP, const
         double q = hinv * hinv;
         for (int d = 0; d < kn; ++d) q *= hinv;
         en[r] = (kn & 1) ? -q : q;
+    }
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        int nx, ny, nz;
+        midx_inv(c + 1, nx, ny, nz);
+        cz[c] = (unsigned char)nz;
+        cs1[c] = nz >= 2 ? (unsigned char)(midx(nx + 2, ny, nz - 2) - 1) : 0;
+        cs2[c] = nz >= 2 ? (unsigned char)(midx(nx, ny + 2, nz - 2) - 1) : 0;
     }
     __syncthreads();
     const int i0 = tile_item0[tile], ni = tile_nitems[tile];
@@ -378,16 +388,16 @@ __device__ __forceinline__ void m2l_reduce_h_body(int p, int KPF, int KRP, const
         rows[ci * K + red_full(r)] = s * en[r];
     }
     __syncthreads();
-    if ((int)threadIdx.x < nc) {
-        double *v = rows + threadIdx.x * K;
-        for (int c = 0; c < K; ++c) {
-            int nx, ny, nz;
-            midx_inv(c + 1, nx, ny, nz);
-            if (nz < 2) continue;
-            v[c] = -v[midx(nx + 2, ny, nz - 2) - 1] - v[midx(nx, ny + 2, nz - 2) - 1];
+    // columns with n_z = z from those with n_z = z - 2, z = 2 .. p in turn
+    for (int z = 2; z <= p; ++z) {
+        for (int j = threadIdx.x; j < nc * K; j += blockDim.x) {
+            const int ci = j / K, c = j - ci * K;
+            if (cz[c] != z) continue;
+            double *v = rows + ci * K;
+            v[c] = -v[cs1[c]] - v[cs2[c]];
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int j = threadIdx.x; j < nc * K; j += blockDim.x) {
         const int ci = j / K, c = j - ci * K;
         const long long hid = (1ll << t.level) + t.keys[tb + ci];
