@@ -184,7 +184,7 @@ struct UniEnts {
     }
 };
 
-template <typename real, typename Ents>
+template <typename real, typename Ents, int PT = P2P_T, int PCH = P2P_CH>
 __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, const Ents &ents,
                                          const double *Vrow, const typename vec4<real>::t *A,
                                          const typename vec2<real>::t *B,
@@ -209,7 +209,7 @@ __device__ __forceinline__ void p2p_body(int p, int KP, int L, const int *leaf_s
 // The near field (and, with Vrow, the smooth field) of one leaf's nt dipoles
 // at t0..: its own dipoles first, then the entries e0..e1 of its near list,
 // each giving a source range and the shift (target centre - source centre).
-template <typename real, typename Ents>
+template <typename real, typename Ents, int PT, int PCH>
 __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, const Ents &ents,
                                          const double *Vrow, const typename vec4<real>::t *A,
                                          const typename vec2<real>::t *B,
@@ -218,25 +218,26 @@ __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, 
     typedef typename vec4<real>::t R4;
     typedef typename vec2<real>::t R2;
     extern __shared__ __align__(16) unsigned char smraw[];
-    R4 *sp = reinterpret_cast<R4 *>(smraw);              // [P2P_CH]
-    R2 *sm = reinterpret_cast<R2 *>(sp + P2P_CH);         // [P2P_CH]
-    R4 *esh = reinterpret_cast<R4 *>(sm + P2P_CH);        // [P2P_NE] source shift
+    R4 *sp = reinterpret_cast<R4 *>(smraw);              // [PCH]
+    R2 *sm = reinterpret_cast<R2 *>(sp + PCH);         // [PCH]
+    R4 *esh = reinterpret_cast<R4 *>(sm + PCH);        // [P2P_NE] source shift
     int *est = reinterpret_cast<int *>(esh + P2P_NE);     // [P2P_NE] source start
     int *epf = est + P2P_NE;                              // [P2P_NE + 1] prefix of counts
     real *vs = reinterpret_cast<real *>(epf + P2P_NE + 4);  // [KP]
-    __shared__ int wsum[P2P_T / 32];
+    __shared__ int wsum[PT / 32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = nterms(p) - 1;
     const bool with_l2p = Vrow != nullptr;
+    constexpr int NE = 2 * PT < P2P_NE ? 2 * PT : P2P_NE;  // entries per metadata chunk
     if (with_l2p)
-        for (int c = tid; c < K; c += P2P_T) vs[c] = (real)Vrow[c];
+        for (int c = tid; c < K; c += PT) vs[c] = (real)Vrow[c];
 
-    for (int tb = 0; tb < nt; tb += P2P_TPT * P2P_T) {
-        const int ntc = min(nt - tb, P2P_TPT * P2P_T);
+    for (int tb = 0; tb < nt; tb += P2P_TPT * PT) {
+        const int ntc = min(nt - tb, P2P_TPT * PT);
         const int ngrp = P2P_WARP_STRIPES ? 32 * ((ntc + 32 * P2P_TPT - 1) / (32 * P2P_TPT))
                                           : (ntc + P2P_TPT - 1) / P2P_TPT;
-        const int S = max(1, P2P_T / ngrp);
+        const int S = max(1, PT / ngrp);
         const int q = tid % ngrp, stripe = tid / ngrp;
         const bool active = stripe < S;
         const int i0 = tb + P2P_TPT * q;
@@ -251,10 +252,10 @@ __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, 
         }
 
         // 1) the leaf's own dipoles (shift 0), r = 0 possible
-        for (int b0 = 0; b0 < nt; b0 += P2P_CH) {
-            const int len = min(P2P_CH, nt - b0);
+        for (int b0 = 0; b0 < nt; b0 += PCH) {
+            const int len = min(PCH, nt - b0);
             __syncthreads();
-            for (int v = tid; v < len; v += P2P_T) {
+            for (int v = tid; v < len; v += PT) {
                 sp[v] = A[t0 + b0 + v];
                 sm[v] = B[t0 + b0 + v];
             }
@@ -265,9 +266,10 @@ __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, 
                 p2p_range<real, true>(sp, sm, j0, j1, tx, hs);
             }
         }
-        // 2) the other near leaves, in chunks of P2P_NE entries
-        for (int ec = e0; ec < e1; ec += P2P_NE) {
-            const int nec = min(P2P_NE, e1 - ec);
+        // 2) the other near leaves, in chunks of NE entries (each thread
+        // stages the metadata of two entries of a chunk)
+        for (int ec = e0; ec < e1; ec += NE) {
+            const int nec = min(NE, e1 - ec);
             __syncthreads();
             int c0 = 0, c1 = 0;
             for (int r = 0; r < 2; ++r) {
@@ -297,15 +299,15 @@ __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, 
             if (2 * tid + 1 < nec) epf[2 * tid + 1] = ex + c0;
             if (tid == 0) {
                 int tot = 0;
-                for (int w = 0; w < P2P_T / 32; ++w) tot += wsum[w];
+                for (int w = 0; w < PT / 32; ++w) tot += wsum[w];
                 epf[nec] = tot;
             }
             __syncthreads();
             const int total = epf[nec];
-            for (int b0 = 0; b0 < total; b0 += P2P_CH) {
-                const int len = min(P2P_CH, total - b0);
+            for (int b0 = 0; b0 < total; b0 += PCH) {
+                const int len = min(PCH, total - b0);
                 if (b0) __syncthreads();
-                for (int e = warp; e < nec; e += P2P_T / 32) {
+                for (int e = warp; e < nec; e += PT / 32) {
                     int lo = max(epf[e], b0), hi = min(epf[e + 1], b0 + len);
                     if (lo >= hi) continue;
                     int off = est[e] - epf[e];
@@ -401,9 +403,11 @@ struct AdaEnts {
     }
 };
 
-// near field + smooth field of the adaptive tree's leaves, one block per leaf
-template <typename real>
-__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+// near field + smooth field of the adaptive tree's leaves, one block per
+// leaf; PT threads and PCH staged sources (a smaller block for the small
+// leaves of adaptive trees: more blocks resident per SM)
+template <typename real, int PT, int PCH>
+__global__ void __launch_bounds__(PT, CCFMM_P2P_MINB * (P2P_T / PT))
     k_ap2p(int p, int KP, const int *leaves, const int *p0, const int *np, const int *near_first,
            const int *near_num, const int *near_src, const double4 *cen,
            const typename vec4<real>::t *A, const typename vec2<real>::t *B, const double *V,
@@ -413,8 +417,39 @@ __global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
     const double4 cc = cen[c];
     const AdaEnts ents{p0, np, near_src, cen, cc.x, cc.y, cc.z, c};
     const int e0 = near_first[c];
-    p2p_leaf<real>(p, p0[c], np[c], e0, e0 + near_num[c], ents,
-                   V ? V + (long long)c * KP : nullptr, A, B, H);
+    p2p_leaf<real, AdaEnts, PT, PCH>(p, p0[c], np[c], e0, e0 + near_num[c], ents,
+                                     V ? V + (long long)c * KP : nullptr, A, B, H);
+}
+
+template <typename real, int PT, int PCH>
+static void run_ap2p(int p, int KP, int nleaf, const int *leaves, const int *p0, const int *np,
+                     const int *near_first, const int *near_num, const int *near_src,
+                     const double4 *cen, const typename vec4<real>::t *A,
+                     const typename vec2<real>::t *B, const double *V, typename vec4<real>::t *H,
+                     cudaStream_t s)
+{
+    static_assert(PCH * 4 >= 3 * P2P_TPT * PT, "the stripe sums reuse the staging buffer");
+    const size_t smem = (size_t)PCH * (sizeof(typename vec4<real>::t) + sizeof(typename vec2<real>::t)) +
+                        (size_t)P2P_NE * sizeof(typename vec4<real>::t) + (2 * P2P_NE + 4) * sizeof(int) +
+                        (size_t)KP * sizeof(real) + 64;
+    cudaFuncSetAttribute(k_ap2p<real, PT, PCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    note_launch();
+    k_ap2p<real, PT, PCH><<<(unsigned)nleaf, PT, smem, s>>>(p, KP, leaves, p0, np, near_first,
+                                                            near_num, near_src, cen, A, B, V, H);
+}
+
+// block shape of the adaptive near field: 128 threads and 1536 staged
+// sources (the complete tree's; default), or CCFMM_AP2P=64 (64 threads, 768
+// sources: more blocks per SM, measured slower on the ensemble)
+static int ap2p_threads()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("CCFMM_AP2P");
+        v = (e && atoi(e) == 64) ? 64 : 128;
+    }
+    return v;
 }
 
 template <typename real>
@@ -425,13 +460,12 @@ void launch_ap2p(int p, int KP, int nleaf, const int *leaves, const int *p0, con
                  cudaStream_t s)
 {
     if (nleaf <= 0) return;
-    const size_t smem = (size_t)P2P_CH * (sizeof(typename vec4<real>::t) + sizeof(typename vec2<real>::t)) +
-                        (size_t)P2P_NE * sizeof(typename vec4<real>::t) + (2 * P2P_NE + 4) * sizeof(int) +
-                        (size_t)KP * sizeof(real) + 64;
-    cudaFuncSetAttribute(k_ap2p<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    note_launch();
-    k_ap2p<real><<<(unsigned)nleaf, P2P_T, smem, s>>>(p, KP, leaves, p0, np, near_first, near_num,
-                                                      near_src, cen, A, B, V, H);
+    if (ap2p_threads() == 128)
+        run_ap2p<real, P2P_T, P2P_CH>(p, KP, nleaf, leaves, p0, np, near_first, near_num,
+                                      near_src, cen, A, B, V, H, s);
+    else
+        run_ap2p<real, 64, P2P_CH / 2>(p, KP, nleaf, leaves, p0, np, near_first, near_num,
+                                       near_src, cen, A, B, V, H, s);
 }
 
 template void launch_ap2p<float>(int, int, int, const int *, const int *, const int *, const int *,
