@@ -1005,6 +1005,15 @@ void afree(ABuf &b)
 
 template <typename T> T *AP(ABuf &b) { return reinterpret_cast<T *>(b.p); }
 
+// scratch of one build step, freed when it goes out of scope (on every
+// return path); cudaFree waits for the kernels still using it
+struct ATmp : ABuf {
+    ATmp() = default;
+    ATmp(const ATmp &) = delete;
+    ATmp &operator=(const ATmp &) = delete;
+    ~ATmp() { afree(*this); }
+};
+
 bool is_dev(const void *p)
 {
     cudaPointerAttributes a;
@@ -1092,7 +1101,7 @@ ccfmm_status build_tree(ccfmm_adaptive_t h, const double *ubox, const double *sp
     const cudaStream_t s = h->stream;
     const long long n = h->N;
     const int ns = h->ns;
-    ABuf dbox, dsplit;
+    ATmp dbox, dsplit;
     if (ubox) {
         ATRY(aalloc(dbox, 6 * sizeof(double)));
         ACK(cudaMemcpyAsync(dbox.p, ubox, 6 * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1108,8 +1117,9 @@ ccfmm_status build_tree(ccfmm_adaptive_t h, const double *ubox, const double *sp
                                split ? AP<double>(dsplit) : nullptr, s_default, AP<AGeom>(h->geo),
                                AP<int>(h->flags));
     ACK(cudaGetLastError());
-    ABuf klo, khi, idx, k2, v2, k3, v3, shi;
-    for (ABuf *b : {&klo, &khi, &idx, &k2, &v2, &k3, &v3, &shi, &h->perm}) ATRY(aalloc(*b, 4 * n));
+    ATmp klo, khi, idx, k2, v2, k3, v3, shi;
+    for (ABuf *b : std::initializer_list<ABuf *>{&klo, &khi, &idx, &k2, &v2, &k3, &v3, &shi, &h->perm})
+        ATRY(aalloc(*b, 4 * n));
     note_launch();
     k_akeys<<<nblk(n, 256), 256, 0, s>>>(AP<double>(h->pos), n, AP<long long>(h->offd), ns,
                                          AP<AGeom>(h->geo), AP<uint32_t>(klo), AP<uint32_t>(khi),
@@ -1132,7 +1142,7 @@ ccfmm_status build_tree(ccfmm_adaptive_t h, const double *ubox, const double *sp
     ACK(cudaGetLastError());
 
     // cells: chain lengths, numbering, cells
-    ABuf len, first, total;
+    ATmp len, first, total;
     ATRY(aalloc(len, 4 * n));
     ATRY(aalloc(first, 4 * n));
     ATRY(aalloc(total, 64));
@@ -1160,7 +1170,7 @@ ccfmm_status build_tree(ccfmm_adaptive_t h, const double *ubox, const double *sp
     ACK(cudaGetLastError());
 
     // leaves, in cell order
-    ABuf flag, rank;
+    ATmp flag, rank;
     ATRY(aalloc(flag, 4 * (size_t)nc));
     ATRY(aalloc(rank, 4 * (size_t)nc));
     ATRY(aalloc(stemp, std::max(stemp.bytes, std::max(radix_temp_bytes(nc), scan_temp_bytes(nc)))));
@@ -1173,8 +1183,9 @@ ccfmm_status build_tree(ccfmm_adaptive_t h, const double *ubox, const double *sp
     note_launch();
     k_leaf_list<<<nblk(nc, 256), 256, 0, s>>>(nc, AP<int>(flag), AP<int>(rank), AP<int>(h->leaves));
     // cells of each level, in cell order (a stable sort by level)
-    ABuf cid, lk, lk2, lv2, hist;
-    for (ABuf *b : {&cid, &lk, &lk2, &lv2, &h->lvl_cells}) ATRY(aalloc(*b, 4 * (size_t)nc));
+    ATmp cid, lk, lk2, lv2, hist;
+    for (ABuf *b : std::initializer_list<ABuf *>{&cid, &lk, &lk2, &lv2, &h->lvl_cells})
+        ATRY(aalloc(*b, 4 * (size_t)nc));
     ATRY(aalloc(hist, 4 * (AMAXL + 2)));
     ACK(cudaMemsetAsync(hist.p, 0, 4 * (AMAXL + 2), s));
     note_launch();
@@ -1202,7 +1213,7 @@ ccfmm_status build_lists(ccfmm_adaptive_t h, ABuf &stemp)
     const int nc = h->nc, ns = h->ns;
     int maxnl = 0;
     for (int l = 0; l <= h->maxL; ++l) maxnl = std::max(maxnl, h->lvl_off[l + 1] - h->lvl_off[l]);
-    ABuf cand_a, cand_b, cfirst, cnum, cnt, off, total;
+    ATmp cand_a, cand_b, cfirst, cnum, cnt, off, total;
     ATRY(aalloc(cand_a, 4 * (size_t)std::max(ns, 1)));
     ATRY(aalloc(cfirst, 4 * (size_t)nc));
     ATRY(aalloc(cnum, 4 * (size_t)nc));
@@ -1307,8 +1318,8 @@ template <typename real> ccfmm_status build_m2l(ccfmm_adaptive_t h, ABuf &stemp)
     ATRY(aalloc(h->ps, 4 * (size_t)std::max(nf, 1ll)));
     h->nd = h->n64 = h->n16 = 0;
     if (nf > 0) {
-        ABuf K1, K2, K3, K4, V1, V2, V3, V4, khi, ksm, gflag, grank, total;
-        for (ABuf *b : {&K1, &K2, &K3, &K4, &V1, &V2, &V3, &V4, &khi, &ksm, &gflag, &grank})
+        ATmp K1, K2, K3, K4, V1, V2, V3, V4, khi, ksm, gflag, grank, total;
+        for (ABuf *b : std::initializer_list<ABuf *>{&K1, &K2, &K3, &K4, &V1, &V2, &V3, &V4, &khi, &ksm, &gflag, &grank})
             ATRY(aalloc(*b, 4 * (size_t)nf));
         ATRY(aalloc(total, 64));
         ATRY(aalloc(stemp, std::max(stemp.bytes, std::max(radix_temp_bytes(nf), scan_temp_bytes(nf)))));
@@ -1347,8 +1358,9 @@ template <typename real> ccfmm_status build_m2l(ccfmm_adaptive_t h, ABuf &stemp)
         ACK(cudaGetLastError());
         ATRY(to_host(h, &h->nd, total.p, 1));
         const int nd = h->nd;
-        ABuf gstart, c64, c16, o64, o16;
-        for (ABuf *b : {&gstart, &c64, &c16, &o64, &o16}) ATRY(aalloc(*b, 4 * (size_t)nd));
+        ATmp gstart, c64, c16, o64, o16;
+        for (ABuf *b : std::initializer_list<ABuf *>{&gstart, &c64, &c16, &o64, &o16})
+            ATRY(aalloc(*b, 4 * (size_t)nd));
         ATRY(aalloc(h->sep, sizeof(double4) * (size_t)nd));
         ATRY(aalloc(h->rpow, sizeof(float) * (PMAX + 2) * (size_t)nd));
         note_launch();
@@ -1671,7 +1683,7 @@ static ccfmm_status adaptive_create(const double *positions, const double *momen
         return bail(CCFMM_ERR_CUDA);
     }
     const double s_default = p > 3 ? 0.74 * (double)p * (double)p : 8.0;
-    ABuf stemp;
+    ATmp stemp;
     st = aalloc(stemp, std::max(radix_temp_bytes(N), scan_temp_bytes(N)));
     if (st == CCFMM_OK) st = build_tree(h, box, split, s_default, stemp);
     if (st == CCFMM_OK) st = build_lists(h, stemp);
