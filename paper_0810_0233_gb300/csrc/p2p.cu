@@ -11,13 +11,13 @@
 
 namespace ccfmm {
 
-// sources staged per batch and resident blocks per SM (the register budget);
-// compile-time tunables
+// sources staged per batch and resident blocks per SM of the FP32 kernels
+// (the register budget; FP64 keeps 4); compile-time tunables
 #ifndef CCFMM_P2P_CH
-#define CCFMM_P2P_CH 1536
+#define CCFMM_P2P_CH 1024
 #endif
 #ifndef CCFMM_P2P_MINB
-#define CCFMM_P2P_MINB 4
+#define CCFMM_P2P_MINB 6
 #endif
 #ifndef CCFMM_P2P_UNROLL
 #define CCFMM_P2P_UNROLL 2
@@ -26,6 +26,7 @@ constexpr int P2P_T = 128;    // threads per block
 constexpr int P2P_CH = CCFMM_P2P_CH;  // sources staged in shared memory per batch
 constexpr int P2P_UNROLL = CCFMM_P2P_UNROLL;  // unroll of the pair loop
 constexpr int P2P_NE = 256;   // near-list entries whose metadata is staged at once
+template <typename real> constexpr int p2p_minb() { return sizeof(real) == 4 ? CCFMM_P2P_MINB : 4; }
 
 template <typename real> __device__ __forceinline__ real rsq(real r2);
 // one MUFU operation: separations here are never subnormal, so the
@@ -93,6 +94,122 @@ __device__ __forceinline__ void stripe_range(int len, int S, int stripe, int &j0
     j0 = min(len, stripe * chunk);
     j1 = min(len, j0 + chunk);
 }
+
+// FP32 near field in packed two-lane arithmetic (f32x2 add/mul/fma): the
+// staged sources are stored in pairs, {x0 x1 y0 y1} {z0 z1 mx0 mx1}
+// {my0 my1 mz0 mz1}, and each step of the pair loop takes two sources in
+// the two lanes against one target whose coordinates are duplicated once.
+// The two lanes keep separate sums, added at the end of the range.  An odd
+// batch is padded with a source of zero moment at 1e30 (r^2 overflows to
+// inf, so r^-1 = 0 and it adds exactly zero).  Compile-time switch
+// CCFMM_P2P_X2 (FP32 only; the FP64 path is always scalar).
+#ifndef CCFMM_P2P_X2
+#define CCFMM_P2P_X2 1
+#endif
+constexpr bool P2P_X2 = CCFMM_P2P_X2 != 0;
+
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <bool SELF>
+__device__ __forceinline__ void p2p_range_x2(const float4 (*sq)[3], int u0, int u1,
+                                             const float (&tx)[P2P_TPT][3],
+                                             float (&hs)[P2P_TPT][3])
+{
+    float2 tp[P2P_TPT][3], h[P2P_TPT][3];
+#pragma unroll
+    for (int i = 0; i < P2P_TPT; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            tp[i][k] = make_float2(tx[i][k], tx[i][k]);
+            h[i][k] = make_float2(0.f, 0.f);
+        }
+    const float2 three = make_float2(3.f, 3.f);
+#pragma unroll P2P_UNROLL
+    for (int u = u0; u < u1; ++u) {
+        const float4 a = sq[u][0], b = sq[u][1], c = sq[u][2];
+        const float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
+        const float2 sz = make_float2(b.x, b.y), mx = make_float2(b.z, b.w);
+        const float2 my = make_float2(c.x, c.y), mz = make_float2(c.z, c.w);
+#pragma unroll
+        for (int i = 0; i < P2P_TPT; ++i) {
+            const float2 rx = __fadd2_rn(tp[i][0], f2neg(sx));
+            const float2 ry = __fadd2_rn(tp[i][1], f2neg(sy));
+            const float2 rz = __fadd2_rn(tp[i][2], f2neg(sz));
+            const float2 r2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+            float2 ri = make_float2(rsq<float>(r2.x), rsq<float>(r2.y));
+            if (SELF) {
+                ri.x = r2.x > 0.f ? ri.x : 0.f;
+                ri.y = r2.y > 0.f ? ri.y : 0.f;
+            }
+            const float2 ri2 = __fmul2_rn(ri, ri);
+            const float2 ri3 = __fmul2_rn(ri2, ri);
+            const float2 mr = __ffma2_rn(mz, rz, __ffma2_rn(my, ry, __fmul2_rn(mx, rx)));
+            const float2 t = __fmul2_rn(__fmul2_rn(three, mr), ri2);
+            h[i][0] = __ffma2_rn(ri3, __ffma2_rn(t, rx, f2neg(mx)), h[i][0]);
+            h[i][1] = __ffma2_rn(ri3, __ffma2_rn(t, ry, f2neg(my)), h[i][1]);
+            h[i][2] = __ffma2_rn(ri3, __ffma2_rn(t, rz, f2neg(mz)), h[i][2]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < P2P_TPT; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) hs[i][k] += h[i][k].x + h[i][k].y;
+}
+
+// the staged-source buffer of p2p_leaf (PCH sources, 24 bytes each), in the
+// scalar layout (sp[PCH] positions + first moment component, sm[PCH] the
+// other two) or the packed pair layout above
+template <typename real, int PCH> struct SrcStage {
+    typedef typename vec4<real>::t R4;
+    typedef typename vec2<real>::t R2;
+    static constexpr bool X2 = P2P_X2 && sizeof(real) == 4;
+    unsigned char *base;
+    __device__ __forceinline__ void put(int v, const R4 &a, const R2 &m) const
+    {
+        if constexpr (X2) {
+            float *q = reinterpret_cast<float *>(base) + 12 * (v >> 1) + (v & 1);
+            q[0] = a.x;
+            q[2] = a.y;
+            q[4] = a.z;
+            q[6] = a.w;
+            q[8] = m.x;
+            q[10] = m.y;
+        } else {
+            reinterpret_cast<R4 *>(base)[v] = a;
+            reinterpret_cast<R2 *>(base + PCH * sizeof(R4))[v] = m;
+        }
+    }
+    // after the len sources of a batch are staged (one thread)
+    __device__ __forceinline__ void pad(int len) const
+    {
+        if constexpr (X2) {
+            if (len & 1) {
+                R4 a;
+                a.x = a.y = a.z = 1e30f;
+                a.w = 0.f;
+                R2 m;
+                m.x = m.y = 0.f;
+                put(len, a, m);
+            }
+        }
+    }
+    template <bool SELF>
+    __device__ __forceinline__ void range(int len, int S, int stripe,
+                                          const real (&tx)[P2P_TPT][3],
+                                          real (&hs)[P2P_TPT][3]) const
+    {
+        int j0, j1;
+        if constexpr (X2) {
+            stripe_range((len + 1) >> 1, S, stripe, j0, j1);
+            p2p_range_x2<SELF>(reinterpret_cast<const float4 (*)[3]>(base), j0, j1, tx, hs);
+        } else {
+            stripe_range(len, S, stripe, j0, j1);
+            p2p_range<real, SELF>(reinterpret_cast<const R4 *>(base),
+                                  reinterpret_cast<const R2 *>(base + PCH * sizeof(R4)), j0, j1,
+                                  tx, hs);
+        }
+    }
+};
 
 // Smooth field (Eq. H, H = -grad V) of one target from its leaf's Taylor
 // coefficients vs[] (column t - 1 holds the multi-index t), x relative to
@@ -184,13 +301,13 @@ struct UniEnts {
     }
 };
 
-template <typename real, typename Ents, int PT = P2P_T, int PCH = P2P_CH>
+template <typename real, typename Ents, bool L2P, int PT = P2P_T, int PCH = P2P_CH>
 __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, const Ents &ents,
                                          const double *Vrow, const typename vec4<real>::t *A,
                                          const typename vec2<real>::t *B,
                                          typename vec4<real>::t *H);
 
-template <typename real>
+template <typename real, bool L2P>
 __device__ __forceinline__ void p2p_body(int p, int KP, int L, const int *leaf_start,
                                          const int2 *near_nl, const NearEnt *near, const Geom *g,
                                          const typename vec4<real>::t *A,
@@ -203,13 +320,16 @@ __device__ __forceinline__ void p2p_body(int p, int KP, int L, const int *leaf_s
     const long long hid = (1ll << L) + key;
     UniEnts ents{leaf_start, near, g->w[L][0], g->w[L][1], g->w[L][2], (int)key};
     // V == nullptr: near field only (L2P by k_l2p once V is complete)
-    p2p_leaf<real>(p, t0, nt, nlk.x, nlk.x + nlk.y, ents, V ? V + hid * KP : nullptr, A, B, H);
+    p2p_leaf<real, UniEnts, L2P>(p, t0, nt, nlk.x, nlk.x + nlk.y, ents,
+                                 V ? V + hid * KP : nullptr, A, B, H);
 }
 
 // The near field (and, with Vrow, the smooth field) of one leaf's nt dipoles
 // at t0..: its own dipoles first, then the entries e0..e1 of its near list,
 // each giving a source range and the shift (target centre - source centre).
-template <typename real, typename Ents, int PT, int PCH>
+// L2P = false compiles the near field alone (Vrow is then ignored): without
+// the smooth-field epilogue the kernel needs fewer registers.
+template <typename real, typename Ents, bool L2P, int PT, int PCH>
 __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, const Ents &ents,
                                          const double *Vrow, const typename vec4<real>::t *A,
                                          const typename vec2<real>::t *B,
@@ -225,10 +345,12 @@ __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, 
     int *epf = est + P2P_NE;                              // [P2P_NE + 1] prefix of counts
     real *vs = reinterpret_cast<real *>(epf + P2P_NE + 4);  // [KP]
     __shared__ int wsum[PT / 32];
+    const SrcStage<real, PCH> stage{smraw};
+    static_assert(PCH % 2 == 0, "the packed layout stages sources in pairs");
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = nterms(p) - 1;
-    const bool with_l2p = Vrow != nullptr;
+    const bool with_l2p = L2P && Vrow != nullptr;
     constexpr int NE = 2 * PT < P2P_NE ? 2 * PT : P2P_NE;  // entries per metadata chunk
     if (with_l2p)
         for (int c = tid; c < K; c += PT) vs[c] = (real)Vrow[c];
@@ -255,16 +377,10 @@ __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, 
         for (int b0 = 0; b0 < nt; b0 += PCH) {
             const int len = min(PCH, nt - b0);
             __syncthreads();
-            for (int v = tid; v < len; v += PT) {
-                sp[v] = A[t0 + b0 + v];
-                sm[v] = B[t0 + b0 + v];
-            }
+            for (int v = tid; v < len; v += PT) stage.put(v, A[t0 + b0 + v], B[t0 + b0 + v]);
+            if (tid == 0) stage.pad(len);
             __syncthreads();
-            if (active) {
-                int j0, j1;
-                stripe_range(len, S, stripe, j0, j1);
-                p2p_range<real, true>(sp, sm, j0, j1, tx, hs);
-            }
+            if (active) stage.template range<true>(len, S, stripe, tx, hs);
         }
         // 2) the other near leaves, in chunks of NE entries (each thread
         // stages the metadata of two entries of a chunk)
@@ -319,16 +435,12 @@ __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, 
                         o.y = a.y - sh.y;
                         o.z = a.z - sh.z;
                         o.w = a.w;
-                        sp[gv - b0] = o;
-                        sm[gv - b0] = B[off + gv];
+                        stage.put(gv - b0, o, B[off + gv]);
                     }
                 }
+                if (tid == 0) stage.pad(len);
                 __syncthreads();
-                if (active) {
-                    int j0, j1;
-                    stripe_range(len, S, stripe, j0, j1);
-                    p2p_range<real, false>(sp, sm, j0, j1, tx, hs);
-                }
+                if (active) stage.template range<false>(len, S, stripe, tx, hs);
                 __syncthreads();
             }
         }
@@ -373,13 +485,13 @@ __device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, 
     }
 }
 
-template <typename real>
-__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+template <typename real, bool L2P>
+__global__ void __launch_bounds__(P2P_T, p2p_minb<real>())
     k_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl, const NearEnt *near,
           const Geom *g, const typename vec4<real>::t *A, const typename vec2<real>::t *B,
           const double *V, typename vec4<real>::t *H)
 {
-    p2p_body<real>(p, KP, L, leaf_start, near_nl, near, g, A, B, V, H, blockIdx.x);
+    p2p_body<real, L2P>(p, KP, L, leaf_start, near_nl, near, g, A, B, V, H, blockIdx.x);
 }
 
 // Near entries of the adaptive-depth tree: a partner leaf cell of any
@@ -406,8 +518,8 @@ struct AdaEnts {
 // near field + smooth field of the adaptive tree's leaves, one block per
 // leaf; PT threads and PCH staged sources (a smaller block for the small
 // leaves of adaptive trees: more blocks resident per SM)
-template <typename real, int PT, int PCH>
-__global__ void __launch_bounds__(PT, CCFMM_P2P_MINB * (P2P_T / PT))
+template <typename real, bool L2P, int PT, int PCH>
+__global__ void __launch_bounds__(PT, p2p_minb<real>() * (P2P_T / PT))
     k_ap2p(int p, int KP, const int *leaves, const int *p0, const int *np, const int *near_first,
            const int *near_num, const int *near_src, const double4 *cen,
            const typename vec4<real>::t *A, const typename vec2<real>::t *B, const double *V,
@@ -417,8 +529,8 @@ __global__ void __launch_bounds__(PT, CCFMM_P2P_MINB * (P2P_T / PT))
     const double4 cc = cen[c];
     const AdaEnts ents{p0, np, near_src, cen, cc.x, cc.y, cc.z, c};
     const int e0 = near_first[c];
-    p2p_leaf<real, AdaEnts, PT, PCH>(p, p0[c], np[c], e0, e0 + near_num[c], ents,
-                                     V ? V + (long long)c * KP : nullptr, A, B, H);
+    p2p_leaf<real, AdaEnts, L2P, PT, PCH>(p, p0[c], np[c], e0, e0 + near_num[c], ents,
+                                          V ? V + (long long)c * KP : nullptr, A, B, H);
 }
 
 template <typename real, int PT, int PCH>
@@ -432,11 +544,18 @@ static void run_ap2p(int p, int KP, int nleaf, const int *leaves, const int *p0,
     const size_t smem = (size_t)PCH * (sizeof(typename vec4<real>::t) + sizeof(typename vec2<real>::t)) +
                         (size_t)P2P_NE * sizeof(typename vec4<real>::t) + (2 * P2P_NE + 4) * sizeof(int) +
                         (size_t)KP * sizeof(real) + 64;
-    cudaFuncSetAttribute(k_ap2p<real, PT, PCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
     note_launch();
-    k_ap2p<real, PT, PCH><<<(unsigned)nleaf, PT, smem, s>>>(p, KP, leaves, p0, np, near_first,
-                                                            near_num, near_src, cen, A, B, V, H);
+    if (V) {
+        cudaFuncSetAttribute(k_ap2p<real, true, PT, PCH>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ap2p<real, true, PT, PCH><<<(unsigned)nleaf, PT, smem, s>>>(
+            p, KP, leaves, p0, np, near_first, near_num, near_src, cen, A, B, V, H);
+    } else {
+        cudaFuncSetAttribute(k_ap2p<real, false, PT, PCH>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ap2p<real, false, PT, PCH><<<(unsigned)nleaf, PT, smem, s>>>(
+            p, KP, leaves, p0, np, near_first, near_num, near_src, cen, A, B, V, H);
+    }
 }
 
 // block shape of the adaptive near field: 128 threads and 1536 staged
@@ -476,14 +595,17 @@ template void launch_ap2p<double>(int, int, int, const int *, const int *, const
                                   const double4 *, const double2 *, const double *, double4 *,
                                   cudaStream_t);
 
-// every member's leaves in one launch (ensemble step)
-__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+// every member's leaves in one launch (ensemble step), near field alone
+// (the members' V are not read: the smooth field follows by k_l2p_batch);
+// at most 5 blocks per SM: with the member's argument record it spills at 6
+constexpr int P2P_MINB_BATCH = CCFMM_P2P_MINB > 5 ? 5 : CCFMM_P2P_MINB;
+__global__ void __launch_bounds__(P2P_T, P2P_MINB_BATCH)
     k_p2p_batch(const P2PArgs *a, const int *bstart, int nm)
 {
     int key;
     const P2PArgs &x = a[batch_member(bstart, nm, blockIdx.x, key)];
-    p2p_body<float>(x.p, x.KP, x.L, x.leaf_start, x.near_nl, x.near, x.g, x.A, x.B, x.V, x.H,
-                    key);
+    p2p_body<float, false>(x.p, x.KP, x.L, x.leaf_start, x.near_nl, x.near, x.g, x.A, x.B,
+                           nullptr, x.H, key);
 }
 
 void launch_p2p_batch(const P2PArgs *d_args, const int *d_bstart, int nm, int nblocks, int KP,
@@ -525,7 +647,7 @@ __device__ __forceinline__ void red_add4(float4 *p, float a, float b, float c)
                  : "memory");
 }
 
-__global__ void __launch_bounds__(P2P_T, CCFMM_P2P_MINB)
+__global__ void __launch_bounds__(P2P_T, 4)
     k_p2p_sym(int L, const int *leaf_start, const int2 *near_nl, const NearEnt *near,
               const Geom *g, const float4 *A, const float2 *B, float4 *H)
 {
@@ -734,10 +856,19 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl
                   (size_t)P2P_NE * sizeof(typename vec4<real>::t) + (2 * P2P_NE + 4) * sizeof(int) +
                   (size_t)KP * sizeof(real) + 64;
     static_assert(P2P_CH * 4 >= 3 * P2P_TPT * P2P_T, "the stripe sums reuse the staging buffer");
-    cudaFuncSetAttribute(k_p2p<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
-    k_p2p<real><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start, near_nl, near,
-                                                         d_geom, A, B, V, H);
+    if (V) {
+        cudaFuncSetAttribute(k_p2p<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_p2p<real, true><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start, near_nl,
+                                                                   near, d_geom, A, B, V, H);
+    } else {
+        cudaFuncSetAttribute(k_p2p<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_p2p<real, false><<<(unsigned)(1ll << L), P2P_T, smem, s>>>(p, KP, L, leaf_start,
+                                                                    near_nl, near, d_geom, A, B,
+                                                                    nullptr, H);
+    }
 }
 
 // L2P (Eq. H, H = -grad V) of every dipole of a leaf (one warp per leaf),
