@@ -20,7 +20,7 @@ namespace ccfmm {
 #define CCFMM_P2P_MINB 6
 #endif
 #ifndef CCFMM_P2P_UNROLL
-#define CCFMM_P2P_UNROLL 2
+#define CCFMM_P2P_UNROLL 4
 #endif
 constexpr int P2P_T = 128;    // threads per block
 constexpr int P2P_CH = CCFMM_P2P_CH;  // sources staged in shared memory per batch
