@@ -284,8 +284,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def describe_ensemble(ns, total, p, theta, tree="adaptive"):
-    if tree == "adaptive":
+def describe_ensemble(ns, total, p, theta, tree="adaptive", astep="graph"):
+    if tree == "adaptive" and astep == "persistent":
+        how = ("adaptive-depth trees (a cell splits while it holds more than s dipoles, s per "
+               "size class by the library's autotuner); one CUDA graph launch holding one "
+               "persistent kernel whose blocks take every stage's tiles of all samples from "
+               "one task queue (bounded waits between the stages)")
+        prec = ("FP32 bulk, M2L on 3xTF32 warp-level MMA; FP64 D tensors; per-cell M2L sums "
+                "in FP32, L2L in FP64")
+    elif tree == "adaptive":
         how = ("adaptive-depth trees (a cell splits while it holds more than s dipoles, s per "
                "size class by the library's autotuner); one CUDA graph launch, one kernel per "
                "stage over all samples (per level for M2M and L2L)")
@@ -321,7 +328,7 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
     if adaptive:
         b = C.Adaptive(torch.from_numpy(P_).to(dev), torch.from_numpy(M_).to(dev), p, theta,
                        offsets=o, precision=args.precision, stream=stream,
-                       autotune=not args.no_autotune)
+                       autotune=not args.no_autotune, persistent=args.astep == "persistent")
     else:
         b = C.Batch(torch.from_numpy(P_).to(dev), torch.from_numpy(M_).to(dev), o, p, theta,
                     precision=args.precision, stream=stream, autotune=not args.no_autotune)
@@ -389,7 +396,7 @@ def run_ensemble(args, torch, dist, C, world, rank, dev, stream):
             "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": describe_ensemble(ns, len(pos), p, theta, args.tree),
+            "config": describe_ensemble(ns, len(pos), p, theta, args.tree, args.astep),
             "e2e": {"value": all_total * args.steps / t_e2e, "unit": "fields/s",
                     "ms_per_step": 1e3 * t_e2e / args.steps, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": int(total * 24 + len(mine) * 8),
@@ -447,6 +454,9 @@ def main():
                          "autotuner")
     ap.add_argument("--tree", default="adaptive", choices=["adaptive", "uniform"],
                     help="ensemble: adaptive-depth trees (default) or complete trees")
+    ap.add_argument("--astep", default="graph", choices=["graph", "persistent"],
+                    help="ensemble on adaptive trees: the stages as kernels of one graph "
+                         "(default) or one persistent kernel over a task queue")
     ap.add_argument("--no-selector", action="store_true",
                     help="skip the selector object (learned (p, theta, leaf) at 1e-4)")
     ap.add_argument("--profile", action="store_true",

@@ -514,10 +514,21 @@ ccfmm_status fmm_adaptive_create(const double *positions, const double *moments,
  *             fastest mean evaluation time over `trials` timed evaluations
  *             (after one warm-up) wins.  Trials run on the handle's stream
  *             at creation.
- *   trials    timed evaluations per candidate (<= 0: 3). */
+ *   trials    timed evaluations per candidate (<= 0: 3).
+ *   persistent  nonzero: every evaluation (and step) is one launch of a
+ *             persistent kernel whose blocks take the stages' tiles of all
+ *             samples from one task queue (rotation, permutation, P2M, M2M
+ *             level by level, fold, M2L items, L2L level by level, near field,
+ *             L2P, unpermute, energies), a task waiting for the phases it
+ *             depends on with bounded polls; a wait that runs out ends the
+ *             launch and the call returns CCFMM_ERR_TIMEOUT.  Needs the mixed
+ *             path with the tensor-core M2L (p in 2..6): CCFMM_ERR_ARG
+ *             otherwise.  Zero: the stages as separate kernels in one CUDA
+ *             graph (the near field beside the far chain). */
 typedef struct {
     int32_t autotune;
     int32_t trials;
+    int32_t persistent;
 } ccfmm_adaptive_opts;
 
 ccfmm_status fmm_adaptive_create_ex(const double *positions, const double *moments,

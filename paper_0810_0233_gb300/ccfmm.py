@@ -578,10 +578,12 @@ class Lattice:
 
 class Adaptive:
     """Adaptive-depth tree (fmm_adaptive_*): one system, or an ensemble of
-    independent samples (``offsets``) evaluated together."""
+    independent samples (``offsets``) evaluated together.  persistent=True:
+    every evaluation is one launch of the persistent step kernel (task queue
+    over the stages of all samples) instead of a graph of stage kernels."""
 
     def __init__(self, positions, moments, p, theta, split=None, offsets=None, box=None,
-                 precision="mixed", stream=None, autotune=False, trials=3):
+                 precision="mixed", stream=None, autotune=False, trials=3, persistent=False):
         lib = load()
         self._lib = lib
         if offsets is None:
@@ -606,7 +608,7 @@ class Adaptive:
         prec = {"mixed": MIXED, "fp32": MIXED, "fp64": FP64}[precision]
         self.p = int(p)
         h = _vp()
-        opts = (ctypes.c_int32 * 2)(1 if autotune else 0, int(trials))
+        opts = (ctypes.c_int32 * 3)(1 if autotune else 0, int(trials), 1 if persistent else 0)
         _check(lib.fmm_adaptive_create_ex(pp, pm, _vp(off.ctypes.data), self.ns, int(p),
                                           float(theta), sp, bp, prec,
                                           _vp(ctypes.addressof(opts)), _stream_ptr(stream),

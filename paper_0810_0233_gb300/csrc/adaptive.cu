@@ -34,6 +34,7 @@
 // per-sample energies; captured once into a CUDA graph.
 #include "../../include/ccfmm.h"
 #include "ccfmm_dev.cuh"
+#include "stages.cuh"
 
 #include <math.h>
 #include <stdarg.h>
@@ -48,20 +49,7 @@
 
 namespace ccfmm {
 
-constexpr int AMAXL = 40;     // deepest level (keys of 40 bits)
 constexpr int ASTACK = 96;    // depth-first stack of the leaf refinement
-constexpr int AW = 4;         // warps per block of the per-cell kernels
-
-struct AGeom {               // one sample's tree geometry
-    double lo[3], ext[3];
-    int axis[AMAXL + 1];          // axis halved to make level l (l >= 1)
-    int nsplit[AMAXL + 1][3];     // splits of each axis in the first l levels
-    double w[AMAXL + 1][3];       // cell widths of level l
-    double w2[AMAXL + 1];         // squared diagonal, (w0^2 + w1^2) + w2^2
-    double rad[AMAXL + 1];        // half diagonal, 0.5 sqrt(w2)
-    double sh[AMAXL + 1][PMAX + 1];  // (w_l / 2)^t / t! along the axis split at level l
-    double s;                     // split while a cell holds more than s
-};
 
 // ------------------------------------------------------------------ keys
 // Box and split sequence of each sample (one block per sample): the given
@@ -718,16 +706,6 @@ __global__ void k_item_fill(int nd, const int *gstart, long long nf, const int *
 }
 
 // ---------------------------------------------------------------- upward / downward
-// Shift tables of the one-axis translations: for coefficient column c
-// (multi-index n = c + 1) and axis s, the columns of n - t e_s (M2M, t = 0 ..
-// n_s, the zero multi-index left out) and of n + t e_s (L2L, t = 0 .. p - |n|),
-// in order of t.
-constexpr int KPMAX = ((nterms(PMAX) - 1 + 7) / 8) * 8;
-struct ShiftTab {
-    uint8_t m2m_n[3][KPMAX], l2l_n[3][KPMAX];
-    uint8_t m2m_c[3][KPMAX][PMAX + 1], l2l_c[3][KPMAX][PMAX + 1];
-};
-
 __global__ void k_shift_tab(int p, ShiftTab *tb)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -756,57 +734,18 @@ __global__ void k_shift_tab(int p, ShiftTab *tb)
 }
 
 // M2M (Eq. momentshift) into every internal cell of one level, one warp per
-// cell: the children sit at -/+ half their width along the axis split at
-// their level.
+// cell (am2m_cell)
 template <typename real>
 __global__ void __launch_bounds__(32 * AW) k_am2m(int p, int KP, const int *cells, int ncl,
                                                   const int *smp, const int *lev, const int *ch,
                                                   const AGeom *geo, const ShiftTab *tb, real *Q)
 {
-    __shared__ real fs[AW][2][PMAX + 1];
-    __shared__ real qs[AW][2][KPMAX];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ AM2MWarp<real> ws[AW];
+    const int w = threadIdx.x >> 5;
     const int idx = blockIdx.x * AW + w;
     if (idx >= ncl) return;
-    const int c = cells[idx];
-    const int b0 = ch[2 * c], b1 = ch[2 * c + 1];
-    if (b0 < 0 && b1 < 0) return;  // a leaf: P2M wrote its moments
-    for (int col = lane; col < KP; col += 32) {
-        qs[w][0][col] = b0 >= 0 ? Q[(long long)b0 * KP + col] : (real)0;
-        qs[w][1][col] = b1 >= 0 ? Q[(long long)b1 * KP + col] : (real)0;
-    }
-    const AGeom &g = geo[smp[c]];
-    const int l = lev[c], sx = g.axis[l + 1];
-    if (lane < 2) {
-        const real hw = (real)(0.5 * g.w[l + 1][sx]);
-        const real cs = lane ? hw : -hw;
-        real f = (real)1;
-        fs[w][lane][0] = f;
-        for (int t = 1; t <= p; ++t) {
-            f = f * cs / (real)t;
-            fs[w][lane][t] = f;
-        }
-    }
-    __syncwarp();
-    for (int col = lane; col < KP; col += 32) {
-        real acc = (real)0;
-        const int n = tb->m2m_n[sx][col];
-        const uint8_t *cl = tb->m2m_c[sx][col];
-        for (int b = 0; b < 2; ++b) {
-            if ((b ? b1 : b0) < 0) continue;
-            for (int t = 0; t < n; ++t) acc += fs[w][b][t] * qs[w][b][cl[t]];
-        }
-        Q[(long long)c * KP + col] = acc;
-    }
+    am2m_cell<real>(p, KP, cells[idx], smp, lev, ch, geo, tb, Q, ws[w]);
 }
-
-// Completion of the harmonic reduction: for full column c the reduced
-// column (or -1), n_z, and for n_z >= 2 the full columns of n - 2e_z + 2e_x
-// and n - 2e_z + 2e_y (V_n = -V of those two).
-struct HarmTab {
-    int8_t red[KPMAX];
-    uint8_t nz[KPMAX], s1[KPMAX], s2[KPMAX];
-};
 
 __global__ void k_harm_tab(int p, HarmTab *ht)
 {
@@ -833,9 +772,7 @@ __global__ void k_harm_tab(int p, HarmTab *ht)
 }
 
 // L2L (Eq. taylorshift, FP64) into every cell of one level, one warp per
-// cell: V = the cell's own M2L sum + the parent's V shifted to the cell.
-// RED: the M2L sum is the reduced accumulator (rows of KRP), completed to
-// all columns first.
+// cell (al2l_cell)
 template <typename acc_t, bool RED>
 __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, int KRP, const int *cells,
                                                   int ncl, const int *smp, const int *lev,
@@ -843,52 +780,11 @@ __global__ void __launch_bounds__(32 * AW) k_al2l(int p, int KP, int KRP, const 
                                                   const AGeom *geo, const ShiftTab *tb,
                                                   const HarmTab *ht, const acc_t *VF, double *V)
 {
-    __shared__ double fs[AW][PMAX + 1];
-    __shared__ double vp[AW][KPMAX];
-    __shared__ double vm[AW][RED ? KPMAX : 1];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ AL2LWarp ws[AW];
+    const int w = threadIdx.x >> 5;
     const int idx = blockIdx.x * AW + w;
     if (idx >= ncl) return;
-    const int c = cells[idx];
-    const int pr = par[c];
-    const int K = nterms(p) - 1;
-    const long long row = (long long)c * KP;
-    if (RED) {
-        for (int col = lane; col < K; col += 32) {
-            const int r = ht->red[col];
-            vm[w][col] = r >= 0 ? (double)VF[(long long)c * KRP + r] : 0.0;
-        }
-        __syncwarp();
-        for (int z = 2; z <= p; ++z) {
-            for (int col = lane; col < K; col += 32)
-                if (ht->nz[col] == z) vm[w][col] = -vm[w][ht->s1[col]] - vm[w][ht->s2[col]];
-            __syncwarp();
-        }
-    }
-    auto m2l = [&](int col) -> double { return RED ? vm[w][col] : (double)VF[row + col]; };
-    if (pr < 0) {
-        for (int col = lane; col < KP; col += 32) V[row + col] = col < K ? m2l(col) : 0.0;
-        return;
-    }
-    const AGeom &g = geo[smp[c]];
-    const int l = lev[c], sx = g.axis[l];
-    if (lane <= p) {
-        const double f = g.sh[l][lane];
-        fs[w][lane] = (ic[c].w || !(lane & 1)) ? f : -f;
-    }
-    for (int col = lane; col < KP; col += 32) vp[w][col] = V[(long long)pr * KP + col];
-    __syncwarp();
-    for (int col = lane; col < KP; col += 32) {
-        if (col >= K) {
-            V[row + col] = 0.0;
-            continue;
-        }
-        const int n = tb->l2l_n[sx][col];
-        const uint8_t *cl = tb->l2l_c[sx][col];
-        double acc = 0.0;
-        for (int t = 0; t < n; ++t) acc += fs[w][t] * vp[w][cl[t]];
-        V[row + col] = m2l(col) + acc;
-    }
+    al2l_cell<acc_t, RED>(p, KP, KRP, cells[idx], smp, lev, par, ic, geo, tb, ht, VF, V, ws[w]);
 }
 
 // fields back to input order in FP64
@@ -897,12 +793,7 @@ __global__ void k_aunperm(long long n, const int *perm, const typename vec4<real
                           double *Hd)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const long long o = perm[i];
-    const typename vec4<real>::t h = H[i];
-    Hd[3 * o] = (double)h.x;
-    Hd[3 * o + 1] = (double)h.y;
-    Hd[3 * o + 2] = (double)h.z;
+    if (i < n) aunperm_one<real>(i, perm, H, Hd);
 }
 
 // E = -1/2 sum m.H per sample, one block per sample, fixed order
@@ -910,17 +801,254 @@ __global__ void __launch_bounds__(256) k_aenergy(const long long *off, const dou
                                                  const double *Hd, double *E)
 {
     __shared__ double red[256];
-    const int s = blockIdx.x;
-    double e = 0.0;
-    for (long long i = off[s] + threadIdx.x; i < off[s + 1]; i += 256)
-        e += mom[3 * i] * Hd[3 * i] + mom[3 * i + 1] * Hd[3 * i + 1] + mom[3 * i + 2] * Hd[3 * i + 2];
-    red[threadIdx.x] = e;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    aenergy_sample<256>(blockIdx.x, off, mom, Hd, E, red);
+}
+
+// ------------------------------------------------------------ persistent step
+// The whole evaluation of the forest (FP32 path, tensor-core M2L over the
+// harmonic reduction) in one launch of persistent blocks of 128 threads that
+// take tasks from one queue.  A task is a (stage, tile) of all samples at
+// once: a chunk of dipoles for the rotation, the moment permutation and the
+// unpermute, four leaves (one warp each) for P2M and L2P, four cells of one
+// level for M2M and L2L, four cells for the fold, one M2L item of more than 16
+// pairs or four of at most 16, one leaf for the near field, one sample for
+// the energy.  The tasks of a stage form a phase; a task may wait for up to
+// two phases to be complete (done[ph] == need[ph]), and every phase it waits
+// for lies wholly before it in the queue.  Blocks take tasks in queue order
+// (one atomic counter), so the earliest unfinished task never waits on a
+// later one and the queue drains whatever number of blocks is resident.
+// Waits poll with a bound (poll_limit polls, nanosleep between them): a wait
+// that runs out sets err and its block stops; every block stops once err is
+// set, so the launch always ends.  The host zeroes head, err and done before
+// each launch.
+enum ATask : int {
+    AT_ROT = 0,
+    AT_PERM,
+    AT_P2M,
+    AT_M2M,
+    AT_FOLD,
+    AT_M2L_BIG,
+    AT_M2L_SMALL,
+    AT_L2L,
+    AT_P2P,
+    AT_L2P,
+    AT_UNPERM,
+    AT_ENERGY
+};
+constexpr int ACHUNK = 2048;  // dipoles per task of the elementwise stages
+constexpr int ASTEP_T = 128;  // threads per block
+
+struct AStepArgs {
+    const int4 *tasks;  // x = type | phase << 8, y, z: task range, w = waits + 1 (16 bits each)
+    int ntask;
+    int *ctl;           // [0] head, [1] err, [2 ..] done per phase
+    const int *need;    // tasks per phase
+    long long poll_limit;
+    int rotate;
+    int p, KP, KRP, ldD, n16, nc;
+    long long N;
+    double *mom;
+    const RotateParams *prm;
+    const int *perm;
+    float4 *A, *H;
+    float2 *B;
+    double *Hd, *E, *V;
+    const long long *offd;
+    const int *leaves, *p0, *np, *near_first, *near_num, *near_src;
+    const double4 *cen;
+    float *Q, *Qr, *VFr;
+    const int *lvl_cells, *smp, *lev, *ch, *par;
+    const int4 *ic;
+    const AGeom *geo;
+    const ShiftTab *shift;
+    const HarmTab *harm;
+    const int4 *it64, *it16;
+    const int *pt, *ps;
+    const float *rpow, *D;
+    const uint16_t *itr;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// thread 0: wait (bounded) until phase ph is complete; false when the wait
+// ran out or another block has given up
+__device__ __forceinline__ bool astep_wait(const AStepArgs &a, int ph)
+{
+    if (ph < 0) return true;
+    const int need = a.need[ph];
+    const int *done = a.ctl + 2 + ph;
+    for (long long it = 0;; ++it) {
+        if (ld_acquire(done) >= need) return true;
+        if (it >= a.poll_limit || ld_acquire(a.ctl + 1)) return false;
+        __nanosleep(it < 32 ? 64 : 512);
     }
-    if (threadIdx.x == 0) E[s] = -0.5 * red[0];
+}
+
+// thread 0: the next task whose phases are complete, or x = -1 (queue empty,
+// or stop)
+__device__ __forceinline__ int4 astep_next(const AStepArgs &a)
+{
+    const int4 stop = make_int4(-1, 0, 0, 0);
+    if (ld_acquire(a.ctl + 1)) return stop;
+    const int t = atomicAdd(a.ctl, 1);
+    if (t >= a.ntask) return stop;
+    const int4 tk = a.tasks[t];
+    if (!astep_wait(a, (tk.w & 0xffff) - 1) || !astep_wait(a, (tk.w >> 16) - 1)) {
+        atomicExch(a.ctl + 1, 1);
+        return stop;
+    }
+    __threadfence();
+    return tk;
+}
+
+template <int P>
+__global__ void __launch_bounds__(ASTEP_T, CCFMM_P2P_MINB) k_astep(const AStepArgs a)
+{
+    constexpr int KRP = red_padded(P);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int4 s_task;
+    const int tid = threadIdx.x, w = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_task = astep_next(a);
+        __syncthreads();
+        const int4 tk = s_task;
+        if (tk.x < 0) break;
+        const int type = tk.x & 255;
+        switch (type) {
+        case AT_ROT:
+            if (a.rotate)
+                for (long long i = (long long)tk.y * ACHUNK + tid;
+                     i < min(a.N, (long long)(tk.y + 1) * ACHUNK); i += ASTEP_T)
+                    rotate_one(a.mom, i, a.prm);
+            break;
+        case AT_PERM:
+            for (long long i = (long long)tk.y * ACHUNK + tid;
+                 i < min(a.N, (long long)(tk.y + 1) * ACHUNK); i += ASTEP_T)
+                permute_one<float>(i, a.mom, a.perm, a.A, a.B);
+            break;
+        case AT_P2M: {
+            const int li = tk.y + w;
+            const bool live = li < tk.z;
+            const int c = live ? a.leaves[li] : 0;
+            const int s0 = live ? a.p0[c] : 0, s1 = live ? s0 + a.np[c] : 0;
+            p2m_run<float>(P, a.KP, live, s0, s1, a.A, a.B, a.Q + (long long)c * a.KP,
+                           *reinterpret_cast<P2MScratch<float> *>(smraw));
+            break;
+        }
+        case AT_M2M: {
+            const int idx = tk.y + w;
+            if (idx < tk.z)
+                am2m_cell<float>(P, a.KP, a.lvl_cells[idx], a.smp, a.lev, a.ch, a.geo, a.shift,
+                                 a.Q, reinterpret_cast<AM2MWarp<float> *>(smraw)[w]);
+            break;
+        }
+        case AT_FOLD: {
+            const int c = tk.y + w;
+            if (c < a.nc)
+                afold_cell(P, a.KP, KRP, c, a.Q, a.Qr, reinterpret_cast<float *>(smraw) + w * AF_ROW);
+            break;
+        }
+        case AT_M2L_BIG:
+            am2l_big_item<KRP>(P, a.it64[tk.y], a.pt, a.ps, a.rpow, a.D, a.ldD, a.itr, a.Qr,
+                               a.VFr, smraw);
+            break;
+        case AT_M2L_SMALL:
+            am2l_small_items<KRP>(P, a.it16, a.n16, tk.y, a.pt, a.ps, a.rpow, a.D, a.ldD, a.itr,
+                                  a.Qr, a.VFr, smraw);
+            break;
+        case AT_L2L: {
+            const int idx = tk.y + w;
+            if (idx < tk.z)
+                al2l_cell<float, true>(P, a.KP, KRP, a.lvl_cells[idx], a.smp, a.lev, a.par, a.ic,
+                                       a.geo, a.shift, a.harm, a.VFr, a.V,
+                                       reinterpret_cast<AL2LWarp *>(smraw)[w]);
+            break;
+        }
+        case AT_P2P: {
+            const int c = a.leaves[tk.y];
+            const double4 cc = a.cen[c];
+            const AdaEnts ents{a.p0, a.np, a.near_src, a.cen, cc.x, cc.y, cc.z, c};
+            const int e0 = a.near_first[c];
+            p2p_leaf<float, AdaEnts, false, ASTEP_T, P2P_CH>(P, a.p0[c], a.np[c], e0,
+                                                             e0 + a.near_num[c], ents, nullptr,
+                                                             a.A, a.B, a.H);
+            break;
+        }
+        case AT_L2P: {
+            const int li = tk.y + w;
+            if (li < tk.z)
+                al2p_leaf<float, P>(a.KP, a.leaves[li], a.p0, a.np, a.A, a.V, a.H,
+                                    reinterpret_cast<float *>(smraw) + w * nterms(PMAX));
+            break;
+        }
+        case AT_UNPERM:
+            for (long long i = (long long)tk.y * ACHUNK + tid;
+                 i < min(a.N, (long long)(tk.y + 1) * ACHUNK); i += ASTEP_T)
+                aunperm_one<float>(i, a.perm, a.H, a.Hd);
+            break;
+        case AT_ENERGY:
+            aenergy_sample<ASTEP_T>(tk.y, a.offd, a.mom, a.Hd, a.E,
+                                    reinterpret_cast<double *>(smraw));
+            break;
+        default: break;
+        }
+        // every thread's writes reach the GPU scope before the phase counter
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(a.ctl + 2 + (tk.x >> 8), 1);
+    }
+}
+
+// dynamic shared memory of k_astep<P>: the largest stage scratch
+template <int P> size_t astep_smem(int KP, int ldD)
+{
+    constexpr int KRP = red_padded(P);
+    size_t m = (size_t)P2P_CH * (sizeof(float4) + sizeof(float2)) + (size_t)P2P_NE * sizeof(float4) +
+               (2 * P2P_NE + 4) * sizeof(int) + (size_t)KP * sizeof(float) + 64;
+    m = std::max(m, sizeof(P2MScratch<float>));
+    m = std::max(m, AW * sizeof(AM2MWarp<float>));
+    m = std::max(m, AW * sizeof(AL2LWarp));
+    m = std::max(m, (size_t)AW * AF_ROW * sizeof(float));
+    m = std::max(m, am2l_big_smem<KRP>(ldD));
+    m = std::max(m, am2l_small_smem<KRP>(ldD));
+    m = std::max(m, (size_t)L2P_W * nterms(PMAX) * sizeof(float));
+    m = std::max(m, (size_t)ASTEP_T * sizeof(double));
+    return (m + 15) & ~(size_t)15;
+}
+
+// launch with as many blocks as fit the SMs (no more than tasks)
+template <int P> cudaError_t launch_astep_p(const AStepArgs &a, cudaStream_t s)
+{
+    const size_t smem = astep_smem<P>(a.KP, a.ldD);
+    cudaError_t e = cudaFuncSetAttribute(k_astep<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_astep<P>, ASTEP_T, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(a.ntask, std::max(1, per) * nsm));
+    note_launch();
+    k_astep<P><<<grid, ASTEP_T, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_astep(int p, const AStepArgs &a, cudaStream_t s)
+{
+    switch (p) {
+    case 2: return launch_astep_p<2>(a, s);
+    case 3: return launch_astep_p<3>(a, s);
+    case 4: return launch_astep_p<4>(a, s);
+    case 5: return launch_astep_p<5>(a, s);
+    case 6: return launch_astep_p<6>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace ccfmm
@@ -1070,6 +1198,13 @@ struct ccfmm_adaptive_s {
     long long kernels_per_eval = 0;
     double ms_build = 0.0;
     bool evaluated = false;
+    // persistent step (k_astep): task queue, tasks per phase, control words
+    // (head, err, done per phase) and a pinned copy of err
+    bool persistent = false;
+    int qntask = 0, qnphase = 0;
+    long long qpoll = 1ll << 24;
+    ABuf qtasks, qneed, qctl;
+    int *hctl = nullptr;
 };
 
 
@@ -1425,6 +1560,65 @@ template <typename real> ccfmm_status build_m2l(ccfmm_adaptive_t h, ABuf &stemp)
 // overlap on, the near field (without the smooth field) runs on the handle's
 // stream while P2M, M2M, M2L and L2L run on the high-priority stream; the
 // smooth field is added after the join.
+void enqueue_persistent(ccfmm_adaptive_t h, bool rotate)
+{
+    const cudaStream_t s = h->stream;
+    cudaMemsetAsync(h->VFr.p, 0, sizeof(float) * (size_t)h->nc * h->KRP, s);
+    cudaMemsetAsync(h->qctl.p, 0, sizeof(int) * (2 + (size_t)h->qnphase), s);
+    AStepArgs a;
+    a.tasks = AP<int4>(h->qtasks);
+    a.ntask = h->qntask;
+    a.ctl = AP<int>(h->qctl);
+    a.need = AP<int>(h->qneed);
+    a.poll_limit = h->qpoll;
+    a.rotate = rotate ? 1 : 0;
+    a.p = h->p;
+    a.KP = h->KP;
+    a.KRP = h->KRP;
+    a.ldD = h->ldD;
+    a.n16 = h->n16;
+    a.nc = h->nc;
+    a.N = h->N;
+    a.mom = AP<double>(h->mom);
+    a.prm = AP<RotateParams>(h->prm);
+    a.perm = AP<int>(h->perm);
+    a.A = AP<float4>(h->A);
+    a.H = AP<float4>(h->H);
+    a.B = AP<float2>(h->B);
+    a.Hd = AP<double>(h->Hd);
+    a.E = AP<double>(h->E);
+    a.V = AP<double>(h->V);
+    a.offd = AP<long long>(h->offd);
+    a.leaves = AP<int>(h->leaves);
+    a.p0 = AP<int>(h->p0);
+    a.np = AP<int>(h->np);
+    a.near_first = AP<int>(h->near_first);
+    a.near_num = AP<int>(h->near_num);
+    a.near_src = AP<int>(h->near_src);
+    a.cen = AP<double4>(h->cen);
+    a.Q = AP<float>(h->Q);
+    a.Qr = AP<float>(h->Qr);
+    a.VFr = AP<float>(h->VFr);
+    a.lvl_cells = AP<int>(h->lvl_cells);
+    a.smp = AP<int>(h->smp);
+    a.lev = AP<int>(h->lev);
+    a.ch = AP<int>(h->ch);
+    a.par = AP<int>(h->par);
+    a.ic = AP<int4>(h->ic);
+    a.geo = AP<AGeom>(h->geo);
+    a.shift = AP<ShiftTab>(h->shift);
+    a.harm = AP<HarmTab>(h->harm);
+    a.it64 = AP<int4>(h->it64);
+    a.it16 = AP<int4>(h->it16);
+    a.pt = AP<int>(h->pt);
+    a.ps = AP<int>(h->ps);
+    a.rpow = AP<float>(h->rpow);
+    a.D = AP<float>(h->D);
+    a.itr = AP<uint16_t>(h->itr);
+    launch_astep(h->p, a, s);
+    h->kernels_per_eval = 1;
+}
+
 template <typename real> void enqueue_eval(ccfmm_adaptive_t h, bool rotate)
 {
     typedef typename vec4<real>::t R4;
@@ -1520,13 +1714,111 @@ template <typename real> void enqueue_eval(ccfmm_adaptive_t h, bool rotate)
     h->kernels_per_eval = k - (rotate ? 1 : 0);
 }
 
+// The task queue of the persistent step (k_astep), in the order the blocks
+// take it: the rotation, the moment permutation, then the far chain's phases
+// (P2M; M2M level by level from the deepest; the fold; the M2L items; L2L
+// level by level from the roots), each waiting for the one before it, with
+// an equal share of the near-field leaves after each phase (they wait only
+// for the permutation and keep the SMs busy while a level completes); then
+// L2P (waits for the last L2L level and the whole near field), the unpermute
+// and the energies.  CCFMM_ASTEP_STALL=1 (tests of the time-out path) asks
+// one task more of the M2L phase than it has and lets every wait give up
+// after 2^12 polls.
+ccfmm_status enable_persistent(ccfmm_adaptive_t h)
+{
+    if (h->dbl || !h->red || h->p < 2 || h->p > 6)
+        return afail(CCFMM_ERR_ARG, "the persistent step needs the FP32 path with the "
+                                    "tensor-core M2L (p in 2..6)");
+    std::vector<int4> t;
+    std::vector<int> need;
+    auto phase = [&]() {
+        need.push_back(0);
+        return (int)need.size() - 1;
+    };
+    auto add = [&](int type, int ph, long long y, long long z, int w1, int w2) {
+        t.push_back(make_int4(type | (ph << 8), (int)y, (int)z, (w1 + 1) | ((w2 + 1) << 16)));
+        ++need[ph];
+    };
+    const long long nch = (h->N + ACHUNK - 1) / ACHUNK;
+    const int ph_rot = phase();
+    for (long long i = 0; i < nch; ++i) add(AT_ROT, ph_rot, i, 0, -1, -1);
+    const int ph_perm = phase();
+    for (long long i = 0; i < nch; ++i) add(AT_PERM, ph_perm, i, 0, ph_rot, -1);
+    // far-chain phases: (type, y, z) of each task
+    std::vector<std::vector<int3>> far;
+    auto level_tasks = [&](int type, int l) {
+        const int a = h->lvl_off[l], b = h->lvl_off[l + 1];
+        if (b <= a) return;
+        far.emplace_back();
+        for (int i = a; i < b; i += AW) far.back().push_back(make_int3(type, i, b));
+    };
+    far.emplace_back();
+    for (int li = 0; li < h->nleaf; li += P2M_W) far.back().push_back(make_int3(AT_P2M, li, h->nleaf));
+    for (int l = h->maxL - 1; l >= 0; --l) level_tasks(AT_M2M, l);
+    far.emplace_back();
+    for (int c = 0; c < h->nc; c += AW) far.back().push_back(make_int3(AT_FOLD, c, h->nc));
+    const size_t m2l_phase = far.size();
+    far.emplace_back();
+    for (int i = 0; i < h->n64; ++i) far.back().push_back(make_int3(AT_M2L_BIG, i, 0));
+    for (int g = 0; g < (h->n16 + 3) / 4; ++g) far.back().push_back(make_int3(AT_M2L_SMALL, g, 0));
+    for (int l = 0; l <= h->maxL; ++l) level_tasks(AT_L2L, l);
+    const int ph_p2p = phase();
+    int prev = ph_perm, ph_m2l = -1;
+    long long next = 0;
+    const long long nf = (long long)far.size();
+    for (long long k = 0; k < nf; ++k) {
+        const int ph = phase();
+        if ((size_t)k == m2l_phase) ph_m2l = ph;
+        for (const int3 &x : far[k]) add(x.x, ph, x.y, x.z, prev, -1);
+        prev = ph;
+        for (const long long upto = (long long)h->nleaf * (k + 1) / (nf + 1); next < upto; ++next)
+            add(AT_P2P, ph_p2p, next, 0, ph_perm, -1);
+    }
+    for (; next < h->nleaf; ++next) add(AT_P2P, ph_p2p, next, 0, ph_perm, -1);
+    const int ph_l2p = phase();
+    for (int li = 0; li < h->nleaf; li += L2P_W) add(AT_L2P, ph_l2p, li, h->nleaf, prev, ph_p2p);
+    const int ph_un = phase();
+    for (long long i = 0; i < nch; ++i) add(AT_UNPERM, ph_un, i, 0, ph_l2p, -1);
+    const int ph_e = phase();
+    for (int i = 0; i < h->ns; ++i) add(AT_ENERGY, ph_e, i, 0, ph_un, -1);
+    if ((long long)t.size() > INT32_MAX / 2 || need.size() > 0xfffe)
+        return afail(CCFMM_ERR_ARG, "forest too large for the persistent step's task queue");
+    const char *e = getenv("CCFMM_ASTEP_STALL");
+    if (e && atoi(e) != 0 && ph_m2l >= 0) {
+        ++need[ph_m2l];
+        h->qpoll = 1ll << 12;
+    }
+    ATRY(aalloc(h->qtasks, sizeof(int4) * t.size()));
+    ATRY(aalloc(h->qneed, sizeof(int) * need.size()));
+    ATRY(aalloc(h->qctl, sizeof(int) * (2 + need.size())));
+    if (!h->hctl && cudaMallocHost(&h->hctl, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        h->hctl = nullptr;
+        return afail(CCFMM_ERR_ALLOC, "pinned allocation failed");
+    }
+    ACK(cudaMemcpy(h->qtasks.p, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice));
+    ACK(cudaMemcpy(h->qneed.p, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice));
+    h->qntask = (int)t.size();
+    h->qnphase = (int)need.size();
+    h->kernels_per_eval = 1;
+    for (int i = 0; i < 2; ++i)
+        if (h->gexec[i]) {
+            cudaGraphExecDestroy(h->gexec[i]);
+            h->gexec[i] = nullptr;
+        }
+    h->persistent = true;
+    return CCFMM_OK;
+}
+
 ccfmm_status run(ccfmm_adaptive_t h, int rotate, double *H_out, double *E_out)
 {
     const cudaStream_t s = h->stream;
     if (!h->gexec[rotate]) {
         cudaGraph_t g = nullptr;
         ACK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        if (h->dbl)
+        if (h->persistent)
+            enqueue_persistent(h, rotate != 0);
+        else if (h->dbl)
             enqueue_eval<double>(h, rotate != 0);
         else
             enqueue_eval<float>(h, rotate != 0);
@@ -1545,7 +1837,7 @@ ccfmm_status run(ccfmm_adaptive_t h, int rotate, double *H_out, double *E_out)
         }
     }
     else
-        note_launch((int)(h->kernels_per_eval + rotate));
+        note_launch((int)(h->kernels_per_eval + (h->persistent ? 0 : rotate)));
     ACK(cudaGraphLaunch(h->gexec[rotate], s));
     if (H_out)
         ACK(cudaMemcpyAsync(H_out, h->Hd.p, sizeof(double) * 3 * (size_t)h->N,
@@ -1553,7 +1845,11 @@ ccfmm_status run(ccfmm_adaptive_t h, int rotate, double *H_out, double *E_out)
     if (E_out)
         ACK(cudaMemcpyAsync(E_out, h->E.p, sizeof(double) * (size_t)h->ns,
                             is_dev(E_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (h->persistent)
+        ACK(cudaMemcpyAsync(h->hctl, AP<int>(h->qctl) + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     ACK(cudaStreamSynchronize(s));
+    if (h->persistent && *h->hctl)
+        return afail(CCFMM_ERR_TIMEOUT, "persistent step: a bounded wait between its stages gave up");
     h->evaluated = true;
     return CCFMM_OK;
 }
@@ -1575,9 +1871,11 @@ void fmm_adaptive_destroy(ccfmm_adaptive_t h)
                     &h->ic, &h->cen, &h->leaves, &h->lvl_cells, &h->near_first, &h->near_num,
                     &h->near_src, &h->far_t, &h->far_s, &h->pt, &h->ps, &h->sep, &h->rpow, &h->D, &h->it64,
                     &h->it16, &h->fdense, &h->fst, &h->fq, &h->fval, &h->itab, &h->Q, &h->VF,
-                    &h->V, &h->shift, &h->Qr, &h->VFr, &h->itr, &h->harm, &h->prm};
+                    &h->V, &h->shift, &h->Qr, &h->VFr, &h->itr, &h->harm, &h->prm,
+                    &h->qtasks, &h->qneed, &h->qctl};
     for (ABuf *b : bufs) afree(*b);
     if (h->hprm) cudaFreeHost(h->hprm);
+    if (h->hctl) cudaFreeHost(h->hctl);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->s_far) cudaStreamDestroy(h->s_far);
@@ -1715,15 +2013,12 @@ ccfmm_status fmm_adaptive_create(const double *positions, const double *moments,
 // (s0 = the given split, or Eq. so), timed over `trials` evaluations after
 // one warm-up; the fastest mean wins, and the final forest takes each
 // sample's class threshold.
-ccfmm_status fmm_adaptive_create_ex(const double *positions, const double *moments,
-                                    const int64_t *offsets, int nsamples, int p, double theta,
-                                    const double *split, const double *box, ccfmm_prec prec,
-                                    const ccfmm_adaptive_opts *opts, void *stream,
-                                    ccfmm_adaptive_t *out)
+static ccfmm_status adaptive_create_tuned(const double *positions, const double *moments,
+                                         const int64_t *offsets, int nsamples, int p,
+                                         double theta, const double *split, const double *box,
+                                         ccfmm_prec prec, const ccfmm_adaptive_opts *opts,
+                                         void *stream, ccfmm_adaptive_t *out)
 {
-    if (!opts || !opts->autotune)
-        return adaptive_create(positions, moments, offsets, nsamples, p, theta, split, box, prec,
-                               stream, out);
     set_last_error("");
     if (!out || !positions || !moments || !offsets || nsamples < 1)
         return afail(CCFMM_ERR_ARG, "bad argument");
@@ -1813,6 +2108,29 @@ ccfmm_status fmm_adaptive_create_ex(const double *positions, const double *momen
             (*out)->tune_split.push_back(best[c]);
         }
     return CCFMM_OK;
+}
+
+ccfmm_status fmm_adaptive_create_ex(const double *positions, const double *moments,
+                                    const int64_t *offsets, int nsamples, int p, double theta,
+                                    const double *split, const double *box, ccfmm_prec prec,
+                                    const ccfmm_adaptive_opts *opts, void *stream,
+                                    ccfmm_adaptive_t *out)
+{
+    ccfmm_status st =
+        (opts && opts->autotune)
+            ? adaptive_create_tuned(positions, moments, offsets, nsamples, p, theta, split, box,
+                                    prec, opts, stream, out)
+            : adaptive_create(positions, moments, offsets, nsamples, p, theta, split, box, prec,
+                              stream, out);
+    if (st != CCFMM_OK || !opts || !opts->persistent) return st;
+    st = enable_persistent(*out);
+    if (st != CCFMM_OK) {
+        const std::string msg = ccfmm_last_error();
+        fmm_adaptive_destroy(*out);
+        *out = nullptr;
+        set_last_error(msg.c_str());
+    }
+    return st;
 }
 
 ccfmm_status fmm_adaptive_tuning(ccfmm_adaptive_t h, int32_t *nclasses, int64_t *class_nmin,

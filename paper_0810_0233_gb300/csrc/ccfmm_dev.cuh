@@ -61,7 +61,7 @@ __host__ __device__ inline int m2l_kend(int p, int maxdeg, int n)
 // 2k + 1 of the order in the library's order; reduced column r of order k
 // (k^2 - 1 <= r < (k+1)^2 - 1) is full column T(k-1) - 1 + r - (k^2 - 1).
 __host__ __device__ constexpr int red_count(int p) { return (p + 1) * (p + 1) - 1; }
-inline int red_padded(int p) { return ((red_count(p) + 7) / 8) * 8; }
+__host__ __device__ constexpr int red_padded(int p) { return ((red_count(p) + 7) / 8) * 8; }
 __host__ __device__ inline int red_order(int r)
 {
     int k = 1;

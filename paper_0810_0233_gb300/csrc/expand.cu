@@ -3,6 +3,7 @@
 //   (level, far offset), P2M (Eq. multipolemoments), M2M (Eq. momentshift),
 //   L2L (Eq. taylorshift) and L2P (Eq. H, H = -grad V).
 #include "ccfmm_dev.cuh"
+#include "stages.cuh"
 
 namespace ccfmm {
 
@@ -20,23 +21,6 @@ __device__ __forceinline__ int loc_in_order(int nx, int ny, int nz)
     return nz * (2 * k + 3 - nz) / 2 + ny;
 }
 
-__device__ __forceinline__ unsigned pack3(int a, int b, int c)
-{
-    return (unsigned)a | ((unsigned)b << 5) | ((unsigned)c << 10);
-}
-
-// fill an smem table of the coefficient multi-indices mi[c] = index c+1
-__device__ __forceinline__ void fill_mi(unsigned *mi, int K)
-{
-    for (int c = threadIdx.x; c < K; c += blockDim.x) {
-        int x, y, z;
-        midx_inv(c + 1, x, y, z);
-        mi[c] = pack3(x, y, z);
-    }
-}
-__device__ __forceinline__ int px(unsigned v) { return (int)(v & 31u); }
-__device__ __forceinline__ int py(unsigned v) { return (int)((v >> 5) & 31u); }
-__device__ __forceinline__ int pz(unsigned v) { return (int)((v >> 10) & 31u); }
 
 // ---------------------------------------------------------------------------
 // F table (Eqs. Dn, Dnr).  D_n(r) = r^-(2|n|+1) sum_{|q|=|n|} F_n(q) r^q with
@@ -204,86 +188,6 @@ void launch_itable(int p, int KP, int maxdeg, uint16_t *it, cudaStream_t s)
     k_itable<<<(KP * KP + 255) / 256, 256, 0, s>>>(p, KP, maxdeg, it);
 }
 
-// ---------------------------------------------------------------------------
-// P2M (Eq. multipolemoments): Q_n = sum_i sum_a m_ia r_i^(n-e_a)/(n-e_a)!
-// about the leaf centre, for every leaf (empty leaves get zeros).
-// ---------------------------------------------------------------------------
-// One warp per leaf, P2M_W leaves per block: a lane stages one dipole of the
-// leaf (powers x^j/j! of its leaf-relative coordinates, by reciprocal
-// constants) and then owns coefficients lane, lane + 32, ...
-constexpr int P2M_W = 4;
-constexpr int P2M_R = (nterms(PMAX) - 1 + 31) / 32;  // coefficient rounds per lane
-
-// P2M of the dipoles s0..s1 (coordinates relative to the leaf centre) into
-// Qrow[0..KP) by warp w of the block; every thread of the block calls it
-// (the multi-index table is filled block-wide), live = false for warps
-// without a leaf.
-template <typename real>
-__device__ __forceinline__ void p2m_run(int p, int KP, bool live, int s0, int s1,
-                                        const typename vec4<real>::t *A,
-                                        const typename vec2<real>::t *B, real *Qrow)
-{
-    __shared__ real pw[P2M_W][32][3][PMAX];
-    __shared__ real mm[P2M_W][32][3];
-    __shared__ unsigned mi[nterms(PMAX)];
-    const real inv[PMAX] = {(real)0, (real)1, (real)0.5, (real)1 / (real)3, (real)0.25,
-                            (real)0.2, (real)1 / (real)6, (real)1 / (real)7};
-    const int K = nterms(p) - 1;
-    fill_mi(mi, K);
-    __syncthreads();
-    if (!live) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    real acc[P2M_R];
-#pragma unroll
-    for (int r = 0; r < P2M_R; ++r) acc[r] = (real)0;
-    for (int base = s0; base < s1; base += 32) {
-        __syncwarp();
-        const int i = base + lane;
-        if (i < s1) {
-            const typename vec4<real>::t a = A[i];
-            const typename vec2<real>::t b = B[i];
-            const real x[3] = {a.x, a.y, a.z};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                real v = (real)1;
-                pw[w][lane][d][0] = v;
-#pragma unroll
-                for (int j = 1; j < PMAX; ++j)
-                    if (j < p) {
-                        v = v * x[d] * inv[j];
-                        pw[w][lane][d][j] = v;
-                    }
-            }
-            mm[w][lane][0] = a.w;
-            mm[w][lane][1] = b.x;
-            mm[w][lane][2] = b.y;
-        }
-        __syncwarp();
-        const int cnt = min(32, s1 - base);
-#pragma unroll
-        for (int r = 0; r < P2M_R; ++r) {
-            const int c = lane + 32 * r;
-            if (c < K) {
-                const unsigned n = mi[c];
-                const int nx = px(n), ny = py(n), nz = pz(n);
-                real sum = (real)0;
-                for (int d = 0; d < cnt; ++d) {
-                    const real(*q)[PMAX] = pw[w][d];
-                    if (nx > 0) sum += mm[w][d][0] * q[0][nx - 1] * q[1][ny] * q[2][nz];
-                    if (ny > 0) sum += mm[w][d][1] * q[0][nx] * q[1][ny - 1] * q[2][nz];
-                    if (nz > 0) sum += mm[w][d][2] * q[0][nx] * q[1][ny] * q[2][nz - 1];
-                }
-                acc[r] += sum;
-            }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < P2M_R; ++r) {
-        const int c = lane + 32 * r;
-        if (c < KP) Qrow[c] = c < K ? acc[r] : (real)0;
-    }
-}
-
 template <typename real>
 __device__ __forceinline__ void p2m_body(int p, int KP, int L, const int *leaf_start,
                                          const typename vec4<real>::t *A,
@@ -294,7 +198,8 @@ __device__ __forceinline__ void p2m_body(int p, int KP, int L, const int *leaf_s
     const bool live = key < (1ll << L);
     const int s0 = live ? leaf_start[key] : 0, s1 = live ? leaf_start[key + 1] : 0;
     const long long hid = (1ll << L) + key;
-    p2m_run<real>(p, KP, live, s0, s1, A, B, live ? Q + hid * KP : Q);
+    __shared__ P2MScratch<real> sc;
+    p2m_run<real>(p, KP, live, s0, s1, A, B, live ? Q + hid * KP : Q, sc);
 }
 
 template <typename real>
@@ -344,7 +249,8 @@ __global__ void __launch_bounds__(32 * P2M_W) k_ap2m(int p, int KP, int nleaf, c
     const bool live = li < nleaf;
     const int c = live ? leaves[li] : 0;
     const int s0 = live ? p0[c] : 0, s1 = live ? s0 + np[c] : 0;
-    p2m_run<real>(p, KP, live, s0, s1, A, B, Q + (long long)c * KP);
+    __shared__ P2MScratch<real> sc;
+    p2m_run<real>(p, KP, live, s0, s1, A, B, Q + (long long)c * KP, sc);
 }
 
 template <typename real>

@@ -17,6 +17,7 @@
 // Thread layout: warp w owns coefficient rows 8w..8w+7, lane owns field
 // cells 4*lane..4*lane+3, so each thread keeps a 4 x 8 accumulator tile.
 #include "ccfmm_dev.cuh"
+#include "stages.cuh"
 
 #include <stdlib.h>
 #include <string.h>
@@ -589,176 +590,6 @@ static void am2l_dispatch(int p, int KP, const int4 *items, int nitems, const in
 #undef AM2L
 }
 
-// ---------------------------------------------------------------------------
-// The same contraction on the tensor cores, FP32 path (3xTF32: each operand
-// x = hi + lo with hi = tf32(x), lo = tf32(x - hi); A B ~ Alo Bhi + Ahi Blo +
-// Ahi Bhi with FP32 accumulation).  The operator of an item is built from
-// its D row for 16-row tiles, which the warp-level MMA (mma.sync m16n8k8,
-// TF32) takes directly from registers: a warp owns 16 pairs (rows) x all
-// KP columns, K in steps of 8; its A fragments are the scaled moments of the
-// 16 sources read from global memory, its B fragments M[k][n] = D~_{n+k}.
-//   BIG:   one item per block (groups of more than 16 pairs, items of at
-//          most 512): the block first stores every B fragment of the item's
-//          operator, split, in shared memory (fragment order), then its four
-//          warps take the item's 16-pair chunks in turn.
-//   SMALL: one item per warp (groups of at most 16 pairs): B fragments are
-//          formed from the D row as they are used.
-// The contraction runs over the harmonic reduction (moments folded by the
-// Laplace identity of the D tensors, (p+1)^2 - 1 columns on either side):
-// Q rows, the index table and the accumulator VF are the reduced ones.
-// Fragment layouts (PTX ISA, mma.m16n8k8 with .tf32): g = lane / 4,
-// t = lane % 4; A: a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4);
-// B: b0 (k = t, n = g), b1 (k = t + 4, n = g); C: c0 (g, 2t), c1 (g, 2t + 1),
-// c2 (g + 8, 2t), c3 (g + 8, 2t + 1).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t tf32_rna(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
-{
-    hi = tf32_rna(x);
-    lo = tf32_rna(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1)
-{
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void red_add2(float *p, float a, float b)
-{
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
-}
-
-// scale tables of one item from its row of rho^-d (d = 0 .. p + 1, formed in
-// FP64 at the build), over the reduced columns: gk[c] = rho^-|k|,
-// en[c] = (-1)^|n| rho^-(|n|+1) (zero beyond the reduced count); threads
-// tid0.. step nth
-__device__ __forceinline__ void am2l_scales(int p, int KP, const float *pw, float *gk,
-                                            float *en, int tid0, int nth)
-{
-    const int K = red_count(p);
-    for (int c = tid0; c < KP; c += nth) {
-        float gv = 0.f, ev = 0.f;
-        if (c < K) {
-            const int d = red_order(c);
-            gv = pw[d];
-            ev = (d & 1) ? -pw[d + 1] : pw[d + 1];
-        }
-        gk[c] = gv;
-        en[c] = ev;
-    }
-}
-
-// 16 pairs (rows) from pair c0 of the item: A from the sources' moments,
-// B from bfrag (BIG, fragment order in shared memory) or from Dl and the
-// index table; the results added to the targets' accumulators
-// compile-time choice of the chunk's instruction order: 0 (default) forms the
-// A fragments of one k-step at a time and issues the three passes of each
-// column tile together; 1 loads every A element first and issues the passes
-// over all column tiles in turn (more registers)
-#ifndef CCFMM_AM2L_PRELOAD
-#define CCFMM_AM2L_PRELOAD 0
-#endif
-
-template <int KP, bool BIG>
-__device__ __forceinline__ void am2l_bfrag(int ks, int nt, const float4 *bfrag, const float *Dl,
-                                           const uint16_t *its, uint32_t &bh0, uint32_t &bh1,
-                                           uint32_t &bl0, uint32_t &bl1)
-{
-    constexpr int KS = KP / 8;
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    if (BIG) {
-        const float4 b = bfrag[(ks * KS + nt) * 32 + lane];
-        bh0 = __float_as_uint(b.x);
-        bh1 = __float_as_uint(b.y);
-        bl0 = __float_as_uint(b.z);
-        bl1 = __float_as_uint(b.w);
-    } else {
-        const int k = 8 * ks + t, n = 8 * nt + g;
-        tf32_split(Dl[its[k * KP + n]], bh0, bl0);
-        tf32_split(Dl[its[(k + 4) * KP + n]], bh1, bl1);
-    }
-}
-
-template <int KP, bool BIG>
-__device__ __forceinline__ void am2l_mma_chunk(const int4 &item, int c0, const int *pt,
-                                               const int *ps, const float *Q, const float *gk,
-                                               const float *en, const float4 *bfrag,
-                                               const float *Dl, const uint16_t *its, float *VF)
-{
-    constexpr int KS = KP / 8;
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int r0 = c0 + g, r1 = c0 + g + 8;
-    const bool v0 = r0 < item.y, v1 = r1 < item.y;
-    const float *q0 = Q + (long long)(v0 ? ps[item.x + r0] : 0) * KP;
-    const float *q1 = Q + (long long)(v1 ? ps[item.x + r1] : 0) * KP;
-    float c[KS][4];
-#pragma unroll
-    for (int n = 0; n < KS; ++n) c[n][0] = c[n][1] = c[n][2] = c[n][3] = 0.f;
-#if CCFMM_AM2L_PRELOAD
-    float x[KS][4];
-#pragma unroll
-    for (int ks = 0; ks < KS; ++ks) {
-        const int col = 8 * ks + t;
-        x[ks][0] = v0 ? q0[col] : 0.f;
-        x[ks][1] = v1 ? q1[col] : 0.f;
-        x[ks][2] = v0 ? q0[col + 4] : 0.f;
-        x[ks][3] = v1 ? q1[col + 4] : 0.f;
-    }
-#endif
-#pragma unroll
-    for (int ks = 0; ks < KS; ++ks) {
-        const int col = 8 * ks + t;
-        const float g0 = gk[col], g4 = gk[col + 4];
-#if CCFMM_AM2L_PRELOAD
-        const float y0 = x[ks][0], y1 = x[ks][1], y2 = x[ks][2], y3 = x[ks][3];
-#else
-        const float y0 = v0 ? q0[col] : 0.f, y1 = v1 ? q1[col] : 0.f;
-        const float y2 = v0 ? q0[col + 4] : 0.f, y3 = v1 ? q1[col + 4] : 0.f;
-#endif
-        uint32_t ah[4], al[4];
-        tf32_split(y0 * g0, ah[0], al[0]);
-        tf32_split(y1 * g0, ah[1], al[1]);
-        tf32_split(y2 * g4, ah[2], al[2]);
-        tf32_split(y3 * g4, ah[3], al[3]);
-#if CCFMM_AM2L_PRELOAD
-        uint32_t bh0[KS], bh1[KS], bl0[KS], bl1[KS];
-#pragma unroll
-        for (int nt = 0; nt < KS; ++nt)
-            am2l_bfrag<KP, BIG>(ks, nt, bfrag, Dl, its, bh0[nt], bh1[nt], bl0[nt], bl1[nt]);
-#pragma unroll
-        for (int nt = 0; nt < KS; ++nt) mma_tf32(c[nt], al, bh0[nt], bh1[nt]);
-#pragma unroll
-        for (int nt = 0; nt < KS; ++nt) mma_tf32(c[nt], ah, bl0[nt], bl1[nt]);
-#pragma unroll
-        for (int nt = 0; nt < KS; ++nt) mma_tf32(c[nt], ah, bh0[nt], bh1[nt]);
-#else
-#pragma unroll
-        for (int nt = 0; nt < KS; ++nt) {
-            uint32_t bh0, bh1, bl0, bl1;
-            am2l_bfrag<KP, BIG>(ks, nt, bfrag, Dl, its, bh0, bh1, bl0, bl1);
-            mma_tf32(c[nt], al, bh0, bh1);
-            mma_tf32(c[nt], ah, bl0, bl1);
-            mma_tf32(c[nt], ah, bh0, bh1);
-        }
-#endif
-    }
-    const int t0 = v0 ? pt[item.x + r0] : -1, t1 = v1 ? pt[item.x + r1] : -1;
-#pragma unroll
-    for (int nt = 0; nt < KS; ++nt) {
-        const int col = 8 * nt + 2 * t;
-        const float e0 = en[col], e1 = en[col + 1];
-        if (t0 >= 0) red_add2(VF + (long long)t0 * KP + col, c[nt][0] * e0, c[nt][1] * e1);
-        if (t1 >= 0) red_add2(VF + (long long)t1 * KP + col, c[nt][2] * e0, c[nt][3] * e1);
-    }
-}
-
 template <int KP>
 __global__ void __launch_bounds__(128) k_am2l_mma_big(int p, const int4 *items, const int *pt,
                                                       const int *ps, const float *rpow,
@@ -766,31 +597,8 @@ __global__ void __launch_bounds__(128) k_am2l_mma_big(int p, const int4 *items, 
                                                       const uint16_t *it, const float *Q,
                                                       float *VF)
 {
-    constexpr int KS = KP / 8;
     extern __shared__ __align__(16) unsigned char smraw[];
-    float4 *bfrag = reinterpret_cast<float4 *>(smraw);  // [KS * KS * 32]
-    float *Dl = reinterpret_cast<float *>(bfrag + KS * KS * 32);  // [ldD]
-    float *gk = Dl + ldD, *en = gk + KP;                          // [KP], [KP]
-    const int4 item = items[blockIdx.x];
-    const int tid = threadIdx.x;
-    const float *Drow = D + (long long)item.z * ldD;
-    for (int i = tid; i < ldD; i += blockDim.x) Dl[i] = Drow[i];
-    am2l_scales(p, KP, rpow + (long long)item.z * (PMAX + 2), gk, en, tid, blockDim.x);
-    __syncthreads();
-    for (int idx = tid; idx < KS * KS * 32; idx += blockDim.x) {
-        const int tile = idx >> 5, ln = idx & 31;
-        const int ks = tile / KS, nt = tile - ks * KS;
-        const int k = 8 * ks + (ln & 3), n = 8 * nt + (ln >> 2);
-        uint32_t h0, l0, h1, l1;
-        tf32_split(Dl[it[k * KP + n]], h0, l0);
-        tf32_split(Dl[it[(k + 4) * KP + n]], h1, l1);
-        bfrag[idx] = make_float4(__uint_as_float(h0), __uint_as_float(h1), __uint_as_float(l0),
-                                 __uint_as_float(l1));
-    }
-    __syncthreads();
-    const int warp = tid >> 5;
-    for (int c0 = 16 * warp; c0 < item.y; c0 += 64)
-        am2l_mma_chunk<KP, true>(item, c0, pt, ps, Q, gk, en, bfrag, Dl, it, VF);
+    am2l_big_item<KP>(p, items[blockIdx.x], pt, ps, rpow, D, ldD, it, Q, VF, smraw);
 }
 
 template <int KP>
@@ -801,23 +609,7 @@ __global__ void __launch_bounds__(128) k_am2l_mma_small(int p, const int4 *items
                                                         const float *Q, float *VF)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    uint16_t *its = reinterpret_cast<uint16_t *>(smraw);  // [KP * KP] index table
-    float *wbase = reinterpret_cast<float *>(smraw + ((KP * KP * 2 + 15) & ~15));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per = ((ldD + 2 * KP) + 3) & ~3;  // floats per warp
-    float *Dl = wbase + warp * per;
-    float *gk = Dl + ldD, *en = gk + KP;
-    for (int i = threadIdx.x; i < KP * KP; i += blockDim.x) its[i] = it[i];
-    __syncthreads();
-    const int ii = blockIdx.x * 4 + warp;
-    if (ii >= nitems) return;
-    const int4 item = items[ii];
-    const float *Drow = D + (long long)item.z * ldD;
-    for (int i = lane; i < ldD; i += 32) Dl[i] = Drow[i];
-    am2l_scales(p, KP, rpow + (long long)item.z * (PMAX + 2), gk, en, lane, 32);
-    __syncwarp();
-    for (int c0 = 0; c0 < item.y; c0 += 16)
-        am2l_mma_chunk<KP, false>(item, c0, pt, ps, Q, gk, en, nullptr, Dl, its, VF);
+    am2l_small_items<KP>(p, items, nitems, blockIdx.x, pt, ps, rpow, D, ldD, it, Q, VF, smraw);
 }
 
 template <int KP>
@@ -825,18 +617,15 @@ static void run_am2l_mma(int p, const int4 *items, int nitems, bool big, const i
                          const int *ps, const float *rpow, const float *D, int ldD,
                          const uint16_t *it, const float *Q, float *VF, cudaStream_t s)
 {
-    constexpr int KS = KP / 8;
     note_launch();
     if (big) {
-        const size_t smem = (size_t)KS * KS * 32 * sizeof(float4) +
-                            sizeof(float) * (ldD + 2 * KP) + 16;
+        const size_t smem = am2l_big_smem<KP>(ldD);
         cudaFuncSetAttribute(k_am2l_mma_big<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         k_am2l_mma_big<KP><<<(unsigned)nitems, 128, smem, s>>>(p, items, pt, ps, rpow, D, ldD,
                                                                 it, Q, VF);
     } else {
-        const int per = ((ldD + 2 * KP) + 3) & ~3;
-        const size_t smem = ((KP * KP * 2 + 15) & ~15) + sizeof(float) * 4 * per + 16;
+        const size_t smem = am2l_small_smem<KP>(ldD);
         cudaFuncSetAttribute(k_am2l_mma_small<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         k_am2l_mma_small<KP><<<(unsigned)((nitems + 3) / 4), 128, smem, s>>>(
@@ -862,25 +651,11 @@ constexpr int AF_W = 8;
 __global__ void __launch_bounds__(32 * AF_W) k_afold(int p, int KPF, int KRP, int nc,
                                                      const float *Q, float *Qr)
 {
-    __shared__ float row[AF_W][((nterms(PMAX) - 1 + 7) / 8) * 8];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ float row[AF_W][AF_ROW];
+    const int w = threadIdx.x >> 5;
     const long long c = (long long)blockIdx.x * AF_W + w;
     if (c >= nc) return;
-    const int K = nterms(p) - 1, KR = red_count(p);
-    for (int j = lane; j < K; j += 32) row[w][j] = Q[c * KPF + j];
-    __syncwarp();
-    if (lane >= 1 && lane < p) {
-        const int k = lane + 1, base = nterms(k - 1) - 1;
-        for (int z = k; z >= 2; --z)
-            for (int y = 0; y <= k - z; ++y) {
-                const float v = row[w][base + z * (2 * k + 3 - z) / 2 + y];
-                const int zt = z - 2, lt = base + zt * (2 * k + 3 - zt) / 2;
-                row[w][lt + y] -= v;      // (x + 2, y, z - 2)
-                row[w][lt + y + 2] -= v;  // (x, y + 2, z - 2)
-            }
-    }
-    __syncwarp();
-    for (int r = lane; r < KRP; r += 32) Qr[c * KRP + r] = r < KR ? row[w][red_full(r)] : 0.f;
+    afold_cell(p, KPF, KRP, c, Q, Qr, row[w]);
 }
 
 // the reduced index table from the full one: itr[k][n] = it[full k][full n]

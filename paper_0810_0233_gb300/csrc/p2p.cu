@@ -3,6 +3,7 @@
 // updateField), the final unpermute + energy (E = -1/2 sum m.H), and the
 // FP64 direct sum used to measure the error of the fast method.
 #include "ccfmm_dev.cuh"
+#include "stages.cuh"
 
 #include <stdlib.h>
 #include <string.h>
@@ -10,480 +11,6 @@
 #include <algorithm>
 
 namespace ccfmm {
-
-// sources staged per batch and resident blocks per SM of the FP32 kernels
-// (the register budget; FP64 keeps 4); compile-time tunables
-#ifndef CCFMM_P2P_CH
-#define CCFMM_P2P_CH 1024
-#endif
-#ifndef CCFMM_P2P_MINB
-#define CCFMM_P2P_MINB 6
-#endif
-#ifndef CCFMM_P2P_UNROLL
-#define CCFMM_P2P_UNROLL 4
-#endif
-constexpr int P2P_T = 128;    // threads per block
-constexpr int P2P_CH = CCFMM_P2P_CH;  // sources staged in shared memory per batch
-constexpr int P2P_UNROLL = CCFMM_P2P_UNROLL;  // unroll of the pair loop
-constexpr int P2P_NE = 256;   // near-list entries whose metadata is staged at once
-template <typename real> constexpr int p2p_minb() { return sizeof(real) == 4 ? CCFMM_P2P_MINB : 4; }
-
-template <typename real> __device__ __forceinline__ real rsq(real r2);
-// one MUFU operation: separations here are never subnormal, so the
-// subnormal-range handling that rsqrtf carries is not needed
-template <> __device__ __forceinline__ float rsq<float>(float r2)
-{
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(r2));
-    return r;
-}
-template <> __device__ __forceinline__ double rsq<double>(double r2) { return 1.0 / sqrt(r2); }
-
-// Field of dipole (m) at s on the target t: h += [3 (m.u) u - m] / r^3,
-// written as h += r^-3 (3 (m.r) r^-2 r - m).  SELF: the source may sit on the
-// target (r = 0), which then contributes nothing.
-template <typename real, bool SELF>
-__device__ __forceinline__ void dip_pair(real tx, real ty, real tz, real sx, real sy, real sz,
-                                         real mx, real my, real mz, real &hx, real &hy, real &hz)
-{
-    real rx = tx - sx, ry = ty - sy, rz = tz - sz;
-    real r2 = rx * rx + ry * ry + rz * rz;
-    real ri = rsq<real>(r2);
-    if (SELF) ri = r2 > (real)0 ? ri : (real)0;
-    real ri2 = ri * ri;
-    real ri3 = ri2 * ri;
-    real t = (real)3 * (mx * rx + my * ry + mz * rz) * ri2;
-    hx += ri3 * (t * rx - mx);
-    hy += ri3 * (t * ry - my);
-    hz += ri3 * (t * rz - mz);
-}
-
-// targets per thread, and whether target groups are padded to whole warps
-// (then all lanes of a warp share one stripe of sources: broadcast shared
-// loads, uniform loop bounds)
-#ifndef CCFMM_P2P_TPT
-#define CCFMM_P2P_TPT 2
-#endif
-#ifndef CCFMM_P2P_WARPS
-#define CCFMM_P2P_WARPS 0
-#endif
-constexpr int P2P_TPT = CCFMM_P2P_TPT;
-constexpr bool P2P_WARP_STRIPES = CCFMM_P2P_WARPS != 0;
-
-template <typename real, bool SELF>
-__device__ __forceinline__ void p2p_range(const typename vec4<real>::t *sp,
-                                          const typename vec2<real>::t *sm, int j0, int j1,
-                                          const real (&tx)[P2P_TPT][3], real (&hs)[P2P_TPT][3])
-{
-#pragma unroll P2P_UNROLL
-    for (int j = j0; j < j1; ++j) {
-        typename vec4<real>::t s = sp[j];
-        typename vec2<real>::t m = sm[j];
-#pragma unroll
-        for (int i = 0; i < P2P_TPT; ++i)
-            dip_pair<real, SELF>(tx[i][0], tx[i][1], tx[i][2], s.x, s.y, s.z, s.w, m.x, m.y,
-                                 hs[i][0], hs[i][1], hs[i][2]);
-    }
-}
-
-// contiguous stripe [j0, j1) of a batch of len sources; the chunk length is
-// odd so that lanes of different stripes read different shared-memory banks
-__device__ __forceinline__ void stripe_range(int len, int S, int stripe, int &j0, int &j1)
-{
-    int chunk = ((len + S - 1) / S) | 1;
-    j0 = min(len, stripe * chunk);
-    j1 = min(len, j0 + chunk);
-}
-
-// FP32 near field in packed two-lane arithmetic (f32x2 add/mul/fma): the
-// staged sources are stored in pairs, {x0 x1 y0 y1} {z0 z1 mx0 mx1}
-// {my0 my1 mz0 mz1}, and each step of the pair loop takes two sources in
-// the two lanes against one target whose coordinates are duplicated once.
-// The two lanes keep separate sums, added at the end of the range.  An odd
-// batch is padded with a source of zero moment at 1e30 (r^2 overflows to
-// inf, so r^-1 = 0 and it adds exactly zero).  Compile-time switch
-// CCFMM_P2P_X2 (FP32 only; the FP64 path is always scalar).
-#ifndef CCFMM_P2P_X2
-#define CCFMM_P2P_X2 1
-#endif
-constexpr bool P2P_X2 = CCFMM_P2P_X2 != 0;
-
-__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
-
-template <bool SELF>
-__device__ __forceinline__ void p2p_range_x2(const float4 (*sq)[3], int u0, int u1,
-                                             const float (&tx)[P2P_TPT][3],
-                                             float (&hs)[P2P_TPT][3])
-{
-    float2 tp[P2P_TPT][3], h[P2P_TPT][3];
-#pragma unroll
-    for (int i = 0; i < P2P_TPT; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            tp[i][k] = make_float2(tx[i][k], tx[i][k]);
-            h[i][k] = make_float2(0.f, 0.f);
-        }
-    const float2 three = make_float2(3.f, 3.f);
-#pragma unroll P2P_UNROLL
-    for (int u = u0; u < u1; ++u) {
-        const float4 a = sq[u][0], b = sq[u][1], c = sq[u][2];
-        const float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
-        const float2 sz = make_float2(b.x, b.y), mx = make_float2(b.z, b.w);
-        const float2 my = make_float2(c.x, c.y), mz = make_float2(c.z, c.w);
-#pragma unroll
-        for (int i = 0; i < P2P_TPT; ++i) {
-            const float2 rx = __fadd2_rn(tp[i][0], f2neg(sx));
-            const float2 ry = __fadd2_rn(tp[i][1], f2neg(sy));
-            const float2 rz = __fadd2_rn(tp[i][2], f2neg(sz));
-            const float2 r2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
-            float2 ri = make_float2(rsq<float>(r2.x), rsq<float>(r2.y));
-            if (SELF) {
-                ri.x = r2.x > 0.f ? ri.x : 0.f;
-                ri.y = r2.y > 0.f ? ri.y : 0.f;
-            }
-            const float2 ri2 = __fmul2_rn(ri, ri);
-            const float2 ri3 = __fmul2_rn(ri2, ri);
-            const float2 mr = __ffma2_rn(mz, rz, __ffma2_rn(my, ry, __fmul2_rn(mx, rx)));
-            const float2 t = __fmul2_rn(__fmul2_rn(three, mr), ri2);
-            h[i][0] = __ffma2_rn(ri3, __ffma2_rn(t, rx, f2neg(mx)), h[i][0]);
-            h[i][1] = __ffma2_rn(ri3, __ffma2_rn(t, ry, f2neg(my)), h[i][1]);
-            h[i][2] = __ffma2_rn(ri3, __ffma2_rn(t, rz, f2neg(mz)), h[i][2]);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < P2P_TPT; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) hs[i][k] += h[i][k].x + h[i][k].y;
-}
-
-// the staged-source buffer of p2p_leaf (PCH sources, 24 bytes each), in the
-// scalar layout (sp[PCH] positions + first moment component, sm[PCH] the
-// other two) or the packed pair layout above
-template <typename real, int PCH> struct SrcStage {
-    typedef typename vec4<real>::t R4;
-    typedef typename vec2<real>::t R2;
-    static constexpr bool X2 = P2P_X2 && sizeof(real) == 4;
-    unsigned char *base;
-    __device__ __forceinline__ void put(int v, const R4 &a, const R2 &m) const
-    {
-        if constexpr (X2) {
-            float *q = reinterpret_cast<float *>(base) + 12 * (v >> 1) + (v & 1);
-            q[0] = a.x;
-            q[2] = a.y;
-            q[4] = a.z;
-            q[6] = a.w;
-            q[8] = m.x;
-            q[10] = m.y;
-        } else {
-            reinterpret_cast<R4 *>(base)[v] = a;
-            reinterpret_cast<R2 *>(base + PCH * sizeof(R4))[v] = m;
-        }
-    }
-    // after the len sources of a batch are staged (one thread)
-    __device__ __forceinline__ void pad(int len) const
-    {
-        if constexpr (X2) {
-            if (len & 1) {
-                R4 a;
-                a.x = a.y = a.z = 1e30f;
-                a.w = 0.f;
-                R2 m;
-                m.x = m.y = 0.f;
-                put(len, a, m);
-            }
-        }
-    }
-    template <bool SELF>
-    __device__ __forceinline__ void range(int len, int S, int stripe,
-                                          const real (&tx)[P2P_TPT][3],
-                                          real (&hs)[P2P_TPT][3]) const
-    {
-        int j0, j1;
-        if constexpr (X2) {
-            stripe_range((len + 1) >> 1, S, stripe, j0, j1);
-            p2p_range_x2<SELF>(reinterpret_cast<const float4 (*)[3]>(base), j0, j1, tx, hs);
-        } else {
-            stripe_range(len, S, stripe, j0, j1);
-            p2p_range<real, SELF>(reinterpret_cast<const R4 *>(base),
-                                  reinterpret_cast<const R2 *>(base + PCH * sizeof(R4)), j0, j1,
-                                  tx, hs);
-        }
-    }
-};
-
-// Smooth field (Eq. H, H = -grad V) of one target from its leaf's Taylor
-// coefficients vs[] (column t - 1 holds the multi-index t), x relative to
-// the leaf centre:  H_a = -sum_{|m| <= p-1} V_{m+e_a} x^m / m!  (returns the
-// three sums; the caller subtracts them).  The order
-// P = p is a template parameter: the loops over m = (mx, my, mz) unroll, the
-// monomial x^m/m! is one product of the per-axis powers' partial products,
-// and each term is three FMAs on broadcast coefficient loads.  The fused
-// near-field epilogue and the standalone L2P kernel both use it, so the two
-// evaluation paths give the same bits.
-template <typename real> struct Sum3 {
-    real x, y, z;
-};
-
-template <typename real, int P>
-__device__ __forceinline__ Sum3<real> l2p_fixed(const real *vs, real x, real y, real z)
-{
-    real px[P], py[P], pz[P];
-    px[0] = py[0] = pz[0] = (real)1;
-#pragma unroll
-    for (int j = 1; j < P; ++j) {
-        const real inv = (real)1 / (real)j;  // j is a compile-time constant here
-        px[j] = px[j - 1] * x * inv;
-        py[j] = py[j - 1] * y * inv;
-        pz[j] = pz[j - 1] * z * inv;
-    }
-    real s0 = (real)0, s1 = (real)0, s2 = (real)0;
-#pragma unroll
-    for (int mx = 0; mx < P; ++mx) {
-#pragma unroll
-        for (int my = 0; my < P - mx; ++my) {
-            const real b = px[mx] * py[my];
-#pragma unroll
-            for (int mz = 0; mz < P - mx - my; ++mz) {
-                const real mono = b * pz[mz];
-                s0 += vs[midx(mx + 1, my, mz) - 1] * mono;
-                s1 += vs[midx(mx, my + 1, mz) - 1] * mono;
-                s2 += vs[midx(mx, my, mz + 1) - 1] * mono;
-            }
-        }
-    }
-    return Sum3<real>{s0, s1, s2};
-}
-
-// the sums of l2p_fixed for a run-time order (the field is H - sums)
-template <typename real>
-__device__ __forceinline__ Sum3<real> l2p_eval(int p, const real *vs, real x, real y, real z)
-{
-    switch (p) {
-    case 1: return l2p_fixed<real, 1>(vs, x, y, z);
-    case 2: return l2p_fixed<real, 2>(vs, x, y, z);
-    case 3: return l2p_fixed<real, 3>(vs, x, y, z);
-    case 4: return l2p_fixed<real, 4>(vs, x, y, z);
-    case 5: return l2p_fixed<real, 5>(vs, x, y, z);
-    case 6: return l2p_fixed<real, 6>(vs, x, y, z);
-    case 7: return l2p_fixed<real, 7>(vs, x, y, z);
-    default: return l2p_fixed<real, 8>(vs, x, y, z);
-    }
-}
-
-// One block per target leaf; writes H = smooth field (L2P) + near field of
-// every dipole of the leaf.
-//  * Each thread owns two targets and one stripe (a contiguous chunk) of the
-//    staged sources; S = floor(128 / target groups) stripes per batch.
-//  * Sources are staged in shared memory relative to the target leaf centre,
-//    s_j = l_j - (c_target - c_source), so differences are formed between
-//    numbers of leaf-size magnitude; the shift is computed once per near
-//    entry in FP64.
-//  * The leaf's own dipoles are processed first, with the r = 0 test (a
-//    source on the field point contributes nothing, Appendix updateField);
-//    no other leaf can hold a point at the target's position.
-// Near entries of the complete tree: a partner leaf key at the same level
-// and its integer cell offset; the shift is the offset times the leaf widths.
-struct UniEnts {
-    const int *leaf_start;
-    const NearEnt *near;
-    double wx, wy, wz;
-    int self;
-    template <typename R4>
-    __device__ __forceinline__ int get(int e, int &st, R4 &sh) const
-    {
-        NearEnt x = near[e];
-        st = leaf_start[x.src];
-        sh.x = (decltype(sh.x))((double)x.ox * wx);
-        sh.y = (decltype(sh.x))((double)x.oy * wy);
-        sh.z = (decltype(sh.x))((double)x.oz * wz);
-        sh.w = (decltype(sh.x))0;
-        return (x.src == self) ? 0 : leaf_start[x.src + 1] - st;
-    }
-};
-
-template <typename real, typename Ents, bool L2P, int PT = P2P_T, int PCH = P2P_CH>
-__device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, const Ents &ents,
-                                         const double *Vrow, const typename vec4<real>::t *A,
-                                         const typename vec2<real>::t *B,
-                                         typename vec4<real>::t *H);
-
-template <typename real, bool L2P>
-__device__ __forceinline__ void p2p_body(int p, int KP, int L, const int *leaf_start,
-                                         const int2 *near_nl, const NearEnt *near, const Geom *g,
-                                         const typename vec4<real>::t *A,
-                                         const typename vec2<real>::t *B, const double *V,
-                                         typename vec4<real>::t *H, long long key)
-{
-    const int t0 = leaf_start[key], nt = leaf_start[key + 1] - t0;
-    if (nt == 0) return;
-    const int2 nlk = near_nl[key];  // (first entry, count) of the leaf's near list
-    const long long hid = (1ll << L) + key;
-    UniEnts ents{leaf_start, near, g->w[L][0], g->w[L][1], g->w[L][2], (int)key};
-    // V == nullptr: near field only (L2P by k_l2p once V is complete)
-    p2p_leaf<real, UniEnts, L2P>(p, t0, nt, nlk.x, nlk.x + nlk.y, ents,
-                                 V ? V + hid * KP : nullptr, A, B, H);
-}
-
-// The near field (and, with Vrow, the smooth field) of one leaf's nt dipoles
-// at t0..: its own dipoles first, then the entries e0..e1 of its near list,
-// each giving a source range and the shift (target centre - source centre).
-// L2P = false compiles the near field alone (Vrow is then ignored): without
-// the smooth-field epilogue the kernel needs fewer registers.
-template <typename real, typename Ents, bool L2P, int PT, int PCH>
-__device__ __forceinline__ void p2p_leaf(int p, int t0, int nt, int e0, int e1, const Ents &ents,
-                                         const double *Vrow, const typename vec4<real>::t *A,
-                                         const typename vec2<real>::t *B,
-                                         typename vec4<real>::t *H)
-{
-    typedef typename vec4<real>::t R4;
-    typedef typename vec2<real>::t R2;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    R4 *sp = reinterpret_cast<R4 *>(smraw);              // [PCH]
-    R2 *sm = reinterpret_cast<R2 *>(sp + PCH);         // [PCH]
-    R4 *esh = reinterpret_cast<R4 *>(sm + PCH);        // [P2P_NE] source shift
-    int *est = reinterpret_cast<int *>(esh + P2P_NE);     // [P2P_NE] source start
-    int *epf = est + P2P_NE;                              // [P2P_NE + 1] prefix of counts
-    real *vs = reinterpret_cast<real *>(epf + P2P_NE + 4);  // [KP]
-    __shared__ int wsum[PT / 32];
-    const SrcStage<real, PCH> stage{smraw};
-    static_assert(PCH % 2 == 0, "the packed layout stages sources in pairs");
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = nterms(p) - 1;
-    const bool with_l2p = L2P && Vrow != nullptr;
-    constexpr int NE = 2 * PT < P2P_NE ? 2 * PT : P2P_NE;  // entries per metadata chunk
-    if (with_l2p)
-        for (int c = tid; c < K; c += PT) vs[c] = (real)Vrow[c];
-
-    for (int tb = 0; tb < nt; tb += P2P_TPT * PT) {
-        const int ntc = min(nt - tb, P2P_TPT * PT);
-        const int ngrp = P2P_WARP_STRIPES ? 32 * ((ntc + 32 * P2P_TPT - 1) / (32 * P2P_TPT))
-                                          : (ntc + P2P_TPT - 1) / P2P_TPT;
-        const int S = max(1, PT / ngrp);
-        const int q = tid % ngrp, stripe = tid / ngrp;
-        const bool active = stripe < S;
-        const int i0 = tb + P2P_TPT * q;
-        real tx[P2P_TPT][3], hs[P2P_TPT][3];
-#pragma unroll
-        for (int i = 0; i < P2P_TPT; ++i) {
-            R4 a = A[t0 + min(i0 + i, tb + ntc - 1)];
-            tx[i][0] = a.x;
-            tx[i][1] = a.y;
-            tx[i][2] = a.z;
-            hs[i][0] = hs[i][1] = hs[i][2] = (real)0;
-        }
-
-        // 1) the leaf's own dipoles (shift 0), r = 0 possible
-        for (int b0 = 0; b0 < nt; b0 += PCH) {
-            const int len = min(PCH, nt - b0);
-            __syncthreads();
-            for (int v = tid; v < len; v += PT) stage.put(v, A[t0 + b0 + v], B[t0 + b0 + v]);
-            if (tid == 0) stage.pad(len);
-            __syncthreads();
-            if (active) stage.template range<true>(len, S, stripe, tx, hs);
-        }
-        // 2) the other near leaves, in chunks of NE entries (each thread
-        // stages the metadata of two entries of a chunk)
-        for (int ec = e0; ec < e1; ec += NE) {
-            const int nec = min(NE, e1 - ec);
-            __syncthreads();
-            int c0 = 0, c1 = 0;
-            for (int r = 0; r < 2; ++r) {
-                int e = 2 * tid + r;
-                int cnt = 0;
-                if (e < nec) {
-                    int st;
-                    R4 sh;
-                    cnt = ents.get(ec + e, st, sh);
-                    est[e] = st;
-                    esh[e] = sh;
-                }
-                if (r == 0) c0 = cnt; else c1 = cnt;
-            }
-            // exclusive prefix of the counts (two per thread)
-            int v = c0 + c1, x = v;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (lane == 31) wsum[warp] = x;
-            __syncthreads();
-            int base = 0;
-            for (int w = 0; w < warp; ++w) base += wsum[w];
-            int ex = base + x - v;
-            if (2 * tid < nec) epf[2 * tid] = ex;
-            if (2 * tid + 1 < nec) epf[2 * tid + 1] = ex + c0;
-            if (tid == 0) {
-                int tot = 0;
-                for (int w = 0; w < PT / 32; ++w) tot += wsum[w];
-                epf[nec] = tot;
-            }
-            __syncthreads();
-            const int total = epf[nec];
-            for (int b0 = 0; b0 < total; b0 += PCH) {
-                const int len = min(PCH, total - b0);
-                if (b0) __syncthreads();
-                for (int e = warp; e < nec; e += PT / 32) {
-                    int lo = max(epf[e], b0), hi = min(epf[e + 1], b0 + len);
-                    if (lo >= hi) continue;
-                    int off = est[e] - epf[e];
-                    R4 sh = esh[e];
-                    for (int gv = lo + lane; gv < hi; gv += 32) {
-                        R4 a = A[off + gv];
-                        R4 o;
-                        o.x = a.x - sh.x;
-                        o.y = a.y - sh.y;
-                        o.z = a.z - sh.z;
-                        o.w = a.w;
-                        stage.put(gv - b0, o, B[off + gv]);
-                    }
-                }
-                if (tid == 0) stage.pad(len);
-                __syncthreads();
-                if (active) stage.template range<false>(len, S, stripe, tx, hs);
-                __syncthreads();
-            }
-        }
-        // 3) reduce the stripes, add the smooth field, store
-        __syncthreads();
-        real *red = reinterpret_cast<real *>(sp);
-#pragma unroll
-        for (int i = 0; i < P2P_TPT; ++i)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) red[(3 * P2P_TPT) * tid + 3 * i + k] = hs[i][k];
-        __syncthreads();
-        real f[P2P_TPT][3];
-#pragma unroll
-        for (int i = 0; i < P2P_TPT; ++i) f[i][0] = f[i][1] = f[i][2] = (real)0;
-        if (tid < ngrp) {
-            for (int st = 0; st < S; ++st) {
-                const real *rr = red + (3 * P2P_TPT) * (st * ngrp + tid);
-#pragma unroll
-                for (int i = 0; i < P2P_TPT; ++i)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) f[i][k] += rr[3 * i + k];
-            }
-        }
-        __syncthreads();
-        if (tid < ngrp) {
-#pragma unroll
-            for (int i = 0; i < P2P_TPT; ++i) {
-                if (with_l2p) {
-                    const Sum3<real> sl = l2p_eval<real>(p, vs, tx[i][0], tx[i][1], tx[i][2]);
-                    f[i][0] -= sl.x;
-                    f[i][1] -= sl.y;
-                    f[i][2] -= sl.z;
-                }
-                R4 o;
-                o.x = f[i][0];
-                o.y = f[i][1];
-                o.z = f[i][2];
-                o.w = (real)0;
-                if (i0 + i < tb + ntc) H[t0 + i0 + i] = o;
-            }
-        }
-    }
-}
 
 template <typename real, bool L2P>
 __global__ void __launch_bounds__(P2P_T, p2p_minb<real>())
@@ -493,27 +20,6 @@ __global__ void __launch_bounds__(P2P_T, p2p_minb<real>())
 {
     p2p_body<real, L2P>(p, KP, L, leaf_start, near_nl, near, g, A, B, V, H, blockIdx.x);
 }
-
-// Near entries of the adaptive-depth tree: a partner leaf cell of any
-// level; the shift is the difference of the two cells' centres, in FP64.
-struct AdaEnts {
-    const int *p0, *np, *src;
-    const double4 *cen;
-    double cx, cy, cz;
-    int self;
-    template <typename R4>
-    __device__ __forceinline__ int get(int e, int &st, R4 &sh) const
-    {
-        const int b = src[e];
-        const double4 c = cen[b];
-        st = p0[b];
-        sh.x = (decltype(sh.x))(cx - c.x);
-        sh.y = (decltype(sh.x))(cy - c.y);
-        sh.z = (decltype(sh.x))(cz - c.z);
-        sh.w = (decltype(sh.x))0;
-        return b == self ? 0 : np[b];
-    }
-};
 
 // near field + smooth field of the adaptive tree's leaves, one block per
 // leaf; PT threads and PCH staged sources (a smaller block for the small
@@ -874,7 +380,6 @@ void launch_p2p(int p, int KP, int L, const int *leaf_start, const int2 *near_nl
 // L2P (Eq. H, H = -grad V) of every dipole of a leaf (one warp per leaf),
 // added to the near field that k_p2p stored without its fused L2P: the same
 // operations in the same order as the fused epilogue.
-constexpr int L2P_W = 4;  // leaves (warps) per block
 
 template <typename real, int P>
 __device__ __forceinline__ void l2p_body(int KP, int L, const int *leaf_start,
@@ -919,23 +424,10 @@ __global__ void __launch_bounds__(32 * L2P_W) k_al2p(int KP, int nleaf, const in
                                                      const double *V, typename vec4<real>::t *H)
 {
     __shared__ real vs[L2P_W][nterms(PMAX)];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int K = nterms(P) - 1;
+    const int w = threadIdx.x >> 5;
     const int li = blockIdx.x * L2P_W + w;
     if (li >= nleaf) return;
-    const int c = leaves[li];
-    const int t0 = p0[c], nt = np[c];
-    for (int k = lane; k < K; k += 32) vs[w][k] = (real)V[(long long)c * KP + k];
-    __syncwarp();
-    for (int i = lane; i < nt; i += 32) {
-        const typename vec4<real>::t a = A[t0 + i];
-        typename vec4<real>::t h = H[t0 + i];
-        const Sum3<real> sl = l2p_fixed<real, P>(vs[w], a.x, a.y, a.z);
-        h.x -= sl.x;
-        h.y -= sl.y;
-        h.z -= sl.z;
-        H[t0 + i] = h;
-    }
+    al2p_leaf<real, P>(KP, leaves[li], p0, np, A, V, H, vs[w]);
 }
 
 template <typename real>

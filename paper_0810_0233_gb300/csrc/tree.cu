@@ -3,6 +3,7 @@
 // non-empty-leaf histogram that selects the depth, leaf ranges, and the
 // sorted dipole arrays (coordinates relative to the leaf centre).
 #include "ccfmm_dev.cuh"
+#include "stages.cuh"
 
 #include <math.h>
 
@@ -297,14 +298,8 @@ template <typename real>
 __global__ void k_permute_moments(const double *mom, const int *perm, long long n,
                                   typename vec4<real>::t *A, typename vec2<real>::t *B)
 {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    long long i = perm[s];
-    A[s].w = (real)mom[3 * i];
-    typename vec2<real>::t bv;
-    bv.x = (real)mom[3 * i + 1];
-    bv.y = (real)mom[3 * i + 2];
-    B[s] = bv;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) permute_one<real>(s, mom, perm, A, B);
 }
 
 template <typename real>

@@ -273,3 +273,78 @@ def test_autotuner_picks_per_class_and_stays_exact():
             nc = len(f.cells())
             check_mixed(H[off[i]:off[i + 1]], E[i], V[c0:c0 + nc], f, p)
             c0 += nc
+
+
+def _forest(sizes, seed0):
+    rng = np.random.default_rng(seed0)
+    ps, ms = [], []
+    for i, n in enumerate(sizes):
+        pos, mom = W.clustered(n, seed=seed0 + i)
+        ps.append(pos + rng.uniform(-1e3, 1e3, 3))
+        ms.append(mom)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    return ps, ms, off, np.concatenate(ps), np.concatenate(ms)
+
+
+@pytest.mark.parametrize("p,theta,split", [(3, 0.5, 10.0), (5, 0.5, 18.0), (6, 0.4, 26.0)])
+def test_persistent_step_equals_oracle(p, theta, split):
+    """The persistent step kernel (one launch, task queue over all samples'
+    stages): every sample within the mixed bounds of the oracle, the same
+    fields as the graph of stage kernels to rounding, and a step = the
+    oracle's rotation then an evaluation."""
+    sizes = [300, 2200, 900, 5000, 1700]
+    ps, ms, off, pos, mom = _forest(sizes, 620 + p)
+    with C.Adaptive(pos, mom, p, theta, split=split, offsets=off, persistent=True) as g, \
+            C.Adaptive(pos, mom, p, theta, split=split, offsets=off) as r:
+        assert g.stats()["kernels_per_eval"] == 1
+        H, E = g.evaluate()
+        Hr, Er = r.evaluate()
+        assert rel(H, Hr) < 1e-6
+        assert np.allclose(E, Er, rtol=1e-6, atol=0)
+        Q, V = g.expansions()
+        c0 = 0
+        for i in range(len(sizes)):
+            f = O.OracleAFMM(ps[i], ms[i], p, theta, split)
+            f.run()
+            nc = len(f.cells())
+            check_mixed(H[off[i]:off[i + 1]], E[i], V[c0:c0 + nc], f, p)
+            c0 += nc
+        for step in range(2):
+            H, E = g.step(seed=21, step=step, max_angle=0.05)
+            Hr, Er = r.step(seed=21, step=step, max_angle=0.05)
+            mom = O.rotate_moments(mom, 21, step, 0.05)
+            assert np.allclose(g.moments(), mom, rtol=0, atol=1e-14)
+            assert rel(H, Hr) < 1e-6
+        i = 3
+        sl = slice(off[i], off[i + 1])
+        f = O.OracleAFMM(pos[sl], mom[sl], p, theta, split)
+        f.run()
+        assert rel(H[sl], f.field()) < TOLMIX
+        assert LP.dipole_max_err(H[sl], f.field()) < LP.DIPOLE_TOL
+
+
+def test_persistent_step_needs_the_mixed_tensor_core_path():
+    pos, mom = W.clustered(800, seed=3)
+    with pytest.raises(C.CCFMMError):
+        C.Adaptive(pos, mom, 4, 0.5, split=10.0, precision="fp64", persistent=True)
+    with pytest.raises(C.CCFMMError):
+        C.Adaptive(pos, mom, 7, 0.5, split=10.0, persistent=True)
+
+
+def test_persistent_step_wait_gives_up(monkeypatch):
+    """CCFMM_ASTEP_STALL=1 asks one task more of the M2L phase than the queue
+    holds, so the L2L tasks' bounded waits run out: the evaluation reports
+    CCFMM_ERR_TIMEOUT, and a handle built afterwards evaluates exactly."""
+    sizes = [500, 1200]
+    ps, ms, off, pos, mom = _forest(sizes, 77)
+    monkeypatch.setenv("CCFMM_ASTEP_STALL", "1")
+    with C.Adaptive(pos, mom, 4, 0.5, split=10.0, offsets=off, persistent=True) as g:
+        with pytest.raises(C.CCFMMError) as e:
+            g.evaluate()
+        assert e.value.status == C.ERR_TIMEOUT, e.value
+    monkeypatch.delenv("CCFMM_ASTEP_STALL")
+    with C.Adaptive(pos, mom, 4, 0.5, split=10.0, offsets=off, persistent=True) as g:
+        H, E = g.evaluate()
+        f = O.OracleAFMM(ps[1], ms[1], 4, 0.5, 10.0)
+        f.run()
+        assert rel(H[off[1]:off[2]], f.field()) < TOLMIX
