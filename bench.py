@@ -39,9 +39,13 @@ NCU_TRAFFIC = {"p2p": {"bytes": 112658432, "src": "e08033eddc6b"},
 TF32_PER_BF16 = 1.1 / 2.25
 
 
-def _src_hash(name):
-    with open(os.path.join(ROOT, "paper_0810_0233_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+def _src_hash(names):
+    """Hash of the kernel's source files (a name or a list of names)."""
+    h = hashlib.sha1()
+    for name in ([names] if isinstance(names, str) else names):
+        with open(os.path.join(ROOT, "paper_0810_0233_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def _peaks():
@@ -581,7 +585,7 @@ def main():
     KM = (P + 1) * (P + 1) - 1 if tc else K
     flops = {"p2p": 30.0 * st["p2p_pairs"], "m2l": 2.0 * KM * KM * st["far_pairs"]}
     tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
-    src = {"p2p": "p2p.cu", "m2l": "m2l_tc.cu" if tc else "m2l.cu"}
+    src = {"p2p": ["p2p.cu", "stages.cuh"], "m2l": "m2l_tc.cu" if tc else "m2l.cu"}
 
     def traffic(k):
         # the capture is of the 10^6-dipole ferrofluid: other workloads have none

@@ -69,10 +69,18 @@ def check_fp64(H, E, Q, V, f, pos_n, p):
     assert rel(V, f.locals()[:, cols]) < TOL64
 
 
+def energy_bar(f, Href):
+    """Bar on the mixed energy: 10 TOLMIX |E|, or, where the sum -1/2 sum m.H
+    cancels, what the field bar implies: |dE| = 1/2 |sum m.dH| <=
+    1/2 |m| |dH| (Cauchy-Schwarz) with |dH| < TOLMIX |H|."""
+    cs = 0.5 * np.linalg.norm(f.mom) * np.linalg.norm(Href)
+    return max(10 * TOLMIX * abs(f.energy()), TOLMIX * cs)
+
+
 def check_mixed(H, E, V, f, p):
     Href = f.field()
     assert rel(H, Href) < TOLMIX
-    assert abs(E - f.energy()) <= 10 * TOLMIX * abs(f.energy())
+    assert abs(E - f.energy()) <= energy_bar(f, Href)
     assert LP.dipole_max_err(H, Href) < LP.DIPOLE_TOL
     oc = f.cells()
     Vo = f.locals()[:, lib_to_oracle_cols(p)]
