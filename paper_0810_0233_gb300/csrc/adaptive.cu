@@ -809,14 +809,16 @@ __global__ void __launch_bounds__(256) k_aenergy(const long long *off, const dou
 // harmonic reduction) in one launch of persistent blocks of 128 threads that
 // take tasks from one queue.  A task is a (stage, tile) of all samples at
 // once: a chunk of dipoles for the rotation, the moment permutation and the
-// unpermute, four leaves (one warp each) for P2M and L2P, four cells of one
-// level for M2M and L2L, four cells for the fold, one M2L item of more than 16
-// pairs or four of at most 16, one leaf for the near field, one sample for
-// the energy.  The tasks of a stage form a phase; a task may wait for up to
-// two phases to be complete (done[ph] == need[ph]), and every phase it waits
-// for lies wholly before it in the queue.  Blocks take tasks in queue order
-// (one atomic counter), so the earliest unfinished task never waits on a
-// later one and the queue drains whatever number of blocks is resident.
+// unpermute, 16 leaves (a warp each, four at a time) for P2M and L2P, 16 cells
+// of one level for M2M and L2L, 16 cells for the fold, one M2L item of more
+// than 16 pairs or 16 of at most 16, one leaf for the near field, one sample
+// for the energy.  The tasks of a stage form a phase; a task may wait for up
+// to two phases to be complete (done[ph] == need[ph]), and every phase it
+// waits for lies wholly before it in the queue.  Blocks take queue indices in
+// order (one atomic counter; a block fetches its next index while its current
+// task runs), so the earliest unfinished task never waits on a later one and
+// the queue drains whatever number of blocks is resident.  A block remembers
+// the phases it has found complete and polls only for new ones.
 // Waits poll with a bound (poll_limit polls, nanosleep between them): a wait
 // that runs out sets err and its block stops; every block stops once err is
 // set, so the launch always ends.  The host zeroes head, err and done before
@@ -836,6 +838,9 @@ enum ATask : int {
     AT_ENERGY
 };
 constexpr int ACHUNK = 2048;  // dipoles per task of the elementwise stages
+constexpr int ACELLS = 16;    // cells (leaves) per task of the warp-per-cell stages
+constexpr int AGROUPS = 4;    // groups of four small M2L items per task
+constexpr int ASEEN = 256;    // phases whose completion a block remembers
 constexpr int ASTEP_T = 128;  // threads per block
 
 struct AStepArgs {
@@ -876,33 +881,45 @@ __device__ __forceinline__ int ld_acquire(const int *p)
 }
 
 // thread 0: wait (bounded) until phase ph is complete; false when the wait
-// ran out or another block has given up
-__device__ __forceinline__ bool astep_wait(const AStepArgs &a, int ph)
+// ran out or another block has given up.  seen: the phases this block has
+// already found complete (a phase stays complete for the rest of the launch);
+// fresh = true when a phase was newly found complete.
+__device__ __forceinline__ bool astep_wait(const AStepArgs &a, int ph, unsigned *seen,
+                                           bool &fresh)
 {
     if (ph < 0) return true;
+    if (ph < ASEEN && ((seen[ph >> 5] >> (ph & 31)) & 1u)) return true;
     const int need = a.need[ph];
     const int *done = a.ctl + 2 + ph;
     for (long long it = 0;; ++it) {
-        if (ld_acquire(done) >= need) return true;
+        if (ld_acquire(done) >= need) {
+            if (ph < ASEEN) seen[ph >> 5] |= 1u << (ph & 31);
+            fresh = true;
+            return true;
+        }
         if (it >= a.poll_limit || ld_acquire(a.ctl + 1)) return false;
         __nanosleep(it < 32 ? 64 : 512);
     }
 }
 
-// thread 0: the next task whose phases are complete, or x = -1 (queue empty,
-// or stop)
-__device__ __forceinline__ int4 astep_next(const AStepArgs &a)
+// thread 0: task nxt of the queue once its phases are complete, or x = -1
+// (queue empty, or stop); nxt becomes the queue index of the block's next
+// task, fetched while this one runs
+__device__ __forceinline__ int4 astep_take(const AStepArgs &a, int &nxt, unsigned *seen)
 {
     const int4 stop = make_int4(-1, 0, 0, 0);
     if (ld_acquire(a.ctl + 1)) return stop;
-    const int t = atomicAdd(a.ctl, 1);
+    const int t = nxt;
     if (t >= a.ntask) return stop;
     const int4 tk = a.tasks[t];
-    if (!astep_wait(a, (tk.w & 0xffff) - 1) || !astep_wait(a, (tk.w >> 16) - 1)) {
+    nxt = atomicAdd(a.ctl, 1);
+    bool fresh = false;
+    if (!astep_wait(a, (tk.w & 0xffff) - 1, seen, fresh) ||
+        !astep_wait(a, (tk.w >> 16) - 1, seen, fresh)) {
         atomicExch(a.ctl + 1, 1);
         return stop;
     }
-    __threadfence();
+    if (fresh) __threadfence();
     return tk;
 }
 
@@ -912,9 +929,14 @@ __global__ void __launch_bounds__(ASTEP_T, CCFMM_P2P_MINB) k_astep(const AStepAr
     constexpr int KRP = red_padded(P);
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int4 s_task;
+    __shared__ unsigned s_seen[ASEEN / 32];
     const int tid = threadIdx.x, w = tid >> 5;
+    int nxt = 0;
+    if (tid < ASEEN / 32) s_seen[tid] = 0u;
+    if (tid == 0) nxt = atomicAdd(a.ctl, 1);
+    __syncthreads();
     for (;;) {
-        if (tid == 0) s_task = astep_next(a);
+        if (tid == 0) s_task = astep_take(a, nxt, s_seen);
         __syncthreads();
         const int4 tk = s_task;
         if (tk.x < 0) break;
@@ -931,44 +953,49 @@ __global__ void __launch_bounds__(ASTEP_T, CCFMM_P2P_MINB) k_astep(const AStepAr
                  i < min(a.N, (long long)(tk.y + 1) * ACHUNK); i += ASTEP_T)
                 permute_one<float>(i, a.mom, a.perm, a.A, a.B);
             break;
-        case AT_P2M: {
-            const int li = tk.y + w;
-            const bool live = li < tk.z;
-            const int c = live ? a.leaves[li] : 0;
-            const int s0 = live ? a.p0[c] : 0, s1 = live ? s0 + a.np[c] : 0;
-            p2m_run<float>(P, a.KP, live, s0, s1, a.A, a.B, a.Q + (long long)c * a.KP,
-                           *reinterpret_cast<P2MScratch<float> *>(smraw));
+        case AT_P2M:
+            for (int r = 0; r < ACELLS; r += P2M_W) {
+                const int li = tk.y + r + w;
+                const bool live = li < tk.z;
+                const int c = live ? a.leaves[li] : 0;
+                const int s0 = live ? a.p0[c] : 0, s1 = live ? s0 + a.np[c] : 0;
+                p2m_run<float>(P, a.KP, live, s0, s1, a.A, a.B, a.Q + (long long)c * a.KP,
+                               *reinterpret_cast<P2MScratch<float> *>(smraw));
+                __syncthreads();
+            }
             break;
-        }
-        case AT_M2M: {
-            const int idx = tk.y + w;
-            if (idx < tk.z)
+        case AT_M2M:
+            for (int idx = tk.y + w; idx < min(tk.z, tk.y + ACELLS); idx += AW) {
                 am2m_cell<float>(P, a.KP, a.lvl_cells[idx], a.smp, a.lev, a.ch, a.geo, a.shift,
                                  a.Q, reinterpret_cast<AM2MWarp<float> *>(smraw)[w]);
+                __syncwarp();
+            }
             break;
-        }
-        case AT_FOLD: {
-            const int c = tk.y + w;
-            if (c < a.nc)
+        case AT_FOLD:
+            for (int c = tk.y + w; c < min(a.nc, tk.y + ACELLS); c += AW) {
                 afold_cell(P, a.KP, KRP, c, a.Q, a.Qr, reinterpret_cast<float *>(smraw) + w * AF_ROW);
+                __syncwarp();
+            }
             break;
-        }
         case AT_M2L_BIG:
             am2l_big_item<KRP>(P, a.it64[tk.y], a.pt, a.ps, a.rpow, a.D, a.ldD, a.itr, a.Qr,
                                a.VFr, smraw);
             break;
         case AT_M2L_SMALL:
-            am2l_small_items<KRP>(P, a.it16, a.n16, tk.y, a.pt, a.ps, a.rpow, a.D, a.ldD, a.itr,
-                                  a.Qr, a.VFr, smraw);
+            for (int g = tk.y; g < min(tk.z, tk.y + AGROUPS); ++g) {
+                am2l_small_items<KRP>(P, a.it16, a.n16, g, a.pt, a.ps, a.rpow, a.D, a.ldD, a.itr,
+                                      a.Qr, a.VFr, smraw);
+                __syncthreads();
+            }
             break;
-        case AT_L2L: {
-            const int idx = tk.y + w;
-            if (idx < tk.z)
+        case AT_L2L:
+            for (int idx = tk.y + w; idx < min(tk.z, tk.y + ACELLS); idx += AW) {
                 al2l_cell<float, true>(P, a.KP, KRP, a.lvl_cells[idx], a.smp, a.lev, a.par, a.ic,
                                        a.geo, a.shift, a.harm, a.VFr, a.V,
                                        reinterpret_cast<AL2LWarp *>(smraw)[w]);
+                __syncwarp();
+            }
             break;
-        }
         case AT_P2P: {
             const int c = a.leaves[tk.y];
             const double4 cc = a.cen[c];
@@ -979,13 +1006,13 @@ __global__ void __launch_bounds__(ASTEP_T, CCFMM_P2P_MINB) k_astep(const AStepAr
                                                              a.A, a.B, a.H);
             break;
         }
-        case AT_L2P: {
-            const int li = tk.y + w;
-            if (li < tk.z)
+        case AT_L2P:
+            for (int li = tk.y + w; li < min(tk.z, tk.y + ACELLS); li += L2P_W) {
                 al2p_leaf<float, P>(a.KP, a.leaves[li], a.p0, a.np, a.A, a.V, a.H,
                                     reinterpret_cast<float *>(smraw) + w * nterms(PMAX));
+                __syncwarp();
+            }
             break;
-        }
         case AT_UNPERM:
             for (long long i = (long long)tk.y * ACHUNK + tid;
                  i < min(a.N, (long long)(tk.y + 1) * ACHUNK); i += ASTEP_T)
@@ -1750,17 +1777,18 @@ ccfmm_status enable_persistent(ccfmm_adaptive_t h)
         const int a = h->lvl_off[l], b = h->lvl_off[l + 1];
         if (b <= a) return;
         far.emplace_back();
-        for (int i = a; i < b; i += AW) far.back().push_back(make_int3(type, i, b));
+        for (int i = a; i < b; i += ACELLS) far.back().push_back(make_int3(type, i, b));
     };
     far.emplace_back();
-    for (int li = 0; li < h->nleaf; li += P2M_W) far.back().push_back(make_int3(AT_P2M, li, h->nleaf));
+    for (int li = 0; li < h->nleaf; li += ACELLS) far.back().push_back(make_int3(AT_P2M, li, h->nleaf));
     for (int l = h->maxL - 1; l >= 0; --l) level_tasks(AT_M2M, l);
     far.emplace_back();
-    for (int c = 0; c < h->nc; c += AW) far.back().push_back(make_int3(AT_FOLD, c, h->nc));
+    for (int c = 0; c < h->nc; c += ACELLS) far.back().push_back(make_int3(AT_FOLD, c, h->nc));
     const size_t m2l_phase = far.size();
     far.emplace_back();
     for (int i = 0; i < h->n64; ++i) far.back().push_back(make_int3(AT_M2L_BIG, i, 0));
-    for (int g = 0; g < (h->n16 + 3) / 4; ++g) far.back().push_back(make_int3(AT_M2L_SMALL, g, 0));
+    const int ng = (h->n16 + 3) / 4;
+    for (int g = 0; g < ng; g += AGROUPS) far.back().push_back(make_int3(AT_M2L_SMALL, g, ng));
     for (int l = 0; l <= h->maxL; ++l) level_tasks(AT_L2L, l);
     const int ph_p2p = phase();
     int prev = ph_perm, ph_m2l = -1;
@@ -1776,7 +1804,7 @@ ccfmm_status enable_persistent(ccfmm_adaptive_t h)
     }
     for (; next < h->nleaf; ++next) add(AT_P2P, ph_p2p, next, 0, ph_perm, -1);
     const int ph_l2p = phase();
-    for (int li = 0; li < h->nleaf; li += L2P_W) add(AT_L2P, ph_l2p, li, h->nleaf, prev, ph_p2p);
+    for (int li = 0; li < h->nleaf; li += ACELLS) add(AT_L2P, ph_l2p, li, h->nleaf, prev, ph_p2p);
     const int ph_un = phase();
     for (long long i = 0; i < nch; ++i) add(AT_UNPERM, ph_un, i, 0, ph_l2p, -1);
     const int ph_e = phase();
