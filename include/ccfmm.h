@@ -582,6 +582,36 @@ ccfmm_status fmm_adaptive_expansions(ccfmm_adaptive_t a, double *Q_out, double *
 
 void fmm_adaptive_destroy(ccfmm_adaptive_t a);
 
+/* The persistent step's task queue for a forest of the given shape, as
+ * fmm_adaptive_create_ex with opts->persistent builds it (host only, no GPU;
+ * for inspection and tests).
+ *   N, nsamples, nleaf, ncells  dipoles, samples, leaf cells, cells
+ *   max_level      deepest level; level_offsets: max_level + 2 offsets of
+ *                  each level's cells in the level-ordered cell list
+ *                  (nondecreasing, 0 first, ncells last)
+ *   n_big, n_small M2L items of more than 16 pairs / of at most 16
+ *   tasks          4 int32 per task in queue order: type | phase << 8, y, z,
+ *                  (wait1 + 1) | (wait2 + 1) << 16 (0: no wait); types 0..11
+ *                  = rotation, permutation, P2M, M2M, fold, big M2L item,
+ *                  small M2L items, L2L, near field, L2P, unpermute, energy;
+ *                  a tile of a warp-per-cell stage is [y, min(z, y + tiles[1]))
+ *                  of its list (leaves, the level's cells, cells; small M2L:
+ *                  groups of four items [y, min(z, y + tiles[2]))), a dipole
+ *                  chunk is [y tiles[0], (y + 1) tiles[0]), a big item, a near-
+ *                  field leaf or a sample is y.  May be NULL (count only).
+ *   capacity       tasks room (in tasks); *ntasks receives the count
+ *   need           tasks of each phase (may be NULL); need_capacity its room;
+ *                  *nphases receives the phase count
+ *   tiles          3 int32 (may be NULL): dipoles per chunk, cells per tile,
+ *                  small-item groups per tile
+ * Errors: CCFMM_ERR_ARG on an inconsistent shape; nothing is written past a
+ * capacity (the counts are still returned). */
+ccfmm_status fmm_adaptive_queue(int64_t N, int32_t nsamples, int32_t nleaf, int32_t ncells,
+                                int32_t max_level, const int32_t *level_offsets, int32_t n_big,
+                                int32_t n_small, int32_t *tasks, int64_t capacity,
+                                int64_t *ntasks, int32_t *need, int32_t need_capacity,
+                                int32_t *nphases, int32_t *tiles);
+
 #ifdef __cplusplus
 }
 #endif

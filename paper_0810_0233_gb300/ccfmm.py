@@ -141,6 +141,10 @@ def load():
             "fmm_adaptive_pairs": (_int, [_vp, _int, _vp, _i64, ctypes.POINTER(_i64)]),
             "fmm_adaptive_expansions": (_int, [_vp, _vp, _vp]),
             "fmm_adaptive_destroy": (None, [_vp]),
+            "fmm_adaptive_queue": (_int, [_i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32,
+                                          _vp, _i64, ctypes.POINTER(_i64), _vp, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32), _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -708,3 +712,24 @@ class Adaptive:
         V = np.zeros((nc, K))
         _check(self._lib.fmm_adaptive_expansions(self._h, _vp(Q.ctypes.data), _vp(V.ctypes.data)))
         return Q, V
+
+
+def adaptive_queue(N, nsamples, nleaf, ncells, level_offsets, n_big, n_small):
+    """The persistent step's task queue for a forest of this shape
+    (fmm_adaptive_queue, host only): (tasks as an ntasks x 4 int32 array,
+    tasks per phase, (dipoles per chunk, cells per tile, small-item groups
+    per tile))."""
+    lib = load()
+    off = np.ascontiguousarray(np.asarray(level_offsets, np.int32))
+    nt, nph = _i64(), ctypes.c_int32()
+    args = (int(N), int(nsamples), int(nleaf), int(ncells), len(off) - 2,
+            _vp(off.ctypes.data), int(n_big), int(n_small))
+    _check(lib.fmm_adaptive_queue(*args, None, 0, ctypes.byref(nt), None, 0, ctypes.byref(nph),
+                                  None))
+    tasks = np.zeros((max(nt.value, 1), 4), np.int32)
+    need = np.zeros(max(nph.value, 1), np.int32)
+    tiles = np.zeros(3, np.int32)
+    _check(lib.fmm_adaptive_queue(*args, _vp(tasks.ctypes.data), nt.value, ctypes.byref(nt),
+                                  _vp(need.ctypes.data), nph.value, ctypes.byref(nph),
+                                  _vp(tiles.ctypes.data)))
+    return tasks[:nt.value], need[:nph.value], tuple(int(x) for x in tiles)

@@ -1751,13 +1751,19 @@ template <typename real> void enqueue_eval(ccfmm_adaptive_t h, bool rotate)
 // and the energies.  CCFMM_ASTEP_STALL=1 (tests of the time-out path) asks
 // one task more of the M2L phase than it has and lets every wait give up
 // after 2^12 polls.
-ccfmm_status enable_persistent(ccfmm_adaptive_t h)
+// Shape of a forest for the persistent step's task queue.
+struct AQShape {
+    long long N;
+    int ns, nleaf, nc, maxL, n64, n16;
+    const int *lvl_off;  // maxL + 2 offsets of each level's cells in the level-ordered list
+};
+
+// The task queue of the persistent step (k_astep) for a forest of shape q:
+// t in queue order, need[ph] = tasks of phase ph, ph_m2l = the M2L phase.
+void build_queue(const AQShape &q, std::vector<int4> &t, std::vector<int> &need, int &ph_m2l)
 {
-    if (h->dbl || !h->red || h->p < 2 || h->p > 6)
-        return afail(CCFMM_ERR_ARG, "the persistent step needs the FP32 path with the "
-                                    "tensor-core M2L (p in 2..6)");
-    std::vector<int4> t;
-    std::vector<int> need;
+    t.clear();
+    need.clear();
     auto phase = [&]() {
         need.push_back(0);
         return (int)need.size() - 1;
@@ -1766,7 +1772,7 @@ ccfmm_status enable_persistent(ccfmm_adaptive_t h)
         t.push_back(make_int4(type | (ph << 8), (int)y, (int)z, (w1 + 1) | ((w2 + 1) << 16)));
         ++need[ph];
     };
-    const long long nch = (h->N + ACHUNK - 1) / ACHUNK;
+    const long long nch = (q.N + ACHUNK - 1) / ACHUNK;
     const int ph_rot = phase();
     for (long long i = 0; i < nch; ++i) add(AT_ROT, ph_rot, i, 0, -1, -1);
     const int ph_perm = phase();
@@ -1774,24 +1780,25 @@ ccfmm_status enable_persistent(ccfmm_adaptive_t h)
     // far-chain phases: (type, y, z) of each task
     std::vector<std::vector<int3>> far;
     auto level_tasks = [&](int type, int l) {
-        const int a = h->lvl_off[l], b = h->lvl_off[l + 1];
+        const int a = q.lvl_off[l], b = q.lvl_off[l + 1];
         if (b <= a) return;
         far.emplace_back();
         for (int i = a; i < b; i += ACELLS) far.back().push_back(make_int3(type, i, b));
     };
     far.emplace_back();
-    for (int li = 0; li < h->nleaf; li += ACELLS) far.back().push_back(make_int3(AT_P2M, li, h->nleaf));
-    for (int l = h->maxL - 1; l >= 0; --l) level_tasks(AT_M2M, l);
+    for (int li = 0; li < q.nleaf; li += ACELLS) far.back().push_back(make_int3(AT_P2M, li, q.nleaf));
+    for (int l = q.maxL - 1; l >= 0; --l) level_tasks(AT_M2M, l);
     far.emplace_back();
-    for (int c = 0; c < h->nc; c += ACELLS) far.back().push_back(make_int3(AT_FOLD, c, h->nc));
+    for (int c = 0; c < q.nc; c += ACELLS) far.back().push_back(make_int3(AT_FOLD, c, q.nc));
     const size_t m2l_phase = far.size();
     far.emplace_back();
-    for (int i = 0; i < h->n64; ++i) far.back().push_back(make_int3(AT_M2L_BIG, i, 0));
-    const int ng = (h->n16 + 3) / 4;
+    for (int i = 0; i < q.n64; ++i) far.back().push_back(make_int3(AT_M2L_BIG, i, 0));
+    const int ng = (q.n16 + 3) / 4;
     for (int g = 0; g < ng; g += AGROUPS) far.back().push_back(make_int3(AT_M2L_SMALL, g, ng));
-    for (int l = 0; l <= h->maxL; ++l) level_tasks(AT_L2L, l);
+    for (int l = 0; l <= q.maxL; ++l) level_tasks(AT_L2L, l);
     const int ph_p2p = phase();
-    int prev = ph_perm, ph_m2l = -1;
+    int prev = ph_perm;
+    ph_m2l = -1;
     long long next = 0;
     const long long nf = (long long)far.size();
     for (long long k = 0; k < nf; ++k) {
@@ -1799,16 +1806,28 @@ ccfmm_status enable_persistent(ccfmm_adaptive_t h)
         if ((size_t)k == m2l_phase) ph_m2l = ph;
         for (const int3 &x : far[k]) add(x.x, ph, x.y, x.z, prev, -1);
         prev = ph;
-        for (const long long upto = (long long)h->nleaf * (k + 1) / (nf + 1); next < upto; ++next)
+        for (const long long upto = (long long)q.nleaf * (k + 1) / (nf + 1); next < upto; ++next)
             add(AT_P2P, ph_p2p, next, 0, ph_perm, -1);
     }
-    for (; next < h->nleaf; ++next) add(AT_P2P, ph_p2p, next, 0, ph_perm, -1);
+    for (; next < q.nleaf; ++next) add(AT_P2P, ph_p2p, next, 0, ph_perm, -1);
     const int ph_l2p = phase();
-    for (int li = 0; li < h->nleaf; li += ACELLS) add(AT_L2P, ph_l2p, li, h->nleaf, prev, ph_p2p);
+    for (int li = 0; li < q.nleaf; li += ACELLS) add(AT_L2P, ph_l2p, li, q.nleaf, prev, ph_p2p);
     const int ph_un = phase();
     for (long long i = 0; i < nch; ++i) add(AT_UNPERM, ph_un, i, 0, ph_l2p, -1);
     const int ph_e = phase();
-    for (int i = 0; i < h->ns; ++i) add(AT_ENERGY, ph_e, i, 0, ph_un, -1);
+    for (int i = 0; i < q.ns; ++i) add(AT_ENERGY, ph_e, i, 0, ph_un, -1);
+}
+
+ccfmm_status enable_persistent(ccfmm_adaptive_t h)
+{
+    if (h->dbl || !h->red || h->p < 2 || h->p > 6)
+        return afail(CCFMM_ERR_ARG, "the persistent step needs the FP32 path with the "
+                                    "tensor-core M2L (p in 2..6)");
+    std::vector<int4> t;
+    std::vector<int> need;
+    int ph_m2l = -1;
+    build_queue(AQShape{h->N, h->ns, h->nleaf, h->nc, h->maxL, h->n64, h->n16, h->lvl_off.data()},
+                t, need, ph_m2l);
     if ((long long)t.size() > INT32_MAX / 2 || need.size() > 0xfffe)
         return afail(CCFMM_ERR_ARG, "forest too large for the persistent step's task queue");
     const char *e = getenv("CCFMM_ASTEP_STALL");
@@ -1886,6 +1905,46 @@ ccfmm_status run(ccfmm_adaptive_t h, int rotate, double *H_out, double *E_out)
 
 // ================================================================== C-ABI
 extern "C" {
+
+ccfmm_status fmm_adaptive_queue(int64_t N, int32_t nsamples, int32_t nleaf, int32_t ncells,
+                                int32_t max_level, const int32_t *level_offsets, int32_t n_big,
+                                int32_t n_small, int32_t *tasks, int64_t capacity,
+                                int64_t *ntasks, int32_t *need, int32_t need_capacity,
+                                int32_t *nphases, int32_t *tiles)
+{
+    set_last_error("");
+    if (!ntasks || !nphases || !level_offsets) return afail(CCFMM_ERR_ARG, "NULL argument");
+    if (N < 1 || nsamples < 1 || nleaf < 1 || ncells < nleaf || max_level < 0 ||
+        max_level > AMAXL || n_big < 0 || n_small < 0 || capacity < 0 || need_capacity < 0)
+        return afail(CCFMM_ERR_ARG, "bad forest shape");
+    if (level_offsets[0] != 0 || level_offsets[max_level + 1] != ncells)
+        return afail(CCFMM_ERR_ARG, "level offsets must run from 0 to ncells");
+    for (int l = 0; l <= max_level; ++l)
+        if (level_offsets[l + 1] < level_offsets[l])
+            return afail(CCFMM_ERR_ARG, "level offsets must not decrease");
+    std::vector<int4> t;
+    std::vector<int> need_v;
+    int ph_m2l = -1;
+    build_queue(AQShape{N, nsamples, nleaf, ncells, max_level, n_big, n_small, level_offsets},
+                t, need_v, ph_m2l);
+    *ntasks = (int64_t)t.size();
+    *nphases = (int32_t)need_v.size();
+    if (tasks)
+        for (size_t i = 0; i < t.size() && (int64_t)i < capacity; ++i) {
+            tasks[4 * i] = t[i].x;
+            tasks[4 * i + 1] = t[i].y;
+            tasks[4 * i + 2] = t[i].z;
+            tasks[4 * i + 3] = t[i].w;
+        }
+    if (need)
+        for (size_t i = 0; i < need_v.size() && (int64_t)i < need_capacity; ++i) need[i] = need_v[i];
+    if (tiles) {
+        tiles[0] = ACHUNK;
+        tiles[1] = ACELLS;
+        tiles[2] = AGROUPS;
+    }
+    return CCFMM_OK;
+}
 
 void fmm_adaptive_destroy(ccfmm_adaptive_t h)
 {
