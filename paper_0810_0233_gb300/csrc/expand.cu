@@ -1,7 +1,8 @@
 // expand.cu -- Cartesian expansion operators of Sec. III on the GPU:
 //   F table of Eqs. Dn / Dnr and the derivative tensors D_n per distinct
 //   (level, far offset), P2M (Eq. multipolemoments), M2M (Eq. momentshift),
-//   L2L (Eq. taylorshift) and L2P (Eq. H, H = -grad V).
+//   L2L (Eq. taylorshift) and L2P (Eq. H, H = -grad V).  P2M's body
+//   (p2m_run) is in stages.cuh.
 #include "ccfmm_dev.cuh"
 #include "stages.cuh"
 

@@ -1,4 +1,6 @@
 // m2l.cu -- M2L (Eq. taylorcalc) as offset-grouped dense contractions.
+// (The adaptive tree's tensor-core item bodies and the moment fold are in
+// stages.cuh; their kernels are here.)
 //
 // V_n = (-1)^|n| sum_k D_{n+k}(c) Q_k, c = field-cell centre - partner centre,
 // 1 <= |n|, |k| <= p: the square truncation, or, on request, only the terms

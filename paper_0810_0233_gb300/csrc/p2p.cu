@@ -1,7 +1,8 @@
 // p2p.cu -- near field (Eq. H2 as read: field of dipole j at i,
 // [3 (m_j.u) u - m_j] / r^3) over each leaf's nearPartners (Appendix,
 // updateField), the final unpermute + energy (E = -1/2 sum m.H), and the
-// FP64 direct sum used to measure the error of the fast method.
+// FP64 direct sum used to measure the error of the fast method.  The leaf
+// body (p2p_leaf), the pair loops and the L2P sums are in stages.cuh.
 #include "ccfmm_dev.cuh"
 #include "stages.cuh"
 
