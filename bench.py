@@ -262,7 +262,7 @@ def run_reference(args):
                           "fields/s over those samples (no rotation)")
         config["l2"] = "not applicable (CPU)"
     else:
-        pos, mom = workload(args.workload)
+        pos, mom = workload(args.workload, args.n)
         for it in range(args.warmup + args.steps):
             res = cpu_oracle_sample(pos, mom, p, theta, nleaves=256, seed=100 + it)
             if it >= args.warmup:
